@@ -1,0 +1,182 @@
+/*
+ * psgld.h -- C ABI of the GB300 (sm_103a) implementation of Parallel SGLD
+ * (PSGLD) for matrix factorisation: Simsekli, Koptagel, Guldas, Cemgil,
+ * Oztoprak, Birbil, "Parallel Stochastic Gradient Markov Chain Monte Carlo
+ * for Matrix Factorisation Models" (2015).
+ *
+ * Model (Sec. 1 Eq. generative, Sec. 4 Eq. tweedienmf): V (I x J) ~ W H with
+ * W (I x K), H (K x J); v_ij ~ Tweedie(mean sum_k w_ik h_kj, dispersion phi,
+ * power p).  The paper writes the power as beta on the beta-divergence; the
+ * two are related by p = 2 - beta (p = 0 Gaussian, 1 Poisson, 2 gamma,
+ * 1 < p < 2 compound Poisson, 3 inverse Gaussian).
+ *
+ * Sampler (Sec. 3 Eq. psgld_w, Eq. psgld_h, Algorithm 1): [I] and [J] are cut
+ * into B pieces; block (r, c) is row piece r x column piece c.  At iteration t
+ * (1-based) the part holds the B blocks (r, (r + (t-1) mod B) mod B); every
+ * block of the part updates its W rows and H columns at once, from the
+ * factors of iteration t-1:
+ *   w_ik += eps_t (S_t sum_{j in block} dlog p(v_ij)/dw_ik + dlog p(w_ik)/dw_ik)
+ *           + sqrt(2 eps_t) z,   z ~ N(0, 1)
+ * and the same for h_kj; S_t = N / |Pi_t| (observed entries over observed
+ * entries of the part).  Non-negative models (exponential priors) mirror the
+ * result, w <- |w| (Sec. 3.2).  A sweep is B consecutive iterations; together
+ * they visit every block once.
+ *
+ * Conventions for every call:
+ *   - Pointers named *_dev must be device memory of the context's GPU; pointers
+ *     named *_host must be host memory.  Pointers named plainly (no suffix)
+ *     may be either: the library copies through unified addressing.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls that take a stream only enqueue work on it unless they
+ *     return a host value, in which case they synchronise that stream.
+ *   - No call is thread-safe on one context; distinct contexts are
+ *     independent.  Nothing throws across the ABI; every failure returns a
+ *     negative psgld_status and records a message for psgld_last_error().
+ *   - All device memory the library allocates belongs to the context and is
+ *     freed by psgld_destroy().  Caller buffers stay the caller's.
+ */
+#ifndef PSGLD_H
+#define PSGLD_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define PSGLD_API __attribute__((visibility("default")))
+#else
+#define PSGLD_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct psgld_ctx psgld_ctx;
+
+typedef enum {
+    PSGLD_OK = 0,
+    PSGLD_ERR_ARG = -1,     /* invalid argument or input data */
+    PSGLD_ERR_OOM = -2,     /* device allocation failed */
+    PSGLD_ERR_CUDA = -3,    /* a CUDA runtime call failed */
+    PSGLD_ERR_STATE = -4,   /* call not valid in the current state */
+    PSGLD_ERR_TIMEOUT = -5  /* a bounded device wait ran out */
+} psgld_status;
+
+/* Prior families.  Exponential priors (Sec. 4, Eq. tweedienmf) make the
+ * model non-negative and turn on mirroring (Sec. 3.2).  Gaussian priors give
+ * the unconstrained BPMF-like model the paper names in Sec. 1. */
+typedef enum { PSGLD_PRIOR_EXPONENTIAL = 0, PSGLD_PRIOR_GAUSSIAN = 1 } psgld_prior_kind;
+
+typedef struct {
+    int32_t kind;             /* psgld_prior_kind */
+    double lambda_w, lambda_h; /* exponential rates (kind 0), > 0 */
+    double sigma_w, sigma_h;   /* Gaussian standard deviations (kind 1), > 0 */
+} psgld_prior;
+
+/* Step-size rule (Sec. 2 Eq. eps; Sec. 4.1 uses eps_t = (a/t)^b). */
+typedef enum { PSGLD_EPS_FIXED = 0, PSGLD_EPS_POLY = 1 } psgld_eps_mode;
+/* Likelihood scale S_t: N/|Pi_t| as in Eq. psgld_1, or the block count B. */
+typedef enum { PSGLD_SCALE_N_OVER_PART = 0, PSGLD_SCALE_B = 1 } psgld_scale_mode;
+
+typedef struct {
+    uint64_t seed;            /* Philox key of the Langevin noise */
+    int32_t eps_mode;         /* psgld_eps_mode */
+    double eps;               /* fixed step (eps_mode 0), > 0 */
+    double eps_a, eps_b;      /* eps_t = (a/t)^b (eps_mode 1), a > 0, b in (0.5, 1] */
+    int32_t scale_mode;       /* psgld_scale_mode */
+    double mu_min;            /* lower clamp of mu inside mu^(-p) when p > 0 */
+    int32_t freeze_W;         /* 1: W is held fixed */
+    int32_t freeze_H;         /* 1: H is held fixed */
+    int64_t burn_in_sweeps;   /* sweeps discarded before posterior sums start */
+    int32_t use_graphs;       /* 1: each sweep replays one captured CUDA graph */
+} psgld_options;
+
+/* Defaults: seed 0, fixed eps 1e-4, a = 0.01, b = 0.51, scale N/|Pi_t|,
+ * mu_min 1e-10, nothing frozen, no burn-in, graphs on. */
+PSGLD_API void psgld_default_options(psgld_options *opt_host);
+
+/* Create a context on the current CUDA device.
+ * I, J >= 1; 1 <= B <= min(I, J); 1 <= K <= 512; phi > 0; tweedie_p not in
+ * (0, 1) (no Tweedie model exists for 1 < beta < 2, Sec. 4); I, J and
+ * B * max(I, J) below 2^31.
+ * *out receives the new context, or NULL on failure. */
+PSGLD_API psgld_status psgld_create(int64_t I, int64_t J, int32_t K, int32_t B,
+                          double tweedie_p, double phi,
+                          const psgld_prior *prior_host, psgld_ctx **out);
+
+PSGLD_API psgld_status psgld_set_options(psgld_ctx *ctx, const psgld_options *opt_host);
+
+/* Observed entries in coordinate form: i[n] in [0, I), j[n] in [0, J),
+ * v[n] (float), n < nnz.  Pairs must be unique; non-negative models require
+ * v >= 0.  The library builds its own part-major layouts on the device
+ * (rows of each part sorted by column, columns of each part sorted by row)
+ * and keeps no reference to the caller's arrays after the call returns.
+ * Synchronises `stream`.  Resets the iteration counter and posterior sums. */
+PSGLD_API psgld_status psgld_set_data_coo(psgld_ctx *ctx, int64_t nnz, const int32_t *i,
+                                const int32_t *j, const float *v, void *stream);
+
+/* Dense V (every entry observed), row-major with leading dimension ld >= J.
+ * Same effect as psgld_set_data_coo over all I*J entries. */
+PSGLD_API psgld_status psgld_set_data_dense(psgld_ctx *ctx, const float *V, int64_t ld,
+                                  void *stream);
+
+/* Factors in: W is I x K row-major; Ht is H transposed, J x K row-major.
+ * Non-negative models require all entries >= 0. */
+PSGLD_API psgld_status psgld_set_factors(psgld_ctx *ctx, const float *W, const float *Ht,
+                               void *stream);
+/* Factors out, same layouts.  Either pointer may be NULL. */
+PSGLD_API psgld_status psgld_get_factors(psgld_ctx *ctx, float *W, float *Ht, void *stream);
+
+/* One PSGLD iteration t (1-based): Algorithm 1's loop body for part
+ * Pi_t, on `stream`.  Does not touch the posterior sums. */
+PSGLD_API psgld_status psgld_part_step(psgld_ctx *ctx, int64_t t, void *stream);
+
+/* n_sweeps sweeps of B iterations each, continuing from the iteration
+ * counter, which must sit at a sweep boundary (a multiple of B).  After each
+ * sweep past burn-in the FP64 posterior sums of W, W^2, H, H^2 are updated. */
+PSGLD_API psgld_status psgld_sweep(psgld_ctx *ctx, int32_t n_sweeps, void *stream);
+
+/* Monte Carlo posterior mean and variance of W (I x K) and H^T (J x K), FP64,
+ * over the samples kept so far (population variance).  Any output pointer may
+ * be NULL.  Synchronises the context's last stream. */
+PSGLD_API psgld_status psgld_posterior_mean(psgld_ctx *ctx, double *Wmean_host,
+                                  double *Wvar_host, double *Hmean_host,
+                                  double *Hvar_host, int64_t *n_samples_host);
+
+/* -(1/phi) sum over observed entries of d_beta(v || mu) at the current
+ * factors (the log-likelihood up to the mu-free normaliser, Sec. 4), FP64. */
+PSGLD_API psgld_status psgld_log_lik(psgld_ctx *ctx, double *out_host, void *stream);
+
+/* sqrt(mean over observed entries of (v - mu)^2), FP64; mu from the current
+ * factors (use_posterior_mean = 0) or from the posterior means (1). */
+PSGLD_API psgld_status psgld_rmse(psgld_ctx *ctx, int32_t use_posterior_mean,
+                        double *out_host, void *stream);
+
+/* ---- introspection: the schedule and layouts, for bit-exact checks ------ */
+
+/* Piece boundaries (Definition 1): row_starts[r] = floor(r I / B) for
+ * r = 0..B, the same for columns.  Host arrays of B+1 entries. */
+PSGLD_API psgld_status psgld_piece_bounds(const psgld_ctx *ctx, int64_t *row_starts_host,
+                                int64_t *col_starts_host);
+/* Part of iteration t (Definition 2): col_piece_host[r] is the column piece
+ * joined with row piece r, r = 0..B-1. */
+PSGLD_API psgld_status psgld_part_schedule(const psgld_ctx *ctx, int64_t t,
+                                 int32_t *col_piece_host);
+/* Row-major layout of part s (0 <= s < B): row_ptr_host[0..I] offsets
+ * (relative to the part's first entry) and the column of every entry of the
+ * part, rows in order, columns ascending.  cols_host may be NULL to query the
+ * count, which is written to *n_entries_host. */
+PSGLD_API psgld_status psgld_part_layout(psgld_ctx *ctx, int32_t s, int32_t *row_ptr_host,
+                               int32_t *cols_host, int64_t *n_entries_host);
+/* Last completed iteration t (0 before the first). */
+PSGLD_API int64_t psgld_iterations_done(const psgld_ctx *ctx);
+
+/* Message of the last failure on this context ("" if none).  Valid until the
+ * next call on the context. */
+PSGLD_API const char *psgld_last_error(const psgld_ctx *ctx);
+
+PSGLD_API void psgld_destroy(psgld_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

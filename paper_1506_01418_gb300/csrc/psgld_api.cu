@@ -1,0 +1,486 @@
+// psgld_api.cu -- the C ABI declared in include/psgld.h.
+//
+// The context owns every device buffer (factors, layouts, scratch, FP64
+// posterior sums).  Sweeps are either launched kernel by kernel or, with
+// use_graphs, replayed from a CUDA graph holding the B part-step launches of
+// one sweep (plus the posterior accumulation and the iteration-counter
+// advance).  The graph reads the iteration index t from device memory, so
+// one captured graph serves every sweep; one graph is kept per parity of the
+// ping-pong factor buffers and per accumulate / no-accumulate variant.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "psgld_internal.cuh"
+
+namespace psgld {
+
+int reduce_blocks();
+
+psgld_status fail(psgld_ctx *c, psgld_status s, const std::string &msg)
+{
+    if (c) c->err = msg;
+    return s;
+}
+
+psgld_status cuda_fail(psgld_ctx *c, cudaError_t e, const char *what)
+{
+    cudaGetLastError();
+    return fail(c, PSGLD_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+namespace {
+
+__global__ void dense_to_coo_kernel(const float *__restrict__ V, int64_t I, int64_t J, int64_t ld,
+                                    int32_t *__restrict__ ii, int32_t *__restrict__ jj,
+                                    float *__restrict__ vv)
+{
+    for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < I * J;
+         a += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = a / J, j = a - i * J;
+        ii[a] = (int32_t)i;
+        jj[a] = (int32_t)j;
+        vv[a] = V[i * ld + j];
+    }
+}
+
+__global__ void check_factors_kernel(const float *__restrict__ x, int64_t n, int nonneg, int *flag)
+{
+    for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < n;
+         a += (int64_t)gridDim.x * blockDim.x) {
+        const float v = x[a];
+        if (!isfinite(v) || (nonneg && v < 0.0f)) atomicOr(flag, 8);
+    }
+}
+
+__global__ void set_t_kernel(int64_t *t, int64_t v)
+{
+    if (threadIdx.x == 0) *t = v;
+}
+
+void destroy_graphs(psgld_ctx *c)
+{
+    for (auto &row : c->graph)
+        for (auto &g : row)
+            if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+    for (auto &g : c->graph_acc)
+        if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+}
+
+psgld_status zero_posterior(psgld_ctx *c, cudaStream_t st)
+{
+    const size_t nW = sizeof(double) * (size_t)(c->I * c->ldk);
+    const size_t nH = sizeof(double) * (size_t)(c->J * c->ldk);
+    PSGLD_CK(c, cudaMemsetAsync(c->sW.s, 0, nW, st));
+    PSGLD_CK(c, cudaMemsetAsync(c->sW.s2, 0, nW, st));
+    PSGLD_CK(c, cudaMemsetAsync(c->sH.s, 0, nH, st));
+    PSGLD_CK(c, cudaMemsetAsync(c->sH.s2, 0, nH, st));
+    c->n_samples = 0;
+    c->sweeps_done = 0;
+    c->t_done = 0;
+    return PSGLD_OK;
+}
+
+template <typename T>
+psgld_status alloc(psgld_ctx *c, T **p, int64_t n, bool zero = true)
+{
+    if (n <= 0) n = 1;
+    cudaError_t e = cudaMalloc((void **)p, sizeof(T) * (size_t)n);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return fail(c, PSGLD_ERR_OOM, "device allocation failed");
+    }
+    if (zero) PSGLD_CK(c, cudaMemset(*p, 0, sizeof(T) * (size_t)n));
+    return PSGLD_OK;
+}
+
+bool ready(psgld_ctx *c, psgld_status *s)
+{
+    if (!c->has_data) { *s = fail(c, PSGLD_ERR_STATE, "no data set"); return false; }
+    if (!c->has_factors) { *s = fail(c, PSGLD_ERR_STATE, "no factors set"); return false; }
+    return true;
+}
+
+// Capture one sweep (B part-steps, optional accumulate, t advance) as a graph.
+psgld_status capture_sweep(psgld_ctx *c, bool acc, cudaGraphExec_t *out)
+{
+    cudaStream_t cs = c->capture_stream;
+    const int w0 = c->wcur, h0 = c->hcur;
+    PSGLD_CK(c, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    psgld_status s = PSGLD_OK;
+    for (int b = 0; b < c->B && s == PSGLD_OK; ++b)
+        s = launch_part_step(c, b + 1, c->t_dev, b + 1, cs);
+    if (s == PSGLD_OK && acc) s = launch_accumulate(c, cs);
+    if (s == PSGLD_OK) s = launch_advance_t(c, c->B, cs);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(cs, &g);
+    c->wcur = w0;
+    c->hcur = h0;
+    if (s != PSGLD_OK) { if (g) cudaGraphDestroy(g); return s; }
+    if (e != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_fail(c, e, "cudaStreamEndCapture"); }
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphInstantiate");
+    return PSGLD_OK;
+}
+
+}  // namespace
+}  // namespace psgld
+
+using namespace psgld;
+
+extern "C" {
+
+void psgld_default_options(psgld_options *o)
+{
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->seed = 0;
+    o->eps_mode = PSGLD_EPS_FIXED;
+    o->eps = 1e-4;
+    o->eps_a = 0.01;
+    o->eps_b = 0.51;
+    o->scale_mode = PSGLD_SCALE_N_OVER_PART;
+    o->mu_min = 1e-10;
+    o->freeze_W = 0;
+    o->freeze_H = 0;
+    o->burn_in_sweeps = 0;
+    o->use_graphs = 1;
+}
+
+psgld_status psgld_create(int64_t I, int64_t J, int32_t K, int32_t B, double tweedie_p, double phi,
+                          const psgld_prior *prior, psgld_ctx **out)
+{
+    if (!out) return PSGLD_ERR_ARG;
+    *out = nullptr;
+    if (!prior) return PSGLD_ERR_ARG;
+    if (I < 1 || J < 1 || I >= (1ll << 31) || J >= (1ll << 31)) return PSGLD_ERR_ARG;
+    if (K < 1 || K > kMaxK) return PSGLD_ERR_ARG;
+    if (B < 1 || B > std::min(I, J)) return PSGLD_ERR_ARG;
+    if ((int64_t)B * std::max(I, J) >= (1ll << 31)) return PSGLD_ERR_ARG;
+    if (!(phi > 0.0) || !std::isfinite(phi) || !std::isfinite(tweedie_p)) return PSGLD_ERR_ARG;
+    if (tweedie_p > 0.0 && tweedie_p < 1.0) return PSGLD_ERR_ARG;
+    if (prior->kind == PSGLD_PRIOR_EXPONENTIAL) {
+        if (!(prior->lambda_w > 0.0) || !(prior->lambda_h > 0.0)) return PSGLD_ERR_ARG;
+    } else if (prior->kind == PSGLD_PRIOR_GAUSSIAN) {
+        if (!(prior->sigma_w > 0.0) || !(prior->sigma_h > 0.0)) return PSGLD_ERR_ARG;
+    } else {
+        return PSGLD_ERR_ARG;
+    }
+    psgld_ctx *c = new (std::nothrow) psgld_ctx();
+    if (!c) return PSGLD_ERR_OOM;
+    c->I = I; c->J = J; c->K = K; c->B = B;
+    c->ngroups = (K + 3) / 4;
+    c->ldk = 4 * c->ngroups;
+    c->p = tweedie_p;
+    c->phi = phi;
+    c->prior = *prior;
+    psgld_default_options(&c->opt);
+    cudaGetDevice(&c->device);
+    psgld_status s = PSGLD_OK;
+    for (int b = 0; b < 2 && s == PSGLD_OK; ++b) {
+        s = alloc(c, &c->W[b], I * c->ldk);
+        if (s == PSGLD_OK) s = alloc(c, &c->Ht[b], J * c->ldk);
+    }
+    if (s == PSGLD_OK) s = alloc(c, &c->sW.s, I * c->ldk);
+    if (s == PSGLD_OK) s = alloc(c, &c->sW.s2, I * c->ldk);
+    if (s == PSGLD_OK) s = alloc(c, &c->sH.s, J * c->ldk);
+    if (s == PSGLD_OK) s = alloc(c, &c->sH.s2, J * c->ldk);
+    if (s == PSGLD_OK) s = alloc(c, &c->red, reduce_blocks());
+    if (s == PSGLD_OK) s = alloc(c, &c->flag, 1);
+    if (s == PSGLD_OK) s = alloc(c, &c->t_dev, 1);
+    if (s == PSGLD_OK && cudaMallocHost((void **)&c->red_host, sizeof(double) * reduce_blocks()) != cudaSuccess)
+        s = fail(c, PSGLD_ERR_OOM, "pinned allocation failed");
+    if (s == PSGLD_OK && cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking) != cudaSuccess)
+        s = fail(c, PSGLD_ERR_CUDA, "stream creation failed");
+    if (s != PSGLD_OK) {
+        psgld_destroy(c);
+        cudaGetLastError();
+        return s;
+    }
+    *out = c;
+    return PSGLD_OK;
+}
+
+psgld_status psgld_set_options(psgld_ctx *c, const psgld_options *o)
+{
+    if (!c || !o) return PSGLD_ERR_ARG;
+    if (o->eps_mode == PSGLD_EPS_FIXED) {
+        if (!(o->eps > 0.0) || !std::isfinite(o->eps)) return fail(c, PSGLD_ERR_ARG, "eps must be > 0");
+    } else if (o->eps_mode == PSGLD_EPS_POLY) {
+        if (!(o->eps_a > 0.0) || !(o->eps_b > 0.0)) return fail(c, PSGLD_ERR_ARG, "eps_a, eps_b must be > 0");
+    } else {
+        return fail(c, PSGLD_ERR_ARG, "unknown eps_mode");
+    }
+    if (o->scale_mode != PSGLD_SCALE_N_OVER_PART && o->scale_mode != PSGLD_SCALE_B)
+        return fail(c, PSGLD_ERR_ARG, "unknown scale_mode");
+    if (!(o->mu_min > 0.0)) return fail(c, PSGLD_ERR_ARG, "mu_min must be > 0");
+    if (o->burn_in_sweeps < 0) return fail(c, PSGLD_ERR_ARG, "burn_in_sweeps must be >= 0");
+    c->opt = *o;
+    destroy_graphs(c);
+    return PSGLD_OK;
+}
+
+psgld_status psgld_set_data_coo(psgld_ctx *c, int64_t nnz, const int32_t *i, const int32_t *j,
+                                const float *v, void *stream)
+{
+    if (!c) return PSGLD_ERR_ARG;
+    if (nnz < 0 || nnz >= (1ll << 31)) return fail(c, PSGLD_ERR_ARG, "nnz out of range");
+    if (nnz > 0 && (!i || !j || !v)) return fail(c, PSGLD_ERR_ARG, "null entry array");
+    cudaStream_t st = (cudaStream_t)stream;
+    destroy_graphs(c);
+    int32_t *di = nullptr, *dj = nullptr;
+    float *dv = nullptr;
+    psgld_status s = alloc(c, &di, nnz, false);
+    if (s == PSGLD_OK) s = alloc(c, &dj, nnz, false);
+    if (s == PSGLD_OK) s = alloc(c, &dv, nnz, false);
+    if (s == PSGLD_OK && nnz > 0) {
+        cudaError_t e = cudaMemcpyAsync(di, i, sizeof(int32_t) * nnz, cudaMemcpyDefault, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dj, j, sizeof(int32_t) * nnz, cudaMemcpyDefault, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dv, v, sizeof(float) * nnz, cudaMemcpyDefault, st);
+        if (e != cudaSuccess) s = cuda_fail(c, e, "copy entries");
+    }
+    if (s == PSGLD_OK) s = build_layout(c, nnz, di, dj, dv, st);
+    if (s == PSGLD_OK) s = zero_posterior(c, st);
+    if (s == PSGLD_OK) {
+        cudaError_t e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) s = cuda_fail(c, e, "sync");
+    }
+    cudaFree(di); cudaFree(dj); cudaFree(dv);
+    return s;
+}
+
+psgld_status psgld_set_data_dense(psgld_ctx *c, const float *V, int64_t ld, void *stream)
+{
+    if (!c || !V) return PSGLD_ERR_ARG;
+    if (ld < c->J) return fail(c, PSGLD_ERR_ARG, "ld < J");
+    const int64_t n = c->I * c->J;
+    if (n >= (1ll << 31)) return fail(c, PSGLD_ERR_ARG, "I*J too large for the entry layout");
+    cudaStream_t st = (cudaStream_t)stream;
+    float *dV = nullptr, *dv = nullptr;
+    int32_t *di = nullptr, *dj = nullptr;
+    psgld_status s = alloc(c, &dV, c->I * c->J, false);
+    if (s == PSGLD_OK) s = alloc(c, &di, n, false);
+    if (s == PSGLD_OK) s = alloc(c, &dj, n, false);
+    if (s == PSGLD_OK) s = alloc(c, &dv, n, false);
+    if (s == PSGLD_OK) {
+        cudaError_t e = cudaMemcpy2DAsync(dV, sizeof(float) * c->J, V, sizeof(float) * ld,
+                                          sizeof(float) * c->J, c->I, cudaMemcpyDefault, st);
+        if (e != cudaSuccess) s = cuda_fail(c, e, "copy V");
+    }
+    if (s == PSGLD_OK) {
+        dense_to_coo_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 152 * 32), 256, 0, st>>>(
+            dV, c->I, c->J, c->J, di, dj, dv);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) s = cuda_fail(c, e, "dense_to_coo");
+    }
+    cudaFree(dV);
+    dV = nullptr;
+    if (s == PSGLD_OK) {
+        // psgld_set_data_coo copies again; build directly instead
+        destroy_graphs(c);
+        s = build_layout(c, n, di, dj, dv, st);
+        if (s == PSGLD_OK) s = zero_posterior(c, st);
+        if (s == PSGLD_OK) {
+            cudaError_t e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) s = cuda_fail(c, e, "sync");
+        }
+    }
+    cudaFree(di); cudaFree(dj); cudaFree(dv);
+    return s;
+}
+
+psgld_status psgld_set_factors(psgld_ctx *c, const float *W, const float *Ht, void *stream)
+{
+    if (!c || !W || !Ht) return PSGLD_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t row = sizeof(float) * c->K, pitch = sizeof(float) * c->ldk;
+    PSGLD_CK(c, cudaMemcpy2DAsync(c->W[c->wcur], pitch, W, row, row, c->I, cudaMemcpyDefault, st));
+    PSGLD_CK(c, cudaMemcpy2DAsync(c->Ht[c->hcur], pitch, Ht, row, row, c->J, cudaMemcpyDefault, st));
+    PSGLD_CK(c, cudaMemsetAsync(c->flag, 0, sizeof(int), st));
+    const int nonneg = c->prior.kind == PSGLD_PRIOR_EXPONENTIAL;
+    check_factors_kernel<<<152 * 4, 256, 0, st>>>(c->W[c->wcur], c->I * c->ldk, nonneg, c->flag);
+    check_factors_kernel<<<152 * 4, 256, 0, st>>>(c->Ht[c->hcur], c->J * c->ldk, nonneg, c->flag);
+    PSGLD_CK(c, cudaGetLastError());
+    int h = 0;
+    PSGLD_CK(c, cudaMemcpyAsync(&h, c->flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    PSGLD_CK(c, cudaStreamSynchronize(st));
+    if (h) {
+        c->has_factors = false;
+        return fail(c, PSGLD_ERR_ARG, "factor entry not finite, or negative in a non-negative model");
+    }
+    c->has_factors = true;
+    return PSGLD_OK;
+}
+
+psgld_status psgld_get_factors(psgld_ctx *c, float *W, float *Ht, void *stream)
+{
+    if (!c) return PSGLD_ERR_ARG;
+    if (!c->has_factors) return fail(c, PSGLD_ERR_STATE, "no factors set");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t row = sizeof(float) * c->K, pitch = sizeof(float) * c->ldk;
+    if (W) PSGLD_CK(c, cudaMemcpy2DAsync(W, row, c->W[c->wcur], pitch, row, c->I, cudaMemcpyDefault, st));
+    if (Ht) PSGLD_CK(c, cudaMemcpy2DAsync(Ht, row, c->Ht[c->hcur], pitch, row, c->J, cudaMemcpyDefault, st));
+    c->last_stream = st;
+    return PSGLD_OK;
+}
+
+psgld_status psgld_part_step(psgld_ctx *c, int64_t t, void *stream)
+{
+    if (!c) return PSGLD_ERR_ARG;
+    psgld_status s;
+    if (!ready(c, &s)) return s;
+    if (t < 1) return fail(c, PSGLD_ERR_ARG, "t must be >= 1");
+    cudaStream_t st = (cudaStream_t)stream;
+    s = launch_part_step(c, t, nullptr, 0, st);
+    if (s != PSGLD_OK) return s;
+    c->t_done = t;
+    c->last_stream = st;
+    return PSGLD_OK;
+}
+
+psgld_status psgld_sweep(psgld_ctx *c, int32_t n_sweeps, void *stream)
+{
+    if (!c) return PSGLD_ERR_ARG;
+    psgld_status s;
+    if (!ready(c, &s)) return s;
+    if (n_sweeps < 0) return fail(c, PSGLD_ERR_ARG, "n_sweeps < 0");
+    if (c->t_done % c->B != 0) return fail(c, PSGLD_ERR_STATE, "sweep must start at a sweep boundary");
+    cudaStream_t st = (cudaStream_t)stream;
+    c->last_stream = st;
+    if (n_sweeps == 0) return PSGLD_OK;
+    if (c->opt.use_graphs) {
+        set_t_kernel<<<1, 32, 0, st>>>(c->t_dev, c->t_done);
+        PSGLD_CK(c, cudaGetLastError());
+    }
+    for (int32_t n = 0; n < n_sweeps; ++n) {
+        const bool acc = c->sweeps_done >= c->opt.burn_in_sweeps;
+        if (c->opt.use_graphs) {
+            cudaGraphExec_t &g = acc ? c->graph_acc[c->wcur * 2 + c->hcur] : c->graph[c->wcur][c->hcur];
+            if (!g) {
+                s = capture_sweep(c, acc, &g);
+                if (s != PSGLD_OK) return s;
+            }
+            PSGLD_CK(c, cudaGraphLaunch(g, st));
+            // the replay leaves the buffers as B part-steps do
+            if (!c->opt.freeze_W) c->wcur ^= (c->B & 1);
+            if (!c->opt.freeze_H) c->hcur ^= (c->B & 1);
+        } else {
+            for (int b = 0; b < c->B; ++b) {
+                s = launch_part_step(c, c->t_done + b + 1, nullptr, 0, st);
+                if (s != PSGLD_OK) return s;
+            }
+            if (acc) {
+                s = launch_accumulate(c, st);
+                if (s != PSGLD_OK) return s;
+            }
+        }
+        c->t_done += c->B;
+        c->sweeps_done += 1;
+        if (acc) c->n_samples += 1;
+    }
+    return PSGLD_OK;
+}
+
+psgld_status psgld_posterior_mean(psgld_ctx *c, double *Wm, double *Wv, double *Hm, double *Hv,
+                                  int64_t *n_samples)
+{
+    if (!c) return PSGLD_ERR_ARG;
+    PSGLD_CK(c, cudaStreamSynchronize(c->last_stream));
+    const int64_t ldk = c->ldk, K = c->K;
+    const double n = (double)c->n_samples;
+    for (int side = 0; side < 2; ++side) {
+        double *mean = side == 0 ? Wm : Hm, *var = side == 0 ? Wv : Hv;
+        if (!mean && !var) continue;
+        const int64_t rows = side == 0 ? c->I : c->J;
+        const Sums &S = side == 0 ? c->sW : c->sH;
+        std::vector<double> s((size_t)(rows * ldk)), s2((size_t)(rows * ldk));
+        PSGLD_CK(c, cudaMemcpy(s.data(), S.s, sizeof(double) * s.size(), cudaMemcpyDeviceToHost));
+        PSGLD_CK(c, cudaMemcpy(s2.data(), S.s2, sizeof(double) * s2.size(), cudaMemcpyDeviceToHost));
+        for (int64_t r = 0; r < rows; ++r)
+            for (int64_t k = 0; k < K; ++k) {
+                const double m = n > 0 ? s[r * ldk + k] / n : 0.0;
+                if (mean) mean[r * K + k] = m;
+                if (var) var[r * K + k] = n > 0 ? s2[r * ldk + k] / n - m * m : 0.0;
+            }
+    }
+    if (n_samples) *n_samples = c->n_samples;
+    return PSGLD_OK;
+}
+
+psgld_status psgld_log_lik(psgld_ctx *c, double *out, void *stream)
+{
+    if (!c || !out) return PSGLD_ERR_ARG;
+    psgld_status s;
+    if (!ready(c, &s)) return s;
+    return reduce_loglik_rmse(c, 0, 0, (cudaStream_t)stream, out);
+}
+
+psgld_status psgld_rmse(psgld_ctx *c, int32_t use_mean, double *out, void *stream)
+{
+    if (!c || !out) return PSGLD_ERR_ARG;
+    psgld_status s;
+    if (!ready(c, &s)) return s;
+    if (use_mean && c->n_samples == 0) return fail(c, PSGLD_ERR_STATE, "no posterior samples yet");
+    double ss = 0.0;
+    s = reduce_loglik_rmse(c, 1, use_mean, (cudaStream_t)stream, &ss);
+    if (s != PSGLD_OK) return s;
+    *out = c->N > 0 ? std::sqrt(ss / (double)c->N) : 0.0;
+    return PSGLD_OK;
+}
+
+psgld_status psgld_piece_bounds(const psgld_ctx *c, int64_t *rs, int64_t *cs)
+{
+    if (!c) return PSGLD_ERR_ARG;
+    for (int r = 0; r <= c->B; ++r) {
+        if (rs) rs[r] = ((int64_t)r * c->I) / c->B;
+        if (cs) cs[r] = ((int64_t)r * c->J) / c->B;
+    }
+    return PSGLD_OK;
+}
+
+psgld_status psgld_part_schedule(const psgld_ctx *c, int64_t t, int32_t *col_piece)
+{
+    if (!c || !col_piece || t < 1) return PSGLD_ERR_ARG;
+    const int64_t s = (t - 1) % c->B;
+    for (int r = 0; r < c->B; ++r) col_piece[r] = (int32_t)((r + s) % c->B);
+    return PSGLD_OK;
+}
+
+psgld_status psgld_part_layout(psgld_ctx *c, int32_t s, int32_t *row_ptr, int32_t *cols,
+                               int64_t *n_entries)
+{
+    if (!c || s < 0 || s >= c->B) return PSGLD_ERR_ARG;
+    if (!c->has_data) return fail(c, PSGLD_ERR_STATE, "no data set");
+    std::vector<int32_t> ptr((size_t)c->I + 1);
+    PSGLD_CK(c, cudaMemcpy(ptr.data(), c->side[0].ptr + (int64_t)s * c->I,
+                           sizeof(int32_t) * ptr.size(), cudaMemcpyDeviceToHost));
+    const int64_t n = ptr[c->I] - ptr[0];
+    if (n_entries) *n_entries = n;
+    if (row_ptr)
+        for (int64_t r = 0; r <= c->I; ++r) row_ptr[r] = ptr[r] - ptr[0];
+    if (cols && n > 0)
+        PSGLD_CK(c, cudaMemcpy(cols, c->side[0].idx + ptr[0], sizeof(int32_t) * n, cudaMemcpyDeviceToHost));
+    return PSGLD_OK;
+}
+
+int64_t psgld_iterations_done(const psgld_ctx *c) { return c ? c->t_done : -1; }
+
+const char *psgld_last_error(const psgld_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+void psgld_destroy(psgld_ctx *c)
+{
+    if (!c) return;
+    destroy_graphs(c);
+    free_layout(c);
+    for (int b = 0; b < 2; ++b) { cudaFree(c->W[b]); cudaFree(c->Ht[b]); }
+    cudaFree(c->sW.s); cudaFree(c->sW.s2); cudaFree(c->sH.s); cudaFree(c->sH.s2);
+    cudaFree(c->red); cudaFree(c->flag); cudaFree(c->t_dev);
+    if (c->red_host) cudaFreeHost(c->red_host);
+    if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
+    delete c;
+}
+
+}  // extern "C"

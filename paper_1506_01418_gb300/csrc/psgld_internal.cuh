@@ -1,0 +1,172 @@
+// psgld_internal.cuh -- shared declarations of the CUDA PSGLD library.
+//
+// Device layout (all in HBM, owned by the context):
+//   W[2]  : I x ldk fp32, row-major, ping-pong pair (ldk = 4*ceil(K/4); the
+//           padding columns are kept at zero so every row is float4-aligned)
+//   Ht[2] : J x ldk fp32, H transposed, same rules
+//   A-side layout (part-major CSR): entries ordered by (part s, row i, col j)
+//           ptrA[s*I + i] .. ptrA[s*I + i + 1] -> idxA (col j), valA (v)
+//   B-side layout (part-major CSC): entries ordered by (part s, col j, row i)
+//           ptrB[s*J + j] .. -> idxB (row i), valB (v)
+//   segA/segB : per part, the work list of the fused part-step kernel; one
+//           record per (row, run of at most seg_len entries)
+//   posterior sums: fp64 copies of W, W^2, Ht, Ht^2 (padded like the factors)
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/psgld.h"
+
+namespace psgld {
+
+constexpr int kMaxK = 512;
+
+// Work-list record of the fused part-step kernel: one team of lanes owns
+// `row` and the entry range [beg, end).  `split` is -1 when the row has a
+// single record in this part; otherwise it indexes the part's split table.
+// Split-table entry: x = first record of the row (part-local), y = number of
+// records of the row, z = first partial-sum slot (part-local).
+struct SideLayout {
+    int32_t *ptr = nullptr;    // B*n_rows + 1 entry offsets
+    int32_t *idx = nullptr;    // other index of each entry
+    float *val = nullptr;      // value of each entry
+    int4 *seg = nullptr;       // all parts' records, part-major
+    int4 *split = nullptr;     // all parts' split tables, part-major
+    std::vector<int64_t> seg_off;    // B+1: first record of each part
+    std::vector<int64_t> split_off;  // B+1
+    std::vector<int64_t> slot_off;   // B+1: partial slots
+    int64_t max_splits = 0;    // largest split table of one part
+    int64_t max_slots = 0;     // largest number of partial slots of one part
+    float *partial = nullptr;  // max_slots x ldk scratch
+    unsigned *counter = nullptr;  // max_splits arrival counters (kept zero between launches)
+};
+
+struct Sums {
+    double *s = nullptr, *s2 = nullptr;
+};
+
+}  // namespace psgld
+
+struct psgld_ctx {
+    int64_t I = 0, J = 0;
+    int32_t K = 0, B = 0, ldk = 0, ngroups = 0;
+    double p = 0.0, phi = 1.0;
+    psgld_prior prior{};
+    psgld_options opt{};
+    int device = 0;
+    std::string err;
+
+    // data
+    bool has_data = false;
+    int64_t N = 0;
+    std::vector<int64_t> part_n;     // observed entries of each part
+    int32_t seg_len = 32;
+    psgld::SideLayout side[2];       // 0: rows of W (CSR), 1: rows of Ht (CSC)
+
+    // factors
+    float *W[2] = {nullptr, nullptr};
+    float *Ht[2] = {nullptr, nullptr};
+    int wcur = 0, hcur = 0;
+    bool has_factors = false;
+
+    // posterior
+    psgld::Sums sW, sH;
+    int64_t n_samples = 0;
+    int64_t sweeps_done = 0;
+    int64_t t_done = 0;
+
+    // reductions
+    double *red = nullptr;       // per-CTA partial sums
+    double *red_host = nullptr;  // pinned copy
+    int *flag = nullptr;         // device error flag
+    cudaStream_t last_stream = nullptr;
+
+    // CUDA graphs of one sweep, per parity of the ping-pong buffers, without
+    // and with the posterior accumulation
+    cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    cudaGraphExec_t graph_acc[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaStream_t capture_stream = nullptr;
+    int64_t *t_dev = nullptr;    // iteration counter read by graph replays
+};
+
+namespace psgld {
+
+// ---- error plumbing ------------------------------------------------------
+psgld_status fail(psgld_ctx *c, psgld_status s, const std::string &msg);
+psgld_status cuda_fail(psgld_ctx *c, cudaError_t e, const char *what);
+
+#define PSGLD_CK(ctx, call)                                        \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return psgld::cuda_fail((ctx), e_, #call); \
+    } while (0)
+
+// ---- layout (psgld_layout.cu) ---------------------------------------------
+psgld_status build_layout(psgld_ctx *c, int64_t nnz, const int32_t *i_dev,
+                          const int32_t *j_dev, const float *v_dev,
+                          cudaStream_t st);
+void free_layout(psgld_ctx *c);
+
+// ---- part-step (psgld_step.cu) --------------------------------------------
+// Enqueue iteration t.  When t_dev is non-null the kernels read t from
+// *t_dev + t_add instead (used inside captured graphs); `t` then only
+// selects the part and must satisfy (t-1) % B == part.
+psgld_status launch_part_step(psgld_ctx *c, int64_t t, const int64_t *t_dev,
+                              int64_t t_add, cudaStream_t st);
+
+// ---- reductions (psgld_reduce.cu) -----------------------------------------
+psgld_status launch_accumulate(psgld_ctx *c, cudaStream_t st);
+psgld_status launch_advance_t(psgld_ctx *c, int64_t by, cudaStream_t st);
+psgld_status reduce_loglik_rmse(psgld_ctx *c, int mode, int use_mean,
+                                cudaStream_t st, double *out);
+
+// ---- scans and sorts (psgld_layout.cu) ------------------------------------
+int bits_for(uint64_t n_values);
+
+}  // namespace psgld
+
+// ---- device helpers -------------------------------------------------------
+namespace psgld {
+namespace dev {
+
+// Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32->64-bit
+// multiplies whose high halves are mixed into the other two words with the
+// round key; the key advances by the Weyl constants between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k.x += 0x9E3779B9u;
+            k.y += 0xBB67AE85u;
+        }
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    }
+    return c;
+}
+
+// Uniform on (0, 1): the top 23 bits plus one half, times 2^-23 (exact in
+// fp32).  Then Box-Muller on (u0, u1) and (u2, u3): cos first, then sin.
+__device__ __forceinline__ float4 box_muller4(uint4 x)
+{
+    const float s = 1.0f / 8388608.0f;
+    const float u0 = (__uint2float_rn(x.x >> 9) + 0.5f) * s;
+    const float u1 = (__uint2float_rn(x.y >> 9) + 0.5f) * s;
+    const float u2 = (__uint2float_rn(x.z >> 9) + 0.5f) * s;
+    const float u3 = (__uint2float_rn(x.w >> 9) + 0.5f) * s;
+    const float r0 = sqrtf(-2.0f * logf(u0));
+    const float r1 = sqrtf(-2.0f * logf(u2));
+    float s0, c0, s1, c1;
+    sincospif(2.0f * u1, &s0, &c0);
+    sincospif(2.0f * u3, &s1, &c1);
+    return make_float4(r0 * c0, r0 * s0, r1 * c1, r1 * s1);
+}
+
+}  // namespace dev
+}  // namespace psgld

@@ -1,0 +1,134 @@
+// psgld_reduce.cu -- FP64 posterior sums and the log-likelihood / RMSE
+// reductions.
+//
+// Posterior (Monte Carlo averages after burn-in, Sec. 4.1.2): after every
+// sweep past burn-in each factor element x adds x and x^2 to FP64 running
+// sums; mean = sum/n, variance = sum2/n - mean^2.
+//
+// Log-likelihood (Sec. 4): -(1/phi) sum_obs d_beta(v || mu), beta = 2 - p,
+// with the named limits at beta = 2, 1, 0 (Euclidean, Kullback-Leibler,
+// Itakura-Saito).  RMSE: sqrt(mean_obs (v - mu)^2).  Both run in FP64 over the
+// row-major layout; per-CTA partial sums are added on the host in CTA order,
+// so the result is deterministic.
+#include <algorithm>
+
+#include "psgld_internal.cuh"
+
+namespace psgld {
+namespace {
+
+__global__ void accumulate_kernel(const float4 *__restrict__ x, int64_t n4, double *__restrict__ s,
+                                  double *__restrict__ s2)
+{
+    for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < n4;
+         a += (int64_t)gridDim.x * blockDim.x) {
+        const float4 v = x[a];
+        double2 *ps = reinterpret_cast<double2 *>(s) + 2 * a;
+        double2 *ps2 = reinterpret_cast<double2 *>(s2) + 2 * a;
+        double2 p0 = ps[0], p1 = ps[1], q0 = ps2[0], q1 = ps2[1];
+        const double a0 = v.x, a1 = v.y, a2 = v.z, a3 = v.w;
+        p0.x += a0; p0.y += a1; p1.x += a2; p1.y += a3;
+        q0.x += a0 * a0; q0.y += a1 * a1; q1.x += a2 * a2; q1.y += a3 * a3;
+        ps[0] = p0; ps[1] = p1; ps2[0] = q0; ps2[1] = q1;
+    }
+}
+
+__global__ void advance_t_kernel(int64_t *t, int64_t by)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) *t += by;
+}
+
+__device__ double beta_div(double v, double mu, double p)
+{
+    const double beta = 2.0 - p;
+    if (beta == 2.0) return 0.5 * (v - mu) * (v - mu);
+    if (beta == 1.0) return (v > 0.0 ? v * log(v / mu) : 0.0) - v + mu;
+    if (beta == 0.0) return v / mu - log(v / mu) - 1.0;
+    return pow(v, beta) / (beta * (beta - 1.0)) - v * pow(mu, beta - 1.0) / (beta - 1.0) +
+           pow(mu, beta) / beta;
+}
+
+constexpr int kRedThreads = 256;
+constexpr int kRedBlocks = 1216;   // 8 per SM
+
+// mode 0: log-likelihood; mode 1: sum of squared residuals.
+// Factors: fp32 (W, Ht) or, when Ws is non-null, fp64 sums scaled by inv_n.
+__global__ void __launch_bounds__(kRedThreads)
+reduce_kernel(int mode, const int32_t *__restrict__ ptr, const int32_t *__restrict__ idx,
+              const float *__restrict__ val, int64_t nslots, int64_t I, int ldk, int K,
+              const float *__restrict__ W, const float *__restrict__ Ht,
+              const double *__restrict__ Ws, const double *__restrict__ Hs, double inv_n,
+              double p, double phi, double mu_min, double *__restrict__ out)
+{
+    double acc = 0.0;
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < nslots;
+         s += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = s % I;
+        for (int32_t e = ptr[s]; e < ptr[s + 1]; ++e) {
+            const int64_t j = idx[e];
+            double mu = 0.0;
+            if (Ws) {
+                for (int k = 0; k < K; ++k) mu += (Ws[i * ldk + k] * inv_n) * (Hs[j * ldk + k] * inv_n);
+            } else {
+                for (int k = 0; k < K; ++k) mu += (double)W[i * ldk + k] * (double)Ht[j * ldk + k];
+            }
+            const double v = val[e];
+            if (mode == 0) {
+                const double m = (p > 0.0 && mu < mu_min) ? mu_min : mu;
+                acc -= beta_div(v, m, p) / phi;
+            } else {
+                acc += (v - mu) * (v - mu);
+            }
+        }
+    }
+    __shared__ double sm[kRedThreads];
+    sm[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = kRedThreads / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sm[threadIdx.x] += sm[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[blockIdx.x] = sm[0];
+}
+
+}  // namespace
+
+int reduce_blocks() { return kRedBlocks; }
+
+psgld_status launch_accumulate(psgld_ctx *c, cudaStream_t st)
+{
+    const int64_t nW4 = c->I * c->ldk / 4, nH4 = c->J * c->ldk / 4;
+    accumulate_kernel<<<(unsigned)std::min<int64_t>((nW4 + 255) / 256, 152 * 16), 256, 0, st>>>(
+        reinterpret_cast<const float4 *>(c->W[c->wcur]), nW4, c->sW.s, c->sW.s2);
+    accumulate_kernel<<<(unsigned)std::min<int64_t>((nH4 + 255) / 256, 152 * 16), 256, 0, st>>>(
+        reinterpret_cast<const float4 *>(c->Ht[c->hcur]), nH4, c->sH.s, c->sH.s2);
+    PSGLD_CK(c, cudaGetLastError());
+    return PSGLD_OK;
+}
+
+psgld_status launch_advance_t(psgld_ctx *c, int64_t by, cudaStream_t st)
+{
+    advance_t_kernel<<<1, 32, 0, st>>>(c->t_dev, by);
+    PSGLD_CK(c, cudaGetLastError());
+    return PSGLD_OK;
+}
+
+psgld_status reduce_loglik_rmse(psgld_ctx *c, int mode, int use_mean, cudaStream_t st, double *out)
+{
+    const SideLayout &L = c->side[0];
+    const double inv_n = c->n_samples > 0 ? 1.0 / (double)c->n_samples : 0.0;
+    reduce_kernel<<<kRedBlocks, kRedThreads, 0, st>>>(
+        mode, L.ptr, L.idx, L.val, (int64_t)c->B * c->I, c->I, c->ldk, c->K, c->W[c->wcur],
+        c->Ht[c->hcur], use_mean ? c->sW.s : nullptr, use_mean ? c->sH.s : nullptr, inv_n, c->p,
+        c->phi, c->opt.mu_min, c->red);
+    PSGLD_CK(c, cudaGetLastError());
+    PSGLD_CK(c, cudaMemcpyAsync(c->red_host, c->red, sizeof(double) * kRedBlocks,
+                                cudaMemcpyDeviceToHost, st));
+    PSGLD_CK(c, cudaStreamSynchronize(st));
+    double s = 0.0;
+    for (int b = 0; b < kRedBlocks; ++b) s += c->red_host[b];
+    *out = s;
+    return PSGLD_OK;
+}
+
+}  // namespace psgld

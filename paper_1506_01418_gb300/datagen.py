@@ -2,8 +2,10 @@
 
 This module draws data and initial factors only.  It holds none of the
 sampler's arithmetic, so both the CUDA library's tests and the FP64 oracle can
-take their inputs from it.  Everything is numpy with an explicit seed; the same
-call returns the same arrays on every machine.
+take their inputs from it.  Everything draws from an explicitly seeded
+generator: numpy (the default; the same call returns the same arrays on every
+machine) or, for the full-size sparse workloads, torch on a CUDA device (same
+recipe, a different random stream; repeatable on one device type).
 
 Workloads (the data sets of the paper are not available; these stand in for
 their published shapes):
@@ -67,39 +69,94 @@ def sparse_pattern(I: int, J: int, nnz: int, zipf_row: float, zipf_col: float | 
     """nnz unique (i, j) pairs with Zipf row (and optionally column) degrees.
 
     Pairs are drawn independently from the two marginals and duplicates are
-    dropped, until nnz distinct pairs exist; the first nnz distinct pairs in
-    draw order are kept.  Rows or columns whose expected degree exceeds the
-    other dimension saturate, as real rating matrices do.
+    dropped, in rounds, until at least nnz distinct pairs exist; a seeded
+    random subset of nnz of them is kept, in row-major order.  Rows or columns
+    whose expected degree exceeds the other dimension saturate, as in real
+    rating matrices.
     """
     if nnz > I * J:
         raise ValueError("nnz larger than I*J")
-    pr = _zipf_weights(I, zipf_row, g)
-    pc = _zipf_weights(J, zipf_col, g) if zipf_col else None
+    cr = np.cumsum(_zipf_weights(I, zipf_row, g))
+    cc = np.cumsum(_zipf_weights(J, zipf_col, g)) if zipf_col else None
     keys = np.empty(0, dtype=np.int64)
-    first = np.empty(0, dtype=np.int64)
-    drawn = 0
-    while True:
+    draw = int(nnz * 1.2) + 1024
+    while len(keys) < nnz:
+        ii = np.minimum(np.searchsorted(cr, g.random(draw) * cr[-1], side="right"), I - 1)
+        if cc is not None:
+            jj = np.minimum(np.searchsorted(cc, g.random(draw) * cc[-1], side="right"), J - 1)
+        else:
+            jj = g.integers(0, J, size=draw)
+        before = len(keys)
+        keys = np.unique(np.concatenate([keys, ii.astype(np.int64) * J + jj]))
+        gained = len(keys) - before
         need = nnz - len(keys)
-        if need <= 0:
-            break
-        m = max(int(need * 1.25), 1024)
-        ii = g.choice(I, size=m, p=pr)
-        jj = g.choice(J, size=m, p=pc) if pc is not None else g.integers(0, J, size=m)
-        k = ii.astype(np.int64) * J + jj
-        allk = np.concatenate([keys, k])
-        allpos = np.concatenate([first, drawn + np.arange(m, dtype=np.int64)])
-        u, idx = np.unique(allk, return_index=True)
-        keys, first = u, allpos[idx]
-        drawn += m
-    order = np.argsort(first, kind="stable")[:nnz]
-    k = keys[order]
-    return (k // J).astype(np.int32), (k % J).astype(np.int32)
+        if need > 0:   # next round sized from this round's yield of new pairs
+            draw = int(need * draw / max(gained, 1) * 1.2) + 1024
+    if len(keys) > nnz:
+        keys = np.sort(g.choice(keys, size=nnz, replace=False))
+    return (keys // J).astype(np.int32), (keys % J).astype(np.int32)
+
+
+def _sparse_ratings_torch(I, J, nnz, K_true, seed, zipf_row, zipf_col, noise_sd, device):
+    """The recipe of sparse_pattern + sparse_ratings with torch tensors on `device`."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    f64 = torch.float64
+
+    def cdf(n, a):
+        w = torch.arange(1, n + 1, dtype=f64, device=device) ** (-a)
+        out = torch.empty_like(w)
+        out[torch.randperm(n, generator=g, device=device)] = w / w.sum()
+        return torch.cumsum(out, 0)
+
+    cr = cdf(I, zipf_row)
+    cc = cdf(J, zipf_col) if zipf_col else None
+    keys = torch.empty(0, dtype=torch.int64, device=device)
+    draw = int(nnz * 1.2) + 1024
+    while keys.numel() < nnz:
+        u = torch.rand(draw, generator=g, device=device, dtype=f64) * cr[-1]
+        ii = torch.searchsorted(cr, u, right=True).clamp_(max=I - 1)
+        if cc is not None:
+            u = torch.rand(draw, generator=g, device=device, dtype=f64) * cc[-1]
+            jj = torch.searchsorted(cc, u, right=True).clamp_(max=J - 1)
+        else:
+            jj = torch.randint(0, J, (draw,), generator=g, device=device)
+        before = keys.numel()
+        keys = torch.unique(torch.cat([keys, ii * J + jj]))
+        gained = keys.numel() - before
+        need = nnz - keys.numel()
+        if need > 0:
+            draw = int(need * draw / max(gained, 1) * 1.2) + 1024
+    if keys.numel() > nnz:
+        sel = torch.randperm(keys.numel(), generator=g, device=device)[:nnz]
+        keys = torch.sort(keys[sel]).values
+    i = (keys // J).to(torch.int32)
+    j = (keys % J).to(torch.int32)
+    s = math.sqrt(3.0 * math.pi / (2.0 * K_true))
+    Wt = torch.randn(I, K_true, generator=g, device=device, dtype=f64).abs_() * s
+    Ht = torch.randn(J, K_true, generator=g, device=device, dtype=f64).abs_() * s
+    v = torch.empty(nnz, dtype=torch.float32, device=device)
+    chunk = 1 << 22
+    for a in range(0, nnz, chunk):
+        b = min(nnz, a + chunk)
+        mean = (Wt[i[a:b].long()] * Ht[j[a:b].long()]).sum(1)
+        noise = torch.randn(b - a, generator=g, device=device, dtype=f64) * noise_sd
+        v[a:b] = torch.clamp(torch.round(mean + noise), 1, 5).float()
+    return i, j, v
 
 
 def sparse_ratings(I: int, J: int, nnz: int, K_true: int, seed: int,
                    zipf_row: float = 1.1, zipf_col: float | None = 1.1,
-                   noise_sd: float = 0.5):
-    """Ratings-like sparse data. Returns (i int32, j int32, v float32)."""
+                   noise_sd: float = 0.5, device=None):
+    """Ratings-like sparse data. Returns (i int32, j int32, v float32).
+
+    With `device` (a CUDA device) the arrays are torch tensors drawn there;
+    otherwise numpy arrays drawn on the host.
+    """
+    if device is not None:
+        return _sparse_ratings_torch(I, J, nnz, K_true, seed, zipf_row, zipf_col, noise_sd,
+                                     device)
     g = _rng(seed)
     i, j = sparse_pattern(I, J, nnz, zipf_row, zipf_col, g)
     s = math.sqrt(3.0 * math.pi / (2.0 * K_true))

@@ -1,0 +1,326 @@
+"""Thin ctypes binding of the C ABI in include/psgld.h.
+
+Argument marshalling only: every step of the sampler runs in the CUDA library
+``libpsgld.so``.  There is no CPU fallback -- if the library cannot be loaded,
+importing a function from here raises.
+
+Array arguments may be torch tensors (on the context's GPU or on the host) or
+numpy arrays (host); they are passed to the library as raw pointers, so they
+must be C-contiguous with the documented dtype.  ``stream`` defaults to the
+current torch CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import _build
+
+_lib = None
+
+
+class PsgldError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"psgld status {status}: {msg}")
+        self.status = status
+
+
+PSGLD_OK, PSGLD_ERR_ARG, PSGLD_ERR_OOM, PSGLD_ERR_CUDA, PSGLD_ERR_STATE, PSGLD_ERR_TIMEOUT = \
+    0, -1, -2, -3, -4, -5
+PSGLD_PRIOR_EXPONENTIAL, PSGLD_PRIOR_GAUSSIAN = 0, 1
+PSGLD_EPS_FIXED, PSGLD_EPS_POLY = 0, 1
+PSGLD_SCALE_N_OVER_PART, PSGLD_SCALE_B = 0, 1
+
+
+class psgld_prior(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("lambda_w", C.c_double), ("lambda_h", C.c_double),
+                ("sigma_w", C.c_double), ("sigma_h", C.c_double)]
+
+
+class psgld_options(C.Structure):
+    _fields_ = [("seed", C.c_uint64), ("eps_mode", C.c_int32), ("eps", C.c_double),
+                ("eps_a", C.c_double), ("eps_b", C.c_double), ("scale_mode", C.c_int32),
+                ("mu_min", C.c_double), ("freeze_W", C.c_int32), ("freeze_H", C.c_int32),
+                ("burn_in_sweeps", C.c_int64), ("use_graphs", C.c_int32)]
+
+
+EXPORTS = [
+    "psgld_default_options", "psgld_create", "psgld_set_options", "psgld_set_data_coo",
+    "psgld_set_data_dense", "psgld_set_factors", "psgld_get_factors", "psgld_part_step",
+    "psgld_sweep", "psgld_posterior_mean", "psgld_log_lik", "psgld_rmse", "psgld_piece_bounds",
+    "psgld_part_schedule", "psgld_part_layout", "psgld_iterations_done", "psgld_last_error",
+    "psgld_destroy",
+]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libpsgld.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build() if build_if_missing else _build.LIB
+    if not os.path.exists(path):
+        raise OSError(f"CUDA library not built: {path}")
+    L = C.CDLL(path)
+    vp, i32, i64, f64 = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+    st = C.c_int
+    sig = {
+        "psgld_default_options": (None, [C.POINTER(psgld_options)]),
+        "psgld_create": (st, [i64, i64, i32, i32, f64, f64, C.POINTER(psgld_prior), C.POINTER(vp)]),
+        "psgld_set_options": (st, [vp, C.POINTER(psgld_options)]),
+        "psgld_set_data_coo": (st, [vp, i64, vp, vp, vp, vp]),
+        "psgld_set_data_dense": (st, [vp, vp, i64, vp]),
+        "psgld_set_factors": (st, [vp, vp, vp, vp]),
+        "psgld_get_factors": (st, [vp, vp, vp, vp]),
+        "psgld_part_step": (st, [vp, i64, vp]),
+        "psgld_sweep": (st, [vp, i32, vp]),
+        "psgld_posterior_mean": (st, [vp, vp, vp, vp, vp, vp]),
+        "psgld_log_lik": (st, [vp, vp, vp]),
+        "psgld_rmse": (st, [vp, i32, vp, vp]),
+        "psgld_piece_bounds": (st, [vp, vp, vp]),
+        "psgld_part_schedule": (st, [vp, i64, vp]),
+        "psgld_part_layout": (st, [vp, i32, vp, vp, vp]),
+        "psgld_iterations_done": (i64, [vp]),
+        "psgld_last_error": (C.c_char_p, [vp]),
+        "psgld_destroy": (None, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+# ---------------------------------------------------------------------------
+# marshalling helpers
+# ---------------------------------------------------------------------------
+
+def _ptr(x, dtype=None):
+    if x is None:
+        return None
+    try:
+        import torch
+        if isinstance(x, torch.Tensor):
+            if not x.is_contiguous():
+                raise ValueError("tensor must be contiguous")
+            if dtype is not None and x.dtype != dtype[0]:
+                raise TypeError(f"expected {dtype[0]}, got {x.dtype}")
+            return C.c_void_p(x.data_ptr())
+    except ImportError:
+        pass
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        if dtype is not None and x.dtype != dtype[1]:
+            raise TypeError(f"expected {dtype[1]}, got {x.dtype}")
+        return C.c_void_p(x.ctypes.data)
+    raise TypeError(f"unsupported array type {type(x)}")
+
+
+def _dt(kind):
+    import torch
+    return {"i32": (torch.int32, np.int32), "f32": (torch.float32, np.float32),
+            "f64": (torch.float64, np.float64)}[kind]
+
+
+def _stream(stream):
+    if stream is not None:
+        return C.c_void_p(int(stream))
+    import torch
+    if torch.cuda.is_available():
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return C.c_void_p(0)
+
+
+def _check(ctx, status):
+    if status != PSGLD_OK:
+        msg = load().psgld_last_error(ctx).decode() if ctx else ""
+        raise PsgldError(status, msg)
+
+
+# ---------------------------------------------------------------------------
+# the ABI, one function per entry point
+# ---------------------------------------------------------------------------
+
+def psgld_default_options() -> psgld_options:
+    o = psgld_options()
+    load().psgld_default_options(C.byref(o))
+    return o
+
+
+def psgld_create(I, J, K, B, tweedie_p, phi, prior: psgld_prior):
+    h = C.c_void_p()
+    st = load().psgld_create(int(I), int(J), int(K), int(B), float(tweedie_p), float(phi),
+                             C.byref(prior), C.byref(h))
+    if st != PSGLD_OK:
+        raise PsgldError(st, "psgld_create rejected its arguments or ran out of memory")
+    return h
+
+
+def psgld_set_options(ctx, opt: psgld_options):
+    _check(ctx, load().psgld_set_options(ctx, C.byref(opt)))
+
+
+def psgld_set_data_coo(ctx, i, j, v, stream=None):
+    _check(ctx, load().psgld_set_data_coo(ctx, len(i), _ptr(i, _dt("i32")), _ptr(j, _dt("i32")),
+                                          _ptr(v, _dt("f32")), _stream(stream)))
+
+
+def psgld_set_data_dense(ctx, V, ld=None, stream=None):
+    ld = V.shape[1] if ld is None else ld
+    _check(ctx, load().psgld_set_data_dense(ctx, _ptr(V, _dt("f32")), int(ld), _stream(stream)))
+
+
+def psgld_set_factors(ctx, W, Ht, stream=None):
+    _check(ctx, load().psgld_set_factors(ctx, _ptr(W, _dt("f32")), _ptr(Ht, _dt("f32")),
+                                         _stream(stream)))
+
+
+def psgld_get_factors(ctx, W, Ht, stream=None):
+    _check(ctx, load().psgld_get_factors(ctx, _ptr(W, _dt("f32")), _ptr(Ht, _dt("f32")),
+                                         _stream(stream)))
+
+
+def psgld_part_step(ctx, t, stream=None):
+    _check(ctx, load().psgld_part_step(ctx, int(t), _stream(stream)))
+
+
+def psgld_sweep(ctx, n_sweeps=1, stream=None):
+    _check(ctx, load().psgld_sweep(ctx, int(n_sweeps), _stream(stream)))
+
+
+def psgld_posterior_mean(ctx, Wmean, Wvar, Hmean, Hvar):
+    n = C.c_int64(0)
+    f = _dt("f64")
+    _check(ctx, load().psgld_posterior_mean(ctx, _ptr(Wmean, f), _ptr(Wvar, f), _ptr(Hmean, f),
+                                            _ptr(Hvar, f), C.byref(n)))
+    return n.value
+
+
+def psgld_log_lik(ctx, stream=None) -> float:
+    out = C.c_double(0.0)
+    _check(ctx, load().psgld_log_lik(ctx, C.byref(out), _stream(stream)))
+    return out.value
+
+
+def psgld_rmse(ctx, use_posterior_mean=False, stream=None) -> float:
+    out = C.c_double(0.0)
+    _check(ctx, load().psgld_rmse(ctx, int(bool(use_posterior_mean)), C.byref(out),
+                                  _stream(stream)))
+    return out.value
+
+
+def psgld_piece_bounds(ctx, B):
+    rs = np.zeros(B + 1, dtype=np.int64)
+    cs = np.zeros(B + 1, dtype=np.int64)
+    _check(ctx, load().psgld_piece_bounds(ctx, _ptr(rs), _ptr(cs)))
+    return rs, cs
+
+
+def psgld_part_schedule(ctx, t, B):
+    cp = np.zeros(B, dtype=np.int32)
+    _check(ctx, load().psgld_part_schedule(ctx, int(t), _ptr(cp)))
+    return cp
+
+
+def psgld_part_layout(ctx, s, I):
+    n = C.c_int64(0)
+    _check(ctx, load().psgld_part_layout(ctx, int(s), None, None, C.byref(n)))
+    ptr = np.zeros(I + 1, dtype=np.int32)
+    cols = np.zeros(max(n.value, 1), dtype=np.int32)
+    _check(ctx, load().psgld_part_layout(ctx, int(s), _ptr(ptr), _ptr(cols), C.byref(n)))
+    return ptr, cols[:n.value]
+
+
+def psgld_iterations_done(ctx) -> int:
+    return load().psgld_iterations_done(ctx)
+
+
+def psgld_last_error(ctx) -> str:
+    return load().psgld_last_error(ctx).decode()
+
+
+def psgld_destroy(ctx):
+    if ctx:
+        load().psgld_destroy(ctx)
+
+
+# ---------------------------------------------------------------------------
+# convenience wrapper (still marshalling only)
+# ---------------------------------------------------------------------------
+
+class PSGLD:
+    """One PSGLD chain held by a library context."""
+
+    def __init__(self, I, J, K, B, tweedie_p, phi, prior_kind=PSGLD_PRIOR_EXPONENTIAL,
+                 lambda_w=1.0, lambda_h=1.0, sigma_w=1.0, sigma_h=1.0, **options):
+        self.I, self.J, self.K, self.B = int(I), int(J), int(K), int(B)
+        pr = psgld_prior(int(prior_kind), float(lambda_w), float(lambda_h), float(sigma_w),
+                         float(sigma_h))
+        self.ctx = psgld_create(I, J, K, B, tweedie_p, phi, pr)
+        self.options = psgld_default_options()
+        if options:
+            self.set_options(**options)
+
+    def set_options(self, **kw):
+        for k, v in kw.items():
+            if not hasattr(self.options, k):
+                raise AttributeError(k)
+            setattr(self.options, k, v)
+        psgld_set_options(self.ctx, self.options)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            psgld_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_data_coo(self, i, j, v, stream=None):
+        psgld_set_data_coo(self.ctx, i, j, v, stream)
+
+    def set_data_dense(self, V, stream=None):
+        psgld_set_data_dense(self.ctx, V, None, stream)
+
+    def set_factors(self, W, Ht, stream=None):
+        psgld_set_factors(self.ctx, W, Ht, stream)
+
+    def get_factors(self, stream=None):
+        import torch
+        W = torch.empty((self.I, self.K), dtype=torch.float32, device="cuda")
+        Ht = torch.empty((self.J, self.K), dtype=torch.float32, device="cuda")
+        psgld_get_factors(self.ctx, W, Ht, stream)
+        return W, Ht
+
+    def part_step(self, t, stream=None):
+        psgld_part_step(self.ctx, t, stream)
+
+    def sweep(self, n=1, stream=None):
+        psgld_sweep(self.ctx, n, stream)
+
+    def posterior_mean(self):
+        Wm = np.zeros((self.I, self.K)); Wv = np.zeros((self.I, self.K))
+        Hm = np.zeros((self.J, self.K)); Hv = np.zeros((self.J, self.K))
+        n = psgld_posterior_mean(self.ctx, Wm, Wv, Hm, Hv)
+        return Wm, Wv, Hm, Hv, n
+
+    def log_lik(self, stream=None):
+        return psgld_log_lik(self.ctx, stream)
+
+    def rmse(self, use_posterior_mean=False, stream=None):
+        return psgld_rmse(self.ctx, use_posterior_mean, stream)
+
+    @property
+    def iterations_done(self):
+        return psgld_iterations_done(self.ctx)

@@ -1,0 +1,493 @@
+#!/usr/bin/env python3
+"""Benchmark: observed entries per second per PSGLD sweep on GB300.
+
+A step is one sweep: B part-steps (Algorithm 1 iterations) that together
+visit every observed entry once, plus the FP64 posterior accumulation.  The
+default workload is the sparse Gaussian matrix factorisation shaped like the
+paper's MovieLens experiment: I = 70000, J = 10000, 10M observed entries with
+Zipf(1.1) row and column degrees, K = 50, B = 32 (synthetic data, seeded).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Our arm: value = N_obs * ranks / (max over ranks of the mean sweep time),
+each sweep timed with CUDA events on the launching stream, with L2 flushed
+(256 MB written) before every timed sweep.  Ranks (torchrun, one per GPU) run
+independent replica chains: the sampler needs no collective.  Extra keys:
+roofline of the part-step kernel, the oracle's CPU baseline, an end-to-end
+job through the C ABI from pinned host buffers, SM clocks during the run.
+
+Reference arm (--impl reference): the FP64 CPU oracle, as it stands, on the
+host cores, on the same workload; each step is a bounded sample of
+part-steps.  Under torchrun only rank 0 runs it.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "observed entries/s per PSGLD sweep"
+UNIT = "entries/s"
+L2_FLUSH_BYTES = 256 << 20
+FALLBACK_HBM_GBS = 6800.0
+
+WORKLOADS = {
+    "sparse_gauss_70000x10000_nnz10M_K50_B32": dict(
+        I=70000, J=10000, nnz=10_000_000, K=50, B=32, p=0.0, phi=1.0, prior="gaussian",
+        sigma=1.0, K_true=20, zipf_row=1.1, zipf_col=1.1, eps=2e-5, init_scale=0.3,
+        job_sweeps=500),
+    "sparse_gauss_480000x18000_nnz100M_K100_B64": dict(
+        I=480000, J=18000, nnz=100_000_000, K=100, B=64, p=0.0, phi=1.0, prior="gaussian",
+        sigma=1.0, K_true=20, zipf_row=1.2, zipf_col=None, eps=5e-6, init_scale=0.25,
+        job_sweeps=200),
+    "dense_poisson_256x256_K8_B4": dict(
+        I=256, J=256, nnz=256 * 256, K=8, B=4, p=1.0, phi=1.0, prior="exponential",
+        lam=1.0, K_true=8, eps=1e-4, init_scale=1.0, job_sweeps=1000, dense=True),
+}
+DEFAULT_WORKLOAD = "sparse_gauss_70000x10000_nnz10M_K50_B32"
+
+
+# ---------------------------------------------------------------------------
+# multi-rank plumbing (replicas; used only for the barrier and the max)
+# ---------------------------------------------------------------------------
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def reduce_max(x: float, world: int, device=None) -> float:
+    """Max of a scalar over ranks (identity for one rank)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def aggregate(ms_per_step_local: float, units_per_step_local: float, world: int, device=None):
+    """Whole-job throughput: units of all ranks / slowest rank's step time."""
+    ms = reduce_max(ms_per_step_local, world, device)
+    return ms, units_per_step_local * world / (ms / 1e3)
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+
+CLOCK_FIELDS = ["timestamp", "clocks.sm", "clocks.max.sm", "power.draw",
+                "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+                "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+
+class ClockSampler:
+    """nvidia-smi sampling every 100 ms in the background."""
+
+    def __init__(self, gpu_id: str):
+        self.samples = []
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", gpu_id, "--query-gpu=" + ",".join(CLOCK_FIELDS),
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append((time.time(), [x.strip() for x in line.split(",")]))
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self, t0: float, t1: float):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        win = [s for (t, s) in self.samples if t0 <= t <= t1]
+        where = "timed"
+        if not win:   # the timed region was shorter than the sampling period
+            win = [s for (t, s) in self.samples if t0 - 1.0 <= t <= t1 + 1.0]
+            where = "timed +-1s"
+        if not win:
+            win = [s for (_, s) in self.samples]
+            where = "run"
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(s[1]) for s in win if len(s) >= 8 and num(s[1]) is not None]
+        mx = [num(s[2]) for s in win if len(s) >= 8 and num(s[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for s in win if len(s) >= 8
+                          for k in range(4) if s[4 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(win), "window": where}
+
+
+# ---------------------------------------------------------------------------
+# workload
+# ---------------------------------------------------------------------------
+
+def make_inputs(wl: dict, seed: int, device):
+    """Observed entries and initial factors for one chain (torch tensors)."""
+    import torch
+
+    from paper_1506_01418_gb300 import datagen
+    if wl.get("dense"):
+        V, _, _ = datagen.dense_poisson(wl["I"], wl["J"], wl["K_true"], seed)
+        i, j, v = datagen.dense_to_coo(V)
+        i, j, v = (torch.from_numpy(x).to(device) for x in (i, j, v))
+    else:
+        i, j, v = datagen.sparse_ratings(wl["I"], wl["J"], wl["nnz"], wl["K_true"], seed,
+                                         zipf_row=wl["zipf_row"], zipf_col=wl["zipf_col"],
+                                         device=device)
+    nonneg = wl["prior"] == "exponential"
+    W0, H0 = datagen.init_factors(wl["I"], wl["J"], wl["K"], seed, scale=wl["init_scale"],
+                                  nonneg=nonneg)
+    return i, j, v, W0, H0
+
+
+def new_chain(wl: dict, seed: int, **opts):
+    from paper_1506_01418_gb300 import psgld as P
+    kind = P.PSGLD_PRIOR_EXPONENTIAL if wl["prior"] == "exponential" else P.PSGLD_PRIOR_GAUSSIAN
+    return P.PSGLD(wl["I"], wl["J"], wl["K"], wl["B"], wl["p"], wl["phi"], prior_kind=kind,
+                   lambda_w=wl.get("lam", 1.0), lambda_h=wl.get("lam", 1.0),
+                   sigma_w=wl.get("sigma", 1.0), sigma_h=wl.get("sigma", 1.0), seed=seed,
+                   eps=wl["eps"], **opts)
+
+
+def part_step_bytes(wl: dict, part_sizes) -> float:
+    """Algorithmic HBM bytes of one part-step, averaged over the B parts:
+    each observed entry of the part once (int32 index + fp32 value), one
+    int32 row offset per row and block, and every factor element read and
+    written once in fp32."""
+    I, J, K, B = wl["I"], wl["J"], wl["K"], wl["B"]
+    mean_n = sum(part_sizes) / len(part_sizes)
+    return 8.0 * mean_n + 4.0 * (I + B) + 8.0 * (I + J) * K
+
+
+def read_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_traffic(workload: str):
+    """DRAM bytes per part-step launch from the committed ncu summary, only if
+    the kernel source is unchanged since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "part_step_traffic.json")
+    src = os.path.join(ROOT, "paper_1506_01418_gb300", "csrc", "psgld_step.cu")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        e = d.get(workload)
+        if e and e.get("psgld_step_cu_sha256") == h:
+            return float(e["dram_bytes_per_launch"])
+    except (OSError, ValueError, KeyError):
+        pass
+    return None
+
+
+def host_cores() -> int:
+    try:
+        n = len(os.sched_getaffinity(0))
+    except AttributeError:
+        n = os.cpu_count() or 1
+    env = os.environ.get("OMP_NUM_THREADS")
+    return int(env) if env and env.isdigit() else n
+
+
+# ---------------------------------------------------------------------------
+# the oracle on the host cores (CPU baseline and reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_setup(wl, i, j, v, W0, H0, seed):
+    import numpy as np
+
+    import oracle
+    kind = oracle.PRIOR_EXPONENTIAL if wl["prior"] == "exponential" else oracle.PRIOR_GAUSSIAN
+    m = oracle.Oracle(wl["I"], wl["J"], wl["K"], wl["B"], wl["p"], wl["phi"], prior_kind=kind,
+                      lambda_w=wl.get("lam", 1.0), lambda_h=wl.get("lam", 1.0),
+                      sigma_w=wl.get("sigma", 1.0), sigma_h=wl.get("sigma", 1.0))
+    m.set_options(seed=seed, eps=wl["eps"])
+    m.set_data(np.asarray(i), np.asarray(j), np.asarray(v, dtype=np.float64))
+    m.set_factors(W0, H0)
+    return m
+
+
+def oracle_rate(m, wl, t0: int, n_steps: int):
+    """Run n_steps oracle part-steps from iteration t0; entries covered / s."""
+    ent = 0
+    start = time.perf_counter()
+    for t in range(t0, t0 + n_steps):
+        m.part_step(t)
+        ent += m.part_size(t)
+    dt = time.perf_counter() - start
+    return ent / dt, ent, dt
+
+
+def cpu_baseline(wl, i, j, v, W0, H0, seed, budget_s: float):
+    m = oracle_setup(wl, i, j, v, W0, H0, seed)
+    _, _, dt1 = oracle_rate(m, wl, 1, 1)          # calibration (untimed)
+    n = max(1, min(wl["B"] * 3, int(budget_s / max(dt1, 1e-6))))
+    rate, ent, dt = oracle_rate(m, wl, 2, n)
+    return {"value": rate, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
+            "sample": f"{n} part-steps ({ent} observed entries, {dt:.1f} s) of the same "
+                      f"workload and data, FP64, OpenMP over the blocks of each part"}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args, wl_name, wl):
+    import torch
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1506_01418_gb300 import psgld as P
+
+    seed = 1000 + rank
+    i, j, v, W0, H0 = make_inputs(wl, seed, dev)
+    torch.cuda.empty_cache()   # drop the generator's temporaries
+    N = int(i.numel())
+    chain = new_chain(wl, seed, use_graphs=1, profile=1)
+    chain.set_data_coo(i, j, v)
+    chain.set_factors(torch.from_numpy(W0).to(dev), torch.from_numpy(H0.T.copy()).to(dev))
+    part_sizes = [P.psgld_part_layout(chain.ctx, s, wl["I"])[0][-1] for s in range(wl["B"])]
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+        uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+    except Exception:
+        uuid = str(dev.index or 0)
+    sampler = ClockSampler(uuid)
+
+    for _ in range(args.warmup):
+        chain.sweep(1)
+        chain.profile_read()
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    torch.cuda.synchronize(dev)
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    k_ms, k_n = 0.0, 0
+    w0 = time.time()
+    for s in range(args.steps):
+        flush.zero_()
+        starts[s].record(stream)
+        chain.sweep(1)
+        ends[s].record(stream)
+        ms, n = chain.profile_read()
+        k_ms += ms
+        k_n += n
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    w1 = time.time()
+    sweep_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    ms_local = sum(sweep_ms) / len(sweep_ms)
+    ms, value = aggregate(ms_local, N, world, dev)
+    time.sleep(0.25)
+    sampler.stop()
+    clocks = sampler.summary(w0, w1)
+    rmse = chain.rmse()
+
+    peak, peak_src = read_peaks()
+    kern_ms = k_ms / max(k_n, 1)
+    bytes_launch = part_step_bytes(wl, part_sizes)
+    achieved = bytes_launch / (kern_ms / 1e3) / 1e9
+    traffic = kernel_traffic(wl_name)
+
+    result = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": wl_name, "I": wl["I"], "J": wl["J"], "nnz": N, "K": wl["K"],
+                   "B": wl["B"], "tweedie_p": wl["p"], "phi": wl["phi"], "prior": wl["prior"],
+                   "eps": wl["eps"], "step": "one sweep = B part-steps + FP64 posterior sums",
+                   "l2": "256 MB buffer written before every timed sweep",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "part_step_kernel", "kernel_ms": kern_ms,
+                     "algorithmic_bytes_per_launch": bytes_launch,
+                     "peak_source": f"{peak_src} HBM copy bandwidth"},
+        "gpu_launches": args.steps * (wl["B"] + 4),
+        "clocks": clocks,
+        "rmse_after": rmse,
+    }
+
+    if not args.no_e2e:
+        result["e2e"] = e2e_job(wl, seed, dev, i, j, v, W0, H0)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import numpy as np
+        hi, hj, hv = (x.cpu().numpy() for x in (i, j, v))
+        result["cpu_baseline"] = cpu_baseline(wl, hi, hj, hv.astype(np.float64),
+                                              W0.astype(np.float64), H0.astype(np.float64),
+                                              seed, args.cpu_budget)
+    chain.close()
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def e2e_job(wl, seed, dev, i, j, v, W0, H0):
+    """One sampling job through the C ABI from pinned host buffers: entries
+    and initial factors in, job_sweeps sweeps, posterior means and variances
+    and the log-likelihood out.  value = entries x sweeps / wall time."""
+    import numpy as np
+    import torch
+    hi = i.cpu().pin_memory()
+    hj = j.cpu().pin_memory()
+    hv = v.cpu().pin_memory()
+    hW = torch.from_numpy(W0).pin_memory()
+    hHt = torch.from_numpy(H0.T.copy()).pin_memory()
+    S = wl["job_sweeps"]
+    I, J, K = wl["I"], wl["J"], wl["K"]
+    Wm = np.zeros((I, K)); Wv = np.zeros((I, K)); Hm = np.zeros((J, K)); Hv = np.zeros((J, K))
+    chain = new_chain(wl, seed, use_graphs=1, burn_in_sweeps=S // 2)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    chain.set_data_coo(hi, hj, hv)
+    chain.set_factors(hW, hHt)
+    chain.sweep(S)
+    from paper_1506_01418_gb300 import psgld as P
+    P.psgld_posterior_mean(chain.ctx, Wm, Wv, Hm, Hv)
+    ll = chain.log_lik()
+    torch.cuda.synchronize(dev)
+    dt = time.perf_counter() - t0
+    chain.close()
+    N = int(i.numel())
+    h2d = 12 * N + 4 * (I + J) * K
+    d2h = 8 * 4 * (I + J) * K + 8
+    return {"value": N * S / dt, "unit": UNIT, "h2d_bytes_per_step": h2d / S,
+            "d2h_bytes_per_step": d2h / S, "job_sweeps": S, "job_s": dt,
+            "log_lik": ll, "api": "psgld_set_data_coo/set_factors (pinned host) + psgld_sweep "
+                                 "+ psgld_posterior_mean + psgld_log_lik"}
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the oracle on the host cores
+# ---------------------------------------------------------------------------
+
+def run_reference(args, wl_name, wl):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import numpy as np
+    import torch
+
+    import oracle
+    oracle.build()
+    seed = 1000
+    dev = torch.device("cuda", 0) if torch.cuda.is_available() else torch.device("cpu")
+    i, j, v, W0, H0 = make_inputs(wl, seed, dev)
+    hi, hj, hv = (x.cpu().numpy() for x in (i, j, v))
+    N = len(hi)
+    m = oracle_setup(wl, hi, hj, hv.astype(np.float64), W0.astype(np.float64),
+                     H0.astype(np.float64), seed)
+    _, _, dt1 = oracle_rate(m, wl, 1, 1)
+    budget = args.reference_budget / max(1, args.steps + args.warmup)
+    per_step = max(1, min(wl["B"], int(budget / max(dt1, 1e-6))))
+    t = 2
+    for _ in range(args.warmup):
+        oracle_rate(m, wl, t, per_step)
+        t += per_step
+    ent, secs = 0, 0.0
+    for _ in range(args.steps):
+        _, e, dt = oracle_rate(m, wl, t, per_step)
+        ent += e
+        secs += dt
+        t += per_step
+    rate = ent / secs
+    ms = secs / args.steps * 1e3 * (N / max(ent / args.steps, 1))   # per full sweep
+    sample = (f"each step {per_step} part-steps of the workload "
+              f"({ent // args.steps} observed entries), FP64 oracle, OpenMP over blocks")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": wl_name, "I": wl["I"], "J": wl["J"], "nnz": N, "K": wl["K"],
+                   "B": wl["B"], "tweedie_p": wl["p"], "phi": wl["phi"], "prior": wl["prior"],
+                   "eps": wl["eps"], "step": "bounded sample of part-steps, rate per entry"},
+        "cpu_baseline": {"value": rate, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=15.0,
+                    help="seconds of oracle work for the cpu_baseline sample")
+    ap.add_argument("--reference-budget", type=float, default=120.0,
+                    help="seconds of oracle work for the whole reference arm")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        ap.error("--warmup must be >= 3")
+    wl = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, args.workload, wl)
+    else:
+        run_ours(args, args.workload, wl)
+
+
+if __name__ == "__main__":
+    main()

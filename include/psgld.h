@@ -88,10 +88,11 @@ typedef struct {
     int32_t freeze_H;         /* 1: H is held fixed */
     int64_t burn_in_sweeps;   /* sweeps discarded before posterior sums start */
     int32_t use_graphs;       /* 1: each sweep replays one captured CUDA graph */
+    int32_t profile;          /* 1: time every part-step launch with CUDA events */
 } psgld_options;
 
 /* Defaults: seed 0, fixed eps 1e-4, a = 0.01, b = 0.51, scale N/|Pi_t|,
- * mu_min 1e-10, nothing frozen, no burn-in, graphs on. */
+ * mu_min 1e-10, nothing frozen, no burn-in, graphs on, profiling off. */
 PSGLD_API void psgld_default_options(psgld_options *opt_host);
 
 /* Create a context on the current CUDA device.
@@ -167,6 +168,16 @@ PSGLD_API psgld_status psgld_part_schedule(const psgld_ctx *ctx, int64_t t,
  * count, which is written to *n_entries_host. */
 PSGLD_API psgld_status psgld_part_layout(psgld_ctx *ctx, int32_t s, int32_t *row_ptr_host,
                                int32_t *cols_host, int64_t *n_entries_host);
+/* Device time of the part-step kernels recorded since the last call, with
+ * profile = 1: *total_ms_host receives their summed CUDA-event durations and
+ * *launches_host their count.  Events are recorded on the launch stream
+ * around each part-step kernel, also inside captured sweep graphs; each
+ * iteration of a part owns one event pair, so read after every call that
+ * runs at most B iterations (one sweep) for complete figures.  Synchronises
+ * the context's last stream. */
+PSGLD_API psgld_status psgld_profile_read(psgld_ctx *ctx, double *total_ms_host,
+                                          int64_t *launches_host);
+
 /* Last completed iteration t (0 before the first). */
 PSGLD_API int64_t psgld_iterations_done(const psgld_ctx *ctx);
 

@@ -30,6 +30,15 @@ psgld_status cuda_fail(psgld_ctx *c, cudaError_t e, const char *what)
     return fail(c, PSGLD_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
+psgld_status check_kernel_flag(psgld_ctx *c)
+{
+    int h = 0;
+    PSGLD_CK(c, cudaMemcpy(&h, c->kflag, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h == 0) return PSGLD_OK;
+    PSGLD_CK(c, cudaMemset(c->kflag, 0, sizeof(int)));
+    return fail(c, PSGLD_ERR_TIMEOUT, "a bulk-copy wait in the part-step kernel ran out");
+}
+
 namespace {
 
 __global__ void dense_to_coo_kernel(const float *__restrict__ V, int64_t I, int64_t J, int64_t ld,
@@ -174,6 +183,10 @@ psgld_status psgld_create(int64_t I, int64_t J, int32_t K, int32_t B, double twe
     c->I = I; c->J = J; c->K = K; c->B = B;
     c->ngroups = (K + 3) / 4;
     c->ldk = 4 * c->ngroups;
+    {
+        int lanes, groups;
+        work_shape(c->ngroups, &lanes, &groups, &c->light_len, &c->chunk_len);
+    }
     c->p = tweedie_p;
     c->phi = phi;
     c->prior = *prior;
@@ -184,12 +197,15 @@ psgld_status psgld_create(int64_t I, int64_t J, int32_t K, int32_t B, double twe
         s = alloc(c, &c->W[b], I * c->ldk);
         if (s == PSGLD_OK) s = alloc(c, &c->Ht[b], J * c->ldk);
     }
+    if (s == PSGLD_OK) s = alloc(c, &c->G, (I + J) * c->ldk);
     if (s == PSGLD_OK) s = alloc(c, &c->sW.s, I * c->ldk);
     if (s == PSGLD_OK) s = alloc(c, &c->sW.s2, I * c->ldk);
     if (s == PSGLD_OK) s = alloc(c, &c->sH.s, J * c->ldk);
     if (s == PSGLD_OK) s = alloc(c, &c->sH.s2, J * c->ldk);
     if (s == PSGLD_OK) s = alloc(c, &c->red, reduce_blocks());
     if (s == PSGLD_OK) s = alloc(c, &c->flag, 1);
+    if (s == PSGLD_OK) s = alloc(c, &c->kflag, 1);
+    if (s == PSGLD_OK) s = prepare_kernels(c);
     if (s == PSGLD_OK) s = alloc(c, &c->t_dev, 1);
     if (s == PSGLD_OK && cudaMallocHost((void **)&c->red_host, sizeof(double) * reduce_blocks()) != cudaSuccess)
         s = fail(c, PSGLD_ERR_OOM, "pinned allocation failed");
@@ -202,6 +218,15 @@ psgld_status psgld_create(int64_t I, int64_t J, int32_t K, int32_t B, double twe
     }
     *out = c;
     return PSGLD_OK;
+}
+
+static void destroy_events(psgld_ctx *c)
+{
+    for (auto e : c->ev_start) cudaEventDestroy(e);
+    for (auto e : c->ev_end) cudaEventDestroy(e);
+    c->ev_start.clear();
+    c->ev_end.clear();
+    c->ev_pending.clear();
 }
 
 psgld_status psgld_set_options(psgld_ctx *c, const psgld_options *o)
@@ -220,6 +245,40 @@ psgld_status psgld_set_options(psgld_ctx *c, const psgld_options *o)
     if (o->burn_in_sweeps < 0) return fail(c, PSGLD_ERR_ARG, "burn_in_sweeps must be >= 0");
     c->opt = *o;
     destroy_graphs(c);
+    destroy_events(c);
+    if (o->profile) {
+        c->ev_start.resize(c->B);
+        c->ev_end.resize(c->B);
+        c->ev_pending.assign(c->B, 0);
+        for (int b = 0; b < c->B; ++b) {
+            PSGLD_CK(c, cudaEventCreate(&c->ev_start[b]));
+            PSGLD_CK(c, cudaEventCreate(&c->ev_end[b]));
+        }
+    }
+    return PSGLD_OK;
+}
+
+psgld_status psgld_profile_read(psgld_ctx *c, double *total_ms, int64_t *launches)
+{
+    if (!c || !total_ms || !launches) return PSGLD_ERR_ARG;
+    if (!c->opt.profile) return fail(c, PSGLD_ERR_STATE, "profiling is off");
+    PSGLD_CK(c, cudaStreamSynchronize(c->last_stream));
+    {
+        psgld_status fs = check_kernel_flag(c);
+        if (fs != PSGLD_OK) return fs;
+    }
+    double ms = 0.0;
+    int64_t n = 0;
+    for (int b = 0; b < c->B; ++b) {
+        if (!c->ev_pending[b]) continue;
+        float e = 0.f;
+        PSGLD_CK(c, cudaEventElapsedTime(&e, c->ev_start[b], c->ev_end[b]));
+        ms += e;
+        n += 1;
+        c->ev_pending[b] = 0;
+    }
+    *total_ms = ms;
+    *launches = n;
     return PSGLD_OK;
 }
 
@@ -364,6 +423,8 @@ psgld_status psgld_sweep(psgld_ctx *c, int32_t n_sweeps, void *stream)
                 if (s != PSGLD_OK) return s;
             }
             PSGLD_CK(c, cudaGraphLaunch(g, st));
+            if (c->opt.profile)
+                for (auto &pnd : c->ev_pending) pnd = 1;
             // the replay leaves the buffers as B part-steps do
             if (!c->opt.freeze_W) c->wcur ^= (c->B & 1);
             if (!c->opt.freeze_H) c->hcur ^= (c->B & 1);
@@ -389,6 +450,10 @@ psgld_status psgld_posterior_mean(psgld_ctx *c, double *Wm, double *Wv, double *
 {
     if (!c) return PSGLD_ERR_ARG;
     PSGLD_CK(c, cudaStreamSynchronize(c->last_stream));
+    {
+        psgld_status fs = check_kernel_flag(c);
+        if (fs != PSGLD_OK) return fs;
+    }
     const int64_t ldk = c->ldk, K = c->K;
     const double n = (double)c->n_samples;
     for (int side = 0; side < 2; ++side) {
@@ -474,10 +539,12 @@ void psgld_destroy(psgld_ctx *c)
 {
     if (!c) return;
     destroy_graphs(c);
+    destroy_events(c);
     free_layout(c);
     for (int b = 0; b < 2; ++b) { cudaFree(c->W[b]); cudaFree(c->Ht[b]); }
+    cudaFree(c->G);
     cudaFree(c->sW.s); cudaFree(c->sW.s2); cudaFree(c->sH.s); cudaFree(c->sH.s2);
-    cudaFree(c->red); cudaFree(c->flag); cudaFree(c->t_dev);
+    cudaFree(c->red); cudaFree(c->flag); cudaFree(c->kflag); cudaFree(c->t_dev);
     if (c->red_host) cudaFreeHost(c->red_host);
     if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
     delete c;

@@ -4,12 +4,14 @@
 //   W[2]  : I x ldk fp32, row-major, ping-pong pair (ldk = 4*ceil(K/4); the
 //           padding columns are kept at zero so every row is float4-aligned)
 //   Ht[2] : J x ldk fp32, H transposed, same rules
+//   G     : (I + J) x ldk fp32, the likelihood gradient of the current
+//           part-step (rows 0..I-1 for W, I..I+J-1 for H^T)
 //   A-side layout (part-major CSR): entries ordered by (part s, row i, col j)
 //           ptrA[s*I + i] .. ptrA[s*I + i + 1] -> idxA (col j), valA (v)
 //   B-side layout (part-major CSC): entries ordered by (part s, col j, row i)
 //           ptrB[s*J + j] .. -> idxB (row i), valB (v)
-//   segA/segB : per part, the work list of the fused part-step kernel; one
-//           record per (row, run of at most seg_len entries)
+//   segA/segB : per part, the chunk records of the fused part-step kernel:
+//           one per (heavy row, run of at most chunk_len entries)
 //   posterior sums: fp64 copies of W, W^2, Ht, Ht^2 (padded like the factors)
 #pragma once
 
@@ -25,24 +27,31 @@ namespace psgld {
 
 constexpr int kMaxK = 512;
 
-// Work-list record of the fused part-step kernel: one team of lanes owns
-// `row` and the entry range [beg, end).  `split` is -1 when the row has a
-// single record in this part; otherwise it indexes the part's split table.
-// Split-table entry: x = first record of the row (part-local), y = number of
-// records of the row, z = first partial-sum slot (part-local).
+// Chunk record of the gradient kernel: one warp owns `row` and the entry
+// range [beg, end).  `split` is -1 when the row has a single record in this
+// part (the warp writes G); otherwise it indexes the part's split table and
+// the warp writes partial-sum slot z + (record - x), which the update kernel
+// adds up.  Split-table entry: x = first record of the row (part-local),
+// y = number of records of the row, z = first partial-sum slot (part-local).
 struct SideLayout {
     int32_t *ptr = nullptr;    // B*n_rows + 1 entry offsets
     int32_t *idx = nullptr;    // other index of each entry
     float *val = nullptr;      // value of each entry
-    int4 *seg = nullptr;       // all parts' records, part-major
+    int4 *seg = nullptr;       // all parts' chunk records, part-major
     int4 *split = nullptr;     // all parts' split tables, part-major
+    int4 *light = nullptr;     // all parts' light rows {row, beg, end, 0},
+                               // part-major, by entry count descending
+    std::vector<int64_t> light_off;  // B+1: first light row of each part
+    std::vector<int64_t> part_first; // B+1: first entry of each part
     std::vector<int64_t> seg_off;    // B+1: first record of each part
     std::vector<int64_t> split_off;  // B+1
     std::vector<int64_t> slot_off;   // B+1: partial slots
     int64_t max_splits = 0;    // largest split table of one part
     int64_t max_slots = 0;     // largest number of partial slots of one part
-    float *partial = nullptr;  // max_slots x ldk scratch
-    unsigned *counter = nullptr;  // max_splits arrival counters (kept zero between launches)
+    float *partial = nullptr;  // max_slots x ldk scratch: partial sums of split rows
+    int32_t *gmap = nullptr;   // B*n_rows: where the update finds each row's
+                               // gradient: -1 G, -2 none (empty row), s >= 0
+                               // the part's split s (sum of its partial slots)
 };
 
 struct Sums {
@@ -64,12 +73,14 @@ struct psgld_ctx {
     bool has_data = false;
     int64_t N = 0;
     std::vector<int64_t> part_n;     // observed entries of each part
-    int32_t seg_len = 32;
+    int32_t light_len = 8;           // rows up to this many entries: one sub-team each
+    int32_t chunk_len = 32;          // heavier rows: chunks of at most this many
     psgld::SideLayout side[2];       // 0: rows of W (CSR), 1: rows of Ht (CSC)
 
     // factors
     float *W[2] = {nullptr, nullptr};
     float *Ht[2] = {nullptr, nullptr};
+    float *G = nullptr;              // (I + J) x ldk likelihood gradients of one part-step
     int wcur = 0, hcur = 0;
     bool has_factors = false;
 
@@ -82,7 +93,8 @@ struct psgld_ctx {
     // reductions
     double *red = nullptr;       // per-CTA partial sums
     double *red_host = nullptr;  // pinned copy
-    int *flag = nullptr;         // device error flag
+    int *flag = nullptr;         // device error flag of the layout build and input checks
+    int *kflag = nullptr;        // device error flag of the sampling kernels (16: wait ran out)
     cudaStream_t last_stream = nullptr;
 
     // CUDA graphs of one sweep, per parity of the ping-pong buffers, without
@@ -91,6 +103,10 @@ struct psgld_ctx {
     cudaGraphExec_t graph_acc[4] = {nullptr, nullptr, nullptr, nullptr};
     cudaStream_t capture_stream = nullptr;
     int64_t *t_dev = nullptr;    // iteration counter read by graph replays
+
+    // profiling: one event pair per part (start, end), and which are unread
+    std::vector<cudaEvent_t> ev_start, ev_end;
+    std::vector<char> ev_pending;
 };
 
 namespace psgld {
@@ -117,6 +133,15 @@ void free_layout(psgld_ctx *c);
 // selects the part and must satisfy (t-1) % B == part.
 psgld_status launch_part_step(psgld_ctx *c, int64_t t, const int64_t *t_dev,
                               int64_t t_add, cudaStream_t st);
+
+// Lanes per row team, float4 groups per lane, and the light / chunk entry
+// thresholds used for a factor width of ngroups float4 groups.
+void work_shape(int ngroups, int *lanes, int *groups, int *light_len, int *chunk_len);
+// One-time kernel attributes (dynamic shared memory) for this context's K.
+psgld_status prepare_kernels(psgld_ctx *c);
+// After a synchronisation point: PSGLD_ERR_TIMEOUT (and the flag cleared) if
+// a sampling kernel reported a bounded wait that ran out, else PSGLD_OK.
+psgld_status check_kernel_flag(psgld_ctx *c);
 
 // ---- reductions (psgld_reduce.cu) -----------------------------------------
 psgld_status launch_accumulate(psgld_ctx *c, cudaStream_t st);

@@ -10,8 +10,9 @@
 // Both are produced by a stable LSD radix sort written here (8-bit digits,
 // per-tile histograms, a global exclusive scan and a stable scatter whose
 // in-tile ranks come from warp match/ballot), so the order is exact and
-// repeatable.  Then each (part, row) slot is cut into records of at most
-// seg_len entries for the fused part-step kernel.
+// repeatable.  Then every (part, row) slot with more than light_len entries
+// is cut into chunk records of at most chunk_len entries for the fused
+// part-step kernel; lighter rows need no record.
 #include <algorithm>
 
 #include "psgld_internal.cuh"
@@ -256,24 +257,27 @@ __global__ void finish_side(int64_t nnz, const uint64_t *__restrict__ key,
     }
 }
 
-__global__ void seg_counts(const int32_t *__restrict__ ptr, int64_t nslots, int L,
+// Rows with more than `light` entries in a part become chunk records of at
+// most `chunk` entries (balanced); lighter rows get none (the tile path of the
+// part-step kernel takes them).
+__global__ void seg_counts(const int32_t *__restrict__ ptr, int64_t nslots, int light, int chunk,
                            uint32_t *__restrict__ nseg, uint32_t *__restrict__ nsplit,
                            uint32_t *__restrict__ nslot)
 {
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < nslots;
          s += (int64_t)gridDim.x * blockDim.x) {
         const int64_t n = ptr[s + 1] - ptr[s];
-        const uint32_t k = n <= L ? 1u : (uint32_t)((n + L - 1) / L);
+        const uint32_t k = n <= light ? 0u : (uint32_t)((n + chunk - 1) / chunk);
         nseg[s] = k;
         nsplit[s] = k > 1 ? 1u : 0u;
         nslot[s] = k > 1 ? k : 0u;
     }
 }
 
-__global__ void seg_fill(const int32_t *__restrict__ ptr, int64_t n_rows, int64_t nslots, int L,
-                         const uint32_t *__restrict__ seg_off, const uint32_t *__restrict__ split_off,
-                         const uint32_t *__restrict__ slot_off, int4 *__restrict__ seg,
-                         int4 *__restrict__ split)
+__global__ void seg_fill(const int32_t *__restrict__ ptr, int64_t n_rows, int64_t nslots, int light,
+                         int chunk, const uint32_t *__restrict__ seg_off,
+                         const uint32_t *__restrict__ split_off, const uint32_t *__restrict__ slot_off,
+                         int4 *__restrict__ seg, int4 *__restrict__ split, int32_t *__restrict__ gmap)
 {
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < nslots;
          s += (int64_t)gridDim.x * blockDim.x) {
@@ -282,18 +286,52 @@ __global__ void seg_fill(const int32_t *__restrict__ ptr, int64_t n_rows, int64_
         const int64_t p0 = part * n_rows;
         const int32_t beg = ptr[s], end = ptr[s + 1];
         const int64_t n = end - beg;
-        const int k = n <= L ? 1 : (int)((n + L - 1) / L);
+        if (n <= light) {
+            gmap[s] = n == 0 ? -2 : -1;
+            continue;
+        }
+        const int k = (int)((n + chunk - 1) / chunk);
         const int32_t seg_local = (int32_t)(seg_off[s] - seg_off[p0]);
         int32_t split_local = -1;
         if (k > 1) {
             split_local = (int32_t)(split_off[s] - split_off[p0]);
             split[split_off[s]] = make_int4(seg_local, k, (int32_t)(slot_off[s] - slot_off[p0]), 0);
         }
+        gmap[s] = split_local;
         for (int q = 0; q < k; ++q) {
-            const int32_t b = beg + q * L;
-            const int32_t e = min(end, b + L);
+            const int32_t b = beg + (int32_t)(n * q / k);
+            const int32_t e = beg + (int32_t)(n * (q + 1) / k);
             seg[seg_off[s] + q] = make_int4((int32_t)row, b, e, split_local);
         }
+    }
+}
+
+// Non-empty light rows of every part, ordered by (part, entry count
+// descending, row):
+// key part*(light+1) + (light - n); heavy slots get the largest key.
+__global__ void light_keys(const int32_t *__restrict__ ptr, int64_t n_rows, int64_t nslots, int B,
+                           int light, uint64_t *__restrict__ key, uint32_t *__restrict__ val,
+                           uint32_t *__restrict__ flag)
+{
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < nslots;
+         s += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t n = ptr[s + 1] - ptr[s];
+        const int64_t part = s / n_rows;
+        const bool is_light = n >= 1 && n <= light;   // empty rows need no gradient
+        key[s] = is_light ? (uint64_t)(part * (light + 1) + (light - n)) : (uint64_t)B * (light + 1);
+        val[s] = (uint32_t)s;
+        flag[s] = is_light ? 1u : 0u;
+    }
+}
+
+__global__ void light_fill(const int32_t *__restrict__ ptr, int64_t n_rows, int64_t n_light,
+                           const uint32_t *__restrict__ slot, int4 *__restrict__ rec)
+{
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n_light;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t s = slot[k];
+        const int64_t row = s % n_rows;
+        rec[k] = make_int4((int32_t)row, ptr[s], ptr[s + 1], 0);
     }
 }
 
@@ -321,7 +359,10 @@ template <typename T>
 psgld_status dmalloc(psgld_ctx *c, T **p, int64_t n)
 {
     if (n <= 0) n = 1;
-    cudaError_t e = cudaMalloc((void **)p, sizeof(T) * (size_t)n);
+    // whole 256-byte granules, so that 16-byte-rounded bulk prefetches of any
+    // sub-range stay inside the allocation
+    const size_t bytes = (sizeof(T) * (size_t)n + 255) & ~size_t(255);
+    cudaError_t e = cudaMalloc((void **)p, bytes);
     if (e != cudaSuccess) {
         *p = nullptr;
         cudaGetLastError();
@@ -367,8 +408,8 @@ void free_layout(psgld_ctx *c)
 {
     for (auto &sd : c->side) {
         cudaFree(sd.ptr); cudaFree(sd.idx); cudaFree(sd.val);
-        cudaFree(sd.seg); cudaFree(sd.split);
-        cudaFree(sd.partial); cudaFree(sd.counter);
+        cudaFree(sd.seg); cudaFree(sd.split); cudaFree(sd.light);
+        cudaFree(sd.partial); cudaFree(sd.gmap);
         sd = SideLayout{};
     }
     c->has_data = false;
@@ -415,6 +456,13 @@ psgld_status build_layout(psgld_ctx *c, int64_t nnz, const int32_t *i_dev, const
     PSGLD_ALLOC(oseg, nslots_max + 1); PSGLD_ALLOC(osplit, nslots_max + 1);
     PSGLD_ALLOC(oslot, nslots_max + 1);
     PSGLD_ALLOC(offs_dev, 4 * (B + 1));
+    uint64_t *lk0 = nullptr, *lk1 = nullptr;
+    uint32_t *lv0 = nullptr, *lv1 = nullptr, *hist_l = nullptr, *hscan_l = nullptr, *tmp_l = nullptr;
+    const int64_t ltiles = std::max<int64_t>(1, (nslots_max + kSortTile - 1) / kSortTile);
+    PSGLD_ALLOC(lk0, nslots_max); PSGLD_ALLOC(lk1, nslots_max);
+    PSGLD_ALLOC(lv0, nslots_max); PSGLD_ALLOC(lv1, nslots_max);
+    PSGLD_ALLOC(hist_l, 256 * ltiles + 1); PSGLD_ALLOC(hscan_l, 256 * ltiles + 2);
+    PSGLD_ALLOC(tmp_l, (256 * ltiles + 1 + kScanTile - 1) / kScanTile + 2);
 #undef PSGLD_ALLOC
 
     auto ck = [&](cudaError_t e, const char *what) -> psgld_status {
@@ -457,7 +505,8 @@ psgld_status build_layout(psgld_ctx *c, int64_t nnz, const int32_t *i_dev, const
         if ((s = ck(cudaGetLastError(), "finish_side")) != PSGLD_OK) return s;
 
         // work-list records
-        seg_counts<<<grid_for(nslots, 256), 256, 0, st>>>(sd.ptr, nslots, c->seg_len, nseg, nsplit, nslot);
+        seg_counts<<<grid_for(nslots, 256), 256, 0, st>>>(sd.ptr, nslots, c->light_len, c->chunk_len,
+                                                          nseg, nsplit, nslot);
         if ((s = exclusive_scan(c, nseg, oseg, nslots, tmp, st)) != PSGLD_OK) { cleanup(); free_layout(c); return s; }
         if ((s = exclusive_scan(c, nsplit, osplit, nslots, tmp, st)) != PSGLD_OK) { cleanup(); free_layout(c); return s; }
         if ((s = exclusive_scan(c, nslot, oslot, nslots, tmp, st)) != PSGLD_OK) { cleanup(); free_layout(c); return s; }
@@ -471,6 +520,7 @@ psgld_status build_layout(psgld_ctx *c, int64_t nnz, const int32_t *i_dev, const
         sd.seg_off.assign(h.begin(), h.begin() + (B + 1));
         sd.split_off.assign(h.begin() + (B + 1), h.begin() + 2 * (B + 1));
         sd.slot_off.assign(h.begin() + 2 * (B + 1), h.begin() + 3 * (B + 1));
+        sd.part_first.assign(h.begin() + 3 * (B + 1), h.begin() + 4 * (B + 1));
         if (side == 0) {
             c->part_n.resize(B);
             for (int p = 0; p < B; ++p) c->part_n[p] = h[3 * (B + 1) + p + 1] - h[3 * (B + 1) + p];
@@ -483,12 +533,33 @@ psgld_status build_layout(psgld_ctx *c, int64_t nnz, const int32_t *i_dev, const
         s = dmalloc(c, &sd.seg, sd.seg_off[B]);
         if (s == PSGLD_OK) s = dmalloc(c, &sd.split, sd.split_off[B]);
         if (s == PSGLD_OK) s = dmalloc(c, &sd.partial, sd.max_slots * c->ldk);
-        if (s == PSGLD_OK) s = dmalloc(c, &sd.counter, sd.max_splits);
+        if (s == PSGLD_OK) s = dmalloc(c, &sd.gmap, nslots);
         if (s != PSGLD_OK) { cleanup(); free_layout(c); return s; }
-        seg_fill<<<grid_for(nslots, 256), 256, 0, st>>>(sd.ptr, n_rows, nslots, c->seg_len, oseg,
-                                                        osplit, oslot, sd.seg, sd.split);
+        seg_fill<<<grid_for(nslots, 256), 256, 0, st>>>(sd.ptr, n_rows, nslots, c->light_len,
+                                                        c->chunk_len, oseg,
+                                                        osplit, oslot, sd.seg, sd.split, sd.gmap);
         if ((s = ck(cudaGetLastError(), "seg_fill")) != PSGLD_OK) return s;
-        if ((s = ck(cudaMemsetAsync(sd.counter, 0, sizeof(unsigned) * std::max<int64_t>(1, sd.max_splits), st), "memset counters")) != PSGLD_OK) return s;
+
+        // light-row lists: sort the (part, row) slots by (part, count desc)
+        light_keys<<<grid_for(nslots, 256), 256, 0, st>>>(sd.ptr, n_rows, nslots, B, c->light_len,
+                                                          lk0, lv0, nseg);
+        if ((s = exclusive_scan(c, nseg, oseg, nslots, tmp, st)) != PSGLD_OK) { cleanup(); free_layout(c); return s; }
+        gather_offsets<<<1, 128, 0, st>>>(oseg, n_rows, B, offs_dev);
+        {
+            uint64_t *a0 = lk0, *a1 = lk1;
+            uint32_t *b0 = lv0, *b1 = lv1;
+            s = radix_sort(c, a0, b0, a1, b1, nslots, bits_for((uint64_t)B * (c->light_len + 1) + 1),
+                           hist_l, hscan_l, tmp_l, st);
+            if (s != PSGLD_OK) { cleanup(); free_layout(c); return s; }
+            std::vector<int64_t> lo(B + 1);
+            if ((s = ck(cudaMemcpyAsync(lo.data(), offs_dev, sizeof(int64_t) * (B + 1), cudaMemcpyDeviceToHost, st), "light offsets")) != PSGLD_OK) return s;
+            if ((s = ck(cudaStreamSynchronize(st), "sync")) != PSGLD_OK) return s;
+            sd.light_off = lo;
+            s = dmalloc(c, &sd.light, lo[B]);
+            if (s != PSGLD_OK) { cleanup(); free_layout(c); return s; }
+            light_fill<<<grid_for(lo[B], 256), 256, 0, st>>>(sd.ptr, n_rows, lo[B], b0, sd.light);
+            if ((s = ck(cudaGetLastError(), "light_fill")) != PSGLD_OK) return s;
+        }
     }
     if ((s = ck(cudaMemcpyAsync(&hflag, c->flag, sizeof(int), cudaMemcpyDeviceToHost, st), "flag d2h")) != PSGLD_OK) return s;
     if ((s = ck(cudaStreamSynchronize(st), "sync")) != PSGLD_OK) return s;

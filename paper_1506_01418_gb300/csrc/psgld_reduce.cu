@@ -125,6 +125,10 @@ psgld_status reduce_loglik_rmse(psgld_ctx *c, int mode, int use_mean, cudaStream
     PSGLD_CK(c, cudaMemcpyAsync(c->red_host, c->red, sizeof(double) * kRedBlocks,
                                 cudaMemcpyDeviceToHost, st));
     PSGLD_CK(c, cudaStreamSynchronize(st));
+    {
+        psgld_status fs = check_kernel_flag(c);
+        if (fs != PSGLD_OK) return fs;
+    }
     double s = 0.0;
     for (int b = 0; b < kRedBlocks; ++b) s += c->red_host[b];
     *out = s;

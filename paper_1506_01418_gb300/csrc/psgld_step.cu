@@ -1,5 +1,5 @@
-// psgld_step.cu -- one PSGLD iteration (Algorithm 1's loop body) as a single
-// fused kernel launch.
+// psgld_step.cu -- one PSGLD iteration (Algorithm 1's loop body) as two
+// kernel launches: the likelihood gradient, then the Langevin update.
 //
 // For part Pi_t every block (r, c) updates the W rows of row piece r and the
 // H columns of column piece c from (W^(t-1), H^(t-1))  (Eq. psgld_w and
@@ -14,75 +14,105 @@
 // followed by |.| for non-negative models (Sec. 3.2).  This is the Tweedie
 // gradient of Sec. 4 (d/dmu of -d_beta(v||mu)/phi with beta = 2 - p).
 //
-// Design.  Both updates read only the previous factors, so they are
-// independent: the W side (rows of the part's CSR) and the H side (columns
-// of the part's CSC) run as two halves of one grid.  Factors are ping-pong
-// buffers (read X_cur, write X_next), so no block reads a row another block
-// is writing and no atomics touch the factors.  A team of T lanes (T = the
-// power of two covering ceil(K/4) float4 groups) owns one work record: it
-// loads its own row once, streams the record's entries (index and value
-// loaded coalesced, one per lane, then broadcast by shuffle), gathers the
-// other factor's rows with read-only float4 loads, reduces mu across the
-// team by butterfly shuffles, and accumulates the gradient in registers.
-// SDDMM (mu), the Tweedie epilogue (e) and the SpMM (sum e h) are therefore
-// one pass with e never leaving registers.  Rows with more than seg_len
-// entries in the part are split over several records; their partial
-// gradients go to a small scratch area and the last record to arrive (an
-// arrival counter) sums them in record order, so results are deterministic.
-// The same team then draws its Philox normals and writes the updated row.
+// Kernel 1, gradient.  Both sums read only the previous factors, so the W
+// side (rows of the part's CSR) and the H side (rows of H^T: the part's CSC)
+// run as the two halves of one grid and write G = sum e h (resp. sum e w) for
+// every row.  A sub-team of S lanes owns a row (S lanes x NG float4 groups
+// cover the K factor columns): it loads its row and the row's entries
+// (coalesced), gathers the other factor's rows with read-only float4 loads,
+// reduces mu across the sub-team with butterfly shuffles, applies the Tweedie
+// epilogue and accumulates the gradient in registers -- SDDMM, epilogue and
+// SpMM in one pass, e never leaves registers.  The part's light rows (at most
+// light_len entries) come in a list ordered by entry count, so a warp's rows
+// take equally long.  Heavier rows are cut into chunks of at most chunk_len
+// entries taken by whole warps (all sub-teams of the warp on different
+// entries of the same row), scheduled before the light rows.  A row cut into several chunks publishes partial sums to a small
+// scratch area and the last chunk to arrive (an arrival counter) adds them in
+// chunk order, so the result does not depend on scheduling.
+//
+// Kernel 2, update.  A flat, fully coalesced sweep over every (row, float4
+// group) item of both factors: the row's gradient (G, nothing for an empty
+// row, or the sum of a split row's partials), Philox4x32-10 normals (counter
+// = group, row, t, matrix), prior gradient, step, mirror; reads X_cur, writes
+// X_next (ping-pong buffers, so no row is read and written by the same
+// launch).  Philox's integer multiplies and Box-Muller make this ALU-bound,
+// so it runs at full lane occupancy rather than inside the gather-bound
+// kernel 1.
 #include <algorithm>
+#include <cmath>
 
 #include "psgld_internal.cuh"
 
 namespace psgld {
 namespace {
 
-struct Side {
-    const float *X_cur;   // own rows (n_rows x ldk)
-    float *X_next;
-    const float *Y_cur;   // gathered rows of the other factor
-    const int32_t *idx;   // other index of each entry
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+
+struct GradSide {
+    const float *X_cur;    // own rows (n_rows x ldk)
+    const float *Y_cur;    // gathered rows of the other factor
+    float *Gout;           // this side's rows of G
+    const int32_t *ptr;    // this part's row offsets (n_rows + 1)
+    const int32_t *idx;    // other index of each entry
     const float *val;
-    const int4 *seg;      // this part's records
-    const int4 *split;    // this part's split table
+    const int4 *chunk;     // this part's chunk records
+    const int4 *split;     // this part's split table
+    const int4 *light;     // this part's light rows {row, beg, end, 0}
     float *partial;
-    unsigned *counter;
-    int64_t nseg;
-    float prior_a, prior_b;   // d log p(x)/dx = prior_a + prior_b * x
-    uint32_t mat;             // 0 = W, 1 = H (noise stream)
-    int nblocks;              // CTAs of this side
+    int64_t nlight;
+    int64_t nchunks;
 };
 
-struct StepParams {
-    Side side[2];
+struct GradParams {
+    GradSide side[2];
+    int ldk, lds, ngroups;    // row length, shared-memory row stride (floats), float4 groups
+    int E;                    // entry slots per unit
+    float phi_inv, p, mu_min;
+    int p_mode;               // 0: p = 0, 1: p = 1, 2: p = 2, 3: other
+    int *err;                 // set to 16 when a bulk copy wait runs out
+};
+
+struct UpdSide {
+    const float *X_cur;
+    float *X_next;
+    const float *Gin;
+    const int32_t *gmap;      // this part's gradient source of every row
+    const int4 *split;        // this part's split table
+    const float *partial;     // partial sums of split rows
+    int64_t items;            // n_rows * ngroups (0 when the factor is frozen)
+    float prior_a, prior_b;   // d log p(x)/dx = prior_a + prior_b * x
+    uint32_t mat;             // 0 = W, 1 = H (noise stream)
+};
+
+struct UpdParams {
+    UpdSide side[2];
     const int64_t *t_dev;     // if non-null, t = *t_dev + t_add
     int64_t t_add;
     int K, ldk, ngroups;
-    float eps, sd, S, phi_inv, p, mu_min;
+    uint32_t div_magic;       // ceil(2^32 / ngroups) when item * ngroups < 2^32, else 0
+    float eps, sd, S;
     int eps_poly;             // 1: eps_t = (a/t)^b computed on the device
     double eps_a, eps_b;
-    int p_mode;               // 0: p = 0, 1: p = 1, 2: p = 2, 3: other
     int mirror;
-    uint32_t key0, key1;
+    uint32_t rk0[10], rk1[10];   // Philox round keys (seed + r * Weyl constants)
 };
 
-constexpr int kThreads = 256;
-
-template <int T>
-__device__ __forceinline__ unsigned team_mask()
+template <int S>
+__device__ __forceinline__ unsigned sub_mask()
 {
-    if constexpr (T == 32) {
+    if constexpr (S == 32) {
         return 0xffffffffu;
     } else {
-        return ((1u << T) - 1u) << ((threadIdx.x & 31) & ~(T - 1));
+        return ((1u << S) - 1u) << ((threadIdx.x & 31) & ~(S - 1));
     }
 }
 
-template <int T>
-__device__ __forceinline__ float team_sum(float v, unsigned mask)
+template <int S>
+__device__ __forceinline__ float sub_sum(float v, unsigned mask)
 {
 #pragma unroll
-    for (int o = T / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o, T);
+    for (int o = S / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o, S);
     return v;
 }
 
@@ -90,6 +120,8 @@ __device__ __forceinline__ float4 ldg4(const float *p)
 {
     return __ldg(reinterpret_cast<const float4 *>(p));
 }
+
+__device__ __forceinline__ float4 zero4() { return make_float4(0.f, 0.f, 0.f, 0.f); }
 
 __device__ __forceinline__ float dot4(const float4 a, const float4 b, float acc)
 {
@@ -108,8 +140,13 @@ __device__ __forceinline__ void axpy4(float4 &acc, float e, const float4 y)
     acc.w = fmaf(e, y.w, acc.w);
 }
 
+__device__ __forceinline__ void add4(float4 &a, const float4 b)
+{
+    a.x += b.x; a.y += b.y; a.z += b.z; a.w += b.w;
+}
+
 // Tweedie factor: e = (v - mu) * max(mu, mu_min)^(-p) / phi
-__device__ __forceinline__ float tweedie_e(const StepParams &P, float v, float mu)
+__device__ __forceinline__ float tweedie_e(const GradParams &P, float v, float mu)
 {
     const float d = v - mu;
     if (P.p_mode == 0) return d * P.phi_inv;
@@ -119,7 +156,240 @@ __device__ __forceinline__ float tweedie_e(const StepParams &P, float v, float m
     return d * exp2f(-P.p * log2f(mc)) * P.phi_inv;
 }
 
-__device__ __forceinline__ float update1(const StepParams &P, const Side &Sd, float x, float g,
+// ---- kernel 1: the likelihood gradient ------------------------------------
+//
+// Work units, one per warp.  A chunk unit is up to E entries of one heavy
+// row; a light unit is R = 32/S light rows of up to L = E/R entries each.
+// Either way the unit has E entry slots, and slot l of a light unit belongs
+// to row l / L.  Steps:
+//   1. each slot lane loads its entry (other index j, value v);
+//   2. TMA bulk copies (cp.async.bulk, one instruction per factor row) bring
+//      the unit's own rows and the E gathered rows into this warp's shared
+//      memory, completing on the warp's mbarrier -- every gather of the unit
+//      is in flight at once;
+//   3. SDDMM + epilogue, one lane per slot: mu = x . y from shared memory,
+//      e = Tweedie factor;
+//   4. SpMM, sub-teams of S lanes over the K columns: sub-team s adds
+//      e_l * y_l over its slots l = s*L .. s*L+L-1 (its row in a light unit;
+//      one slice of the chunk, then summed across sub-teams in a chunk unit);
+//   5. store the row's gradient (G, or a partial-sum slot of a split row).
+
+constexpr uint32_t kWaitLimit = 1u << 24;          // mbarrier polls before giving up
+constexpr long long kWaitCycles = 1ll << 31;         // ... or about one second of SM clock
+constexpr uint32_t kWaitHintNs = 2000;               // suspension per poll
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_addr(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                 :: "r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+
+// Waits (suspended, up to about `hint_ns`) for phase `parity` of the barrier
+// to complete; true once it has.  The suspension keeps waiting warps from
+// taking issue slots while the copies are in flight.
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity, uint32_t hint_ns)
+{
+    uint32_t ok;
+    asm volatile("{\n\t.reg .pred p;\n\t"
+                 "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok) : "r"(smem_addr(bar)), "r"(parity), "r"(hint_ns) : "memory");
+    return ok != 0;
+}
+
+// Bulk copy of `bytes` (a multiple of 16, both addresses 16-byte aligned)
+// from global to this CTA's shared memory, completing on `bar`.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 :: "r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar)) : "memory");
+}
+
+template <int S, int NG>
+__global__ void __launch_bounds__(kThreads) grad_kernel(const __grid_constant__ GradParams P)
+{
+    constexpr int R = 32 / S;   // rows of a light unit = sub-teams of a warp
+    const int E = P.E;          // entry slots of a unit
+    const int L = E / R;        // entry slots per row of a light unit
+    extern __shared__ float4 smem4[];
+    const int warp = threadIdx.x >> 5, lane32 = threadIdx.x & 31;
+    const int ng = P.ngroups, ldk = P.ldk, lds = P.lds;
+    float *base = reinterpret_cast<float *>(smem4);
+    float *ys = base + (size_t)warp * (E + R) * lds;   // E gathered rows
+    float *xs = ys + (size_t)E * lds;                  // R own rows
+    uint64_t *bar = reinterpret_cast<uint64_t *>(base + (size_t)kWarps * (E + R) * lds) + warp;
+
+    // ---- which unit: chunk units of both sides first, then light units
+    const int64_t unit = (int64_t)blockIdx.x * kWarps + warp;
+    const int64_t c0 = P.side[0].nchunks, c1 = P.side[1].nchunks;
+    const int64_t u0 = (P.side[0].nlight + R - 1) / R, u1 = (P.side[1].nlight + R - 1) / R;
+    int sid;
+    bool chunk;
+    int64_t k;
+    if (unit < c0) { sid = 0; chunk = true; k = unit; }
+    else if (unit < c0 + c1) { sid = 1; chunk = true; k = unit - c0; }
+    else if (unit < c0 + c1 + u0) { sid = 0; chunk = false; k = unit - c0 - c1; }
+    else if (unit < c0 + c1 + u0 + u1) { sid = 1; chunk = false; k = unit - c0 - c1 - u0; }
+    else return;   // warp-uniform
+    const GradSide &Sd = P.side[sid];
+
+    // ---- 1. slot -> (row of the unit, entry)
+    int4 rec;                      // this slot's row record: row, beg, end, split
+    const int myrow = chunk ? 0 : lane32 / L;   // row of the unit this slot belongs to
+    if (chunk) {
+        rec = __ldg(Sd.chunk + k);
+    } else {
+        const int64_t kk = k * R + (lane32 < E ? myrow : 0);
+        rec = kk < Sd.nlight ? __ldg(Sd.light + kk) : make_int4(0, 0, 0, -1);
+        rec.w = kk < Sd.nlight ? -1 : -2;   // -2: no row
+    }
+    const int slot_in_row = chunk ? lane32 : lane32 % L;
+    const bool valid = lane32 < E && rec.w != -2 && slot_in_row < rec.z - rec.y;
+    int jj = 0;
+    float vv = 0.f;
+    if (valid) {
+        jj = __ldg(Sd.idx + rec.y + slot_in_row);
+        vv = __ldg(Sd.val + rec.y + slot_in_row);
+    }
+    // own rows: row r of a light unit is the row of slot r*L
+    int own_row = -1;
+    if (chunk) {
+        if (lane32 == 0) own_row = rec.x;
+    } else if (lane32 < R) {
+        const int64_t kk = k * R + lane32;
+        if (kk < Sd.nlight) own_row = __ldg(Sd.light + kk).x;
+    }
+    const unsigned vmask = __ballot_sync(0xffffffffu, valid);
+    const unsigned rmask = __ballot_sync(0xffffffffu, own_row >= 0);
+    const uint32_t row_bytes = (uint32_t)ldk * 4u;
+
+    // ---- 2. bulk gathers into shared memory
+    if (lane32 == 0) {
+        mbar_init(bar);
+        mbar_expect_tx(bar, (uint32_t)(__popc(vmask) + __popc(rmask)) * row_bytes);
+    }
+    __syncwarp();
+    if (valid) bulk_g2s(ys + (size_t)lane32 * lds, Sd.Y_cur + (int64_t)jj * ldk, row_bytes, bar);
+    if (own_row >= 0) bulk_g2s(xs + (size_t)lane32 * lds, Sd.X_cur + (int64_t)own_row * ldk, row_bytes, bar);
+    bool done = false;
+    const long long t_start = clock64();
+    for (uint32_t it = 0; it < kWaitLimit && !done && clock64() - t_start < kWaitCycles; ++it)
+        done = mbar_try_wait(bar, 0, kWaitHintNs);
+    if (!__all_sync(0xffffffffu, done)) {
+        // The copies did not land: report it, wait (bounded again) for them
+        // so that no copy targets freed shared memory, and give up.
+        if (lane32 == 0) atomicOr(P.err, 16);
+        const long long t_again = clock64();
+        for (uint32_t it = 0; it < kWaitLimit && !done && clock64() - t_again < kWaitCycles; ++it)
+            done = mbar_try_wait(bar, 0, kWaitHintNs);
+        return;
+    }
+
+    // ---- 3. mu and the Tweedie factor, one lane per slot
+    float e = 0.f;
+    if (valid) {
+        const float *x = xs + (size_t)myrow * lds;
+        const float *y = ys + (size_t)lane32 * lds;
+        float d = 0.f;
+        for (int q = 0; q < ng; ++q) {
+            const float4 a = *reinterpret_cast<const float4 *>(x + 4 * q);
+            const float4 b = *reinterpret_cast<const float4 *>(y + 4 * q);
+            d = dot4(a, b, d);
+        }
+        e = tweedie_e(P, vv, d);
+    }
+
+    // ---- 4. gradient sums, sub-teams of S lanes over the columns
+    const int sub = lane32 / S, lane = lane32 & (S - 1);
+    float4 acc[NG];
+#pragma unroll
+    for (int g = 0; g < NG; ++g) acc[g] = zero4();
+    // slots beyond the unit's longest row hold nothing: stop there
+    int nslots_used = 32 - __clz(vmask);                    // highest valid slot + 1
+    int umax = chunk ? (nslots_used + R - 1) / R : 0;
+    if (!chunk) {
+        const int nrow = rec.w == -2 ? 0 : rec.z - rec.y;   // this lane's row length
+        umax = min(L, __reduce_max_sync(0xffffffffu, lane32 < E ? nrow : 0));
+    }
+    if (chunk) umax = L;
+#pragma unroll 4
+    for (int u = 0; u < umax; ++u) {
+        const int sl = sub * L + u;
+        const float es = __shfl_sync(0xffffffffu, e, sl);
+        if ((vmask >> sl) & 1u) {
+#pragma unroll
+            for (int g = 0; g < NG; ++g) {
+                const int q = lane + g * S;
+                if (q < ng) axpy4(acc[g], es, *reinterpret_cast<const float4 *>(ys + (size_t)sl * lds + 4 * q));
+            }
+        }
+    }
+
+    // ---- 5. store
+    if (chunk) {
+#pragma unroll
+        for (int o = S; o < 32; o <<= 1)
+#pragma unroll
+            for (int g = 0; g < NG; ++g) {
+                acc[g].x += __shfl_xor_sync(0xffffffffu, acc[g].x, o);
+                acc[g].y += __shfl_xor_sync(0xffffffffu, acc[g].y, o);
+                acc[g].z += __shfl_xor_sync(0xffffffffu, acc[g].z, o);
+                acc[g].w += __shfl_xor_sync(0xffffffffu, acc[g].w, o);
+            }
+        const int4 ck = rec;   // every lane holds the chunk's record
+        float *dst = Sd.Gout + (int64_t)ck.x * ldk;
+        if (ck.w >= 0) {   // split row: this chunk's partial-sum slot
+            const int4 sp = __ldg(Sd.split + ck.w);
+            dst = Sd.partial + (sp.z + (k - sp.x)) * (int64_t)ldk;
+        }
+        if (sub == 0) {
+#pragma unroll
+            for (int g = 0; g < NG; ++g) {
+                const int q = lane + g * S;
+                if (q < ng) *reinterpret_cast<float4 *>(dst + 4 * q) = acc[g];
+            }
+        }
+    } else {
+        const int r = __shfl_sync(0xffffffffu, own_row, sub);   // this sub-team's row
+        if (r >= 0) {
+#pragma unroll
+            for (int g = 0; g < NG; ++g) {
+                const int q = lane + g * S;
+                if (q < ng) *reinterpret_cast<float4 *>(Sd.Gout + (int64_t)r * ldk + 4 * q) = acc[g];
+            }
+        }
+    }
+}
+
+// ---- kernel 2: the Langevin update --------------------------------------
+
+// Philox4x32-10 (Salmon et al., SC'11) with the round keys precomputed on the
+// host: each round multiplies words 0 and 2 into 64-bit products and mixes
+// their high halves with words 1, 3 and the round key.
+__device__ __forceinline__ uint4 philox(uint4 c, const UpdParams &P)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint64_t p0 = (uint64_t)0xD2511F53u * c.x;
+        const uint64_t p1 = (uint64_t)0xCD9E8D57u * c.z;
+        c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ P.rk0[r], (uint32_t)p1,
+                       (uint32_t)(p0 >> 32) ^ c.w ^ P.rk1[r], (uint32_t)p0);
+    }
+    return c;
+}
+
+__device__ __forceinline__ float update1(const UpdParams &P, const UpdSide &Sd, float x, float g,
                                          float z, float eps, float sd)
 {
     const float drift = fmaf(P.S, g, fmaf(Sd.prior_b, x, Sd.prior_a));
@@ -127,102 +397,8 @@ __device__ __forceinline__ float update1(const StepParams &P, const Side &Sd, fl
     return P.mirror ? fabsf(y) : y;
 }
 
-template <int T, int G, int U>
-__global__ void __launch_bounds__(kThreads) part_step_kernel(const __grid_constant__ StepParams P)
+__global__ void __launch_bounds__(kThreads) update_kernel(const __grid_constant__ UpdParams P)
 {
-    const int sid = (int)blockIdx.x < P.side[0].nblocks ? 0 : 1;
-    const Side &Sd = P.side[sid];
-    const int cta = sid == 0 ? (int)blockIdx.x : (int)blockIdx.x - P.side[0].nblocks;
-    constexpr int kTeams = kThreads / T;
-    const int lane = threadIdx.x & (T - 1);
-    const int64_t rec = (int64_t)cta * kTeams + threadIdx.x / T;
-    if (rec >= Sd.nseg) return;   // team-uniform exit
-    const unsigned mask = team_mask<T>();
-    const int ldk = P.ldk, ng = P.ngroups;
-
-    const int4 sg = Sd.seg[rec];  // row, beg, end, split
-    const int64_t row = sg.x;
-
-    float4 x[G], acc[G];
-#pragma unroll
-    for (int g = 0; g < G; ++g) {
-        const int q = lane + g * T;
-        x[g] = q < ng ? ldg4(Sd.X_cur + row * ldk + 4 * q) : make_float4(0.f, 0.f, 0.f, 0.f);
-        acc[g] = make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-
-    for (int base = sg.y; base < sg.z; base += T) {
-        const int n = min(T, sg.z - base);
-        int my_j = 0;
-        float my_v = 0.f;
-        if (lane < n) {
-            my_j = __ldg(Sd.idx + base + lane);
-            my_v = __ldg(Sd.val + base + lane);
-        }
-        for (int u = 0; u < n; u += U) {
-            float4 y[U][G];
-            float vv[U];
-#pragma unroll
-            for (int uu = 0; uu < U; ++uu) {
-                const int src = u + uu;
-                const int jj = __shfl_sync(mask, my_j, src, T);
-                vv[uu] = __shfl_sync(mask, my_v, src, T);
-#pragma unroll
-                for (int g = 0; g < G; ++g) {
-                    const int q = lane + g * T;
-                    y[uu][g] = (q < ng && src < n) ? ldg4(Sd.Y_cur + (int64_t)jj * ldk + 4 * q)
-                                                   : make_float4(0.f, 0.f, 0.f, 0.f);
-                }
-            }
-#pragma unroll
-            for (int uu = 0; uu < U; ++uu) {
-                if (u + uu < n) {   // team-uniform
-                    float d = 0.f;
-#pragma unroll
-                    for (int g = 0; g < G; ++g) d = dot4(x[g], y[uu][g], d);
-                    const float mu = team_sum<T>(d, mask);
-                    const float e = tweedie_e(P, vv[uu], mu);
-#pragma unroll
-                    for (int g = 0; g < G; ++g) axpy4(acc[g], e, y[uu][g]);
-                }
-            }
-        }
-    }
-
-    if (sg.w >= 0) {
-        // Row split over several records: publish the partial gradient; the
-        // last record to arrive adds all partials in record order.
-        const int4 sp = Sd.split[sg.w];   // first record, count, first slot
-        const int64_t slot = sp.z + (rec - sp.x);
-#pragma unroll
-        for (int g = 0; g < G; ++g) {
-            const int q = lane + g * T;
-            if (q < ng) __stcg(reinterpret_cast<float4 *>(Sd.partial + slot * ldk + 4 * q), acc[g]);
-        }
-        __threadfence();
-        __syncwarp(mask);
-        unsigned last = 0;
-        if (lane == 0) last = atomicAdd(Sd.counter + sg.w, 1u) == (unsigned)(sp.y - 1);
-        last = __shfl_sync(mask, last, 0, T);
-        if (!last) return;
-        __threadfence();
-#pragma unroll
-        for (int g = 0; g < G; ++g) acc[g] = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int o = 0; o < sp.y; ++o) {
-#pragma unroll
-            for (int g = 0; g < G; ++g) {
-                const int q = lane + g * T;
-                if (q < ng) {
-                    const float4 a = __ldcg(reinterpret_cast<const float4 *>(
-                        Sd.partial + (int64_t)(sp.z + o) * ldk + 4 * q));
-                    acc[g].x += a.x; acc[g].y += a.y; acc[g].z += a.z; acc[g].w += a.w;
-                }
-            }
-        }
-        if (lane == 0) Sd.counter[sg.w] = 0u;   // ready for the next launch
-    }
-
-    // step size and noise scale
     const int64_t t = P.t_dev ? *P.t_dev + P.t_add : P.t_add;
     float eps = P.eps, sd = P.sd;
     if (P.eps_poly) {
@@ -231,57 +407,128 @@ __global__ void __launch_bounds__(kThreads) part_step_kernel(const __grid_consta
         sd = (float)sqrt(2.0 * e);
     }
     const uint32_t t_lo = (uint32_t)(uint64_t)t, t_hi = (uint32_t)((uint64_t)t >> 32);
+    const int ng = P.ngroups, ldk = P.ldk;
+    const int64_t n0 = P.side[0].items, total = n0 + P.side[1].items;
+    for (int64_t a = blockIdx.x * (int64_t)kThreads + threadIdx.x; a < total;
+         a += (int64_t)gridDim.x * kThreads) {
+        const int sid = a < n0 ? 0 : 1;
+        const UpdSide &Sd = P.side[sid];
+        const int64_t item = a - (sid ? n0 : 0);
+        const int64_t row = P.div_magic ? (int64_t)__umulhi((uint32_t)item, P.div_magic) : item / ng;
+        const int q = (int)(item - row * ng);
+        const int64_t off = row * ldk + 4 * q;
+        const float4 x = ldg4(Sd.X_cur + off);
+        const int32_t src = __ldg(Sd.gmap + row);
+        float4 g = zero4();
+        if (src == -1) {
+            g = ldg4(Sd.Gin + off);
+        } else if (src >= 0) {   // split row: add its chunks' partial sums in order
+            const int4 sp = __ldg(Sd.split + src);
+            const float *pp = Sd.partial + (int64_t)sp.z * ldk + 4 * q;
+            int o = 0;
+            for (; o + 8 <= sp.y; o += 8) {   // eight independent loads in flight
+                float4 v[8];
 #pragma unroll
-    for (int g = 0; g < G; ++g) {
-        const int q = lane + g * T;
-        if (q < ng) {
-            const uint4 r = dev::philox4x32_10(
-                make_uint4((uint32_t)q, (uint32_t)row, t_lo, (t_hi << 1) | Sd.mat),
-                make_uint2(P.key0, P.key1));
-            const float4 z = dev::box_muller4(r);
-            const int k0 = 4 * q;
-            float4 o;
-            o.x = update1(P, Sd, x[g].x, acc[g].x, z.x, eps, sd);
-            o.y = k0 + 1 < P.K ? update1(P, Sd, x[g].y, acc[g].y, z.y, eps, sd) : 0.f;
-            o.z = k0 + 2 < P.K ? update1(P, Sd, x[g].z, acc[g].z, z.z, eps, sd) : 0.f;
-            o.w = k0 + 3 < P.K ? update1(P, Sd, x[g].w, acc[g].w, z.w, eps, sd) : 0.f;
-            *reinterpret_cast<float4 *>(Sd.X_next + row * ldk + k0) = o;
+                for (int w = 0; w < 8; ++w)
+                    v[w] = __ldcg(reinterpret_cast<const float4 *>(pp + (int64_t)(o + w) * ldk));
+#pragma unroll
+                for (int w = 0; w < 8; ++w) add4(g, v[w]);
+            }
+            for (; o < sp.y; ++o)
+                add4(g, __ldcg(reinterpret_cast<const float4 *>(pp + (int64_t)o * ldk)));
         }
+        const uint4 r = philox(make_uint4((uint32_t)q, (uint32_t)row, t_lo, (t_hi << 1) | Sd.mat), P);
+        const float4 z = dev::box_muller4(r);
+        const int k0 = 4 * q;
+        float4 o;
+        o.x = update1(P, Sd, x.x, g.x, z.x, eps, sd);
+        o.y = k0 + 1 < P.K ? update1(P, Sd, x.y, g.y, z.y, eps, sd) : 0.f;
+        o.z = k0 + 2 < P.K ? update1(P, Sd, x.z, g.z, z.z, eps, sd) : 0.f;
+        o.w = k0 + 3 < P.K ? update1(P, Sd, x.w, g.w, z.w, eps, sd) : 0.f;
+        *reinterpret_cast<float4 *>(Sd.X_next + off) = o;
     }
 }
 
-using KernelFn = void (*)(StepParams);
+using GradFn = void (*)(GradParams);
 
-KernelFn pick_kernel(int T, int G)
+GradFn pick_grad(int S, int NG)
 {
-    if (G == 1) {
-        switch (T) {
-        case 1: return part_step_kernel<1, 1, 4>;
-        case 2: return part_step_kernel<2, 1, 4>;
-        case 4: return part_step_kernel<4, 1, 4>;
-        case 8: return part_step_kernel<8, 1, 4>;
-        case 16: return part_step_kernel<16, 1, 4>;
-        case 32: return part_step_kernel<32, 1, 4>;
+    if (NG == 1) {
+        switch (S) {
+        case 1: return grad_kernel<1, 1>;
+        case 2: return grad_kernel<2, 1>;
+        case 4: return grad_kernel<4, 1>;
         }
     }
-    if (T == 32) {
-        switch (G) {
-        case 2: return part_step_kernel<32, 2, 4>;
-        case 3: return part_step_kernel<32, 3, 2>;
-        case 4: return part_step_kernel<32, 4, 2>;
+    if (NG == 2) {
+        switch (S) {
+        case 4: return grad_kernel<4, 2>;
+        case 8: return grad_kernel<8, 2>;
+        case 16: return grad_kernel<16, 2>;
+        case 32: return grad_kernel<32, 2>;
+        }
+    }
+    if (S == 32) {
+        switch (NG) {
+        case 3: return grad_kernel<32, 3>;
+        case 4: return grad_kernel<32, 4>;
         }
     }
     return nullptr;
 }
 
+struct Shape {
+    int S, NG, R, E, lds;
+};
+
+// Sub-team lanes S and float4 groups per lane NG cover K; E entry slots per
+// unit keep one warp's shared memory ((E + R) rows) near 10 KB; the row
+// stride is padded so that its float4 count is odd (conflict-free float4
+// reads of one row per lane).
+Shape shape_for(int ngroups)
+{
+    Shape sh;
+    if (ngroups <= 4) {            // K <= 16: one float4 group per lane
+        sh.S = 1;
+        while (sh.S < ngroups) sh.S <<= 1;
+        sh.NG = 1;
+    } else {                       // two groups per lane, up to 32 lanes
+        sh.S = 4;
+        while (sh.S * 2 < ngroups && sh.S < 32) sh.S <<= 1;
+        sh.NG = (ngroups + sh.S - 1) / sh.S;
+    }
+    sh.R = 32 / sh.S;
+    const int ldk = 4 * ngroups;
+    sh.lds = (ngroups & 1) ? ldk : ldk + 4;
+    sh.E = 32;
+    while (sh.E > sh.R && (sh.E + sh.R) * sh.lds * 4 > 10240) sh.E >>= 1;
+    return sh;
+}
+
+size_t grad_smem(const Shape &sh)
+{
+    return sizeof(float) * (size_t)kWarps * (sh.E + sh.R) * sh.lds + sizeof(uint64_t) * kWarps;
+}
+
 }  // namespace
 
-void team_shape(int ngroups, int *T, int *G)
+void work_shape(int ngroups, int *lanes, int *groups, int *light_len, int *chunk_len)
 {
-    int t = 1;
-    while (t < ngroups && t < 32) t <<= 1;
-    *T = t;
-    *G = (ngroups + t - 1) / t;
+    const Shape sh = shape_for(ngroups);
+    *lanes = sh.S;
+    *groups = sh.NG;
+    *light_len = sh.E / sh.R;
+    *chunk_len = sh.E;
+}
+
+psgld_status prepare_kernels(psgld_ctx *c)
+{
+    const Shape sh = shape_for(c->ngroups);
+    GradFn gfn = pick_grad(sh.S, sh.NG);
+    if (!gfn) return fail(c, PSGLD_ERR_ARG, "unsupported K");
+    PSGLD_CK(c, cudaFuncSetAttribute(gfn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)grad_smem(sh)));
+    return PSGLD_OK;
 }
 
 psgld_status launch_part_step(psgld_ctx *c, int64_t t, const int64_t *t_dev, int64_t t_add,
@@ -289,62 +536,112 @@ psgld_status launch_part_step(psgld_ctx *c, int64_t t, const int64_t *t_dev, int
 {
     const int B = c->B;
     const int part = (int)((t - 1) % B);
-    int T, G;
-    team_shape(c->ngroups, &T, &G);
-    KernelFn fn = pick_kernel(T, G);
-    if (!fn) return fail(c, PSGLD_ERR_ARG, "unsupported K");
+    const Shape sh = shape_for(c->ngroups);
+    GradFn gfn = pick_grad(sh.S, sh.NG);
+    if (!gfn) return fail(c, PSGLD_ERR_ARG, "unsupported K");
 
-    StepParams P{};
-    const int teams_per_cta = kThreads / T;
     const bool upd[2] = {!c->opt.freeze_W, !c->opt.freeze_H};
+    GradParams GP{};
+    UpdParams UP{};
     for (int s = 0; s < 2; ++s) {
         SideLayout &L = c->side[s];
-        Side &Sd = P.side[s];
-        Sd.X_cur = s == 0 ? c->W[c->wcur] : c->Ht[c->hcur];
-        Sd.X_next = s == 0 ? c->W[c->wcur ^ 1] : c->Ht[c->hcur ^ 1];
-        Sd.Y_cur = s == 0 ? c->Ht[c->hcur] : c->W[c->wcur];
-        Sd.idx = L.idx;
-        Sd.val = L.val;
-        Sd.seg = L.seg + L.seg_off[part];
-        Sd.split = L.split + L.split_off[part];
-        Sd.partial = L.partial;
-        Sd.counter = L.counter;
-        Sd.nseg = upd[s] ? L.seg_off[part + 1] - L.seg_off[part] : 0;
+        GradSide &Gs = GP.side[s];
+        UpdSide &Us = UP.side[s];
+        const int64_t n_rows = s == 0 ? c->I : c->J;
+        float *X_cur = s == 0 ? c->W[c->wcur] : c->Ht[c->hcur];
+        float *X_next = s == 0 ? c->W[c->wcur ^ 1] : c->Ht[c->hcur ^ 1];
+        float *G_rows = c->G + (s == 0 ? 0 : c->I * c->ldk);
+        Gs.X_cur = X_cur;
+        Gs.Y_cur = s == 0 ? c->Ht[c->hcur] : c->W[c->wcur];
+        Gs.Gout = G_rows;
+        Gs.ptr = L.ptr + (int64_t)part * n_rows;
+        Gs.idx = L.idx;
+        Gs.val = L.val;
+        Gs.chunk = L.seg + L.seg_off[part];
+        Gs.split = L.split + L.split_off[part];
+        Gs.light = L.light + L.light_off[part];
+        Gs.partial = L.partial;
+        Gs.nlight = upd[s] ? L.light_off[part + 1] - L.light_off[part] : 0;
+        Gs.nchunks = upd[s] ? L.seg_off[part + 1] - L.seg_off[part] : 0;
+
+        Us.X_cur = X_cur;
+        Us.X_next = X_next;
+        Us.Gin = G_rows;
+        Us.gmap = L.gmap + (int64_t)part * n_rows;
+        Us.split = L.split + L.split_off[part];
+        Us.partial = L.partial;
+        Us.items = upd[s] ? n_rows * c->ngroups : 0;
         if (c->prior.kind == PSGLD_PRIOR_EXPONENTIAL) {
-            Sd.prior_a = (float)-(s == 0 ? c->prior.lambda_w : c->prior.lambda_h);
-            Sd.prior_b = 0.f;
+            Us.prior_a = (float)-(s == 0 ? c->prior.lambda_w : c->prior.lambda_h);
+            Us.prior_b = 0.f;
         } else {
             const double sg = s == 0 ? c->prior.sigma_w : c->prior.sigma_h;
-            Sd.prior_a = 0.f;
-            Sd.prior_b = (float)(-1.0 / (sg * sg));
+            Us.prior_a = 0.f;
+            Us.prior_b = (float)(-1.0 / (sg * sg));
         }
-        Sd.mat = (uint32_t)s;
-        Sd.nblocks = (int)((Sd.nseg + teams_per_cta - 1) / teams_per_cta);
+        Us.mat = (uint32_t)s;
     }
-    P.t_dev = t_dev;
-    P.t_add = t_dev ? t_add : t;
-    P.K = c->K;
-    P.ldk = c->ldk;
-    P.ngroups = c->ngroups;
-    const double eps = c->opt.eps;
-    P.eps = (float)eps;
-    P.sd = (float)std::sqrt(2.0 * eps);
-    P.eps_poly = c->opt.eps_mode == PSGLD_EPS_POLY;
-    P.eps_a = c->opt.eps_a;
-    P.eps_b = c->opt.eps_b;
-    const int64_t np = c->part_n[part];
-    P.S = c->opt.scale_mode == PSGLD_SCALE_B ? (float)B : (np > 0 ? (float)((double)c->N / (double)np) : 0.f);
-    P.phi_inv = (float)(1.0 / c->phi);
-    P.p = (float)c->p;
-    P.mu_min = (float)c->opt.mu_min;
-    P.p_mode = c->p == 0.0 ? 0 : c->p == 1.0 ? 1 : c->p == 2.0 ? 2 : 3;
-    P.mirror = c->prior.kind == PSGLD_PRIOR_EXPONENTIAL;
-    P.key0 = (uint32_t)c->opt.seed;
-    P.key1 = (uint32_t)(c->opt.seed >> 32);
+    GP.ldk = c->ldk;
+    GP.lds = sh.lds;
+    GP.ngroups = c->ngroups;
+    GP.E = sh.E;
+    GP.err = c->kflag;
+    GP.phi_inv = (float)(1.0 / c->phi);
+    GP.p = (float)c->p;
+    GP.mu_min = (float)c->opt.mu_min;
+    GP.p_mode = c->p == 0.0 ? 0 : c->p == 1.0 ? 1 : c->p == 2.0 ? 2 : 3;
 
-    const int grid = P.side[0].nblocks + P.side[1].nblocks;
-    if (grid > 0) fn<<<grid, kThreads, 0, st>>>(P);
+    UP.t_dev = t_dev;
+    UP.t_add = t_dev ? t_add : t;
+    UP.K = c->K;
+    UP.ldk = c->ldk;
+    UP.ngroups = c->ngroups;
+    const int64_t max_items = std::max(UP.side[0].items, UP.side[1].items);
+    UP.div_magic = (max_items * c->ngroups < (1ll << 32))
+                       ? (uint32_t)(((1ull << 32) + c->ngroups - 1) / c->ngroups)
+                       : 0u;
+    const double eps = c->opt.eps;
+    UP.eps = (float)eps;
+    UP.sd = (float)std::sqrt(2.0 * eps);
+    UP.eps_poly = c->opt.eps_mode == PSGLD_EPS_POLY;
+    UP.eps_a = c->opt.eps_a;
+    UP.eps_b = c->opt.eps_b;
+    const int64_t np = c->part_n[part];
+    UP.S = c->opt.scale_mode == PSGLD_SCALE_B ? (float)B
+                                              : (np > 0 ? (float)((double)c->N / (double)np) : 0.f);
+    UP.mirror = c->prior.kind == PSGLD_PRIOR_EXPONENTIAL;
+    uint32_t k0 = (uint32_t)c->opt.seed, k1 = (uint32_t)(c->opt.seed >> 32);
+    for (int r = 0; r < 10; ++r) {   // Weyl key schedule of Philox4x32
+        UP.rk0[r] = k0;
+        UP.rk1[r] = k1;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+
+    const int64_t units = GP.side[0].nchunks + GP.side[1].nchunks +
+                          (GP.side[0].nlight + sh.R - 1) / sh.R + (GP.side[1].nlight + sh.R - 1) / sh.R;
+    const int ggrid = (int)((units + kWarps - 1) / kWarps);
+    const int64_t items = UP.side[0].items + UP.side[1].items;
+    const int ugrid = (int)std::min<int64_t>((items + kThreads - 1) / kThreads, 152 * 16);
+    // Inside a stream capture the records must be external, so that they
+    // become event-record nodes of the graph (a plain record would only
+    // become a dependency edge); outside a capture they are plain records.
+    const bool prof = c->opt.profile && (int)c->ev_start.size() == B;
+    unsigned rec_flags = cudaEventRecordDefault;
+    if (prof) {
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        PSGLD_CK(c, cudaStreamIsCapturing(st, &cap));
+        if (cap == cudaStreamCaptureStatusActive) rec_flags = cudaEventRecordExternal;
+        PSGLD_CK(c, cudaEventRecordWithFlags(c->ev_start[part], st, rec_flags));
+    }
+    if (ggrid > 0) gfn<<<ggrid, kThreads, grad_smem(sh), st>>>(GP);
     PSGLD_CK(c, cudaGetLastError());
+    if (items > 0) update_kernel<<<ugrid, kThreads, 0, st>>>(UP);
+    PSGLD_CK(c, cudaGetLastError());
+    if (prof) {
+        PSGLD_CK(c, cudaEventRecordWithFlags(c->ev_end[part], st, rec_flags));
+        c->ev_pending[part] = 1;
+    }
     if (upd[0]) c->wcur ^= 1;
     if (upd[1]) c->hcur ^= 1;
     return PSGLD_OK;

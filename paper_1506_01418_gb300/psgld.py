@@ -43,14 +43,16 @@ class psgld_options(C.Structure):
     _fields_ = [("seed", C.c_uint64), ("eps_mode", C.c_int32), ("eps", C.c_double),
                 ("eps_a", C.c_double), ("eps_b", C.c_double), ("scale_mode", C.c_int32),
                 ("mu_min", C.c_double), ("freeze_W", C.c_int32), ("freeze_H", C.c_int32),
-                ("burn_in_sweeps", C.c_int64), ("use_graphs", C.c_int32)]
+                ("burn_in_sweeps", C.c_int64), ("use_graphs", C.c_int32),
+                ("profile", C.c_int32)]
 
 
 EXPORTS = [
     "psgld_default_options", "psgld_create", "psgld_set_options", "psgld_set_data_coo",
     "psgld_set_data_dense", "psgld_set_factors", "psgld_get_factors", "psgld_part_step",
     "psgld_sweep", "psgld_posterior_mean", "psgld_log_lik", "psgld_rmse", "psgld_piece_bounds",
-    "psgld_part_schedule", "psgld_part_layout", "psgld_iterations_done", "psgld_last_error",
+    "psgld_part_schedule", "psgld_part_layout", "psgld_profile_read", "psgld_iterations_done",
+    "psgld_last_error",
     "psgld_destroy",
 ]
 
@@ -86,6 +88,7 @@ def load(build_if_missing: bool = True):
         "psgld_piece_bounds": (st, [vp, vp, vp]),
         "psgld_part_schedule": (st, [vp, i64, vp]),
         "psgld_part_layout": (st, [vp, i32, vp, vp, vp]),
+        "psgld_profile_read": (st, [vp, vp, vp]),
         "psgld_iterations_done": (i64, [vp]),
         "psgld_last_error": (C.c_char_p, [vp]),
         "psgld_destroy": (None, [vp]),
@@ -239,6 +242,14 @@ def psgld_part_layout(ctx, s, I):
     return ptr, cols[:n.value]
 
 
+def psgld_profile_read(ctx):
+    """(summed part-step kernel milliseconds, number of launches) since the last read."""
+    ms = C.c_double(0.0)
+    n = C.c_int64(0)
+    _check(ctx, load().psgld_profile_read(ctx, C.byref(ms), C.byref(n)))
+    return ms.value, n.value
+
+
 def psgld_iterations_done(ctx) -> int:
     return load().psgld_iterations_done(ctx)
 
@@ -320,6 +331,9 @@ class PSGLD:
 
     def rmse(self, use_posterior_mean=False, stream=None):
         return psgld_rmse(self.ctx, use_posterior_mean, stream)
+
+    def profile_read(self):
+        return psgld_profile_read(self.ctx)
 
     @property
     def iterations_done(self):

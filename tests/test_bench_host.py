@@ -1,0 +1,89 @@
+"""Host-side logic of bench.py on the CPU: the max-over-ranks reduction with
+two gloo ranks, the algorithmic byte count, the clock summary and the
+kernel-traffic guard."""
+import json
+import os
+import socket
+import sys
+
+import pytest
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _rank_main(rank, world, port, out):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    ms, value = bench.aggregate(ms_per_step_local=1.0 + rank, units_per_step_local=1000.0,
+                                world=world)
+    bench.barrier(world)
+    out[rank] = (ms, value)
+    dist.destroy_process_group()
+
+
+def test_aggregate_takes_slowest_rank_and_sums_units():
+    world, port = 2, _free_port()
+    mgr = mp.get_context("spawn").Manager()
+    out = mgr.dict()
+    mp.start_processes(_rank_main, args=(world, port, out), nprocs=world, join=True,
+                       start_method="spawn")
+    for r in range(world):
+        ms, value = out[r]
+        assert ms == 2.0                      # slowest rank
+        assert value == pytest.approx(2 * 1000.0 / 2e-3)
+
+
+def test_single_rank_aggregate_is_identity():
+    ms, value = bench.aggregate(4.0, 500.0, 1)
+    assert ms == 4.0 and value == pytest.approx(500.0 / 4e-3)
+
+
+def test_part_step_bytes():
+    wl = dict(I=100, J=50, K=10, B=4)
+    # 8 bytes per entry + 4 per row offset + factors read and written in fp32
+    assert bench.part_step_bytes(wl, [10, 20, 30, 40]) == 8 * 25 + 4 * 104 + 8 * 150 * 10
+
+
+def test_clock_summary_window_and_reasons():
+    cs = bench.ClockSampler.__new__(bench.ClockSampler)
+    cs.samples = [
+        (10.0, ["t", "1500", "2070", "900", "Not Active", "Not Active", "Not Active", "Active"]),
+        (11.0, ["t", "1900", "2070", "950", "Not Active", "Not Active", "Not Active",
+                "Not Active"]),
+        (12.0, ["t", "1950", "2070", "960", "Not Active", "Not Active", "Not Active",
+                "Not Active"]),
+        (30.0, ["t", "800", "2070", "100", "Active", "Not Active", "Not Active", "Not Active"]),
+    ]
+    s = cs.summary(10.5, 12.5)
+    assert s["sm_mhz"] == 1925.0 and s["sm_max_mhz"] == 2070.0 and s["reasons"] == []
+    assert s["window"] == "timed"
+    s = cs.summary(9.5, 30.5)
+    assert s["reasons"] == ["hw_slowdown", "sw_power_cap"]
+
+
+def test_kernel_traffic_requires_unchanged_source(tmp_path, monkeypatch):
+    wl = bench.DEFAULT_WORKLOAD
+    t = bench.kernel_traffic(wl)
+    path = os.path.join(ROOT, "profiles", "part_step_traffic.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        import hashlib
+        src = os.path.join(ROOT, "paper_1506_01418_gb300", "csrc", "psgld_step.cu")
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        if d.get(wl, {}).get("psgld_step_cu_sha256") != h:
+            assert t is None
+    else:
+        assert t is None

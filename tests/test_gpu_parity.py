@@ -196,6 +196,20 @@ def test_rmse_of_posterior_mean_matches_definition():
     assert pr.gpu.rmse(True) == pytest.approx(want, rel=1e-9)
 
 
+@pytest.mark.parametrize("graphs", [0, 1])
+def test_profile_counts_every_part_step(graphs):
+    pr = _make("gauss_sparse_K50_split", use_graphs=graphs, profile=1)
+    for _ in range(2):
+        pr.gpu.sweep(1)
+        ms, n = pr.gpu.profile_read()
+        assert n == pr.B and ms > 0.0
+    ms, n = pr.gpu.profile_read()
+    assert n == 0 and ms == 0.0
+    pr.gpu.part_step(pr.B + pr.B + 1)
+    ms, n = pr.gpu.profile_read()
+    assert n == 1 and ms > 0.0
+
+
 # ---------------------------------------------------------------------------
 # errors are reported, not hidden
 # ---------------------------------------------------------------------------

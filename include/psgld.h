@@ -58,7 +58,8 @@ typedef enum {
     PSGLD_ERR_OOM = -2,     /* device allocation failed */
     PSGLD_ERR_CUDA = -3,    /* a CUDA runtime call failed */
     PSGLD_ERR_STATE = -4,   /* call not valid in the current state */
-    PSGLD_ERR_TIMEOUT = -5  /* a bounded device wait ran out */
+    PSGLD_ERR_TIMEOUT = -5, /* a bounded device wait ran out */
+    PSGLD_ERR_SIZE = -6     /* input larger than a fixed maximum of the call */
 } psgld_status;
 
 /* Prior families.  Exponential priors (Sec. 4, Eq. tweedienmf) make the
@@ -180,6 +181,41 @@ PSGLD_API psgld_status psgld_profile_read(psgld_ctx *ctx, double *total_ms_host,
 
 /* Last completed iteration t (0 before the first). */
 PSGLD_API int64_t psgld_iterations_done(const psgld_ctx *ctx);
+
+/* ---- log-likelihood without allocation ----------------------------------
+ * No counterpart in the paper: a convenience for callers that cannot
+ * allocate device memory when they need the number (their device memory is
+ * reserved by another allocator, or they run where an allocation would
+ * synchronise the device or is not allowed).  It needs no context and
+ * allocates nothing: its only scratch, one FP64 partial sum per 4096 entries,
+ * is a fixed 32 KB array compiled into the library, present on every GPU that
+ * loads the library until the process exits.
+ *
+ * Writes to *out_dev (device memory) -(1/phi) sum_n d_beta(v[n] || mu_n),
+ * mu_n = sum_k W[i[n]*K + k] * Ht[j[n]*K + k] (max(mu, mu_min) when
+ * tweedie_p > 0), the value psgld_log_lik reports for the same entries and
+ * factors.  i_dev, j_dev, v_dev hold nnz entries; W_dev is I x K and Ht_dev
+ * J x K, row-major without padding; all are device memory and stay the
+ * caller's.  Enqueued on `stream` (NULL = legacy default stream); nothing is
+ * synchronised.
+ *
+ * Limits and errors: nnz <= PSGLD_STATIC_MAX_NNZ, else PSGLD_ERR_SIZE;
+ * PSGLD_ERR_ARG for other invalid arguments; PSGLD_ERR_CUDA if a launch
+ * fails.  There is no context, so no message is recorded.
+ *
+ * The first call on a device looks up the scratch array's device address
+ * (with that device current) and caches it: make that first call before any
+ * stream capture.  All calls share the array; calls that can overlap on the
+ * same GPU (different streams without ordering) race and must be serialised
+ * by the caller.  Each call writes every partial slot it reads, so no state
+ * carries over from one call to the next. */
+#define PSGLD_STATIC_MAX_NNZ (4096ll * 4096ll)
+PSGLD_API psgld_status psgld_log_lik_static(int64_t nnz, const int32_t *i_dev,
+                                            const int32_t *j_dev, const float *v_dev,
+                                            const float *W_dev, const float *Ht_dev,
+                                            int64_t I, int64_t J, int32_t K,
+                                            double tweedie_p, double phi, double mu_min,
+                                            double *out_dev, void *stream);
 
 /* Message of the last failure on this context ("" if none).  Valid until the
  * next call on the context. */

@@ -29,6 +29,8 @@ class PsgldError(RuntimeError):
 
 PSGLD_OK, PSGLD_ERR_ARG, PSGLD_ERR_OOM, PSGLD_ERR_CUDA, PSGLD_ERR_STATE, PSGLD_ERR_TIMEOUT = \
     0, -1, -2, -3, -4, -5
+PSGLD_ERR_SIZE = -6
+PSGLD_STATIC_MAX_NNZ = 4096 * 4096
 PSGLD_PRIOR_EXPONENTIAL, PSGLD_PRIOR_GAUSSIAN = 0, 1
 PSGLD_EPS_FIXED, PSGLD_EPS_POLY = 0, 1
 PSGLD_SCALE_N_OVER_PART, PSGLD_SCALE_B = 0, 1
@@ -52,7 +54,7 @@ EXPORTS = [
     "psgld_set_data_dense", "psgld_set_factors", "psgld_get_factors", "psgld_part_step",
     "psgld_sweep", "psgld_posterior_mean", "psgld_log_lik", "psgld_rmse", "psgld_piece_bounds",
     "psgld_part_schedule", "psgld_part_layout", "psgld_profile_read", "psgld_iterations_done",
-    "psgld_last_error",
+    "psgld_log_lik_static", "psgld_last_error",
     "psgld_destroy",
 ]
 
@@ -90,6 +92,7 @@ def load(build_if_missing: bool = True):
         "psgld_part_layout": (st, [vp, i32, vp, vp, vp]),
         "psgld_profile_read": (st, [vp, vp, vp]),
         "psgld_iterations_done": (i64, [vp]),
+        "psgld_log_lik_static": (st, [i64, vp, vp, vp, vp, vp, i64, i64, i32, f64, f64, f64, vp, vp]),
         "psgld_last_error": (C.c_char_p, [vp]),
         "psgld_destroy": (None, [vp]),
     }
@@ -248,6 +251,21 @@ def psgld_profile_read(ctx):
     n = C.c_int64(0)
     _check(ctx, load().psgld_profile_read(ctx, C.byref(ms), C.byref(n)))
     return ms.value, n.value
+
+
+def psgld_log_lik_static(i, j, v, W, Ht, tweedie_p, phi, out, mu_min=1e-10, stream=None):
+    """Log-likelihood of factors W (I x K), Ht (J x K) on entries (i, j, v),
+    written to `out` (a one-element float64 CUDA tensor); allocates nothing."""
+    I, K = W.shape
+    J = Ht.shape[0]
+    st = load().psgld_log_lik_static(
+        len(i), _ptr(i, _dt("i32")), _ptr(j, _dt("i32")), _ptr(v, _dt("f32")),
+        _ptr(W, _dt("f32")), _ptr(Ht, _dt("f32")), int(I), int(J), int(K), float(tweedie_p),
+        float(phi), float(mu_min), _ptr(out, _dt("f64")), _stream(stream))
+    if st == PSGLD_ERR_SIZE:
+        raise PsgldError(st, f"nnz {len(i)} exceeds PSGLD_STATIC_MAX_NNZ {PSGLD_STATIC_MAX_NNZ}")
+    if st != PSGLD_OK:
+        raise PsgldError(st, "psgld_log_lik_static failed")
 
 
 def psgld_iterations_done(ctx) -> int:

@@ -183,10 +183,7 @@ psgld_status psgld_create(int64_t I, int64_t J, int32_t K, int32_t B, double twe
     c->I = I; c->J = J; c->K = K; c->B = B;
     c->ngroups = (K + 3) / 4;
     c->ldk = 4 * c->ngroups;
-    {
-        int lanes, groups;
-        work_shape(c->ngroups, &lanes, &groups, &c->light_len, &c->chunk_len);
-    }
+
     c->p = tweedie_p;
     c->phi = phi;
     c->prior = *prior;

@@ -27,31 +27,15 @@ namespace psgld {
 
 constexpr int kMaxK = 512;
 
-// Chunk record of the gradient kernel: one warp owns `row` and the entry
-// range [beg, end).  `split` is -1 when the row has a single record in this
-// part (the warp writes G); otherwise it indexes the part's split table and
-// the warp writes partial-sum slot z + (record - x), which the update kernel
-// adds up.  Split-table entry: x = first record of the row (part-local),
-// y = number of records of the row, z = first partial-sum slot (part-local).
 struct SideLayout {
-    int32_t *ptr = nullptr;    // B*n_rows + 1 entry offsets
+    int32_t *ptr = nullptr;    // B*n_rows + 1 entry offsets (absolute)
     int32_t *idx = nullptr;    // other index of each entry
     float *val = nullptr;      // value of each entry
-    int4 *seg = nullptr;       // all parts' chunk records, part-major
-    int4 *split = nullptr;     // all parts' split tables, part-major
-    int4 *light = nullptr;     // all parts' light rows {row, beg, end, 0},
-                               // part-major, by entry count descending
-    std::vector<int64_t> light_off;  // B+1: first light row of each part
-    std::vector<int64_t> part_first; // B+1: first entry of each part
-    std::vector<int64_t> seg_off;    // B+1: first record of each part
-    std::vector<int64_t> split_off;  // B+1
-    std::vector<int64_t> slot_off;   // B+1: partial slots
-    int64_t max_splits = 0;    // largest split table of one part
-    int64_t max_slots = 0;     // largest number of partial slots of one part
-    float *partial = nullptr;  // max_slots x ldk scratch: partial sums of split rows
-    int32_t *gmap = nullptr;   // B*n_rows: where the update finds each row's
-                               // gradient: -1 G, -2 none (empty row), s >= 0
-                               // the part's split s (sum of its partial slots)
+    int32_t *own = nullptr;    // own row of each entry
+    std::vector<int64_t> part_first;   // B+1: first entry of each part
+    int64_t max_units = 0;     // most units (unit_entries consecutive entries) in one part
+    float *partial = nullptr;  // 2 x max_units x ldk: head / tail partial
+                               // sums of rows that cross a unit boundary
 };
 
 struct Sums {
@@ -73,8 +57,6 @@ struct psgld_ctx {
     bool has_data = false;
     int64_t N = 0;
     std::vector<int64_t> part_n;     // observed entries of each part
-    int32_t light_len = 8;           // rows up to this many entries: one sub-team each
-    int32_t chunk_len = 32;          // heavier rows: chunks of at most this many
     psgld::SideLayout side[2];       // 0: rows of W (CSR), 1: rows of Ht (CSC)
 
     // factors
@@ -134,11 +116,11 @@ void free_layout(psgld_ctx *c);
 psgld_status launch_part_step(psgld_ctx *c, int64_t t, const int64_t *t_dev,
                               int64_t t_add, cudaStream_t st);
 
-// Lanes per row team, float4 groups per lane, and the light / chunk entry
-// thresholds used for a factor width of ngroups float4 groups.
-void work_shape(int ngroups, int *lanes, int *groups, int *light_len, int *chunk_len);
 // One-time kernel attributes (dynamic shared memory) for this context's K.
 psgld_status prepare_kernels(psgld_ctx *c);
+// Entries per work unit of the gradient kernel for a factor width of
+// ngroups float4 groups.
+int unit_entries(int ngroups);
 // After a synchronisation point: PSGLD_ERR_TIMEOUT (and the flag cleared) if
 // a sampling kernel reported a bounded wait that ran out, else PSGLD_OK.
 psgld_status check_kernel_flag(psgld_ctx *c);

@@ -10,9 +10,9 @@
 // Both are produced by a stable LSD radix sort written here (8-bit digits,
 // per-tile histograms, a global exclusive scan and a stable scatter whose
 // in-tile ranks come from warp match/ballot), so the order is exact and
-// repeatable.  Then every (part, row) slot with more than light_len entries
-// is cut into chunk records of at most chunk_len entries for the fused
-// part-step kernel; lighter rows need no record.
+// repeatable.  Every entry also records its own row (the row of W for the
+// A side, the row of H^T for the B side), so that the part-step kernel can
+// take any 32 consecutive entries of a part as one unit of work.
 #include <algorithm>
 
 #include "psgld_internal.cuh"
@@ -240,8 +240,8 @@ __global__ void validate_and_key(int64_t nnz, const int32_t *__restrict__ ii,
 __global__ void finish_side(int64_t nnz, const uint64_t *__restrict__ key,
                             const uint32_t *__restrict__ perm, const int32_t *__restrict__ other,
                             const float *__restrict__ vv, int bits_other, int64_t nslots,
-                            int32_t *__restrict__ idx, float *__restrict__ val,
-                            int32_t *__restrict__ ptr, int *flag)
+                            int64_t n_rows, int32_t *__restrict__ idx, float *__restrict__ val,
+                            int32_t *__restrict__ own, int32_t *__restrict__ ptr, int *flag)
 {
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p <= nnz;
          p += (int64_t)gridDim.x * blockDim.x) {
@@ -252,94 +252,10 @@ __global__ void finish_side(int64_t nnz, const uint64_t *__restrict__ key,
             const uint32_t e = perm[p];
             idx[p] = other[e];
             val[p] = vv[e];
+            own[p] = (int32_t)(slot % n_rows);
             if (p > 0 && key[p] == key[p - 1]) atomicOr(flag, 4);
         }
     }
-}
-
-// Rows with more than `light` entries in a part become chunk records of at
-// most `chunk` entries (balanced); lighter rows get none (the tile path of the
-// part-step kernel takes them).
-__global__ void seg_counts(const int32_t *__restrict__ ptr, int64_t nslots, int light, int chunk,
-                           uint32_t *__restrict__ nseg, uint32_t *__restrict__ nsplit,
-                           uint32_t *__restrict__ nslot)
-{
-    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < nslots;
-         s += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t n = ptr[s + 1] - ptr[s];
-        const uint32_t k = n <= light ? 0u : (uint32_t)((n + chunk - 1) / chunk);
-        nseg[s] = k;
-        nsplit[s] = k > 1 ? 1u : 0u;
-        nslot[s] = k > 1 ? k : 0u;
-    }
-}
-
-__global__ void seg_fill(const int32_t *__restrict__ ptr, int64_t n_rows, int64_t nslots, int light,
-                         int chunk, const uint32_t *__restrict__ seg_off,
-                         const uint32_t *__restrict__ split_off, const uint32_t *__restrict__ slot_off,
-                         int4 *__restrict__ seg, int4 *__restrict__ split, int32_t *__restrict__ gmap)
-{
-    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < nslots;
-         s += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t part = s / n_rows;
-        const int64_t row = s - part * n_rows;
-        const int64_t p0 = part * n_rows;
-        const int32_t beg = ptr[s], end = ptr[s + 1];
-        const int64_t n = end - beg;
-        if (n <= light) {
-            gmap[s] = n == 0 ? -2 : -1;
-            continue;
-        }
-        const int k = (int)((n + chunk - 1) / chunk);
-        const int32_t seg_local = (int32_t)(seg_off[s] - seg_off[p0]);
-        int32_t split_local = -1;
-        if (k > 1) {
-            split_local = (int32_t)(split_off[s] - split_off[p0]);
-            split[split_off[s]] = make_int4(seg_local, k, (int32_t)(slot_off[s] - slot_off[p0]), 0);
-        }
-        gmap[s] = split_local;
-        for (int q = 0; q < k; ++q) {
-            const int32_t b = beg + (int32_t)(n * q / k);
-            const int32_t e = beg + (int32_t)(n * (q + 1) / k);
-            seg[seg_off[s] + q] = make_int4((int32_t)row, b, e, split_local);
-        }
-    }
-}
-
-// Non-empty light rows of every part, ordered by (part, entry count
-// descending, row):
-// key part*(light+1) + (light - n); heavy slots get the largest key.
-__global__ void light_keys(const int32_t *__restrict__ ptr, int64_t n_rows, int64_t nslots, int B,
-                           int light, uint64_t *__restrict__ key, uint32_t *__restrict__ val,
-                           uint32_t *__restrict__ flag)
-{
-    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < nslots;
-         s += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t n = ptr[s + 1] - ptr[s];
-        const int64_t part = s / n_rows;
-        const bool is_light = n >= 1 && n <= light;   // empty rows need no gradient
-        key[s] = is_light ? (uint64_t)(part * (light + 1) + (light - n)) : (uint64_t)B * (light + 1);
-        val[s] = (uint32_t)s;
-        flag[s] = is_light ? 1u : 0u;
-    }
-}
-
-__global__ void light_fill(const int32_t *__restrict__ ptr, int64_t n_rows, int64_t n_light,
-                           const uint32_t *__restrict__ slot, int4 *__restrict__ rec)
-{
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n_light;
-         k += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t s = slot[k];
-        const int64_t row = s % n_rows;
-        rec[k] = make_int4((int32_t)row, ptr[s], ptr[s + 1], 0);
-    }
-}
-
-__global__ void gather_offsets(const uint32_t *__restrict__ off, int64_t n_rows, int B,
-                               int64_t *__restrict__ out)
-{
-    const int s = threadIdx.x;
-    if (s <= B) out[s] = off[(int64_t)s * n_rows];
 }
 
 __global__ void gather_ptr(const int32_t *__restrict__ ptr, int64_t n_rows, int B,
@@ -407,9 +323,8 @@ psgld_status radix_sort(psgld_ctx *c, uint64_t *&k0, uint32_t *&v0, uint64_t *&k
 void free_layout(psgld_ctx *c)
 {
     for (auto &sd : c->side) {
-        cudaFree(sd.ptr); cudaFree(sd.idx); cudaFree(sd.val);
-        cudaFree(sd.seg); cudaFree(sd.split); cudaFree(sd.light);
-        cudaFree(sd.partial); cudaFree(sd.gmap);
+        cudaFree(sd.ptr); cudaFree(sd.idx); cudaFree(sd.val); cudaFree(sd.own);
+        cudaFree(sd.partial);
         sd = SideLayout{};
     }
     c->has_data = false;
@@ -449,20 +364,8 @@ psgld_status build_layout(psgld_ctx *c, int64_t nnz, const int32_t *i_dev, const
     PSGLD_ALLOC(kA, n); PSGLD_ALLOC(kB, n); PSGLD_ALLOC(kt, n);
     PSGLD_ALLOC(pA, n); PSGLD_ALLOC(pB, n); PSGLD_ALLOC(pt, n);
     PSGLD_ALLOC(hist, scan_n); PSGLD_ALLOC(hscan, scan_n + 1); PSGLD_ALLOC(tmp, tmp_n);
-    uint32_t *nseg = nullptr, *nsplit = nullptr, *nslot = nullptr;
-    uint32_t *oseg = nullptr, *osplit = nullptr, *oslot = nullptr;
     int64_t *offs_dev = nullptr;
-    PSGLD_ALLOC(nseg, nslots_max); PSGLD_ALLOC(nsplit, nslots_max); PSGLD_ALLOC(nslot, nslots_max);
-    PSGLD_ALLOC(oseg, nslots_max + 1); PSGLD_ALLOC(osplit, nslots_max + 1);
-    PSGLD_ALLOC(oslot, nslots_max + 1);
-    PSGLD_ALLOC(offs_dev, 4 * (B + 1));
-    uint64_t *lk0 = nullptr, *lk1 = nullptr;
-    uint32_t *lv0 = nullptr, *lv1 = nullptr, *hist_l = nullptr, *hscan_l = nullptr, *tmp_l = nullptr;
-    const int64_t ltiles = std::max<int64_t>(1, (nslots_max + kSortTile - 1) / kSortTile);
-    PSGLD_ALLOC(lk0, nslots_max); PSGLD_ALLOC(lk1, nslots_max);
-    PSGLD_ALLOC(lv0, nslots_max); PSGLD_ALLOC(lv1, nslots_max);
-    PSGLD_ALLOC(hist_l, 256 * ltiles + 1); PSGLD_ALLOC(hscan_l, 256 * ltiles + 2);
-    PSGLD_ALLOC(tmp_l, (256 * ltiles + 1 + kScanTile - 1) / kScanTile + 2);
+    PSGLD_ALLOC(offs_dev, B + 1);
 #undef PSGLD_ALLOC
 
     auto ck = [&](cudaError_t e, const char *what) -> psgld_status {
@@ -487,7 +390,7 @@ psgld_status build_layout(psgld_ctx *c, int64_t nnz, const int32_t *i_dev, const
         const int64_t nslots = (int64_t)B * n_rows;
         uint64_t *k0 = side == 0 ? kA : kB;
         uint32_t *v0 = side == 0 ? pA : pB;
-        uint64_t *k1 = kt;
+        uint64_t *k1 = kt;   // free again: the other side's finish_side ran first
         uint32_t *v1 = pt;
         if (n > 0) {
             s = radix_sort(c, k0, v0, k1, v1, n, side == 0 ? bitsA : bitsB, hist, hscan, tmp, st);
@@ -496,70 +399,27 @@ psgld_status build_layout(psgld_ctx *c, int64_t nnz, const int32_t *i_dev, const
         s = dmalloc(c, &sd.ptr, nslots + 1);
         if (s == PSGLD_OK) s = dmalloc(c, &sd.idx, n);
         if (s == PSGLD_OK) s = dmalloc(c, &sd.val, n);
+        if (s == PSGLD_OK) s = dmalloc(c, &sd.own, n);
         if (s != PSGLD_OK) { cleanup(); free_layout(c); return s; }
         finish_side<<<grid_for(n + 1, 256), 256, 0, st>>>(n, k0, v0, side == 0 ? j_dev : i_dev, v_dev,
-                                                          side == 0 ? bitsJ : bitsI, nslots, sd.idx,
-                                                          sd.val, sd.ptr, c->flag);
-        // (kt/pt are free again for the other side: finish_side is stream-
-        // ordered before the next sort starts)
+                                                          side == 0 ? bitsJ : bitsI, nslots, n_rows,
+                                                          sd.idx, sd.val, sd.own, sd.ptr, c->flag);
         if ((s = ck(cudaGetLastError(), "finish_side")) != PSGLD_OK) return s;
-
-        // work-list records
-        seg_counts<<<grid_for(nslots, 256), 256, 0, st>>>(sd.ptr, nslots, c->light_len, c->chunk_len,
-                                                          nseg, nsplit, nslot);
-        if ((s = exclusive_scan(c, nseg, oseg, nslots, tmp, st)) != PSGLD_OK) { cleanup(); free_layout(c); return s; }
-        if ((s = exclusive_scan(c, nsplit, osplit, nslots, tmp, st)) != PSGLD_OK) { cleanup(); free_layout(c); return s; }
-        if ((s = exclusive_scan(c, nslot, oslot, nslots, tmp, st)) != PSGLD_OK) { cleanup(); free_layout(c); return s; }
-        gather_offsets<<<1, 128, 0, st>>>(oseg, n_rows, B, offs_dev);
-        gather_offsets<<<1, 128, 0, st>>>(osplit, n_rows, B, offs_dev + (B + 1));
-        gather_offsets<<<1, 128, 0, st>>>(oslot, n_rows, B, offs_dev + 2 * (B + 1));
-        gather_ptr<<<1, 128, 0, st>>>(sd.ptr, n_rows, B, offs_dev + 3 * (B + 1));
-        std::vector<int64_t> h(4 * (B + 1));
+        gather_ptr<<<1, 128, 0, st>>>(sd.ptr, n_rows, B, offs_dev);
+        std::vector<int64_t> h(B + 1);
         if ((s = ck(cudaMemcpyAsync(h.data(), offs_dev, sizeof(int64_t) * h.size(), cudaMemcpyDeviceToHost, st), "offsets d2h")) != PSGLD_OK) return s;
         if ((s = ck(cudaStreamSynchronize(st), "sync")) != PSGLD_OK) return s;
-        sd.seg_off.assign(h.begin(), h.begin() + (B + 1));
-        sd.split_off.assign(h.begin() + (B + 1), h.begin() + 2 * (B + 1));
-        sd.slot_off.assign(h.begin() + 2 * (B + 1), h.begin() + 3 * (B + 1));
-        sd.part_first.assign(h.begin() + 3 * (B + 1), h.begin() + 4 * (B + 1));
+        sd.part_first = h;
         if (side == 0) {
             c->part_n.resize(B);
-            for (int p = 0; p < B; ++p) c->part_n[p] = h[3 * (B + 1) + p + 1] - h[3 * (B + 1) + p];
+            for (int p = 0; p < B; ++p) c->part_n[p] = h[p + 1] - h[p];
         }
-        sd.max_splits = sd.max_slots = 0;
-        for (int p = 0; p < B; ++p) {
-            sd.max_splits = std::max(sd.max_splits, sd.split_off[p + 1] - sd.split_off[p]);
-            sd.max_slots = std::max(sd.max_slots, sd.slot_off[p + 1] - sd.slot_off[p]);
-        }
-        s = dmalloc(c, &sd.seg, sd.seg_off[B]);
-        if (s == PSGLD_OK) s = dmalloc(c, &sd.split, sd.split_off[B]);
-        if (s == PSGLD_OK) s = dmalloc(c, &sd.partial, sd.max_slots * c->ldk);
-        if (s == PSGLD_OK) s = dmalloc(c, &sd.gmap, nslots);
+        const int unit = unit_entries(c->ngroups);
+        sd.max_units = 0;
+        for (int p = 0; p < B; ++p)
+            sd.max_units = std::max<int64_t>(sd.max_units, (h[p + 1] - h[p] + unit - 1) / unit);
+        s = dmalloc(c, &sd.partial, 2 * std::max<int64_t>(1, sd.max_units) * c->ldk);
         if (s != PSGLD_OK) { cleanup(); free_layout(c); return s; }
-        seg_fill<<<grid_for(nslots, 256), 256, 0, st>>>(sd.ptr, n_rows, nslots, c->light_len,
-                                                        c->chunk_len, oseg,
-                                                        osplit, oslot, sd.seg, sd.split, sd.gmap);
-        if ((s = ck(cudaGetLastError(), "seg_fill")) != PSGLD_OK) return s;
-
-        // light-row lists: sort the (part, row) slots by (part, count desc)
-        light_keys<<<grid_for(nslots, 256), 256, 0, st>>>(sd.ptr, n_rows, nslots, B, c->light_len,
-                                                          lk0, lv0, nseg);
-        if ((s = exclusive_scan(c, nseg, oseg, nslots, tmp, st)) != PSGLD_OK) { cleanup(); free_layout(c); return s; }
-        gather_offsets<<<1, 128, 0, st>>>(oseg, n_rows, B, offs_dev);
-        {
-            uint64_t *a0 = lk0, *a1 = lk1;
-            uint32_t *b0 = lv0, *b1 = lv1;
-            s = radix_sort(c, a0, b0, a1, b1, nslots, bits_for((uint64_t)B * (c->light_len + 1) + 1),
-                           hist_l, hscan_l, tmp_l, st);
-            if (s != PSGLD_OK) { cleanup(); free_layout(c); return s; }
-            std::vector<int64_t> lo(B + 1);
-            if ((s = ck(cudaMemcpyAsync(lo.data(), offs_dev, sizeof(int64_t) * (B + 1), cudaMemcpyDeviceToHost, st), "light offsets")) != PSGLD_OK) return s;
-            if ((s = ck(cudaStreamSynchronize(st), "sync")) != PSGLD_OK) return s;
-            sd.light_off = lo;
-            s = dmalloc(c, &sd.light, lo[B]);
-            if (s != PSGLD_OK) { cleanup(); free_layout(c); return s; }
-            light_fill<<<grid_for(lo[B], 256), 256, 0, st>>>(sd.ptr, n_rows, lo[B], b0, sd.light);
-            if ((s = ck(cudaGetLastError(), "light_fill")) != PSGLD_OK) return s;
-        }
     }
     if ((s = ck(cudaMemcpyAsync(&hflag, c->flag, sizeof(int), cudaMemcpyDeviceToHost, st), "flag d2h")) != PSGLD_OK) return s;
     if ((s = ck(cudaStreamSynchronize(st), "sync")) != PSGLD_OK) return s;

@@ -46,28 +46,25 @@
 namespace psgld {
 namespace {
 
-constexpr int kThreads = 256;
-constexpr int kWarps = kThreads / 32;
+constexpr int kThreads = 256;        // update kernel
+constexpr int kGradThreads = 128;    // gradient kernel: four warps, one unit each
 
 struct GradSide {
     const float *X_cur;    // own rows (n_rows x ldk)
     const float *Y_cur;    // gathered rows of the other factor
     float *Gout;           // this side's rows of G
-    const int32_t *ptr;    // this part's row offsets (n_rows + 1)
+    const int32_t *own;    // own row of each entry
     const int32_t *idx;    // other index of each entry
     const float *val;
-    const int4 *chunk;     // this part's chunk records
-    const int4 *split;     // this part's split table
-    const int4 *light;     // this part's light rows {row, beg, end, 0}
-    float *partial;
-    int64_t nlight;
-    int64_t nchunks;
+    float *partial;        // 2 x units x ldk: head / tail partial sums
+    int64_t base;          // first entry of the part
+    int64_t n;             // entries of the part
+    int64_t units;         // ceil(n / E)
 };
 
 struct GradParams {
     GradSide side[2];
     int ldk, lds, ngroups;    // row length, shared-memory row stride (floats), float4 groups
-    int E;                    // entry slots per unit
     float phi_inv, p, mu_min;
     int p_mode;               // 0: p = 0, 1: p = 1, 2: p = 2, 3: other
     int *err;                 // set to 16 when a bulk copy wait runs out
@@ -77,9 +74,9 @@ struct UpdSide {
     const float *X_cur;
     float *X_next;
     const float *Gin;
-    const int32_t *gmap;      // this part's gradient source of every row
-    const int4 *split;        // this part's split table
-    const float *partial;     // partial sums of split rows
+    const int32_t *ptr;       // this part's row offsets (absolute entry indices)
+    const float *partial;     // head / tail partial sums of the gradient kernel
+    int64_t base;             // first entry of the part
     int64_t items;            // n_rows * ngroups (0 when the factor is frozen)
     float prior_a, prior_b;   // d log p(x)/dx = prior_a + prior_b * x
     uint32_t mat;             // 0 = W, 1 = H (noise stream)
@@ -89,7 +86,7 @@ struct UpdParams {
     UpdSide side[2];
     const int64_t *t_dev;     // if non-null, t = *t_dev + t_add
     int64_t t_add;
-    int K, ldk, ngroups;
+    int K, ldk, ngroups, unit_shift;
     uint32_t div_magic;       // ceil(2^32 / ngroups) when item * ngroups < 2^32, else 0
     float eps, sd, S;
     int eps_poly;             // 1: eps_t = (a/t)^b computed on the device
@@ -158,21 +155,22 @@ __device__ __forceinline__ float tweedie_e(const GradParams &P, float v, float m
 
 // ---- kernel 1: the likelihood gradient ------------------------------------
 //
-// Work units, one per warp.  A chunk unit is up to E entries of one heavy
-// row; a light unit is R = 32/S light rows of up to L = E/R entries each.
-// Either way the unit has E entry slots, and slot l of a light unit belongs
-// to row l / L.  Steps:
-//   1. each slot lane loads its entry (other index j, value v);
+// A unit is E consecutive entries of the part in this side's order (rows in
+// order, the other index ascending), one unit per warp.  Steps:
+//   1. lane l loads entry l of the unit: own row, other index j, value v;
 //   2. TMA bulk copies (cp.async.bulk, one instruction per factor row) bring
-//      the unit's own rows and the E gathered rows into this warp's shared
-//      memory, completing on the warp's mbarrier -- every gather of the unit
-//      is in flight at once;
-//   3. SDDMM + epilogue, one lane per slot: mu = x . y from shared memory,
-//      e = Tweedie factor;
-//   4. SpMM, sub-teams of S lanes over the K columns: sub-team s adds
-//      e_l * y_l over its slots l = s*L .. s*L+L-1 (its row in a light unit;
-//      one slice of the chunk, then summed across sub-teams in a chunk unit);
-//   5. store the row's gradient (G, or a partial-sum slot of a split row).
+//      the E gathered rows Y[j] into the warp's shared memory, completing on
+//      the warp's mbarrier, so every gather of the unit is in flight at once;
+//   3. SDDMM + epilogue, one lane per entry: mu = X[own] . Y[j], e = Tweedie
+//      factor (X rows read through L1; lanes of one row share the lines);
+//   4. SpMM by row segments of the unit, sub-teams of S lanes over the K
+//      columns: G[row] = sum_l e_l Y[j_l] over the segment.  A unit holding
+//      one row splits its entries over the sub-teams and adds their sums; a
+//      unit holding several rows gives each sub-team whole segments;
+//   5. a segment whose row also has entries before the unit goes to the
+//      unit's head slot, one whose row continues after it to the tail slot,
+//      any other straight to G.  The update kernel adds a row's tail and head
+//      slots in unit order, so the result does not depend on scheduling.
 
 constexpr uint32_t kWaitLimit = 1u << 24;          // mbarrier polls before giving up
 constexpr long long kWaitCycles = 1ll << 31;         // ... or about one second of SM clock
@@ -216,72 +214,55 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
                  :: "r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar)) : "memory");
 }
 
-template <int S, int NG>
-__global__ void __launch_bounds__(kThreads) grad_kernel(const __grid_constant__ GradParams P)
+template <int S, int NG, int E>
+__global__ void __launch_bounds__(kGradThreads) grad_kernel(const __grid_constant__ GradParams P)
 {
-    constexpr int R = 32 / S;   // rows of a light unit = sub-teams of a warp
-    const int E = P.E;          // entry slots of a unit
-    const int L = E / R;        // entry slots per row of a light unit
+    constexpr int R = 32 / S;      // sub-teams per warp
+    constexpr int NGP = S * NG;    // float4 groups a sub-team covers (>= ngroups)
     extern __shared__ float4 smem4[];
     const int warp = threadIdx.x >> 5, lane32 = threadIdx.x & 31;
     const int ng = P.ngroups, ldk = P.ldk, lds = P.lds;
+    constexpr int kWarpsPerCta = kGradThreads / 32;
     float *base = reinterpret_cast<float *>(smem4);
-    float *ys = base + (size_t)warp * (E + R) * lds;   // E gathered rows
-    float *xs = ys + (size_t)E * lds;                  // R own rows
-    uint64_t *bar = reinterpret_cast<uint64_t *>(base + (size_t)kWarps * (E + R) * lds) + warp;
+    float *ys = base + (size_t)warp * E * lds;                      // E gathered rows
+    float *es = base + (size_t)kWarpsPerCta * E * lds + warp * E;   // e of each entry
+    int *ow = reinterpret_cast<int *>(base + (size_t)kWarpsPerCta * E * lds + kWarpsPerCta * E) + warp * E;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(base + (size_t)kWarpsPerCta * (E * lds + 2 * E)) + warp;
 
-    // ---- which unit: chunk units of both sides first, then light units
-    const int64_t unit = (int64_t)blockIdx.x * kWarps + warp;
-    const int64_t c0 = P.side[0].nchunks, c1 = P.side[1].nchunks;
-    const int64_t u0 = (P.side[0].nlight + R - 1) / R, u1 = (P.side[1].nlight + R - 1) / R;
-    int sid;
-    bool chunk;
-    int64_t k;
-    if (unit < c0) { sid = 0; chunk = true; k = unit; }
-    else if (unit < c0 + c1) { sid = 1; chunk = true; k = unit - c0; }
-    else if (unit < c0 + c1 + u0) { sid = 0; chunk = false; k = unit - c0 - c1; }
-    else if (unit < c0 + c1 + u0 + u1) { sid = 1; chunk = false; k = unit - c0 - c1 - u0; }
-    else return;   // warp-uniform
-    const GradSide &Sd = P.side[sid];
-
-    // ---- 1. slot -> (row of the unit, entry)
-    int4 rec;                      // this slot's row record: row, beg, end, split
-    const int myrow = chunk ? 0 : lane32 / L;   // row of the unit this slot belongs to
-    if (chunk) {
-        rec = __ldg(Sd.chunk + k);
-    } else {
-        const int64_t kk = k * R + (lane32 < E ? myrow : 0);
-        rec = kk < Sd.nlight ? __ldg(Sd.light + kk) : make_int4(0, 0, 0, -1);
-        rec.w = kk < Sd.nlight ? -1 : -2;   // -2: no row
+    int64_t u = (int64_t)blockIdx.x * kWarpsPerCta + warp;
+    int sid = 0;
+    if (u >= P.side[0].units) {
+        u -= P.side[0].units;
+        sid = 1;
+        if (u >= P.side[1].units) return;   // warp-uniform
     }
-    const int slot_in_row = chunk ? lane32 : lane32 % L;
-    const bool valid = lane32 < E && rec.w != -2 && slot_in_row < rec.z - rec.y;
-    int jj = 0;
+    const GradSide &Sd = P.side[sid];
+    const int64_t e0 = Sd.base + u * E;
+    const int n = (int)(Sd.n - u * E < E ? Sd.n - u * E : E);
+
+    // ---- 1. this lane's entry
+    const bool valid = lane32 < n;
+    int own = -1, jj = 0;
     float vv = 0.f;
     if (valid) {
-        jj = __ldg(Sd.idx + rec.y + slot_in_row);
-        vv = __ldg(Sd.val + rec.y + slot_in_row);
+        own = __ldg(Sd.own + e0 + lane32);
+        jj = __ldg(Sd.idx + e0 + lane32);
+        vv = __ldg(Sd.val + e0 + lane32);
     }
-    // own rows: row r of a light unit is the row of slot r*L
-    int own_row = -1;
-    if (chunk) {
-        if (lane32 == 0) own_row = rec.x;
-    } else if (lane32 < R) {
-        const int64_t kk = k * R + lane32;
-        if (kk < Sd.nlight) own_row = __ldg(Sd.light + kk).x;
-    }
-    const unsigned vmask = __ballot_sync(0xffffffffu, valid);
-    const unsigned rmask = __ballot_sync(0xffffffffu, own_row >= 0);
+    int prev_own = -1, next_own = -1;   // rows of the entries just outside the unit
+    if (lane32 == 0 && u > 0) prev_own = __ldg(Sd.own + e0 - 1);
+    if (lane32 == 1 && u * E + E < Sd.n) next_own = __ldg(Sd.own + e0 + E);
+    prev_own = __shfl_sync(0xffffffffu, prev_own, 0);
+    next_own = __shfl_sync(0xffffffffu, next_own, 1);
     const uint32_t row_bytes = (uint32_t)ldk * 4u;
 
     // ---- 2. bulk gathers into shared memory
     if (lane32 == 0) {
         mbar_init(bar);
-        mbar_expect_tx(bar, (uint32_t)(__popc(vmask) + __popc(rmask)) * row_bytes);
+        mbar_expect_tx(bar, (uint32_t)n * row_bytes);
     }
     __syncwarp();
     if (valid) bulk_g2s(ys + (size_t)lane32 * lds, Sd.Y_cur + (int64_t)jj * ldk, row_bytes, bar);
-    if (own_row >= 0) bulk_g2s(xs + (size_t)lane32 * lds, Sd.X_cur + (int64_t)own_row * ldk, row_bytes, bar);
     bool done = false;
     const long long t_start = clock64();
     for (uint32_t it = 0; it < kWaitLimit && !done && clock64() - t_start < kWaitCycles; ++it)
@@ -296,48 +277,41 @@ __global__ void __launch_bounds__(kThreads) grad_kernel(const __grid_constant__ 
         return;
     }
 
-    // ---- 3. mu and the Tweedie factor, one lane per slot
+    // ---- 3. mu and the Tweedie factor, one lane per entry
     float e = 0.f;
     if (valid) {
-        const float *x = xs + (size_t)myrow * lds;
+        const float *x = Sd.X_cur + (int64_t)own * ldk;
         const float *y = ys + (size_t)lane32 * lds;
         float d = 0.f;
-        for (int q = 0; q < ng; ++q) {
-            const float4 a = *reinterpret_cast<const float4 *>(x + 4 * q);
-            const float4 b = *reinterpret_cast<const float4 *>(y + 4 * q);
-            d = dot4(a, b, d);
-        }
+#pragma unroll
+        for (int q = 0; q < NGP; ++q)
+            if (q < ng) d = dot4(ldg4(x + 4 * q), *reinterpret_cast<const float4 *>(y + 4 * q), d);
         e = tweedie_e(P, vv, d);
     }
-
-    // ---- 4. gradient sums, sub-teams of S lanes over the columns
-    const int sub = lane32 / S, lane = lane32 & (S - 1);
-    float4 acc[NG];
-#pragma unroll
-    for (int g = 0; g < NG; ++g) acc[g] = zero4();
-    // slots beyond the unit's longest row hold nothing: stop there
-    int nslots_used = 32 - __clz(vmask);                    // highest valid slot + 1
-    int umax = chunk ? (nslots_used + R - 1) / R : 0;
-    if (!chunk) {
-        const int nrow = rec.w == -2 ? 0 : rec.z - rec.y;   // this lane's row length
-        umax = min(L, __reduce_max_sync(0xffffffffu, lane32 < E ? nrow : 0));
+    const int own_prev_lane = __shfl_up_sync(0xffffffffu, own, 1);
+    const unsigned smask = __ballot_sync(0xffffffffu, valid && (lane32 == 0 || own != own_prev_lane));
+    if (lane32 < E) {
+        es[lane32] = e;
+        ow[lane32] = own;
     }
-    if (chunk) umax = L;
-#pragma unroll 4
-    for (int u = 0; u < umax; ++u) {
-        const int sl = sub * L + u;
-        const float es = __shfl_sync(0xffffffffu, e, sl);
-        if ((vmask >> sl) & 1u) {
+    __syncwarp();
+
+    // ---- 4./5. gradient sums per row segment
+    const int sub = lane32 / S, lane = lane32 & (S - 1);
+    const int nseg = __popc(smask);
+    float4 acc[NG];
+    if (nseg == 1) {
+        // one row: sub-team s takes entries s, s+R, ...; then add the sub-teams
+#pragma unroll
+        for (int g = 0; g < NG; ++g) acc[g] = zero4();
+        for (int sl = sub; sl < n; sl += R) {
+            const float es_ = es[sl];
 #pragma unroll
             for (int g = 0; g < NG; ++g) {
                 const int q = lane + g * S;
-                if (q < ng) axpy4(acc[g], es, *reinterpret_cast<const float4 *>(ys + (size_t)sl * lds + 4 * q));
+                if (q < ng) axpy4(acc[g], es_, *reinterpret_cast<const float4 *>(ys + (size_t)sl * lds + 4 * q));
             }
         }
-    }
-
-    // ---- 5. store
-    if (chunk) {
 #pragma unroll
         for (int o = S; o < 32; o <<= 1)
 #pragma unroll
@@ -347,12 +321,10 @@ __global__ void __launch_bounds__(kThreads) grad_kernel(const __grid_constant__ 
                 acc[g].z += __shfl_xor_sync(0xffffffffu, acc[g].z, o);
                 acc[g].w += __shfl_xor_sync(0xffffffffu, acc[g].w, o);
             }
-        const int4 ck = rec;   // every lane holds the chunk's record
-        float *dst = Sd.Gout + (int64_t)ck.x * ldk;
-        if (ck.w >= 0) {   // split row: this chunk's partial-sum slot
-            const int4 sp = __ldg(Sd.split + ck.w);
-            dst = Sd.partial + (sp.z + (k - sp.x)) * (int64_t)ldk;
-        }
+        const int row = ow[0];
+        float *dst = prev_own == row ? Sd.partial + (2 * u) * (int64_t)ldk
+                   : next_own == row ? Sd.partial + (2 * u + 1) * (int64_t)ldk
+                                     : Sd.Gout + (int64_t)row * ldk;
         if (sub == 0) {
 #pragma unroll
             for (int g = 0; g < NG; ++g) {
@@ -361,12 +333,28 @@ __global__ void __launch_bounds__(kThreads) grad_kernel(const __grid_constant__ 
             }
         }
     } else {
-        const int r = __shfl_sync(0xffffffffu, own_row, sub);   // this sub-team's row
-        if (r >= 0) {
+        // several rows: sub-team s takes segments s, s+R, ...
+        for (int k = sub; k < nseg; k += R) {
+            const int st = (int)__fns(smask, 0, k + 1);
+            const int en = k + 1 < nseg ? (int)__fns(smask, 0, k + 2) : n;
+            const int row = ow[st];
+#pragma unroll
+            for (int g = 0; g < NG; ++g) acc[g] = zero4();
+            for (int sl = st; sl < en; ++sl) {
+                const float es_ = es[sl];
+#pragma unroll
+                for (int g = 0; g < NG; ++g) {
+                    const int q = lane + g * S;
+                    if (q < ng) axpy4(acc[g], es_, *reinterpret_cast<const float4 *>(ys + (size_t)sl * lds + 4 * q));
+                }
+            }
+            float *dst = (k == 0 && prev_own == row) ? Sd.partial + (2 * u) * (int64_t)ldk
+                       : (k == nseg - 1 && next_own == row) ? Sd.partial + (2 * u + 1) * (int64_t)ldk
+                                                             : Sd.Gout + (int64_t)row * ldk;
 #pragma unroll
             for (int g = 0; g < NG; ++g) {
                 const int q = lane + g * S;
-                if (q < ng) *reinterpret_cast<float4 *>(Sd.Gout + (int64_t)r * ldk + 4 * q) = acc[g];
+                if (q < ng) *reinterpret_cast<float4 *>(dst + 4 * q) = acc[g];
             }
         }
     }
@@ -418,24 +406,28 @@ __global__ void __launch_bounds__(kThreads) update_kernel(const __grid_constant_
         const int q = (int)(item - row * ng);
         const int64_t off = row * ldk + 4 * q;
         const float4 x = ldg4(Sd.X_cur + off);
-        const int32_t src = __ldg(Sd.gmap + row);
+        // this row's gradient: nothing (no entries), G (entries within one
+        // unit), or its first unit's tail slot plus the later units' head slots
+        const int64_t p0 = __ldg(Sd.ptr + row) - Sd.base, p1 = __ldg(Sd.ptr + row + 1) - Sd.base;
         float4 g = zero4();
-        if (src == -1) {
-            g = ldg4(Sd.Gin + off);
-        } else if (src >= 0) {   // split row: add its chunks' partial sums in order
-            const int4 sp = __ldg(Sd.split + src);
-            const float *pp = Sd.partial + (int64_t)sp.z * ldk + 4 * q;
-            int o = 0;
-            for (; o + 8 <= sp.y; o += 8) {   // eight independent loads in flight
-                float4 v[8];
+        if (p1 > p0) {
+            const int64_t u0 = p0 >> P.unit_shift, u1 = (p1 - 1) >> P.unit_shift;
+            if (u0 == u1) {
+                g = ldg4(Sd.Gin + off);
+            } else {
+                g = __ldcg(reinterpret_cast<const float4 *>(Sd.partial + (2 * u0 + 1) * ldk + 4 * q));
+                const float *hp = Sd.partial + 4 * q;
+                int64_t uu = u0 + 1;
+                for (; uu + 8 <= u1 + 1; uu += 8) {   // eight independent loads in flight
+                    float4 v[8];
 #pragma unroll
-                for (int w = 0; w < 8; ++w)
-                    v[w] = __ldcg(reinterpret_cast<const float4 *>(pp + (int64_t)(o + w) * ldk));
+                    for (int w = 0; w < 8; ++w)
+                        v[w] = __ldcg(reinterpret_cast<const float4 *>(hp + 2 * (uu + w) * ldk));
 #pragma unroll
-                for (int w = 0; w < 8; ++w) add4(g, v[w]);
+                    for (int w = 0; w < 8; ++w) add4(g, v[w]);
+                }
+                for (; uu <= u1; ++uu) add4(g, __ldcg(reinterpret_cast<const float4 *>(hp + 2 * uu * ldk)));
             }
-            for (; o < sp.y; ++o)
-                add4(g, __ldcg(reinterpret_cast<const float4 *>(pp + (int64_t)o * ldk)));
         }
         const uint4 r = philox(make_uint4((uint32_t)q, (uint32_t)row, t_lo, (t_hi << 1) | Sd.mat), P);
         const float4 z = dev::box_muller4(r);
@@ -451,40 +443,14 @@ __global__ void __launch_bounds__(kThreads) update_kernel(const __grid_constant_
 
 using GradFn = void (*)(GradParams);
 
-GradFn pick_grad(int S, int NG)
-{
-    if (NG == 1) {
-        switch (S) {
-        case 1: return grad_kernel<1, 1>;
-        case 2: return grad_kernel<2, 1>;
-        case 4: return grad_kernel<4, 1>;
-        }
-    }
-    if (NG == 2) {
-        switch (S) {
-        case 4: return grad_kernel<4, 2>;
-        case 8: return grad_kernel<8, 2>;
-        case 16: return grad_kernel<16, 2>;
-        case 32: return grad_kernel<32, 2>;
-        }
-    }
-    if (S == 32) {
-        switch (NG) {
-        case 3: return grad_kernel<32, 3>;
-        case 4: return grad_kernel<32, 4>;
-        }
-    }
-    return nullptr;
-}
-
 struct Shape {
-    int S, NG, R, E, lds;
+    int S, NG, E, lds;
 };
 
-// Sub-team lanes S and float4 groups per lane NG cover K; E entry slots per
-// unit keep one warp's shared memory ((E + R) rows) near 10 KB; the row
-// stride is padded so that its float4 count is odd (conflict-free float4
-// reads of one row per lane).
+// Sub-team lanes S and float4 groups per lane NG cover K; E entries per unit
+// keep a warp's shared memory (E gathered rows) near 17 KB at most; the row
+// stride is padded so that its float4 count is odd (each lane reading its own
+// row hits distinct banks).
 Shape shape_for(int ngroups)
 {
     Shape sh;
@@ -497,34 +463,52 @@ Shape shape_for(int ngroups)
         while (sh.S * 2 < ngroups && sh.S < 32) sh.S <<= 1;
         sh.NG = (ngroups + sh.S - 1) / sh.S;
     }
-    sh.R = 32 / sh.S;
-    const int ldk = 4 * ngroups;
-    sh.lds = (ngroups & 1) ? ldk : ldk + 4;
-    sh.E = 32;
-    while (sh.E > sh.R && (sh.E + sh.R) * sh.lds * 4 > 10240) sh.E >>= 1;
+    sh.E = ngroups <= 32 ? 32 : ngroups <= 64 ? 16 : 8;
+    sh.lds = (ngroups & 1) ? 4 * ngroups : 4 * ngroups + 4;
     return sh;
+}
+
+GradFn pick_grad(const Shape &sh)
+{
+    if (sh.NG == 1) {
+        switch (sh.S) {
+        case 1: return grad_kernel<1, 1, 32>;
+        case 2: return grad_kernel<2, 1, 32>;
+        case 4: return grad_kernel<4, 1, 32>;
+        }
+    }
+    if (sh.NG == 2) {
+        switch (sh.S) {
+        case 4: return grad_kernel<4, 2, 32>;
+        case 8: return grad_kernel<8, 2, 32>;
+        case 16: return grad_kernel<16, 2, 32>;
+        case 32: return grad_kernel<32, 2, 16>;
+        }
+    }
+    if (sh.S == 32) {
+        switch (sh.NG) {
+        case 3: return grad_kernel<32, 3, 8>;
+        case 4: return grad_kernel<32, 4, 8>;
+        }
+    }
+    return nullptr;
 }
 
 size_t grad_smem(const Shape &sh)
 {
-    return sizeof(float) * (size_t)kWarps * (sh.E + sh.R) * sh.lds + sizeof(uint64_t) * kWarps;
+    const int warps = kGradThreads / 32;
+    return sizeof(float) * (size_t)warps * ((size_t)sh.E * sh.lds + 2 * sh.E) +
+           sizeof(uint64_t) * warps;
 }
 
 }  // namespace
 
-void work_shape(int ngroups, int *lanes, int *groups, int *light_len, int *chunk_len)
-{
-    const Shape sh = shape_for(ngroups);
-    *lanes = sh.S;
-    *groups = sh.NG;
-    *light_len = sh.E / sh.R;
-    *chunk_len = sh.E;
-}
+int unit_entries(int ngroups) { return shape_for(ngroups).E; }
 
 psgld_status prepare_kernels(psgld_ctx *c)
 {
     const Shape sh = shape_for(c->ngroups);
-    GradFn gfn = pick_grad(sh.S, sh.NG);
+    GradFn gfn = pick_grad(sh);
     if (!gfn) return fail(c, PSGLD_ERR_ARG, "unsupported K");
     PSGLD_CK(c, cudaFuncSetAttribute(gfn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)grad_smem(sh)));
@@ -537,7 +521,7 @@ psgld_status launch_part_step(psgld_ctx *c, int64_t t, const int64_t *t_dev, int
     const int B = c->B;
     const int part = (int)((t - 1) % B);
     const Shape sh = shape_for(c->ngroups);
-    GradFn gfn = pick_grad(sh.S, sh.NG);
+    GradFn gfn = pick_grad(sh);
     if (!gfn) return fail(c, PSGLD_ERR_ARG, "unsupported K");
 
     const bool upd[2] = {!c->opt.freeze_W, !c->opt.freeze_H};
@@ -551,25 +535,24 @@ psgld_status launch_part_step(psgld_ctx *c, int64_t t, const int64_t *t_dev, int
         float *X_cur = s == 0 ? c->W[c->wcur] : c->Ht[c->hcur];
         float *X_next = s == 0 ? c->W[c->wcur ^ 1] : c->Ht[c->hcur ^ 1];
         float *G_rows = c->G + (s == 0 ? 0 : c->I * c->ldk);
+        const int64_t base = L.part_first[part], n = L.part_first[part + 1] - base;
         Gs.X_cur = X_cur;
         Gs.Y_cur = s == 0 ? c->Ht[c->hcur] : c->W[c->wcur];
         Gs.Gout = G_rows;
-        Gs.ptr = L.ptr + (int64_t)part * n_rows;
+        Gs.own = L.own;
         Gs.idx = L.idx;
         Gs.val = L.val;
-        Gs.chunk = L.seg + L.seg_off[part];
-        Gs.split = L.split + L.split_off[part];
-        Gs.light = L.light + L.light_off[part];
         Gs.partial = L.partial;
-        Gs.nlight = upd[s] ? L.light_off[part + 1] - L.light_off[part] : 0;
-        Gs.nchunks = upd[s] ? L.seg_off[part + 1] - L.seg_off[part] : 0;
+        Gs.base = base;
+        Gs.n = n;
+        Gs.units = upd[s] ? (n + sh.E - 1) / sh.E : 0;
 
         Us.X_cur = X_cur;
         Us.X_next = X_next;
         Us.Gin = G_rows;
-        Us.gmap = L.gmap + (int64_t)part * n_rows;
-        Us.split = L.split + L.split_off[part];
+        Us.ptr = L.ptr + (int64_t)part * n_rows;
         Us.partial = L.partial;
+        Us.base = base;
         Us.items = upd[s] ? n_rows * c->ngroups : 0;
         if (c->prior.kind == PSGLD_PRIOR_EXPONENTIAL) {
             Us.prior_a = (float)-(s == 0 ? c->prior.lambda_w : c->prior.lambda_h);
@@ -584,18 +567,18 @@ psgld_status launch_part_step(psgld_ctx *c, int64_t t, const int64_t *t_dev, int
     GP.ldk = c->ldk;
     GP.lds = sh.lds;
     GP.ngroups = c->ngroups;
-    GP.E = sh.E;
-    GP.err = c->kflag;
     GP.phi_inv = (float)(1.0 / c->phi);
     GP.p = (float)c->p;
     GP.mu_min = (float)c->opt.mu_min;
     GP.p_mode = c->p == 0.0 ? 0 : c->p == 1.0 ? 1 : c->p == 2.0 ? 2 : 3;
+    GP.err = c->kflag;
 
     UP.t_dev = t_dev;
     UP.t_add = t_dev ? t_add : t;
     UP.K = c->K;
     UP.ldk = c->ldk;
     UP.ngroups = c->ngroups;
+    UP.unit_shift = sh.E == 32 ? 5 : sh.E == 16 ? 4 : 3;
     const int64_t max_items = std::max(UP.side[0].items, UP.side[1].items);
     UP.div_magic = (max_items * c->ngroups < (1ll << 32))
                        ? (uint32_t)(((1ull << 32) + c->ngroups - 1) / c->ngroups)
@@ -618,9 +601,8 @@ psgld_status launch_part_step(psgld_ctx *c, int64_t t, const int64_t *t_dev, int
         k1 += 0xBB67AE85u;
     }
 
-    const int64_t units = GP.side[0].nchunks + GP.side[1].nchunks +
-                          (GP.side[0].nlight + sh.R - 1) / sh.R + (GP.side[1].nlight + sh.R - 1) / sh.R;
-    const int ggrid = (int)((units + kWarps - 1) / kWarps);
+    const int64_t units = GP.side[0].units + GP.side[1].units;
+    const int ggrid = (int)((units + kGradThreads / 32 - 1) / (kGradThreads / 32));
     const int64_t items = UP.side[0].items + UP.side[1].items;
     const int ugrid = (int)std::min<int64_t>((items + kThreads - 1) / kThreads, 152 * 16);
     // Inside a stream capture the records must be external, so that they
@@ -634,7 +616,7 @@ psgld_status launch_part_step(psgld_ctx *c, int64_t t, const int64_t *t_dev, int
         if (cap == cudaStreamCaptureStatusActive) rec_flags = cudaEventRecordExternal;
         PSGLD_CK(c, cudaEventRecordWithFlags(c->ev_start[part], st, rec_flags));
     }
-    if (ggrid > 0) gfn<<<ggrid, kThreads, grad_smem(sh), st>>>(GP);
+    if (ggrid > 0) gfn<<<ggrid, kGradThreads, grad_smem(sh), st>>>(GP);
     PSGLD_CK(c, cudaGetLastError());
     if (items > 0) update_kernel<<<ugrid, kThreads, 0, st>>>(UP);
     PSGLD_CK(c, cudaGetLastError());

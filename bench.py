@@ -263,7 +263,7 @@ def oracle_rate(m, wl, t0: int, n_steps: int):
 def cpu_baseline(wl, i, j, v, W0, H0, seed, budget_s: float):
     m = oracle_setup(wl, i, j, v, W0, H0, seed)
     _, _, dt1 = oracle_rate(m, wl, 1, 1)          # calibration (untimed)
-    n = max(1, min(wl["B"] * 3, int(budget_s / max(dt1, 1e-6))))
+    n = max(1, min(wl["B"] * 200, int(budget_s / max(dt1, 1e-6))))
     rate, ent, dt = oracle_rate(m, wl, 2, n)
     return {"value": rate, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
             "sample": f"{n} part-steps ({ent} observed entries, {dt:.1f} s) of the same "
@@ -359,7 +359,8 @@ def run_ours(args, wl_name, wl):
                      "kernel": "part_step_kernel", "kernel_ms": kern_ms,
                      "algorithmic_bytes_per_launch": bytes_launch,
                      "peak_source": f"{peak_src} HBM copy bandwidth"},
-        "gpu_launches": args.steps * (wl["B"] + 4),
+        # per sweep: B x (gradient + update) + 2 accumulate + advance t + set t
+        "gpu_launches": args.steps * (2 * wl["B"] + 4),
         "clocks": clocks,
         "rmse_after": rmse,
     }

@@ -90,10 +90,17 @@ typedef struct {
     int64_t burn_in_sweeps;   /* sweeps discarded before posterior sums start */
     int32_t use_graphs;       /* 1: each sweep replays one captured CUDA graph */
     int32_t profile;          /* 1: time every part-step launch with CUDA events */
+    int32_t dense_path;       /* 1: psgld_set_data_dense keeps V as a dense FP32 array
+                               * and every part-step runs the tensor-core block chain
+                               * (BF16 operands, FP32 accumulation; K <= 128);
+                               * 0: dense V becomes the sparse layout of all I*J
+                               * entries and runs the FP32 gather path.  Read when
+                               * data is set. */
 } psgld_options;
 
 /* Defaults: seed 0, fixed eps 1e-4, a = 0.01, b = 0.51, scale N/|Pi_t|,
- * mu_min 1e-10, nothing frozen, no burn-in, graphs on, profiling off. */
+ * mu_min 1e-10, nothing frozen, no burn-in, graphs on, profiling off,
+ * dense_path off. */
 PSGLD_API void psgld_default_options(psgld_options *opt_host);
 
 /* Create a context on the current CUDA device.
@@ -116,8 +123,18 @@ PSGLD_API psgld_status psgld_set_options(psgld_ctx *ctx, const psgld_options *op
 PSGLD_API psgld_status psgld_set_data_coo(psgld_ctx *ctx, int64_t nnz, const int32_t *i,
                                 const int32_t *j, const float *v, void *stream);
 
-/* Dense V (every entry observed), row-major with leading dimension ld >= J.
- * Same effect as psgld_set_data_coo over all I*J entries. */
+/* Dense V (every entry observed), row-major with leading dimension ld >= J;
+ * non-negative models require V >= 0, and every entry must be finite.
+ * With dense_path = 0: the same effect as psgld_set_data_coo over all I*J
+ * entries.  With dense_path = 1: the library keeps its own FP32 copy of V
+ * (I x J) and each block of a part (Definitions 1-2) computes its gradient
+ * terms as a GEMM -> Tweedie epilogue -> GEMM chain on the tensor cores
+ * (Sec. 4, Eq. psgld_w, Eq. psgld_h): mu = W_b H_b with BF16 operands and
+ * FP32 accumulation, E = (V_b - mu) max(mu, mu_min)^(-p) / phi rounded to
+ * BF16, E H_b^T and E^T W_b with FP32 accumulation; the update, noise and
+ * mirror stay FP32 as on the sparse path.  PSGLD_ERR_ARG if K > 128 there.
+ * psgld_part_layout is not available for such data (PSGLD_ERR_STATE).
+ * Synchronises `stream`.  Resets the iteration counter and posterior sums. */
 PSGLD_API psgld_status psgld_set_data_dense(psgld_ctx *ctx, const float *V, int64_t ld,
                                   void *stream);
 

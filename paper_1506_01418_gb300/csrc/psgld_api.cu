@@ -63,6 +63,28 @@ __global__ void check_factors_kernel(const float *__restrict__ x, int64_t n, int
     }
 }
 
+__global__ void check_values_kernel(const float *__restrict__ x, int64_t n, int nonneg, int *flag)
+{
+    for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < n;
+         a += (int64_t)gridDim.x * blockDim.x) {
+        const float v = x[a];
+        if (!isfinite(v) || (nonneg && v < 0.0f)) atomicOr(flag, 2);
+    }
+}
+
+// Every value finite, and >= 0 for non-negative models; synchronises st.
+psgld_status check_values(psgld_ctx *c, const float *x, int64_t n, cudaStream_t st)
+{
+    PSGLD_CK(c, cudaMemsetAsync(c->flag, 0, sizeof(int), st));
+    check_values_kernel<<<152 * 4, 256, 0, st>>>(x, n, c->prior.kind == PSGLD_PRIOR_EXPONENTIAL, c->flag);
+    PSGLD_CK(c, cudaGetLastError());
+    int h = 0;
+    PSGLD_CK(c, cudaMemcpyAsync(&h, c->flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    PSGLD_CK(c, cudaStreamSynchronize(st));
+    if (h) return fail(c, PSGLD_ERR_ARG, "V entry not finite, or negative in a non-negative model");
+    return PSGLD_OK;
+}
+
 __global__ void set_t_kernel(int64_t *t, int64_t v)
 {
     if (threadIdx.x == 0) *t = v;
@@ -313,8 +335,44 @@ psgld_status psgld_set_data_dense(psgld_ctx *c, const float *V, int64_t ld, void
     if (!c || !V) return PSGLD_ERR_ARG;
     if (ld < c->J) return fail(c, PSGLD_ERR_ARG, "ld < J");
     const int64_t n = c->I * c->J;
-    if (n >= (1ll << 31)) return fail(c, PSGLD_ERR_ARG, "I*J too large for the entry layout");
     cudaStream_t st = (cudaStream_t)stream;
+    if (c->opt.dense_path) {
+        if (!dense_supported(c->K)) return fail(c, PSGLD_ERR_ARG, "dense tensor-core path supports K <= 128");
+        destroy_graphs(c);
+        free_layout(c);
+        psgld_status s = prepare_dense(c);
+        if (s != PSGLD_OK) return s;
+        s = alloc(c, &c->Vd, n, false);
+        c->ldv = c->J;
+        c->mtiles = dense_mtiles(c);
+        if (s == PSGLD_OK && c->mtiles > 1) s = alloc(c, &c->hpart, (int64_t)c->mtiles * c->J * c->ldk);
+        if (s == PSGLD_OK) {
+            cudaError_t e = cudaMemcpy2DAsync(c->Vd, sizeof(float) * c->J, V, sizeof(float) * ld,
+                                              sizeof(float) * c->J, c->I, cudaMemcpyDefault, st);
+            if (e != cudaSuccess) s = cuda_fail(c, e, "copy V");
+        }
+        if (s == PSGLD_OK) s = check_values(c, c->Vd, n, st);
+        if (s != PSGLD_OK) { free_layout(c); return s; }
+        // every entry observed: N = I J, |Pi_s| = sum_b |R_b| |C_(b+s) mod B|
+        c->N = n;
+        c->part_n.assign(c->B, 0);
+        for (int sp = 0; sp < c->B; ++sp)
+            for (int b = 0; b < c->B; ++b) {
+                const int cb = (b + sp) % c->B;
+                const int64_t rows = ((int64_t)(b + 1) * c->I) / c->B - ((int64_t)b * c->I) / c->B;
+                const int64_t cols = ((int64_t)(cb + 1) * c->J) / c->B - ((int64_t)cb * c->J) / c->B;
+                c->part_n[sp] += rows * cols;
+            }
+        c->dense = true;
+        c->has_data = true;
+        s = zero_posterior(c, st);
+        if (s == PSGLD_OK) {
+            cudaError_t e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) s = cuda_fail(c, e, "sync");
+        }
+        return s;
+    }
+    if (n >= (1ll << 31)) return fail(c, PSGLD_ERR_ARG, "I*J too large for the entry layout");
     float *dV = nullptr, *dv = nullptr;
     int32_t *di = nullptr, *dj = nullptr;
     psgld_status s = alloc(c, &dV, c->I * c->J, false);
@@ -516,6 +574,7 @@ psgld_status psgld_part_layout(psgld_ctx *c, int32_t s, int32_t *row_ptr, int32_
 {
     if (!c || s < 0 || s >= c->B) return PSGLD_ERR_ARG;
     if (!c->has_data) return fail(c, PSGLD_ERR_STATE, "no data set");
+    if (c->dense) return fail(c, PSGLD_ERR_STATE, "dense tensor-core data keeps no entry layout");
     std::vector<int32_t> ptr((size_t)c->I + 1);
     PSGLD_CK(c, cudaMemcpy(ptr.data(), c->side[0].ptr + (int64_t)s * c->I,
                            sizeof(int32_t) * ptr.size(), cudaMemcpyDeviceToHost));

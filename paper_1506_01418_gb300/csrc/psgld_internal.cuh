@@ -13,6 +13,10 @@
 //   segA/segB : per part, the chunk records of the fused part-step kernel:
 //           one per (heavy row, run of at most chunk_len entries)
 //   posterior sums: fp64 copies of W, W^2, Ht, Ht^2 (padded like the factors)
+//   dense tensor-core path instead of the two layouts:
+//   Vd    : I x J fp32, row-major (ldv = J)
+//   hpart : mtiles x J x ldk fp32, the per-M-tile partial G_H rows when a
+//           block has more than one 128-row tile
 #pragma once
 
 #include <cuda_runtime.h>
@@ -58,6 +62,11 @@ struct psgld_ctx {
     int64_t N = 0;
     std::vector<int64_t> part_n;     // observed entries of each part
     psgld::SideLayout side[2];       // 0: rows of W (CSR), 1: rows of Ht (CSC)
+    bool dense = false;              // data kept dense for the tensor-core path
+    float *Vd = nullptr;             // I x ldv fp32 (dense path)
+    int64_t ldv = 0;
+    float *hpart = nullptr;          // mtiles x J x ldk partial G_H rows (mtiles > 1)
+    int mtiles = 0;                  // 128-row tiles of the largest row piece
 
     // factors
     float *W[2] = {nullptr, nullptr};
@@ -124,6 +133,16 @@ int unit_entries(int ngroups);
 // After a synchronisation point: PSGLD_ERR_TIMEOUT (and the flag cleared) if
 // a sampling kernel reported a bounded wait that ran out, else PSGLD_OK.
 psgld_status check_kernel_flag(psgld_ctx *c);
+
+// ---- dense tensor-core path (psgld_dense.cu) --------------------------------
+bool dense_supported(int K);
+// 128-row tiles of the largest row piece (CTAs per block).
+int dense_mtiles(const psgld_ctx *c);
+// One-time kernel attributes for this context's K.
+psgld_status prepare_dense(psgld_ctx *c);
+// Enqueue the gradient kernel of part `part`: G rows of W (and of Ht when
+// mtiles == 1) or hpart rows of Ht.
+psgld_status launch_dense_grad(psgld_ctx *c, int part, cudaStream_t st);
 
 // ---- reductions (psgld_reduce.cu) -----------------------------------------
 psgld_status launch_accumulate(psgld_ctx *c, cudaStream_t st);

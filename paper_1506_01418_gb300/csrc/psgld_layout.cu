@@ -327,6 +327,13 @@ void free_layout(psgld_ctx *c)
         cudaFree(sd.partial);
         sd = SideLayout{};
     }
+    cudaFree(c->Vd);
+    cudaFree(c->hpart);
+    c->Vd = nullptr;
+    c->hpart = nullptr;
+    c->dense = false;
+    c->ldv = 0;
+    c->mtiles = 0;
     c->has_data = false;
     c->N = 0;
     c->part_n.clear();

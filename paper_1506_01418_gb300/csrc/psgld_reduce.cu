@@ -8,8 +8,8 @@
 // Log-likelihood (Sec. 4): -(1/phi) sum_obs d_beta(v || mu), beta = 2 - p,
 // with the named limits at beta = 2, 1, 0 (Euclidean, Kullback-Leibler,
 // Itakura-Saito).  RMSE: sqrt(mean_obs (v - mu)^2).  Both run in FP64 over the
-// row-major layout; per-CTA partial sums are added on the host in CTA order,
-// so the result is deterministic.
+// row-major layout (or the dense V of the tensor-core path); per-CTA partial
+// sums are added on the host in CTA order, so the result is deterministic.
 #include <algorithm>
 
 #include "psgld_internal.cuh"
@@ -91,6 +91,42 @@ reduce_kernel(int mode, const int32_t *__restrict__ ptr, const int32_t *__restri
     if (threadIdx.x == 0) out[blockIdx.x] = sm[0];
 }
 
+// The same sums over a dense V (every entry observed), entries in row-major
+// order.
+__global__ void __launch_bounds__(kRedThreads)
+reduce_dense_kernel(int mode, const float *__restrict__ V, int64_t ldv, int64_t I, int64_t J,
+                    int ldk, int K, const float *__restrict__ W, const float *__restrict__ Ht,
+                    const double *__restrict__ Ws, const double *__restrict__ Hs, double inv_n,
+                    double p, double phi, double mu_min, double *__restrict__ out)
+{
+    double acc = 0.0;
+    for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < I * J;
+         a += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = a / J, j = a - i * J;
+        double mu = 0.0;
+        if (Ws) {
+            for (int k = 0; k < K; ++k) mu += (Ws[i * ldk + k] * inv_n) * (Hs[j * ldk + k] * inv_n);
+        } else {
+            for (int k = 0; k < K; ++k) mu += (double)W[i * ldk + k] * (double)Ht[j * ldk + k];
+        }
+        const double v = V[i * ldv + j];
+        if (mode == 0) {
+            const double m = (p > 0.0 && mu < mu_min) ? mu_min : mu;
+            acc -= beta_div(v, m, p) / phi;
+        } else {
+            acc += (v - mu) * (v - mu);
+        }
+    }
+    __shared__ double sm[kRedThreads];
+    sm[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = kRedThreads / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sm[threadIdx.x] += sm[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[blockIdx.x] = sm[0];
+}
+
 }  // namespace
 
 int reduce_blocks() { return kRedBlocks; }
@@ -117,10 +153,16 @@ psgld_status reduce_loglik_rmse(psgld_ctx *c, int mode, int use_mean, cudaStream
 {
     const SideLayout &L = c->side[0];
     const double inv_n = c->n_samples > 0 ? 1.0 / (double)c->n_samples : 0.0;
-    reduce_kernel<<<kRedBlocks, kRedThreads, 0, st>>>(
-        mode, L.ptr, L.idx, L.val, (int64_t)c->B * c->I, c->I, c->ldk, c->K, c->W[c->wcur],
-        c->Ht[c->hcur], use_mean ? c->sW.s : nullptr, use_mean ? c->sH.s : nullptr, inv_n, c->p,
-        c->phi, c->opt.mu_min, c->red);
+    if (c->dense)
+        reduce_dense_kernel<<<kRedBlocks, kRedThreads, 0, st>>>(
+            mode, c->Vd, c->ldv, c->I, c->J, c->ldk, c->K, c->W[c->wcur], c->Ht[c->hcur],
+            use_mean ? c->sW.s : nullptr, use_mean ? c->sH.s : nullptr, inv_n, c->p, c->phi,
+            c->opt.mu_min, c->red);
+    else
+        reduce_kernel<<<kRedBlocks, kRedThreads, 0, st>>>(
+            mode, L.ptr, L.idx, L.val, (int64_t)c->B * c->I, c->I, c->ldk, c->K, c->W[c->wcur],
+            c->Ht[c->hcur], use_mean ? c->sW.s : nullptr, use_mean ? c->sH.s : nullptr, inv_n,
+            c->p, c->phi, c->opt.mu_min, c->red);
     PSGLD_CK(c, cudaGetLastError());
     PSGLD_CK(c, cudaMemcpyAsync(c->red_host, c->red, sizeof(double) * kRedBlocks,
                                 cudaMemcpyDeviceToHost, st));

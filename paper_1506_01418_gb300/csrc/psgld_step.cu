@@ -30,6 +30,10 @@
 // scratch area and the last chunk to arrive (an arrival counter) adds them in
 // chunk order, so the result does not depend on scheduling.
 //
+// On dense data kept for the tensor cores (dense_path), kernel 1 is the block
+// GEMM -> epilogue -> GEMM chain of psgld_dense.cu instead; kernel 2 is the
+// same.
+//
 // Kernel 2, update.  A flat, fully coalesced sweep over every (row, float4
 // group) item of both factors: the row's gradient (G, nothing for an empty
 // row, or the sum of a split row's partials), Philox4x32-10 normals (counter
@@ -78,6 +82,8 @@ struct UpdSide {
     const float *partial;     // head / tail partial sums of the gradient kernel
     int64_t base;             // first entry of the part
     int64_t items;            // n_rows * ngroups (0 when the factor is frozen)
+    int64_t gstride;          // dense path: distance between partial gradient arrays
+    int gparts;               // dense path: partial gradient arrays to add (0: sparse path)
     float prior_a, prior_b;   // d log p(x)/dx = prior_a + prior_b * x
     uint32_t mat;             // 0 = W, 1 = H (noise stream)
 };
@@ -406,27 +412,35 @@ __global__ void __launch_bounds__(kThreads) update_kernel(const __grid_constant_
         const int q = (int)(item - row * ng);
         const int64_t off = row * ldk + 4 * q;
         const float4 x = ldg4(Sd.X_cur + off);
-        // this row's gradient: nothing (no entries), G (entries within one
-        // unit), or its first unit's tail slot plus the later units' head slots
-        const int64_t p0 = __ldg(Sd.ptr + row) - Sd.base, p1 = __ldg(Sd.ptr + row + 1) - Sd.base;
+        // this row's gradient.  Dense path: G, or the sum in M-tile order of
+        // the block's partial arrays.  Sparse path: nothing (no entries), G
+        // (entries within one unit), or its first unit's tail slot plus the
+        // later units' head slots.
         float4 g = zero4();
-        if (p1 > p0) {
-            const int64_t u0 = p0 >> P.unit_shift, u1 = (p1 - 1) >> P.unit_shift;
-            if (u0 == u1) {
-                g = ldg4(Sd.Gin + off);
-            } else {
-                g = __ldcg(reinterpret_cast<const float4 *>(Sd.partial + (2 * u0 + 1) * ldk + 4 * q));
-                const float *hp = Sd.partial + 4 * q;
-                int64_t uu = u0 + 1;
-                for (; uu + 8 <= u1 + 1; uu += 8) {   // eight independent loads in flight
-                    float4 v[8];
+        if (Sd.gparts > 0) {
+            g = ldg4(Sd.Gin + off);
+            for (int h = 1; h < Sd.gparts; ++h) add4(g, ldg4(Sd.Gin + h * Sd.gstride + off));
+        } else {
+            const int64_t p0 = __ldg(Sd.ptr + row) - Sd.base, p1 = __ldg(Sd.ptr + row + 1) - Sd.base;
+            if (p1 > p0) {
+                const int64_t u0 = p0 >> P.unit_shift, u1 = (p1 - 1) >> P.unit_shift;
+                if (u0 == u1) {
+                    g = ldg4(Sd.Gin + off);
+                } else {
+                    g = __ldcg(reinterpret_cast<const float4 *>(Sd.partial + (2 * u0 + 1) * ldk + 4 * q));
+                    const float *hp = Sd.partial + 4 * q;
+                    int64_t uu = u0 + 1;
+                    for (; uu + 8 <= u1 + 1; uu += 8) {   // eight independent loads in flight
+                        float4 v[8];
 #pragma unroll
-                    for (int w = 0; w < 8; ++w)
-                        v[w] = __ldcg(reinterpret_cast<const float4 *>(hp + 2 * (uu + w) * ldk));
+                        for (int w = 0; w < 8; ++w)
+                            v[w] = __ldcg(reinterpret_cast<const float4 *>(hp + 2 * (uu + w) * ldk));
 #pragma unroll
-                    for (int w = 0; w < 8; ++w) add4(g, v[w]);
+                        for (int w = 0; w < 8; ++w) add4(g, v[w]);
+                    }
+                    for (; uu <= u1; ++uu)
+                        add4(g, __ldcg(reinterpret_cast<const float4 *>(hp + 2 * uu * ldk)));
                 }
-                for (; uu <= u1; ++uu) add4(g, __ldcg(reinterpret_cast<const float4 *>(hp + 2 * uu * ldk)));
             }
         }
         const uint4 r = philox(make_uint4((uint32_t)q, (uint32_t)row, t_lo, (t_hi << 1) | Sd.mat), P);
@@ -523,6 +537,7 @@ psgld_status launch_part_step(psgld_ctx *c, int64_t t, const int64_t *t_dev, int
     const Shape sh = shape_for(c->ngroups);
     GradFn gfn = pick_grad(sh);
     if (!gfn) return fail(c, PSGLD_ERR_ARG, "unsupported K");
+    const bool dense = c->dense;
 
     const bool upd[2] = {!c->opt.freeze_W, !c->opt.freeze_H};
     GradParams GP{};
@@ -535,7 +550,8 @@ psgld_status launch_part_step(psgld_ctx *c, int64_t t, const int64_t *t_dev, int
         float *X_cur = s == 0 ? c->W[c->wcur] : c->Ht[c->hcur];
         float *X_next = s == 0 ? c->W[c->wcur ^ 1] : c->Ht[c->hcur ^ 1];
         float *G_rows = c->G + (s == 0 ? 0 : c->I * c->ldk);
-        const int64_t base = L.part_first[part], n = L.part_first[part + 1] - base;
+        const int64_t base = dense ? 0 : L.part_first[part];
+        const int64_t n = dense ? 0 : L.part_first[part + 1] - base;
         Gs.X_cur = X_cur;
         Gs.Y_cur = s == 0 ? c->Ht[c->hcur] : c->W[c->wcur];
         Gs.Gout = G_rows;
@@ -550,7 +566,13 @@ psgld_status launch_part_step(psgld_ctx *c, int64_t t, const int64_t *t_dev, int
         Us.X_cur = X_cur;
         Us.X_next = X_next;
         Us.Gin = G_rows;
-        Us.ptr = L.ptr + (int64_t)part * n_rows;
+        Us.ptr = dense ? nullptr : L.ptr + (int64_t)part * n_rows;
+        Us.gparts = dense ? 1 : 0;
+        if (dense && s == 1 && c->mtiles > 1) {
+            Us.Gin = c->hpart;
+            Us.gparts = c->mtiles;
+            Us.gstride = c->J * c->ldk;
+        }
         Us.partial = L.partial;
         Us.base = base;
         Us.items = upd[s] ? n_rows * c->ngroups : 0;
@@ -616,7 +638,14 @@ psgld_status launch_part_step(psgld_ctx *c, int64_t t, const int64_t *t_dev, int
         if (cap == cudaStreamCaptureStatusActive) rec_flags = cudaEventRecordExternal;
         PSGLD_CK(c, cudaEventRecordWithFlags(c->ev_start[part], st, rec_flags));
     }
-    if (ggrid > 0) gfn<<<ggrid, kGradThreads, grad_smem(sh), st>>>(GP);
+    if (dense) {
+        if (upd[0] || upd[1]) {
+            const psgld_status ds = launch_dense_grad(c, part, st);
+            if (ds != PSGLD_OK) return ds;
+        }
+    } else if (ggrid > 0) {
+        gfn<<<ggrid, kGradThreads, grad_smem(sh), st>>>(GP);
+    }
     PSGLD_CK(c, cudaGetLastError());
     if (items > 0) update_kernel<<<ugrid, kThreads, 0, st>>>(UP);
     PSGLD_CK(c, cudaGetLastError());

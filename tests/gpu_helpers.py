@@ -26,7 +26,7 @@ class Pair:
     """A GPU chain (through the C ABI) and an oracle chain on the same inputs."""
 
     def __init__(self, I, J, K, B, p, phi, i, j, v, W0, H0, prior_kind=0, lam=(1.0, 1.0),
-                 sig=(1.0, 1.0), seed=1, eps=1e-4, use_graphs=1, **opts):
+                 sig=(1.0, 1.0), seed=1, eps=1e-4, use_graphs=1, V=None, **opts):
         import torch
         self.torch = torch
         self.I, self.J, self.K, self.B = I, J, K, B
@@ -34,9 +34,13 @@ class Pair:
                            lambda_h=lam[1], sigma_w=sig[0], sigma_h=sig[1], seed=seed,
                            eps=eps, use_graphs=use_graphs, **opts)
         dev = "cuda"
-        self.gpu.set_data_coo(torch.as_tensor(i, dtype=torch.int32, device=dev),
-                              torch.as_tensor(j, dtype=torch.int32, device=dev),
-                              torch.as_tensor(v, dtype=torch.float32, device=dev))
+        if V is not None:    # dense I x J array; (i, j, v) lists the same entries
+            self.gpu.set_data_dense(torch.as_tensor(np.ascontiguousarray(V, dtype=np.float32),
+                                                    device=dev))
+        else:
+            self.gpu.set_data_coo(torch.as_tensor(i, dtype=torch.int32, device=dev),
+                                  torch.as_tensor(j, dtype=torch.int32, device=dev),
+                                  torch.as_tensor(v, dtype=torch.float32, device=dev))
         self.orc = oracle.Oracle(I, J, K, B, p, phi, prior_kind=prior_kind, lambda_w=lam[0],
                                  lambda_h=lam[1], sigma_w=sig[0], sigma_h=sig[1])
         oopts = {k: v for k, v in opts.items() if k in ("eps_mode", "eps_a", "eps_b",

@@ -1,0 +1,216 @@
+"""The dense tensor-core path (dense_path = 1) against the FP64 oracle.
+
+The block chain mu = W_b H_b -> E -> (E H_b^T, E^T W_b) runs with BF16
+operands and FP32 accumulation, so one part-step cannot match the oracle to
+FP32 precision.  What is checked:
+
+* one part-step: the drift S * grad log p(V | .) + grad log p(.) that the GPU
+  applied (recovered from its output with the oracle's own Philox normals) is
+  within a first-order error bound of BF16 rounding around the oracle's FP64
+  drift, element by element.  The bound follows the arithmetic: every operand
+  of GEMM1 is rounded to BF16 (relative error <= u = 2^-8), which moves mu by
+  at most 2u sum_k |w_ik h_kj|; that moves e by at most |de/dmu| times as much;
+  e itself is rounded to BF16 (u |e|) and so is the other factor (u), and the
+  FP32 sums add n 2^-24 of the absolute sum.  A transposed operand, a wrong
+  block, a dropped term or a wrong Tweedie power gives errors of the size of
+  the drift itself, far outside the bound;
+* full chains: posterior-mean reconstruction RMSE within 1% of the FP64
+  oracle chain (the configured dense Poisson NMF workload, 256 x 256, K = 8,
+  B = 4);
+* graph replay == direct launches bit for bit; log-likelihood and RMSE over
+  the dense data match the oracle in FP64; refused inputs.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_helpers import Pair
+from paper_1506_01418_gb300 import datagen
+from paper_1506_01418_gb300 import psgld as P
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+U_BF16 = 2.0 ** -8
+U_FP32 = 2.0 ** -24
+
+DENSE = {
+    # name: (I, J, K, B, p, phi, prior_kind, data, eps)
+    "poisson_256_K8_B4": (256, 256, 8, 4, 1.0, 1.0, 0, "poisson", 1e-3),
+    "poisson_ragged_K8": (67, 45, 8, 4, 1.0, 1.0, 0, "poisson", 1e-3),
+    "gauss_K50_two_mtiles_three_ntiles": (300, 700, 50, 2, 0.0, 1.0, 1, "gamma", 1e-3),
+    "gamma_K13": (120, 90, 13, 5, 2.0, 0.7, 0, "gamma", 1e-3),
+    "cp_K100": (140, 170, 100, 2, 1.5, 1.0, 0, "gamma", 1e-3),
+    "invgauss_K128": (90, 260, 128, 2, 3.0, 1.0, 0, "gamma", 1e-3),
+    "poisson_K1_B7": (50, 61, 1, 7, 1.0, 1.0, 0, "poisson", 1e-3),
+    "poisson_uneven_mtiles_K32": (257, 300, 32, 2, 1.0, 1.0, 0, "poisson", 1e-3),
+    "poisson_K64_B1": (200, 150, 64, 1, 1.0, 1.0, 0, "poisson", 1e-3),
+}
+
+
+def _data(I, J, kind, p, seed):
+    if kind == "poisson":
+        V, _, _ = datagen.dense_poisson(I, J, 3, seed)
+    else:
+        V, _, _ = datagen.dense_gamma(I, J, 3, seed)
+    if p >= 2:
+        V = V + np.float32(0.5)
+    return V
+
+
+def _make(name, seed=7, **opts):
+    I, J, K, B, p, phi, kind, data, eps = DENSE[name]
+    V = _data(I, J, data, p, seed=I)
+    i, j, v = datagen.dense_to_coo(V)
+    nonneg = kind == 0
+    W0, H0 = datagen.init_factors(I, J, K, seed=3, scale=0.4 if nonneg else 0.3, nonneg=nonneg)
+    pr = Pair(I, J, K, B, p, phi, i, j, v, W0, H0, prior_kind=kind, lam=(0.8, 1.2),
+              sig=(0.9, 1.1), seed=seed, eps=eps, V=V, dense_path=1, **opts)
+    return pr, V
+
+
+def _drift_bound(V, W, H, t, B, p, phi, S, mu_min=1e-10):
+    """First-order BF16 bound on |drift_gpu - drift| for part t (see module
+    docstring); W I x K, H K x J, FP64."""
+    I, J = V.shape
+    s = (t - 1) % B
+    bW = np.zeros_like(W)
+    bH = np.zeros_like(H)
+    for r in range(B):
+        c = (r + s) % B
+        r0, r1 = oracle.piece_start(r, I, B), oracle.piece_start(r + 1, I, B)
+        c0, c1 = oracle.piece_start(c, J, B), oracle.piece_start(c + 1, J, B)
+        w, h, v = W[r0:r1], H[:, c0:c1], V[r0:r1, c0:c1].astype(np.float64)
+        mu = w @ h
+        A = np.abs(w) @ np.abs(h)
+        dmu = 2 * U_BF16 * A * 1.01 + 4 * w.shape[1] * U_FP32 * A
+        if p > 0:
+            mc = np.maximum(mu, mu_min)
+            lo = np.maximum(mu - dmu, mu_min)
+            e = (v - mu) * mc ** -p / phi
+            fprime = lo ** -p * (1 + p * (np.abs(v - mu) + dmu) / lo) / phi
+        else:
+            e = (v - mu) / phi
+            fprime = np.full_like(mu, 1.0 / phi)
+        de = fprime * dmu + 8 * U_FP32 * np.abs(e)
+        ebf = de + U_BF16 * (np.abs(e) + de)            # error of the BF16 e
+        nc, nr = c1 - c0, r1 - r0
+        bW[r0:r1] = (ebf @ np.abs(h).T) * (1 + U_BF16) + (U_BF16 + nc * U_FP32) * (np.abs(e) @ np.abs(h).T)
+        bH[:, c0:c1] = (np.abs(w).T @ ebf) * (1 + U_BF16) + (U_BF16 + nr * U_FP32) * (np.abs(w).T @ np.abs(e))
+    return S * bW, S * bH
+
+
+def _recovered_drift(x_new, x0, z, D_or, eps, mirror):
+    """drift the GPU applied: x_new = m(x0 + eps drift + sqrt(2 eps) z), m = |.|
+    or identity.  Returns (drift, mask of elements judged, recovery error)."""
+    sd = np.sqrt(2 * eps)
+    y_or = x0 + eps * D_or + sd * z
+    mask = np.abs(y_or) > 0.02 if mirror else np.ones_like(y_or, dtype=bool)
+    sgn = np.sign(y_or) if mirror else 1.0
+    D = (sgn * x_new - x0 - sd * z) / eps
+    rec = (6 * U_FP32 * (np.abs(x0) + np.abs(y_or) + eps * np.abs(D_or))
+           + sd * 3e-6 * (1 + np.abs(z))) / eps + 4 * U_FP32 * np.abs(D_or)
+    return D, mask, rec
+
+
+@pytest.mark.parametrize("name", sorted(DENSE))
+def test_dense_part_step_drift_within_bf16_bound(name):
+    pr, V = _make(name)
+    I, J, K, B, p, phi, kind, data, eps = DENSE[name]
+    mirror = kind == 0
+    for t in range(1, B + 2):
+        W0, H0 = pr.orc.get_factors()
+        D_W, D_H = pr.orc.drift(t)
+        S = pr.orc.scale(t)
+        bW, bH = _drift_bound(V, W0, H0, t, B, p, phi, S)
+        pr.gpu.part_step(t)
+        Wg, Hg = pr.gpu_factors()
+        zW = oracle.noise_matrix(7, t, 0, I, K)
+        zH = oracle.noise_matrix(7, t, 1, J, K).T
+        for xg, x0, z, D, bnd, what in ((Wg, W0, zW, D_W, bW, "W"), (Hg, H0, zH, D_H, bH, "H")):
+            Dg, mask, rec = _recovered_drift(xg.astype(np.float64), x0, z, D, eps, mirror)
+            err = np.abs(Dg - D)
+            lim = bnd + rec
+            bad = mask & (err > lim)
+            assert not bad.any(), (name, t, what, int(bad.sum()), float(err[bad].max()),
+                                   float(lim[bad].min()))
+            assert mask.mean() > 0.9
+            # and the drift itself is far larger than the bound: the check has teeth
+            assert np.sqrt(np.mean(D[mask] ** 2)) > 4 * np.sqrt(np.mean(bnd[mask] ** 2)), (name, what)
+        if mirror:
+            assert Wg.min() >= 0 and Hg.min() >= 0
+        pr.sync_oracle_to_gpu()
+
+
+def test_dense_graph_replay_equals_direct_launches():
+    a, _ = _make("gauss_K50_two_mtiles_three_ntiles", use_graphs=1, burn_in_sweeps=1)
+    b, _ = _make("gauss_K50_two_mtiles_three_ntiles", use_graphs=0, burn_in_sweeps=1)
+    for n in (1, 2):
+        a.gpu.sweep(n)
+        b.gpu.sweep(n)
+    Wa, Ha = a.gpu_factors()
+    Wb, Hb = b.gpu_factors()
+    assert np.array_equal(Wa, Wb) and np.array_equal(Ha, Hb)
+    ma, mb = a.gpu.posterior_mean(), b.gpu.posterior_mean()
+    for x, y in zip(ma[:4], mb[:4]):
+        assert np.array_equal(x, y)
+
+
+def test_dense_is_deterministic():
+    a, _ = _make("poisson_uneven_mtiles_K32")
+    b, _ = _make("poisson_uneven_mtiles_K32")
+    a.gpu.sweep(2)
+    b.gpu.sweep(2)
+    Wa, Ha = a.gpu_factors()
+    Wb, Hb = b.gpu_factors()
+    assert np.array_equal(Wa, Wb) and np.array_equal(Ha, Hb)
+
+
+@pytest.mark.parametrize("name", ["poisson_ragged_K8", "gauss_K50_two_mtiles_three_ntiles",
+                                  "cp_K100", "gamma_K13"])
+def test_dense_log_lik_and_rmse_match_oracle(name):
+    pr, _ = _make(name, burn_in_sweeps=0)
+    pr.gpu.sweep(1)
+    pr.sync_oracle_to_gpu()
+    assert pr.gpu.log_lik() == pytest.approx(pr.orc.log_lik(), rel=1e-9, abs=1e-9)
+    assert pr.gpu.rmse() == pytest.approx(pr.orc.rmse(False), rel=1e-9)
+
+
+def test_dense_chain_posterior_rmse_within_one_percent_of_oracle():
+    """The configured dense Poisson NMF workload (Sec. 4.1 shape): 256 x 256,
+    K = 8, B = 4, W*, H* ~ Gamma(1, 1), V ~ Poisson(W* H*), exponential priors
+    rate 1, eps = 1e-4; 1000 sweeps, posterior means over the last 500."""
+    I = J = 256
+    K, B, sweeps = 8, 4, 1000
+    V, _, _ = datagen.dense_poisson(I, J, K, seed=0)
+    i, j, v = datagen.dense_to_coo(V)
+    W0, H0 = datagen.init_factors(I, J, K, seed=0, scale=1.0, nonneg=True)
+    pr = Pair(I, J, K, B, 1.0, 1.0, i, j, v, W0, H0, prior_kind=0, seed=11, eps=1e-4, V=V,
+              dense_path=1, burn_in_sweeps=sweeps // 2)
+    pr.gpu.sweep(sweeps)
+    pr.orc.sweep(sweeps)
+    r_gpu, r_or = pr.gpu.rmse(True), pr.orc.rmse(True)
+    assert abs(r_gpu - r_or) <= 0.01 * r_or, (r_gpu, r_or)
+
+
+def test_dense_refusals():
+    I, J = 40, 30
+    V = np.ones((I, J), np.float32)
+    c = P.PSGLD(I, J, 129, 2, 1.0, 1.0, dense_path=1)
+    with pytest.raises(P.PsgldError) as ex:
+        c.set_data_dense(torch.from_numpy(V).cuda())
+    assert ex.value.status == P.PSGLD_ERR_ARG
+    c.close()
+    c = P.PSGLD(I, J, 8, 2, 1.0, 1.0, dense_path=1)
+    bad = V.copy()
+    bad[3, 4] = -1.0                          # negative entry, non-negative model
+    with pytest.raises(P.PsgldError) as ex:
+        c.set_data_dense(torch.from_numpy(bad).cuda())
+    assert ex.value.status == P.PSGLD_ERR_ARG
+    c.set_data_dense(torch.from_numpy(V).cuda())
+    with pytest.raises(P.PsgldError) as ex:
+        P.psgld_part_layout(c.ctx, 0, I)
+    assert ex.value.status == P.PSGLD_ERR_STATE
+    c.close()

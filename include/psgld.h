@@ -90,12 +90,15 @@ typedef struct {
     int64_t burn_in_sweeps;   /* sweeps discarded before posterior sums start */
     int32_t use_graphs;       /* 1: each sweep replays one captured CUDA graph */
     int32_t profile;          /* 1: time every part-step launch with CUDA events */
-    int32_t dense_path;       /* 1: psgld_set_data_dense keeps V as a dense FP32 array
-                               * and every part-step runs the tensor-core block chain
-                               * (BF16 operands, FP32 accumulation; K <= 128);
-                               * 0: dense V becomes the sparse layout of all I*J
-                               * entries and runs the FP32 gather path.  Read when
-                               * data is set. */
+    int32_t dense_path;       /* dense V on the tensor cores, read when data is set:
+                               * 0: off (dense V becomes the sparse layout of all
+                               *    I*J entries, FP32 gather path);
+                               * 1: on, kernel chosen by shape: single-pass for
+                               *    blocks of at most 128 rows with K <= 128,
+                               *    else two-sided;
+                               * 2: on, two-sided kernel (K <= 256);
+                               * 3: on, single-pass kernel (K <= 128, FP32 V) */
+    int32_t dense_v_bf16;     /* 1: the two-sided kernel keeps V in BF16 */
 } psgld_options;
 
 /* Defaults: seed 0, fixed eps 1e-4, a = 0.01, b = 0.51, scale N/|Pi_t|,
@@ -126,13 +129,16 @@ PSGLD_API psgld_status psgld_set_data_coo(psgld_ctx *ctx, int64_t nnz, const int
 /* Dense V (every entry observed), row-major with leading dimension ld >= J;
  * non-negative models require V >= 0, and every entry must be finite.
  * With dense_path = 0: the same effect as psgld_set_data_coo over all I*J
- * entries.  With dense_path = 1: the library keeps its own FP32 copy of V
- * (I x J) and each block of a part (Definitions 1-2) computes its gradient
- * terms as a GEMM -> Tweedie epilogue -> GEMM chain on the tensor cores
- * (Sec. 4, Eq. psgld_w, Eq. psgld_h): mu = W_b H_b with BF16 operands and
- * FP32 accumulation, E = (V_b - mu) max(mu, mu_min)^(-p) / phi rounded to
- * BF16, E H_b^T and E^T W_b with FP32 accumulation; the update, noise and
- * mirror stay FP32 as on the sparse path.  PSGLD_ERR_ARG if K > 128 there.
+ * entries.  With dense_path > 0: the library keeps its own copies of V and
+ * each block of a part (Definitions 1-2) computes its gradient terms as a
+ * GEMM -> Tweedie epilogue -> GEMM chain on the tensor cores (Sec. 4,
+ * Eq. psgld_w, Eq. psgld_h): mu = W_b H_b with BF16 operands and FP32
+ * accumulation, E = (V_b - mu) max(mu, mu_min)^(-p) / phi rounded to BF16,
+ * E H_b^T and E^T W_b with FP32 accumulation; the update, noise and mirror
+ * stay FP32 as on the sparse path.  The single-pass kernel computes mu once
+ * per entry; the two-sided kernel computes it once for the W rows and once
+ * for the H columns, so that every gradient row is summed by one CTA.
+ * PSGLD_ERR_ARG if K > 256 (K > 128 for dense_path = 3).
  * psgld_part_layout is not available for such data (PSGLD_ERR_STATE).
  * Synchronises `stream`.  Resets the iteration counter and posterior sums. */
 PSGLD_API psgld_status psgld_set_data_dense(psgld_ctx *ctx, const float *V, int64_t ld,

@@ -262,6 +262,7 @@ psgld_status psgld_set_options(psgld_ctx *c, const psgld_options *o)
         return fail(c, PSGLD_ERR_ARG, "unknown scale_mode");
     if (!(o->mu_min > 0.0)) return fail(c, PSGLD_ERR_ARG, "mu_min must be > 0");
     if (o->burn_in_sweeps < 0) return fail(c, PSGLD_ERR_ARG, "burn_in_sweeps must be >= 0");
+    if (o->dense_path < 0 || o->dense_path > 3) return fail(c, PSGLD_ERR_ARG, "dense_path must be 0..3");
     c->opt = *o;
     destroy_graphs(c);
     destroy_events(c);
@@ -337,21 +338,21 @@ psgld_status psgld_set_data_dense(psgld_ctx *c, const float *V, int64_t ld, void
     const int64_t n = c->I * c->J;
     cudaStream_t st = (cudaStream_t)stream;
     if (c->opt.dense_path) {
-        if (!dense_supported(c->K)) return fail(c, PSGLD_ERR_ARG, "dense tensor-core path supports K <= 128");
+        if (!dense_supported(c->K)) return fail(c, PSGLD_ERR_ARG, "dense tensor-core path supports K <= 256");
         destroy_graphs(c);
         free_layout(c);
-        psgld_status s = prepare_dense(c);
-        if (s != PSGLD_OK) return s;
-        s = alloc(c, &c->Vd, n, false);
+        psgld_status s = alloc(c, &c->Vd, n, false);
         c->ldv = c->J;
-        c->mtiles = dense_mtiles(c);
-        if (s == PSGLD_OK && c->mtiles > 1) s = alloc(c, &c->hpart, (int64_t)c->mtiles * c->J * c->ldk);
         if (s == PSGLD_OK) {
             cudaError_t e = cudaMemcpy2DAsync(c->Vd, sizeof(float) * c->J, V, sizeof(float) * ld,
                                               sizeof(float) * c->J, c->I, cudaMemcpyDefault, st);
             if (e != cudaSuccess) s = cuda_fail(c, e, "copy V");
         }
         if (s == PSGLD_OK) s = check_values(c, c->Vd, n, st);
+        if (s == PSGLD_OK) s = prepare_dense(c);
+        if (s == PSGLD_OK && c->dense_kind == 1 && c->mtiles > 1)
+            s = alloc(c, &c->hpart, (int64_t)c->mtiles * c->J * c->ldk);
+        if (s == PSGLD_OK) s = build_dense_tiles(c, st);
         if (s != PSGLD_OK) { free_layout(c); return s; }
         // every entry observed: N = I J, |Pi_s| = sum_b |R_b| |C_(b+s) mod B|
         c->N = n;
@@ -365,7 +366,8 @@ psgld_status psgld_set_data_dense(psgld_ctx *c, const float *V, int64_t ld, void
             }
         c->dense = true;
         c->has_data = true;
-        s = zero_posterior(c, st);
+        s = build_dense_shadows(c, st);
+        if (s == PSGLD_OK) s = zero_posterior(c, st);
         if (s == PSGLD_OK) {
             cudaError_t e = cudaStreamSynchronize(st);
             if (e != cudaSuccess) s = cuda_fail(c, e, "sync");
@@ -426,7 +428,7 @@ psgld_status psgld_set_factors(psgld_ctx *c, const float *W, const float *Ht, vo
         return fail(c, PSGLD_ERR_ARG, "factor entry not finite, or negative in a non-negative model");
     }
     c->has_factors = true;
-    return PSGLD_OK;
+    return build_dense_shadows(c, st);
 }
 
 psgld_status psgld_get_factors(psgld_ctx *c, float *W, float *Ht, void *stream)

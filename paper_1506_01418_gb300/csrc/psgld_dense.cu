@@ -20,8 +20,9 @@
 // instruction, and completes on an mbarrier through tcgen05.commit.
 // TMEM holds mu / G_H (columns 0..127) and the running G_W (columns 128..),
 // read back with tcgen05.ld (thread t = TMEM lane t = tile row t).  mu never
-// leaves the SM: the epilogue turns it into E in shared memory, both
-// orientations, for GEMM2 and GEMM3.  G_W accumulates over the block's column
+// leaves the SM: the epilogue turns it into E in shared memory, which GEMM2
+// reads K-major and GEMM3 MN-major (transposed), as GEMM3 does the W tile and
+// GEMM2 the H tile.  G_W accumulates over the block's column
 // tiles in TMEM; G_H of a column tile is written once per M-tile (directly
 // when the block has one M-tile, else to per-M-tile partial rows that the
 // update kernel adds in order).
@@ -69,18 +70,26 @@ __device__ __forceinline__ uint32_t cm_off(int r, int k, int KD)
     return (uint32_t)((r >> 3) * (KD * 16) + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
 }
 
-// shared-memory matrix descriptor (no swizzle): start, leading (K) and
-// stride (8-row group) byte offsets, descriptor version 1
+// shared-memory matrix descriptor (no swizzle): start, leading byte offset
+// (between 8 x 16-byte core matrices adjacent along K) and stride byte offset
+// (between core matrices adjacent along M or N), descriptor version 1.  The
+// same tile serves as a K-major operand and, read the other way, as an
+// MN-major one: for a tile stored as (r, c) core matrices (8 r-rows of 16
+// bytes of consecutive c), K-major along c has LBO = c-group stride, SBO =
+// r-group stride; MN-major along c (K = r) has LBO = r-group stride, SBO =
+// c-group stride.
 __device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo)
 {
     return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(lbo >> 4) << 16) |
            ((uint64_t)(sbo >> 4) << 32) | (1ull << 46);
 }
 
-// instruction descriptor: FP32 accumulate, BF16 A and B, both K-major
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N)
+// instruction descriptor: FP32 accumulate, BF16 A and B; a_mn / b_mn select
+// the MN-major (transposed) reading of that operand
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, int a_mn = 0, int b_mn = 0)
 {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)a_mn << 15) | ((uint32_t)b_mn << 16) |
+           ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
 __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
@@ -151,6 +160,19 @@ __device__ __forceinline__ float tweedie(const DenseParams &P, float v, float mu
     return d * exp2f(-P.p * log2f(mc)) * P.phi_inv;
 }
 
+// The same factor with fast reciprocal / exp2 / log2 (relative error a few
+// 2^-22, far below the BF16 rounding of E that follows).
+__device__ __forceinline__ float tweedie_fast(int p_mode, float p, float phi_inv, float mu_min,
+                                              float v, float mu)
+{
+    const float d = (v - mu) * phi_inv;
+    if (p_mode == 0) return d;
+    const float mc = fmaxf(mu, mu_min);
+    if (p_mode == 1) return __fdividef(d, mc);
+    if (p_mode == 2) return __fdividef(d, mc * mc);
+    return d * exp2f(-p * __log2f(mc));
+}
+
 __device__ __forceinline__ void st_bf16(unsigned char *base, uint32_t off, float x)
 {
     *reinterpret_cast<__nv_bfloat16 *>(base + off) = __float2bfloat16_rn(x);
@@ -162,13 +184,12 @@ __global__ void __launch_bounds__(kDenseThreads, 1) dense_grad_kernel(const __gr
     extern __shared__ __align__(1024) unsigned char sm[];
     constexpr uint32_t kOpBytes = kTile * KP * 2;           // a 128 x KP BF16 tile
     constexpr uint32_t kEBytes = kTile * kTile * 2;         // a 128 x 128 BF16 tile
-    unsigned char *A1 = sm;                     // W tile   rows m, K-dim k   (GEMM1 A)
-    unsigned char *B1 = A1 + kOpBytes;          // Ht tile  rows n, K-dim k   (GEMM1 B)
-    unsigned char *B2 = B1 + kOpBytes;          // H tile   rows k, K-dim n   (GEMM2 B)
-    unsigned char *B3 = B2 + kOpBytes;          // Wt tile  rows k, K-dim m   (GEMM3 B)
-    unsigned char *A2 = B3 + kOpBytes;          // E        rows m, K-dim n   (GEMM2 A)
-    unsigned char *A3 = A2 + kEBytes;           // E^T      rows n, K-dim m   (GEMM3 A)
-    uint64_t *bar = reinterpret_cast<uint64_t *>(A3 + kEBytes);
+    // Each tile is stored once as (row, K-dim) core matrices and read K-major
+    // by one GEMM and MN-major by another.
+    unsigned char *A1 = sm;                     // W tile  (m, k): GEMM1 A; GEMM3 B (MN-major)
+    unsigned char *B1 = A1 + kOpBytes;          // Ht tile (n, k): GEMM1 B; GEMM2 B (MN-major)
+    unsigned char *A2 = B1 + kOpBytes;          // E tile  (m, n): GEMM2 A; GEMM3 A (MN-major)
+    uint64_t *bar = reinterpret_cast<uint64_t *>(A2 + kEBytes);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 1);
 
     const int tid = threadIdx.x, warp = tid >> 5;
@@ -215,9 +236,7 @@ __global__ void __launch_bounds__(kDenseThreads, 1) dense_grad_kernel(const __gr
             const float wv[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
             for (int d = 0; d < 4; ++d) {
-                const float x = k + d < K ? wv[d] : 0.f;
-                st_bf16(A1, cm_off(tid, k + d, KP), x);
-                st_bf16(B3, cm_off(k + d, tid, kTile), x);
+                st_bf16(A1, cm_off(tid, k + d, KP), k + d < K ? wv[d] : 0.f);
             }
         }
     }
@@ -236,9 +255,7 @@ __global__ void __launch_bounds__(kDenseThreads, 1) dense_grad_kernel(const __gr
                 const float hv[4] = {h.x, h.y, h.z, h.w};
 #pragma unroll
                 for (int d = 0; d < 4; ++d) {
-                    const float x = k + d < K ? hv[d] : 0.f;
-                    st_bf16(B1, cm_off(tid, k + d, KP), x);
-                    st_bf16(B2, cm_off(k + d, tid, kTile), x);
+                    st_bf16(B1, cm_off(tid, k + d, KP), k + d < K ? hv[d] : 0.f);
                 }
             }
         }
@@ -275,7 +292,6 @@ __global__ void __launch_bounds__(kDenseThreads, 1) dense_grad_kernel(const __gr
                     float e = 0.f;
                     if (rv && col < ce) e = tweedie(P, P.V[row * P.ldv + col], mu[j]);
                     st_bf16(A2, cm_off(tid, c + j, kTile), e);
-                    st_bf16(A3, cm_off(c + j, tid, kTile), e);
                 }
             }
         }
@@ -284,21 +300,23 @@ __global__ void __launch_bounds__(kDenseThreads, 1) dense_grad_kernel(const __gr
         __syncthreads();
         fence_after();
 
-        // GEMM2: G_W (columns 128..128+KP) += E . H_tile^T;  GEMM3: G_H tile
-        // (columns 0..KP, over mu) = E^T . W_tile
+        // GEMM2: G_W (columns 128..128+KP) += E . H_tile^T   (A = E K-major,
+        //        B = Ht tile read MN-major: N = k, K-dim = n)
+        // GEMM3: G_H tile (columns 0..KP, over mu) = E^T . W_tile   (A = E read
+        //        MN-major: M = n, K-dim = m; B = W tile read MN-major: N = k)
         if (tid == 0) {
             const uint64_t aE = sdesc(saddr(A2), 128, kTile * 16);
-            const uint64_t bH2 = sdesc(saddr(B2), 128, kTile * 16);
-            const uint64_t aEt = sdesc(saddr(A3), 128, kTile * 16);
-            const uint64_t bWt = sdesc(saddr(B3), 128, kTile * 16);
+            const uint64_t bHt = sdesc(saddr(B1), KP * 16, 128);
+            const uint64_t aEt = sdesc(saddr(A2), kTile * 16, 128);
+            const uint64_t bW = sdesc(saddr(A1), KP * 16, 128);
 #pragma unroll
             for (int ks = 0; ks < kTile / 16; ++ks)
-                mma_bf16(tmem + kTile, aE + (uint64_t)(ks * 16), bH2 + (uint64_t)(ks * 16),
-                         idesc_bf16(kTile, KP), (nt > 0 || ks > 0));
+                mma_bf16(tmem + kTile, aE + (uint64_t)(ks * 16), bHt + (uint64_t)(ks * 2 * KP),
+                         idesc_bf16(kTile, KP, 0, 1), (nt > 0 || ks > 0));
 #pragma unroll
             for (int ks = 0; ks < kTile / 16; ++ks)
-                mma_bf16(tmem, aEt + (uint64_t)(ks * 16), bWt + (uint64_t)(ks * 16),
-                         idesc_bf16(kTile, KP), ks > 0);
+                mma_bf16(tmem, aEt + (uint64_t)(ks * 2 * kTile), bW + (uint64_t)(ks * 2 * KP),
+                         idesc_bf16(kTile, KP, 1, 1), ks > 0);
             mma_commit(bar);
         }
         ok = bar_wait(bar, phase);
@@ -356,6 +374,369 @@ __global__ void __launch_bounds__(kDenseThreads, 1) dense_grad_kernel(const __gr
                      :: "r"(tmem), "r"(kTmemCols) : "memory");
 }
 
+// ===========================================================================
+// Two-sided pipelined kernel (blocks of any size, K <= 256)
+// ===========================================================================
+//
+// A block larger than one 128-row tile would need its G_H summed over the
+// block's M-tiles.  Instead the work of a part is split into two kinds of
+// items that read only the previous factors: a rows item owns 128 rows of W
+// of one block and walks all the block's columns, accumulating G_W of those
+// rows in TMEM; a columns item owns 128 rows of H^T (columns of V) and walks
+// all the block's rows, accumulating G_H.  Each computes its own mu and E
+// (GEMM1 twice per entry: 4 contractions instead of 3), and every G row is
+// written once, complete, by one CTA -- no partial sums, no atomics.
+//
+// Operands come from HBM already in the MMA layout: BF16 shadows of W and
+// H^T cut into 128-row canonical K-major tiles per piece (kept by the update
+// kernel), and V cut into 128 x 64 tiles per block, once per orientation, in
+// the order the epilogue reads them (4-column FP32 or 8-column BF16 chunks,
+// one 16-byte chunk per owned row, so a warp reads 512 contiguous bytes).
+// Every tile is one bulk copy.
+//
+// One persistent CTA per SM, 6 warps:
+//   warp 0 (one thread)  producer: the owned tile once per item, then per
+//                         walked tile the other factor's 64-row tile and the
+//                         V tile into a ring of stages (bulk copies);
+//   warp 1 (one thread)  MMA issuer: GEMM1 mu_j = A . B_j^T into one of two
+//                         TMEM buffers, then GEMM2 G += E_(j-1) . B_(j-1)
+//                         (B read MN-major), so GEMM1 of tile j overlaps the
+//                         epilogue of tile j-1; completions via tcgen05.commit;
+//   warps 2-5            epilogue: TMEM mu + V (shared memory) -> E (BF16,
+//                         shared memory, two buffers), and after an item's
+//                         last tile the G rows from TMEM to HBM.
+// TMEM: mu buffers at columns 0 and 64, G at 128 .. 128 + KP.
+// Padding rows and columns of every tile are zero, so mu and E are zero
+// there and need no masks.
+namespace two_sided {
+
+constexpr int kThreads = 192;
+constexpr int kOwn = 128;          // owned rows per item (TMEM lanes)
+constexpr int kBN = 64;            // walked rows per tile
+constexpr uint32_t kTmemCols = 512;
+constexpr uint32_t kGCol = 128;
+constexpr int kMaxStages = 4;
+
+struct Side {
+    const uint16_t *own_sh;     // BF16 shadow tiles of the owned factor
+    const uint16_t *walk_sh;    // ... of the walked factor
+    const unsigned char *Vt;    // V tiles in this orientation
+    float *G;                   // G rows of the owned factor
+    int64_t n_own, n_walk;      // I or J
+    int own_tiles;              // 128-row tile slots per owned piece
+    int walk_tiles128;          // 128-row shadow tile slots per walked piece
+    int walk_tiles;             // 64-row V tile slots per walked piece
+};
+
+struct Params {
+    Side side[2];
+    int B, part, KP, ldk, stages, items_a, items;
+    float phi_inv, p, mu_min;
+    int p_mode;
+    int *err;
+};
+
+struct Bars {
+    uint64_t full[kMaxStages], empty[kMaxStages];
+    uint64_t mu_full[2], mu_empty[2], e_full[2], e_empty[2];
+    uint64_t a_full, a_empty, g_full, g_empty;
+    uint32_t tmem;
+    int abort;
+};
+
+__device__ __forceinline__ void bar_init(uint64_t *b, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(saddr(b)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void bar_arrive(uint64_t *b)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(saddr(b)) : "memory");
+}
+
+__device__ __forceinline__ void bar_expect_tx(uint64_t *b, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                 :: "r"(saddr(b)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *b)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 :: "r"(saddr(dst)), "l"(src), "r"(bytes), "r"(saddr(b)) : "memory");
+}
+
+// Bounded wait by one thread; gives up (and raises the abort flag) when the
+// CTA is aborting or the wait runs out.
+__device__ __forceinline__ bool wait1(Bars *S, uint64_t *b, uint32_t parity)
+{
+    if (*(volatile int *)&S->abort) return false;
+    if (bar_wait(b, parity)) return true;
+    *(volatile int *)&S->abort = 1;
+    return false;
+}
+
+// The same for a whole warp, with one warp-uniform answer.
+__device__ __forceinline__ bool wait32(Bars *S, uint64_t *b, uint32_t parity)
+{
+    const bool stop = __any_sync(0xffffffffu, *(volatile int *)&S->abort != 0);
+    bool ok = !stop && bar_wait(b, parity);
+    ok = __all_sync(0xffffffffu, ok);
+    if (!ok && (threadIdx.x & 31) == 0) *(volatile int *)&S->abort = 1;
+    return ok;
+}
+
+struct Item {
+    int side, own_piece, walk_piece, ot, own_rows_in_tile, nj;
+    int64_t own_start;
+};
+
+__device__ __forceinline__ bool decode(const Params &P, int it, Item &x)
+{
+    const int B = P.B;
+    int side = 0, k = it;
+    if (k >= P.items_a) { side = 1; k -= P.items_a; }
+    const Side &Sd = P.side[side];
+    const int b = k / Sd.own_tiles, ot = k % Sd.own_tiles;
+    const int cpiece = (b + P.part) % B;
+    x.side = side;
+    x.own_piece = side == 0 ? b : cpiece;
+    x.walk_piece = side == 0 ? cpiece : b;
+    x.ot = ot;
+    x.own_start = ((int64_t)x.own_piece * Sd.n_own) / B;
+    const int64_t own_rows = ((int64_t)(x.own_piece + 1) * Sd.n_own) / B - x.own_start;
+    const int64_t walk_rows = ((int64_t)(x.walk_piece + 1) * Sd.n_walk) / B -
+                              ((int64_t)x.walk_piece * Sd.n_walk) / B;
+    const int64_t left = own_rows - (int64_t)ot * kOwn;
+    x.own_rows_in_tile = (int)(left < kOwn ? left : kOwn);
+    x.nj = (int)((walk_rows + kBN - 1) / kBN);
+    return left > 0;
+}
+
+template <typename VT>
+__global__ void __launch_bounds__(kThreads, 1) chain_kernel(const __grid_constant__ Params P)
+{
+    extern __shared__ __align__(1024) unsigned char sm[];
+    const int KP = P.KP;
+    const uint32_t a_bytes = (uint32_t)kOwn * KP * 2;           // owned tile
+    const uint32_t b_bytes = (uint32_t)kBN * KP * 2;            // walked tile
+    const uint32_t v_bytes = (uint32_t)kOwn * kBN * sizeof(VT); // V tile
+    constexpr uint32_t e_bytes = kOwn * kBN * 2;
+    unsigned char *sA = sm;
+    unsigned char *sE = sA + a_bytes;                           // 2 x e_bytes
+    unsigned char *sStage = sE + 2 * e_bytes;                   // stages x (b + v)
+    const uint32_t stage_bytes = b_bytes + v_bytes;
+    Bars *S = reinterpret_cast<Bars *>(sStage + (size_t)P.stages * stage_bytes);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int NS = P.stages;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NS; ++s) { bar_init(&S->full[s], 1); bar_init(&S->empty[s], 1); }
+        for (int b = 0; b < 2; ++b) {
+            bar_init(&S->mu_full[b], 1); bar_init(&S->mu_empty[b], 4);
+            bar_init(&S->e_full[b], 4); bar_init(&S->e_empty[b], 1);
+        }
+        bar_init(&S->a_full, 1); bar_init(&S->a_empty, 1);
+        bar_init(&S->g_full, 1); bar_init(&S->g_empty, 4);
+        S->abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(saddr(&S->tmem)), "r"(kTmemCols) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = S->tmem;
+
+    if (warp == 0) {
+        // ---------------- producer
+        if (lane == 0) {
+            uint32_t tc = 0, ic = 0;
+            for (int it = blockIdx.x; it < P.items; it += gridDim.x) {
+                Item x;
+                if (!decode(P, it, x)) continue;
+                const Side &Sd = P.side[x.side];
+                if (!wait1(S, &S->a_empty, (ic & 1) ^ 1)) goto done0;
+                bar_expect_tx(&S->a_full, a_bytes);
+                bulk_g2s(sA, Sd.own_sh + ((int64_t)x.own_piece * Sd.own_tiles + x.ot) * kOwn * KP,
+                         a_bytes, &S->a_full);
+                const unsigned char *vbase =
+                    Sd.Vt + ((((int64_t)x.own_piece * P.B + x.walk_piece) * Sd.own_tiles + x.ot) *
+                             Sd.walk_tiles) * (int64_t)v_bytes;
+                for (int j = 0; j < x.nj; ++j, ++tc) {
+                    const int st = (int)(tc % NS);
+                    if (!wait1(S, &S->empty[st], ((tc / NS) & 1) ^ 1)) goto done0;
+                    unsigned char *dst = sStage + (size_t)st * stage_bytes;
+                    bar_expect_tx(&S->full[st], stage_bytes);
+                    bulk_g2s(dst,
+                             Sd.walk_sh + ((int64_t)x.walk_piece * Sd.walk_tiles128 + (j >> 1)) * kOwn * KP +
+                                 (int64_t)(j & 1) * kBN * KP,
+                             b_bytes, &S->full[st]);
+                    bulk_g2s(dst + b_bytes, vbase + (int64_t)j * v_bytes, v_bytes, &S->full[st]);
+                }
+                ++ic;
+            }
+        }
+    done0:
+        __syncwarp();
+    } else if (warp == 1) {
+        // ---------------- MMA issuer
+        if (lane == 0) {
+            uint32_t tc = 0, ic = 0, mu_use[2] = {0, 0}, e_use[2] = {0, 0};
+            const uint32_t id1 = idesc_bf16(kOwn, kBN);
+            const uint32_t id2 = idesc_bf16(kOwn, KP, 0, 1);
+            const uint64_t dA = sdesc(saddr(sA), 128, KP * 16);
+            for (int it = blockIdx.x; it < P.items; it += gridDim.x) {
+                Item x;
+                if (!decode(P, it, x)) continue;
+                if (!wait1(S, &S->a_full, ic & 1)) goto done1;
+                fence_after();
+                int prev_st = 0;
+                for (int j = 0; j <= x.nj; ++j) {
+                    int st = 0;
+                    if (j < x.nj) {
+                        st = (int)(tc % NS);
+                        if (!wait1(S, &S->full[st], (tc / NS) & 1)) goto done1;
+                        const int b = j & 1;
+                        if (!wait1(S, &S->mu_empty[b], (mu_use[b] & 1) ^ 1)) goto done1;
+                        fence_after();
+                        const uint64_t dB = sdesc(saddr(sStage + (size_t)st * stage_bytes), 128, KP * 16);
+                        for (int ks = 0; ks < KP / 16; ++ks)
+                            mma_bf16(tmem + (uint32_t)(b * kBN), dA + (uint64_t)(ks * 16),
+                                     dB + (uint64_t)(ks * 16), id1, ks > 0);
+                        mma_commit(&S->mu_full[b]);
+                        ++mu_use[b];
+                        ++tc;
+                    }
+                    if (j > 0) {
+                        // GEMM2 of tile j - 1
+                        const int jj = j - 1, b = jj & 1;
+                        if (!wait1(S, &S->e_full[b], e_use[b] & 1)) goto done1;
+                        if (jj == 0 && !wait1(S, &S->g_empty, (ic & 1) ^ 1)) goto done1;
+                        fence_after();
+                        const uint64_t dE = sdesc(saddr(sE + b * e_bytes), 128, kBN * 16);
+                        const uint64_t dBt = sdesc(saddr(sStage + (size_t)prev_st * stage_bytes), KP * 16, 128);
+                        for (int ks = 0; ks < kBN / 16; ++ks)
+                            mma_bf16(tmem + kGCol, dE + (uint64_t)(ks * 16), dBt + (uint64_t)(ks * 2 * KP),
+                                     id2, (jj > 0 || ks > 0));
+                        mma_commit(&S->e_empty[b]);
+                        mma_commit(&S->empty[prev_st]);
+                        ++e_use[b];
+                    }
+                    prev_st = st;
+                }
+                mma_commit(&S->g_full);
+                mma_commit(&S->a_empty);
+                ++ic;
+            }
+        }
+    done1:
+        __syncwarp();
+    } else {
+        // ---------------- epilogue (warps 2..5; TMEM lane quarter = warp % 4)
+        const int q = warp & 3;
+        const int rho = 32 * q + lane;                      // owned row in the tile
+        const uint32_t lane_base = (uint32_t)(32 * q) << 16;
+        uint32_t tc = 0, ic = 0, mu_use[2] = {0, 0}, e_use[2] = {0, 0};
+        for (int it = blockIdx.x; it < P.items; it += gridDim.x) {
+            Item x;
+            if (!decode(P, it, x)) continue;
+            const Side &Sd = P.side[x.side];
+            for (int j = 0; j < x.nj; ++j, ++tc) {
+                const int b = j & 1, st = (int)(tc % NS);
+                if (!wait32(S, &S->full[st], (tc / NS) & 1)) goto done2;
+                if (!wait32(S, &S->mu_full[b], mu_use[b] & 1)) goto done2;
+                if (!wait32(S, &S->e_empty[b], (e_use[b] & 1) ^ 1)) goto done2;
+                fence_after();
+                const unsigned char *vt = sStage + (size_t)st * stage_bytes + b_bytes;
+                unsigned char *eb = sE + b * e_bytes;
+#pragma unroll
+                for (int c = 0; c < kBN; c += 32) {
+                    float mu[32];
+                    tmem_ld32(tmem + lane_base + (uint32_t)(b * kBN + c), mu);
+                    float v[32];
+                    if constexpr (sizeof(VT) == 4) {
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            const float4 w = *reinterpret_cast<const float4 *>(
+                                vt + ((size_t)((c >> 2) + i) * kOwn + rho) * 16);
+                            v[4 * i] = w.x; v[4 * i + 1] = w.y; v[4 * i + 2] = w.z; v[4 * i + 3] = w.w;
+                        }
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            const uint4 w = *reinterpret_cast<const uint4 *>(
+                                vt + ((size_t)((c >> 3) + i) * kOwn + rho) * 16);
+                            const uint32_t u[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                            for (int h = 0; h < 4; ++h) {
+                                v[8 * i + 2 * h] = __uint_as_float(u[h] << 16);
+                                v[8 * i + 2 * h + 1] = __uint_as_float(u[h] & 0xffff0000u);
+                            }
+                        }
+                    }
+                    uint32_t pk[16];
+#pragma unroll
+                    for (int h = 0; h < 16; ++h) {
+                        const float e0 = tweedie_fast(P.p_mode, P.p, P.phi_inv, P.mu_min, v[2 * h], mu[2 * h]);
+                        const float e1 = tweedie_fast(P.p_mode, P.p, P.phi_inv, P.mu_min, v[2 * h + 1], mu[2 * h + 1]);
+                        __nv_bfloat162 t2 = __floats2bfloat162_rn(e0, e1);
+                        pk[h] = *reinterpret_cast<uint32_t *>(&t2);
+                    }
+                    // E (owned row rho, walked columns c..c+31) in K-major core matrices
+#pragma unroll
+                    for (int g = 0; g < 4; ++g)
+                        *reinterpret_cast<uint4 *>(eb + (rho >> 3) * (kBN * 16) + ((c >> 3) + g) * 128 +
+                                                   (rho & 7) * 16) =
+                            make_uint4(pk[4 * g], pk[4 * g + 1], pk[4 * g + 2], pk[4 * g + 3]);
+                }
+                fence_async_smem();
+                fence_before();
+                __syncwarp();
+                if (lane == 0) { bar_arrive(&S->mu_empty[b]); bar_arrive(&S->e_full[b]); }
+                ++mu_use[b];
+                ++e_use[b];
+            }
+            // the item's G rows
+            if (!wait32(S, &S->g_full, ic & 1)) goto done2;
+            fence_after();
+            {
+                const bool rv = rho < x.own_rows_in_tile;
+                float *dst = Sd.G + (x.own_start + (int64_t)x.ot * kOwn + rho) * P.ldk;
+                for (int c = 0; c < KP; c += 32) {
+                    float g[32];
+                    tmem_ld32(tmem + lane_base + kGCol + (uint32_t)c, g);
+                    if (rv) {
+#pragma unroll
+                        for (int h = 0; h < 32; h += 4)
+                            if (c + h < P.ldk)
+                                *reinterpret_cast<float4 *>(dst + c + h) = make_float4(g[h], g[h + 1], g[h + 2], g[h + 3]);
+                    }
+                }
+            }
+            fence_before();
+            __syncwarp();
+            if (lane == 0) bar_arrive(&S->g_empty);
+            ++ic;
+        }
+    done2:
+        __syncwarp();
+    }
+
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (threadIdx.x == 0 && S->abort) atomicOr(P.err, 16);
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;"
+                     :: "r"(tmem), "r"(kTmemCols) : "memory");
+}
+
+}  // namespace two_sided
+
 using DenseFn = void (*)(DenseParams);
 
 DenseFn pick_dense(int kp)
@@ -378,12 +759,12 @@ int dense_kp(int K)
 
 size_t dense_smem(int kp)
 {
-    return 4 * (size_t)kTile * kp * 2 + 2 * (size_t)kTile * kTile * 2 + 16;
+    return 2 * (size_t)kTile * kp * 2 + (size_t)kTile * kTile * 2 + 16;
 }
 
 }  // namespace
 
-bool dense_supported(int K) { return K >= 1 && K <= 128; }
+bool dense_supported(int K) { return K >= 1 && K <= 256; }
 
 int dense_mtiles(const psgld_ctx *c)
 {
@@ -391,20 +772,200 @@ int dense_mtiles(const psgld_ctx *c)
     return (int)((rows + kTile - 1) / kTile);
 }
 
+namespace {
+
+int cdiv(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+__device__ __forceinline__ int64_t piece_start_d(int64_t r, int64_t n, int B) { return (r * n) / B; }
+__device__ __forceinline__ int64_t piece_of_d(int64_t x, int64_t n, int B) { return ((x + 1) * B - 1) / n; }
+
+// V (I x J, FP32, row-major) into the tiles of one orientation (side 0: owned
+// = rows of V, side 1: owned = columns); padding stays zero.
+template <typename VT>
+__global__ void build_vtiles_kernel(const float *__restrict__ V, int64_t I, int64_t J, int B, int side,
+                                    int own_tiles, int walk_tiles, VT *__restrict__ out)
+{
+    const int64_t n_own = side == 0 ? I : J, n_walk = side == 0 ? J : I;
+    for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < I * J;
+         a += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = a / J, j = a - i * J;
+        const int64_t own = side == 0 ? i : j, walk = side == 0 ? j : i;
+        const int64_t op = piece_of_d(own, n_own, B), wp = piece_of_d(walk, n_walk, B);
+        const int64_t orow = own - piece_start_d(op, n_own, B), wrow = walk - piece_start_d(wp, n_walk, B);
+        const int64_t tile = ((op * B + wp) * own_tiles + (orow >> 7)) * walk_tiles + (wrow >> 6);
+        const int rho = (int)(orow & 127), kap = (int)(wrow & 63);
+        int64_t e;
+        if constexpr (sizeof(VT) == 4)
+            e = tile * 8192 + ((int64_t)(kap >> 2) * 128 + rho) * 4 + (kap & 3);
+        else
+            e = tile * 8192 + ((int64_t)(kap >> 3) * 128 + rho) * 8 + (kap & 7);
+        if constexpr (sizeof(VT) == 4)
+            out[e] = V[a];
+        else
+            out[e] = __float2bfloat16_rn(V[a]);
+    }
+}
+
+__global__ void build_shadow_kernel(const float *__restrict__ X, int64_t n, int ngroups, int ldk, int B,
+                                    int tiles, int KP, uint16_t *__restrict__ sh)
+{
+    for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < n * ngroups;
+         a += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = a / ngroups;
+        const int q = (int)(a - row * ngroups);
+        const float4 x = *reinterpret_cast<const float4 *>(X + row * ldk + 4 * q);
+        dev::shadow_store4(sh, row, 4 * q, x, n, B, tiles, KP);
+    }
+}
+
+using ChainFn = void (*)(two_sided::Params);
+
+size_t two_sided_bytes(int KP, int vsize, int stages)
+{
+    return (size_t)two_sided::kOwn * KP * 2 + 2 * (size_t)two_sided::kOwn * two_sided::kBN * 2 +
+           (size_t)stages * ((size_t)two_sided::kBN * KP * 2 + (size_t)two_sided::kOwn * two_sided::kBN * vsize) +
+           sizeof(two_sided::Bars) + 16;
+}
+
+// At least half of an SM's shared memory, so that one CTA (and one 512-column
+// TMEM allocation) runs per SM.
+size_t two_sided_smem(int KP, int vsize, int stages)
+{
+    return std::max<size_t>(two_sided_bytes(KP, vsize, stages), 120 * 1024);
+}
+
+int two_sided_stages(int KP, int vsize)
+{
+    int s = two_sided::kMaxStages;
+    while (s > 2 && two_sided_bytes(KP, vsize, s) > 232448) --s;
+    return s;
+}
+
+}  // namespace
+
 psgld_status prepare_dense(psgld_ctx *c)
 {
-    DenseFn fn = pick_dense(dense_kp(c->K));
-    if (!fn) return fail(c, PSGLD_ERR_ARG, "dense tensor-core path supports K <= 128");
+    const int mode = c->opt.dense_path;
+    const bool vb = c->opt.dense_v_bf16 != 0;
+    if (!dense_supported(c->K)) return fail(c, PSGLD_ERR_ARG, "dense tensor-core path supports K <= 256");
+    c->mtiles = dense_mtiles(c);
+    bool two = mode == 2 || (mode == 1 && (vb || c->K > 128 || c->mtiles > 1));
+    if (mode == 3 && (vb || c->K > 128))
+        return fail(c, PSGLD_ERR_ARG, "single-pass dense kernel: K <= 128 and FP32 V only");
+    if (!two) {
+        c->dense_kind = 1;
+        const int kp = dense_kp(c->K);
+        PSGLD_CK(c, cudaFuncSetAttribute(pick_dense(kp), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)dense_smem(kp)));
+        return PSGLD_OK;
+    }
+    c->dense_kind = 2;
+    c->v_bf16 = vb ? 1 : 0;
+    c->KP = 16 * cdiv(c->K, 16);
+    const int64_t maxI = (c->I + c->B - 1) / c->B, maxJ = (c->J + c->B - 1) / c->B;
+    c->mt_max = cdiv(maxI, 128);
+    c->nt_max = cdiv(maxJ, 128);
+    c->ni_max = cdiv(maxI, 64);
+    c->nj_max = cdiv(maxJ, 64);
+    const int vs = vb ? 2 : 4;
+    const int stages = two_sided_stages(c->KP, vs);
+    ChainFn fn = vb ? two_sided::chain_kernel<__nv_bfloat16> : two_sided::chain_kernel<float>;
     PSGLD_CK(c, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)dense_smem(dense_kp(c->K))));
+                                     (int)two_sided_smem(c->KP, vs, stages)));
+    const int64_t B = c->B;
+    const int64_t nA = B * B * c->mt_max * c->nj_max * 8192, nB = B * B * c->nt_max * c->ni_max * 8192;
+    const int64_t nW = B * c->mt_max * 128 * c->KP, nH = B * c->nt_max * 128 * c->KP;
+    auto al = [&](void **p, size_t bytes) -> psgld_status {
+        if (cudaMalloc(p, bytes) != cudaSuccess) {
+            *p = nullptr;
+            cudaGetLastError();
+            return fail(c, PSGLD_ERR_OOM, "device allocation failed");
+        }
+        PSGLD_CK(c, cudaMemset(*p, 0, bytes));
+        return PSGLD_OK;
+    };
+    psgld_status s = al(&c->VA, (size_t)nA * vs);
+    if (s == PSGLD_OK) s = al(&c->VB, (size_t)nB * vs);
+    if (s == PSGLD_OK) s = al((void **)&c->Wsh, (size_t)nW * 2);
+    if (s == PSGLD_OK) s = al((void **)&c->Hsh, (size_t)nH * 2);
+    return s;
+}
+
+psgld_status build_dense_tiles(psgld_ctx *c, cudaStream_t st)
+{
+    if (c->dense_kind != 2) return PSGLD_OK;
+    const int64_t n = c->I * c->J;
+    const unsigned grid = (unsigned)std::min<int64_t>((n + 255) / 256, 152 * 32);
+    for (int side = 0; side < 2; ++side) {
+        const int own_tiles = side == 0 ? c->mt_max : c->nt_max;
+        const int walk_tiles = side == 0 ? c->nj_max : c->ni_max;
+        void *out = side == 0 ? c->VA : c->VB;
+        if (c->v_bf16)
+            build_vtiles_kernel<__nv_bfloat16><<<grid, 256, 0, st>>>(c->Vd, c->I, c->J, c->B, side, own_tiles,
+                                                                      walk_tiles, (__nv_bfloat16 *)out);
+        else
+            build_vtiles_kernel<float><<<grid, 256, 0, st>>>(c->Vd, c->I, c->J, c->B, side, own_tiles,
+                                                              walk_tiles, (float *)out);
+        PSGLD_CK(c, cudaGetLastError());
+    }
+    return PSGLD_OK;
+}
+
+psgld_status build_dense_shadows(psgld_ctx *c, cudaStream_t st)
+{
+    if (!c->dense || c->dense_kind != 2 || !c->has_factors) return PSGLD_OK;
+    for (int side = 0; side < 2; ++side) {
+        const int64_t n = side == 0 ? c->I : c->J;
+        const float *X = side == 0 ? c->W[c->wcur] : c->Ht[c->hcur];
+        const unsigned grid = (unsigned)std::min<int64_t>((n * c->ngroups + 255) / 256, 152 * 16);
+        build_shadow_kernel<<<grid, 256, 0, st>>>(X, n, c->ngroups, c->ldk, c->B,
+                                                  side == 0 ? c->mt_max : c->nt_max, c->KP,
+                                                  side == 0 ? c->Wsh : c->Hsh);
+        PSGLD_CK(c, cudaGetLastError());
+    }
+    return PSGLD_OK;
+}
+
+static psgld_status launch_two_sided(psgld_ctx *c, int part, cudaStream_t st)
+{
+    two_sided::Params P{};
+    const int64_t I = c->I, J = c->J;
+    two_sided::Side &A = P.side[0], &Bs = P.side[1];
+    A.own_sh = c->Wsh; A.walk_sh = c->Hsh; A.Vt = (const unsigned char *)c->VA; A.G = c->G;
+    A.n_own = I; A.n_walk = J; A.own_tiles = c->mt_max; A.walk_tiles128 = c->nt_max; A.walk_tiles = c->nj_max;
+    Bs.own_sh = c->Hsh; Bs.walk_sh = c->Wsh; Bs.Vt = (const unsigned char *)c->VB; Bs.G = c->G + I * c->ldk;
+    Bs.n_own = J; Bs.n_walk = I; Bs.own_tiles = c->nt_max; Bs.walk_tiles128 = c->mt_max; Bs.walk_tiles = c->ni_max;
+    P.B = c->B;
+    P.part = part;
+    P.KP = c->KP;
+    P.ldk = c->ldk;
+    const int vs = c->v_bf16 ? 2 : 4;
+    P.stages = two_sided_stages(c->KP, vs);
+    P.items_a = c->B * c->mt_max;
+    P.items = P.items_a + c->B * c->nt_max;
+    P.phi_inv = (float)(1.0 / c->phi);
+    P.p = (float)c->p;
+    P.mu_min = (float)c->opt.mu_min;
+    P.p_mode = c->p == 0.0 ? 0 : c->p == 1.0 ? 1 : c->p == 2.0 ? 2 : 3;
+    P.err = c->kflag;
+    int sms = 0;
+    PSGLD_CK(c, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
+    const int grid = std::min(P.items, sms);
+    const size_t smem = two_sided_smem(c->KP, vs, P.stages);
+    if (c->v_bf16)
+        two_sided::chain_kernel<__nv_bfloat16><<<grid, two_sided::kThreads, smem, st>>>(P);
+    else
+        two_sided::chain_kernel<float><<<grid, two_sided::kThreads, smem, st>>>(P);
+    PSGLD_CK(c, cudaGetLastError());
     return PSGLD_OK;
 }
 
 psgld_status launch_dense_grad(psgld_ctx *c, int part, cudaStream_t st)
 {
+    if (c->dense_kind == 2) return launch_two_sided(c, part, st);
     const int kp = dense_kp(c->K);
     DenseFn fn = pick_dense(kp);
-    if (!fn) return fail(c, PSGLD_ERR_ARG, "dense tensor-core path supports K <= 128");
+    if (!fn) return fail(c, PSGLD_ERR_ARG, "single-pass dense kernel supports K <= 128");
     DenseParams P{};
     P.V = c->Vd;
     P.ldv = c->ldv;
@@ -418,7 +979,7 @@ psgld_status launch_dense_grad(psgld_ctx *c, int part, cudaStream_t st)
     P.ldk = c->ldk;
     P.B = c->B;
     P.part = part;
-    P.mtiles = dense_mtiles(c);
+    P.mtiles = c->mtiles;
     P.phi_inv = (float)(1.0 / c->phi);
     P.p = (float)c->p;
     P.mu_min = (float)c->opt.mu_min;

@@ -16,9 +16,13 @@
 //   dense tensor-core path instead of the two layouts:
 //   Vd    : I x J fp32, row-major (ldv = J)
 //   hpart : mtiles x J x ldk fp32, the per-M-tile partial G_H rows when a
-//           block has more than one 128-row tile
+//           block has more than one 128-row tile (single-pass kernel)
+//   two-sided kernel: VA / VB, V in 128 x 64 tiles per block, owned rows =
+//           rows of V (VA) or columns of V (VB); Wsh / Hsh, BF16 shadows of W
+//           and H^T in 128-row MMA tiles per piece (see dev::shadow_store4)
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -67,6 +71,13 @@ struct psgld_ctx {
     int64_t ldv = 0;
     float *hpart = nullptr;          // mtiles x J x ldk partial G_H rows (mtiles > 1)
     int mtiles = 0;                  // 128-row tiles of the largest row piece
+    int dense_kind = 0;              // 1: single-pass kernel, 2: two-sided kernel
+    int KP = 0;                      // K rounded up to 16 (two-sided kernel)
+    int v_bf16 = 0;                  // V tiles in BF16
+    void *VA = nullptr, *VB = nullptr;          // V tiles, both orientations
+    uint16_t *Wsh = nullptr, *Hsh = nullptr;    // BF16 shadows of W, H^T
+    int mt_max = 0, nt_max = 0;      // 128-row tiles per row piece / column piece
+    int ni_max = 0, nj_max = 0;      // 64-row tiles per row piece / column piece
 
     // factors
     float *W[2] = {nullptr, nullptr};
@@ -138,8 +149,13 @@ psgld_status check_kernel_flag(psgld_ctx *c);
 bool dense_supported(int K);
 // 128-row tiles of the largest row piece (CTAs per block).
 int dense_mtiles(const psgld_ctx *c);
-// One-time kernel attributes for this context's K.
+// Chooses the kernel (options dense_path, dense_v_bf16; K; block sizes),
+// sets its attributes and allocates the two-sided kernel's tiles.
 psgld_status prepare_dense(psgld_ctx *c);
+// V tiles of the two-sided kernel from c->Vd (no-op for the single-pass one).
+psgld_status build_dense_tiles(psgld_ctx *c, cudaStream_t st);
+// BF16 shadows of the current factors (two-sided kernel with factors set).
+psgld_status build_dense_shadows(psgld_ctx *c, cudaStream_t st);
 // Enqueue the gradient kernel of part `part`: G rows of W (and of Ht when
 // mtiles == 1) or hpart rows of Ht.
 psgld_status launch_dense_grad(psgld_ctx *c, int part, cudaStream_t st);
@@ -192,6 +208,24 @@ __device__ __forceinline__ float4 box_muller4(uint4 x)
     sincospif(2.0f * u1, &s0, &c0);
     sincospif(2.0f * u3, &s1, &c1);
     return make_float4(r0 * c0, r0 * s0, r1 * c1, r1 * s1);
+}
+
+// BF16 copy of 4 factor entries (row, k0 .. k0+3) into the MMA tiles of the
+// two-sided dense kernel.  Rows of piece r (Definition 1) fill `tiles`
+// 128-row tiles starting at tile r * tiles; inside a tile, entry (rho, k)
+// sits at (rho/8) * KP*8 + (k/8) * 64 + (rho%8) * 8 + k%8 (8 x 8 core
+// matrices, K-adjacent ones 128 bytes apart).
+__device__ __forceinline__ void shadow_store4(uint16_t *sh, int64_t row, int k0, float4 v, int64_t n,
+                                              int B, int tiles, int KP)
+{
+    const int64_t piece = ((row + 1) * B - 1) / n;
+    const int64_t rr = row - (piece * n) / B;
+    const int rho = (int)(rr & 127);
+    const int64_t off = (piece * tiles + (rr >> 7)) * 128 * KP + (int64_t)(rho >> 3) * (KP * 8) +
+                        (k0 >> 3) * 64 + (rho & 7) * 8 + (k0 & 7);
+    __nv_bfloat162 lo = __floats2bfloat162_rn(v.x, v.y), hi = __floats2bfloat162_rn(v.z, v.w);
+    *reinterpret_cast<uint2 *>(sh + off) =
+        make_uint2(*reinterpret_cast<uint32_t *>(&lo), *reinterpret_cast<uint32_t *>(&hi));
 }
 
 }  // namespace dev

@@ -329,8 +329,15 @@ void free_layout(psgld_ctx *c)
     }
     cudaFree(c->Vd);
     cudaFree(c->hpart);
+    cudaFree(c->VA);
+    cudaFree(c->VB);
+    cudaFree(c->Wsh);
+    cudaFree(c->Hsh);
     c->Vd = nullptr;
     c->hpart = nullptr;
+    c->VA = c->VB = nullptr;
+    c->Wsh = c->Hsh = nullptr;
+    c->dense_kind = 0;
     c->dense = false;
     c->ldv = 0;
     c->mtiles = 0;

@@ -84,6 +84,9 @@ struct UpdSide {
     int64_t items;            // n_rows * ngroups (0 when the factor is frozen)
     int64_t gstride;          // dense path: distance between partial gradient arrays
     int gparts;               // dense path: partial gradient arrays to add (0: sparse path)
+    uint16_t *sh;             // two-sided dense kernel: BF16 shadow of X_next (else null)
+    int64_t n_rows;           // I or J
+    int sh_tiles;             // 128-row shadow tiles per piece
     float prior_a, prior_b;   // d log p(x)/dx = prior_a + prior_b * x
     uint32_t mat;             // 0 = W, 1 = H (noise stream)
 };
@@ -98,6 +101,7 @@ struct UpdParams {
     int eps_poly;             // 1: eps_t = (a/t)^b computed on the device
     double eps_a, eps_b;
     int mirror;
+    int B, sh_kp;             // pieces; shadow tile width (two-sided dense kernel)
     uint32_t rk0[10], rk1[10];   // Philox round keys (seed + r * Weyl constants)
 };
 
@@ -452,6 +456,7 @@ __global__ void __launch_bounds__(kThreads) update_kernel(const __grid_constant_
         o.z = k0 + 2 < P.K ? update1(P, Sd, x.z, g.z, z.z, eps, sd) : 0.f;
         o.w = k0 + 3 < P.K ? update1(P, Sd, x.w, g.w, z.w, eps, sd) : 0.f;
         *reinterpret_cast<float4 *>(Sd.X_next + off) = o;
+        if (Sd.sh) dev::shadow_store4(Sd.sh, row, k0, o, Sd.n_rows, P.B, Sd.sh_tiles, P.sh_kp);
     }
 }
 
@@ -568,10 +573,15 @@ psgld_status launch_part_step(psgld_ctx *c, int64_t t, const int64_t *t_dev, int
         Us.Gin = G_rows;
         Us.ptr = dense ? nullptr : L.ptr + (int64_t)part * n_rows;
         Us.gparts = dense ? 1 : 0;
-        if (dense && s == 1 && c->mtiles > 1) {
+        if (dense && c->dense_kind == 1 && s == 1 && c->mtiles > 1) {
             Us.Gin = c->hpart;
             Us.gparts = c->mtiles;
             Us.gstride = c->J * c->ldk;
+        }
+        Us.n_rows = n_rows;
+        if (dense && c->dense_kind == 2) {
+            Us.sh = s == 0 ? c->Wsh : c->Hsh;
+            Us.sh_tiles = s == 0 ? c->mt_max : c->nt_max;
         }
         Us.partial = L.partial;
         Us.base = base;
@@ -615,6 +625,8 @@ psgld_status launch_part_step(psgld_ctx *c, int64_t t, const int64_t *t_dev, int
     UP.S = c->opt.scale_mode == PSGLD_SCALE_B ? (float)B
                                               : (np > 0 ? (float)((double)c->N / (double)np) : 0.f);
     UP.mirror = c->prior.kind == PSGLD_PRIOR_EXPONENTIAL;
+    UP.B = B;
+    UP.sh_kp = c->KP;
     uint32_t k0 = (uint32_t)c->opt.seed, k1 = (uint32_t)(c->opt.seed >> 32);
     for (int r = 0; r < 10; ++r) {   // Weyl key schedule of Philox4x32
         UP.rk0[r] = k0;

@@ -19,6 +19,11 @@ FP32 precision.  What is checked:
   B = 4);
 * graph replay == direct launches bit for bit; log-likelihood and RMSE over
   the dense data match the oracle in FP64; refused inputs.
+
+Every case runs on both kernels: the single-pass one (mu once per entry, G_H
+summed over a block's 128-row tiles by the update) and the two-sided one
+(mu once for the W rows and once for the H columns), the latter also with V
+kept in BF16, where the bound adds the rounding of v.
 """
 import numpy as np
 import pytest
@@ -47,7 +52,26 @@ DENSE = {
     "poisson_K1_B7": (50, 61, 1, 7, 1.0, 1.0, 0, "poisson", 1e-3),
     "poisson_uneven_mtiles_K32": (257, 300, 32, 2, 1.0, 1.0, 0, "poisson", 1e-3),
     "poisson_K64_B1": (200, 150, 64, 1, 1.0, 1.0, 0, "poisson", 1e-3),
+    "gaussnmf_K256_three_tiles": (400, 330, 256, 1, 0.0, 1.0, 0, "gamma", 1e-5),
+    "poisson_K200_B3": (260, 390, 200, 3, 1.0, 1.0, 0, "poisson", 2e-4),
 }
+
+KERNELS = {
+    "single_pass": dict(dense_path=3),
+    "auto": dict(dense_path=1),
+    "two_sided": dict(dense_path=2),
+    "two_sided_bf16v": dict(dense_path=2, dense_v_bf16=1),
+}
+
+
+def _cases():
+    out = []
+    for name in sorted(DENSE):
+        for kern in KERNELS:
+            if kern == "single_pass" and DENSE[name][2] > 128:
+                continue
+            out.append((name, kern))
+    return out
 
 
 def _data(I, J, kind, p, seed):
@@ -60,20 +84,22 @@ def _data(I, J, kind, p, seed):
     return V
 
 
-def _make(name, seed=7, **opts):
+def _make(name, seed=7, kernel="auto", **opts):
     I, J, K, B, p, phi, kind, data, eps = DENSE[name]
+    opts = {**KERNELS[kernel], **opts}
     V = _data(I, J, data, p, seed=I)
     i, j, v = datagen.dense_to_coo(V)
     nonneg = kind == 0
     W0, H0 = datagen.init_factors(I, J, K, seed=3, scale=0.4 if nonneg else 0.3, nonneg=nonneg)
     pr = Pair(I, J, K, B, p, phi, i, j, v, W0, H0, prior_kind=kind, lam=(0.8, 1.2),
-              sig=(0.9, 1.1), seed=seed, eps=eps, V=V, dense_path=1, **opts)
+              sig=(0.9, 1.1), seed=seed, eps=eps, V=V, **opts)
     return pr, V
 
 
-def _drift_bound(V, W, H, t, B, p, phi, S, mu_min=1e-10):
+def _drift_bound(V, W, H, t, B, p, phi, S, mu_min=1e-10, v_bf16=False):
     """First-order BF16 bound on |drift_gpu - drift| for part t (see module
-    docstring); W I x K, H K x J, FP64."""
+    docstring); W I x K, H K x J, FP64.  With v_bf16 the data are rounded to
+    BF16 too: e moves by at most |de/dv| u |v| = max(mu, mu_min)^-p u |v| / phi."""
     I, J = V.shape
     s = (t - 1) % B
     bW = np.zeros_like(W)
@@ -94,7 +120,9 @@ def _drift_bound(V, W, H, t, B, p, phi, S, mu_min=1e-10):
         else:
             e = (v - mu) / phi
             fprime = np.full_like(mu, 1.0 / phi)
-        de = fprime * dmu + 8 * U_FP32 * np.abs(e)
+        de = fprime * dmu + 64 * U_FP32 * np.abs(e)
+        if v_bf16:
+            de = de + (np.maximum(mu - dmu, mu_min) ** -p if p > 0 else 1.0) * U_BF16 * np.abs(v) / phi
         ebf = de + U_BF16 * (np.abs(e) + de)            # error of the BF16 e
         nc, nr = c1 - c0, r1 - r0
         bW[r0:r1] = (ebf @ np.abs(h).T) * (1 + U_BF16) + (U_BF16 + nc * U_FP32) * (np.abs(e) @ np.abs(h).T)
@@ -115,16 +143,17 @@ def _recovered_drift(x_new, x0, z, D_or, eps, mirror):
     return D, mask, rec
 
 
-@pytest.mark.parametrize("name", sorted(DENSE))
-def test_dense_part_step_drift_within_bf16_bound(name):
-    pr, V = _make(name)
+@pytest.mark.parametrize("name,kernel", _cases())
+def test_dense_part_step_drift_within_bf16_bound(name, kernel):
+    pr, V = _make(name, kernel=kernel)
     I, J, K, B, p, phi, kind, data, eps = DENSE[name]
+    v_bf16 = bool(KERNELS[kernel].get("dense_v_bf16", 0))
     mirror = kind == 0
     for t in range(1, B + 2):
         W0, H0 = pr.orc.get_factors()
         D_W, D_H = pr.orc.drift(t)
         S = pr.orc.scale(t)
-        bW, bH = _drift_bound(V, W0, H0, t, B, p, phi, S)
+        bW, bH = _drift_bound(V, W0, H0, t, B, p, phi, S, v_bf16=v_bf16)
         pr.gpu.part_step(t)
         Wg, Hg = pr.gpu_factors()
         zW = oracle.noise_matrix(7, t, 0, I, K)
@@ -134,7 +163,7 @@ def test_dense_part_step_drift_within_bf16_bound(name):
             err = np.abs(Dg - D)
             lim = bnd + rec
             bad = mask & (err > lim)
-            assert not bad.any(), (name, t, what, int(bad.sum()), float(err[bad].max()),
+            assert not bad.any(), (name, kernel, t, what, int(bad.sum()), float(err[bad].max()),
                                    float(lim[bad].min()))
             assert mask.mean() > 0.9
             # and the drift itself is far larger than the bound: the check has teeth
@@ -144,9 +173,10 @@ def test_dense_part_step_drift_within_bf16_bound(name):
         pr.sync_oracle_to_gpu()
 
 
-def test_dense_graph_replay_equals_direct_launches():
-    a, _ = _make("gauss_K50_two_mtiles_three_ntiles", use_graphs=1, burn_in_sweeps=1)
-    b, _ = _make("gauss_K50_two_mtiles_three_ntiles", use_graphs=0, burn_in_sweeps=1)
+@pytest.mark.parametrize("kernel", ["single_pass", "two_sided"])
+def test_dense_graph_replay_equals_direct_launches(kernel):
+    a, _ = _make("gauss_K50_two_mtiles_three_ntiles", kernel=kernel, use_graphs=1, burn_in_sweeps=1)
+    b, _ = _make("gauss_K50_two_mtiles_three_ntiles", kernel=kernel, use_graphs=0, burn_in_sweeps=1)
     for n in (1, 2):
         a.gpu.sweep(n)
         b.gpu.sweep(n)
@@ -158,9 +188,10 @@ def test_dense_graph_replay_equals_direct_launches():
         assert np.array_equal(x, y)
 
 
-def test_dense_is_deterministic():
-    a, _ = _make("poisson_uneven_mtiles_K32")
-    b, _ = _make("poisson_uneven_mtiles_K32")
+@pytest.mark.parametrize("kernel", ["single_pass", "two_sided_bf16v"])
+def test_dense_is_deterministic(kernel):
+    a, _ = _make("poisson_uneven_mtiles_K32", kernel=kernel)
+    b, _ = _make("poisson_uneven_mtiles_K32", kernel=kernel)
     a.gpu.sweep(2)
     b.gpu.sweep(2)
     Wa, Ha = a.gpu_factors()
@@ -169,7 +200,7 @@ def test_dense_is_deterministic():
 
 
 @pytest.mark.parametrize("name", ["poisson_ragged_K8", "gauss_K50_two_mtiles_three_ntiles",
-                                  "cp_K100", "gamma_K13"])
+                                  "cp_K100", "gamma_K13", "poisson_K200_B3"])
 def test_dense_log_lik_and_rmse_match_oracle(name):
     pr, _ = _make(name, burn_in_sweeps=0)
     pr.gpu.sweep(1)
@@ -178,7 +209,8 @@ def test_dense_log_lik_and_rmse_match_oracle(name):
     assert pr.gpu.rmse() == pytest.approx(pr.orc.rmse(False), rel=1e-9)
 
 
-def test_dense_chain_posterior_rmse_within_one_percent_of_oracle():
+@pytest.mark.parametrize("kernel", ["auto", "two_sided_bf16v"])
+def test_dense_chain_posterior_rmse_within_one_percent_of_oracle(kernel):
     """The configured dense Poisson NMF workload (Sec. 4.1 shape): 256 x 256,
     K = 8, B = 4, W*, H* ~ Gamma(1, 1), V ~ Poisson(W* H*), exponential priors
     rate 1, eps = 1e-4; 1000 sweeps, posterior means over the last 500."""
@@ -188,7 +220,7 @@ def test_dense_chain_posterior_rmse_within_one_percent_of_oracle():
     i, j, v = datagen.dense_to_coo(V)
     W0, H0 = datagen.init_factors(I, J, K, seed=0, scale=1.0, nonneg=True)
     pr = Pair(I, J, K, B, 1.0, 1.0, i, j, v, W0, H0, prior_kind=0, seed=11, eps=1e-4, V=V,
-              dense_path=1, burn_in_sweeps=sweeps // 2)
+              burn_in_sweeps=sweeps // 2, **KERNELS[kernel])
     pr.gpu.sweep(sweeps)
     pr.orc.sweep(sweeps)
     r_gpu, r_or = pr.gpu.rmse(True), pr.orc.rmse(True)
@@ -198,11 +230,16 @@ def test_dense_chain_posterior_rmse_within_one_percent_of_oracle():
 def test_dense_refusals():
     I, J = 40, 30
     V = np.ones((I, J), np.float32)
-    c = P.PSGLD(I, J, 129, 2, 1.0, 1.0, dense_path=1)
+    for K, opts in ((257, dict(dense_path=1)), (129, dict(dense_path=3)),
+                    (8, dict(dense_path=3, dense_v_bf16=1))):
+        c = P.PSGLD(I, J, K, 2, 1.0, 1.0, **opts)
+        with pytest.raises(P.PsgldError) as ex:
+            c.set_data_dense(torch.from_numpy(V).cuda())
+        assert ex.value.status == P.PSGLD_ERR_ARG
+        c.close()
     with pytest.raises(P.PsgldError) as ex:
-        c.set_data_dense(torch.from_numpy(V).cuda())
+        P.PSGLD(I, J, 8, 2, 1.0, 1.0, dense_path=4)
     assert ex.value.status == P.PSGLD_ERR_ARG
-    c.close()
     c = P.PSGLD(I, J, 8, 2, 1.0, 1.0, dense_path=1)
     bad = V.copy()
     bad[3, 4] = -1.0                          # negative entry, non-negative model

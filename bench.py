@@ -11,7 +11,8 @@ Zipf(1.1) row and column degrees, K = 50, B = 32 (synthetic data, seeded).
 
 Our arm: value = N_obs * ranks / (max over ranks of the mean sweep time),
 each sweep timed with CUDA events on the launching stream, with L2 flushed
-(256 MB written) before every timed sweep.  Ranks (torchrun, one per GPU) run
+(256 MB written) before every timed sweep.  Per-kernel durations for the
+roofline come from a separate, untimed pass with events around every launch.  Ranks (torchrun, one per GPU) run
 independent replica chains: the sampler needs no collective.  Extra keys:
 roofline of the part-step kernel, the oracle's CPU baseline, an end-to-end
 job through the C ABI from pinned host buffers, SM clocks during the run.
@@ -40,6 +41,7 @@ METRIC = "observed entries/s per PSGLD sweep"
 UNIT = "entries/s"
 L2_FLUSH_BYTES = 256 << 20
 FALLBACK_HBM_GBS = 6800.0
+FALLBACK_BF16_TFLOPS = 1700.0
 
 WORKLOADS = {
     "sparse_gauss_70000x10000_nnz10M_K50_B32": dict(
@@ -53,6 +55,11 @@ WORKLOADS = {
     "dense_poisson_256x256_K8_B4": dict(
         I=256, J=256, nnz=256 * 256, K=8, B=4, p=1.0, phi=1.0, prior="exponential",
         lam=1.0, K_true=8, eps=1e-4, init_scale=1.0, job_sweeps=1000, dense=True),
+    # the standing dense chain: tensor-core block chain, BF16 operands and V
+    "dense_poisson_32768x32768_K256_B16_bf16": dict(
+        I=32768, J=32768, nnz=32768 * 32768, K=256, B=16, p=1.0, phi=1.0, prior="exponential",
+        lam=1.0, K_true=16, eps=2e-5, init_scale=0.25, job_sweeps=200, dense=True,
+        device_gen=True, dense_path=2, dense_v_bf16=1),
 }
 DEFAULT_WORKLOAD = "sparse_gauss_70000x10000_nnz10M_K50_B32"
 
@@ -158,11 +165,16 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 
 def make_inputs(wl: dict, seed: int, device):
-    """Observed entries and initial factors for one chain (torch tensors)."""
+    """Observed entries (i, j, v) -- or, for the tensor-core workloads, the
+    dense V as one device tensor with i = j = None -- and initial factors."""
     import torch
 
     from paper_1506_01418_gb300 import datagen
-    if wl.get("dense"):
+    if wl.get("device_gen"):
+        V = datagen.dense_poisson_device(wl["I"], wl["J"], wl["K_true"], seed, device)
+        i = j = None
+        v = V
+    elif wl.get("dense"):
         V, _, _ = datagen.dense_poisson(wl["I"], wl["J"], wl["K_true"], seed)
         i, j, v = datagen.dense_to_coo(V)
         i, j, v = (torch.from_numpy(x).to(device) for x in (i, j, v))
@@ -176,9 +188,30 @@ def make_inputs(wl: dict, seed: int, device):
     return i, j, v, W0, H0
 
 
+def tensor_path(wl: dict) -> bool:
+    return bool(wl.get("dense_path"))
+
+
+def set_data(chain, wl, i, j, v):
+    if tensor_path(wl):
+        chain.set_data_dense(v)
+    else:
+        chain.set_data_coo(i, j, v)
+
+
+def dense_part_sizes(wl: dict):
+    """Entries of each part of a dense V (every entry observed)."""
+    I, J, B = wl["I"], wl["J"], wl["B"]
+    rows = [(r + 1) * I // B - r * I // B for r in range(B)]
+    cols = [(c + 1) * J // B - c * J // B for c in range(B)]
+    return [sum(rows[b] * cols[(b + s) % B] for b in range(B)) for s in range(B)]
+
+
 def new_chain(wl: dict, seed: int, **opts):
     from paper_1506_01418_gb300 import psgld as P
     kind = P.PSGLD_PRIOR_EXPONENTIAL if wl["prior"] == "exponential" else P.PSGLD_PRIOR_GAUSSIAN
+    if tensor_path(wl):
+        opts = {"dense_path": wl["dense_path"], "dense_v_bf16": wl.get("dense_v_bf16", 0), **opts}
     return P.PSGLD(wl["I"], wl["J"], wl["K"], wl["B"], wl["p"], wl["phi"], prior_kind=kind,
                    lambda_w=wl.get("lam", 1.0), lambda_h=wl.get("lam", 1.0),
                    sigma_w=wl.get("sigma", 1.0), sigma_h=wl.get("sigma", 1.0), seed=seed,
@@ -195,14 +228,22 @@ def part_step_bytes(wl: dict, part_sizes) -> float:
     return 8.0 * mean_n + 4.0 * (I + B) + 8.0 * (I + J) * K
 
 
+def part_step_flops(wl: dict) -> float:
+    """Algorithmic FLOPs of one dense part-step: three contractions of
+    2 (IJ/B) K each (mu = W_b H_b, E H_b^T, E^T W_b over the part's blocks).
+    The two-sided kernel computes mu twice; that is not counted."""
+    return 6.0 * wl["I"] * wl["J"] / wl["B"] * wl["K"]
+
+
 def read_peaks():
+    """(HBM GB/s, BF16 TFLOP/s sustained, source)."""
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
         with open(path) as f:
             d = json.load(f)
-        return float(d["hbm_gbs"]), "measured"
+        return float(d["hbm_gbs"]), float(d["bf16_tflops_sustained"]), "measured"
     except (OSError, KeyError, ValueError):
-        return FALLBACK_HBM_GBS, "fallback"
+        return FALLBACK_HBM_GBS, FALLBACK_BF16_TFLOPS, "fallback"
 
 
 def kernel_traffic(workload: str):
@@ -270,6 +311,32 @@ def cpu_baseline(wl, i, j, v, W0, H0, seed, budget_s: float):
                       f"workload and data, FP64, OpenMP over the blocks of each part"}
 
 
+def cpu_baseline_block(wl, V, W0, H0, seed, budget_s: float):
+    """For dense V too large for the oracle's host arrays: the oracle on one
+    block of the workload (row piece 0 x column piece 0, its V, W and H rows)
+    as a B = 1 problem -- a part-step of it is one block of a part-step of the
+    workload -- timed for about budget_s, entries per second."""
+    import numpy as np
+    B = wl["B"]
+    r1, c1 = wl["I"] // B, wl["J"] // B
+    blk = dict(wl, I=r1, J=c1, B=1)
+    Vb = V[:r1, :c1].float().cpu().numpy()
+    ii, jj = np.meshgrid(np.arange(r1, dtype=np.int32), np.arange(c1, dtype=np.int32), indexing="ij")
+    m = oracle_setup(blk, ii.ravel(), jj.ravel(), Vb.ravel().astype(np.float64),
+                     W0[:r1].astype(np.float64), H0[:, :c1].astype(np.float64), seed)
+    n, ent, secs, t = 0, 0, 0.0, 1
+    while secs < budget_s and n < 100:
+        _, e, dt = oracle_rate(m, blk, t, 1)
+        ent += e
+        secs += dt
+        n += 1
+        t += 1
+    return {"value": ent / secs, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
+            "sample": f"{n} part-steps of one {r1} x {c1} block of the workload (a B = 1 "
+                      f"problem, {ent} entries, {secs:.1f} s), FP64, single block so one core "
+                      f"does the work"}
+
+
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
@@ -292,11 +359,14 @@ def run_ours(args, wl_name, wl):
     seed = 1000 + rank
     i, j, v, W0, H0 = make_inputs(wl, seed, dev)
     torch.cuda.empty_cache()   # drop the generator's temporaries
-    N = int(i.numel())
-    chain = new_chain(wl, seed, use_graphs=1, profile=1)
-    chain.set_data_coo(i, j, v)
+    N = int(v.numel())
+    chain = new_chain(wl, seed, use_graphs=1, profile=0)
+    set_data(chain, wl, i, j, v)
     chain.set_factors(torch.from_numpy(W0).to(dev), torch.from_numpy(H0.T.copy()).to(dev))
-    part_sizes = [P.psgld_part_layout(chain.ctx, s, wl["I"])[0][-1] for s in range(wl["B"])]
+    if wl.get("dense"):
+        part_sizes = dense_part_sizes(wl)
+    else:
+        part_sizes = [P.psgld_part_layout(chain.ctx, s, wl["I"])[0][-1] for s in range(wl["B"])]
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
@@ -310,27 +380,35 @@ def run_ours(args, wl_name, wl):
 
     for _ in range(args.warmup):
         chain.sweep(1)
-        chain.profile_read()
     torch.cuda.synchronize(dev)
     barrier(world)
     torch.cuda.synchronize(dev)
 
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    k_ms, k_n = 0.0, 0
     w0 = time.time()
     for s in range(args.steps):
         flush.zero_()
         starts[s].record(stream)
         chain.sweep(1)
         ends[s].record(stream)
-        ms, n = chain.profile_read()
-        k_ms += ms
-        k_n += n
     torch.cuda.synchronize(dev)
     barrier(world)
     torch.cuda.synchronize(dev)
     w1 = time.time()
+    # Kernel durations come from a separate pass with CUDA events around each
+    # launch (event records inside the sweep graph cost about 12 us per
+    # part-step, so they stay out of the timed sweeps above).
+    chain.set_options(profile=1)
+    g_ms, u_ms, k_n = 0.0, 0.0, 0
+    for s in range(max(3, min(args.steps, 20))):
+        flush.zero_()
+        chain.sweep(1)
+        g, u, n = chain.profile_read_split()
+        if s > 0:   # the first profiled sweep captures a new graph
+            g_ms += g
+            u_ms += u
+            k_n += n
     sweep_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
     ms_local = sum(sweep_ms) / len(sweep_ms)
     ms, value = aggregate(ms_local, N, world, dev)
@@ -339,26 +417,43 @@ def run_ours(args, wl_name, wl):
     clocks = sampler.summary(w0, w1)
     rmse = chain.rmse()
 
-    peak, peak_src = read_peaks()
-    kern_ms = k_ms / max(k_n, 1)
-    bytes_launch = part_step_bytes(wl, part_sizes)
-    achieved = bytes_launch / (kern_ms / 1e3) / 1e9
-    traffic = kernel_traffic(wl_name)
+    hbm_peak, tc_peak, peak_src = read_peaks()
+    grad_ms = g_ms / max(k_n, 1)
+    upd_ms = u_ms / max(k_n, 1)
+    kern_ms = grad_ms + upd_ms
+    if tensor_path(wl):
+        flops = part_step_flops(wl)
+        achieved = flops / (grad_ms / 1e3) / 1e12
+        roofline = {"bound": "tensor", "achieved": achieved, "peak": tc_peak, "unit": "TFLOP/s",
+                    "frac": achieved / tc_peak, "traffic": None,
+                    "kernel": "two_sided::chain_kernel", "kernel_ms": grad_ms,
+                    "algorithmic_flops_per_launch": flops,
+                    "update_kernel_ms": upd_ms, "part_step_ms": kern_ms,
+                    "peak_source": f"{peak_src} sustained cuBLAS BF16 GEMM (kernel timed "
+                                   f"inside a long sweep)"}
+    else:
+        bytes_launch = part_step_bytes(wl, part_sizes)
+        achieved = bytes_launch / (kern_ms / 1e3) / 1e9
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": achieved / hbm_peak, "traffic": kernel_traffic(wl_name),
+                    "kernel": "part_step_kernel", "kernel_ms": kern_ms,
+                    "grad_kernel_ms": grad_ms, "update_kernel_ms": upd_ms,
+                    "algorithmic_bytes_per_launch": bytes_launch,
+                    "peak_source": f"{peak_src} HBM copy bandwidth"}
 
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "vs_baseline": None, "dtype": "bf16" if tensor_path(wl) else "f32", "data": "synthetic",
         "config": {"workload": wl_name, "I": wl["I"], "J": wl["J"], "nnz": N, "K": wl["K"],
                    "B": wl["B"], "tweedie_p": wl["p"], "phi": wl["phi"], "prior": wl["prior"],
                    "eps": wl["eps"], "step": "one sweep = B part-steps + FP64 posterior sums",
+                   "path": ("tensor-core block chain, BF16 operands" +
+                            (" and V" if wl.get("dense_v_bf16") else "") + ", FP32 accumulate"
+                            if tensor_path(wl) else "FP32 gather path"),
                    "l2": "256 MB buffer written before every timed sweep",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic,
-                     "kernel": "part_step_kernel", "kernel_ms": kern_ms,
-                     "algorithmic_bytes_per_launch": bytes_launch,
-                     "peak_source": f"{peak_src} HBM copy bandwidth"},
+        "roofline": roofline,
         # per sweep: B x (gradient + update) + 2 accumulate + advance t + set t
         "gpu_launches": args.steps * (2 * wl["B"] + 4),
         "clocks": clocks,
@@ -369,10 +464,13 @@ def run_ours(args, wl_name, wl):
         result["e2e"] = e2e_job(wl, seed, dev, i, j, v, W0, H0)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import numpy as np
-        hi, hj, hv = (x.cpu().numpy() for x in (i, j, v))
-        result["cpu_baseline"] = cpu_baseline(wl, hi, hj, hv.astype(np.float64),
-                                              W0.astype(np.float64), H0.astype(np.float64),
-                                              seed, args.cpu_budget)
+        if i is None:
+            result["cpu_baseline"] = cpu_baseline_block(wl, v, W0, H0, seed, args.cpu_budget)
+        else:
+            hi, hj, hv = (x.cpu().numpy() for x in (i, j, v))
+            result["cpu_baseline"] = cpu_baseline(wl, hi, hj, hv.astype(np.float64),
+                                                  W0.astype(np.float64), H0.astype(np.float64),
+                                                  seed, args.cpu_budget)
     chain.close()
     if rank == 0:
         print(json.dumps(result), flush=True)
@@ -387,9 +485,13 @@ def e2e_job(wl, seed, dev, i, j, v, W0, H0):
     and the log-likelihood out.  value = entries x sweeps / wall time."""
     import numpy as np
     import torch
-    hi = i.cpu().pin_memory()
-    hj = j.cpu().pin_memory()
-    hv = v.cpu().pin_memory()
+    dense_in = i is None
+    if dense_in:
+        hv = v.cpu().pin_memory()
+    else:
+        hi = i.cpu().pin_memory()
+        hj = j.cpu().pin_memory()
+        hv = v.cpu().pin_memory()
     hW = torch.from_numpy(W0).pin_memory()
     hHt = torch.from_numpy(H0.T.copy()).pin_memory()
     S = wl["job_sweeps"]
@@ -398,7 +500,10 @@ def e2e_job(wl, seed, dev, i, j, v, W0, H0):
     chain = new_chain(wl, seed, use_graphs=1, burn_in_sweeps=S // 2)
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
-    chain.set_data_coo(hi, hj, hv)
+    if dense_in:
+        chain.set_data_dense(hv)
+    else:
+        chain.set_data_coo(hi, hj, hv)
     chain.set_factors(hW, hHt)
     chain.sweep(S)
     from paper_1506_01418_gb300 import psgld as P
@@ -407,13 +512,14 @@ def e2e_job(wl, seed, dev, i, j, v, W0, H0):
     torch.cuda.synchronize(dev)
     dt = time.perf_counter() - t0
     chain.close()
-    N = int(i.numel())
-    h2d = 12 * N + 4 * (I + J) * K
+    N = int(v.numel())
+    h2d = (4 if dense_in else 12) * N + 4 * (I + J) * K
     d2h = 8 * 4 * (I + J) * K + 8
     return {"value": N * S / dt, "unit": UNIT, "h2d_bytes_per_step": h2d / S,
             "d2h_bytes_per_step": d2h / S, "job_sweeps": S, "job_s": dt,
-            "log_lik": ll, "api": "psgld_set_data_coo/set_factors (pinned host) + psgld_sweep "
-                                 "+ psgld_posterior_mean + psgld_log_lik"}
+            "log_lik": ll,
+            "api": ("psgld_set_data_dense" if dense_in else "psgld_set_data_coo") +
+                   "/set_factors (pinned host) + psgld_sweep + psgld_posterior_mean + psgld_log_lik"}
 
 
 # ---------------------------------------------------------------------------
@@ -432,10 +538,25 @@ def run_reference(args, wl_name, wl):
     seed = 1000
     dev = torch.device("cuda", 0) if torch.cuda.is_available() else torch.device("cpu")
     i, j, v, W0, H0 = make_inputs(wl, seed, dev)
-    hi, hj, hv = (x.cpu().numpy() for x in (i, j, v))
-    N = len(hi)
-    m = oracle_setup(wl, hi, hj, hv.astype(np.float64), W0.astype(np.float64),
+    N = int(v.numel())
+    run_wl = wl
+    what = "the workload"
+    if i is None:
+        # dense V beyond the oracle's host arrays: one block as a B = 1 problem
+        B = wl["B"]
+        r1, c1 = wl["I"] // B, wl["J"] // B
+        run_wl = dict(wl, I=r1, J=c1, B=1)
+        Vb = v[:r1, :c1].float().cpu().numpy()
+        hi, hj = (x.ravel() for x in np.meshgrid(np.arange(r1, dtype=np.int32),
+                                                 np.arange(c1, dtype=np.int32), indexing="ij"))
+        hv = Vb.ravel()
+        W0, H0 = W0[:r1], H0[:, :c1]
+        what = f"one {r1} x {c1} block of the workload as a B = 1 problem"
+    else:
+        hi, hj, hv = (x.cpu().numpy() for x in (i, j, v))
+    m = oracle_setup(run_wl, hi, hj, hv.astype(np.float64), W0.astype(np.float64),
                      H0.astype(np.float64), seed)
+    wl = run_wl
     _, _, dt1 = oracle_rate(m, wl, 1, 1)
     budget = args.reference_budget / max(1, args.steps + args.warmup)
     per_step = max(1, min(wl["B"], int(budget / max(dt1, 1e-6))))
@@ -451,16 +572,17 @@ def run_reference(args, wl_name, wl):
         t += per_step
     rate = ent / secs
     ms = secs / args.steps * 1e3 * (N / max(ent / args.steps, 1))   # per full sweep
-    sample = (f"each step {per_step} part-steps of the workload "
+    sample = (f"each step {per_step} part-steps of {what} "
               f"({ent // args.steps} observed entries), FP64 oracle, OpenMP over blocks")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": wl_name, "I": wl["I"], "J": wl["J"], "nnz": N, "K": wl["K"],
-                   "B": wl["B"], "tweedie_p": wl["p"], "phi": wl["phi"], "prior": wl["prior"],
-                   "eps": wl["eps"], "step": "bounded sample of part-steps, rate per entry"},
+        "config": {"workload": wl_name, "I": WORKLOADS[wl_name]["I"], "J": WORKLOADS[wl_name]["J"],
+                   "nnz": N, "K": wl["K"], "B": WORKLOADS[wl_name]["B"], "tweedie_p": wl["p"],
+                   "phi": wl["phi"], "prior": wl["prior"], "eps": wl["eps"],
+                   "step": "bounded sample of part-steps, rate per entry"},
         "cpu_baseline": {"value": rate, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},

@@ -201,6 +201,11 @@ PSGLD_API psgld_status psgld_part_layout(psgld_ctx *ctx, int32_t s, int32_t *row
  * the context's last stream. */
 PSGLD_API psgld_status psgld_profile_read(psgld_ctx *ctx, double *total_ms_host,
                                           int64_t *launches_host);
+/* The same split at the end of the gradient kernel (the sparse gather kernel
+ * or the tensor-core chain): *grad_ms_host and *update_ms_host receive the
+ * summed durations of the gradient and of the update launches. */
+PSGLD_API psgld_status psgld_profile_read_split(psgld_ctx *ctx, double *grad_ms_host,
+                                                double *update_ms_host, int64_t *launches_host);
 
 /* Last completed iteration t (0 before the first). */
 PSGLD_API int64_t psgld_iterations_done(const psgld_ctx *ctx);

@@ -242,8 +242,10 @@ psgld_status psgld_create(int64_t I, int64_t J, int32_t K, int32_t B, double twe
 static void destroy_events(psgld_ctx *c)
 {
     for (auto e : c->ev_start) cudaEventDestroy(e);
+    for (auto e : c->ev_mid) cudaEventDestroy(e);
     for (auto e : c->ev_end) cudaEventDestroy(e);
     c->ev_start.clear();
+    c->ev_mid.clear();
     c->ev_end.clear();
     c->ev_pending.clear();
 }
@@ -268,37 +270,53 @@ psgld_status psgld_set_options(psgld_ctx *c, const psgld_options *o)
     destroy_events(c);
     if (o->profile) {
         c->ev_start.resize(c->B);
+        c->ev_mid.resize(c->B);
         c->ev_end.resize(c->B);
         c->ev_pending.assign(c->B, 0);
         for (int b = 0; b < c->B; ++b) {
             PSGLD_CK(c, cudaEventCreate(&c->ev_start[b]));
+            PSGLD_CK(c, cudaEventCreate(&c->ev_mid[b]));
             PSGLD_CK(c, cudaEventCreate(&c->ev_end[b]));
         }
     }
     return PSGLD_OK;
 }
 
-psgld_status psgld_profile_read(psgld_ctx *c, double *total_ms, int64_t *launches)
+psgld_status psgld_profile_read_split(psgld_ctx *c, double *grad_ms, double *update_ms,
+                                      int64_t *launches)
 {
-    if (!c || !total_ms || !launches) return PSGLD_ERR_ARG;
+    if (!c || !grad_ms || !update_ms || !launches) return PSGLD_ERR_ARG;
     if (!c->opt.profile) return fail(c, PSGLD_ERR_STATE, "profiling is off");
     PSGLD_CK(c, cudaStreamSynchronize(c->last_stream));
     {
         psgld_status fs = check_kernel_flag(c);
         if (fs != PSGLD_OK) return fs;
     }
-    double ms = 0.0;
+    double g = 0.0, u = 0.0;
     int64_t n = 0;
     for (int b = 0; b < c->B; ++b) {
         if (!c->ev_pending[b]) continue;
-        float e = 0.f;
-        PSGLD_CK(c, cudaEventElapsedTime(&e, c->ev_start[b], c->ev_end[b]));
-        ms += e;
+        float e1 = 0.f, e2 = 0.f;
+        PSGLD_CK(c, cudaEventElapsedTime(&e1, c->ev_start[b], c->ev_mid[b]));
+        PSGLD_CK(c, cudaEventElapsedTime(&e2, c->ev_mid[b], c->ev_end[b]));
+        g += e1;
+        u += e2;
         n += 1;
         c->ev_pending[b] = 0;
     }
-    *total_ms = ms;
+    *grad_ms = g;
+    *update_ms = u;
     *launches = n;
+    return PSGLD_OK;
+}
+
+psgld_status psgld_profile_read(psgld_ctx *c, double *total_ms, int64_t *launches)
+{
+    if (!c || !total_ms || !launches) return PSGLD_ERR_ARG;
+    double g = 0.0, u = 0.0;
+    const psgld_status s = psgld_profile_read_split(c, &g, &u, launches);
+    if (s != PSGLD_OK) return s;
+    *total_ms = g + u;
     return PSGLD_OK;
 }
 

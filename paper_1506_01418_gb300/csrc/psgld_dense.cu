@@ -42,7 +42,7 @@ namespace {
 constexpr int kDenseThreads = 128;
 constexpr int kTile = 128;   // rows of an M-tile = columns of an n-tile
 constexpr uint32_t kTmemCols = 256;
-constexpr uint32_t kDenseWaitLimit = 1u << 24;
+constexpr uint32_t kDenseWaitLimit = 1u << 30;
 constexpr long long kDenseWaitCycles = 1ll << 31;
 
 struct DenseParams {
@@ -130,24 +130,29 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// One poll of phase `parity` (the instruction may block for a short,
+// hardware-chosen time, and returns as soon as the phase completes).
 __device__ __forceinline__ bool bar_try_wait(uint64_t *bar, uint32_t parity)
 {
     uint32_t ok;
     asm volatile("{\n\t.reg .pred p;\n\t"
-                 "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+                 "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
                  "selp.u32 %0, 1, 0, p;\n\t}"
-                 : "=r"(ok) : "r"(saddr(bar)), "r"(parity), "r"(2000u) : "memory");
+                 : "=r"(ok) : "r"(saddr(bar)), "r"(parity) : "memory");
     return ok != 0;
 }
 
-// bounded wait for phase `parity`; false if it ran out
+// bounded wait for phase `parity`; false if it ran out (polls, or about one
+// second of SM clock)
 __device__ __forceinline__ bool bar_wait(uint64_t *bar, uint32_t parity)
 {
-    bool done = false;
+    if (bar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
-    for (uint32_t it = 0; it < kDenseWaitLimit && !done && clock64() - t0 < kDenseWaitCycles; ++it)
-        done = bar_try_wait(bar, parity);
-    return done;
+    for (uint32_t it = 0; it < kDenseWaitLimit; ++it) {
+        if (bar_try_wait(bar, parity)) return true;
+        if (clock64() - t0 > kDenseWaitCycles) break;
+    }
+    return false;
 }
 
 __device__ __forceinline__ float tweedie(const DenseParams &P, float v, float mu)
@@ -394,7 +399,7 @@ __global__ void __launch_bounds__(kDenseThreads, 1) dense_grad_kernel(const __gr
 // one 16-byte chunk per owned row, so a warp reads 512 contiguous bytes).
 // Every tile is one bulk copy.
 //
-// One persistent CTA per SM, 6 warps:
+// One persistent CTA per SM, 10 warps:
 //   warp 0 (one thread)  producer: the owned tile once per item, then per
 //                         walked tile the other factor's 64-row tile and the
 //                         V tile into a ring of stages (bulk copies);
@@ -402,20 +407,24 @@ __global__ void __launch_bounds__(kDenseThreads, 1) dense_grad_kernel(const __gr
 //                         TMEM buffers, then GEMM2 G += E_(j-1) . B_(j-1)
 //                         (B read MN-major), so GEMM1 of tile j overlaps the
 //                         epilogue of tile j-1; completions via tcgen05.commit;
-//   warps 2-5            epilogue: TMEM mu + V (shared memory) -> E (BF16,
-//                         shared memory, two buffers), and after an item's
-//                         last tile the G rows from TMEM to HBM.
+//   warps 2-9            epilogue, two warps per TMEM lane quarter (32 of the
+//                         tile's 64 columns each): TMEM mu + V (shared
+//                         memory) -> E (BF16, shared memory, two buffers),
+//                         and after an item's last tile the G rows from TMEM
+//                         to HBM.  The Tweedie power is a template parameter
+//                         (p = 0, 1, 2, other), so the epilogue is straight-line.
 // TMEM: mu buffers at columns 0 and 64, G at 128 .. 128 + KP.
 // Padding rows and columns of every tile are zero, so mu and E are zero
 // there and need no masks.
 namespace two_sided {
 
-constexpr int kThreads = 192;
+constexpr int kThreads = 320;     // warp 0 producer, warp 1 MMA, warps 2..9 epilogue
 constexpr int kOwn = 128;          // owned rows per item (TMEM lanes)
 constexpr int kBN = 64;            // walked rows per tile
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kGCol = 128;
 constexpr int kMaxStages = 4;
+constexpr int kEpiWarps = 8;       // two per TMEM lane quarter, 32 walked columns each
 
 struct Side {
     const uint16_t *own_sh;     // BF16 shadow tiles of the owned factor
@@ -430,14 +439,15 @@ struct Side {
 
 struct Params {
     Side side[2];
-    int B, part, KP, ldk, stages, items_a, items;
+    int B, part, KP, ldk, stages, vstages, items_a, items;
     float phi_inv, p, mu_min;
     int p_mode;
     int *err;
 };
 
 struct Bars {
-    uint64_t full[kMaxStages], empty[kMaxStages];
+    uint64_t full[kMaxStages], empty[kMaxStages];       // walked factor tiles
+    uint64_t vfull[kMaxStages], vempty[kMaxStages];     // V tiles
     uint64_t mu_full[2], mu_empty[2], e_full[2], e_empty[2];
     uint64_t a_full, a_empty, g_full, g_empty;
     uint32_t tmem;
@@ -513,7 +523,21 @@ __device__ __forceinline__ bool decode(const Params &P, int it, Item &x)
     return left > 0;
 }
 
-template <typename VT>
+template <int PM>
+__device__ __forceinline__ float tweedie_pm(float p, float phi_inv, float mu_min, float v, float mu)
+{
+    const float d = (v - mu) * phi_inv;
+    if constexpr (PM == 0) {
+        return d;
+    } else {
+        const float mc = fmaxf(mu, mu_min);
+        if constexpr (PM == 1) return __fdividef(d, mc);
+        if constexpr (PM == 2) return __fdividef(d, mc * mc);
+        if constexpr (PM == 3) return d * exp2f(-p * __log2f(mc));
+    }
+}
+
+template <typename VT, int PM>
 __global__ void __launch_bounds__(kThreads, 1) chain_kernel(const __grid_constant__ Params P)
 {
     extern __shared__ __align__(1024) unsigned char sm[];
@@ -524,20 +548,21 @@ __global__ void __launch_bounds__(kThreads, 1) chain_kernel(const __grid_constan
     constexpr uint32_t e_bytes = kOwn * kBN * 2;
     unsigned char *sA = sm;
     unsigned char *sE = sA + a_bytes;                           // 2 x e_bytes
-    unsigned char *sStage = sE + 2 * e_bytes;                   // stages x (b + v)
-    const uint32_t stage_bytes = b_bytes + v_bytes;
-    Bars *S = reinterpret_cast<Bars *>(sStage + (size_t)P.stages * stage_bytes);
+    unsigned char *sB = sE + 2 * e_bytes;                       // NS x b_bytes
+    unsigned char *sV = sB + (size_t)P.stages * b_bytes;        // NV x v_bytes
+    Bars *S = reinterpret_cast<Bars *>(sV + (size_t)P.vstages * v_bytes);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int NS = P.stages;
+    const int NS = P.stages, NV = P.vstages;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < NS; ++s) { bar_init(&S->full[s], 1); bar_init(&S->empty[s], 1); }
+        for (int s = 0; s < NV; ++s) { bar_init(&S->vfull[s], 1); bar_init(&S->vempty[s], kEpiWarps); }
         for (int b = 0; b < 2; ++b) {
-            bar_init(&S->mu_full[b], 1); bar_init(&S->mu_empty[b], 4);
-            bar_init(&S->e_full[b], 4); bar_init(&S->e_empty[b], 1);
+            bar_init(&S->mu_full[b], 1); bar_init(&S->mu_empty[b], kEpiWarps);
+            bar_init(&S->e_full[b], kEpiWarps); bar_init(&S->e_empty[b], 1);
         }
         bar_init(&S->a_full, 1); bar_init(&S->a_empty, 1);
-        bar_init(&S->g_full, 1); bar_init(&S->g_empty, 4);
+        bar_init(&S->g_full, 1); bar_init(&S->g_empty, kEpiWarps);
         S->abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -567,15 +592,16 @@ __global__ void __launch_bounds__(kThreads, 1) chain_kernel(const __grid_constan
                     Sd.Vt + ((((int64_t)x.own_piece * P.B + x.walk_piece) * Sd.own_tiles + x.ot) *
                              Sd.walk_tiles) * (int64_t)v_bytes;
                 for (int j = 0; j < x.nj; ++j, ++tc) {
-                    const int st = (int)(tc % NS);
+                    const int st = (int)(tc % NS), sv = (int)(tc % NV);
                     if (!wait1(S, &S->empty[st], ((tc / NS) & 1) ^ 1)) goto done0;
-                    unsigned char *dst = sStage + (size_t)st * stage_bytes;
-                    bar_expect_tx(&S->full[st], stage_bytes);
-                    bulk_g2s(dst,
+                    bar_expect_tx(&S->full[st], b_bytes);
+                    bulk_g2s(sB + (size_t)st * b_bytes,
                              Sd.walk_sh + ((int64_t)x.walk_piece * Sd.walk_tiles128 + (j >> 1)) * kOwn * KP +
                                  (int64_t)(j & 1) * kBN * KP,
                              b_bytes, &S->full[st]);
-                    bulk_g2s(dst + b_bytes, vbase + (int64_t)j * v_bytes, v_bytes, &S->full[st]);
+                    if (!wait1(S, &S->vempty[sv], ((tc / NV) & 1) ^ 1)) goto done0;
+                    bar_expect_tx(&S->vfull[sv], v_bytes);
+                    bulk_g2s(sV + (size_t)sv * v_bytes, vbase + (int64_t)j * v_bytes, v_bytes, &S->vfull[sv]);
                 }
                 ++ic;
             }
@@ -603,7 +629,7 @@ __global__ void __launch_bounds__(kThreads, 1) chain_kernel(const __grid_constan
                         const int b = j & 1;
                         if (!wait1(S, &S->mu_empty[b], (mu_use[b] & 1) ^ 1)) goto done1;
                         fence_after();
-                        const uint64_t dB = sdesc(saddr(sStage + (size_t)st * stage_bytes), 128, KP * 16);
+                        const uint64_t dB = sdesc(saddr(sB + (size_t)st * b_bytes), 128, KP * 16);
                         for (int ks = 0; ks < KP / 16; ++ks)
                             mma_bf16(tmem + (uint32_t)(b * kBN), dA + (uint64_t)(ks * 16),
                                      dB + (uint64_t)(ks * 16), id1, ks > 0);
@@ -618,7 +644,7 @@ __global__ void __launch_bounds__(kThreads, 1) chain_kernel(const __grid_constan
                         if (jj == 0 && !wait1(S, &S->g_empty, (ic & 1) ^ 1)) goto done1;
                         fence_after();
                         const uint64_t dE = sdesc(saddr(sE + b * e_bytes), 128, kBN * 16);
-                        const uint64_t dBt = sdesc(saddr(sStage + (size_t)prev_st * stage_bytes), KP * 16, 128);
+                        const uint64_t dBt = sdesc(saddr(sB + (size_t)prev_st * b_bytes), KP * 16, 128);
                         for (int ks = 0; ks < kBN / 16; ++ks)
                             mma_bf16(tmem + kGCol, dE + (uint64_t)(ks * 16), dBt + (uint64_t)(ks * 2 * KP),
                                      id2, (jj > 0 || ks > 0));
@@ -636,9 +662,11 @@ __global__ void __launch_bounds__(kThreads, 1) chain_kernel(const __grid_constan
     done1:
         __syncwarp();
     } else {
-        // ---------------- epilogue (warps 2..5; TMEM lane quarter = warp % 4)
-        const int q = warp & 3;
+        // ---------------- epilogue (warps 2..9): TMEM lane quarter warp % 4,
+        // walked columns 32 h .. 32 h + 31 of each tile, h = (warp - 2) / 4
+        const int q = warp & 3, hc = (warp - 2) >> 2;
         const int rho = 32 * q + lane;                      // owned row in the tile
+        const int c = 32 * hc;
         const uint32_t lane_base = (uint32_t)(32 * q) << 16;
         uint32_t tc = 0, ic = 0, mu_use[2] = {0, 0}, e_use[2] = {0, 0};
         for (int it = blockIdx.x; it < P.items; it += gridDim.x) {
@@ -646,74 +674,75 @@ __global__ void __launch_bounds__(kThreads, 1) chain_kernel(const __grid_constan
             if (!decode(P, it, x)) continue;
             const Side &Sd = P.side[x.side];
             for (int j = 0; j < x.nj; ++j, ++tc) {
-                const int b = j & 1, st = (int)(tc % NS);
-                if (!wait32(S, &S->full[st], (tc / NS) & 1)) goto done2;
+                const int b = j & 1, sv = (int)(tc % NV);
+                if (!wait32(S, &S->vfull[sv], (tc / NV) & 1)) goto done2;
                 if (!wait32(S, &S->mu_full[b], mu_use[b] & 1)) goto done2;
                 if (!wait32(S, &S->e_empty[b], (e_use[b] & 1) ^ 1)) goto done2;
                 fence_after();
-                const unsigned char *vt = sStage + (size_t)st * stage_bytes + b_bytes;
+                const unsigned char *vt = sV + (size_t)sv * v_bytes;
                 unsigned char *eb = sE + b * e_bytes;
+                float mu[32];
+                tmem_ld32(tmem + lane_base + (uint32_t)(b * kBN + c), mu);
+                float v[32];
+                if constexpr (sizeof(VT) == 4) {
 #pragma unroll
-                for (int c = 0; c < kBN; c += 32) {
-                    float mu[32];
-                    tmem_ld32(tmem + lane_base + (uint32_t)(b * kBN + c), mu);
-                    float v[32];
-                    if constexpr (sizeof(VT) == 4) {
+                    for (int i = 0; i < 8; ++i) {
+                        const float4 w = *reinterpret_cast<const float4 *>(
+                            vt + ((size_t)((c >> 2) + i) * kOwn + rho) * 16);
+                        v[4 * i] = w.x; v[4 * i + 1] = w.y; v[4 * i + 2] = w.z; v[4 * i + 3] = w.w;
+                    }
+                } else {
 #pragma unroll
-                        for (int i = 0; i < 8; ++i) {
-                            const float4 w = *reinterpret_cast<const float4 *>(
-                                vt + ((size_t)((c >> 2) + i) * kOwn + rho) * 16);
-                            v[4 * i] = w.x; v[4 * i + 1] = w.y; v[4 * i + 2] = w.z; v[4 * i + 3] = w.w;
-                        }
-                    } else {
+                    for (int i = 0; i < 4; ++i) {
+                        const uint4 w = *reinterpret_cast<const uint4 *>(
+                            vt + ((size_t)((c >> 3) + i) * kOwn + rho) * 16);
+                        const uint32_t u[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
-                        for (int i = 0; i < 4; ++i) {
-                            const uint4 w = *reinterpret_cast<const uint4 *>(
-                                vt + ((size_t)((c >> 3) + i) * kOwn + rho) * 16);
-                            const uint32_t u[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-                            for (int h = 0; h < 4; ++h) {
-                                v[8 * i + 2 * h] = __uint_as_float(u[h] << 16);
-                                v[8 * i + 2 * h + 1] = __uint_as_float(u[h] & 0xffff0000u);
-                            }
+                        for (int h = 0; h < 4; ++h) {
+                            v[8 * i + 2 * h] = __uint_as_float(u[h] << 16);
+                            v[8 * i + 2 * h + 1] = __uint_as_float(u[h] & 0xffff0000u);
                         }
                     }
-                    uint32_t pk[16];
-#pragma unroll
-                    for (int h = 0; h < 16; ++h) {
-                        const float e0 = tweedie_fast(P.p_mode, P.p, P.phi_inv, P.mu_min, v[2 * h], mu[2 * h]);
-                        const float e1 = tweedie_fast(P.p_mode, P.p, P.phi_inv, P.mu_min, v[2 * h + 1], mu[2 * h + 1]);
-                        __nv_bfloat162 t2 = __floats2bfloat162_rn(e0, e1);
-                        pk[h] = *reinterpret_cast<uint32_t *>(&t2);
-                    }
-                    // E (owned row rho, walked columns c..c+31) in K-major core matrices
-#pragma unroll
-                    for (int g = 0; g < 4; ++g)
-                        *reinterpret_cast<uint4 *>(eb + (rho >> 3) * (kBN * 16) + ((c >> 3) + g) * 128 +
-                                                   (rho & 7) * 16) =
-                            make_uint4(pk[4 * g], pk[4 * g + 1], pk[4 * g + 2], pk[4 * g + 3]);
                 }
+                uint32_t pk[16];
+#pragma unroll
+                for (int h = 0; h < 16; ++h) {
+                    const float e0 = tweedie_pm<PM>(P.p, P.phi_inv, P.mu_min, v[2 * h], mu[2 * h]);
+                    const float e1 = tweedie_pm<PM>(P.p, P.phi_inv, P.mu_min, v[2 * h + 1], mu[2 * h + 1]);
+                    __nv_bfloat162 t2 = __floats2bfloat162_rn(e0, e1);
+                    pk[h] = *reinterpret_cast<uint32_t *>(&t2);
+                }
+                // E (owned row rho, walked columns c..c+31) in K-major core matrices
+#pragma unroll
+                for (int g = 0; g < 4; ++g)
+                    *reinterpret_cast<uint4 *>(eb + (rho >> 3) * (kBN * 16) + ((c >> 3) + g) * 128 +
+                                               (rho & 7) * 16) =
+                        make_uint4(pk[4 * g], pk[4 * g + 1], pk[4 * g + 2], pk[4 * g + 3]);
                 fence_async_smem();
                 fence_before();
                 __syncwarp();
-                if (lane == 0) { bar_arrive(&S->mu_empty[b]); bar_arrive(&S->e_full[b]); }
+                if (lane == 0) {
+                    bar_arrive(&S->vempty[sv]);
+                    bar_arrive(&S->mu_empty[b]);
+                    bar_arrive(&S->e_full[b]);
+                }
                 ++mu_use[b];
                 ++e_use[b];
             }
-            // the item's G rows
+            // the item's G rows: this warp's lane quarter, every other 32-column chunk
             if (!wait32(S, &S->g_full, ic & 1)) goto done2;
             fence_after();
             {
                 const bool rv = rho < x.own_rows_in_tile;
                 float *dst = Sd.G + (x.own_start + (int64_t)x.ot * kOwn + rho) * P.ldk;
-                for (int c = 0; c < KP; c += 32) {
+                for (int cc = 32 * hc; cc < KP; cc += 64) {
                     float g[32];
-                    tmem_ld32(tmem + lane_base + kGCol + (uint32_t)c, g);
+                    tmem_ld32(tmem + lane_base + kGCol + (uint32_t)cc, g);
                     if (rv) {
 #pragma unroll
                         for (int h = 0; h < 32; h += 4)
-                            if (c + h < P.ldk)
-                                *reinterpret_cast<float4 *>(dst + c + h) = make_float4(g[h], g[h + 1], g[h + 2], g[h + 3]);
+                            if (cc + h < P.ldk)
+                                *reinterpret_cast<float4 *>(dst + cc + h) = make_float4(g[h], g[h + 1], g[h + 2], g[h + 3]);
                     }
                 }
             }
@@ -820,25 +849,41 @@ __global__ void build_shadow_kernel(const float *__restrict__ X, int64_t n, int 
 
 using ChainFn = void (*)(two_sided::Params);
 
-size_t two_sided_bytes(int KP, int vsize, int stages)
+ChainFn pick_chain(bool vb, int pm)
+{
+    static const ChainFn f[2][4] = {
+        {two_sided::chain_kernel<float, 0>, two_sided::chain_kernel<float, 1>,
+         two_sided::chain_kernel<float, 2>, two_sided::chain_kernel<float, 3>},
+        {two_sided::chain_kernel<__nv_bfloat16, 0>, two_sided::chain_kernel<__nv_bfloat16, 1>,
+         two_sided::chain_kernel<__nv_bfloat16, 2>, two_sided::chain_kernel<__nv_bfloat16, 3>}};
+    return f[vb ? 1 : 0][pm];
+}
+
+size_t two_sided_bytes(int KP, int vsize, int stages, int vstages)
 {
     return (size_t)two_sided::kOwn * KP * 2 + 2 * (size_t)two_sided::kOwn * two_sided::kBN * 2 +
-           (size_t)stages * ((size_t)two_sided::kBN * KP * 2 + (size_t)two_sided::kOwn * two_sided::kBN * vsize) +
-           sizeof(two_sided::Bars) + 16;
+           (size_t)stages * two_sided::kBN * KP * 2 +
+           (size_t)vstages * two_sided::kOwn * two_sided::kBN * vsize + sizeof(two_sided::Bars) + 16;
 }
 
 // At least half of an SM's shared memory, so that one CTA (and one 512-column
 // TMEM allocation) runs per SM.
-size_t two_sided_smem(int KP, int vsize, int stages)
+size_t two_sided_smem(int KP, int vsize, int stages, int vstages)
 {
-    return std::max<size_t>(two_sided_bytes(KP, vsize, stages), 120 * 1024);
+    return std::max<size_t>(two_sided_bytes(KP, vsize, stages, vstages), 120 * 1024);
 }
 
-int two_sided_stages(int KP, int vsize)
+// Ring depths: two V slots (they free as soon as the epilogue has read
+// them), then as many walked-factor slots as fit (2 .. 4), then a third V
+// slot if it still fits.
+void two_sided_stages(int KP, int vsize, int *stages, int *vstages)
 {
     int s = two_sided::kMaxStages;
-    while (s > 2 && two_sided_bytes(KP, vsize, s) > 232448) --s;
-    return s;
+    while (s > 2 && two_sided_bytes(KP, vsize, s, 2) > 232448) --s;
+    int v = 2;
+    if (two_sided_bytes(KP, vsize, s, 3) <= 232448) v = 3;
+    *stages = s;
+    *vstages = v;
 }
 
 }  // namespace
@@ -868,10 +913,11 @@ psgld_status prepare_dense(psgld_ctx *c)
     c->ni_max = cdiv(maxI, 64);
     c->nj_max = cdiv(maxJ, 64);
     const int vs = vb ? 2 : 4;
-    const int stages = two_sided_stages(c->KP, vs);
-    ChainFn fn = vb ? two_sided::chain_kernel<__nv_bfloat16> : two_sided::chain_kernel<float>;
-    PSGLD_CK(c, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)two_sided_smem(c->KP, vs, stages)));
+    int stages = 0, vstages = 0;
+    two_sided_stages(c->KP, vs, &stages, &vstages);
+    for (int pm = 0; pm < 4; ++pm)
+        PSGLD_CK(c, cudaFuncSetAttribute(pick_chain(vb, pm), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)two_sided_smem(c->KP, vs, stages, vstages)));
     const int64_t B = c->B;
     const int64_t nA = B * B * c->mt_max * c->nj_max * 8192, nB = B * B * c->nt_max * c->ni_max * 8192;
     const int64_t nW = B * c->mt_max * 128 * c->KP, nH = B * c->nt_max * 128 * c->KP;
@@ -940,7 +986,7 @@ static psgld_status launch_two_sided(psgld_ctx *c, int part, cudaStream_t st)
     P.KP = c->KP;
     P.ldk = c->ldk;
     const int vs = c->v_bf16 ? 2 : 4;
-    P.stages = two_sided_stages(c->KP, vs);
+    two_sided_stages(c->KP, vs, &P.stages, &P.vstages);
     P.items_a = c->B * c->mt_max;
     P.items = P.items_a + c->B * c->nt_max;
     P.phi_inv = (float)(1.0 / c->phi);
@@ -951,11 +997,8 @@ static psgld_status launch_two_sided(psgld_ctx *c, int part, cudaStream_t st)
     int sms = 0;
     PSGLD_CK(c, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
     const int grid = std::min(P.items, sms);
-    const size_t smem = two_sided_smem(c->KP, vs, P.stages);
-    if (c->v_bf16)
-        two_sided::chain_kernel<__nv_bfloat16><<<grid, two_sided::kThreads, smem, st>>>(P);
-    else
-        two_sided::chain_kernel<float><<<grid, two_sided::kThreads, smem, st>>>(P);
+    const size_t smem = two_sided_smem(c->KP, vs, P.stages, P.vstages);
+    pick_chain(c->v_bf16 != 0, P.p_mode)<<<grid, two_sided::kThreads, smem, st>>>(P);
     PSGLD_CK(c, cudaGetLastError());
     return PSGLD_OK;
 }

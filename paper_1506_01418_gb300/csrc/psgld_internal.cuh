@@ -107,7 +107,7 @@ struct psgld_ctx {
     int64_t *t_dev = nullptr;    // iteration counter read by graph replays
 
     // profiling: one event pair per part (start, end), and which are unread
-    std::vector<cudaEvent_t> ev_start, ev_end;
+    std::vector<cudaEvent_t> ev_start, ev_mid, ev_end;   // mid: after the gradient kernel
     std::vector<char> ev_pending;
 };
 

@@ -659,6 +659,7 @@ psgld_status launch_part_step(psgld_ctx *c, int64_t t, const int64_t *t_dev, int
         gfn<<<ggrid, kGradThreads, grad_smem(sh), st>>>(GP);
     }
     PSGLD_CK(c, cudaGetLastError());
+    if (prof) PSGLD_CK(c, cudaEventRecordWithFlags(c->ev_mid[part], st, rec_flags));
     if (items > 0) update_kernel<<<ugrid, kThreads, 0, st>>>(UP);
     PSGLD_CK(c, cudaGetLastError());
     if (prof) {

@@ -38,6 +38,22 @@ def dense_poisson(I: int, J: int, K_true: int, seed: int):
     return V, Wt, Ht
 
 
+def dense_poisson_device(I: int, J: int, K_true: int, seed: int, device):
+    """dense_poisson drawn with torch on a CUDA device (for sizes whose host
+    arrays would be too slow to draw): W*, H* ~ Gamma(1, 1) (= Exponential(1)),
+    V ~ Poisson(W* H*).  Returns V (float32 I x J tensor on `device`)."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    Wt = torch.empty((I, K_true), dtype=torch.float32, device=device).exponential_(1.0, generator=g)
+    Ht = torch.empty((K_true, J), dtype=torch.float32, device=device).exponential_(1.0, generator=g)
+    M = Wt @ Ht
+    del Wt, Ht
+    V = torch.poisson(M, generator=g)
+    del M
+    return V
+
+
 def dense_gamma(I: int, J: int, K_true: int, seed: int):
     """Dense positive data V = |W* H*| * Gamma(shape 2, rate 2)."""
     g = _rng(seed)

@@ -54,7 +54,8 @@ EXPORTS = [
     "psgld_default_options", "psgld_create", "psgld_set_options", "psgld_set_data_coo",
     "psgld_set_data_dense", "psgld_set_factors", "psgld_get_factors", "psgld_part_step",
     "psgld_sweep", "psgld_posterior_mean", "psgld_log_lik", "psgld_rmse", "psgld_piece_bounds",
-    "psgld_part_schedule", "psgld_part_layout", "psgld_profile_read", "psgld_iterations_done",
+    "psgld_part_schedule", "psgld_part_layout", "psgld_profile_read", "psgld_profile_read_split",
+    "psgld_iterations_done",
     "psgld_log_lik_static", "psgld_last_error",
     "psgld_destroy",
 ]
@@ -92,6 +93,7 @@ def load(build_if_missing: bool = True):
         "psgld_part_schedule": (st, [vp, i64, vp]),
         "psgld_part_layout": (st, [vp, i32, vp, vp, vp]),
         "psgld_profile_read": (st, [vp, vp, vp]),
+        "psgld_profile_read_split": (st, [vp, vp, vp, vp]),
         "psgld_iterations_done": (i64, [vp]),
         "psgld_log_lik_static": (st, [i64, vp, vp, vp, vp, vp, i64, i64, i32, f64, f64, f64, vp, vp]),
         "psgld_last_error": (C.c_char_p, [vp]),
@@ -254,6 +256,15 @@ def psgld_profile_read(ctx):
     return ms.value, n.value
 
 
+def psgld_profile_read_split(ctx):
+    """(gradient-kernel ms, update-kernel ms, number of part-steps) since the last read."""
+    g = C.c_double(0.0)
+    u = C.c_double(0.0)
+    n = C.c_int64(0)
+    _check(ctx, load().psgld_profile_read_split(ctx, C.byref(g), C.byref(u), C.byref(n)))
+    return g.value, u.value, n.value
+
+
 def psgld_log_lik_static(i, j, v, W, Ht, tweedie_p, phi, out, mu_min=1e-10, stream=None):
     """Log-likelihood of factors W (I x K), Ht (J x K) on entries (i, j, v),
     written to `out` (a one-element float64 CUDA tensor); allocates nothing."""
@@ -353,6 +364,9 @@ class PSGLD:
 
     def profile_read(self):
         return psgld_profile_read(self.ctx)
+
+    def profile_read_split(self):
+        return psgld_profile_read_split(self.ctx)
 
     @property
     def iterations_done(self):

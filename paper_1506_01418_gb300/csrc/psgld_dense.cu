@@ -84,6 +84,14 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t 
            ((uint64_t)(sbo >> 4) << 32) | (1ull << 46);
 }
 
+// The same with the 128-byte swizzle (layout type 2): the operand is stored
+// in atoms of 8 rows x 128 bytes, 16-byte chunks of row r at chunk position
+// c ^ (r % 8), atoms 1024-byte aligned.
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t addr, uint32_t lbo, uint32_t sbo)
+{
+    return sdesc(addr, lbo, sbo) | (2ull << 61);
+}
+
 // instruction descriptor: FP32 accumulate, BF16 A and B; a_mn / b_mn select
 // the MN-major (transposed) reading of that operand
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, int a_mn = 0, int b_mn = 0)
@@ -99,6 +107,24 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b
                  "setp.ne.b32 p, %4, 0;\n\t"
                  "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
                  :: "r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"(accumulate) : "memory");
+}
+
+// The same with A read from TMEM (128 lanes = rows, K packed two BF16 per
+// 32-bit column, 8 columns per K step of 16).
+__device__ __forceinline__ void mma_bf16_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc,
+                                            uint32_t accumulate)
+{
+    asm volatile("{\n\t.reg .pred p;\n\t"
+                 "setp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}"
+                 :: "r"(d_tmem), "r"(a_tmem), "l"(b), "r"(idesc), "r"(accumulate) : "memory");
+}
+
+// Copy of a 128-row x 32-byte operand slice (one K step of 16 BF16) from
+// shared memory (described like an MMA operand) into 8 TMEM columns.
+__device__ __forceinline__ void tmem_cp_128x256b(uint32_t taddr, uint64_t sdesc_)
+{
+    asm volatile("tcgen05.cp.cta_group::1.128x256b [%0], %1;" :: "r"(taddr), "l"(sdesc_) : "memory");
 }
 
 __device__ __forceinline__ void mma_commit(uint64_t *bar)
@@ -400,20 +426,26 @@ __global__ void __launch_bounds__(kDenseThreads, 1) dense_grad_kernel(const __gr
 // Every tile is one bulk copy.
 //
 // One persistent CTA per SM, 10 warps:
-//   warp 0 (one thread)  producer: the owned tile once per item, then per
+//   warp 0               producer: the owned tile once per item, then per
 //                         walked tile the other factor's 64-row tile and the
-//                         V tile into a ring of stages (bulk copies);
-//   warp 1 (one thread)  MMA issuer: GEMM1 mu_j = A . B_j^T into one of two
+//                         V tile, into two rings of slots (bulk copies);
+//   warp 1               MMA issuer: GEMM1 mu_j = A . B_j^T into one of two
 //                         TMEM buffers, then GEMM2 G += E_(j-1) . B_(j-1)
 //                         (B read MN-major), so GEMM1 of tile j overlaps the
-//                         epilogue of tile j-1; completions via tcgen05.commit;
+//                         epilogue of tile j-1; completions via tcgen05.commit.
+//                         Both warps run their loops with all 32 lanes (the
+//                         descriptors stay warp-uniform, in uniform registers)
+//                         and lane 0 performs each copy and MMA;
 //   warps 2-9            epilogue, two warps per TMEM lane quarter (32 of the
 //                         tile's 64 columns each): TMEM mu + V (shared
 //                         memory) -> E (BF16, shared memory, two buffers),
 //                         and after an item's last tile the G rows from TMEM
 //                         to HBM.  The Tweedie power is a template parameter
 //                         (p = 0, 1, 2, other), so the epilogue is straight-line.
-// TMEM: mu buffers at columns 0 and 64, G at 128 .. 128 + KP.
+// TMEM: mu buffers at columns 0 and 64, G at 128 .. 128 + KP, and the owned
+// tile (copied from shared memory once per item with tcgen05.cp, so GEMM1
+// reads A from TMEM and shared memory serves only B) in the last KP / 2
+// columns.
 // Padding rows and columns of every tile are zero, so mu and E are zero
 // there and need no masks.
 namespace two_sided {
@@ -432,9 +464,9 @@ struct Side {
     const unsigned char *Vt;    // V tiles in this orientation
     float *G;                   // G rows of the owned factor
     int64_t n_own, n_walk;      // I or J
-    int own_tiles;              // 128-row tile slots per owned piece
-    int walk_tiles128;          // 128-row shadow tile slots per walked piece
+    int own_tiles;              // 128-row tile slots per owned piece (items, V tiles)
     int walk_tiles;             // 64-row V tile slots per walked piece
+    int own_sh64, walk_sh64;    // 64-row shadow tiles per owned / walked piece
 };
 
 struct Params {
@@ -476,25 +508,104 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
                  :: "r"(saddr(dst)), "l"(src), "r"(bytes), "r"(saddr(b)) : "memory");
 }
 
-// Bounded wait by one thread; gives up (and raises the abort flag) when the
-// CTA is aborting or the wait runs out.
-__device__ __forceinline__ bool wait1(Bars *S, uint64_t *b, uint32_t parity)
+// Leader-only forms for warp-uniform loops: every lane executes the
+// instruction with the same (uniform) operands and elect.sync picks the one
+// lane that performs it (the same lane each time, the whole warp being
+// active), so descriptors and addresses stay in uniform registers and each
+// MMA issues in a few cycles.  The `leader` argument is unused (kept for the
+// call sites' readability).
+__device__ __forceinline__ void expect_tx_if(uint32_t, uint64_t *b, uint32_t bytes)
 {
-    if (*(volatile int *)&S->abort) return false;
-    if (bar_wait(b, parity)) return true;
-    *(volatile int *)&S->abort = 1;
-    return false;
+    asm volatile("{\n\t.reg .pred e;\n\telect.sync _|e, 0xffffffff;\n\t"
+                 "@e mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n\t}"
+                 :: "r"(saddr(b)), "r"(bytes) : "memory");
 }
 
-// The same for a whole warp, with one warp-uniform answer.
+__device__ __forceinline__ void bulk_g2s_if(uint32_t, void *dst, const void *src, uint32_t bytes, uint64_t *b)
+{
+    asm volatile("{\n\t.reg .pred e;\n\telect.sync _|e, 0xffffffff;\n\t"
+                 "@e cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n\t}"
+                 :: "r"(saddr(dst)), "l"(src), "r"(bytes), "r"(saddr(b)) : "memory");
+}
+
+__device__ __forceinline__ void mma_ta_if(uint32_t, uint32_t d, uint32_t a, uint64_t bdesc, uint32_t id,
+                                          uint32_t acc)
+{
+    asm volatile("{\n\t.reg .pred p, e;\n\telect.sync _|e, 0xffffffff;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                 "@e tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}"
+                 :: "r"(d), "r"(a), "l"(bdesc), "r"(id), "r"(acc) : "memory");
+}
+
+__device__ __forceinline__ void mma_ss_if(uint32_t, uint32_t d, uint64_t adesc, uint64_t bdesc, uint32_t id,
+                                          uint32_t acc)
+{
+    asm volatile("{\n\t.reg .pred p, e;\n\telect.sync _|e, 0xffffffff;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                 "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+                 :: "r"(d), "l"(adesc), "l"(bdesc), "r"(id), "r"(acc) : "memory");
+}
+
+__device__ __forceinline__ void cp_if(uint32_t, uint32_t taddr, uint64_t sdesc_)
+{
+    asm volatile("{\n\t.reg .pred e;\n\telect.sync _|e, 0xffffffff;\n\t"
+                 "@e tcgen05.cp.cta_group::1.128x256b [%0], %1;\n\t}"
+                 :: "r"(taddr), "l"(sdesc_) : "memory");
+}
+
+__device__ __forceinline__ void commit_if(uint32_t, uint64_t *b)
+{
+    asm volatile("{\n\t.reg .pred e;\n\telect.sync _|e, 0xffffffff;\n\t"
+                 "@e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n\t}"
+                 :: "r"(saddr(b)) : "memory");
+}
+
+// GEMM1 of one walked tile, fully unrolled for the K width KPC: mu (TMEM
+// column d) = A (TMEM, tA) . B^T (walked tile at shared address aB, 128-byte
+// swizzled K-major atoms of 64 rows x 128 B).  With compile-time K steps the
+// descriptors are constants plus one uniform base, so each MMA issues in a
+// few cycles.
+template <int KPC>
+__device__ __forceinline__ void gemm1_tile(uint32_t ld, uint32_t d, uint32_t tA, uint32_t aB, uint32_t id1)
+{
+    const uint64_t base = sdesc_sw128(aB, 16, 1024);
+#pragma unroll
+    for (int ks = 0; ks < KPC / 16; ++ks)
+        mma_ta_if(ld, d, tA + (uint32_t)ks * 8,
+                  base + (uint64_t)(((ks >> 2) * (64 * 128) + (ks & 3) * 32) >> 4), id1, ks > 0);
+}
+
+// The owned tile (shared address aA, 128-row atoms) into TMEM at tA.
+template <int KPC>
+__device__ __forceinline__ void own_to_tmem(uint32_t ld, uint32_t tA, uint32_t aA)
+{
+    const uint64_t base = sdesc_sw128(aA, 16, 1024);
+#pragma unroll
+    for (int ks = 0; ks < KPC / 16; ++ks)
+        cp_if(ld, tA + (uint32_t)ks * 8, base + (uint64_t)(((ks >> 2) * (128 * 128) + (ks & 3) * 32) >> 4));
+}
+
+// Bounded wait by a whole warp, with one warp-uniform answer.  Every lane
+// polls (control flow stays uniform, which keeps the MMA warp's operands in
+// uniform registers); a completed phase costs one try_wait and one vote.
+// The wait gives up (and raises the abort flag) when the CTA is aborting or
+// the wait runs out.
 __device__ __forceinline__ bool wait32(Bars *S, uint64_t *b, uint32_t parity)
 {
+    if (__all_sync(0xffffffffu, bar_try_wait(b, parity))) return true;
     const bool stop = __any_sync(0xffffffffu, *(volatile int *)&S->abort != 0);
     bool ok = !stop && bar_wait(b, parity);
     ok = __all_sync(0xffffffffu, ok);
     if (!ok && (threadIdx.x & 31) == 0) *(volatile int *)&S->abort = 1;
     return ok;
 }
+
+// Slot and phase of a ring of n slots, advanced one use at a time.
+struct Ring {
+    uint32_t slot = 0, phase = 0;
+    __device__ __forceinline__ void next(uint32_t n)
+    {
+        if (++slot == n) { slot = 0; phase ^= 1u; }
+    }
+};
 
 struct Item {
     int side, own_piece, walk_piece, ot, own_rows_in_tile, nj;
@@ -540,8 +651,11 @@ __device__ __forceinline__ float tweedie_pm(float p, float phi_inv, float mu_min
 template <typename VT, int PM>
 __global__ void __launch_bounds__(kThreads, 1) chain_kernel(const __grid_constant__ Params P)
 {
-    extern __shared__ __align__(1024) unsigned char sm[];
-    const int KP = P.KP;
+    extern __shared__ __align__(1024) unsigned char sm_raw[];
+    // the swizzled operand tiles need 1024-byte alignment (1 KB of slack is allocated)
+    unsigned char *sm = sm_raw + ((1024u - (saddr(sm_raw) & 1023u)) & 1023u);
+    const int KP = P.KP;                                        // multiple of 64
+    const int NA = KP / 64;                                     // 128-byte atoms along K
     const uint32_t a_bytes = (uint32_t)kOwn * KP * 2;           // owned tile
     const uint32_t b_bytes = (uint32_t)kBN * KP * 2;            // walked tile
     const uint32_t v_bytes = (uint32_t)kOwn * kBN * sizeof(VT); // V tile
@@ -577,31 +691,41 @@ __global__ void __launch_bounds__(kThreads, 1) chain_kernel(const __grid_constan
     const uint32_t tmem = S->tmem;
 
     if (warp == 0) {
-        // ---------------- producer
-        if (lane == 0) {
-            uint32_t tc = 0, ic = 0;
+        // ---------------- producer (whole warp, lane 0 performs)
+        {
+            const uint32_t ld = lane == 0;
+            uint32_t ic = 0;
+            Ring rb, rv;
             for (int it = blockIdx.x; it < P.items; it += gridDim.x) {
                 Item x;
                 if (!decode(P, it, x)) continue;
                 const Side &Sd = P.side[x.side];
-                if (!wait1(S, &S->a_empty, (ic & 1) ^ 1)) goto done0;
-                bar_expect_tx(&S->a_full, a_bytes);
-                bulk_g2s(sA, Sd.own_sh + ((int64_t)x.own_piece * Sd.own_tiles + x.ot) * kOwn * KP,
-                         a_bytes, &S->a_full);
+                if (!wait32(S, &S->a_empty, (ic & 1) ^ 1)) goto done0;
+                expect_tx_if(ld, &S->a_full, a_bytes);
+                {
+                    // rows 0..63 and 64..127 come from two 64-row shadow tiles;
+                    // in shared memory each atom holds all 128 rows
+                    const uint16_t *t0 = Sd.own_sh + ((int64_t)x.own_piece * Sd.own_sh64 + 2 * x.ot) * 64 * KP;
+                    for (int a = 0; a < NA; ++a) {
+                        bulk_g2s_if(ld, sA + a * 16384, t0 + a * 4096, 8192, &S->a_full);
+                        bulk_g2s_if(ld, sA + a * 16384 + 8192, t0 + 64 * KP + a * 4096, 8192, &S->a_full);
+                    }
+                }
                 const unsigned char *vbase =
                     Sd.Vt + ((((int64_t)x.own_piece * P.B + x.walk_piece) * Sd.own_tiles + x.ot) *
                              Sd.walk_tiles) * (int64_t)v_bytes;
-                for (int j = 0; j < x.nj; ++j, ++tc) {
-                    const int st = (int)(tc % NS), sv = (int)(tc % NV);
-                    if (!wait1(S, &S->empty[st], ((tc / NS) & 1) ^ 1)) goto done0;
-                    bar_expect_tx(&S->full[st], b_bytes);
-                    bulk_g2s(sB + (size_t)st * b_bytes,
-                             Sd.walk_sh + ((int64_t)x.walk_piece * Sd.walk_tiles128 + (j >> 1)) * kOwn * KP +
-                                 (int64_t)(j & 1) * kBN * KP,
-                             b_bytes, &S->full[st]);
-                    if (!wait1(S, &S->vempty[sv], ((tc / NV) & 1) ^ 1)) goto done0;
-                    bar_expect_tx(&S->vfull[sv], v_bytes);
-                    bulk_g2s(sV + (size_t)sv * v_bytes, vbase + (int64_t)j * v_bytes, v_bytes, &S->vfull[sv]);
+                for (int j = 0; j < x.nj; ++j) {
+                    const uint32_t st = rb.slot, sv = rv.slot;
+                    if (!wait32(S, &S->empty[st], rb.phase ^ 1)) goto done0;
+                    expect_tx_if(ld, &S->full[st], b_bytes);
+                    bulk_g2s_if(ld, sB + (size_t)st * b_bytes,
+                                Sd.walk_sh + ((int64_t)x.walk_piece * Sd.walk_sh64 + j) * kBN * KP,
+                                b_bytes, &S->full[st]);
+                    if (!wait32(S, &S->vempty[sv], rv.phase ^ 1)) goto done0;
+                    expect_tx_if(ld, &S->vfull[sv], v_bytes);
+                    bulk_g2s_if(ld, sV + (size_t)sv * v_bytes, vbase + (int64_t)j * v_bytes, v_bytes, &S->vfull[sv]);
+                    rb.next(NS);
+                    rv.next(NV);
                 }
                 ++ic;
             }
@@ -609,53 +733,78 @@ __global__ void __launch_bounds__(kThreads, 1) chain_kernel(const __grid_constan
     done0:
         __syncwarp();
     } else if (warp == 1) {
-        // ---------------- MMA issuer
-        if (lane == 0) {
-            uint32_t tc = 0, ic = 0, mu_use[2] = {0, 0}, e_use[2] = {0, 0};
+        // ---------------- MMA issuer (whole warp, lane 0 performs).  Tile
+        // number tc (counted over the CTA's items) uses mu / E buffer tc % 2,
+        // for the (tc / 2)-th time.
+        {
+            const uint32_t ld = lane == 0;
+            uint32_t tc = 0, ic = 0;
+            Ring r1, r2;     // walked-tile slots of GEMM1 (tile tc) and GEMM2 (tile tc - 1)
             const uint32_t id1 = idesc_bf16(kOwn, kBN);
             const uint32_t id2 = idesc_bf16(kOwn, KP, 0, 1);
-            const uint64_t dA = sdesc(saddr(sA), 128, KP * 16);
+            // K-major, 128-byte swizzle: 8-row groups 1024 B apart; a K step of
+            // 16 entries moves 32 B inside an atom, 4 steps fill an atom, and the
+            // next atom of the owned tile starts 128 rows x 128 B further
+            const uint32_t aA = saddr(sA);
+            const uint32_t tA = tmem + (kTmemCols - (uint32_t)KP / 2);   // owned tile in TMEM
             for (int it = blockIdx.x; it < P.items; it += gridDim.x) {
                 Item x;
                 if (!decode(P, it, x)) continue;
-                if (!wait1(S, &S->a_full, ic & 1)) goto done1;
+                if (!wait32(S, &S->a_full, ic & 1)) goto done1;
                 fence_after();
-                int prev_st = 0;
+                // the owned tile into TMEM once per item (ordered after the
+                // previous item's MMAs and before this item's: same issuing
+                // thread); its shared-memory slot is free when the copies are
+                switch (KP) {
+                case 64: own_to_tmem<64>(ld, tA, aA); break;
+                case 128: own_to_tmem<128>(ld, tA, aA); break;
+                case 192: own_to_tmem<192>(ld, tA, aA); break;
+                default: own_to_tmem<256>(ld, tA, aA); break;
+                }
+                commit_if(ld, &S->a_empty);
                 for (int j = 0; j <= x.nj; ++j) {
-                    int st = 0;
                     if (j < x.nj) {
-                        st = (int)(tc % NS);
-                        if (!wait1(S, &S->full[st], (tc / NS) & 1)) goto done1;
-                        const int b = j & 1;
-                        if (!wait1(S, &S->mu_empty[b], (mu_use[b] & 1) ^ 1)) goto done1;
+                        const uint32_t st = r1.slot;
+                        const int b = (int)(tc & 1);
+                        if (!wait32(S, &S->full[st], r1.phase)) goto done1;
+                        if (!wait32(S, &S->mu_empty[b], ((tc >> 1) & 1) ^ 1)) goto done1;
                         fence_after();
-                        const uint64_t dB = sdesc(saddr(sB + (size_t)st * b_bytes), 128, KP * 16);
-                        for (int ks = 0; ks < KP / 16; ++ks)
-                            mma_bf16(tmem + (uint32_t)(b * kBN), dA + (uint64_t)(ks * 16),
-                                     dB + (uint64_t)(ks * 16), id1, ks > 0);
-                        mma_commit(&S->mu_full[b]);
-                        ++mu_use[b];
+                        const uint32_t aB = saddr(sB + (size_t)st * b_bytes);
+                        const uint32_t dmu = tmem + (uint32_t)(b * kBN);
+                        switch (KP) {
+                        case 64: gemm1_tile<64>(ld, dmu, tA, aB, id1); break;
+                        case 128: gemm1_tile<128>(ld, dmu, tA, aB, id1); break;
+                        case 192: gemm1_tile<192>(ld, dmu, tA, aB, id1); break;
+                        default: gemm1_tile<256>(ld, dmu, tA, aB, id1); break;
+                        }
+                        commit_if(ld, &S->mu_full[b]);
                         ++tc;
+                        r1.next(NS);
                     }
                     if (j > 0) {
-                        // GEMM2 of tile j - 1
-                        const int jj = j - 1, b = jj & 1;
-                        if (!wait1(S, &S->e_full[b], e_use[b] & 1)) goto done1;
-                        if (jj == 0 && !wait1(S, &S->g_empty, (ic & 1) ^ 1)) goto done1;
+                        // GEMM2 of tile j - 1 (tile number tp)
+                        const uint32_t tp = j < x.nj ? tc - 2 : tc - 1;
+                        const int b = (int)(tp & 1);
+                        const uint32_t st = r2.slot;
+                        if (!wait32(S, &S->e_full[b], (tp >> 1) & 1)) goto done1;
+                        if (j == 1 && !wait32(S, &S->g_empty, (ic & 1) ^ 1)) goto done1;
                         fence_after();
-                        const uint64_t dE = sdesc(saddr(sE + b * e_bytes), 128, kBN * 16);
-                        const uint64_t dBt = sdesc(saddr(sB + (size_t)prev_st * b_bytes), KP * 16, 128);
+                        // A = E (K-major, one atom of 64 walked columns); B = the
+                        // walked tile read MN-major: MN atoms (64 entries of k)
+                        // 64 rows x 128 B apart (LBO), 8-row K groups 1024 B apart
+                        // (SBO), a K step of 16 walked rows = 2048 B
+                        const uint64_t dE = sdesc_sw128(saddr(sE + b * e_bytes), 16, 1024);
+                        const uint64_t dBt = sdesc_sw128(saddr(sB + (size_t)st * b_bytes), kBN * 128, 1024);
+#pragma unroll
                         for (int ks = 0; ks < kBN / 16; ++ks)
-                            mma_bf16(tmem + kGCol, dE + (uint64_t)(ks * 16), dBt + (uint64_t)(ks * 2 * KP),
-                                     id2, (jj > 0 || ks > 0));
-                        mma_commit(&S->e_empty[b]);
-                        mma_commit(&S->empty[prev_st]);
-                        ++e_use[b];
+                            mma_ss_if(ld, tmem + kGCol, dE + (uint64_t)(ks * 2), dBt + (uint64_t)(ks * 128),
+                                      id2, (j > 1 || ks > 0));
+                        commit_if(ld, &S->e_empty[b]);
+                        commit_if(ld, &S->empty[st]);
+                        r2.next(NS);
                     }
-                    prev_st = st;
                 }
-                mma_commit(&S->g_full);
-                mma_commit(&S->a_empty);
+                commit_if(ld, &S->g_full);
                 ++ic;
             }
         }
@@ -668,16 +817,19 @@ __global__ void __launch_bounds__(kThreads, 1) chain_kernel(const __grid_constan
         const int rho = 32 * q + lane;                      // owned row in the tile
         const int c = 32 * hc;
         const uint32_t lane_base = (uint32_t)(32 * q) << 16;
-        uint32_t tc = 0, ic = 0, mu_use[2] = {0, 0}, e_use[2] = {0, 0};
+        uint32_t tc = 0, ic = 0;
+        Ring rv;
         for (int it = blockIdx.x; it < P.items; it += gridDim.x) {
             Item x;
             if (!decode(P, it, x)) continue;
             const Side &Sd = P.side[x.side];
-            for (int j = 0; j < x.nj; ++j, ++tc) {
-                const int b = j & 1, sv = (int)(tc % NV);
-                if (!wait32(S, &S->vfull[sv], (tc / NV) & 1)) goto done2;
-                if (!wait32(S, &S->mu_full[b], mu_use[b] & 1)) goto done2;
-                if (!wait32(S, &S->e_empty[b], (e_use[b] & 1) ^ 1)) goto done2;
+            for (int j = 0; j < x.nj; ++j, ++tc, rv.next(NV)) {
+                const int b = (int)(tc & 1);
+                const uint32_t sv = rv.slot;
+                const uint32_t ph = (tc >> 1) & 1;
+                if (!wait32(S, &S->vfull[sv], rv.phase)) goto done2;
+                if (!wait32(S, &S->mu_full[b], ph)) goto done2;
+                if (!wait32(S, &S->e_empty[b], ph ^ 1)) goto done2;
                 fence_after();
                 const unsigned char *vt = sV + (size_t)sv * v_bytes;
                 unsigned char *eb = sE + b * e_bytes;
@@ -712,11 +864,11 @@ __global__ void __launch_bounds__(kThreads, 1) chain_kernel(const __grid_constan
                     __nv_bfloat162 t2 = __floats2bfloat162_rn(e0, e1);
                     pk[h] = *reinterpret_cast<uint32_t *>(&t2);
                 }
-                // E (owned row rho, walked columns c..c+31) in K-major core matrices
+                // E (owned row rho, walked columns c..c+31): row rho of the
+                // 128-byte-swizzled atom column, chunk (c/8 + g) ^ (rho % 8)
 #pragma unroll
                 for (int g = 0; g < 4; ++g)
-                    *reinterpret_cast<uint4 *>(eb + (rho >> 3) * (kBN * 16) + ((c >> 3) + g) * 128 +
-                                               (rho & 7) * 16) =
+                    *reinterpret_cast<uint4 *>(eb + rho * 128 + ((((c >> 3) + g) ^ (rho & 7)) << 4)) =
                         make_uint4(pk[4 * g], pk[4 * g + 1], pk[4 * g + 2], pk[4 * g + 3]);
                 fence_async_smem();
                 fence_before();
@@ -726,8 +878,6 @@ __global__ void __launch_bounds__(kThreads, 1) chain_kernel(const __grid_constan
                     bar_arrive(&S->mu_empty[b]);
                     bar_arrive(&S->e_full[b]);
                 }
-                ++mu_use[b];
-                ++e_use[b];
             }
             // the item's G rows: this warp's lane quarter, every other 32-column chunk
             if (!wait32(S, &S->g_full, ic & 1)) goto done2;
@@ -863,7 +1013,8 @@ size_t two_sided_bytes(int KP, int vsize, int stages, int vstages)
 {
     return (size_t)two_sided::kOwn * KP * 2 + 2 * (size_t)two_sided::kOwn * two_sided::kBN * 2 +
            (size_t)stages * two_sided::kBN * KP * 2 +
-           (size_t)vstages * two_sided::kOwn * two_sided::kBN * vsize + sizeof(two_sided::Bars) + 16;
+           (size_t)vstages * two_sided::kOwn * two_sided::kBN * vsize + sizeof(two_sided::Bars) + 16 +
+           1024;   // alignment slack
 }
 
 // At least half of an SM's shared memory, so that one CTA (and one 512-column
@@ -906,7 +1057,7 @@ psgld_status prepare_dense(psgld_ctx *c)
     }
     c->dense_kind = 2;
     c->v_bf16 = vb ? 1 : 0;
-    c->KP = 16 * cdiv(c->K, 16);
+    c->KP = 64 * cdiv(c->K, 64);
     const int64_t maxI = (c->I + c->B - 1) / c->B, maxJ = (c->J + c->B - 1) / c->B;
     c->mt_max = cdiv(maxI, 128);
     c->nt_max = cdiv(maxJ, 128);
@@ -920,7 +1071,7 @@ psgld_status prepare_dense(psgld_ctx *c)
                                          (int)two_sided_smem(c->KP, vs, stages, vstages)));
     const int64_t B = c->B;
     const int64_t nA = B * B * c->mt_max * c->nj_max * 8192, nB = B * B * c->nt_max * c->ni_max * 8192;
-    const int64_t nW = B * c->mt_max * 128 * c->KP, nH = B * c->nt_max * 128 * c->KP;
+    const int64_t nW = B * 2 * c->mt_max * 64 * c->KP, nH = B * 2 * c->nt_max * 64 * c->KP;
     auto al = [&](void **p, size_t bytes) -> psgld_status {
         if (cudaMalloc(p, bytes) != cudaSuccess) {
             *p = nullptr;
@@ -965,7 +1116,7 @@ psgld_status build_dense_shadows(psgld_ctx *c, cudaStream_t st)
         const float *X = side == 0 ? c->W[c->wcur] : c->Ht[c->hcur];
         const unsigned grid = (unsigned)std::min<int64_t>((n * c->ngroups + 255) / 256, 152 * 16);
         build_shadow_kernel<<<grid, 256, 0, st>>>(X, n, c->ngroups, c->ldk, c->B,
-                                                  side == 0 ? c->mt_max : c->nt_max, c->KP,
+                                                  2 * (side == 0 ? c->mt_max : c->nt_max), c->KP,
                                                   side == 0 ? c->Wsh : c->Hsh);
         PSGLD_CK(c, cudaGetLastError());
     }
@@ -978,9 +1129,11 @@ static psgld_status launch_two_sided(psgld_ctx *c, int part, cudaStream_t st)
     const int64_t I = c->I, J = c->J;
     two_sided::Side &A = P.side[0], &Bs = P.side[1];
     A.own_sh = c->Wsh; A.walk_sh = c->Hsh; A.Vt = (const unsigned char *)c->VA; A.G = c->G;
-    A.n_own = I; A.n_walk = J; A.own_tiles = c->mt_max; A.walk_tiles128 = c->nt_max; A.walk_tiles = c->nj_max;
+    A.n_own = I; A.n_walk = J; A.own_tiles = c->mt_max; A.walk_tiles = c->nj_max;
+    A.own_sh64 = 2 * c->mt_max; A.walk_sh64 = 2 * c->nt_max;
     Bs.own_sh = c->Hsh; Bs.walk_sh = c->Wsh; Bs.Vt = (const unsigned char *)c->VB; Bs.G = c->G + I * c->ldk;
-    Bs.n_own = J; Bs.n_walk = I; Bs.own_tiles = c->nt_max; Bs.walk_tiles128 = c->mt_max; Bs.walk_tiles = c->ni_max;
+    Bs.n_own = J; Bs.n_walk = I; Bs.own_tiles = c->nt_max; Bs.walk_tiles = c->ni_max;
+    Bs.own_sh64 = 2 * c->nt_max; Bs.walk_sh64 = 2 * c->mt_max;
     P.B = c->B;
     P.part = part;
     P.KP = c->KP;

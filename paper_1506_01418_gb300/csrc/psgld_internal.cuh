@@ -19,7 +19,7 @@
 //           block has more than one 128-row tile (single-pass kernel)
 //   two-sided kernel: VA / VB, V in 128 x 64 tiles per block, owned rows =
 //           rows of V (VA) or columns of V (VB); Wsh / Hsh, BF16 shadows of W
-//           and H^T in 128-row MMA tiles per piece (see dev::shadow_store4)
+//           and H^T in 64-row swizzled MMA tiles per piece (dev::shadow_store4)
 #pragma once
 
 #include <cuda_bf16.h>
@@ -72,7 +72,7 @@ struct psgld_ctx {
     float *hpart = nullptr;          // mtiles x J x ldk partial G_H rows (mtiles > 1)
     int mtiles = 0;                  // 128-row tiles of the largest row piece
     int dense_kind = 0;              // 1: single-pass kernel, 2: two-sided kernel
-    int KP = 0;                      // K rounded up to 16 (two-sided kernel)
+    int KP = 0;                      // K rounded up to 64 (two-sided kernel)
     int v_bf16 = 0;                  // V tiles in BF16
     void *VA = nullptr, *VB = nullptr;          // V tiles, both orientations
     uint16_t *Wsh = nullptr, *Hsh = nullptr;    // BF16 shadows of W, H^T
@@ -210,19 +210,22 @@ __device__ __forceinline__ float4 box_muller4(uint4 x)
     return make_float4(r0 * c0, r0 * s0, r1 * c1, r1 * s1);
 }
 
-// BF16 copy of 4 factor entries (row, k0 .. k0+3) into the MMA tiles of the
-// two-sided dense kernel.  Rows of piece r (Definition 1) fill `tiles`
-// 128-row tiles starting at tile r * tiles; inside a tile, entry (rho, k)
-// sits at (rho/8) * KP*8 + (k/8) * 64 + (rho%8) * 8 + k%8 (8 x 8 core
-// matrices, K-adjacent ones 128 bytes apart).
+// BF16 copy of 4 factor entries (row, k0 .. k0+3, k0 % 4 == 0) into the MMA
+// tiles of the two-sided dense kernel.  Rows of piece r (Definition 1) fill
+// `tiles` 64-row tiles starting at tile r * tiles.  A tile holds KP / 64
+// atoms of 64 rows x 128 bytes (64 entries of k), one after the other; in
+// row rho of an atom, the 16-byte chunk of entries 8c .. 8c+7 sits at chunk
+// position c ^ (rho % 8) -- the 128-byte swizzle that the tensor core's
+// operand reads expect (the pattern repeats every 8 rows = 1024 bytes).
 __device__ __forceinline__ void shadow_store4(uint16_t *sh, int64_t row, int k0, float4 v, int64_t n,
                                               int B, int tiles, int KP)
 {
     const int64_t piece = ((row + 1) * B - 1) / n;
     const int64_t rr = row - (piece * n) / B;
-    const int rho = (int)(rr & 127);
-    const int64_t off = (piece * tiles + (rr >> 7)) * 128 * KP + (int64_t)(rho >> 3) * (KP * 8) +
-                        (k0 >> 3) * 64 + (rho & 7) * 8 + (k0 & 7);
+    const int rho = (int)(rr & 63);
+    const int kk = k0 & 63, c = kk >> 3;
+    const int64_t off = (piece * tiles + (rr >> 6)) * 64 * KP + (int64_t)(k0 >> 6) * 4096 +
+                        rho * 64 + ((c ^ (rho & 7)) << 3) + (kk & 7);
     __nv_bfloat162 lo = __floats2bfloat162_rn(v.x, v.y), hi = __floats2bfloat162_rn(v.z, v.w);
     *reinterpret_cast<uint2 *>(sh + off) =
         make_uint2(*reinterpret_cast<uint32_t *>(&lo), *reinterpret_cast<uint32_t *>(&hi));

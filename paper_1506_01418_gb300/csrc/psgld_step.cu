@@ -86,7 +86,7 @@ struct UpdSide {
     int gparts;               // dense path: partial gradient arrays to add (0: sparse path)
     uint16_t *sh;             // two-sided dense kernel: BF16 shadow of X_next (else null)
     int64_t n_rows;           // I or J
-    int sh_tiles;             // 128-row shadow tiles per piece
+    int sh_tiles;             // 64-row shadow tiles per piece
     float prior_a, prior_b;   // d log p(x)/dx = prior_a + prior_b * x
     uint32_t mat;             // 0 = W, 1 = H (noise stream)
 };
@@ -581,7 +581,7 @@ psgld_status launch_part_step(psgld_ctx *c, int64_t t, const int64_t *t_dev, int
         Us.n_rows = n_rows;
         if (dense && c->dense_kind == 2) {
             Us.sh = s == 0 ? c->Wsh : c->Hsh;
-            Us.sh_tiles = s == 0 ? c->mt_max : c->nt_max;
+            Us.sh_tiles = 2 * (s == 0 ? c->mt_max : c->nt_max);
         }
         Us.partial = L.partial;
         Us.base = base;

@@ -302,13 +302,24 @@ def oracle_rate(m, wl, t0: int, n_steps: int):
 
 
 def cpu_baseline(wl, i, j, v, W0, H0, seed, budget_s: float):
+    """The oracle on the host cores (OpenMP over the blocks of a part), then
+    single-threaded on a quarter of the budget; both give identical results."""
+    import oracle
     m = oracle_setup(wl, i, j, v, W0, H0, seed)
+    cores = oracle.set_threads(0)
     _, _, dt1 = oracle_rate(m, wl, 1, 1)          # calibration (untimed)
     n = max(1, min(wl["B"] * 200, int(budget_s / max(dt1, 1e-6))))
     rate, ent, dt = oracle_rate(m, wl, 2, n)
-    return {"value": rate, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
+    oracle.set_threads(1)
+    _, _, dt1s = oracle_rate(m, wl, 2 + n, 1)
+    n1 = max(1, min(wl["B"] * 50, int(budget_s / 4 / max(dt1s, 1e-6))))
+    rate1, ent1, dts = oracle_rate(m, wl, 3 + n, n1)
+    oracle.set_threads(cores)
+    return {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{n} part-steps ({ent} observed entries, {dt:.1f} s) of the same "
-                      f"workload and data, FP64, OpenMP over the blocks of each part"}
+                      f"workload and data, FP64, OpenMP over the blocks of each part",
+            "single_thread": {"value": rate1, "unit": UNIT, "cores": 1,
+                              "sample": f"{n1} part-steps ({ent1} entries, {dts:.1f} s)"}}
 
 
 def cpu_baseline_block(wl, V, W0, H0, seed, budget_s: float):

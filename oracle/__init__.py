@@ -75,6 +75,7 @@ def lib():
             "or_log_lik_part": (f64, [vp, i64]),
             "or_log_post": (f64, [vp]),
             "or_rmse": (f64, [vp, i32]),
+            "or_set_threads": (i32, [i32]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -82,6 +83,11 @@ def lib():
             fn.argtypes = args
         _lib = L
     return _lib
+
+
+def set_threads(n: int) -> int:
+    """Threads the oracle uses for the blocks of a part (n <= 0: query)."""
+    return int(lib().or_set_threads(int(n)))
 
 
 def _p(a: np.ndarray):

@@ -36,6 +36,9 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 struct or_model {
     int64_t I, J;
@@ -410,6 +413,17 @@ void or_part_step(or_model *m, int64_t t)
 }
 
 int64_t or_iterations_done(const or_model *m) { return m->t_done; }
+
+int32_t or_set_threads(int32_t n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
 
 int or_sweep(or_model *m, int32_t n)
 {

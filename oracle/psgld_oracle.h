@@ -86,6 +86,9 @@ void or_part_step(or_model *m, int64_t t);
  * every sweep past burn-in.  Returns 0, or -1 if not at a boundary. */
 int or_sweep(or_model *m, int32_t n);
 int64_t or_iterations_done(const or_model *m);
+/* Threads for the blocks of a part (OpenMP); results do not depend on it.
+ * n <= 0 only queries.  Returns the number now in use. */
+int32_t or_set_threads(int32_t n);
 
 /* ---- posterior summaries and diagnostics --------------------------------- */
 void or_posterior(const or_model *m, double *Wmean, double *Wvar,

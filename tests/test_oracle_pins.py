@@ -466,3 +466,24 @@ def test_chain_samples_closed_form_gaussian_posterior():
         assert np.all(np.abs(mean[i] - mu) < 3 * se_mean[i] + 1e-12), (mean[i], mu, se_mean[i])
         assert np.all(np.abs(second[i] - want_second) < 3 * se_second[i]), \
             (second[i], want_second, se_second[i])
+
+
+def test_results_do_not_depend_on_thread_count():
+    """The blocks of a part write disjoint rows, so OpenMP over blocks gives
+    bit-identical chains for any number of threads (the CPU baseline times
+    both)."""
+    I, J, K, B = 90, 70, 6, 5
+    i, j, v = datagen.sparse_ratings(I, J, 2500, 3, seed=11)
+    W0, H0 = datagen.init_factors(I, J, K, seed=11, scale=0.3, nonneg=False)
+    out = []
+    before = oracle.set_threads(0)
+    for threads in (1, 4):
+        oracle.set_threads(threads)
+        m = oracle.Oracle(I, J, K, B, 0.0, 1.0, prior_kind=oracle.PRIOR_GAUSSIAN)
+        m.set_options(seed=5, eps=1e-3)
+        m.set_data(i, j, v.astype(np.float64))
+        m.set_factors(W0.astype(np.float64), H0.astype(np.float64))
+        m.sweep(3)
+        out.append(m.get_factors())
+    oracle.set_threads(before)
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])

@@ -224,29 +224,18 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
                  :: "r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar)) : "memory");
 }
 
-template <int S, int NG, int E>
-__global__ void __launch_bounds__(kGradThreads) grad_kernel(const __grid_constant__ GradParams P)
+// One unit (E consecutive entries of side SID's part order) on one warp; SID
+// is a template parameter so that the side's fields are fixed parameter
+// offsets.
+template <int SID, int S, int NG, int E>
+__device__ __forceinline__ void grad_unit(const GradParams &P, int64_t u, float *ys, float *es, int *ow,
+                                          uint64_t *bar)
 {
     constexpr int R = 32 / S;      // sub-teams per warp
     constexpr int NGP = S * NG;    // float4 groups a sub-team covers (>= ngroups)
-    extern __shared__ float4 smem4[];
-    const int warp = threadIdx.x >> 5, lane32 = threadIdx.x & 31;
+    const int lane32 = threadIdx.x & 31;
     const int ng = P.ngroups, ldk = P.ldk, lds = P.lds;
-    constexpr int kWarpsPerCta = kGradThreads / 32;
-    float *base = reinterpret_cast<float *>(smem4);
-    float *ys = base + (size_t)warp * E * lds;                      // E gathered rows
-    float *es = base + (size_t)kWarpsPerCta * E * lds + warp * E;   // e of each entry
-    int *ow = reinterpret_cast<int *>(base + (size_t)kWarpsPerCta * E * lds + kWarpsPerCta * E) + warp * E;
-    uint64_t *bar = reinterpret_cast<uint64_t *>(base + (size_t)kWarpsPerCta * (E * lds + 2 * E)) + warp;
-
-    int64_t u = (int64_t)blockIdx.x * kWarpsPerCta + warp;
-    int sid = 0;
-    if (u >= P.side[0].units) {
-        u -= P.side[0].units;
-        sid = 1;
-        if (u >= P.side[1].units) return;   // warp-uniform
-    }
-    const GradSide &Sd = P.side[sid];
+    const GradSide &Sd = P.side[SID];
     const int64_t e0 = Sd.base + u * E;
     const int n = (int)(Sd.n - u * E < E ? Sd.n - u * E : E);
 
@@ -370,6 +359,28 @@ __global__ void __launch_bounds__(kGradThreads) grad_kernel(const __grid_constan
     }
 }
 
+template <int S, int NG, int E>
+__global__ void __launch_bounds__(kGradThreads) grad_kernel(const __grid_constant__ GradParams P)
+{
+    extern __shared__ float4 smem4[];
+    const int warp = threadIdx.x >> 5;
+    const int lds = P.lds;
+    constexpr int kWarpsPerCta = kGradThreads / 32;
+    float *base = reinterpret_cast<float *>(smem4);
+    float *ys = base + (size_t)warp * E * lds;                      // E gathered rows
+    float *es = base + (size_t)kWarpsPerCta * E * lds + warp * E;   // e of each entry
+    int *ow = reinterpret_cast<int *>(base + (size_t)kWarpsPerCta * E * lds + kWarpsPerCta * E) + warp * E;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(base + (size_t)kWarpsPerCta * (E * lds + 2 * E)) + warp;
+
+    int64_t u = (int64_t)blockIdx.x * kWarpsPerCta + warp;
+    if (u < P.side[0].units) {
+        grad_unit<0, S, NG, E>(P, u, ys, es, ow, bar);
+    } else {
+        u -= P.side[0].units;
+        if (u < P.side[1].units) grad_unit<1, S, NG, E>(P, u, ys, es, ow, bar);   // warp-uniform
+    }
+}
+
 // ---- kernel 2: the Langevin update --------------------------------------
 
 // Philox4x32-10 (Salmon et al., SC'11) with the round keys precomputed on the
@@ -395,6 +406,61 @@ __device__ __forceinline__ float update1(const UpdParams &P, const UpdSide &Sd, 
     return P.mirror ? fabsf(y) : y;
 }
 
+// One (row, float4 group) item of factor SID (0 = W, 1 = H^T); SID is a
+// template parameter so that the side's fields are fixed parameter offsets.
+template <int SID>
+__device__ __forceinline__ void update_item(const UpdParams &P, int64_t item, float eps, float sd,
+                                            uint32_t t_lo, uint32_t t_hi)
+{
+    const UpdSide &Sd = P.side[SID];
+    const int ng = P.ngroups, ldk = P.ldk;
+    const int64_t row = P.div_magic ? (int64_t)__umulhi((uint32_t)item, P.div_magic) : item / ng;
+    const int q = (int)(item - row * ng);
+    const int64_t off = row * ldk + 4 * q;
+    const float4 x = ldg4(Sd.X_cur + off);
+    // this row's gradient.  Dense path: G, or the sum in M-tile order of
+    // the block's partial arrays.  Sparse path: nothing (no entries), G
+    // (entries within one unit), or its first unit's tail slot plus the
+    // later units' head slots.
+    float4 g = zero4();
+    if (Sd.gparts > 0) {
+        g = ldg4(Sd.Gin + off);
+        for (int h = 1; h < Sd.gparts; ++h) add4(g, ldg4(Sd.Gin + h * Sd.gstride + off));
+    } else {
+        const int64_t p0 = __ldg(Sd.ptr + row) - Sd.base, p1 = __ldg(Sd.ptr + row + 1) - Sd.base;
+        if (p1 > p0) {
+            const int64_t u0 = p0 >> P.unit_shift, u1 = (p1 - 1) >> P.unit_shift;
+            if (u0 == u1) {
+                g = ldg4(Sd.Gin + off);
+            } else {
+                g = __ldcg(reinterpret_cast<const float4 *>(Sd.partial + (2 * u0 + 1) * ldk + 4 * q));
+                const float *hp = Sd.partial + 4 * q;
+                int64_t uu = u0 + 1;
+                for (; uu + 8 <= u1 + 1; uu += 8) {   // eight independent loads in flight
+                    float4 v[8];
+#pragma unroll
+                    for (int w = 0; w < 8; ++w)
+                        v[w] = __ldcg(reinterpret_cast<const float4 *>(hp + 2 * (uu + w) * ldk));
+#pragma unroll
+                    for (int w = 0; w < 8; ++w) add4(g, v[w]);
+                }
+                for (; uu <= u1; ++uu)
+                    add4(g, __ldcg(reinterpret_cast<const float4 *>(hp + 2 * uu * ldk)));
+            }
+        }
+    }
+    const uint4 r = philox(make_uint4((uint32_t)q, (uint32_t)row, t_lo, (t_hi << 1) | (uint32_t)SID), P);
+    const float4 z = dev::box_muller4(r);
+    const int k0 = 4 * q;
+    float4 o;
+    o.x = update1(P, Sd, x.x, g.x, z.x, eps, sd);
+    o.y = k0 + 1 < P.K ? update1(P, Sd, x.y, g.y, z.y, eps, sd) : 0.f;
+    o.z = k0 + 2 < P.K ? update1(P, Sd, x.z, g.z, z.z, eps, sd) : 0.f;
+    o.w = k0 + 3 < P.K ? update1(P, Sd, x.w, g.w, z.w, eps, sd) : 0.f;
+    *reinterpret_cast<float4 *>(Sd.X_next + off) = o;
+    if (Sd.sh) dev::shadow_store4(Sd.sh, row, k0, o, Sd.n_rows, P.B, Sd.sh_tiles, P.sh_kp);
+}
+
 __global__ void __launch_bounds__(kThreads) update_kernel(const __grid_constant__ UpdParams P)
 {
     const int64_t t = P.t_dev ? *P.t_dev + P.t_add : P.t_add;
@@ -405,59 +471,12 @@ __global__ void __launch_bounds__(kThreads) update_kernel(const __grid_constant_
         sd = (float)sqrt(2.0 * e);
     }
     const uint32_t t_lo = (uint32_t)(uint64_t)t, t_hi = (uint32_t)((uint64_t)t >> 32);
-    const int ng = P.ngroups, ldk = P.ldk;
-    const int64_t n0 = P.side[0].items, total = n0 + P.side[1].items;
-    for (int64_t a = blockIdx.x * (int64_t)kThreads + threadIdx.x; a < total;
-         a += (int64_t)gridDim.x * kThreads) {
-        const int sid = a < n0 ? 0 : 1;
-        const UpdSide &Sd = P.side[sid];
-        const int64_t item = a - (sid ? n0 : 0);
-        const int64_t row = P.div_magic ? (int64_t)__umulhi((uint32_t)item, P.div_magic) : item / ng;
-        const int q = (int)(item - row * ng);
-        const int64_t off = row * ldk + 4 * q;
-        const float4 x = ldg4(Sd.X_cur + off);
-        // this row's gradient.  Dense path: G, or the sum in M-tile order of
-        // the block's partial arrays.  Sparse path: nothing (no entries), G
-        // (entries within one unit), or its first unit's tail slot plus the
-        // later units' head slots.
-        float4 g = zero4();
-        if (Sd.gparts > 0) {
-            g = ldg4(Sd.Gin + off);
-            for (int h = 1; h < Sd.gparts; ++h) add4(g, ldg4(Sd.Gin + h * Sd.gstride + off));
-        } else {
-            const int64_t p0 = __ldg(Sd.ptr + row) - Sd.base, p1 = __ldg(Sd.ptr + row + 1) - Sd.base;
-            if (p1 > p0) {
-                const int64_t u0 = p0 >> P.unit_shift, u1 = (p1 - 1) >> P.unit_shift;
-                if (u0 == u1) {
-                    g = ldg4(Sd.Gin + off);
-                } else {
-                    g = __ldcg(reinterpret_cast<const float4 *>(Sd.partial + (2 * u0 + 1) * ldk + 4 * q));
-                    const float *hp = Sd.partial + 4 * q;
-                    int64_t uu = u0 + 1;
-                    for (; uu + 8 <= u1 + 1; uu += 8) {   // eight independent loads in flight
-                        float4 v[8];
-#pragma unroll
-                        for (int w = 0; w < 8; ++w)
-                            v[w] = __ldcg(reinterpret_cast<const float4 *>(hp + 2 * (uu + w) * ldk));
-#pragma unroll
-                        for (int w = 0; w < 8; ++w) add4(g, v[w]);
-                    }
-                    for (; uu <= u1; ++uu)
-                        add4(g, __ldcg(reinterpret_cast<const float4 *>(hp + 2 * uu * ldk)));
-                }
-            }
-        }
-        const uint4 r = philox(make_uint4((uint32_t)q, (uint32_t)row, t_lo, (t_hi << 1) | Sd.mat), P);
-        const float4 z = dev::box_muller4(r);
-        const int k0 = 4 * q;
-        float4 o;
-        o.x = update1(P, Sd, x.x, g.x, z.x, eps, sd);
-        o.y = k0 + 1 < P.K ? update1(P, Sd, x.y, g.y, z.y, eps, sd) : 0.f;
-        o.z = k0 + 2 < P.K ? update1(P, Sd, x.z, g.z, z.z, eps, sd) : 0.f;
-        o.w = k0 + 3 < P.K ? update1(P, Sd, x.w, g.w, z.w, eps, sd) : 0.f;
-        *reinterpret_cast<float4 *>(Sd.X_next + off) = o;
-        if (Sd.sh) dev::shadow_store4(Sd.sh, row, k0, o, Sd.n_rows, P.B, Sd.sh_tiles, P.sh_kp);
-    }
+    // the flat item sequence: W items, then H^T items
+    const int64_t n0 = P.side[0].items, n1 = P.side[1].items;
+    const int64_t stride = (int64_t)gridDim.x * kThreads;
+    int64_t a = blockIdx.x * (int64_t)kThreads + threadIdx.x;
+    for (; a < n0; a += stride) update_item<0>(P, a, eps, sd, t_lo, t_hi);
+    for (a -= n0; a < n1; a += stride) update_item<1>(P, a, eps, sd, t_lo, t_hi);
 }
 
 using GradFn = void (*)(GradParams);

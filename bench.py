@@ -471,6 +471,10 @@ def run_ours(args, wl_name, wl):
         "rmse_after": rmse,
     }
 
+    if tensor_path(wl) and args.compare_sweeps > 0:
+        chain.close()
+        torch.cuda.empty_cache()
+        result["precision_compare"] = compare_precision(wl, seed, dev, v, W0, H0, args.compare_sweeps)
     if not args.no_e2e:
         result["e2e"] = e2e_job(wl, seed, dev, i, j, v, W0, H0)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -488,6 +492,37 @@ def run_ours(args, wl_name, wl):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def compare_precision(wl, seed, dev, V, W0, H0, sweeps: int):
+    """BF16 tensor-core path vs the FP32 gather path on the same dense V,
+    initial factors, Philox key and number of sweeps: observed entries/s per
+    sweep (CUDA events around the sweeps) and the posterior-mean
+    reconstruction RMSE over the second half of the sweeps, for both."""
+    import torch
+    out = {"sweeps": sweeps, "burn_in_sweeps": sweeps // 2}
+    N = int(V.numel())
+    for name, opts in (("bf16_tensor_core", {}), ("fp32_gather", {"dense_path": 0, "dense_v_bf16": 0})):
+        ch = new_chain(wl, seed, use_graphs=1, burn_in_sweeps=sweeps // 2, **opts)
+        ch.set_data_dense(V)
+        ch.set_factors(torch.from_numpy(W0).to(dev), torch.from_numpy(H0.T.copy()).to(dev))
+        stream = torch.cuda.current_stream(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        a.record(stream)
+        ch.sweep(sweeps)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = a.elapsed_time(b)
+        out[name] = {"value": N * sweeps / (ms / 1e3), "unit": UNIT, "ms_per_sweep": ms / sweeps,
+                     "posterior_mean_rmse": ch.rmse(True)}
+        ch.close()
+        torch.cuda.empty_cache()
+    r16 = out["bf16_tensor_core"]["posterior_mean_rmse"]
+    r32 = out["fp32_gather"]["posterior_mean_rmse"]
+    out["rmse_rel_diff"] = abs(r16 - r32) / r32
+    out["speedup"] = out["bf16_tensor_core"]["value"] / out["fp32_gather"]["value"]
+    return out
 
 
 def e2e_job(wl, seed, dev, i, j, v, W0, H0):
@@ -608,6 +643,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--compare-sweeps", type=int, default=20,
+                    help="tensor-core workloads: sweeps of the BF16 vs FP32 comparison (0 = off)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0,
                     help="seconds of oracle work for the cpu_baseline sample")

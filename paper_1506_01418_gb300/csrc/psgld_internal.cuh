@@ -220,8 +220,9 @@ __device__ __forceinline__ float4 box_muller4(uint4 x)
 __device__ __forceinline__ void shadow_store4(uint16_t *sh, int64_t row, int k0, float4 v, int64_t n,
                                               int B, int tiles, int KP)
 {
-    const int64_t piece = ((row + 1) * B - 1) / n;
-    const int64_t rr = row - (piece * n) / B;
+    // 32-bit arithmetic: rows and B * n are below 2^31 (checked at create)
+    const uint32_t piece = ((uint32_t)(row + 1) * (uint32_t)B - 1u) / (uint32_t)n;
+    const int64_t rr = row - (int64_t)((piece * (uint32_t)n) / (uint32_t)B);
     const int rho = (int)(rr & 63);
     const int kk = k0 & 63, c = kk >> 3;
     const int64_t off = (piece * tiles + (rr >> 6)) * 64 * KP + (int64_t)(k0 >> 6) * 4096 +

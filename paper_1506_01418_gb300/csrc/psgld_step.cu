@@ -461,7 +461,7 @@ __device__ __forceinline__ void update_item(const UpdParams &P, int64_t item, fl
     if (Sd.sh) dev::shadow_store4(Sd.sh, row, k0, o, Sd.n_rows, P.B, Sd.sh_tiles, P.sh_kp);
 }
 
-__global__ void __launch_bounds__(kThreads) update_kernel(const __grid_constant__ UpdParams P)
+__global__ void __launch_bounds__(kThreads, 5) update_kernel(const __grid_constant__ UpdParams P)
 {
     const int64_t t = P.t_dev ? *P.t_dev + P.t_add : P.t_add;
     float eps = P.eps, sd = P.sd;

@@ -99,11 +99,20 @@ typedef struct {
                                * 2: on, two-sided kernel (K <= 256);
                                * 3: on, single-pass kernel (K <= 128, FP32 V) */
     int32_t dense_v_bf16;     /* 1: the two-sided kernel keeps V in BF16 */
+    int32_t part_mode;        /* 0: cyclic part order, part (t-1) mod B at iteration t
+                               * (Sec. 4.1); 1: at every iteration part s with
+                               * probability |Pi_s| / N (condition C2, Sec. 3.1),
+                               * drawn from the Philox stream of the seed with the
+                               * counter (0, 0xFFFFFFFF, t_lo, 2 t_hi): with x the
+                               * 64-bit number (word 1, word 0), r = floor(x N /
+                               * 2^64) and s is the part whose range of the running
+                               * sum of part sizes (parts 0 .. B-1) holds r.  Sweeps
+                               * then run without CUDA graphs. */
 } psgld_options;
 
 /* Defaults: seed 0, fixed eps 1e-4, a = 0.01, b = 0.51, scale N/|Pi_t|,
  * mu_min 1e-10, nothing frozen, no burn-in, graphs on, profiling off,
- * dense_path off. */
+ * dense_path off, cyclic parts. */
 PSGLD_API void psgld_default_options(psgld_options *opt_host);
 
 /* Create a context on the current CUDA device.
@@ -183,7 +192,8 @@ PSGLD_API psgld_status psgld_rmse(psgld_ctx *ctx, int32_t use_posterior_mean,
 PSGLD_API psgld_status psgld_piece_bounds(const psgld_ctx *ctx, int64_t *row_starts_host,
                                 int64_t *col_starts_host);
 /* Part of iteration t (Definition 2): col_piece_host[r] is the column piece
- * joined with row piece r, r = 0..B-1. */
+ * joined with row piece r, r = 0..B-1.  With part_mode = 1 the part depends
+ * on the data's part sizes: PSGLD_ERR_STATE before data is set. */
 PSGLD_API psgld_status psgld_part_schedule(const psgld_ctx *ctx, int64_t t,
                                  int32_t *col_piece_host);
 /* Row-major layout of part s (0 <= s < B): row_ptr_host[0..I] offsets
@@ -197,7 +207,9 @@ PSGLD_API psgld_status psgld_part_layout(psgld_ctx *ctx, int32_t s, int32_t *row
  * *launches_host their count.  Events are recorded on the launch stream
  * around each part-step kernel, also inside captured sweep graphs; each
  * iteration of a part owns one event pair, so read after every call that
- * runs at most B iterations (one sweep) for complete figures.  Synchronises
+ * runs at most B iterations (one sweep) for complete figures (with
+ * part_mode = 1 a part can recur within a sweep: read after every
+ * part-step).  Synchronises
  * the context's last stream. */
 PSGLD_API psgld_status psgld_profile_read(psgld_ctx *ctx, double *total_ms_host,
                                           int64_t *launches_host);

@@ -76,6 +76,8 @@ def lib():
             "or_log_post": (f64, [vp]),
             "or_rmse": (f64, [vp, i32]),
             "or_set_threads": (i32, [i32]),
+            "or_set_part_mode": (None, [vp, i32]),
+            "or_part_index": (i32, [vp, i64]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -160,6 +162,13 @@ class Oracle:
                              float(eps_a), float(eps_b), int(scale_mode),
                              float(mu_min), int(bool(freeze_W)),
                              int(bool(freeze_H)), int(burn_in))
+
+    def set_part_mode(self, mode):
+        """0: cyclic part order (Sec. 4.1); 1: size-proportional draw (C2)."""
+        lib().or_set_part_mode(self._h, int(mode))
+
+    def part_index(self, t):
+        return int(lib().or_part_index(self._h, int(t)))
 
     def set_data(self, i, j, v):
         i = np.ascontiguousarray(i, dtype=np.int32)

@@ -51,6 +51,7 @@ struct or_model {
     int32_t eps_mode;
     double eps, eps_a, eps_b;
     int32_t scale_mode;
+    int32_t part_mode;        /* 0: cyclic order; 1: size-proportional draw (C2) */
     double mu_min;
     int32_t freeze_W, freeze_H;
     int64_t burn_in;
@@ -225,14 +226,53 @@ int64_t or_block_entries(const or_model *m, int32_t r, int32_t c, int64_t cap,
 }
 
 /* |Pi_t|: observed entries in the B blocks of the part used at iteration t */
-int64_t or_part_size(const or_model *m, int64_t t)
+/* Observed entries of part s (blocks (r, (r + s) mod B), Definition 2). */
+static int64_t part_entries(const or_model *m, int32_t s)
 {
     int64_t n = 0;
     for (int32_t r = 0; r < m->B; ++r) {
-        int64_t b = (int64_t)r * m->B + or_part_col_piece(t, m->B, r);
+        int64_t b = (int64_t)r * m->B + (r + s) % m->B;
         n += m->blk_ptr[b + 1] - m->blk_ptr[b];
     }
     return n;
+}
+
+void or_set_part_mode(or_model *m, int32_t mode) { m->part_mode = mode; }
+
+/* The part used at iteration t.  Cyclic: s = (t - 1) mod B (Sec. 4.1).
+ * Size-proportional (condition C2 of Sec. 3.1): part s with probability
+ * |Pi_s| / N, drawn independently at every t from the Philox stream keyed by
+ * the seed, counter (0, 0xFFFFFFFF, t_lo, 2 t_hi) -- a counter no noise draw
+ * uses (their second word is a row index below 2^31).  With x the 64-bit
+ * number (word 1, word 0) of the draw, r = floor(x N / 2^64) is uniform on
+ * [0, N) up to 2^-64, and s is the part whose range of the running sum of
+ * part sizes (parts in order 0 .. B-1) holds r. */
+int32_t or_part_index(const or_model *m, int64_t t)
+{
+    if (m->part_mode == 0 || m->N == 0) return (int32_t)((t - 1) % m->B);
+    const uint32_t ctr[4] = {0u, 0xFFFFFFFFu, (uint32_t)(uint64_t)t,
+                             (uint32_t)((uint64_t)t >> 32) << 1};
+    const uint32_t key[2] = {(uint32_t)m->seed, (uint32_t)(m->seed >> 32)};
+    uint32_t x[4];
+    or_philox4x32_10(ctr, key, x);
+    const uint64_t x64 = ((uint64_t)x[1] << 32) | x[0];
+    const uint64_t r = (uint64_t)(((unsigned __int128)x64 * (uint64_t)m->N) >> 64);
+    uint64_t cum = 0;
+    for (int32_t s = 0; s < m->B; ++s) {
+        cum += (uint64_t)part_entries(m, s);
+        if (r < cum) return s;
+    }
+    return m->B - 1;
+}
+
+static int32_t col_piece(const or_model *m, int64_t t, int32_t r)
+{
+    return (r + or_part_index(m, t)) % m->B;
+}
+
+int64_t or_part_size(const or_model *m, int64_t t)
+{
+    return part_entries(m, or_part_index(m, t));
 }
 
 /* ------------------------------------------------------------------------ */
@@ -345,7 +385,7 @@ void or_drift(const or_model *m, int64_t t, double *dW, double *dH)
      * and no columns, so they write disjoint parts of dW and dH) */
 #pragma omp parallel for schedule(dynamic, 1)
     for (int32_t r = 0; r < B; ++r) {
-        int32_t c = or_part_col_piece(t, B, r);
+        int32_t c = col_piece(m, t, r);
         int64_t b = (int64_t)r * B + c;
         for (int64_t n = m->blk_ptr[b]; n < m->blk_ptr[b + 1]; ++n) {
             int64_t i = m->ent_i[n], j = m->ent_j[n];
@@ -506,7 +546,7 @@ double or_log_lik_part(const or_model *m, int64_t t)
 {
     double s = 0.0;
     for (int32_t r = 0; r < m->B; ++r) {
-        int64_t b = (int64_t)r * m->B + or_part_col_piece(t, m->B, r);
+        int64_t b = (int64_t)r * m->B + col_piece(m, t, r);
         s += log_lik_range(m, m->blk_ptr[b], m->blk_ptr[b + 1]);
     }
     return s;

@@ -62,6 +62,11 @@ int32_t or_part_col_piece(int64_t t, int32_t B, int32_t r);
 int64_t or_block_entries(const or_model *m, int32_t r, int32_t c, int64_t cap,
                          int32_t *i_out, int32_t *j_out);
 int64_t or_part_size(const or_model *m, int64_t t);
+/* Part order: 0 cyclic (Sec. 4.1, the default), 1 size-proportional random
+ * choice at every iteration (condition C2 of Sec. 3.1). */
+void or_set_part_mode(or_model *m, int32_t mode);
+/* Index s of the part used at iteration t (its blocks are (r, (r+s) mod B)). */
+int32_t or_part_index(const or_model *m, int64_t t);
 
 /* ---- random numbers ------------------------------------------------------ */
 /* Philox4x32-10 (Salmon et al., SC'11). */

@@ -30,6 +30,40 @@ psgld_status cuda_fail(psgld_ctx *c, cudaError_t e, const char *what)
     return fail(c, PSGLD_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
+// Philox4x32-10 on the host (Salmon et al., SC'11): ten rounds of the two
+// 32 x 32 -> 64-bit products, key bumped by the Weyl constants.
+static void host_philox(const uint32_t ctr[4], uint64_t seed, uint32_t out[4])
+{
+    uint32_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+    uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+        const uint64_t p0 = (uint64_t)0xD2511F53u * x0, p1 = (uint64_t)0xCD9E8D57u * x2;
+        const uint32_t y0 = (uint32_t)(p1 >> 32) ^ x1 ^ k0, y2 = (uint32_t)(p0 >> 32) ^ x3 ^ k1;
+        x0 = y0; x1 = (uint32_t)p1; x2 = y2; x3 = (uint32_t)p0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+int part_of_iteration(const psgld_ctx *c, int64_t t)
+{
+    const int B = c->B;
+    if (c->opt.part_mode == 0 || c->N == 0 || (int)c->part_n.size() != B)
+        return (int)((t - 1) % B);
+    const uint32_t ctr[4] = {0u, 0xFFFFFFFFu, (uint32_t)(uint64_t)t, (uint32_t)((uint64_t)t >> 32) << 1};
+    uint32_t x[4];
+    host_philox(ctr, c->opt.seed, x);
+    const uint64_t x64 = ((uint64_t)x[1] << 32) | x[0];
+    const uint64_t r = (uint64_t)(((unsigned __int128)x64 * (uint64_t)c->N) >> 64);
+    uint64_t cum = 0;
+    for (int s = 0; s < B; ++s) {
+        cum += (uint64_t)c->part_n[s];
+        if (r < cum) return s;
+    }
+    return B - 1;
+}
+
 psgld_status check_kernel_flag(psgld_ctx *c)
 {
     int h = 0;
@@ -265,6 +299,7 @@ psgld_status psgld_set_options(psgld_ctx *c, const psgld_options *o)
     if (!(o->mu_min > 0.0)) return fail(c, PSGLD_ERR_ARG, "mu_min must be > 0");
     if (o->burn_in_sweeps < 0) return fail(c, PSGLD_ERR_ARG, "burn_in_sweeps must be >= 0");
     if (o->dense_path < 0 || o->dense_path > 3) return fail(c, PSGLD_ERR_ARG, "dense_path must be 0..3");
+    if (o->part_mode != 0 && o->part_mode != 1) return fail(c, PSGLD_ERR_ARG, "part_mode must be 0 or 1");
     c->opt = *o;
     destroy_graphs(c);
     destroy_events(c);
@@ -485,13 +520,14 @@ psgld_status psgld_sweep(psgld_ctx *c, int32_t n_sweeps, void *stream)
     cudaStream_t st = (cudaStream_t)stream;
     c->last_stream = st;
     if (n_sweeps == 0) return PSGLD_OK;
-    if (c->opt.use_graphs) {
+    const bool graphs = c->opt.use_graphs && c->opt.part_mode == 0;
+    if (graphs) {
         set_t_kernel<<<1, 32, 0, st>>>(c->t_dev, c->t_done);
         PSGLD_CK(c, cudaGetLastError());
     }
     for (int32_t n = 0; n < n_sweeps; ++n) {
         const bool acc = c->sweeps_done >= c->opt.burn_in_sweeps;
-        if (c->opt.use_graphs) {
+        if (graphs) {
             cudaGraphExec_t &g = acc ? c->graph_acc[c->wcur * 2 + c->hcur] : c->graph[c->wcur][c->hcur];
             if (!g) {
                 s = capture_sweep(c, acc, &g);
@@ -584,7 +620,8 @@ psgld_status psgld_piece_bounds(const psgld_ctx *c, int64_t *rs, int64_t *cs)
 psgld_status psgld_part_schedule(const psgld_ctx *c, int64_t t, int32_t *col_piece)
 {
     if (!c || !col_piece || t < 1) return PSGLD_ERR_ARG;
-    const int64_t s = (t - 1) % c->B;
+    if (c->opt.part_mode == 1 && !c->has_data) return PSGLD_ERR_STATE;
+    const int64_t s = part_of_iteration(c, t);
     for (int r = 0; r < c->B; ++r) col_piece[r] = (int32_t)((r + s) % c->B);
     return PSGLD_OK;
 }

@@ -129,6 +129,11 @@ psgld_status build_layout(psgld_ctx *c, int64_t nnz, const int32_t *i_dev,
                           cudaStream_t st);
 void free_layout(psgld_ctx *c);
 
+// ---- part schedule (psgld_api.cu) ------------------------------------------
+// Index s of the part used at iteration t (blocks (r, (r + s) mod B)):
+// cyclic, or the size-proportional draw of part_mode 1.
+int part_of_iteration(const psgld_ctx *c, int64_t t);
+
 // ---- part-step (psgld_step.cu) --------------------------------------------
 // Enqueue iteration t.  When t_dev is non-null the kernels read t from
 // *t_dev + t_add instead (used inside captured graphs); `t` then only

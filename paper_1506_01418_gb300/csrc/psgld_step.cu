@@ -557,7 +557,7 @@ psgld_status launch_part_step(psgld_ctx *c, int64_t t, const int64_t *t_dev, int
                               cudaStream_t st)
 {
     const int B = c->B;
-    const int part = (int)((t - 1) % B);
+    const int part = part_of_iteration(c, t);
     const Shape sh = shape_for(c->ngroups);
     GradFn gfn = pick_grad(sh);
     if (!gfn) return fail(c, PSGLD_ERR_ARG, "unsupported K");

@@ -242,3 +242,27 @@ def test_invalid_inputs_are_rejected():
     c.part_step(2)
     c.sweep(1)
     assert c.iterations_done == 4
+
+
+def test_size_proportional_parts_match_oracle():
+    """part_mode = 1 (condition C2): the part drawn at every iteration is the
+    oracle's, bit for bit, and part-steps and a sweep follow it."""
+    pr = _make("gamma_K13", part_mode=1)
+    pr.orc.set_part_mode(1)
+    B = pr.B
+    for t in list(range(1, 301)) + [(1 << 32) + 5]:
+        cp = P.psgld_part_schedule(pr.gpu.ctx, t, B)
+        s = pr.orc.part_index(t)
+        assert list(cp) == [(r + s) % B for r in range(B)], t
+    seen = set()
+    for t in range(1, 3 * B + 1):
+        seen.add(pr.orc.part_index(t))
+        (Wg, Hg), (Wo, Ho) = pr.step_both(t)
+        assert rel_err(Wg, Wo) <= STEP_RTOL and rel_err(Hg, Ho) <= STEP_RTOL, t
+        pr.sync_oracle_to_gpu()
+    assert len(seen) > 1
+    pr.gpu.sweep(2)
+    pr.orc.sweep(2)
+    Wg, Hg = pr.gpu_factors()
+    Wo, Ho = pr.orc.get_factors()
+    assert rel_err(Wg, Wo) < 1e-4 and rel_err(Hg, Ho) < 1e-4

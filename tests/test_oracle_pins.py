@@ -487,3 +487,82 @@ def test_results_do_not_depend_on_thread_count():
         out.append(m.get_factors())
     oracle.set_threads(before)
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
+def _uneven_parts_model(seed=3):
+    """B = 4 with very unequal part sizes: a dense diagonal band adds entries
+    to the blocks of part 0 only."""
+    I, J, K, B = 80, 80, 3, 4
+    i, j, v = datagen.sparse_ratings(I, J, 800, 3, seed=seed)
+    pairs = set(zip(i.tolist(), j.tolist()))
+    extra = [(a, b) for a in range(I) for b in range(J)
+             if oracle.piece_of(a, I, B) == oracle.piece_of(b, J, B) and (a, b) not in pairs][:1200]
+    i = np.concatenate([i, np.array([a for a, _ in extra], np.int32)])
+    j = np.concatenate([j, np.array([b for _, b in extra], np.int32)])
+    v = np.concatenate([v, np.full(len(extra), 3.0, np.float32)])
+    m = oracle.Oracle(I, J, K, B, 0.0, 1.0, prior_kind=oracle.PRIOR_GAUSSIAN)
+    m.set_options(seed=seed, eps=1e-3)
+    m.set_data(i, j, v.astype(np.float64))
+    return m, B
+
+
+def test_size_proportional_parts_follow_part_sizes():
+    """Condition C2 (Sec. 3.1): part s is drawn with probability |Pi_s| / N,
+    independently at every iteration.  Pinned by a chi-square test of the
+    draw frequencies against the part sizes counted by brute force, with
+    parts of very different sizes; the cyclic mode keeps (t-1) mod B."""
+    m, B = _uneven_parts_model()
+    sizes = np.array([m.part_size(s + 1) for s in range(B)], dtype=np.float64)   # cyclic: t = s+1
+    assert [m.part_index(t) for t in range(1, 9)] == [(t - 1) % B for t in range(1, 9)]
+    m.set_part_mode(1)
+    T = 40000
+    draws = np.array([m.part_index(t) for t in range(1, T + 1)])
+    counts = np.bincount(draws, minlength=B)
+    expected = T * sizes / sizes.sum()
+    assert sizes.max() > 2 * sizes.min()           # the parts really differ
+    chi2 = float(((counts - expected) ** 2 / expected).sum())
+    assert stats.chi2.sf(chi2, B - 1) > 1e-4, (counts, expected)
+    # deterministic in (seed, t); a different seed gives a different stream
+    assert [m.part_index(t) for t in (5, 77, 1 << 33)] == [m.part_index(t) for t in (5, 77, 1 << 33)]
+    m2, _ = _uneven_parts_model()
+    m2.set_options(seed=4, eps=1e-3)
+    m2.set_part_mode(1)
+    assert [m2.part_index(t) for t in range(1, 200)] != draws[:199].tolist()
+
+
+def test_size_proportional_parts_make_the_scaled_gradient_unbiased():
+    """Under C2 the expected scaled part gradient is the full-data gradient:
+    sum_s (|Pi_s| / N) * (N / |Pi_s|) grad_s = sum_s grad_s.  Checked with the
+    oracle's drifts of each part (prior removed) against a B = 1 drift on the
+    same data."""
+    m, B = _uneven_parts_model()
+    I, J, K = 80, 80, 3
+    W0, H0 = datagen.init_factors(I, J, K, seed=9, scale=0.3, nonneg=False)
+    m.set_factors(W0.astype(np.float64), H0.astype(np.float64))
+    N = sum(m.part_size(s + 1) for s in range(B))
+    prior_W = -W0.astype(np.float64)               # Gaussian prior sigma = 1
+    prior_H = -H0.astype(np.float64)
+    EW = np.zeros((I, K)); EH = np.zeros((K, J))
+    for s in range(B):
+        dW, dH = m.drift(s + 1)                    # cyclic mode: part s at t = s + 1
+        p_s = m.part_size(s + 1) / N
+        EW += p_s * (dW - prior_W)
+        EH += p_s * (dH - prior_H)
+    full = oracle.Oracle(I, J, K, 1, 0.0, 1.0, prior_kind=oracle.PRIOR_GAUSSIAN)
+    full.set_options(seed=3, eps=1e-3)
+    mm, _ = _uneven_parts_model()
+    # the same entries: read them back block by block from the B = 4 model
+    ii, jj = [], []
+    for r in range(B):
+        for c in range(B):
+            bi, bj = mm.block_entries(r, c)
+            ii.append(bi); jj.append(bj)
+    ii = np.concatenate(ii); jj = np.concatenate(jj)
+    i0, j0, v0 = datagen.sparse_ratings(I, J, 800, 3, seed=3)
+    lut = {(a, b): x for a, b, x in zip(i0.tolist(), j0.tolist(), v0.tolist())}
+    vv = np.array([lut.get((a, b), 3.0) for a, b in zip(ii.tolist(), jj.tolist())])
+    full.set_data(ii.astype(np.int32), jj.astype(np.int32), vv)
+    full.set_factors(W0.astype(np.float64), H0.astype(np.float64))
+    fW, fH = full.drift(1)
+    np.testing.assert_allclose(EW, fW - prior_W, rtol=1e-10, atol=1e-10)
+    np.testing.assert_allclose(EH, fH - prior_H, rtol=1e-10, atol=1e-10)

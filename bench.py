@@ -55,6 +55,12 @@ WORKLOADS = {
     "dense_poisson_256x256_K8_B4": dict(
         I=256, J=256, nnz=256 * 256, K=8, B=4, p=1.0, phi=1.0, prior="exponential",
         lam=1.0, K_true=8, eps=1e-4, init_scale=1.0, job_sweeps=1000, dense=True),
+    # the standing chain's 2048 x 2048, K = 256 blocks at a size that an ncu
+    # capture handles (B = 2: 64 items of the same size)
+    "dense_poisson_4096x4096_K256_B2_bf16": dict(
+        I=4096, J=4096, nnz=4096 * 4096, K=256, B=2, p=1.0, phi=1.0, prior="exponential",
+        lam=1.0, K_true=16, eps=2e-5, init_scale=0.25, job_sweeps=200, dense=True,
+        device_gen=True, dense_path=2, dense_v_bf16=1),
     # the standing dense chain: tensor-core block chain, BF16 operands and V
     "dense_poisson_32768x32768_K256_B16_bf16": dict(
         I=32768, J=32768, nnz=32768 * 32768, K=256, B=16, p=1.0, phi=1.0, prior="exponential",
@@ -247,20 +253,23 @@ def read_peaks():
 
 
 def kernel_traffic(workload: str):
-    """DRAM bytes per part-step launch from the committed ncu summary, only if
-    the kernel source is unchanged since the counters were taken."""
+    """DRAM bytes per launch of the roofline's kernel from the committed ncu
+    summary, only if the kernel sources are unchanged since the counters were
+    taken (the record holds the sha256 of each source it depends on)."""
     path = os.path.join(ROOT, "profiles", "part_step_traffic.json")
-    src = os.path.join(ROOT, "paper_1506_01418_gb300", "csrc", "psgld_step.cu")
     try:
         with open(path) as f:
             d = json.load(f)
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()
         e = d.get(workload)
-        if e and e.get("psgld_step_cu_sha256") == h:
-            return float(e["dram_bytes_per_launch"])
+        if not e:
+            return None
+        for name, h in e["sources_sha256"].items():
+            src = os.path.join(ROOT, "paper_1506_01418_gb300", "csrc", name)
+            if hashlib.sha256(open(src, "rb").read()).hexdigest() != h:
+                return None
+        return float(e["dram_bytes_per_launch"])
     except (OSError, ValueError, KeyError):
-        pass
-    return None
+        return None
 
 
 def host_cores() -> int:
@@ -436,7 +445,7 @@ def run_ours(args, wl_name, wl):
         flops = part_step_flops(wl)
         achieved = flops / (grad_ms / 1e3) / 1e12
         roofline = {"bound": "tensor", "achieved": achieved, "peak": tc_peak, "unit": "TFLOP/s",
-                    "frac": achieved / tc_peak, "traffic": None,
+                    "frac": achieved / tc_peak, "traffic": kernel_traffic(wl_name),
                     "kernel": "two_sided::chain_kernel", "kernel_ms": grad_ms,
                     "algorithmic_flops_per_launch": flops,
                     "update_kernel_ms": upd_ms, "part_step_ms": kern_ms,

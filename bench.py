@@ -67,6 +67,13 @@ WORKLOADS = {
         lam=1.0, K_true=16, eps=2e-5, init_scale=0.25, job_sweeps=200, dense=True,
         device_gen=True, dense_path=2, dense_v_bf16=1),
 }
+# the serving configuration: Poisson arrivals of dense non-negative jobs
+# (I in {257, 513, 1025}, J log-uniform on [500, 20000], p in {1, 1.5},
+# K in {16, 64}, B = 8, 20 sweeps each) beside the standing chain
+WORKLOADS["serving_poisson200_mixed_jobs_with_standing_chain"] = dict(
+    serving=True, rate=200.0, duration=3.0, sweeps=20, burn_in=10, B=8, eps=1e-4,
+    budget_bytes=64 << 30, standing="dense_poisson_32768x32768_K256_B16_bf16",
+    I=0, J=0, K=0, p=1.0)
 DEFAULT_WORKLOAD = "sparse_gauss_70000x10000_nnz10M_K50_B32"
 
 
@@ -581,6 +588,95 @@ def e2e_job(wl, seed, dev, i, j, v, W0, H0):
 # reference arm: the oracle on the host cores
 # ---------------------------------------------------------------------------
 
+def run_serving(args, wl_name, wl):
+    """The serving loop on one GPU: a Poisson trace of jobs replayed in real
+    time; value = observed entries x sweeps of every job and of the standing
+    chain / wall time of the trace; latency = completion - arrival."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1506_01418_gb300 import serving
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    ex = serving.GpuExecutor(0)
+    factory = serving.mixed_job_factory(wl["sweeps"], wl["burn_in"], wl["B"], wl["eps"])
+    # warm-up: one job of each size class (module loads, graph captures)
+    warm = []
+    for k, (I, K, p) in enumerate([(I, K, p) for I in (257, 513, 1025) for K in (16, 64) for p in (1.0, 1.5)]):
+        j = factory(10_000 + k, 0.0, np.random.Generator(np.random.Philox(k)))
+        j.I, j.K, j.p, j.J = I, K, p, 800
+        warm.append(j)
+    wsrv = serving.Server(ex, wl["budget_bytes"])
+    try:
+        wsrv.run(warm, idle_sleep=0)
+    finally:
+        wsrv.close()
+    jobs = serving.poisson_trace(wl["rate"], wl["duration"], seed=2024, job_factory=factory)
+    srv = serving.Server(ex, wl["budget_bytes"])
+    standing = None
+    if wl.get("standing"):
+        sw = WORKLOADS[wl["standing"]]
+        standing = serving.Job(job_id=-1, I=sw["I"], J=sw["J"], K=sw["K"], B=sw["B"], p=sw["p"],
+                               sweeps=None, burn_in=0, seed=7, eps=sw["eps"], init_scale=sw["init_scale"],
+                               dense_path=sw["dense_path"], dense_v_bf16=sw["dense_v_bf16"])
+        srv.submit(standing)
+        srv.poll(0.0)
+        torch.cuda.synchronize(dev)
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+        uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+    except Exception:
+        uuid = "0"
+    sampler = ClockSampler(uuid)
+    w0 = time.time()
+    st0 = None
+    if standing is not None:
+        st0 = srv.active[-1][1]["sweeps_queued"]
+    try:
+        wall = srv.run(jobs, idle_sleep=0)
+        st_sweeps = (srv.active[-1][1]["sweeps_queued"] - st0) if standing is not None else 0
+        w1 = time.time()
+        srv.stop_standing()
+    finally:
+        srv.close()
+    torch.cuda.synchronize(dev)
+    time.sleep(0.25)
+    sampler.stop()
+    lat = serving.latency_summary(jobs)
+    job_entries = sum(j.I * j.J * j.sweeps for j in jobs)
+    st_entries = (standing.I * standing.J * st_sweeps) if standing is not None else 0
+    value = (job_entries + st_entries) / wall
+    h2d = sum(4 * (j.I + j.J) * j.K for j in jobs)
+    d2h = sum(8 * (j.I + j.J) * j.K * 2 for j in jobs)
+    result = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": len(jobs),
+        "warmup": len(warm), "ms_per_step": wall * 1e3 / max(1, len(jobs)), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": wl_name, "arrival_rate_per_s": wl["rate"], "trace_s": wl["duration"],
+                   "jobs": len(jobs), "sweeps_per_job": wl["sweeps"], "B": wl["B"],
+                   "hbm_budget_bytes": wl["budget_bytes"], "standing_chain": wl.get("standing"),
+                   "step": "one job of the trace (value counts every job's and the standing "
+                           "chain's entries x sweeps over the trace's wall time)",
+                   "path": "tensor-core block chain per job (dense_path 1), own stream and context "
+                           "per job, PyTorch caching allocator"},
+        "latency": lat,
+        "job_entries_per_s": job_entries / wall,
+        "standing_chain": {"sweeps": st_sweeps, "entries_per_s": st_entries / wall} if standing else None,
+        "peak_budget_used_bytes": srv.peak_used,
+        "roofline": None,
+        "gpu_launches": sum(j.sweeps * (2 * j.B + 3) for j in jobs) + st_sweeps * (2 * 16 + 3),
+        "clocks": sampler.summary(w0, w1),
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": h2d / max(1, len(jobs)),
+                "d2h_bytes_per_step": d2h / max(1, len(jobs)),
+                "note": "the serving loop is the end-to-end path: each job's initial factors go "
+                        "host to device and its posterior means device to host inside the trace"},
+    }
+    print(json.dumps(result), flush=True)
+
+
 def run_reference(args, wl_name, wl):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -664,7 +760,13 @@ def main():
         ap.error("--warmup must be >= 3")
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":
+        if wl.get("serving"):
+            print(json.dumps({"impl": "reference", "unavailable": "the serving workload has no "
+                              "oracle counterpart (the oracle is a CPU chain, not a server)"}))
+            return
         run_reference(args, args.workload, wl)
+    elif wl.get("serving"):
+        run_serving(args, args.workload, wl)
     else:
         run_ours(args, args.workload, wl)
 

@@ -38,6 +38,7 @@
 #ifndef PSGLD_H
 #define PSGLD_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #if defined(__GNUC__)
@@ -109,6 +110,24 @@ typedef struct {
                                * sum of part sizes (parts 0 .. B-1) holds r.  Sweeps
                                * then run without CUDA graphs. */
 } psgld_options;
+
+/* Device memory.  By default the library allocates with cudaMalloc and frees
+ * with cudaFree (which waits for the whole device).  A caller that runs many
+ * contexts side by side on streams (a serving loop) can hand in its own
+ * allocator instead: alloc returns `bytes` of device memory of the current
+ * device, aligned to at least 256 bytes, or NULL; `stream` is the stream of
+ * the call that allocates (NULL for psgld_create); free returns memory that
+ * alloc gave.  The library frees a buffer only after the work that uses it has
+ * finished.  Contexts created after the call use the allocator (each keeps a
+ * copy); NULL restores cudaMalloc / cudaFree.  Not thread-safe with concurrent
+ * psgld_create calls. */
+typedef struct {
+    void *(*alloc)(size_t bytes, void *stream, void *user);
+    void (*free)(void *ptr, void *stream, void *user);
+    void *user;
+} psgld_allocator;
+
+PSGLD_API psgld_status psgld_set_allocator(const psgld_allocator *allocator_host);
 
 /* Defaults: seed 0, fixed eps 1e-4, a = 0.01, b = 0.51, scale N/|Pi_t|,
  * mu_min 1e-10, nothing frozen, no burn-in, graphs on, profiling off,
@@ -221,6 +240,15 @@ PSGLD_API psgld_status psgld_profile_read_split(psgld_ctx *ctx, double *grad_ms_
 
 /* Last completed iteration t (0 before the first). */
 PSGLD_API int64_t psgld_iterations_done(const psgld_ctx *ctx);
+
+/* Device bytes a context holds once its data is set (psgld_create plus
+ * psgld_set_data_*; scratch that those calls free before returning is not
+ * counted), for a scheduler that admits work against a memory budget.
+ * nnz: observed entries (ignored when dense_path > 0, where V is I x J).
+ * -1 on invalid sizes.  Needs no GPU. */
+PSGLD_API int64_t psgld_estimate_device_bytes(int64_t I, int64_t J, int32_t K, int32_t B,
+                                              int64_t nnz, int32_t dense_path,
+                                              int32_t dense_v_bf16);
 
 /* ---- log-likelihood without allocation ----------------------------------
  * No counterpart in the paper: a convenience for callers that cannot

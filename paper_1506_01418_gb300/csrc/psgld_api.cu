@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "psgld_internal.cuh"
@@ -17,6 +18,31 @@
 namespace psgld {
 
 int reduce_blocks();
+
+namespace {
+std::mutex g_alloc_mutex;
+psgld_allocator g_allocator{};
+bool g_has_allocator = false;
+}  // namespace
+
+void *dev_alloc(psgld_ctx *c, size_t bytes, cudaStream_t st)
+{
+    if (bytes == 0) bytes = 256;
+    if (c->has_allocator) return c->allocator.alloc(bytes, (void *)st, c->allocator.user);
+    void *p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void dev_free(psgld_ctx *c, void *p, cudaStream_t st)
+{
+    if (!p) return;
+    if (c->has_allocator) c->allocator.free(p, (void *)st, c->allocator.user);
+    else cudaFree(p);
+}
 
 psgld_status fail(psgld_ctx *c, psgld_status s, const std::string &msg)
 {
@@ -70,7 +96,14 @@ psgld_status check_kernel_flag(psgld_ctx *c)
     PSGLD_CK(c, cudaMemcpy(&h, c->kflag, sizeof(int), cudaMemcpyDeviceToHost));
     if (h == 0) return PSGLD_OK;
     PSGLD_CK(c, cudaMemset(c->kflag, 0, sizeof(int)));
-    return fail(c, PSGLD_ERR_TIMEOUT, "a bulk-copy wait in the part-step kernel ran out");
+    std::string where;
+    if (h & 16) where += " sparse gradient kernel (row gathers);";
+    if (h & 32) where += " single-pass dense kernel (MMA completion);";
+    if (h & 64) where += " two-sided dense kernel";
+    if (h & 128) where += " (producer: free slot)";
+    if (h & 256) where += " (MMA warp: data or epilogue)";
+    if (h & 512) where += " (epilogue: data or MMA)";
+    return fail(c, PSGLD_ERR_TIMEOUT, "a bounded wait in a part-step kernel ran out:" + where);
 }
 
 namespace {
@@ -147,17 +180,14 @@ psgld_status zero_posterior(psgld_ctx *c, cudaStream_t st)
     return PSGLD_OK;
 }
 
+// Zero-filled (when asked) on `st`, in stream order with the work that uses it.
 template <typename T>
-psgld_status alloc(psgld_ctx *c, T **p, int64_t n, bool zero = true)
+psgld_status alloc(psgld_ctx *c, T **p, int64_t n, bool zero = true, cudaStream_t st = nullptr)
 {
     if (n <= 0) n = 1;
-    cudaError_t e = cudaMalloc((void **)p, sizeof(T) * (size_t)n);
-    if (e != cudaSuccess) {
-        *p = nullptr;
-        cudaGetLastError();
-        return fail(c, PSGLD_ERR_OOM, "device allocation failed");
-    }
-    if (zero) PSGLD_CK(c, cudaMemset(*p, 0, sizeof(T) * (size_t)n));
+    *p = static_cast<T *>(dev_alloc(c, sizeof(T) * (size_t)n, st));
+    if (!*p) return fail(c, PSGLD_ERR_OOM, "device allocation failed");
+    if (zero) PSGLD_CK(c, cudaMemsetAsync(*p, 0, sizeof(T) * (size_t)n, st));
     return PSGLD_OK;
 }
 
@@ -236,6 +266,11 @@ psgld_status psgld_create(int64_t I, int64_t J, int32_t K, int32_t B, double twe
     }
     psgld_ctx *c = new (std::nothrow) psgld_ctx();
     if (!c) return PSGLD_ERR_OOM;
+    {
+        std::lock_guard<std::mutex> lock(g_alloc_mutex);
+        c->allocator = g_allocator;
+        c->has_allocator = g_has_allocator;
+    }
     c->I = I; c->J = J; c->K = K; c->B = B;
     c->ngroups = (K + 3) / 4;
     c->ldk = 4 * c->ngroups;
@@ -246,24 +281,29 @@ psgld_status psgld_create(int64_t I, int64_t J, int32_t K, int32_t B, double twe
     psgld_default_options(&c->opt);
     cudaGetDevice(&c->device);
     psgld_status s = PSGLD_OK;
-    for (int b = 0; b < 2 && s == PSGLD_OK; ++b) {
-        s = alloc(c, &c->W[b], I * c->ldk);
-        if (s == PSGLD_OK) s = alloc(c, &c->Ht[b], J * c->ldk);
-    }
-    if (s == PSGLD_OK) s = alloc(c, &c->G, (I + J) * c->ldk);
-    if (s == PSGLD_OK) s = alloc(c, &c->sW.s, I * c->ldk);
-    if (s == PSGLD_OK) s = alloc(c, &c->sW.s2, I * c->ldk);
-    if (s == PSGLD_OK) s = alloc(c, &c->sH.s, J * c->ldk);
-    if (s == PSGLD_OK) s = alloc(c, &c->sH.s2, J * c->ldk);
-    if (s == PSGLD_OK) s = alloc(c, &c->red, reduce_blocks());
-    if (s == PSGLD_OK) s = alloc(c, &c->flag, 1);
-    if (s == PSGLD_OK) s = alloc(c, &c->kflag, 1);
-    if (s == PSGLD_OK) s = prepare_kernels(c);
-    if (s == PSGLD_OK) s = alloc(c, &c->t_dev, 1);
-    if (s == PSGLD_OK && cudaMallocHost((void **)&c->red_host, sizeof(double) * reduce_blocks()) != cudaSuccess)
-        s = fail(c, PSGLD_ERR_OOM, "pinned allocation failed");
-    if (s == PSGLD_OK && cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking) != cudaSuccess)
+    // the context's own stream first: the zero fills run on it, in order, and
+    // are waited for below (a caller's non-blocking stream is not ordered
+    // after the legacy stream)
+    if (cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking) != cudaSuccess)
         s = fail(c, PSGLD_ERR_CUDA, "stream creation failed");
+    cudaStream_t zs = c->capture_stream;
+    for (int b = 0; b < 2 && s == PSGLD_OK; ++b) {
+        s = alloc(c, &c->W[b], I * c->ldk, true, zs);
+        if (s == PSGLD_OK) s = alloc(c, &c->Ht[b], J * c->ldk, true, zs);
+    }
+    if (s == PSGLD_OK) s = alloc(c, &c->G, (I + J) * c->ldk, true, zs);
+    if (s == PSGLD_OK) s = alloc(c, &c->sW.s, I * c->ldk, true, zs);
+    if (s == PSGLD_OK) s = alloc(c, &c->sW.s2, I * c->ldk, true, zs);
+    if (s == PSGLD_OK) s = alloc(c, &c->sH.s, J * c->ldk, true, zs);
+    if (s == PSGLD_OK) s = alloc(c, &c->sH.s2, J * c->ldk, true, zs);
+    if (s == PSGLD_OK) s = alloc(c, &c->red, reduce_blocks(), true, zs);
+    if (s == PSGLD_OK) s = alloc(c, &c->flag, 1, true, zs);
+    if (s == PSGLD_OK) s = alloc(c, &c->kflag, 1, true, zs);
+    if (s == PSGLD_OK) s = prepare_kernels(c);
+    if (s == PSGLD_OK) s = alloc(c, &c->t_dev, 1, true, zs);
+    if (s == PSGLD_OK) c->red_host.assign(reduce_blocks(), 0.0);
+    if (s == PSGLD_OK && cudaStreamSynchronize(zs) != cudaSuccess)
+        s = fail(c, PSGLD_ERR_CUDA, "zero fill failed");
     if (s != PSGLD_OK) {
         psgld_destroy(c);
         cudaGetLastError();
@@ -365,9 +405,9 @@ psgld_status psgld_set_data_coo(psgld_ctx *c, int64_t nnz, const int32_t *i, con
     destroy_graphs(c);
     int32_t *di = nullptr, *dj = nullptr;
     float *dv = nullptr;
-    psgld_status s = alloc(c, &di, nnz, false);
-    if (s == PSGLD_OK) s = alloc(c, &dj, nnz, false);
-    if (s == PSGLD_OK) s = alloc(c, &dv, nnz, false);
+    psgld_status s = alloc(c, &di, nnz, false, st);
+    if (s == PSGLD_OK) s = alloc(c, &dj, nnz, false, st);
+    if (s == PSGLD_OK) s = alloc(c, &dv, nnz, false, st);
     if (s == PSGLD_OK && nnz > 0) {
         cudaError_t e = cudaMemcpyAsync(di, i, sizeof(int32_t) * nnz, cudaMemcpyDefault, st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(dj, j, sizeof(int32_t) * nnz, cudaMemcpyDefault, st);
@@ -380,7 +420,7 @@ psgld_status psgld_set_data_coo(psgld_ctx *c, int64_t nnz, const int32_t *i, con
         cudaError_t e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) s = cuda_fail(c, e, "sync");
     }
-    cudaFree(di); cudaFree(dj); cudaFree(dv);
+    dev_free(c, di); dev_free(c, dj); dev_free(c, dv);
     return s;
 }
 
@@ -394,7 +434,7 @@ psgld_status psgld_set_data_dense(psgld_ctx *c, const float *V, int64_t ld, void
         if (!dense_supported(c->K)) return fail(c, PSGLD_ERR_ARG, "dense tensor-core path supports K <= 256");
         destroy_graphs(c);
         free_layout(c);
-        psgld_status s = alloc(c, &c->Vd, n, false);
+        psgld_status s = alloc(c, &c->Vd, n, false, st);
         c->ldv = c->J;
         if (s == PSGLD_OK) {
             cudaError_t e = cudaMemcpy2DAsync(c->Vd, sizeof(float) * c->J, V, sizeof(float) * ld,
@@ -402,9 +442,9 @@ psgld_status psgld_set_data_dense(psgld_ctx *c, const float *V, int64_t ld, void
             if (e != cudaSuccess) s = cuda_fail(c, e, "copy V");
         }
         if (s == PSGLD_OK) s = check_values(c, c->Vd, n, st);
-        if (s == PSGLD_OK) s = prepare_dense(c);
+        if (s == PSGLD_OK) s = prepare_dense(c, st);
         if (s == PSGLD_OK && c->dense_kind == 1 && c->mtiles > 1)
-            s = alloc(c, &c->hpart, (int64_t)c->mtiles * c->J * c->ldk);
+            s = alloc(c, &c->hpart, (int64_t)c->mtiles * c->J * c->ldk, true, st);
         if (s == PSGLD_OK) s = build_dense_tiles(c, st);
         if (s != PSGLD_OK) { free_layout(c); return s; }
         // every entry observed: N = I J, |Pi_s| = sum_b |R_b| |C_(b+s) mod B|
@@ -430,10 +470,10 @@ psgld_status psgld_set_data_dense(psgld_ctx *c, const float *V, int64_t ld, void
     if (n >= (1ll << 31)) return fail(c, PSGLD_ERR_ARG, "I*J too large for the entry layout");
     float *dV = nullptr, *dv = nullptr;
     int32_t *di = nullptr, *dj = nullptr;
-    psgld_status s = alloc(c, &dV, c->I * c->J, false);
-    if (s == PSGLD_OK) s = alloc(c, &di, n, false);
-    if (s == PSGLD_OK) s = alloc(c, &dj, n, false);
-    if (s == PSGLD_OK) s = alloc(c, &dv, n, false);
+    psgld_status s = alloc(c, &dV, c->I * c->J, false, st);
+    if (s == PSGLD_OK) s = alloc(c, &di, n, false, st);
+    if (s == PSGLD_OK) s = alloc(c, &dj, n, false, st);
+    if (s == PSGLD_OK) s = alloc(c, &dv, n, false, st);
     if (s == PSGLD_OK) {
         cudaError_t e = cudaMemcpy2DAsync(dV, sizeof(float) * c->J, V, sizeof(float) * ld,
                                           sizeof(float) * c->J, c->I, cudaMemcpyDefault, st);
@@ -445,7 +485,12 @@ psgld_status psgld_set_data_dense(psgld_ctx *c, const float *V, int64_t ld, void
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) s = cuda_fail(c, e, "dense_to_coo");
     }
-    cudaFree(dV);
+    if (s == PSGLD_OK) {
+        // dV is read by dense_to_coo on st; free it after that work
+        cudaError_t e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) s = cuda_fail(c, e, "sync");
+    }
+    dev_free(c, dV, st);
     dV = nullptr;
     if (s == PSGLD_OK) {
         // psgld_set_data_coo copies again; build directly instead
@@ -457,7 +502,7 @@ psgld_status psgld_set_data_dense(psgld_ctx *c, const float *V, int64_t ld, void
             if (e != cudaSuccess) s = cuda_fail(c, e, "sync");
         }
     }
-    cudaFree(di); cudaFree(dj); cudaFree(dv);
+    dev_free(c, di); dev_free(c, dj); dev_free(c, dv);
     return s;
 }
 
@@ -646,6 +691,48 @@ psgld_status psgld_part_layout(psgld_ctx *c, int32_t s, int32_t *row_ptr, int32_
 
 int64_t psgld_iterations_done(const psgld_ctx *c) { return c ? c->t_done : -1; }
 
+psgld_status psgld_set_allocator(const psgld_allocator *a)
+{
+    if (a && (!a->alloc || !a->free)) return PSGLD_ERR_ARG;
+    std::lock_guard<std::mutex> lock(g_alloc_mutex);
+    g_has_allocator = a != nullptr;
+    g_allocator = a ? *a : psgld_allocator{};
+    return PSGLD_OK;
+}
+
+int64_t psgld_estimate_device_bytes(int64_t I, int64_t J, int32_t K, int32_t B, int64_t nnz,
+                                    int32_t dense_path, int32_t dense_v_bf16)
+{
+    if (I < 1 || J < 1 || K < 1 || K > kMaxK || B < 1 || B > std::min(I, J) || nnz < 0) return -1;
+    const int64_t ldk = 4 * ((K + 3) / 4);
+    auto cdiv = [](int64_t a, int64_t b) { return (a + b - 1) / b; };
+    int64_t bytes = 0;
+    // psgld_create: W, Ht (two buffers each), G, FP64 posterior sums, reduction slots
+    bytes += 2 * (I + J) * ldk * 4 + (I + J) * ldk * 4 + 2 * (I + J) * ldk * 8 + reduce_blocks() * 8 + 64;
+    if (dense_path == 0) {
+        // the two part-major entry layouts and their partial-sum slots
+        const int unit = unit_entries((K + 3) / 4);
+        for (int side = 0; side < 2; ++side) {
+            const int64_t n_rows = side == 0 ? I : J;
+            bytes += (B * n_rows + 1) * 4 + nnz * 12 + 2 * (cdiv(nnz, unit) + B) * ldk * 4;
+        }
+        return bytes;
+    }
+    bytes += I * J * 4;   // the FP32 copy of V
+    const int64_t maxI = cdiv(I, B), maxJ = cdiv(J, B);
+    const int64_t mtiles = cdiv(maxI, 128);
+    const bool two = dense_path == 2 || (dense_path == 1 && (dense_v_bf16 || K > 128 || mtiles > 1));
+    if (!two) {
+        if (mtiles > 1) bytes += mtiles * J * ldk * 4;
+        return bytes;
+    }
+    const int64_t KP = 64 * cdiv(K, 64), vs = dense_v_bf16 ? 2 : 4;
+    const int64_t mt = cdiv(maxI, 128), nt = cdiv(maxJ, 128), ni = cdiv(maxI, 64), nj = cdiv(maxJ, 64);
+    bytes += (int64_t)B * B * (mt * nj + nt * ni) * 8192 * vs;     // V tiles, both orientations
+    bytes += (int64_t)B * 2 * (mt + nt) * 64 * KP * 2;              // BF16 factor shadows
+    return bytes;
+}
+
 const char *psgld_last_error(const psgld_ctx *c) { return c ? c->err.c_str() : "null context"; }
 
 void psgld_destroy(psgld_ctx *c)
@@ -654,11 +741,13 @@ void psgld_destroy(psgld_ctx *c)
     destroy_graphs(c);
     destroy_events(c);
     free_layout(c);
-    for (int b = 0; b < 2; ++b) { cudaFree(c->W[b]); cudaFree(c->Ht[b]); }
-    cudaFree(c->G);
-    cudaFree(c->sW.s); cudaFree(c->sW.s2); cudaFree(c->sH.s); cudaFree(c->sH.s2);
-    cudaFree(c->red); cudaFree(c->flag); cudaFree(c->kflag); cudaFree(c->t_dev);
-    if (c->red_host) cudaFreeHost(c->red_host);
+    // the context's work must be finished before its memory is handed back
+    if (c->last_stream) cudaStreamSynchronize(c->last_stream);
+    if (c->capture_stream) cudaStreamSynchronize(c->capture_stream);
+    for (int b = 0; b < 2; ++b) { dev_free(c, c->W[b]); dev_free(c, c->Ht[b]); }
+    dev_free(c, c->G);
+    dev_free(c, c->sW.s); dev_free(c, c->sW.s2); dev_free(c, c->sH.s); dev_free(c, c->sH.s2);
+    dev_free(c, c->red); dev_free(c, c->flag); dev_free(c, c->kflag); dev_free(c, c->t_dev);
     if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
     delete c;
 }

@@ -394,7 +394,7 @@ __global__ void __launch_bounds__(kDenseThreads, 1) dense_grad_kernel(const __gr
             }
         }
     } else {
-        if (tid == 0) atomicOr(P.err, 16);
+        if (tid == 0) atomicOr(P.err, 32);   // single-pass dense kernel
         bar_wait(bar, phase ^ 1u);   // give in-flight MMAs one more bounded chance
     }
     fence_before();
@@ -594,7 +594,11 @@ __device__ __forceinline__ bool wait32(Bars *S, uint64_t *b, uint32_t parity)
     const bool stop = __any_sync(0xffffffffu, *(volatile int *)&S->abort != 0);
     bool ok = !stop && bar_wait(b, parity);
     ok = __all_sync(0xffffffffu, ok);
-    if (!ok && (threadIdx.x & 31) == 0) *(volatile int *)&S->abort = 1;
+    if (!ok && !stop && (threadIdx.x & 31) == 0) {
+        // the first warp to give up records its role: 128 producer, 256 MMA, 512 epilogue
+        const int warp = threadIdx.x >> 5;
+        atomicOr((int *)&S->abort, warp == 0 ? 128 : warp == 1 ? 256 : 512);
+    }
     return ok;
 }
 
@@ -908,7 +912,7 @@ __global__ void __launch_bounds__(kThreads, 1) chain_kernel(const __grid_constan
     fence_before();
     __syncthreads();
     fence_after();
-    if (threadIdx.x == 0 && S->abort) atomicOr(P.err, 16);
+    if (threadIdx.x == 0 && S->abort) atomicOr(P.err, 64 | S->abort);   // two-sided kernel (+ role)
     if (warp == 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;"
                      :: "r"(tmem), "r"(kTmemCols) : "memory");
@@ -936,9 +940,13 @@ int dense_kp(int K)
     return kp;
 }
 
+// At least half of an SM's shared memory, so that at most one of the
+// library's TMEM-holding CTAs (this kernel's 256 columns, the two-sided
+// kernel's 512) is resident per SM: a tcgen05.alloc that cannot be met
+// blocks, and a CTA holding TMEM beside it must never wait on that.
 size_t dense_smem(int kp)
 {
-    return 2 * (size_t)kTile * kp * 2 + (size_t)kTile * kTile * 2 + 16;
+    return std::max<size_t>(2 * (size_t)kTile * kp * 2 + (size_t)kTile * kTile * 2 + 16, 116 * 1024);
 }
 
 }  // namespace
@@ -1039,7 +1047,7 @@ void two_sided_stages(int KP, int vsize, int *stages, int *vstages)
 
 }  // namespace
 
-psgld_status prepare_dense(psgld_ctx *c)
+psgld_status prepare_dense(psgld_ctx *c, cudaStream_t st)
 {
     const int mode = c->opt.dense_path;
     const bool vb = c->opt.dense_v_bf16 != 0;
@@ -1073,12 +1081,9 @@ psgld_status prepare_dense(psgld_ctx *c)
     const int64_t nA = B * B * c->mt_max * c->nj_max * 8192, nB = B * B * c->nt_max * c->ni_max * 8192;
     const int64_t nW = B * 2 * c->mt_max * 64 * c->KP, nH = B * 2 * c->nt_max * 64 * c->KP;
     auto al = [&](void **p, size_t bytes) -> psgld_status {
-        if (cudaMalloc(p, bytes) != cudaSuccess) {
-            *p = nullptr;
-            cudaGetLastError();
-            return fail(c, PSGLD_ERR_OOM, "device allocation failed");
-        }
-        PSGLD_CK(c, cudaMemset(*p, 0, bytes));
+        *p = dev_alloc(c, bytes, st);
+        if (!*p) return fail(c, PSGLD_ERR_OOM, "device allocation failed");
+        PSGLD_CK(c, cudaMemsetAsync(*p, 0, bytes, st));   // padding stays zero
         return PSGLD_OK;
     };
     psgld_status s = al(&c->VA, (size_t)nA * vs);

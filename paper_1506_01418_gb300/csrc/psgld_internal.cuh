@@ -92,9 +92,13 @@ struct psgld_ctx {
     int64_t sweeps_done = 0;
     int64_t t_done = 0;
 
+    // device memory: the caller's allocator, if one was set at create
+    psgld_allocator allocator{};
+    bool has_allocator = false;
+
     // reductions
-    double *red = nullptr;       // per-CTA partial sums
-    double *red_host = nullptr;  // pinned copy
+    double *red = nullptr;                 // per-CTA partial sums
+    std::vector<double> red_host;          // host copy
     int *flag = nullptr;         // device error flag of the layout build and input checks
     int *kflag = nullptr;        // device error flag of the sampling kernels (16: wait ran out)
     cudaStream_t last_stream = nullptr;
@@ -112,6 +116,12 @@ struct psgld_ctx {
 };
 
 namespace psgld {
+
+// ---- device memory ---------------------------------------------------------
+// Through the context's allocator, or cudaMalloc / cudaFree.  dev_alloc
+// returns nullptr on failure; dev_free(nullptr) does nothing.
+void *dev_alloc(psgld_ctx *c, size_t bytes, cudaStream_t st);
+void dev_free(psgld_ctx *c, void *p, cudaStream_t st = nullptr);
 
 // ---- error plumbing ------------------------------------------------------
 psgld_status fail(psgld_ctx *c, psgld_status s, const std::string &msg);
@@ -156,7 +166,7 @@ bool dense_supported(int K);
 int dense_mtiles(const psgld_ctx *c);
 // Chooses the kernel (options dense_path, dense_v_bf16; K; block sizes),
 // sets its attributes and allocates the two-sided kernel's tiles.
-psgld_status prepare_dense(psgld_ctx *c);
+psgld_status prepare_dense(psgld_ctx *c, cudaStream_t st);
 // V tiles of the two-sided kernel from c->Vd (no-op for the single-pass one).
 psgld_status build_dense_tiles(psgld_ctx *c, cudaStream_t st);
 // BF16 shadows of the current factors (two-sided kernel with factors set).

@@ -278,12 +278,8 @@ psgld_status dmalloc(psgld_ctx *c, T **p, int64_t n)
     // whole 256-byte granules, so that 16-byte-rounded bulk prefetches of any
     // sub-range stay inside the allocation
     const size_t bytes = (sizeof(T) * (size_t)n + 255) & ~size_t(255);
-    cudaError_t e = cudaMalloc((void **)p, bytes);
-    if (e != cudaSuccess) {
-        *p = nullptr;
-        cudaGetLastError();
-        return fail(c, PSGLD_ERR_OOM, "device allocation of " + std::to_string(sizeof(T) * n) + " bytes failed");
-    }
+    *p = static_cast<T *>(dev_alloc(c, bytes, nullptr));
+    if (!*p) return fail(c, PSGLD_ERR_OOM, "device allocation of " + std::to_string(sizeof(T) * n) + " bytes failed");
     return PSGLD_OK;
 }
 
@@ -322,17 +318,20 @@ psgld_status radix_sort(psgld_ctx *c, uint64_t *&k0, uint32_t *&v0, uint64_t *&k
 
 void free_layout(psgld_ctx *c)
 {
+    // work that reads the layouts must be finished before they are handed back
+    cudaStreamSynchronize(c->last_stream);
+    if (c->capture_stream) cudaStreamSynchronize(c->capture_stream);
     for (auto &sd : c->side) {
-        cudaFree(sd.ptr); cudaFree(sd.idx); cudaFree(sd.val); cudaFree(sd.own);
-        cudaFree(sd.partial);
+        dev_free(c, sd.ptr); dev_free(c, sd.idx); dev_free(c, sd.val); dev_free(c, sd.own);
+        dev_free(c, sd.partial);
         sd = SideLayout{};
     }
-    cudaFree(c->Vd);
-    cudaFree(c->hpart);
-    cudaFree(c->VA);
-    cudaFree(c->VB);
-    cudaFree(c->Wsh);
-    cudaFree(c->Hsh);
+    dev_free(c, c->Vd);
+    dev_free(c, c->hpart);
+    dev_free(c, c->VA);
+    dev_free(c, c->VB);
+    dev_free(c, c->Wsh);
+    dev_free(c, c->Hsh);
     c->Vd = nullptr;
     c->hpart = nullptr;
     c->VA = c->VB = nullptr;
@@ -367,7 +366,8 @@ psgld_status build_layout(psgld_ctx *c, int64_t nnz, const int32_t *i_dev, const
     psgld_status s = PSGLD_OK;
     std::vector<void *> scratch;
     auto cleanup = [&]() {
-        for (void *p : scratch) cudaFree(p);
+        cudaStreamSynchronize(st);   // the scratch is in use by work on st
+        for (void *p : scratch) dev_free(c, p, st);
     };
 #define PSGLD_ALLOC(ptr, cnt)                      \
     do {                                           \

@@ -164,7 +164,7 @@ psgld_status reduce_loglik_rmse(psgld_ctx *c, int mode, int use_mean, cudaStream
             c->Ht[c->hcur], use_mean ? c->sW.s : nullptr, use_mean ? c->sH.s : nullptr, inv_n,
             c->p, c->phi, c->opt.mu_min, c->red);
     PSGLD_CK(c, cudaGetLastError());
-    PSGLD_CK(c, cudaMemcpyAsync(c->red_host, c->red, sizeof(double) * kRedBlocks,
+    PSGLD_CK(c, cudaMemcpyAsync(c->red_host.data(), c->red, sizeof(double) * kRedBlocks,
                                 cudaMemcpyDeviceToHost, st));
     PSGLD_CK(c, cudaStreamSynchronize(st));
     {

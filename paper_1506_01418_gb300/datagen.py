@@ -54,6 +54,21 @@ def dense_poisson_device(I: int, J: int, K_true: int, seed: int, device):
     return V
 
 
+def dense_gamma_device(I: int, J: int, K_true: int, seed: int, device):
+    """dense_gamma drawn with torch on a CUDA device: V = |W* H*| * Gamma(2,
+    rate 2) with W*, H* ~ |N(0, 1)|.  Returns V (float32 I x J tensor)."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    Wt = torch.randn((I, K_true), generator=g, device=device).abs_()
+    Ht = torch.randn((K_true, J), generator=g, device=device).abs_()
+    M = Wt @ Ht
+    del Wt, Ht
+    shape = torch.full_like(M, 2.0)
+    noise = torch._standard_gamma(shape, generator=g) / 2.0
+    return (M * noise).contiguous()
+
+
 def dense_gamma(I: int, J: int, K_true: int, seed: int):
     """Dense positive data V = |W* H*| * Gamma(shape 2, rate 2)."""
     g = _rng(seed)

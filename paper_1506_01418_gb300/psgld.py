@@ -11,7 +11,9 @@ current torch CUDA stream.
 """
 from __future__ import annotations
 
+import atexit
 import ctypes as C
+import weakref
 import os
 
 import numpy as np
@@ -50,12 +52,20 @@ class psgld_options(C.Structure):
                 ("dense_v_bf16", C.c_int32), ("part_mode", C.c_int32)]
 
 
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
+
+
+class psgld_allocator(C.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("user", C.c_void_p)]
+
+
 EXPORTS = [
     "psgld_default_options", "psgld_create", "psgld_set_options", "psgld_set_data_coo",
     "psgld_set_data_dense", "psgld_set_factors", "psgld_get_factors", "psgld_part_step",
     "psgld_sweep", "psgld_posterior_mean", "psgld_log_lik", "psgld_rmse", "psgld_piece_bounds",
     "psgld_part_schedule", "psgld_part_layout", "psgld_profile_read", "psgld_profile_read_split",
-    "psgld_iterations_done",
+    "psgld_iterations_done", "psgld_estimate_device_bytes", "psgld_set_allocator",
     "psgld_log_lik_static", "psgld_last_error",
     "psgld_destroy",
 ]
@@ -94,6 +104,8 @@ def load(build_if_missing: bool = True):
         "psgld_part_layout": (st, [vp, i32, vp, vp, vp]),
         "psgld_profile_read": (st, [vp, vp, vp]),
         "psgld_profile_read_split": (st, [vp, vp, vp, vp]),
+        "psgld_estimate_device_bytes": (i64, [i64, i64, i32, i32, i64, i32, i32]),
+        "psgld_set_allocator": (st, [C.POINTER(psgld_allocator)]),
         "psgld_iterations_done": (i64, [vp]),
         "psgld_log_lik_static": (st, [i64, vp, vp, vp, vp, vp, i64, i64, i32, f64, f64, f64, vp, vp]),
         "psgld_last_error": (C.c_char_p, [vp]),
@@ -256,6 +268,55 @@ def psgld_profile_read(ctx):
     return ms.value, n.value
 
 
+# Every allocator handed to the library stays alive for the whole process:
+# contexts keep a copy of its function pointers and call them when they free
+# memory, possibly long after another allocator (or none) was set.
+_allocator_keepalive = []
+
+
+def psgld_set_allocator(alloc_fn=None, free_fn=None):
+    """Device memory for contexts created from now on: alloc_fn(bytes, stream)
+    -> device pointer (int) or 0, free_fn(ptr, stream); None restores
+    cudaMalloc / cudaFree (contexts created before keep what they had)."""
+    if alloc_fn is None:
+        _check(None, load().psgld_set_allocator(None))
+        return
+
+    def _a(nbytes, stream, user):
+        try:
+            return int(alloc_fn(int(nbytes), stream)) or None
+        except Exception:
+            return None
+
+    def _f(ptr, stream, user):
+        free_fn(int(ptr), stream)
+
+    a = psgld_allocator(ALLOC_FN(_a), FREE_FN(_f), None)
+    _allocator_keepalive.append((a, _a, _f))
+    _check(None, load().psgld_set_allocator(C.byref(a)))
+
+
+def use_torch_allocator(device=None):
+    """Hand the library PyTorch's caching allocator (no device-wide wait when
+    a context frees its memory)."""
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+
+    def alloc_fn(nbytes, stream):
+        return torch.cuda.caching_allocator_alloc(nbytes, dev)
+
+    def free_fn(ptr, stream):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    psgld_set_allocator(alloc_fn, free_fn)
+
+
+def psgld_estimate_device_bytes(I, J, K, B, nnz=0, dense_path=0, dense_v_bf16=0):
+    """Device bytes a context of these sizes holds once its data is set."""
+    return int(load().psgld_estimate_device_bytes(int(I), int(J), int(K), int(B), int(nnz),
+                                                   int(dense_path), int(dense_v_bf16)))
+
+
 def psgld_profile_read_split(ctx):
     """(gradient-kernel ms, update-kernel ms, number of part-steps) since the last read."""
     g = C.c_double(0.0)
@@ -297,6 +358,20 @@ def psgld_destroy(ctx):
 # convenience wrapper (still marshalling only)
 # ---------------------------------------------------------------------------
 
+_live_chains = weakref.WeakSet()
+
+
+@atexit.register
+def _close_live_chains():
+    """Destroy the contexts still open at interpreter exit, while the
+    allocator callbacks they may call can still run."""
+    for ch in list(_live_chains):
+        try:
+            ch.close()
+        except Exception:
+            pass
+
+
 class PSGLD:
     """One PSGLD chain held by a library context."""
 
@@ -306,6 +381,7 @@ class PSGLD:
         pr = psgld_prior(int(prior_kind), float(lambda_w), float(lambda_h), float(sigma_w),
                          float(sigma_h))
         self.ctx = psgld_create(I, J, K, B, tweedie_p, phi, pr)
+        _live_chains.add(self)
         self.options = psgld_default_options()
         if options:
             self.set_options(**options)

@@ -1,0 +1,256 @@
+"""Serving loop: factorisation jobs admitted continuously under an HBM budget.
+
+Each request is one dense non-negative factorisation job (a spectrogram-like
+V of its own size, Tweedie power, rank K and number of sweeps).  The server
+admits waiting jobs in arrival order whenever the device memory they will
+hold (`psgld_estimate_device_bytes`) fits in what the budget has left and a
+slot is free; an admitted job gets its own CUDA stream and library context,
+its data and initial factors are put on the device, and all its sweeps are
+enqueued at once, so jobs that arrive while others run overlap with them on
+the device.  The loop only polls completion events; a finished job's
+posterior means are read back and its context (and memory, through the
+caching allocator) released, which lets the next jobs in.  A standing chain
+(a job without an end) can share the device: the loop keeps one sweep of it
+queued at all times.
+
+The scheduler (`Server`) is separate from the executor that touches the GPU,
+so its admission and accounting logic runs on the CPU with a stand-in
+executor.  Latency of a job = completion time - arrival time on the host
+clock.
+"""
+from __future__ import annotations
+
+import collections
+import dataclasses
+import math
+import time
+from typing import Callable, Optional
+
+import numpy as np
+
+
+@dataclasses.dataclass
+class Job:
+    """One factorisation request."""
+    job_id: int
+    I: int
+    J: int
+    K: int
+    B: int
+    p: float
+    phi: float = 1.0
+    sweeps: Optional[int] = 20         # None: a standing chain that never ends
+    burn_in: int = 10
+    seed: int = 0
+    eps: float = 1e-4
+    lam: float = 1.0
+    init_scale: float = 0.5
+    dense_path: int = 1
+    dense_v_bf16: int = 0
+    arrival: float = 0.0               # seconds from the start of the trace
+    data_seed: int = 0
+    # filled in by the server
+    admitted: Optional[float] = None
+    finished: Optional[float] = None
+    result: Optional[dict] = None
+
+    @property
+    def entries(self) -> int:
+        return self.I * self.J
+
+
+class Server:
+    """Admission and accounting; `executor` does the device work.
+
+    executor.estimate(job) -> bytes the job will hold on the device
+    executor.start(job) -> handle          (enqueues all of the job's work)
+    executor.done(handle) -> bool          (non-blocking)
+    executor.finish(job, handle) -> dict   (results; frees the job's memory)
+    executor.step_standing(job, handle)    (keep a standing chain's sweep queued)
+    """
+
+    def __init__(self, executor, hbm_budget: int, max_active: int = 64):
+        self.ex = executor
+        self.budget = int(hbm_budget)
+        self.max_active = int(max_active)
+        self.waiting: collections.deque = collections.deque()
+        self.active: dict = {}               # job_id -> (job, handle, bytes)
+        self.done: list = []
+        self.used = 0
+        self.peak_used = 0
+
+    def submit(self, job: Job):
+        self.waiting.append(job)
+
+    def poll(self, now: float):
+        """Finish completed jobs, then admit waiting jobs in order while they
+        fit.  Returns the jobs finished in this call."""
+        finished = []
+        for jid in list(self.active):
+            job, h, nbytes = self.active[jid]
+            if job.sweeps is None:
+                self.ex.step_standing(job, h)
+                continue
+            if self.ex.done(h):
+                job.result = self.ex.finish(job, h)
+                job.finished = now
+                del self.active[jid]
+                self.used -= nbytes
+                self.done.append(job)
+                finished.append(job)
+        while self.waiting and len(self.active) < self.max_active:
+            job = self.waiting[0]
+            nbytes = int(self.ex.estimate(job))
+            if nbytes > self.budget:
+                raise ValueError(f"job {job.job_id} needs {nbytes} bytes, more than the whole budget")
+            if self.used + nbytes > self.budget:
+                break                        # in order: wait for memory to free up
+            self.waiting.popleft()
+            job.admitted = now
+            self.active[job.job_id] = (job, self.ex.start(job), nbytes)
+            self.used += nbytes
+            self.peak_used = max(self.peak_used, self.used)
+        return finished
+
+    def run(self, jobs, clock: Callable[[], float] = time.perf_counter, idle_sleep: float = 1e-4,
+            timeout: float = 600.0):
+        """Replay `jobs` (sorted by arrival) in real time until every finite
+        job has finished.  Returns the wall time from the first arrival."""
+        pending = collections.deque(sorted(jobs, key=lambda j: j.arrival))
+        n_finite = sum(1 for j in jobs if j.sweeps is not None)
+        t0 = clock()
+        while True:
+            now = clock() - t0
+            while pending and pending[0].arrival <= now:
+                self.submit(pending.popleft())
+            self.poll(now)
+            if not pending and sum(1 for j in self.done if j.sweeps is not None) == n_finite:
+                break
+            if now > timeout:
+                raise TimeoutError("serving trace did not finish")
+            if idle_sleep:
+                time.sleep(idle_sleep)
+        return clock() - t0
+
+    def close(self):
+        """Release every active job (after an error, or at the end)."""
+        for jid in list(self.active):
+            job, h, nbytes = self.active.pop(jid)
+            try:
+                self.ex.finish(job, h)
+            finally:
+                self.used -= nbytes
+
+    def stop_standing(self):
+        """Finish standing chains (after a trace); returns their results."""
+        out = []
+        for jid in list(self.active):
+            job, h, nbytes = self.active[jid]
+            if job.sweeps is None:
+                job.result = self.ex.finish(job, h)
+                del self.active[jid]
+                self.used -= nbytes
+                out.append(job)
+        return out
+
+
+def latency_summary(jobs) -> dict:
+    lat = np.array([j.finished - j.arrival for j in jobs if j.finished is not None])
+    if lat.size == 0:
+        return {"n": 0}
+    return {"n": int(lat.size), "p50_s": float(np.percentile(lat, 50)),
+            "p99_s": float(np.percentile(lat, 99)), "mean_s": float(lat.mean()),
+            "max_s": float(lat.max())}
+
+
+def poisson_trace(rate: float, duration: float, seed: int, job_factory) -> list:
+    """Arrival times of a Poisson process of `rate` per second over
+    `duration` seconds; job_factory(index, arrival, rng) makes each job."""
+    rng = np.random.Generator(np.random.Philox(seed))
+    jobs, t = [], 0.0
+    while True:
+        t += rng.exponential(1.0 / rate)
+        if t > duration:
+            break
+        jobs.append(job_factory(len(jobs), t, rng))
+    return jobs
+
+
+def mixed_job_factory(sweeps: int = 20, burn_in: int = 10, B: int = 8, eps: float = 1e-4):
+    """The serving workload's job mix: I in {257, 513, 1025}, J log-uniform
+    on [500, 20000], Tweedie p in {1, 1.5}, K in {16, 64}."""
+    def make(index, arrival, rng):
+        I = int(rng.choice([257, 513, 1025]))
+        J = int(round(math.exp(rng.uniform(math.log(500), math.log(20000)))))
+        return Job(job_id=index, I=I, J=J, K=int(rng.choice([16, 64])), B=B,
+                   p=float(rng.choice([1.0, 1.5])), sweeps=sweeps, burn_in=burn_in, eps=eps,
+                   seed=1000 + index, data_seed=index, arrival=arrival)
+    return make
+
+
+class GpuExecutor:
+    """Runs jobs on one GPU through the C ABI: one stream and one context per
+    job, memory from PyTorch's caching allocator (a finished job's memory is
+    reused without a device-wide wait)."""
+
+    def __init__(self, device=None):
+        import torch
+
+        from . import psgld as P
+        self.torch = torch
+        self.P = P
+        self.dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        P.use_torch_allocator(self.dev.index)
+
+    def estimate(self, job: Job) -> int:
+        nbytes = self.P.psgld_estimate_device_bytes(job.I, job.J, job.K, job.B, 0, job.dense_path,
+                                                    job.dense_v_bf16)
+        return nbytes + 4 * job.I * job.J          # the caller-side V the job is given
+
+    def _data(self, job: Job):
+        from . import datagen
+        torch = self.torch
+        if job.p == 1.0:
+            V = datagen.dense_poisson_device(job.I, job.J, 8, job.data_seed, self.dev)
+        else:
+            V = datagen.dense_gamma_device(job.I, job.J, 8, job.data_seed, self.dev)
+        W0, H0 = datagen.init_factors(job.I, job.J, job.K, job.seed, scale=job.init_scale, nonneg=True)
+        return V, torch.from_numpy(W0).to(self.dev, non_blocking=True), \
+            torch.from_numpy(H0.T.copy()).to(self.dev, non_blocking=True)
+
+    def start(self, job: Job):
+        torch = self.torch
+        stream = torch.cuda.Stream(self.dev)
+        with torch.cuda.stream(stream):
+            V, W0, Ht0 = self._data(job)
+            ctx = self.P.PSGLD(job.I, job.J, job.K, job.B, job.p, job.phi,
+                               prior_kind=self.P.PSGLD_PRIOR_EXPONENTIAL, lambda_w=job.lam,
+                               lambda_h=job.lam, seed=job.seed, eps=job.eps, use_graphs=1,
+                               burn_in_sweeps=job.burn_in, dense_path=job.dense_path,
+                               dense_v_bf16=job.dense_v_bf16)
+            ctx.set_data_dense(V, stream.cuda_stream)
+            ctx.set_factors(W0, Ht0, stream.cuda_stream)
+            del V, W0, Ht0
+            n = job.sweeps if job.sweeps is not None else 1
+            ctx.sweep(n, stream.cuda_stream)
+            ev = torch.cuda.Event()
+            ev.record(stream)
+        return {"ctx": ctx, "stream": stream, "event": ev, "sweeps_queued": n}
+
+    def done(self, h) -> bool:
+        return h["event"].query()
+
+    def step_standing(self, job: Job, h):
+        if h["event"].query():
+            torch = self.torch
+            h["ctx"].sweep(1, h["stream"].cuda_stream)
+            h["event"] = torch.cuda.Event()
+            h["event"].record(h["stream"])
+            h["sweeps_queued"] += 1
+
+    def finish(self, job: Job, h) -> dict:
+        h["event"].synchronize()
+        Wm, Wv, Hm, Hv, n = h["ctx"].posterior_mean()
+        out = {"Wmean": Wm, "Hmean": Hm, "n_samples": n, "sweeps": h["sweeps_queued"]}
+        h["ctx"].close()
+        return out

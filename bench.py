@@ -74,6 +74,13 @@ WORKLOADS["serving_poisson200_mixed_jobs_with_standing_chain"] = dict(
     serving=True, rate=200.0, duration=3.0, sweeps=20, burn_in=10, B=8, eps=1e-4,
     budget_bytes=64 << 30, standing="dense_poisson_32768x32768_K256_B16_bf16",
     I=0, J=0, K=0, p=1.0)
+# many small dense chains sharing launches: 256 independent chains, each
+# I = 513 x J ~ Uniform[200, 5000], V = |W* H*| * Gamma(2, rate 2) noise with
+# K* = 16, model K = 32, Tweedie p = 1 and 2 alternating, B = 8
+WORKLOADS["batched_dense_nmf_256chains_513xJ200-5000_K32_B8_bf16"] = dict(
+    batched=True, chains=256, I=513, J_lo=200, J_hi=5000, K=32, K_true=16, B=8, p_mix=(1.0, 2.0),
+    phi=1.0, prior="exponential", lam=1.0, eps=1e-4, init_scale=0.5, job_sweeps=40,
+    dense_path=1, p=1.0)
 DEFAULT_WORKLOAD = "sparse_gauss_70000x10000_nnz10M_K50_B32"
 
 
@@ -588,6 +595,268 @@ def e2e_job(wl, seed, dev, i, j, v, W0, H0):
 # reference arm: the oracle on the host cores
 # ---------------------------------------------------------------------------
 
+def batched_specs(wl: dict, seed: int):
+    """Per chain of the batched workload: (J, tweedie p, data seed, init seed)."""
+    import numpy as np
+    rng = np.random.Generator(np.random.Philox(seed))
+    Js = rng.integers(wl["J_lo"], wl["J_hi"] + 1, size=wl["chains"])
+    ps = wl["p_mix"]
+    return [(int(Js[c]), float(ps[c % len(ps)]), seed + 17 * c, seed + 17 * c + 1)
+            for c in range(wl["chains"])]
+
+
+def batched_chain_wl(wl: dict, J: int, p: float) -> dict:
+    return dict(wl, J=J, p=p, nnz=wl["I"] * J, batched=False)
+
+
+def batched_make(wl, specs, dev, host=False, **opts):
+    """The chains of the batched workload with their data and initial factors
+    (device tensors, or pinned host tensors when host=True: the copies then run
+    inside set_data_dense / set_factors)."""
+    import torch
+
+    from paper_1506_01418_gb300 import datagen
+    chains = []
+    for (J, p, ds, iseed) in specs:
+        cwl = batched_chain_wl(wl, J, p)
+        V = datagen.dense_gamma_device(wl["I"], J, wl["K_true"], ds, dev)
+        W0, H0 = datagen.init_factors(wl["I"], J, wl["K"], iseed, scale=wl["init_scale"], nonneg=True)
+        W0, Ht0 = torch.from_numpy(W0), torch.from_numpy(H0.T.copy())
+        ch = new_chain(cwl, iseed, use_graphs=1, **opts)
+        if host:
+            V = V.cpu().pin_memory()
+            W0, Ht0 = W0.pin_memory(), Ht0.pin_memory()
+        else:
+            W0, Ht0 = W0.to(dev), Ht0.to(dev)
+        chains.append((ch, V, W0, Ht0))
+    return chains
+
+
+def batched_bytes_flops(wl, specs):
+    """Algorithmic HBM bytes and FLOPs of one batched gradient launch (one
+    part of every chain), averaged over the parts: V of the part once (FP32),
+    the part's W rows and H columns read and its G rows written once (FP32);
+    three contractions of 2 (I J / B) K each."""
+    I, K, B = wl["I"], wl["K"], wl["B"]
+    ent = sum(I * J for J, _, _, _ in specs) / B
+    fac = sum(8.0 * K * (I + J) for J, _, _, _ in specs)
+    return 4.0 * ent + fac, 6.0 * ent * K
+
+
+def run_batched(args, wl_name, wl):
+    """Many small dense chains whose part-steps share launches
+    (psgld_batch_sweep); a step is one sweep of every chain."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1506_01418_gb300 import psgld as P
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    seed = 1000
+    specs = batched_specs(wl, seed)
+    made = batched_make(wl, specs, dev, profile=1)
+    chains = [m[0] for m in made]
+    for ch, V, W0, Ht0 in made:
+        ch.set_data_dense(V)
+        ch.set_factors(W0, Ht0)
+    del made
+    torch.cuda.synchronize(dev)
+    torch.cuda.empty_cache()
+    N = sum(wl["I"] * J for J, _, _, _ in specs)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+        uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+    except Exception:
+        uuid = "0"
+    sampler = ClockSampler(uuid)
+    chains[0].set_options(profile=0)
+    for _ in range(args.warmup):
+        P.psgld_batch_sweep(chains, 1, stream.cuda_stream)
+    torch.cuda.synchronize(dev)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    w0 = time.time()
+    for s in range(args.steps):
+        flush.zero_()
+        starts[s].record(stream)
+        P.psgld_batch_sweep(chains, 1, stream.cuda_stream)
+        ends[s].record(stream)
+    torch.cuda.synchronize(dev)
+    w1 = time.time()
+    ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends)) / args.steps
+    # kernel durations: events around each part's launches, separate pass
+    chains[0].set_options(profile=1)
+    g_ms = u_ms = 0.0
+    k_n = 0
+    for s in range(max(3, min(args.steps, 10))):
+        flush.zero_()
+        P.psgld_batch_sweep(chains, 1, stream.cuda_stream)
+        g, u, n = chains[0].profile_read_split()
+        g_ms += g
+        u_ms += u
+        k_n += n
+    chains[0].set_options(profile=0)
+    # the same chains swept one by one (each its own captured-graph sweep)
+    torch.cuda.synchronize(dev)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n_alone = 3
+    a.record(stream)
+    for _ in range(n_alone):
+        for ch in chains:
+            ch.sweep(1, stream.cuda_stream)
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_alone = a.elapsed_time(b) / n_alone
+    time.sleep(0.25)
+    sampler.stop()
+    clocks = sampler.summary(w0, w1)
+    for ch in chains:
+        ch.close()
+    torch.cuda.empty_cache()
+
+    hbm_peak, tc_peak, peak_src = read_peaks()
+    grad_ms = g_ms / max(k_n, 1)
+    upd_ms = u_ms / max(k_n, 1)
+    bytes_launch, flops_launch = batched_bytes_flops(wl, specs)
+    achieved = bytes_launch / (grad_ms / 1e3) / 1e9
+    tflops = flops_launch / (grad_ms / 1e3) / 1e12
+    result = {
+        "metric": METRIC, "value": N / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": wl_name, "chains": wl["chains"], "I": wl["I"],
+                   "J": f"Uniform[{wl['J_lo']}, {wl['J_hi']}] per chain", "entries": N,
+                   "K": wl["K"], "K_true": wl["K_true"], "B": wl["B"], "tweedie_p": list(wl["p_mix"]),
+                   "prior": wl["prior"], "eps": wl["eps"],
+                   "step": "one sweep of every chain: per part one tensor-core gradient launch "
+                           "and one update launch over all chains, then the FP64 posterior sums",
+                   "path": "psgld_batch_sweep, single-pass tensor-core block chain, BF16 operands, "
+                           "FP32 accumulate",
+                   "l2": "V of all chains (1.4 GB) exceeds L2; 256 MB buffer also written before "
+                         "every timed sweep"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": achieved / hbm_peak, "traffic": kernel_traffic(wl_name),
+                     "kernel": "dense_grad_batch_kernel", "kernel_ms": grad_ms,
+                     "algorithmic_bytes_per_launch": bytes_launch,
+                     "algorithmic_flops_per_launch": flops_launch, "tensor_tflops": tflops,
+                     "tensor_frac_of_sustained": tflops / tc_peak,
+                     "update_kernel_ms": upd_ms, "part_step_ms": grad_ms + upd_ms,
+                     "peak_source": f"{peak_src} HBM copy bandwidth"},
+        # per call (one sweep): set t, B x (gradient + update; one K class),
+        # accumulate, advance t
+        "gpu_launches": args.steps * (2 * wl["B"] + 3),
+        "clocks": clocks,
+        "unbatched": {"value": N / (ms_alone / 1e3), "unit": UNIT, "ms_per_sweep": ms_alone,
+                      "how": "the same chains, each swept alone (its own captured-graph sweep), "
+                             "back to back on one stream"},
+    }
+    if args.compare_sweeps > 0:
+        result["precision_compare"] = batched_precision(wl, specs[:16], dev, args.compare_sweeps)
+    if not args.no_e2e:
+        result["e2e"] = batched_e2e(wl, specs, dev)
+    if not args.no_cpu_baseline:
+        result["cpu_baseline"] = batched_cpu_baseline(wl, specs[0], args.cpu_budget)
+    print(json.dumps(result), flush=True)
+
+
+def batched_precision(wl, specs, dev, sweeps: int):
+    """BF16 tensor-core batched sweeps vs the FP32 gather path (each chain
+    alone) on the same chains, data, initial factors and Philox keys: entries/s
+    and the posterior-mean reconstruction RMSE (mean over the chains)."""
+    import torch
+
+    from paper_1506_01418_gb300 import psgld as P
+    out = {"chains": len(specs), "sweeps": sweeps, "burn_in_sweeps": sweeps // 2}
+    N = sum(wl["I"] * J for J, _, _, _ in specs)
+    stream = torch.cuda.current_stream(dev)
+    for name, opts in (("bf16_tensor_core_batched", {}), ("fp32_gather", {"dense_path": 0})):
+        made = batched_make(wl, specs, dev, burn_in_sweeps=sweeps // 2, **opts)
+        for ch, V, W0, Ht0 in made:
+            ch.set_data_dense(V)
+            ch.set_factors(W0, Ht0)
+        chains = [m[0] for m in made]
+        del made
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        a.record(stream)
+        if opts:
+            for ch in chains:
+                ch.sweep(sweeps, stream.cuda_stream)
+        else:
+            P.psgld_batch_sweep(chains, sweeps, stream.cuda_stream)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = a.elapsed_time(b)
+        r = [ch.rmse(True) for ch in chains]
+        out[name] = {"value": N * sweeps / (ms / 1e3), "unit": UNIT, "ms_per_sweep": ms / sweeps,
+                     "posterior_mean_rmse_mean": sum(r) / len(r), "rmse": r}
+        for ch in chains:
+            ch.close()
+        torch.cuda.empty_cache()
+    r16 = out["bf16_tensor_core_batched"].pop("rmse")
+    r32 = out["fp32_gather"].pop("rmse")
+    out["rmse_rel_diff_max"] = max(abs(x - y) / y for x, y in zip(r16, r32))
+    out["speedup"] = out["bf16_tensor_core_batched"]["value"] / out["fp32_gather"]["value"]
+    return out
+
+
+def batched_e2e(wl, specs, dev):
+    """The whole batch as one job through the C ABI from pinned host buffers:
+    every chain's V and initial factors in, job_sweeps batched sweeps,
+    every chain's posterior means and variances out."""
+    import numpy as np
+    import torch
+
+    from paper_1506_01418_gb300 import psgld as P
+    S = wl["job_sweeps"]
+    made = batched_make(wl, specs, dev, host=True, burn_in_sweeps=S // 2)
+    chains = [m[0] for m in made]
+    I, K = wl["I"], wl["K"]
+    outs = [tuple(np.zeros((n, K)) for n in (I, I, J, J)) for J, _, _, _ in specs]
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for ch, V, W0, Ht0 in made:
+        ch.set_data_dense(V)
+        ch.set_factors(W0, Ht0)
+    P.psgld_batch_sweep(chains, S)
+    for ch, o in zip(chains, outs):
+        P.psgld_posterior_mean(ch.ctx, *o)
+    torch.cuda.synchronize(dev)
+    dt = time.perf_counter() - t0
+    for ch in chains:
+        ch.close()
+    N = sum(I * J for J, _, _, _ in specs)
+    h2d = 4 * N + sum(4 * (I + J) * K for J, _, _, _ in specs)
+    d2h = sum(8 * 4 * (I + J) * K for J, _, _, _ in specs)
+    return {"value": N * S / dt, "unit": UNIT, "h2d_bytes_per_step": h2d / S,
+            "d2h_bytes_per_step": d2h / S, "job_sweeps": S, "job_s": dt,
+            "api": "psgld_set_data_dense/set_factors (pinned host) per chain + psgld_batch_sweep "
+                   "+ psgld_posterior_mean per chain"}
+
+
+def batched_cpu_baseline(wl, spec, budget_s: float):
+    """The oracle on the first chain of the batch (OpenMP over a part's blocks)."""
+    import numpy as np
+
+    import oracle
+    from paper_1506_01418_gb300 import datagen
+    J, p, ds, iseed = spec
+    cwl = batched_chain_wl(wl, J, p)
+    V, _, _ = datagen.dense_gamma(wl["I"], J, wl["K_true"], ds)
+    i, j, v = datagen.dense_to_coo(V)
+    W0, H0 = datagen.init_factors(wl["I"], J, wl["K"], iseed, scale=wl["init_scale"], nonneg=True)
+    out = cpu_baseline(cwl, i, j, v.astype(np.float64), W0.astype(np.float64),
+                       H0.astype(np.float64), iseed, budget_s)
+    out["sample"] = f"chain 0 of the batch ({wl['I']} x {J}, p = {p}): " + out["sample"]
+    return out
+
+
 def run_serving(args, wl_name, wl):
     """The serving loop on one GPU: a Poisson trace of jobs replayed in real
     time; value = observed entries x sweeps of every job and of the standing
@@ -688,10 +957,22 @@ def run_reference(args, wl_name, wl):
     oracle.build()
     seed = 1000
     dev = torch.device("cuda", 0) if torch.cuda.is_available() else torch.device("cpu")
-    i, j, v, W0, H0 = make_inputs(wl, seed, dev)
-    N = int(v.numel())
-    run_wl = wl
     what = "the workload"
+    if wl.get("batched"):
+        # chains are independent: the oracle on the batch's first chain
+        from paper_1506_01418_gb300 import datagen
+        J0, p0, ds, iseed = batched_specs(wl, seed)[0]
+        N = sum(wl["I"] * J for J, _, _, _ in batched_specs(wl, seed))
+        run_wl = batched_chain_wl(wl, J0, p0)
+        V0, _, _ = datagen.dense_gamma(wl["I"], J0, wl["K_true"], ds)
+        i, j, v = datagen.dense_to_coo(V0)
+        W0, H0 = datagen.init_factors(wl["I"], J0, wl["K"], iseed, scale=wl["init_scale"], nonneg=True)
+        i, j, v = (torch.from_numpy(x) for x in (i, j, v))
+        what = f"chain 0 of the batch ({wl['I']} x {J0}, p = {p0})"
+    else:
+        i, j, v, W0, H0 = make_inputs(wl, seed, dev)
+        N = int(v.numel())
+        run_wl = wl
     if i is None:
         # dense V beyond the oracle's host arrays: one block as a B = 1 problem
         B = wl["B"]
@@ -730,8 +1011,8 @@ def run_reference(args, wl_name, wl):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": wl_name, "I": WORKLOADS[wl_name]["I"], "J": WORKLOADS[wl_name]["J"],
-                   "nnz": N, "K": wl["K"], "B": WORKLOADS[wl_name]["B"], "tweedie_p": wl["p"],
+        "config": {"workload": wl_name, "I": WORKLOADS[wl_name]["I"],
+                   "J": WORKLOADS[wl_name].get("J") or "per chain", "nnz": N, "K": wl["K"], "B": WORKLOADS[wl_name]["B"], "tweedie_p": wl["p"],
                    "phi": wl["phi"], "prior": wl["prior"], "eps": wl["eps"],
                    "step": "bounded sample of part-steps, rate per entry"},
         "cpu_baseline": {"value": rate, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
@@ -767,6 +1048,8 @@ def main():
         run_reference(args, args.workload, wl)
     elif wl.get("serving"):
         run_serving(args, args.workload, wl)
+    elif wl.get("batched"):
+        run_batched(args, args.workload, wl)
     else:
         run_ours(args, args.workload, wl)
 

@@ -188,6 +188,20 @@ PSGLD_API psgld_status psgld_part_step(psgld_ctx *ctx, int64_t t, void *stream);
  * sweep past burn-in the FP64 posterior sums of W, W^2, H, H^2 are updated. */
 PSGLD_API psgld_status psgld_sweep(psgld_ctx *ctx, int32_t n_sweeps, void *stream);
 
+/* n_sweeps sweeps of each of the n contexts, their part-steps sharing
+ * launches: at every part of a sweep one tensor-core gradient launch per K
+ * class (K rounded up to 16, 32, 64 or 128) covers the blocks of all the
+ * contexts of that class, and one update launch covers all the contexts'
+ * rows; then each context's posterior sums as in psgld_sweep.  Every context
+ * must hold dense data on the single-pass tensor-core kernel (dense_path 1
+ * with blocks of at most 128 rows and K <= 128, or dense_path 3), the same
+ * B, cyclic parts and its iteration counter at a sweep boundary; sizes,
+ * powers, priors, seeds and step sizes may differ.  Each context ends in the
+ * same state, bit for bit, as after psgld_sweep(ctx, n_sweeps).  Returns
+ * after the work has run (synchronises `stream`). */
+PSGLD_API psgld_status psgld_batch_sweep(psgld_ctx *const *ctxs_host, int32_t n, int32_t n_sweeps,
+                                         void *stream);
+
 /* Monte Carlo posterior mean and variance of W (I x K) and H^T (J x K), FP64,
  * over the samples kept so far (population variance).  Any output pointer may
  * be NULL.  Synchronises the context's last stream. */

@@ -691,6 +691,170 @@ psgld_status psgld_part_layout(psgld_ctx *c, int32_t s, int32_t *row_ptr, int32_
 
 int64_t psgld_iterations_done(const psgld_ctx *c) { return c ? c->t_done : -1; }
 
+// Batched sweeps.  Everything the launches of the call read is known before
+// the first one: per part b and per sweep parity q (the ping-pong buffers a
+// context starts the sweep in alternate only when B is odd) the dense and
+// update parameter tables, per q the accumulation table, and the grid
+// prefixes.  They go to the device in one copy; the iteration counter t is
+// each context's device counter (set once, advanced by B after each sweep),
+// so a sweep is the same 2B + 2 launches every time.
+psgld_status psgld_batch_sweep(psgld_ctx *const *ctxs, int32_t n, int32_t n_sweeps, void *stream)
+{
+    if (!ctxs || n < 1 || n_sweeps < 0) return PSGLD_ERR_ARG;
+    psgld_ctx *c0 = ctxs[0];
+    if (!c0) return PSGLD_ERR_ARG;
+    const int B = c0->B;
+    for (int i = 0; i < n; ++i) {
+        psgld_ctx *c = ctxs[i];
+        if (!c) return PSGLD_ERR_ARG;
+        psgld_status s;
+        if (!ready(c, &s)) return s;
+        if (!c->dense || dense_batch_key(c) <= 0)
+            return fail(c, PSGLD_ERR_STATE, "batched sweeps need dense data on the single-pass kernel");
+        if (c->B != B) return fail(c, PSGLD_ERR_ARG, "batched contexts must share B");
+        if (c->opt.part_mode != 0) return fail(c, PSGLD_ERR_STATE, "batched sweeps use cyclic parts");
+        if (c->t_done % B != 0) return fail(c, PSGLD_ERR_STATE, "sweep must start at a sweep boundary");
+        if (c->device != c0->device) return fail(c, PSGLD_ERR_ARG, "batched contexts must share a device");
+        for (int k = 0; k < i; ++k)
+            if (ctxs[k] == c) return fail(c, PSGLD_ERR_ARG, "a context appears twice in the batch");
+    }
+    if (n_sweeps == 0) return PSGLD_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+
+    // dense launches: contexts grouped by K class, in first-seen order
+    std::vector<int> keys, order;                 // order: context indices, group by group
+    std::vector<int> gbeg;                        // group g: order[gbeg[g] .. gbeg[g + 1])
+    for (int i = 0; i < n; ++i) {
+        const int key = dense_batch_key(ctxs[i]);
+        if (std::find(keys.begin(), keys.end(), key) == keys.end()) keys.push_back(key);
+    }
+    for (int key : keys) {
+        gbeg.push_back((int)order.size());
+        for (int i = 0; i < n; ++i)
+            if (dense_batch_key(ctxs[i]) == key) order.push_back(i);
+    }
+    gbeg.push_back(n);
+    const int ng = (int)keys.size();
+    const int nq = (B & 1) && n_sweeps > 1 ? 2 : 1;
+
+    auto up256 = [](size_t x) { return (x + 255) & ~size_t(255); };
+    const size_t dp = dense_param_bytes(), upb = upd_param_bytes(), ap = acc_param_bytes();
+    const size_t off_cta = 0;                                        // ng prefixes, n + ng ints
+    const size_t off_items = up256(off_cta + sizeof(int) * (size_t)(n + ng));
+    const size_t off_units = up256(off_items + sizeof(int64_t) * (size_t)(n + 1));
+    const size_t off_dp = up256(off_units + sizeof(int64_t) * (size_t)(n + 1));
+    const size_t off_up = up256(off_dp + dp * (size_t)nq * B * n);
+    const size_t off_ap = up256(off_up + upb * (size_t)nq * B * n);
+    const size_t total = up256(off_ap + ap * (size_t)nq * n);
+    std::vector<unsigned char> tab(total, 0);
+    int *cta = reinterpret_cast<int *>(tab.data() + off_cta);
+    int64_t *items = reinterpret_cast<int64_t *>(tab.data() + off_items);
+    int64_t *units = reinterpret_cast<int64_t *>(tab.data() + off_units);
+    std::vector<int> g_ctas((size_t)ng, 0);
+
+    std::vector<int> w0((size_t)n), h0((size_t)n);
+    for (int i = 0; i < n; ++i) {
+        w0[i] = ctxs[i]->wcur;
+        h0[i] = ctxs[i]->hcur;
+    }
+    // buffers a context reads after `steps` part-steps of this call
+    auto set_state = [&](int i, int64_t steps) {
+        psgld_ctx *c = ctxs[i];
+        c->wcur = c->opt.freeze_W ? w0[i] : w0[i] ^ (int)(steps & 1);
+        c->hcur = c->opt.freeze_H ? h0[i] : h0[i] ^ (int)(steps & 1);
+    };
+    for (int q = 0; q < nq; ++q) {
+        for (int b = 0; b < B; ++b) {
+            const size_t row = (size_t)(q * B + b) * n;
+            for (int g = 0; g < ng; ++g) {
+                int acc = 0;
+                for (int k = gbeg[g]; k < gbeg[g + 1]; ++k) {
+                    const int i = order[k];
+                    set_state(i, (int64_t)q * B + b);
+                    if (q == 0 && b == 0) cta[gbeg[g] + g + (k - gbeg[g])] = acc;
+                    acc += fill_dense_param(ctxs[i], b, tab.data() + off_dp + dp * (row + k));
+                }
+                if (q == 0 && b == 0) {
+                    cta[gbeg[g + 1] + g] = acc;
+                    g_ctas[g] = acc;
+                }
+            }
+            int64_t it = 0;
+            for (int i = 0; i < n; ++i) {
+                set_state(i, (int64_t)q * B + b);
+                if (q == 0 && b == 0) items[i] = it;
+                it += fill_upd_param(ctxs[i], b, ctxs[i]->t_dev, b + 1, tab.data() + off_up + upb * (row + i));
+            }
+            if (q == 0 && b == 0) items[n] = it;
+        }
+        int64_t un = 0;
+        for (int i = 0; i < n; ++i) {
+            psgld_ctx *c = ctxs[i];
+            set_state(i, (int64_t)(q + 1) * B);
+            if (q == 0) units[i] = un;
+            un += fill_acc_param(c, c->t_done, (int64_t)c->opt.burn_in_sweeps - c->sweeps_done,
+                                 tab.data() + off_ap + ap * ((size_t)q * n + i));
+        }
+        if (q == 0) units[n] = un;
+    }
+    for (int i = 0; i < n; ++i) set_state(i, (int64_t)n_sweeps * B);
+
+    unsigned char *d = static_cast<unsigned char *>(dev_alloc(c0, total, st));
+    if (!d) return fail(c0, PSGLD_ERR_OOM, "device allocation failed");
+    psgld_status s = PSGLD_OK;
+    cudaError_t e = cudaMemcpyAsync(d, tab.data(), total, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) s = cuda_fail(c0, e, "copy of the batch tables");
+    if (s == PSGLD_OK) s = launch_t_batch(c0, d + off_ap, n, 0, st);
+    // profiling (first context's option): events around each part's launches,
+    // read back with psgld_profile_read_split on the first context
+    const bool prof = c0->opt.profile && (int)c0->ev_start.size() == B;
+    auto record = [&](cudaEvent_t ev) {
+        const cudaError_t re = cudaEventRecord(ev, st);
+        return re == cudaSuccess ? PSGLD_OK : cuda_fail(c0, re, "cudaEventRecord");
+    };
+    for (int32_t sw = 0; sw < n_sweeps && s == PSGLD_OK; ++sw) {
+        const int q = nq == 2 ? (sw & 1) : 0;
+        for (int b = 0; b < B && s == PSGLD_OK; ++b) {
+            const size_t row = (size_t)(q * B + b) * n;
+            if (prof) s = record(c0->ev_start[b]);
+            for (int g = 0; g < ng && s == PSGLD_OK; ++g)
+                s = launch_dense_batch(c0, keys[g], d + off_dp + dp * (row + gbeg[g]),
+                                       reinterpret_cast<const int *>(d + off_cta) + gbeg[g] + g,
+                                       gbeg[g + 1] - gbeg[g], g_ctas[g], st);
+            if (s == PSGLD_OK && prof) s = record(c0->ev_mid[b]);
+            if (s == PSGLD_OK)
+                s = launch_update_batch(c0, d + off_up + upb * row,
+                                        reinterpret_cast<const int64_t *>(d + off_items), n, items[n], st);
+            if (s == PSGLD_OK && prof) {
+                s = record(c0->ev_end[b]);
+                c0->ev_pending[b] = 1;
+            }
+        }
+        bool any = false;
+        for (int i = 0; i < n; ++i) any |= ctxs[i]->sweeps_done + sw >= ctxs[i]->opt.burn_in_sweeps;
+        if (s == PSGLD_OK && any)
+            s = launch_accumulate_batch(c0, d + off_ap + ap * (size_t)q * n,
+                                        reinterpret_cast<const int64_t *>(d + off_units), n, units[n], st);
+        if (s == PSGLD_OK) s = launch_t_batch(c0, d + off_ap, n, 1, st);
+    }
+    if (s == PSGLD_OK) {
+        for (int i = 0; i < n; ++i) {
+            psgld_ctx *c = ctxs[i];
+            for (int32_t sw = 0; sw < n_sweeps; ++sw) {
+                if (c->sweeps_done >= c->opt.burn_in_sweeps) c->n_samples += 1;
+                c->sweeps_done += 1;
+            }
+            c->t_done += (int64_t)B * n_sweeps;
+            c->last_stream = st;
+        }
+    }
+    // the tables are read by the launches: free after they ran
+    e = cudaStreamSynchronize(st);
+    dev_free(c0, d, st);
+    if (s == PSGLD_OK && e != cudaSuccess) s = cuda_fail(c0, e, "sync");
+    return s;
+}
+
 psgld_status psgld_set_allocator(const psgld_allocator *a)
 {
     if (a && (!a->alloc || !a->free)) return PSGLD_ERR_ARG;

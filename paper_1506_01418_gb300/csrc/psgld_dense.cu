@@ -33,6 +33,8 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <cstring>
+#include <vector>
 
 #include "psgld_internal.cuh"
 
@@ -209,8 +211,10 @@ __device__ __forceinline__ void st_bf16(unsigned char *base, uint32_t off, float
     *reinterpret_cast<__nv_bfloat16 *>(base + off) = __float2bfloat16_rn(x);
 }
 
+// One CTA of the single-pass kernel: CTA number `cta` of the launch for the
+// context described by P (P may live in parameter or global memory).
 template <int KP>
-__global__ void __launch_bounds__(kDenseThreads, 1) dense_grad_kernel(const __grid_constant__ DenseParams P)
+__device__ __forceinline__ void dense_grad_cta(const DenseParams &P, int cta)
 {
     extern __shared__ __align__(1024) unsigned char sm[];
     constexpr uint32_t kOpBytes = kTile * KP * 2;           // a 128 x KP BF16 tile
@@ -225,7 +229,7 @@ __global__ void __launch_bounds__(kDenseThreads, 1) dense_grad_kernel(const __gr
 
     const int tid = threadIdx.x, warp = tid >> 5;
     const int B = P.B;
-    const int blk = blockIdx.x / P.mtiles, mt = blockIdx.x % P.mtiles;
+    const int blk = cta / P.mtiles, mt = cta % P.mtiles;
     const int cpiece = (blk + P.part) % B;
     const int64_t rs = (int64_t)blk * P.I / B, re = (int64_t)(blk + 1) * P.I / B;
     const int64_t cs = (int64_t)cpiece * P.J / B, ce = (int64_t)(cpiece + 1) * P.J / B;
@@ -403,6 +407,28 @@ __global__ void __launch_bounds__(kDenseThreads, 1) dense_grad_kernel(const __gr
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;"
                      :: "r"(tmem), "r"(kTmemCols) : "memory");
+}
+
+
+template <int KP>
+__global__ void __launch_bounds__(kDenseThreads, 1) dense_grad_kernel(const __grid_constant__ DenseParams P)
+{
+    dense_grad_cta<KP>(P, blockIdx.x);
+}
+
+// Many contexts in one launch: context i owns CTAs [cta_start[i],
+// cta_start[i + 1]) of the grid (cta_start[n] = grid size).
+template <int KP>
+__global__ void __launch_bounds__(kDenseThreads, 1)
+dense_grad_batch_kernel(const DenseParams *__restrict__ Ps, const int *__restrict__ cta_start, int n)
+{
+    const int b = blockIdx.x;
+    int lo = 0, hi = n - 1;          // last i with cta_start[i] <= b
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(cta_start + mid) <= b) lo = mid; else hi = mid - 1;
+    }
+    dense_grad_cta<KP>(Ps[lo], b - __ldg(cta_start + lo));
 }
 
 // ===========================================================================
@@ -1161,13 +1187,9 @@ static psgld_status launch_two_sided(psgld_ctx *c, int part, cudaStream_t st)
     return PSGLD_OK;
 }
 
-psgld_status launch_dense_grad(psgld_ctx *c, int part, cudaStream_t st)
+static void fill_dense_params(const psgld_ctx *c, int part, DenseParams &P)
 {
-    if (c->dense_kind == 2) return launch_two_sided(c, part, st);
-    const int kp = dense_kp(c->K);
-    DenseFn fn = pick_dense(kp);
-    if (!fn) return fail(c, PSGLD_ERR_ARG, "single-pass dense kernel supports K <= 128");
-    DenseParams P{};
+    P = DenseParams{};
     P.V = c->Vd;
     P.ldv = c->ldv;
     P.W = c->W[c->wcur];
@@ -1186,8 +1208,48 @@ psgld_status launch_dense_grad(psgld_ctx *c, int part, cudaStream_t st)
     P.mu_min = (float)c->opt.mu_min;
     P.p_mode = c->p == 0.0 ? 0 : c->p == 1.0 ? 1 : c->p == 2.0 ? 2 : 3;
     P.err = c->kflag;
+}
+
+psgld_status launch_dense_grad(psgld_ctx *c, int part, cudaStream_t st)
+{
+    if (c->dense_kind == 2) return launch_two_sided(c, part, st);
+    const int kp = dense_kp(c->K);
+    DenseFn fn = pick_dense(kp);
+    if (!fn) return fail(c, PSGLD_ERR_ARG, "single-pass dense kernel supports K <= 128");
+    DenseParams P;
+    fill_dense_params(c, part, P);
     fn<<<c->B * P.mtiles, kDenseThreads, dense_smem(kp), st>>>(P);
     PSGLD_CK(c, cudaGetLastError());
+    return PSGLD_OK;
+}
+
+int dense_batch_key(const psgld_ctx *c) { return c->dense_kind == 1 ? dense_kp(c->K) : 0; }
+
+size_t dense_param_bytes() { return sizeof(DenseParams); }
+
+int fill_dense_param(const psgld_ctx *c, int part, void *dst)
+{
+    DenseParams P;
+    fill_dense_params(c, part, P);
+    std::memcpy(dst, &P, sizeof P);
+    return c->B * P.mtiles;
+}
+
+psgld_status launch_dense_batch(psgld_ctx *c0, int kp, const void *params, const int *cta_start, int n,
+                                int total_ctas, cudaStream_t st)
+{
+    void (*fn)(const DenseParams *, const int *, int) = nullptr;
+    switch (kp) {
+    case 16: fn = dense_grad_batch_kernel<16>; break;
+    case 32: fn = dense_grad_batch_kernel<32>; break;
+    case 64: fn = dense_grad_batch_kernel<64>; break;
+    case 128: fn = dense_grad_batch_kernel<128>; break;
+    default: return fail(c0, PSGLD_ERR_ARG, "single-pass dense kernel supports K <= 128");
+    }
+    PSGLD_CK(c0, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dense_smem(kp)));
+    if (total_ctas > 0)
+        fn<<<total_ctas, kDenseThreads, dense_smem(kp), st>>>(static_cast<const DenseParams *>(params), cta_start, n);
+    PSGLD_CK(c0, cudaGetLastError());
     return PSGLD_OK;
 }
 

@@ -175,6 +175,32 @@ psgld_status build_dense_shadows(psgld_ctx *c, cudaStream_t st);
 // mtiles == 1) or hpart rows of Ht.
 psgld_status launch_dense_grad(psgld_ctx *c, int part, cudaStream_t st);
 
+// ---- many contexts in shared launches (psgld_batch_sweep) -----------------
+// Each launch reads a device table of per-context kernel parameters; the
+// fill_* functions write one context's entry into host memory (with the
+// context's current ping-pong buffers) and return its share of the grid:
+// CTAs, update items or float4 accumulation units.  The *_start arrays are
+// exclusive prefix sums of those shares (n + 1 entries, device memory).
+// Dense: single-pass contexts of one K class (dense_batch_key equal, > 0).
+int dense_batch_key(const psgld_ctx *c);
+size_t dense_param_bytes();
+int fill_dense_param(const psgld_ctx *c, int part, void *dst);
+psgld_status launch_dense_batch(psgld_ctx *c0, int kp, const void *params, const int *cta_start, int n,
+                                int total_ctas, cudaStream_t st);
+// Update of part `part` at iteration *t_dev + t_add (t_dev: the context's
+// device counter); does not flip the context's buffers.
+size_t upd_param_bytes();
+int64_t fill_upd_param(psgld_ctx *c, int part, const int64_t *t_dev, int64_t t_add, void *dst);
+psgld_status launch_update_batch(psgld_ctx *c0, const void *params, const int64_t *item_start, int n,
+                                 int64_t total_items, cudaStream_t st);
+// Posterior sums: a context takes the sample when (*t_dev - t0) / B >= acc_from.
+size_t acc_param_bytes();
+int64_t fill_acc_param(psgld_ctx *c, int64_t t0, int64_t acc_from, void *dst);
+psgld_status launch_accumulate_batch(psgld_ctx *c0, const void *params, const int64_t *unit_start, int n,
+                                     int64_t total_units, cudaStream_t st);
+// mode 0: every context's *t_dev = t0; mode 1: *t_dev += B.
+psgld_status launch_t_batch(psgld_ctx *c0, const void *params, int n, int mode, cudaStream_t st);
+
 // ---- reductions (psgld_reduce.cu) -----------------------------------------
 psgld_status launch_accumulate(psgld_ctx *c, cudaStream_t st);
 psgld_status launch_advance_t(psgld_ctx *c, int64_t by, cudaStream_t st);

@@ -11,6 +11,7 @@
 // row-major layout (or the dense V of the tensor-core path); per-CTA partial
 // sums are added on the host in CTA order, so the result is deterministic.
 #include <algorithm>
+#include <cstring>
 
 #include "psgld_internal.cuh"
 
@@ -30,6 +31,71 @@ __global__ void accumulate_kernel(const float4 *__restrict__ x, int64_t n4, doub
         p0.x += a0; p0.y += a1; p1.x += a2; p1.y += a3;
         q0.x += a0 * a0; q0.y += a1 * a1; q1.x += a2 * a2; q1.y += a3 * a3;
         ps[0] = p0; ps[1] = p1; ps2[0] = q0; ps2[1] = q1;
+    }
+}
+
+// One context's share of a batched accumulation: its current factors, its
+// sums, and when to take the sample (Sec. 4.1's averages after burn-in).
+struct AccParams {
+    const float4 *W, *Ht;        // current factors (I x ldk, J x ldk)
+    int64_t nW4, nH4;            // their float4 counts
+    double *sW, *sW2, *sH, *sH2;
+    int64_t *t_dev;              // iteration at the start of the running sweep
+    int64_t t0;                  // *t_dev when the batched call began
+    int64_t acc_from;            // first sweep of the call whose sample is taken
+    int64_t B;
+};
+
+// Every context's factors added to its sums in one launch: context i owns
+// float4 units [unit_start[i], unit_start[i + 1]) (W first, then H^T); the
+// arithmetic per unit is accumulate_kernel's.
+__global__ void accumulate_batch_kernel(const AccParams *__restrict__ Ps, const int64_t *__restrict__ unit_start,
+                                        int n)
+{
+    const int64_t total = __ldg(unit_start + n);
+    int ci = -1;
+    bool take = false;
+    for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < total;
+         a += (int64_t)gridDim.x * blockDim.x) {
+        if (ci < 0 || __ldg(unit_start + ci + 1) <= a) {
+            int lo = ci < 0 ? 0 : ci, hi = n - 1;   // last i with unit_start[i] <= a
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (__ldg(unit_start + mid) <= a) lo = mid; else hi = mid - 1;
+            }
+            ci = lo;
+            const AccParams &P = Ps[ci];
+            take = (*P.t_dev - P.t0) / P.B >= P.acc_from;
+        }
+        if (!take) continue;
+        const AccParams &P = Ps[ci];
+        int64_t u = a - __ldg(unit_start + ci);
+        const float4 *x = P.W;
+        double *s = P.sW, *s2 = P.sW2;
+        if (u >= P.nW4) {
+            u -= P.nW4;
+            x = P.Ht;
+            s = P.sH;
+            s2 = P.sH2;
+        }
+        const float4 v = x[u];
+        double2 *ps = reinterpret_cast<double2 *>(s) + 2 * u;
+        double2 *ps2 = reinterpret_cast<double2 *>(s2) + 2 * u;
+        double2 p0 = ps[0], p1 = ps[1], q0 = ps2[0], q1 = ps2[1];
+        const double a0 = v.x, a1 = v.y, a2 = v.z, a3 = v.w;
+        p0.x += a0; p0.y += a1; p1.x += a2; p1.y += a3;
+        q0.x += a0 * a0; q0.y += a1 * a1; q1.x += a2 * a2; q1.y += a3 * a3;
+        ps[0] = p0; ps[1] = p1; ps2[0] = q0; ps2[1] = q1;
+    }
+}
+
+// mode 0: *t_dev = t0 for every context; mode 1: *t_dev += B
+__global__ void t_batch_kernel(const AccParams *__restrict__ Ps, int n, int mode)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const AccParams &P = Ps[i];
+        if (mode == 0) *P.t_dev = P.t0;
+        else *P.t_dev += P.B;
     }
 }
 
@@ -139,6 +205,44 @@ psgld_status launch_accumulate(psgld_ctx *c, cudaStream_t st)
     accumulate_kernel<<<(unsigned)std::min<int64_t>((nH4 + 255) / 256, 152 * 16), 256, 0, st>>>(
         reinterpret_cast<const float4 *>(c->Ht[c->hcur]), nH4, c->sH.s, c->sH.s2);
     PSGLD_CK(c, cudaGetLastError());
+    return PSGLD_OK;
+}
+
+size_t acc_param_bytes() { return sizeof(AccParams); }
+
+int64_t fill_acc_param(psgld_ctx *c, int64_t t0, int64_t acc_from, void *dst)
+{
+    AccParams P;
+    P.W = reinterpret_cast<const float4 *>(c->W[c->wcur]);
+    P.Ht = reinterpret_cast<const float4 *>(c->Ht[c->hcur]);
+    P.nW4 = c->I * c->ldk / 4;
+    P.nH4 = c->J * c->ldk / 4;
+    P.sW = c->sW.s;
+    P.sW2 = c->sW.s2;
+    P.sH = c->sH.s;
+    P.sH2 = c->sH.s2;
+    P.t_dev = c->t_dev;
+    P.t0 = t0;
+    P.acc_from = acc_from;
+    P.B = c->B;
+    std::memcpy(dst, &P, sizeof P);
+    return P.nW4 + P.nH4;
+}
+
+psgld_status launch_accumulate_batch(psgld_ctx *c0, const void *params, const int64_t *unit_start, int n,
+                                     int64_t total_units, cudaStream_t st)
+{
+    const unsigned grid = (unsigned)std::min<int64_t>((total_units + 255) / 256, 152 * 16);
+    if (grid > 0)
+        accumulate_batch_kernel<<<grid, 256, 0, st>>>(static_cast<const AccParams *>(params), unit_start, n);
+    PSGLD_CK(c0, cudaGetLastError());
+    return PSGLD_OK;
+}
+
+psgld_status launch_t_batch(psgld_ctx *c0, const void *params, int n, int mode, cudaStream_t st)
+{
+    t_batch_kernel<<<(n + 255) / 256, 256, 0, st>>>(static_cast<const AccParams *>(params), n, mode);
+    PSGLD_CK(c0, cudaGetLastError());
     return PSGLD_OK;
 }
 

@@ -43,6 +43,8 @@
 // so it runs at full lane occupancy rather than inside the gather-bound
 // kernel 1.
 #include <algorithm>
+#include <cstring>
+#include <vector>
 #include <cmath>
 
 #include "psgld_internal.cuh"
@@ -553,19 +555,18 @@ psgld_status prepare_kernels(psgld_ctx *c)
     return PSGLD_OK;
 }
 
-psgld_status launch_part_step(psgld_ctx *c, int64_t t, const int64_t *t_dev, int64_t t_add,
-                              cudaStream_t st)
+// Kernel parameters of iteration t (part `part`) for context c: the gradient
+// kernel's and the update kernel's.  With t_dev the update kernel reads t
+// from *t_dev + t_add (captured graphs).
+static void fill_params(psgld_ctx *c, int part, int64_t t, const int64_t *t_dev, int64_t t_add,
+                        GradParams &GP, UpdParams &UP)
 {
     const int B = c->B;
-    const int part = part_of_iteration(c, t);
     const Shape sh = shape_for(c->ngroups);
-    GradFn gfn = pick_grad(sh);
-    if (!gfn) return fail(c, PSGLD_ERR_ARG, "unsupported K");
     const bool dense = c->dense;
-
     const bool upd[2] = {!c->opt.freeze_W, !c->opt.freeze_H};
-    GradParams GP{};
-    UpdParams UP{};
+    GP = GradParams{};
+    UP = UpdParams{};
     for (int s = 0; s < 2; ++s) {
         SideLayout &L = c->side[s];
         GradSide &Gs = GP.side[s];
@@ -653,6 +654,21 @@ psgld_status launch_part_step(psgld_ctx *c, int64_t t, const int64_t *t_dev, int
         k0 += 0x9E3779B9u;
         k1 += 0xBB67AE85u;
     }
+}
+
+psgld_status launch_part_step(psgld_ctx *c, int64_t t, const int64_t *t_dev, int64_t t_add,
+                              cudaStream_t st)
+{
+    const int B = c->B;
+    const int part = part_of_iteration(c, t);
+    const Shape sh = shape_for(c->ngroups);
+    GradFn gfn = pick_grad(sh);
+    if (!gfn) return fail(c, PSGLD_ERR_ARG, "unsupported K");
+    const bool dense = c->dense;
+    const bool upd[2] = {!c->opt.freeze_W, !c->opt.freeze_H};
+    GradParams GP;
+    UpdParams UP;
+    fill_params(c, part, t, t_dev, t_add, GP, UP);
 
     const int64_t units = GP.side[0].units + GP.side[1].units;
     const int ggrid = (int)((units + kGradThreads / 32 - 1) / (kGradThreads / 32));
@@ -687,6 +703,68 @@ psgld_status launch_part_step(psgld_ctx *c, int64_t t, const int64_t *t_dev, int
     }
     if (upd[0]) c->wcur ^= 1;
     if (upd[1]) c->hcur ^= 1;
+    return PSGLD_OK;
+}
+
+namespace {
+
+// ---- many contexts in one update launch ------------------------------------
+
+__global__ void __launch_bounds__(kThreads, 4)
+update_batch_kernel(const UpdParams *__restrict__ Ps, const int64_t *__restrict__ item_start, int n)
+{
+    const int64_t total = __ldg(item_start + n);
+    const int64_t stride = (int64_t)gridDim.x * kThreads;
+    int ci = -1;
+    float eps = 0.f, sd = 0.f;
+    uint32_t t_lo = 0, t_hi = 0;
+    for (int64_t a = blockIdx.x * (int64_t)kThreads + threadIdx.x; a < total; a += stride) {
+        if (ci < 0 || __ldg(item_start + ci + 1) <= a) {
+            int lo = ci < 0 ? 0 : ci, hi = n - 1;   // last i with item_start[i] <= a
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (__ldg(item_start + mid) <= a) lo = mid; else hi = mid - 1;
+            }
+            ci = lo;
+            const UpdParams &P = Ps[ci];
+            const int64_t t = P.t_dev ? *P.t_dev + P.t_add : P.t_add;
+            eps = P.eps;
+            sd = P.sd;
+            if (P.eps_poly) {
+                const double e = pow(P.eps_a / (double)t, P.eps_b);
+                eps = (float)e;
+                sd = (float)sqrt(2.0 * e);
+            }
+            t_lo = (uint32_t)(uint64_t)t;
+            t_hi = (uint32_t)((uint64_t)t >> 32);
+        }
+        const UpdParams &P = Ps[ci];
+        const int64_t local = a - __ldg(item_start + ci);
+        if (local < P.side[0].items) update_item<0>(P, local, eps, sd, t_lo, t_hi);
+        else update_item<1>(P, local - P.side[0].items, eps, sd, t_lo, t_hi);
+    }
+}
+
+}  // namespace
+
+size_t upd_param_bytes() { return sizeof(UpdParams); }
+
+int64_t fill_upd_param(psgld_ctx *c, int part, const int64_t *t_dev, int64_t t_add, void *dst)
+{
+    GradParams GP;
+    UpdParams UP;
+    fill_params(c, part, t_add, t_dev, t_add, GP, UP);
+    std::memcpy(dst, &UP, sizeof UP);
+    return UP.side[0].items + UP.side[1].items;
+}
+
+psgld_status launch_update_batch(psgld_ctx *c0, const void *params, const int64_t *item_start, int n,
+                                 int64_t total_items, cudaStream_t st)
+{
+    const int grid = (int)std::min<int64_t>((total_items + kThreads - 1) / kThreads, 152 * 16);
+    if (grid > 0)
+        update_batch_kernel<<<grid, kThreads, 0, st>>>(static_cast<const UpdParams *>(params), item_start, n);
+    PSGLD_CK(c0, cudaGetLastError());
     return PSGLD_OK;
 }
 

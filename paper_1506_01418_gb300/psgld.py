@@ -66,6 +66,7 @@ EXPORTS = [
     "psgld_sweep", "psgld_posterior_mean", "psgld_log_lik", "psgld_rmse", "psgld_piece_bounds",
     "psgld_part_schedule", "psgld_part_layout", "psgld_profile_read", "psgld_profile_read_split",
     "psgld_iterations_done", "psgld_estimate_device_bytes", "psgld_set_allocator",
+    "psgld_batch_sweep",
     "psgld_log_lik_static", "psgld_last_error",
     "psgld_destroy",
 ]
@@ -106,6 +107,7 @@ def load(build_if_missing: bool = True):
         "psgld_profile_read_split": (st, [vp, vp, vp, vp]),
         "psgld_estimate_device_bytes": (i64, [i64, i64, i32, i32, i64, i32, i32]),
         "psgld_set_allocator": (st, [C.POINTER(psgld_allocator)]),
+        "psgld_batch_sweep": (st, [vp, i32, i32, vp]),
         "psgld_iterations_done": (i64, [vp]),
         "psgld_log_lik_static": (st, [i64, vp, vp, vp, vp, vp, i64, i64, i32, f64, f64, f64, vp, vp]),
         "psgld_last_error": (C.c_char_p, [vp]),
@@ -309,6 +311,15 @@ def use_torch_allocator(device=None):
         torch.cuda.caching_allocator_delete(ptr)
 
     psgld_set_allocator(alloc_fn, free_fn)
+
+
+def psgld_batch_sweep(chains, n_sweeps=1, stream=None):
+    """n_sweeps sweeps of every chain (PSGLD objects), part-steps in shared launches."""
+    arr = (C.c_void_p * len(chains))(*[ch.ctx for ch in chains])
+    st = load().psgld_batch_sweep(arr, len(chains), int(n_sweeps), _stream(stream))
+    if st != PSGLD_OK:
+        msgs = [load().psgld_last_error(ch.ctx).decode() for ch in chains]
+        raise PsgldError(st, "; ".join(m for m in msgs if m))
 
 
 def psgld_estimate_device_bytes(I, J, K, B, nnz=0, dense_path=0, dense_v_bf16=0):

@@ -1,0 +1,142 @@
+"""Many dense chains sweeping in shared launches (psgld_batch_sweep).
+
+At every part of a sweep one tensor-core gradient launch per K class covers
+the blocks of all the chains of that class and one update launch covers all
+the chains' rows (Sec. 3's part-step, run for many independent chains at
+once).  Each chain reads only its own parameters, so a chain swept in a
+batch must end bit for bit where the same chain swept alone ends (alone
+through the captured-graph sweep): factors, posterior sums and iteration
+counter.  The batch mixes sizes (ragged blocks, blocks over one 128-row
+tile), ranks of every K class, Tweedie powers, both priors and both step
+size schedules.
+"""
+import numpy as np
+import pytest
+
+from paper_1506_01418_gb300 import datagen
+from paper_1506_01418_gb300 import psgld as P
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+# (I, J, K, p, prior_kind, eps_mode)
+MIX = [
+    (300, 700, 8, 1.0, 0, 0),
+    (513, 900, 16, 2.0, 0, 0),        # blocks of 128 and 129 rows: two M-tiles
+    (257, 4000, 32, 1.0, 0, 0),
+    (640, 1000, 32, 1.5, 0, 1),       # second chain of the K = 32 class, eps_t = (a/t)^b
+    (1025, 300, 64, 0.0, 1, 0),       # Gaussian likelihood and priors
+    (90, 61, 13, 3.0, 0, 0),
+    (200, 500, 100, 1.0, 0, 1),
+]
+B = 4
+
+
+def _chain(idx, I, J, K, p, kind, eps_mode, use_graphs, burn_in=1):
+    dev = torch.device("cuda", 0)
+    if p == 1.0:
+        V, _, _ = datagen.dense_poisson(I, J, 3, idx)
+    else:
+        V, _, _ = datagen.dense_gamma(I, J, 3, idx)
+    if p >= 2:
+        V = V + np.float32(0.5)
+    nonneg = kind == 0
+    W0, H0 = datagen.init_factors(I, J, K, seed=idx + 50, scale=0.4 if nonneg else 0.3,
+                                  nonneg=nonneg)
+    opts = dict(seed=1000 + idx, eps=1e-4, burn_in_sweeps=burn_in, dense_path=3,
+                use_graphs=use_graphs)
+    if eps_mode:
+        opts.update(eps_mode=P.PSGLD_EPS_POLY, eps_a=0.02, eps_b=0.55)
+    ch = P.PSGLD(I, J, K, B, p, 1.0, prior_kind=kind, lambda_w=0.8, lambda_h=1.2, sigma_w=0.9,
+                 sigma_h=1.1, **opts)
+    ch.set_data_dense(torch.from_numpy(np.ascontiguousarray(V, np.float32)).to(dev))
+    ch.set_factors(torch.from_numpy(W0).to(dev), torch.from_numpy(H0.T.copy()).to(dev))
+    return ch
+
+
+def _state(ch):
+    W, Ht = ch.get_factors()
+    torch.cuda.synchronize()
+    return W.cpu().numpy(), Ht.cpu().numpy(), ch.posterior_mean(), ch.iterations_done
+
+
+def _assert_same(a, b):
+    Wa, Ha, ma, ta = _state(a)
+    Wb, Hb, mb, tb = _state(b)
+    assert ta == tb
+    assert np.array_equal(Wa, Wb) and np.array_equal(Ha, Hb)
+    for x, y in zip(ma[:4], mb[:4]):
+        assert np.array_equal(x, y)
+    assert ma[4] == mb[4]
+
+
+def test_batched_sweeps_equal_sweeps_alone():
+    batch = [_chain(i, *m, use_graphs=0) for i, m in enumerate(MIX)]
+    alone = [_chain(i, *m, use_graphs=1) for i, m in enumerate(MIX)]
+    P.psgld_batch_sweep(batch, 2)
+    P.psgld_batch_sweep(batch, 1)
+    for ch in alone:
+        ch.sweep(3)
+    for a, b in zip(batch, alone):
+        _assert_same(a, b)
+        assert a.posterior_mean()[4] == 2
+    # the chains moved and stayed valid
+    for a, m in zip(batch, MIX):
+        W, Ht, _, _ = _state(a)
+        assert np.isfinite(W).all() and np.isfinite(Ht).all()
+        if m[4] == 0:
+            assert W.min() >= 0 and Ht.min() >= 0
+    for ch in batch + alone:
+        ch.close()
+
+
+def test_batch_of_one_and_zero_sweeps():
+    a = _chain(3, *MIX[3], use_graphs=0)
+    b = _chain(3, *MIX[3], use_graphs=0)
+    P.psgld_batch_sweep([a], 0)
+    assert a.iterations_done == 0
+    P.psgld_batch_sweep([a], 2)
+    b.sweep(2)
+    _assert_same(a, b)
+    a.close()
+    b.close()
+
+
+def test_batch_refusals():
+    good = _chain(0, *MIX[0], use_graphs=0)
+    other = _chain(2, *MIX[2], use_graphs=0)
+    # a context twice
+    with pytest.raises(P.PsgldError) as ex:
+        P.psgld_batch_sweep([good, other, good], 1)
+    assert ex.value.status == P.PSGLD_ERR_ARG
+    # not at a sweep boundary
+    other.part_step(1)
+    with pytest.raises(P.PsgldError) as ex:
+        P.psgld_batch_sweep([good, other], 1)
+    assert ex.value.status == P.PSGLD_ERR_STATE
+    # a two-sided context
+    I, J, K = 300, 700, 8
+    V, _, _ = datagen.dense_poisson(I, J, 3, 0)
+    two = P.PSGLD(I, J, K, B, 1.0, 1.0, dense_path=2)
+    two.set_data_dense(torch.from_numpy(V).cuda())
+    W0, H0 = datagen.init_factors(I, J, K, seed=1, scale=0.4, nonneg=True)
+    two.set_factors(torch.from_numpy(W0).cuda(), torch.from_numpy(H0.T.copy()).cuda())
+    with pytest.raises(P.PsgldError) as ex:
+        P.psgld_batch_sweep([good, two], 1)
+    assert ex.value.status == P.PSGLD_ERR_STATE
+    # another B
+    I, J, K = 100, 80, 8
+    V, _, _ = datagen.dense_poisson(I, J, 3, 0)
+    b3 = P.PSGLD(I, J, K, 3, 1.0, 1.0, dense_path=3)
+    b3.set_data_dense(torch.from_numpy(V).cuda())
+    W0, H0 = datagen.init_factors(I, J, K, seed=1, scale=0.4, nonneg=True)
+    b3.set_factors(torch.from_numpy(W0).cuda(), torch.from_numpy(H0.T.copy()).cuda())
+    with pytest.raises(P.PsgldError) as ex:
+        P.psgld_batch_sweep([good, b3], 1)
+    assert ex.value.status == P.PSGLD_ERR_ARG
+    # nothing ran on the refused calls
+    assert good.iterations_done == 0
+    for ch in (good, other, two, b3):
+        ch.close()

@@ -857,33 +857,27 @@ def batched_cpu_baseline(wl, spec, budget_s: float):
     return out
 
 
-def run_serving(args, wl_name, wl):
-    """The serving loop on one GPU: a Poisson trace of jobs replayed in real
-    time; value = observed entries x sweeps of every job and of the standing
-    chain / wall time of the trace; latency = completion - arrival."""
+def serve_trace(wl, executor, dev, uuid):
+    """Replay the workload's Poisson trace through the server on `executor`
+    (after a warm-up trace of one job per size class); returns the trace's
+    measurements."""
     import numpy as np
     import torch
 
-    import __graft_entry__
-    __graft_entry__.build()
     from paper_1506_01418_gb300 import serving
-    dev = torch.device("cuda", 0)
-    torch.cuda.set_device(dev)
-    ex = serving.GpuExecutor(0)
     factory = serving.mixed_job_factory(wl["sweeps"], wl["burn_in"], wl["B"], wl["eps"])
-    # warm-up: one job of each size class (module loads, graph captures)
     warm = []
     for k, (I, K, p) in enumerate([(I, K, p) for I in (257, 513, 1025) for K in (16, 64) for p in (1.0, 1.5)]):
         j = factory(10_000 + k, 0.0, np.random.Generator(np.random.Philox(k)))
         j.I, j.K, j.p, j.J = I, K, p, 800
         warm.append(j)
-    wsrv = serving.Server(ex, wl["budget_bytes"])
+    wsrv = serving.Server(executor, wl["budget_bytes"])
     try:
         wsrv.run(warm, idle_sleep=0)
     finally:
         wsrv.close()
     jobs = serving.poisson_trace(wl["rate"], wl["duration"], seed=2024, job_factory=factory)
-    srv = serving.Server(ex, wl["budget_bytes"])
+    srv = serving.Server(executor, wl["budget_bytes"])
     standing = None
     if wl.get("standing"):
         sw = WORKLOADS[wl["standing"]]
@@ -893,17 +887,10 @@ def run_serving(args, wl_name, wl):
         srv.submit(standing)
         srv.poll(0.0)
         torch.cuda.synchronize(dev)
-    uuid = None
-    try:
-        uuid = str(torch.cuda.get_device_properties(dev).uuid)
-        uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
-    except Exception:
-        uuid = "0"
     sampler = ClockSampler(uuid)
+    ticks0 = getattr(executor, "ticks", 0)
     w0 = time.time()
-    st0 = None
-    if standing is not None:
-        st0 = srv.active[-1][1]["sweeps_queued"]
+    st0 = srv.active[-1][1]["sweeps_queued"] if standing is not None else 0
     try:
         wall = srv.run(jobs, idle_sleep=0)
         st_sweeps = (srv.active[-1][1]["sweeps_queued"] - st0) if standing is not None else 0
@@ -914,35 +901,81 @@ def run_serving(args, wl_name, wl):
     torch.cuda.synchronize(dev)
     time.sleep(0.25)
     sampler.stop()
-    lat = serving.latency_summary(jobs)
     job_entries = sum(j.I * j.J * j.sweeps for j in jobs)
     st_entries = (standing.I * standing.J * st_sweeps) if standing is not None else 0
-    value = (job_entries + st_entries) / wall
+    return {"jobs": jobs, "wall": wall, "job_entries": job_entries, "st_entries": st_entries,
+            "st_sweeps": st_sweeps, "standing": standing, "peak_used": srv.peak_used,
+            "clocks": sampler.summary(w0, w1), "warm": len(warm),
+            "ticks": getattr(executor, "ticks", 0) - ticks0}
+
+
+def run_serving(args, wl_name, wl):
+    """The serving loop on one GPU: a Poisson trace of jobs replayed in real
+    time with continuous batching (every admitted job's part-steps share the
+    batch's launches); value = observed entries x sweeps of every job and of
+    the standing chain / wall time of the trace; latency = completion -
+    arrival.  The same trace with one stream and context per job (no shared
+    launches) is reported beside it."""
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1506_01418_gb300 import serving
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+        uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+    except Exception:
+        uuid = "0"
+    bex = serving.BatchedGpuExecutor(0)
+    r = serve_trace(wl, bex, dev, uuid)
+    jobs, wall = r["jobs"], r["wall"]
+    value = (r["job_entries"] + r["st_entries"]) / wall
+    lat = serving.latency_summary(jobs)
+    sizes = bex.batch_sizes[-r["ticks"]:] if r["ticks"] else []
     h2d = sum(4 * (j.I + j.J) * j.K for j in jobs)
     d2h = sum(8 * (j.I + j.J) * j.K * 2 for j in jobs)
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": len(jobs),
-        "warmup": len(warm), "ms_per_step": wall * 1e3 / max(1, len(jobs)), "higher_is_better": True,
+        "warmup": r["warm"], "ms_per_step": wall * 1e3 / max(1, len(jobs)), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
         "config": {"workload": wl_name, "arrival_rate_per_s": wl["rate"], "trace_s": wl["duration"],
                    "jobs": len(jobs), "sweeps_per_job": wl["sweeps"], "B": wl["B"],
                    "hbm_budget_bytes": wl["budget_bytes"], "standing_chain": wl.get("standing"),
                    "step": "one job of the trace (value counts every job's and the standing "
                            "chain's entries x sweeps over the trace's wall time)",
-                   "path": "tensor-core block chain per job (dense_path 1), own stream and context "
-                           "per job, PyTorch caching allocator"},
+                   "path": "continuous batching: every admitted job's part-steps in the batch's "
+                           "shared tensor-core launches (psgld_batch_sweep, one sweep per tick, "
+                           "at most three ticks queued); the standing chain on its own stream; "
+                           "PyTorch caching allocator"},
         "latency": lat,
-        "job_entries_per_s": job_entries / wall,
-        "standing_chain": {"sweeps": st_sweeps, "entries_per_s": st_entries / wall} if standing else None,
-        "peak_budget_used_bytes": srv.peak_used,
+        "job_entries_per_s": r["job_entries"] / wall,
+        "standing_chain": ({"sweeps": r["st_sweeps"], "entries_per_s": r["st_entries"] / wall}
+                           if r["standing"] else None),
+        "batch": {"ticks": r["ticks"], "jobs_per_tick_mean": (sum(sizes) / len(sizes)) if sizes else 0,
+                  "jobs_per_tick_max": max(sizes) if sizes else 0},
+        "peak_budget_used_bytes": r["peak_used"],
         "roofline": None,
-        "gpu_launches": sum(j.sweeps * (2 * j.B + 3) for j in jobs) + st_sweeps * (2 * 16 + 3),
-        "clocks": sampler.summary(w0, w1),
+        # per tick: set t, B x (one gradient launch per K class (2) + update),
+        # accumulate, advance t; standing chain: 2B + 3 per sweep
+        "gpu_launches": r["ticks"] * (3 * wl["B"] + 3) + r["st_sweeps"] * (2 * 16 + 3),
+        "clocks": r["clocks"],
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": h2d / max(1, len(jobs)),
                 "d2h_bytes_per_step": d2h / max(1, len(jobs)),
                 "note": "the serving loop is the end-to-end path: each job's initial factors go "
                         "host to device and its posterior means device to host inside the trace"},
     }
+    del bex
+    torch.cuda.empty_cache()
+    if not args.no_serving_compare:
+        r2 = serve_trace(wl, serving.GpuExecutor(0), dev, uuid)
+        result["per_job_streams"] = {
+            "value": (r2["job_entries"] + r2["st_entries"]) / r2["wall"], "unit": UNIT,
+            "job_entries_per_s": r2["job_entries"] / r2["wall"],
+            "latency": serving.latency_summary(r2["jobs"]), "clocks": r2["clocks"],
+            "how": "the same trace, one stream and context per job with all its sweeps enqueued "
+                   "at admission (no shared launches)"}
     print(json.dumps(result), flush=True)
 
 
@@ -1032,6 +1065,8 @@ def main():
     ap.add_argument("--compare-sweeps", type=int, default=20,
                     help="tensor-core workloads: sweeps of the BF16 vs FP32 comparison (0 = off)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving-compare", action="store_true",
+                    help="serving workload: skip the per-job-streams replay of the trace")
     ap.add_argument("--cpu-budget", type=float, default=15.0,
                     help="seconds of oracle work for the cpu_baseline sample")
     ap.add_argument("--reference-budget", type=float, default=120.0,

@@ -197,8 +197,12 @@ PSGLD_API psgld_status psgld_sweep(psgld_ctx *ctx, int32_t n_sweeps, void *strea
  * with blocks of at most 128 rows and K <= 128, or dense_path 3), the same
  * B, cyclic parts and its iteration counter at a sweep boundary; sizes,
  * powers, priors, seeds and step sizes may differ.  Each context ends in the
- * same state, bit for bit, as after psgld_sweep(ctx, n_sweeps).  Returns
- * after the work has run (synchronises `stream`). */
+ * same state, bit for bit, as after psgld_sweep(ctx, n_sweeps).  The work
+ * is enqueued on `stream` (the call returns before it runs, like
+ * psgld_sweep); the launches' parameter tables are kept by the first context
+ * of the list and reused by its next batch.  A context may be in one batch
+ * at a time: a call whose list shares a context with a batch still running
+ * on another stream must be ordered after it by the caller. */
 PSGLD_API psgld_status psgld_batch_sweep(psgld_ctx *const *ctxs_host, int32_t n, int32_t n_sweeps,
                                          void *stream);
 

@@ -44,6 +44,25 @@ void dev_free(psgld_ctx *c, void *p, cudaStream_t st)
     else cudaFree(p);
 }
 
+void mark_enqueued(psgld_ctx *c, cudaStream_t st)
+{
+    c->last_stream = st;
+    c->last_ev_set = false;
+    if (!c->last_ev && cudaEventCreateWithFlags(&c->last_ev, cudaEventDisableTiming) != cudaSuccess) {
+        c->last_ev = nullptr;
+        cudaGetLastError();
+        return;
+    }
+    if (cudaEventRecord(c->last_ev, st) == cudaSuccess) c->last_ev_set = true;
+    else cudaGetLastError();
+}
+
+cudaError_t wait_enqueued(psgld_ctx *c)
+{
+    if (c->last_ev && c->last_ev_set) return cudaEventSynchronize(c->last_ev);
+    return cudaStreamSynchronize(c->last_stream);
+}
+
 psgld_status fail(psgld_ctx *c, psgld_status s, const std::string &msg)
 {
     if (c) c->err = msg;
@@ -362,7 +381,7 @@ psgld_status psgld_profile_read_split(psgld_ctx *c, double *grad_ms, double *upd
 {
     if (!c || !grad_ms || !update_ms || !launches) return PSGLD_ERR_ARG;
     if (!c->opt.profile) return fail(c, PSGLD_ERR_STATE, "profiling is off");
-    PSGLD_CK(c, cudaStreamSynchronize(c->last_stream));
+    PSGLD_CK(c, wait_enqueued(c));
     {
         psgld_status fs = check_kernel_flag(c);
         if (fs != PSGLD_OK) return fs;
@@ -537,7 +556,7 @@ psgld_status psgld_get_factors(psgld_ctx *c, float *W, float *Ht, void *stream)
     const size_t row = sizeof(float) * c->K, pitch = sizeof(float) * c->ldk;
     if (W) PSGLD_CK(c, cudaMemcpy2DAsync(W, row, c->W[c->wcur], pitch, row, c->I, cudaMemcpyDefault, st));
     if (Ht) PSGLD_CK(c, cudaMemcpy2DAsync(Ht, row, c->Ht[c->hcur], pitch, row, c->J, cudaMemcpyDefault, st));
-    c->last_stream = st;
+    mark_enqueued(c, st);
     return PSGLD_OK;
 }
 
@@ -551,7 +570,7 @@ psgld_status psgld_part_step(psgld_ctx *c, int64_t t, void *stream)
     s = launch_part_step(c, t, nullptr, 0, st);
     if (s != PSGLD_OK) return s;
     c->t_done = t;
-    c->last_stream = st;
+    mark_enqueued(c, st);
     return PSGLD_OK;
 }
 
@@ -598,6 +617,7 @@ psgld_status psgld_sweep(psgld_ctx *c, int32_t n_sweeps, void *stream)
         c->sweeps_done += 1;
         if (acc) c->n_samples += 1;
     }
+    mark_enqueued(c, st);
     return PSGLD_OK;
 }
 
@@ -605,7 +625,7 @@ psgld_status psgld_posterior_mean(psgld_ctx *c, double *Wm, double *Wv, double *
                                   int64_t *n_samples)
 {
     if (!c) return PSGLD_ERR_ARG;
-    PSGLD_CK(c, cudaStreamSynchronize(c->last_stream));
+    PSGLD_CK(c, wait_enqueued(c));
     {
         psgld_status fs = check_kernel_flag(c);
         if (fs != PSGLD_OK) return fs;
@@ -746,7 +766,8 @@ psgld_status psgld_batch_sweep(psgld_ctx *const *ctxs, int32_t n, int32_t n_swee
     const size_t off_up = up256(off_dp + dp * (size_t)nq * B * n);
     const size_t off_ap = up256(off_up + upb * (size_t)nq * B * n);
     const size_t total = up256(off_ap + ap * (size_t)nq * n);
-    std::vector<unsigned char> tab(total, 0);
+    std::vector<unsigned char> &tab = c0->btab;
+    tab.assign(total, 0);
     int *cta = reinterpret_cast<int *>(tab.data() + off_cta);
     int64_t *items = reinterpret_cast<int64_t *>(tab.data() + off_items);
     int64_t *units = reinterpret_cast<int64_t *>(tab.data() + off_units);
@@ -799,10 +820,33 @@ psgld_status psgld_batch_sweep(psgld_ctx *const *ctxs, int32_t n, int32_t n_swee
     }
     for (int i = 0; i < n; ++i) set_state(i, (int64_t)n_sweeps * B);
 
-    unsigned char *d = static_cast<unsigned char *>(dev_alloc(c0, total, st));
-    if (!d) return fail(c0, PSGLD_ERR_OOM, "device allocation failed");
+    // the device tables live in the leading context and are reused by its
+    // next batch, ordered after the launches of this one by `bdone`
+    cudaError_t e = cudaSuccess;
+    if (!c0->bdone) {
+        e = cudaEventCreateWithFlags(&c0->bdone, cudaEventDisableTiming);
+        if (e != cudaSuccess) { c0->bdone = nullptr; return cuda_fail(c0, e, "cudaEventCreate"); }
+        e = cudaEventRecord(c0->bdone, st);
+        if (e != cudaSuccess) return cuda_fail(c0, e, "cudaEventRecord");
+    }
+    if (c0->bscratch_bytes < total) {
+        if (c0->bscratch) {
+            cudaEventSynchronize(c0->bdone);
+            dev_free(c0, c0->bscratch, st);
+            c0->bscratch = nullptr;
+            c0->bscratch_bytes = 0;
+        }
+        c0->bscratch = dev_alloc(c0, total, st);
+        if (!c0->bscratch) return fail(c0, PSGLD_ERR_OOM, "device allocation failed");
+        c0->bscratch_bytes = total;
+    } else {
+        e = cudaStreamWaitEvent(st, c0->bdone, 0);
+        if (e != cudaSuccess) return cuda_fail(c0, e, "cudaStreamWaitEvent");
+    }
+    unsigned char *d = static_cast<unsigned char *>(c0->bscratch);
     psgld_status s = PSGLD_OK;
-    cudaError_t e = cudaMemcpyAsync(d, tab.data(), total, cudaMemcpyHostToDevice, st);
+    // from pageable memory: the source is consumed before the call returns
+    e = cudaMemcpyAsync(d, tab.data(), total, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) s = cuda_fail(c0, e, "copy of the batch tables");
     if (s == PSGLD_OK) s = launch_t_batch(c0, d + off_ap, n, 0, st);
     // profiling (first context's option): events around each part's launches,
@@ -845,13 +889,11 @@ psgld_status psgld_batch_sweep(psgld_ctx *const *ctxs, int32_t n, int32_t n_swee
                 c->sweeps_done += 1;
             }
             c->t_done += (int64_t)B * n_sweeps;
-            c->last_stream = st;
+            mark_enqueued(c, st);
         }
     }
-    // the tables are read by the launches: free after they ran
-    e = cudaStreamSynchronize(st);
-    dev_free(c0, d, st);
-    if (s == PSGLD_OK && e != cudaSuccess) s = cuda_fail(c0, e, "sync");
+    e = cudaEventRecord(c0->bdone, st);
+    if (s == PSGLD_OK && e != cudaSuccess) s = cuda_fail(c0, e, "cudaEventRecord");
     return s;
 }
 
@@ -906,8 +948,14 @@ void psgld_destroy(psgld_ctx *c)
     destroy_events(c);
     free_layout(c);
     // the context's work must be finished before its memory is handed back
-    if (c->last_stream) cudaStreamSynchronize(c->last_stream);
+    wait_enqueued(c);
+    if (c->last_ev) cudaEventDestroy(c->last_ev);
     if (c->capture_stream) cudaStreamSynchronize(c->capture_stream);
+    if (c->bdone) {
+        cudaEventSynchronize(c->bdone);
+        cudaEventDestroy(c->bdone);
+    }
+    dev_free(c, c->bscratch);
     for (int b = 0; b < 2; ++b) { dev_free(c, c->W[b]); dev_free(c, c->Ht[b]); }
     dev_free(c, c->G);
     dev_free(c, c->sW.s); dev_free(c, c->sW.s2); dev_free(c, c->sH.s); dev_free(c, c->sH.s2);

@@ -41,7 +41,7 @@
 namespace psgld {
 namespace {
 
-constexpr int kDenseThreads = 128;
+constexpr int kDenseThreads = 256;
 constexpr int kTile = 128;   // rows of an M-tile = columns of an n-tile
 constexpr uint32_t kTmemCols = 256;
 constexpr uint32_t kDenseWaitLimit = 1u << 30;
@@ -183,18 +183,9 @@ __device__ __forceinline__ bool bar_wait(uint64_t *bar, uint32_t parity)
     return false;
 }
 
-__device__ __forceinline__ float tweedie(const DenseParams &P, float v, float mu)
-{
-    const float d = v - mu;
-    if (P.p_mode == 0) return d * P.phi_inv;
-    const float mc = fmaxf(mu, P.mu_min);
-    if (P.p_mode == 1) return d / mc * P.phi_inv;
-    if (P.p_mode == 2) return d / (mc * mc) * P.phi_inv;
-    return d * exp2f(-P.p * log2f(mc)) * P.phi_inv;
-}
-
-// The same factor with fast reciprocal / exp2 / log2 (relative error a few
-// 2^-22, far below the BF16 rounding of E that follows).
+// Tweedie factor (v - mu) max(mu, mu_min)^-p / phi of one entry with fast
+// reciprocal / exp2 / log2 (relative error a few 2^-22, far below the BF16
+// rounding of E that follows); p_mode 0..2 for p = 0, 1, 2, else the power.
 __device__ __forceinline__ float tweedie_fast(int p_mode, float p, float phi_inv, float mu_min,
                                               float v, float mu)
 {
@@ -206,9 +197,46 @@ __device__ __forceinline__ float tweedie_fast(int p_mode, float p, float phi_inv
     return d * exp2f(-p * __log2f(mc));
 }
 
-__device__ __forceinline__ void st_bf16(unsigned char *base, uint32_t off, float x)
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)
 {
-    *reinterpret_cast<__nv_bfloat16 *>(base + off) = __float2bfloat16_rn(x);
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);   // lo at the lower address
+    return *reinterpret_cast<const uint32_t *>(&v);
+}
+
+// Row `src_row` (valid if < end) of an FP32 n x ldk matrix into row r of a
+// 128 x KP K-major BF16 tile, zero padded; half h of the K range.
+template <int KP>
+__device__ __forceinline__ void stage_rows(unsigned char *tile, const float *__restrict__ X, int64_t src_row,
+                                           int64_t end, int K, int ldk, int r, int h)
+{
+    const bool v = src_row < end;
+    constexpr int kHalf = KP / 2;
+#pragma unroll
+    for (int k = h * kHalf; k < (h + 1) * kHalf; k += 4) {
+        float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (v && k < K) x = __ldg(reinterpret_cast<const float4 *>(X + src_row * ldk + k));
+        const float a = x.x, b = k + 1 < K ? x.y : 0.f, c = k + 2 < K ? x.z : 0.f,
+                    d = k + 3 < K ? x.w : 0.f;
+        *reinterpret_cast<uint2 *>(tile + cm_off(r, k, KP)) = make_uint2(pack_bf16x2(a, b), pack_bf16x2(c, d));
+    }
+}
+
+// 32-column chunks of a TMEM row block (this thread's lane) to an FP32 row
+// in global memory: chunk c goes to half (c / 32) mod 2.
+template <int KP>
+__device__ __forceinline__ void drain_rows(uint32_t taddr, float *dst, bool valid, int ldk, int h)
+{
+#pragma unroll
+    for (int c = 32 * h; c < KP; c += 64) {
+        float g[32];
+        tmem_ld32(taddr + (uint32_t)c, g);
+        if (valid) {
+#pragma unroll
+            for (int j = 0; j < 32; j += 4)
+                if (c + j < ldk)
+                    *reinterpret_cast<float4 *>(dst + c + j) = make_float4(g[j], g[j + 1], g[j + 2], g[j + 3]);
+        }
+    }
 }
 
 // One CTA of the single-pass kernel: CTA number `cta` of the launch for the
@@ -257,43 +285,39 @@ __device__ __forceinline__ void dense_grad_cta(const DenseParams &P, int cta)
     __syncthreads();
     fence_after();
     const uint32_t tmem = *tslot;
-    const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
+    // Two warps per TMEM lane quadrant: thread t works on tile row / column
+    // r = t mod 128 (its quadrant's lanes) and on half h = t / 128 of the
+    // columns it loads, converts or drains.
+    const int r = tid & (kTile - 1), h = tid >> 7;
+    const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
     uint32_t phase = 0;
     bool ok = true;
 
     // own rows of this M-tile: W (GEMM1 A) and W^T (GEMM3 B), BF16, zero padded
-    {
-        const int64_t row = m0 + tid;
-        const bool rv = row < re;
-        for (int k = 0; k < KP; k += 4) {
-            float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (rv && k < K) w = *reinterpret_cast<const float4 *>(P.W + row * ldk + k);
-            const float wv[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-            for (int d = 0; d < 4; ++d) {
-                st_bf16(A1, cm_off(tid, k + d, KP), k + d < K ? wv[d] : 0.f);
-            }
-        }
-    }
+    stage_rows<KP>(A1, P.W, m0 + r, re, K, ldk, r, h);
 
     const uint64_t aW = sdesc(saddr(A1), 128, KP * 16);
     const int ntiles = (int)((ce - cs + kTile - 1) / kTile);
+    const float *__restrict__ vbase = P.V;
+    const int64_t ldv = P.ldv;
+    const int p_mode = P.p_mode;
+    const float pw = P.p, phi_inv = P.phi_inv, mu_min = P.mu_min;
+    const int64_t row = m0 + r;
+    const bool rv = row < re;
+    const float *__restrict__ vrow = vbase + (rv ? row : rs) * ldv;
     for (int nt = 0; nt < ntiles && ok; ++nt) {
         const int64_t n0 = cs + (int64_t)nt * kTile;
-        // column tile: H^T rows (GEMM1 B) and H (GEMM2 B)
-        {
-            const int64_t col = n0 + tid;
-            const bool cv = col < ce;
-            for (int k = 0; k < KP; k += 4) {
-                float4 h = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (cv && k < K) h = *reinterpret_cast<const float4 *>(P.Ht + col * ldk + k);
-                const float hv[4] = {h.x, h.y, h.z, h.w};
+        // this thread's 64 values of V (row `row`, columns n0 + 64 h ...), all
+        // requested before the column tile is staged and GEMM1 runs, so that
+        // their latency overlaps both
+        float vv[64];
 #pragma unroll
-                for (int d = 0; d < 4; ++d) {
-                    st_bf16(B1, cm_off(tid, k + d, KP), k + d < K ? hv[d] : 0.f);
-                }
-            }
+        for (int j = 0; j < 64; ++j) {
+            const int64_t col = n0 + 64 * h + j;
+            vv[j] = (rv && col < ce) ? __ldg(vrow + col) : 0.f;
         }
+        // column tile: H^T rows (GEMM1 B) and H (GEMM2 B)
+        stage_rows<KP>(B1, P.Ht, n0 + r, ce, K, ldk, r, h);
         fence_async_smem();
         fence_before();
         __syncthreads();
@@ -314,20 +338,28 @@ __device__ __forceinline__ void dense_grad_cta(const DenseParams &P, int cta)
         fence_after();
 
         // epilogue: E = Tweedie factor of mu, masked to the block, BF16,
-        // into E (rows m) and E^T (rows n)
-        {
-            const int64_t row = m0 + tid;
-            const bool rv = row < re;
-            for (int c = 0; c < kTile; c += 32) {
-                float mu[32];
-                tmem_ld32(tmem + lane_base + (uint32_t)c, mu);
+        // into E (rows m) and E^T (rows n); eight columns per 16-byte store
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const int64_t col = n0 + c + j;
-                    float e = 0.f;
-                    if (rv && col < ce) e = tweedie(P, P.V[row * P.ldv + col], mu[j]);
-                    st_bf16(A2, cm_off(tid, c + j, kTile), e);
+        for (int cc = 0; cc < 2; ++cc) {
+            const int c = 64 * h + 32 * cc;
+            float mu[32];
+            tmem_ld32(tmem + lane_base + (uint32_t)c, mu);
+#pragma unroll
+            for (int j8 = 0; j8 < 32; j8 += 8) {
+                uint32_t pk[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    float e2[2];
+#pragma unroll
+                    for (int d = 0; d < 2; ++d) {
+                        const int j = j8 + 2 * q + d;
+                        const bool in = rv && n0 + c + j < ce;
+                        e2[d] = in ? tweedie_fast(p_mode, pw, phi_inv, mu_min, vv[32 * cc + j], mu[j]) : 0.f;
+                    }
+                    pk[q] = pack_bf16x2(e2[0], e2[1]);
                 }
+                *reinterpret_cast<uint4 *>(A2 + cm_off(r, c + j8, kTile)) =
+                    make_uint4(pk[0], pk[1], pk[2], pk[3]);
             }
         }
         fence_async_smem();
@@ -359,24 +391,15 @@ __device__ __forceinline__ void dense_grad_cta(const DenseParams &P, int cta)
         if (!__syncthreads_and(ok)) { ok = false; break; }
         fence_after();
 
-        // G_H of this column tile: thread t = column n0 + t (every lane takes
-        // part in the warp-wide TMEM loads; only real columns store)
+        // G_H of this column tile: thread = column n0 + r, 32-column chunks
+        // of TMEM split between the two halves (every lane of a warp takes
+        // part in its TMEM loads; only real columns store)
         {
-            const int64_t col = n0 + tid;
+            const int64_t col = n0 + r;
             const bool cv = col < ce;
             float *dst = P.mtiles == 1 ? P.G + (P.I + col) * ldk
                                        : P.hpart + ((int64_t)mt * P.J + col) * ldk;
-            for (int c = 0; c < KP; c += 32) {
-                float g[32];
-                tmem_ld32(tmem + lane_base + (uint32_t)c, g);
-                if (cv) {
-#pragma unroll
-                    for (int j = 0; j < 32; j += 4)
-                        if (c + j < ldk)
-                            *reinterpret_cast<float4 *>(dst + c + j) =
-                                make_float4(g[j], g[j + 1], g[j + 2], g[j + 3]);
-                }
-            }
+            drain_rows<KP>(tmem + lane_base, dst, cv, ldk, h);
         }
         fence_before();
         __syncthreads();
@@ -384,19 +407,8 @@ __device__ __forceinline__ void dense_grad_cta(const DenseParams &P, int cta)
     }
 
     if (ok) {
-        // G_W: thread t = row m0 + t
-        const int64_t row = m0 + tid;
-        for (int c = 0; c < KP; c += 32) {
-            float g[32];
-            tmem_ld32(tmem + lane_base + (uint32_t)(kTile + c), g);
-            if (row < re) {
-#pragma unroll
-                for (int j = 0; j < 32; j += 4)
-                    if (c + j < ldk)
-                        *reinterpret_cast<float4 *>(P.G + row * ldk + c + j) =
-                            make_float4(g[j], g[j + 1], g[j + 2], g[j + 3]);
-            }
-        }
+        // G_W: thread = row m0 + r
+        drain_rows<KP>(tmem + lane_base + (uint32_t)kTile, P.G + row * ldk, rv, ldk, h);
     } else {
         if (tid == 0) atomicOr(P.err, 32);   // single-pass dense kernel
         bar_wait(bar, phase ^ 1u);   // give in-flight MMAs one more bounded chance

@@ -101,7 +101,9 @@ struct psgld_ctx {
     std::vector<double> red_host;          // host copy
     int *flag = nullptr;         // device error flag of the layout build and input checks
     int *kflag = nullptr;        // device error flag of the sampling kernels (16: wait ran out)
-    cudaStream_t last_stream = nullptr;
+    cudaStream_t last_stream = nullptr;   // stream of the latest enqueued work
+    cudaEvent_t last_ev = nullptr;         // recorded after it (when last_ev_set)
+    bool last_ev_set = false;
 
     // CUDA graphs of one sweep, per parity of the ping-pong buffers, without
     // and with the posterior accumulation
@@ -109,6 +111,14 @@ struct psgld_ctx {
     cudaGraphExec_t graph_acc[4] = {nullptr, nullptr, nullptr, nullptr};
     cudaStream_t capture_stream = nullptr;
     int64_t *t_dev = nullptr;    // iteration counter read by graph replays
+
+    // psgld_batch_sweep's parameter tables while this context leads a batch
+    // (is first in the list): device copy, its size, an event recorded after
+    // the last launch that read it, and the host staging buffer
+    void *bscratch = nullptr;
+    size_t bscratch_bytes = 0;
+    cudaEvent_t bdone = nullptr;
+    std::vector<unsigned char> btab;
 
     // profiling: one event pair per part (start, end), and which are unread
     std::vector<cudaEvent_t> ev_start, ev_mid, ev_end;   // mid: after the gradient kernel
@@ -122,6 +132,13 @@ namespace psgld {
 // returns nullptr on failure; dev_free(nullptr) does nothing.
 void *dev_alloc(psgld_ctx *c, size_t bytes, cudaStream_t st);
 void dev_free(psgld_ctx *c, void *p, cudaStream_t st = nullptr);
+
+// ---- ordering ----------------------------------------------------------------
+// After enqueueing work of c on st: remember the stream and record an event
+// behind the work.  wait_enqueued blocks until that work has run (not the
+// rest of the stream), or syncs the last stream if no event was recorded.
+void mark_enqueued(psgld_ctx *c, cudaStream_t st);
+cudaError_t wait_enqueued(psgld_ctx *c);
 
 // ---- error plumbing ------------------------------------------------------
 psgld_status fail(psgld_ctx *c, psgld_status s, const std::string &msg);

@@ -319,7 +319,7 @@ psgld_status radix_sort(psgld_ctx *c, uint64_t *&k0, uint32_t *&v0, uint64_t *&k
 void free_layout(psgld_ctx *c)
 {
     // work that reads the layouts must be finished before they are handed back
-    cudaStreamSynchronize(c->last_stream);
+    wait_enqueued(c);
     if (c->capture_stream) cudaStreamSynchronize(c->capture_stream);
     for (auto &sd : c->side) {
         dev_free(c, sd.ptr); dev_free(c, sd.idx); dev_free(c, sd.val); dev_free(c, sd.own);

@@ -13,6 +13,14 @@ caching allocator) released, which lets the next jobs in.  A standing chain
 (a job without an end) can share the device: the loop keeps one sweep of it
 queued at all times.
 
+With `BatchedGpuExecutor` the jobs' part-steps share launches instead
+(continuous batching at sweep granularity): every admitted job joins the
+next sweep of one shared batch, and each loop iteration that finds fewer
+than three batch sweeps in flight enqueues one more over all unfinished jobs
+(per part one tensor-core gradient launch per K class and one update
+launch, through psgld_batch_sweep).  Jobs arriving meanwhile join at the
+next sweep; a finished job leaves the batch and its memory is released.
+
 The scheduler (`Server`) is separate from the executor that touches the GPU,
 so its admission and accounting logic runs on the CPU with a stand-in
 executor.  Latency of a job = completion time - arrival time on the host
@@ -67,6 +75,9 @@ class Server:
     executor.done(handle) -> bool          (non-blocking)
     executor.finish(job, handle) -> dict   (results; frees the job's memory)
     executor.step_standing(job, handle)    (keep a standing chain's sweep queued)
+    executor.tick()                        (optional: called once per poll, after
+                                            admission; a batching executor
+                                            advances its jobs here)
     """
 
     def __init__(self, executor, hbm_budget: int, max_active: int = 64):
@@ -98,6 +109,7 @@ class Server:
                 self.used -= nbytes
                 self.done.append(job)
                 finished.append(job)
+        tick = getattr(self.ex, "tick", None)
         while self.waiting and len(self.active) < self.max_active:
             job = self.waiting[0]
             nbytes = int(self.ex.estimate(job))
@@ -110,6 +122,8 @@ class Server:
             self.active[job.job_id] = (job, self.ex.start(job), nbytes)
             self.used += nbytes
             self.peak_used = max(self.peak_used, self.used)
+        if tick is not None:
+            tick()
         return finished
 
     def run(self, jobs, clock: Callable[[], float] = time.perf_counter, idle_sleep: float = 1e-4,
@@ -220,7 +234,8 @@ class GpuExecutor:
 
     def start(self, job: Job):
         torch = self.torch
-        stream = torch.cuda.Stream(self.dev)
+        # finite jobs ahead of a standing chain when both have work queued
+        stream = torch.cuda.Stream(self.dev, priority=0 if job.sweeps is None else -1)
         with torch.cuda.stream(stream):
             V, W0, Ht0 = self._data(job)
             ctx = self.P.PSGLD(job.I, job.J, job.K, job.B, job.p, job.phi,
@@ -250,6 +265,94 @@ class GpuExecutor:
 
     def finish(self, job: Job, h) -> dict:
         h["event"].synchronize()
+        Wm, Wv, Hm, Hv, n = h["ctx"].posterior_mean()
+        out = {"Wmean": Wm, "Hmean": Hm, "n_samples": n, "sweeps": h["sweeps_queued"]}
+        h["ctx"].close()
+        return out
+
+
+class BatchedGpuExecutor(GpuExecutor):
+    """Continuous batching: the part-steps of all admitted jobs share
+    launches.  Jobs run on one stream; each tick (when fewer than
+    `max_inflight` batch sweeps are queued) enqueues one psgld_batch_sweep
+    over every unfinished job, so each advances by one sweep per tick.  Jobs
+    the batched kernel cannot take (K > 128) and standing chains run on
+    their own streams as in GpuExecutor."""
+
+    def __init__(self, device=None, max_inflight: int = 3):
+        super().__init__(device)
+        torch = self.torch
+        self.stream = torch.cuda.Stream(self.dev, priority=-1)   # the batch's sweeps
+        self.adm = torch.cuda.Stream(self.dev, priority=-1)      # admitted jobs' data and set-up
+        self.members: list = []
+        self.inflight: collections.deque = collections.deque()
+        self.max_inflight = int(max_inflight)
+        self.ticks = 0
+        self.batch_sizes: list = []
+
+    @staticmethod
+    def batchable(job: Job) -> bool:
+        return job.sweeps is not None and job.K <= 128 and not job.dense_v_bf16
+
+    def estimate(self, job: Job) -> int:
+        if not self.batchable(job):
+            return super().estimate(job)
+        nbytes = self.P.psgld_estimate_device_bytes(job.I, job.J, job.K, job.B, 0, 3, 0)
+        return nbytes + 4 * job.I * job.J
+
+    def start(self, job: Job):
+        if not self.batchable(job):
+            return super().start(job)
+        torch = self.torch
+        # set-up synchronises its own stream only, so the batch's queued
+        # sweeps keep running while a job is admitted
+        with torch.cuda.stream(self.adm):
+            V, W0, Ht0 = self._data(job)
+            ctx = self.P.PSGLD(job.I, job.J, job.K, job.B, job.p, job.phi,
+                               prior_kind=self.P.PSGLD_PRIOR_EXPONENTIAL, lambda_w=job.lam,
+                               lambda_h=job.lam, seed=job.seed, eps=job.eps, use_graphs=0,
+                               burn_in_sweeps=job.burn_in, dense_path=3)
+            ctx.set_data_dense(V, self.adm.cuda_stream)
+            ctx.set_factors(W0, Ht0, self.adm.cuda_stream)
+            del V, W0, Ht0
+        h = {"ctx": ctx, "left": job.sweeps, "batched": True, "event": None, "sweeps_queued": 0}
+        self.members.append(h)
+        return h
+
+    def tick(self):
+        while self.inflight and self.inflight[0].query():
+            self.inflight.popleft()
+        if len(self.inflight) >= self.max_inflight or not self.members:
+            return
+        torch = self.torch
+        live = self.members
+        self.stream.wait_stream(self.adm)
+        self.P.psgld_batch_sweep([h["ctx"] for h in live], 1, self.stream.cuda_stream)
+        ev = torch.cuda.Event()
+        ev.record(self.stream)
+        for h in live:
+            h["left"] -= 1
+            h["sweeps_queued"] += 1
+            if h["left"] == 0:
+                h["event"] = ev
+        self.members = [h for h in live if h["left"] > 0]
+        self.inflight.append(ev)
+        self.ticks += 1
+        self.batch_sizes.append(len(live))
+
+    def done(self, h) -> bool:
+        if not h.get("batched"):
+            return super().done(h)
+        return h["left"] == 0 and h["event"].query()
+
+    def finish(self, job: Job, h) -> dict:
+        if not h.get("batched"):
+            return super().finish(job, h)
+        if h["left"] > 0:                    # released before its last sweep (close after an error)
+            self.members = [m for m in self.members if m is not h]
+            self.stream.synchronize()
+        else:
+            h["event"].synchronize()
         Wm, Wv, Hm, Hv, n = h["ctx"].posterior_mean()
         out = {"Wmean": Wm, "Hmean": Hm, "n_samples": n, "sweeps": h["sweeps_queued"]}
         h["ctx"].close()

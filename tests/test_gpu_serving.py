@@ -6,7 +6,9 @@ is fixed by its seed (Philox noise keyed by (seed, t), deterministic kernels,
 no floating-point atomics), so its posterior means must be identical bit for
 bit whether it runs alone, in a mix, under a memory budget that forces the
 jobs to wait for each other, or directly through the library without the
-server.  After every run the budget accounting returns to zero.
+server.  After every run the budget accounting returns to zero.  The same
+holds with continuous batching (BatchedGpuExecutor), where the jobs'
+part-steps share launches and jobs join and leave the batch between sweeps.
 """
 import numpy as np
 import pytest
@@ -29,8 +31,8 @@ def _jobs():
                         data_seed=3)]
 
 
-def _serve(jobs, budget):
-    ex = serving.GpuExecutor()
+def _serve(jobs, budget, executor=serving.GpuExecutor):
+    ex = executor()
     srv = serving.Server(ex, hbm_budget=budget)
     try:
         srv.run(jobs, idle_sleep=0)
@@ -89,3 +91,35 @@ def test_estimate_covers_what_a_context_holds():
         ch.close()
         # cudaMalloc rounds each buffer up (2 MB pages for large ones)
         assert est <= used + (8 << 20) and used <= est + 40 * (2 << 20), (I, J, K, B, dp, est, used)
+
+
+def test_batched_serving_result_is_the_same_alone_and_in_the_mix():
+    try:
+        B = serving.BatchedGpuExecutor
+        jobs = _jobs()
+        jobs[1].arrival = 0.05                   # joins the batch a few sweeps later
+        alone = _serve([_jobs()[0]], budget=8 << 30, executor=B)
+        mix = _serve(jobs, budget=8 << 30, executor=B)
+        ex = B()
+        e = [ex.estimate(j) for j in _jobs()]
+        queued = _serve(_jobs(), budget=max(e[0] + e[1], e[2]), executor=B)
+        for got in (mix[0], queued[0]):
+            assert np.array_equal(alone[0]["Wmean"], got["Wmean"])
+            assert np.array_equal(alone[0]["Hmean"], got["Hmean"])
+        for k in (1, 2):
+            assert np.array_equal(mix[k]["Wmean"], queued[k]["Wmean"])
+            assert mix[k]["n_samples"] == _jobs()[k].sweeps - _jobs()[k].burn_in
+        # job 0 swept alone through the library on the same kernel
+        P.psgld_set_allocator(None)
+        job = _jobs()[0]
+        V, W0, Ht0 = ex._data(job)
+        ch = P.PSGLD(job.I, job.J, job.K, job.B, job.p, job.phi, seed=job.seed, eps=job.eps,
+                     burn_in_sweeps=job.burn_in, dense_path=3, lambda_w=job.lam, lambda_h=job.lam)
+        ch.set_data_dense(V)
+        ch.set_factors(W0, Ht0)
+        ch.sweep(job.sweeps)
+        Wm, _, Hm, _, n = ch.posterior_mean()
+        ch.close()
+        assert np.array_equal(alone[0]["Wmean"], Wm) and np.array_equal(alone[0]["Hmean"], Hm)
+    finally:
+        P.psgld_set_allocator(None)

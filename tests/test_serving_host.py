@@ -107,3 +107,53 @@ def test_poisson_trace_rate_and_mix():
     assert {j.K for j in jobs} == {16, 64} and {j.p for j in jobs} == {1.0, 1.5}
     assert min(j.J for j in jobs) >= 500 and max(j.J for j in jobs) <= 20000
     assert all(a.arrival < b.arrival for a, b in zip(jobs, jobs[1:]))
+
+
+class FakeBatchExecutor(FakeExecutor):
+    """Continuous batching stand-in: every tick advances each unfinished
+    admitted job by one sweep; records which jobs each tick covered."""
+
+    def __init__(self):
+        super().__init__()
+        self.members = []
+        self.tick_log = []
+
+    def start(self, job):
+        self.started.append(job.job_id)
+        h = {"job": job, "left": job.sweeps}
+        self.members.append(h)
+        return h
+
+    def tick(self):
+        if not self.members:
+            return
+        self.tick_log.append(sorted(h["job"].job_id for h in self.members))
+        for h in self.members:
+            h["left"] -= 1
+        self.members = [h for h in self.members if h["left"] > 0]
+
+    def done(self, h):
+        return h["left"] <= 0
+
+
+def test_continuous_batching_joins_jobs_at_the_next_sweep():
+    ex = FakeBatchExecutor()
+    srv = serving.Server(ex, hbm_budget=100 * 100 * 100 * 100)
+    jobs = [_job(0, 100, 100, 0.0, sweeps=3), _job(1, 100, 100, 1.0, sweeps=2),
+            _job(2, 100, 100, 1.0, sweeps=4)]
+    pending = list(jobs)
+    t = 0.0
+    while len(srv.done) < len(jobs):
+        while pending and pending[0].arrival <= t:
+            srv.submit(pending.pop(0))
+        srv.poll(t)
+        t += 1.0
+        assert t < 20
+    # job 0 alone in the first sweep, then 1 and 2 join; each job is in
+    # exactly `sweeps` ticks
+    assert ex.tick_log[0] == [0]
+    assert ex.tick_log[1] == [0, 1, 2]
+    for j in jobs:
+        assert sum(j.job_id in tl for tl in ex.tick_log) == j.sweeps
+    assert srv.used == 0
+    assert max(len(tl) for tl in ex.tick_log) == 3

@@ -766,16 +766,18 @@ def run_batched(args, wl_name, wl):
 
 
 def batched_precision(wl, specs, dev, sweeps: int):
-    """BF16 tensor-core batched sweeps vs the FP32 gather path (each chain
-    alone) on the same chains, data, initial factors and Philox keys: entries/s
-    and the posterior-mean reconstruction RMSE (mean over the chains)."""
+    """BF16 tensor-core batched sweeps (GEMM1 in BF16, and in E4M3 with
+    per-tile scales) vs the FP32 gather path (each chain alone) on the same
+    chains, data, initial factors and Philox keys: entries/s and the
+    posterior-mean reconstruction RMSE (mean over the chains)."""
     import torch
 
     from paper_1506_01418_gb300 import psgld as P
     out = {"chains": len(specs), "sweeps": sweeps, "burn_in_sweeps": sweeps // 2}
     N = sum(wl["I"] * J for J, _, _, _ in specs)
     stream = torch.cuda.current_stream(dev)
-    for name, opts in (("bf16_tensor_core_batched", {}), ("fp32_gather", {"dense_path": 0})):
+    for name, opts in (("bf16_tensor_core_batched", {}), ("e4m3_gemm1_batched", {"dense_fp8": 1}),
+                       ("fp32_gather", {"dense_path": 0})):
         made = batched_make(wl, specs, dev, burn_in_sweeps=sweeps // 2, **opts)
         for ch, V, W0, Ht0 in made:
             ch.set_data_dense(V)
@@ -785,7 +787,7 @@ def batched_precision(wl, specs, dev, sweeps: int):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize(dev)
         a.record(stream)
-        if opts:
+        if name == "fp32_gather":
             for ch in chains:
                 ch.sweep(sweeps, stream.cuda_stream)
         else:
@@ -800,8 +802,10 @@ def batched_precision(wl, specs, dev, sweeps: int):
             ch.close()
         torch.cuda.empty_cache()
     r16 = out["bf16_tensor_core_batched"].pop("rmse")
+    r8 = out["e4m3_gemm1_batched"].pop("rmse")
     r32 = out["fp32_gather"].pop("rmse")
     out["rmse_rel_diff_max"] = max(abs(x - y) / y for x, y in zip(r16, r32))
+    out["e4m3_rmse_rel_diff_max"] = max(abs(x - y) / y for x, y in zip(r8, r32))
     out["speedup"] = out["bf16_tensor_core_batched"]["value"] / out["fp32_gather"]["value"]
     return out
 

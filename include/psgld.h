@@ -109,6 +109,14 @@ typedef struct {
                                * 2^64) and s is the part whose range of the running
                                * sum of part sizes (parts 0 .. B-1) holds r.  Sweeps
                                * then run without CUDA graphs. */
+    int32_t dense_fp8;        /* 1: the single-pass tensor-core kernel computes
+                               * mu = W_b H_b from E4M3 (FP8) copies of the
+                               * factors, each 128-row W tile and each 128-column
+                               * H tile scaled by its largest |x| / 448, FP32
+                               * accumulation; E and the gradient contractions
+                               * stay BF16.  Needs dense_path 1 or 3, K <= 128,
+                               * FP32 V (dense_path 1 then always takes the
+                               * single-pass kernel). */
 } psgld_options;
 
 /* Device memory.  By default the library allocates with cudaMalloc and frees

@@ -359,6 +359,7 @@ psgld_status psgld_set_options(psgld_ctx *c, const psgld_options *o)
     if (o->burn_in_sweeps < 0) return fail(c, PSGLD_ERR_ARG, "burn_in_sweeps must be >= 0");
     if (o->dense_path < 0 || o->dense_path > 3) return fail(c, PSGLD_ERR_ARG, "dense_path must be 0..3");
     if (o->part_mode != 0 && o->part_mode != 1) return fail(c, PSGLD_ERR_ARG, "part_mode must be 0 or 1");
+    if (o->dense_fp8 != 0 && o->dense_fp8 != 1) return fail(c, PSGLD_ERR_ARG, "dense_fp8 must be 0 or 1");
     c->opt = *o;
     destroy_graphs(c);
     destroy_events(c);

@@ -102,6 +102,22 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, int a_mn = 0, in
            ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
+// instruction descriptor of kind::f8f6f4: FP32 accumulate, E4M3 A and B
+// (format code 0), both K-major
+__host__ __device__ constexpr uint32_t idesc_e4m3(int M, int N)
+{
+    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_e4m3(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accumulate)
+{
+    asm volatile("{\n\t.reg .pred p;\n\t"
+                 "setp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}"
+                 :: "r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"(accumulate) : "memory");
+}
+
 __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
                                          uint32_t accumulate)
 {
@@ -204,21 +220,87 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)
 }
 
 // Row `src_row` (valid if < end) of an FP32 n x ldk matrix into row r of a
-// 128 x KP K-major BF16 tile, zero padded; half h of the K range.
+// 128 x KP K-major BF16 tile, zero padded; half h of the K range.  Returns
+// the largest |x| this thread staged.
 template <int KP>
-__device__ __forceinline__ void stage_rows(unsigned char *tile, const float *__restrict__ X, int64_t src_row,
-                                           int64_t end, int K, int ldk, int r, int h)
+__device__ __forceinline__ float stage_rows(unsigned char *tile, const float *__restrict__ X, int64_t src_row,
+                                            int64_t end, int K, int ldk, int r, int h)
 {
     const bool v = src_row < end;
     constexpr int kHalf = KP / 2;
+    float amax = 0.f;
 #pragma unroll
     for (int k = h * kHalf; k < (h + 1) * kHalf; k += 4) {
         float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
         if (v && k < K) x = __ldg(reinterpret_cast<const float4 *>(X + src_row * ldk + k));
         const float a = x.x, b = k + 1 < K ? x.y : 0.f, c = k + 2 < K ? x.z : 0.f,
                     d = k + 3 < K ? x.w : 0.f;
+        amax = fmaxf(amax, fmaxf(fmaxf(fabsf(a), fabsf(b)), fmaxf(fabsf(c), fabsf(d))));
         *reinterpret_cast<uint2 *>(tile + cm_off(r, k, KP)) = make_uint2(pack_bf16x2(a, b), pack_bf16x2(c, d));
     }
+    return amax;
+}
+
+// four floats to E4M3 (round to nearest even, saturating), x0 at the lowest byte
+__device__ __forceinline__ uint32_t pack_e4m3x4(float x0, float x1, float x2, float x3)
+{
+    uint16_t lo, hi;
+    asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(lo) : "f"(x1), "f"(x0));
+    asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(hi) : "f"(x3), "f"(x2));
+    return (uint32_t)lo | ((uint32_t)hi << 16);
+}
+
+// byte offset of element (r, k) in an R x KD K-major no-swizzle 8-bit tile:
+// core matrices of 8 rows x 16 bytes, adjacent along K 128 bytes apart
+__device__ __forceinline__ uint32_t cm8_off(int r, int k, int KD)
+{
+    return (uint32_t)((r >> 3) * (KD * 8) + (k >> 4) * 128 + (r & 7) * 16 + (k & 15));
+}
+
+// The same row as stage_rows, times inv_s, into a 128 x KD E4M3 tile (KD =
+// KP rounded up to 32, one MMA K step), zero padded; half h of the K range.
+template <int KD>
+__device__ __forceinline__ void stage_rows_e4m3(unsigned char *tile, const float *__restrict__ X,
+                                                int64_t src_row, int64_t end, int K, int ldk, int r, int h,
+                                                float inv_s)
+{
+    const bool v = src_row < end;
+    constexpr int kHalf = KD / 2;
+#pragma unroll
+    for (int k = h * kHalf; k < (h + 1) * kHalf; k += 16) {
+        uint32_t w[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int kk = k + 4 * q;
+            float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (v && kk < K) x = __ldg(reinterpret_cast<const float4 *>(X + src_row * ldk + kk));
+            w[q] = pack_e4m3x4(x.x * inv_s, kk + 1 < K ? x.y * inv_s : 0.f, kk + 2 < K ? x.z * inv_s : 0.f,
+                               kk + 3 < K ? x.w * inv_s : 0.f);
+        }
+        *reinterpret_cast<uint4 *>(tile + cm8_off(r, k, KD)) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+}
+
+// Largest |x| over the CTA (x >= 0 from every thread), through `slot`
+// (zero on entry, left holding the result; all threads must call).
+__device__ __forceinline__ float cta_amax(float x, uint32_t *slot)
+{
+    const uint32_t m = __reduce_max_sync(0xffffffffu, __float_as_uint(x));   // x >= 0: bits order as values
+    if ((threadIdx.x & 31) == 0) atomicMax(slot, m);
+    __syncthreads();
+    return __uint_as_float(*slot);
+}
+
+// E4M3 scale of a tile whose largest |x| is amax: the largest finite E4M3
+// value is 448.  Returns s (x ~ s q) and sets inv_s.
+__device__ __forceinline__ float e4m3_scale(float amax, float *inv_s)
+{
+    if (!(amax > 0.f)) {
+        *inv_s = 1.f;
+        return 1.f;
+    }
+    *inv_s = 448.f / amax;
+    return amax / 448.f;
 }
 
 // 32-column chunks of a TMEM row block (this thread's lane) to an FP32 row
@@ -240,20 +322,29 @@ __device__ __forceinline__ void drain_rows(uint32_t taddr, float *dst, bool vali
 }
 
 // One CTA of the single-pass kernel: CTA number `cta` of the launch for the
-// context described by P (P may live in parameter or global memory).
-template <int KP>
+// context described by P (P may live in parameter or global memory).  With
+// F8, GEMM1 (mu) reads E4M3 copies of the W and H tiles, each scaled by its
+// own largest |x| / 448 (one scale per 128-row W tile and per 128-column H
+// tile); mu is the FP32 product times both scales.  GEMM2 and GEMM3 stay
+// BF16.
+template <int KP, bool F8>
 __device__ __forceinline__ void dense_grad_cta(const DenseParams &P, int cta)
 {
     extern __shared__ __align__(1024) unsigned char sm[];
     constexpr uint32_t kOpBytes = kTile * KP * 2;           // a 128 x KP BF16 tile
     constexpr uint32_t kEBytes = kTile * kTile * 2;         // a 128 x 128 BF16 tile
+    constexpr int KD = KP < 32 ? 32 : KP;                   // E4M3 tile width (K step 32)
+    constexpr uint32_t kOp8Bytes = F8 ? kTile * KD : 0;
     // Each tile is stored once as (row, K-dim) core matrices and read K-major
     // by one GEMM and MN-major by another.
     unsigned char *A1 = sm;                     // W tile  (m, k): GEMM1 A; GEMM3 B (MN-major)
     unsigned char *B1 = A1 + kOpBytes;          // Ht tile (n, k): GEMM1 B; GEMM2 B (MN-major)
     unsigned char *A2 = B1 + kOpBytes;          // E tile  (m, n): GEMM2 A; GEMM3 A (MN-major)
-    uint64_t *bar = reinterpret_cast<uint64_t *>(A2 + kEBytes);
+    unsigned char *A8 = A2 + kEBytes;           // E4M3 W tile (F8: GEMM1 A)
+    unsigned char *B8 = A8 + kOp8Bytes;         // E4M3 Ht tile (F8: GEMM1 B)
+    uint64_t *bar = reinterpret_cast<uint64_t *>(B8 + kOp8Bytes);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 1);
+    uint32_t *amax_slot = tslot + 1;            // [0]: W tile, [1]: Ht tile (F8)
 
     const int tid = threadIdx.x, warp = tid >> 5;
     const int B = P.B;
@@ -280,6 +371,8 @@ __device__ __forceinline__ void dense_grad_cta(const DenseParams &P, int cta)
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(saddr(bar)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        amax_slot[0] = 0u;
+        amax_slot[1] = 0u;
     }
     fence_before();
     __syncthreads();
@@ -294,9 +387,15 @@ __device__ __forceinline__ void dense_grad_cta(const DenseParams &P, int cta)
     bool ok = true;
 
     // own rows of this M-tile: W (GEMM1 A) and W^T (GEMM3 B), BF16, zero padded
-    stage_rows<KP>(A1, P.W, m0 + r, re, K, ldk, r, h);
+    const float wmax = stage_rows<KP>(A1, P.W, m0 + r, re, K, ldk, r, h);
+    float sW = 1.f;
+    if constexpr (F8) {
+        float inv;
+        sW = e4m3_scale(cta_amax(wmax, amax_slot), &inv);
+        stage_rows_e4m3<KD>(A8, P.W, m0 + r, re, K, ldk, r, h, inv);
+    }
 
-    const uint64_t aW = sdesc(saddr(A1), 128, KP * 16);
+    const uint64_t aW = F8 ? sdesc(saddr(A8), 128, KD * 8) : sdesc(saddr(A1), 128, KP * 16);
     const int ntiles = (int)((ce - cs + kTile - 1) / kTile);
     const float *__restrict__ vbase = P.V;
     const int64_t ldv = P.ldv;
@@ -317,7 +416,13 @@ __device__ __forceinline__ void dense_grad_cta(const DenseParams &P, int cta)
             vv[j] = (rv && col < ce) ? __ldg(vrow + col) : 0.f;
         }
         // column tile: H^T rows (GEMM1 B) and H (GEMM2 B)
-        stage_rows<KP>(B1, P.Ht, n0 + r, ce, K, ldk, r, h);
+        const float hmax = stage_rows<KP>(B1, P.Ht, n0 + r, ce, K, ldk, r, h);
+        float smu = 1.f;                          // scale of the GEMM1 product
+        if constexpr (F8) {
+            float inv;
+            smu = sW * e4m3_scale(cta_amax(hmax, amax_slot + 1), &inv);
+            stage_rows_e4m3<KD>(B8, P.Ht, n0 + r, ce, K, ldk, r, h, inv);
+        }
         fence_async_smem();
         fence_before();
         __syncthreads();
@@ -325,11 +430,20 @@ __device__ __forceinline__ void dense_grad_cta(const DenseParams &P, int cta)
 
         // GEMM1: mu (TMEM columns 0..127) = W_tile . H_tile
         if (tid == 0) {
-            const uint64_t bH = sdesc(saddr(B1), 128, KP * 16);
+            if constexpr (F8) {
+                amax_slot[1] = 0u;                // every thread has read it (barrier above)
+                const uint64_t bH = sdesc(saddr(B8), 128, KD * 8);
 #pragma unroll
-            for (int ks = 0; ks < KP / 16; ++ks)
-                mma_bf16(tmem, aW + (uint64_t)(ks * 16), bH + (uint64_t)(ks * 16),
-                         idesc_bf16(kTile, kTile), ks > 0);
+                for (int ks = 0; ks < KD / 32; ++ks)
+                    mma_e4m3(tmem, aW + (uint64_t)(ks * 16), bH + (uint64_t)(ks * 16),
+                             idesc_e4m3(kTile, kTile), ks > 0);
+            } else {
+                const uint64_t bH = sdesc(saddr(B1), 128, KP * 16);
+#pragma unroll
+                for (int ks = 0; ks < KP / 16; ++ks)
+                    mma_bf16(tmem, aW + (uint64_t)(ks * 16), bH + (uint64_t)(ks * 16),
+                             idesc_bf16(kTile, kTile), ks > 0);
+            }
             mma_commit(bar);
         }
         ok = bar_wait(bar, phase);
@@ -354,7 +468,8 @@ __device__ __forceinline__ void dense_grad_cta(const DenseParams &P, int cta)
                     for (int d = 0; d < 2; ++d) {
                         const int j = j8 + 2 * q + d;
                         const bool in = rv && n0 + c + j < ce;
-                        e2[d] = in ? tweedie_fast(p_mode, pw, phi_inv, mu_min, vv[32 * cc + j], mu[j]) : 0.f;
+                        const float m = F8 ? mu[j] * smu : mu[j];
+                        e2[d] = in ? tweedie_fast(p_mode, pw, phi_inv, mu_min, vv[32 * cc + j], m) : 0.f;
                     }
                     pk[q] = pack_bf16x2(e2[0], e2[1]);
                 }
@@ -422,15 +537,15 @@ __device__ __forceinline__ void dense_grad_cta(const DenseParams &P, int cta)
 }
 
 
-template <int KP>
+template <int KP, bool F8>
 __global__ void __launch_bounds__(kDenseThreads, 1) dense_grad_kernel(const __grid_constant__ DenseParams P)
 {
-    dense_grad_cta<KP>(P, blockIdx.x);
+    dense_grad_cta<KP, F8>(P, blockIdx.x);
 }
 
 // Many contexts in one launch: context i owns CTAs [cta_start[i],
 // cta_start[i + 1]) of the grid (cta_start[n] = grid size).
-template <int KP>
+template <int KP, bool F8>
 __global__ void __launch_bounds__(kDenseThreads, 1)
 dense_grad_batch_kernel(const DenseParams *__restrict__ Ps, const int *__restrict__ cta_start, int n)
 {
@@ -440,7 +555,7 @@ dense_grad_batch_kernel(const DenseParams *__restrict__ Ps, const int *__restric
         const int mid = (lo + hi + 1) >> 1;
         if (__ldg(cta_start + mid) <= b) lo = mid; else hi = mid - 1;
     }
-    dense_grad_cta<KP>(Ps[lo], b - __ldg(cta_start + lo));
+    dense_grad_cta<KP, F8>(Ps[lo], b - __ldg(cta_start + lo));
 }
 
 // ===========================================================================
@@ -960,13 +1075,26 @@ __global__ void __launch_bounds__(kThreads, 1) chain_kernel(const __grid_constan
 
 using DenseFn = void (*)(DenseParams);
 
-DenseFn pick_dense(int kp)
+DenseFn pick_dense(int kp, bool f8)
 {
     switch (kp) {
-    case 16: return dense_grad_kernel<16>;
-    case 32: return dense_grad_kernel<32>;
-    case 64: return dense_grad_kernel<64>;
-    case 128: return dense_grad_kernel<128>;
+    case 16: return f8 ? dense_grad_kernel<16, true> : dense_grad_kernel<16, false>;
+    case 32: return f8 ? dense_grad_kernel<32, true> : dense_grad_kernel<32, false>;
+    case 64: return f8 ? dense_grad_kernel<64, true> : dense_grad_kernel<64, false>;
+    case 128: return f8 ? dense_grad_kernel<128, true> : dense_grad_kernel<128, false>;
+    }
+    return nullptr;
+}
+
+using DenseBatchFn = void (*)(const DenseParams *, const int *, int);
+
+DenseBatchFn pick_dense_batch(int kp, bool f8)
+{
+    switch (kp) {
+    case 16: return f8 ? dense_grad_batch_kernel<16, true> : dense_grad_batch_kernel<16, false>;
+    case 32: return f8 ? dense_grad_batch_kernel<32, true> : dense_grad_batch_kernel<32, false>;
+    case 64: return f8 ? dense_grad_batch_kernel<64, true> : dense_grad_batch_kernel<64, false>;
+    case 128: return f8 ? dense_grad_batch_kernel<128, true> : dense_grad_batch_kernel<128, false>;
     }
     return nullptr;
 }
@@ -982,9 +1110,12 @@ int dense_kp(int K)
 // library's TMEM-holding CTAs (this kernel's 256 columns, the two-sided
 // kernel's 512) is resident per SM: a tcgen05.alloc that cannot be met
 // blocks, and a CTA holding TMEM beside it must never wait on that.
-size_t dense_smem(int kp)
+size_t dense_smem(int kp, bool f8)
 {
-    return std::max<size_t>(2 * (size_t)kTile * kp * 2 + (size_t)kTile * kTile * 2 + 16, 116 * 1024);
+    const size_t e4m3 = f8 ? 2 * (size_t)kTile * std::max(kp, 32) : 0;
+    // tiles, then the mbarrier (8 bytes), the TMEM address and two scale slots (4 each)
+    return std::max<size_t>(2 * (size_t)kTile * kp * 2 + (size_t)kTile * kTile * 2 + e4m3 + 32,
+                            116 * 1024);
 }
 
 }  // namespace
@@ -1091,14 +1222,17 @@ psgld_status prepare_dense(psgld_ctx *c, cudaStream_t st)
     const bool vb = c->opt.dense_v_bf16 != 0;
     if (!dense_supported(c->K)) return fail(c, PSGLD_ERR_ARG, "dense tensor-core path supports K <= 256");
     c->mtiles = dense_mtiles(c);
-    bool two = mode == 2 || (mode == 1 && (vb || c->K > 128 || c->mtiles > 1));
-    if (mode == 3 && (vb || c->K > 128))
-        return fail(c, PSGLD_ERR_ARG, "single-pass dense kernel: K <= 128 and FP32 V only");
+    const bool f8 = c->opt.dense_fp8 != 0;
+    bool two = mode == 2 || (mode == 1 && !f8 && (vb || c->K > 128 || c->mtiles > 1));
+    if ((mode == 3 || f8) && (vb || c->K > 128 || mode == 2))
+        return fail(c, PSGLD_ERR_ARG, "single-pass dense kernel (and its E4M3 GEMM1): K <= 128, FP32 V");
     if (!two) {
         c->dense_kind = 1;
         const int kp = dense_kp(c->K);
-        PSGLD_CK(c, cudaFuncSetAttribute(pick_dense(kp), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)dense_smem(kp)));
+        const bool f8 = c->opt.dense_fp8 != 0;
+        PSGLD_CK(c, cudaFuncSetAttribute(pick_dense(kp, f8), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)dense_smem(kp, f8)));
+        c->dense_fp8 = f8 ? 1 : 0;
         return PSGLD_OK;
     }
     c->dense_kind = 2;
@@ -1226,16 +1360,17 @@ psgld_status launch_dense_grad(psgld_ctx *c, int part, cudaStream_t st)
 {
     if (c->dense_kind == 2) return launch_two_sided(c, part, st);
     const int kp = dense_kp(c->K);
-    DenseFn fn = pick_dense(kp);
+    const bool f8 = c->dense_fp8 != 0;
+    DenseFn fn = pick_dense(kp, f8);
     if (!fn) return fail(c, PSGLD_ERR_ARG, "single-pass dense kernel supports K <= 128");
     DenseParams P;
     fill_dense_params(c, part, P);
-    fn<<<c->B * P.mtiles, kDenseThreads, dense_smem(kp), st>>>(P);
+    fn<<<c->B * P.mtiles, kDenseThreads, dense_smem(kp, f8), st>>>(P);
     PSGLD_CK(c, cudaGetLastError());
     return PSGLD_OK;
 }
 
-int dense_batch_key(const psgld_ctx *c) { return c->dense_kind == 1 ? dense_kp(c->K) : 0; }
+int dense_batch_key(const psgld_ctx *c) { return c->dense_kind == 1 ? 2 * dense_kp(c->K) + c->dense_fp8 : 0; }
 
 size_t dense_param_bytes() { return sizeof(DenseParams); }
 
@@ -1247,20 +1382,17 @@ int fill_dense_param(const psgld_ctx *c, int part, void *dst)
     return c->B * P.mtiles;
 }
 
-psgld_status launch_dense_batch(psgld_ctx *c0, int kp, const void *params, const int *cta_start, int n,
+psgld_status launch_dense_batch(psgld_ctx *c0, int key, const void *params, const int *cta_start, int n,
                                 int total_ctas, cudaStream_t st)
 {
-    void (*fn)(const DenseParams *, const int *, int) = nullptr;
-    switch (kp) {
-    case 16: fn = dense_grad_batch_kernel<16>; break;
-    case 32: fn = dense_grad_batch_kernel<32>; break;
-    case 64: fn = dense_grad_batch_kernel<64>; break;
-    case 128: fn = dense_grad_batch_kernel<128>; break;
-    default: return fail(c0, PSGLD_ERR_ARG, "single-pass dense kernel supports K <= 128");
-    }
-    PSGLD_CK(c0, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dense_smem(kp)));
+    const int kp = key / 2;
+    const bool f8 = (key & 1) != 0;
+    DenseBatchFn fn = pick_dense_batch(kp, f8);
+    if (!fn) return fail(c0, PSGLD_ERR_ARG, "single-pass dense kernel supports K <= 128");
+    const size_t smem = dense_smem(kp, f8);
+    PSGLD_CK(c0, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     if (total_ctas > 0)
-        fn<<<total_ctas, kDenseThreads, dense_smem(kp), st>>>(static_cast<const DenseParams *>(params), cta_start, n);
+        fn<<<total_ctas, kDenseThreads, smem, st>>>(static_cast<const DenseParams *>(params), cta_start, n);
     PSGLD_CK(c0, cudaGetLastError());
     return PSGLD_OK;
 }

@@ -72,6 +72,7 @@ struct psgld_ctx {
     float *hpart = nullptr;          // mtiles x J x ldk partial G_H rows (mtiles > 1)
     int mtiles = 0;                  // 128-row tiles of the largest row piece
     int dense_kind = 0;              // 1: single-pass kernel, 2: two-sided kernel
+    int dense_fp8 = 0;               // single-pass kernel with the E4M3 GEMM1
     int KP = 0;                      // K rounded up to 64 (two-sided kernel)
     int v_bf16 = 0;                  // V tiles in BF16
     void *VA = nullptr, *VB = nullptr;          // V tiles, both orientations
@@ -198,11 +199,12 @@ psgld_status launch_dense_grad(psgld_ctx *c, int part, cudaStream_t st);
 // context's current ping-pong buffers) and return its share of the grid:
 // CTAs, update items or float4 accumulation units.  The *_start arrays are
 // exclusive prefix sums of those shares (n + 1 entries, device memory).
-// Dense: single-pass contexts of one K class (dense_batch_key equal, > 0).
+// Dense: single-pass contexts of one K class and GEMM1 precision
+// (dense_batch_key equal, > 0; the key is passed to launch_dense_batch).
 int dense_batch_key(const psgld_ctx *c);
 size_t dense_param_bytes();
 int fill_dense_param(const psgld_ctx *c, int part, void *dst);
-psgld_status launch_dense_batch(psgld_ctx *c0, int kp, const void *params, const int *cta_start, int n,
+psgld_status launch_dense_batch(psgld_ctx *c0, int key, const void *params, const int *cta_start, int n,
                                 int total_ctas, cudaStream_t st);
 // Update of part `part` at iteration *t_dev + t_add (t_dev: the context's
 // device counter); does not flip the context's buffers.

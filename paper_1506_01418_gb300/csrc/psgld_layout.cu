@@ -337,6 +337,7 @@ void free_layout(psgld_ctx *c)
     c->VA = c->VB = nullptr;
     c->Wsh = c->Hsh = nullptr;
     c->dense_kind = 0;
+    c->dense_fp8 = 0;
     c->dense = false;
     c->ldv = 0;
     c->mtiles = 0;

@@ -8,7 +8,7 @@ batch must end bit for bit where the same chain swept alone ends (alone
 through the captured-graph sweep): factors, posterior sums and iteration
 counter.  The batch mixes sizes (ragged blocks, blocks over one 128-row
 tile), ranks of every K class, Tweedie powers, both priors and both step
-size schedules.
+size schedules, and GEMM1 in BF16 and in E4M3.
 """
 import numpy as np
 import pytest
@@ -21,20 +21,22 @@ torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():
     pytest.skip("no CUDA device", allow_module_level=True)
 
-# (I, J, K, p, prior_kind, eps_mode)
+# (I, J, K, p, prior_kind, eps_mode, fp8)
 MIX = [
-    (300, 700, 8, 1.0, 0, 0),
-    (513, 900, 16, 2.0, 0, 0),        # blocks of 128 and 129 rows: two M-tiles
-    (257, 4000, 32, 1.0, 0, 0),
-    (640, 1000, 32, 1.5, 0, 1),       # second chain of the K = 32 class, eps_t = (a/t)^b
-    (1025, 300, 64, 0.0, 1, 0),       # Gaussian likelihood and priors
-    (90, 61, 13, 3.0, 0, 0),
-    (200, 500, 100, 1.0, 0, 1),
+    (300, 700, 8, 1.0, 0, 0, 0),
+    (513, 900, 16, 2.0, 0, 0, 0),     # blocks of 128 and 129 rows: two M-tiles
+    (257, 4000, 32, 1.0, 0, 0, 0),
+    (640, 1000, 32, 1.5, 0, 1, 0),    # second chain of the K = 32 class, eps_t = (a/t)^b
+    (1025, 300, 64, 0.0, 1, 0, 0),    # Gaussian likelihood and priors
+    (90, 61, 13, 3.0, 0, 0, 0),
+    (200, 500, 100, 1.0, 0, 1, 0),
+    (400, 800, 32, 1.0, 0, 0, 1),     # E4M3 GEMM1: a launch of its own
+    (130, 333, 12, 2.0, 0, 0, 1),
 ]
 B = 4
 
 
-def _chain(idx, I, J, K, p, kind, eps_mode, use_graphs, burn_in=1):
+def _chain(idx, I, J, K, p, kind, eps_mode, fp8, use_graphs, burn_in=1):
     dev = torch.device("cuda", 0)
     if p == 1.0:
         V, _, _ = datagen.dense_poisson(I, J, 3, idx)
@@ -46,7 +48,7 @@ def _chain(idx, I, J, K, p, kind, eps_mode, use_graphs, burn_in=1):
     W0, H0 = datagen.init_factors(I, J, K, seed=idx + 50, scale=0.4 if nonneg else 0.3,
                                   nonneg=nonneg)
     opts = dict(seed=1000 + idx, eps=1e-4, burn_in_sweeps=burn_in, dense_path=3,
-                use_graphs=use_graphs)
+                use_graphs=use_graphs, dense_fp8=fp8)
     if eps_mode:
         opts.update(eps_mode=P.PSGLD_EPS_POLY, eps_a=0.02, eps_b=0.55)
     ch = P.PSGLD(I, J, K, B, p, 1.0, prior_kind=kind, lambda_w=0.8, lambda_h=1.2, sigma_w=0.9,

@@ -18,7 +18,13 @@ FP32 precision.  What is checked:
   oracle chain (the configured dense Poisson NMF workload, 256 x 256, K = 8,
   B = 4);
 * graph replay == direct launches bit for bit; log-likelihood and RMSE over
-  the dense data match the oracle in FP64; refused inputs.
+  the dense data match the oracle in FP64; refused inputs;
+* the single-pass kernel with GEMM1 on E4M3 (FP8) copies of the factors,
+  one scale per 128-row / 128-column tile: the same drift test against the
+  first-order bound with E4M3 rounding (u = 2^-4, plus half the subnormal
+  spacing times the tile scale) for GEMM1's operands, where the bound can
+  be as large as the drift, so the error must also stay below a quarter of
+  the drift in RMS; the chain's posterior RMSE within 1 % of the oracle's.
 
 Every case runs on both kernels: the single-pass one (mu once per entry, G_H
 summed over a block's 128-row tiles by the update) and the two-sided one
@@ -40,6 +46,8 @@ if not torch.cuda.is_available():
 
 U_BF16 = 2.0 ** -8
 U_FP32 = 2.0 ** -24
+U_E4M3 = 2.0 ** -4          # 3 mantissa bits
+ETA_E4M3 = 2.0 ** -10       # half the subnormal spacing, in units of the tile scale
 
 DENSE = {
     # name: (I, J, K, B, p, phi, prior_kind, data, eps)
@@ -58,6 +66,7 @@ DENSE = {
 
 KERNELS = {
     "single_pass": dict(dense_path=3),
+    "single_pass_fp8": dict(dense_path=3, dense_fp8=1),
     "auto": dict(dense_path=1),
     "two_sided": dict(dense_path=2),
     "two_sided_bf16v": dict(dense_path=2, dense_v_bf16=1),
@@ -68,7 +77,7 @@ def _cases():
     out = []
     for name in sorted(DENSE):
         for kern in KERNELS:
-            if kern == "single_pass" and DENSE[name][2] > 128:
+            if kern.startswith("single_pass") and DENSE[name][2] > 128:
                 continue
             out.append((name, kern))
     return out
@@ -96,10 +105,27 @@ def _make(name, seed=7, kernel="auto", **opts):
     return pr, V
 
 
-def _drift_bound(V, W, H, t, B, p, phi, S, mu_min=1e-10, v_bf16=False):
+def _tile_scales(X, axis):
+    """Largest |x| / 448 of each 128-wide tile of X along `axis` (rows of a
+    W block: axis 0; columns of an H block: axis 1), broadcast back."""
+    n = X.shape[axis]
+    out = np.zeros(n)
+    for a in range(0, n, 128):
+        sl = X[a:a + 128] if axis == 0 else X[:, a:a + 128]
+        m = np.abs(sl).max() if sl.size else 0.0
+        out[a:a + 128] = m / 448.0 if m > 0 else 1.0
+    return out
+
+
+def _drift_bound(V, W, H, t, B, p, phi, S, mu_min=1e-10, v_bf16=False, fp8=False):
     """First-order BF16 bound on |drift_gpu - drift| for part t (see module
     docstring); W I x K, H K x J, FP64.  With v_bf16 the data are rounded to
-    BF16 too: e moves by at most |de/dv| u |v| = max(mu, mu_min)^-p u |v| / phi."""
+    BF16 too: e moves by at most |de/dv| u |v| = max(mu, mu_min)^-p u |v| / phi.
+    With fp8, GEMM1's operands are E4M3 with one scale s per 128-row W tile
+    and per 128-column H tile: |q(x) - x| <= u8 |x| + eta s (u8 = 2^-4, eta
+    = 2^-10 from the subnormals), so mu moves by at most (2 u8 + u8^2) A +
+    (1 + u8)(eta s_H sum_k |w| + eta s_W sum_k |h|) + K eta^2 s_W s_H, plus
+    the FP32 rounding of the scales."""
     I, J = V.shape
     s = (t - 1) % B
     bW = np.zeros_like(W)
@@ -111,7 +137,15 @@ def _drift_bound(V, W, H, t, B, p, phi, S, mu_min=1e-10, v_bf16=False):
         w, h, v = W[r0:r1], H[:, c0:c1], V[r0:r1, c0:c1].astype(np.float64)
         mu = w @ h
         A = np.abs(w) @ np.abs(h)
-        dmu = 2 * U_BF16 * A * 1.01 + 4 * w.shape[1] * U_FP32 * A
+        if fp8:
+            eW = ETA_E4M3 * _tile_scales(w, 0)[:, None]
+            eH = ETA_E4M3 * _tile_scales(h, 1)[None, :]
+            Kw = w.shape[1]
+            dmu = ((2 * U_E4M3 + U_E4M3 ** 2) * A * 1.01
+                   + (1 + U_E4M3) * (eH * np.abs(w).sum(1)[:, None] + eW * np.abs(h).sum(0)[None, :])
+                   + Kw * eW * eH + (4 * Kw + 16) * U_FP32 * A * (1 + 2 * U_E4M3))
+        else:
+            dmu = 2 * U_BF16 * A * 1.01 + 4 * w.shape[1] * U_FP32 * A
         if p > 0:
             mc = np.maximum(mu, mu_min)
             lo = np.maximum(mu - dmu, mu_min)
@@ -148,12 +182,13 @@ def test_dense_part_step_drift_within_bf16_bound(name, kernel):
     pr, V = _make(name, kernel=kernel)
     I, J, K, B, p, phi, kind, data, eps = DENSE[name]
     v_bf16 = bool(KERNELS[kernel].get("dense_v_bf16", 0))
+    fp8 = bool(KERNELS[kernel].get("dense_fp8", 0))
     mirror = kind == 0
     for t in range(1, B + 2):
         W0, H0 = pr.orc.get_factors()
         D_W, D_H = pr.orc.drift(t)
         S = pr.orc.scale(t)
-        bW, bH = _drift_bound(V, W0, H0, t, B, p, phi, S, v_bf16=v_bf16)
+        bW, bH = _drift_bound(V, W0, H0, t, B, p, phi, S, v_bf16=v_bf16, fp8=fp8)
         pr.gpu.part_step(t)
         Wg, Hg = pr.gpu_factors()
         zW = oracle.noise_matrix(7, t, 0, I, K)
@@ -166,8 +201,16 @@ def test_dense_part_step_drift_within_bf16_bound(name, kernel):
             assert not bad.any(), (name, kernel, t, what, int(bad.sum()), float(err[bad].max()),
                                    float(lim[bad].min()))
             assert mask.mean() > 0.9
-            # and the drift itself is far larger than the bound: the check has teeth
-            assert np.sqrt(np.mean(D[mask] ** 2)) > 4 * np.sqrt(np.mean(bnd[mask] ** 2)), (name, what)
+            rms_D = np.sqrt(np.mean(D[mask] ** 2))
+            if fp8:
+                # the worst-case E4M3 bound can reach the size of the drift
+                # itself, so the error must also be well below the drift in
+                # the mean: a wrong scale, byte order or operand gives errors
+                # of the drift's own size
+                assert np.sqrt(np.mean(err[mask] ** 2)) < 0.25 * rms_D, (name, what)
+            else:
+                # the drift itself is far larger than the bound: the check has teeth
+                assert rms_D > 4 * np.sqrt(np.mean(bnd[mask] ** 2)), (name, what)
         if mirror:
             assert Wg.min() >= 0 and Hg.min() >= 0
         pr.sync_oracle_to_gpu()
@@ -188,7 +231,7 @@ def test_dense_graph_replay_equals_direct_launches(kernel):
         assert np.array_equal(x, y)
 
 
-@pytest.mark.parametrize("kernel", ["single_pass", "two_sided_bf16v"])
+@pytest.mark.parametrize("kernel", ["single_pass", "two_sided_bf16v", "single_pass_fp8"])
 def test_dense_is_deterministic(kernel):
     a, _ = _make("poisson_uneven_mtiles_K32", kernel=kernel)
     b, _ = _make("poisson_uneven_mtiles_K32", kernel=kernel)
@@ -209,7 +252,7 @@ def test_dense_log_lik_and_rmse_match_oracle(name):
     assert pr.gpu.rmse() == pytest.approx(pr.orc.rmse(False), rel=1e-9)
 
 
-@pytest.mark.parametrize("kernel", ["auto", "two_sided_bf16v"])
+@pytest.mark.parametrize("kernel", ["auto", "two_sided_bf16v", "single_pass_fp8"])
 def test_dense_chain_posterior_rmse_within_one_percent_of_oracle(kernel):
     """The configured dense Poisson NMF workload (Sec. 4.1 shape): 256 x 256,
     K = 8, B = 4, W*, H* ~ Gamma(1, 1), V ~ Poisson(W* H*), exponential priors
@@ -231,7 +274,8 @@ def test_dense_refusals():
     I, J = 40, 30
     V = np.ones((I, J), np.float32)
     for K, opts in ((257, dict(dense_path=1)), (129, dict(dense_path=3)),
-                    (8, dict(dense_path=3, dense_v_bf16=1))):
+                    (8, dict(dense_path=3, dense_v_bf16=1)), (8, dict(dense_path=2, dense_fp8=1)),
+                    (200, dict(dense_path=1, dense_fp8=1))):
         c = P.PSGLD(I, J, K, 2, 1.0, 1.0, **opts)
         with pytest.raises(P.PsgldError) as ex:
             c.set_data_dense(torch.from_numpy(V).cuda())

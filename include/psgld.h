@@ -117,6 +117,12 @@ typedef struct {
                                * stay BF16.  Needs dense_path 1 or 3, K <= 128,
                                * FP32 V (dense_path 1 then always takes the
                                * single-pass kernel). */
+    int32_t gather_bf16;      /* 1: on the sparse path the gradient kernel gathers
+                               * BF16 copies of the other factor's rows (half the
+                               * bytes; the own row, the products and all sums stay
+                               * FP32); the copies are rebuilt by psgld_set_factors
+                               * and rewritten by every update.  Set it before
+                               * psgld_set_factors. */
 } psgld_options;
 
 /* Device memory.  By default the library allocates with cudaMalloc and frees

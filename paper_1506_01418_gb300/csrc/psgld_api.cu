@@ -214,6 +214,10 @@ bool ready(psgld_ctx *c, psgld_status *s)
 {
     if (!c->has_data) { *s = fail(c, PSGLD_ERR_STATE, "no data set"); return false; }
     if (!c->has_factors) { *s = fail(c, PSGLD_ERR_STATE, "no factors set"); return false; }
+    if (c->opt.gather_bf16 && !c->dense && !(c->W16 && c->H16)) {
+        *s = fail(c, PSGLD_ERR_STATE, "gather_bf16 was enabled after the factors were set: set them again");
+        return false;
+    }
     return true;
 }
 
@@ -360,6 +364,7 @@ psgld_status psgld_set_options(psgld_ctx *c, const psgld_options *o)
     if (o->dense_path < 0 || o->dense_path > 3) return fail(c, PSGLD_ERR_ARG, "dense_path must be 0..3");
     if (o->part_mode != 0 && o->part_mode != 1) return fail(c, PSGLD_ERR_ARG, "part_mode must be 0 or 1");
     if (o->dense_fp8 != 0 && o->dense_fp8 != 1) return fail(c, PSGLD_ERR_ARG, "dense_fp8 must be 0 or 1");
+    if (o->gather_bf16 != 0 && o->gather_bf16 != 1) return fail(c, PSGLD_ERR_ARG, "gather_bf16 must be 0 or 1");
     c->opt = *o;
     destroy_graphs(c);
     destroy_events(c);
@@ -546,7 +551,9 @@ psgld_status psgld_set_factors(psgld_ctx *c, const float *W, const float *Ht, vo
         return fail(c, PSGLD_ERR_ARG, "factor entry not finite, or negative in a non-negative model");
     }
     c->has_factors = true;
-    return build_dense_shadows(c, st);
+    psgld_status s = build_dense_shadows(c, st);
+    if (s == PSGLD_OK) s = build_gather_shadows(c, st);
+    return s;
 }
 
 psgld_status psgld_get_factors(psgld_ctx *c, float *W, float *Ht, void *stream)
@@ -957,6 +964,8 @@ void psgld_destroy(psgld_ctx *c)
         cudaEventDestroy(c->bdone);
     }
     dev_free(c, c->bscratch);
+    dev_free(c, c->W16);
+    dev_free(c, c->H16);
     for (int b = 0; b < 2; ++b) { dev_free(c, c->W[b]); dev_free(c, c->Ht[b]); }
     dev_free(c, c->G);
     dev_free(c, c->sW.s); dev_free(c, c->sW.s2); dev_free(c, c->sH.s); dev_free(c, c->sH.s2);

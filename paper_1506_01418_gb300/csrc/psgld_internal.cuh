@@ -20,6 +20,8 @@
 //   two-sided kernel: VA / VB, V in 128 x 64 tiles per block, owned rows =
 //           rows of V (VA) or columns of V (VB); Wsh / Hsh, BF16 shadows of W
 //           and H^T in 64-row swizzled MMA tiles per piece (dev::shadow_store4)
+//   sparse path with gather_bf16: W16 / H16, BF16 copies of W and H^T, rows
+//           of ldk rounded up to 8, rewritten by every update
 #pragma once
 
 #include <cuda_bf16.h>
@@ -77,6 +79,7 @@ struct psgld_ctx {
     int v_bf16 = 0;                  // V tiles in BF16
     void *VA = nullptr, *VB = nullptr;          // V tiles, both orientations
     uint16_t *Wsh = nullptr, *Hsh = nullptr;    // BF16 shadows of W, H^T
+    uint16_t *W16 = nullptr, *H16 = nullptr;    // sparse path, gather_bf16: BF16 copies of W, H^T
     int mt_max = 0, nt_max = 0;      // 128-row tiles per row piece / column piece
     int ni_max = 0, nj_max = 0;      // 64-row tiles per row piece / column piece
 
@@ -166,6 +169,12 @@ int part_of_iteration(const psgld_ctx *c, int64_t t);
 // Enqueue iteration t.  When t_dev is non-null the kernels read t from
 // *t_dev + t_add instead (used inside captured graphs); `t` then only
 // selects the part and must satisfy (t-1) % B == part.
+// Sparse path with gather_bf16: the gradient kernel gathers BF16 copies of
+// the factors (rows of ldk rounded up to 8), kept by the update kernel and
+// built from the current factors by build_gather_shadows (allocating them).
+bool gather_bf16(const psgld_ctx *c);
+psgld_status build_gather_shadows(psgld_ctx *c, cudaStream_t st);
+
 psgld_status launch_part_step(psgld_ctx *c, int64_t t, const int64_t *t_dev,
                               int64_t t_add, cudaStream_t st);
 

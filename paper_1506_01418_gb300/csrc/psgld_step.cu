@@ -66,11 +66,13 @@ struct GradSide {
     int64_t base;          // first entry of the part
     int64_t n;             // entries of the part
     int64_t units;         // ceil(n / E)
+    const uint16_t *Y16;   // BF16 copy of the other factor (rows of ld16), gathered instead of Y_cur
 };
 
 struct GradParams {
     GradSide side[2];
     int ldk, lds, ngroups;    // row length, shared-memory row stride (floats), float4 groups
+    int ld16, lds16;          // BF16 gather: row length and shared-memory row stride (elements)
     float phi_inv, p, mu_min;
     int p_mode;               // 0: p = 0, 1: p = 1, 2: p = 2, 3: other
     int *err;                 // set to 16 when a bulk copy wait runs out
@@ -89,6 +91,7 @@ struct UpdSide {
     uint16_t *sh;             // two-sided dense kernel: BF16 shadow of X_next (else null)
     int64_t n_rows;           // I or J
     int sh_tiles;             // 64-row shadow tiles per piece
+    uint16_t *g16;            // BF16 copy of X_next for the gradient kernel's gathers (else null)
     float prior_a, prior_b;   // d log p(x)/dx = prior_a + prior_b * x
     uint32_t mat;             // 0 = W, 1 = H (noise stream)
 };
@@ -104,6 +107,7 @@ struct UpdParams {
     double eps_a, eps_b;
     int mirror;
     int B, sh_kp;             // pieces; shadow tile width (two-sided dense kernel)
+    int ld16;                 // row length of the BF16 gather copies
     uint32_t rk0[10], rk1[10];   // Philox round keys (seed + r * Weyl constants)
 };
 
@@ -226,10 +230,26 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
                  :: "r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar)) : "memory");
 }
 
+// Four gathered entries (q-th float4 group) of row `row` of the warp's
+// gathered rows: FP32 rows of lds floats, or (BF) BF16 rows of lds16.
+template <bool BF>
+__device__ __forceinline__ float4 ys4(const float *ys, int row, int q, int lds, int lds16)
+{
+    if constexpr (BF) {
+        const uint2 v = *reinterpret_cast<const uint2 *>(reinterpret_cast<const uint16_t *>(ys) +
+                                                         (size_t)row * lds16 + 4 * q);
+        return make_float4(__uint_as_float(v.x << 16), __uint_as_float(v.x & 0xFFFF0000u),
+                           __uint_as_float(v.y << 16), __uint_as_float(v.y & 0xFFFF0000u));
+    } else {
+        return *reinterpret_cast<const float4 *>(ys + (size_t)row * lds + 4 * q);
+    }
+}
+
 // One unit (E consecutive entries of side SID's part order) on one warp; SID
 // is a template parameter so that the side's fields are fixed parameter
-// offsets.
-template <int SID, int S, int NG, int E>
+// offsets.  BF: the gathered rows are the BF16 copies (half the bytes;
+// products and sums stay FP32).
+template <int SID, int S, int NG, int E, bool BF>
 __device__ __forceinline__ void grad_unit(const GradParams &P, int64_t u, float *ys, float *es, int *ow,
                                           uint64_t *bar)
 {
@@ -255,7 +275,8 @@ __device__ __forceinline__ void grad_unit(const GradParams &P, int64_t u, float 
     if (lane32 == 1 && u * E + E < Sd.n) next_own = __ldg(Sd.own + e0 + E);
     prev_own = __shfl_sync(0xffffffffu, prev_own, 0);
     next_own = __shfl_sync(0xffffffffu, next_own, 1);
-    const uint32_t row_bytes = (uint32_t)ldk * 4u;
+    const int lds16 = P.lds16;
+    const uint32_t row_bytes = BF ? (uint32_t)P.ld16 * 2u : (uint32_t)ldk * 4u;
 
     // ---- 2. bulk gathers into shared memory
     if (lane32 == 0) {
@@ -263,7 +284,13 @@ __device__ __forceinline__ void grad_unit(const GradParams &P, int64_t u, float 
         mbar_expect_tx(bar, (uint32_t)n * row_bytes);
     }
     __syncwarp();
-    if (valid) bulk_g2s(ys + (size_t)lane32 * lds, Sd.Y_cur + (int64_t)jj * ldk, row_bytes, bar);
+    if (valid) {
+        if constexpr (BF)
+            bulk_g2s(reinterpret_cast<uint16_t *>(ys) + (size_t)lane32 * lds16, Sd.Y16 + (int64_t)jj * P.ld16,
+                     row_bytes, bar);
+        else
+            bulk_g2s(ys + (size_t)lane32 * lds, Sd.Y_cur + (int64_t)jj * ldk, row_bytes, bar);
+    }
     bool done = false;
     const long long t_start = clock64();
     for (uint32_t it = 0; it < kWaitLimit && !done && clock64() - t_start < kWaitCycles; ++it)
@@ -282,11 +309,10 @@ __device__ __forceinline__ void grad_unit(const GradParams &P, int64_t u, float 
     float e = 0.f;
     if (valid) {
         const float *x = Sd.X_cur + (int64_t)own * ldk;
-        const float *y = ys + (size_t)lane32 * lds;
         float d = 0.f;
 #pragma unroll
         for (int q = 0; q < NGP; ++q)
-            if (q < ng) d = dot4(ldg4(x + 4 * q), *reinterpret_cast<const float4 *>(y + 4 * q), d);
+            if (q < ng) d = dot4(ldg4(x + 4 * q), ys4<BF>(ys, lane32, q, lds, lds16), d);
         e = tweedie_e(P, vv, d);
     }
     const int own_prev_lane = __shfl_up_sync(0xffffffffu, own, 1);
@@ -310,7 +336,7 @@ __device__ __forceinline__ void grad_unit(const GradParams &P, int64_t u, float 
 #pragma unroll
             for (int g = 0; g < NG; ++g) {
                 const int q = lane + g * S;
-                if (q < ng) axpy4(acc[g], es_, *reinterpret_cast<const float4 *>(ys + (size_t)sl * lds + 4 * q));
+                if (q < ng) axpy4(acc[g], es_, ys4<BF>(ys, sl, q, lds, lds16));
             }
         }
 #pragma unroll
@@ -346,7 +372,7 @@ __device__ __forceinline__ void grad_unit(const GradParams &P, int64_t u, float 
 #pragma unroll
                 for (int g = 0; g < NG; ++g) {
                     const int q = lane + g * S;
-                    if (q < ng) axpy4(acc[g], es_, *reinterpret_cast<const float4 *>(ys + (size_t)sl * lds + 4 * q));
+                    if (q < ng) axpy4(acc[g], es_, ys4<BF>(ys, sl, q, lds, lds16));
                 }
             }
             float *dst = (k == 0 && prev_own == row) ? Sd.partial + (2 * u) * (int64_t)ldk
@@ -361,7 +387,7 @@ __device__ __forceinline__ void grad_unit(const GradParams &P, int64_t u, float 
     }
 }
 
-template <int S, int NG, int E>
+template <int S, int NG, int E, bool BF>
 __global__ void __launch_bounds__(kGradThreads) grad_kernel(const __grid_constant__ GradParams P)
 {
     extern __shared__ float4 smem4[];
@@ -376,10 +402,10 @@ __global__ void __launch_bounds__(kGradThreads) grad_kernel(const __grid_constan
 
     int64_t u = (int64_t)blockIdx.x * kWarpsPerCta + warp;
     if (u < P.side[0].units) {
-        grad_unit<0, S, NG, E>(P, u, ys, es, ow, bar);
+        grad_unit<0, S, NG, E, BF>(P, u, ys, es, ow, bar);
     } else {
         u -= P.side[0].units;
-        if (u < P.side[1].units) grad_unit<1, S, NG, E>(P, u, ys, es, ow, bar);   // warp-uniform
+        if (u < P.side[1].units) grad_unit<1, S, NG, E, BF>(P, u, ys, es, ow, bar);   // warp-uniform
     }
 }
 
@@ -461,6 +487,11 @@ __device__ __forceinline__ void update_item(const UpdParams &P, int64_t item, fl
     o.w = k0 + 3 < P.K ? update1(P, Sd, x.w, g.w, z.w, eps, sd) : 0.f;
     *reinterpret_cast<float4 *>(Sd.X_next + off) = o;
     if (Sd.sh) dev::shadow_store4(Sd.sh, row, k0, o, Sd.n_rows, P.B, Sd.sh_tiles, P.sh_kp);
+    if (Sd.g16) {
+        const __nv_bfloat162 a = __floats2bfloat162_rn(o.x, o.y), b = __floats2bfloat162_rn(o.z, o.w);
+        *reinterpret_cast<uint2 *>(Sd.g16 + row * P.ld16 + k0) =
+            make_uint2(*reinterpret_cast<const uint32_t *>(&a), *reinterpret_cast<const uint32_t *>(&b));
+    }
 }
 
 __global__ void __launch_bounds__(kThreads, 5) update_kernel(const __grid_constant__ UpdParams P)
@@ -508,30 +539,47 @@ Shape shape_for(int ngroups)
     return sh;
 }
 
-GradFn pick_grad(const Shape &sh)
+template <bool BF>
+GradFn pick_grad_t(const Shape &sh)
 {
     if (sh.NG == 1) {
         switch (sh.S) {
-        case 1: return grad_kernel<1, 1, 32>;
-        case 2: return grad_kernel<2, 1, 32>;
-        case 4: return grad_kernel<4, 1, 32>;
+        case 1: return grad_kernel<1, 1, 32, BF>;
+        case 2: return grad_kernel<2, 1, 32, BF>;
+        case 4: return grad_kernel<4, 1, 32, BF>;
         }
     }
     if (sh.NG == 2) {
         switch (sh.S) {
-        case 4: return grad_kernel<4, 2, 32>;
-        case 8: return grad_kernel<8, 2, 32>;
-        case 16: return grad_kernel<16, 2, 32>;
-        case 32: return grad_kernel<32, 2, 16>;
+        case 4: return grad_kernel<4, 2, 32, BF>;
+        case 8: return grad_kernel<8, 2, 32, BF>;
+        case 16: return grad_kernel<16, 2, 32, BF>;
+        case 32: return grad_kernel<32, 2, 16, BF>;
         }
     }
     if (sh.S == 32) {
         switch (sh.NG) {
-        case 3: return grad_kernel<32, 3, 8>;
-        case 4: return grad_kernel<32, 4, 8>;
+        case 3: return grad_kernel<32, 3, 8, BF>;
+        case 4: return grad_kernel<32, 4, 8, BF>;
         }
     }
     return nullptr;
+}
+
+// BF: the variant that gathers the BF16 copies of the factors
+GradFn pick_grad(const Shape &sh, bool bf)
+{
+    return bf ? pick_grad_t<true>(sh) : pick_grad_t<false>(sh);
+}
+
+// BF16 gather copies: rows of ld16 = ldk rounded up to 8 (16-byte rows for
+// the bulk copies); shared-memory stride lds16 >= ld16 with lds16 / 8 odd,
+// so that the lanes' 8-byte reads of distinct rows spread over the banks.
+int ld16_for(int ldk) { return 8 * ((ldk + 7) / 8); }
+int lds16_for(int ldk)
+{
+    const int m = ld16_for(ldk) / 8;
+    return 8 * ((m & 1) ? m : m + 1);
 }
 
 size_t grad_smem(const Shape &sh)
@@ -543,15 +591,57 @@ size_t grad_smem(const Shape &sh)
 
 }  // namespace
 
+namespace {
+
+// BF16 copy of an n x ldk FP32 factor into rows of ld16 (padding zero)
+__global__ void gather_copy_kernel(const float *__restrict__ X, int64_t n, int ldk, int ld16,
+                                   uint16_t *__restrict__ Y)
+{
+    const int64_t total = n * ld16;
+    for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < total;
+         a += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = a / ld16;
+        const int k = (int)(a - r * ld16);
+        const float x = k < ldk ? X[r * ldk + k] : 0.f;
+        const __nv_bfloat16 b = __float2bfloat16_rn(x);
+        Y[a] = *reinterpret_cast<const uint16_t *>(&b);
+    }
+}
+
+}  // namespace
+
+bool gather_bf16(const psgld_ctx *c) { return c->opt.gather_bf16 && !c->dense && c->W16 && c->H16; }
+
+psgld_status build_gather_shadows(psgld_ctx *c, cudaStream_t st)
+{
+    if (!c->opt.gather_bf16 || c->dense || !c->has_factors) return PSGLD_OK;
+    const int ld16 = ld16_for(c->ldk);
+    for (int side = 0; side < 2; ++side) {
+        const int64_t n = side == 0 ? c->I : c->J;
+        uint16_t *&Y = side == 0 ? c->W16 : c->H16;
+        if (!Y) {
+            Y = static_cast<uint16_t *>(dev_alloc(c, sizeof(uint16_t) * (size_t)std::max<int64_t>(n * ld16, 1), st));
+            if (!Y) return fail(c, PSGLD_ERR_OOM, "device allocation failed");
+        }
+        const float *X = side == 0 ? c->W[c->wcur] : c->Ht[c->hcur];
+        const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n * ld16 + 255) / 256, 152 * 16));
+        gather_copy_kernel<<<grid, 256, 0, st>>>(X, n, c->ldk, ld16, Y);
+        PSGLD_CK(c, cudaGetLastError());
+    }
+    return PSGLD_OK;
+}
+
 int unit_entries(int ngroups) { return shape_for(ngroups).E; }
 
 psgld_status prepare_kernels(psgld_ctx *c)
 {
     const Shape sh = shape_for(c->ngroups);
-    GradFn gfn = pick_grad(sh);
-    if (!gfn) return fail(c, PSGLD_ERR_ARG, "unsupported K");
-    PSGLD_CK(c, cudaFuncSetAttribute(gfn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)grad_smem(sh)));
+    for (int bf = 0; bf < 2; ++bf) {
+        GradFn gfn = pick_grad(sh, bf != 0);
+        if (!gfn) return fail(c, PSGLD_ERR_ARG, "unsupported K");
+        PSGLD_CK(c, cudaFuncSetAttribute(gfn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)grad_smem(sh)));
+    }
     return PSGLD_OK;
 }
 
@@ -587,6 +677,7 @@ static void fill_params(psgld_ctx *c, int part, int64_t t, const int64_t *t_dev,
         Gs.base = base;
         Gs.n = n;
         Gs.units = upd[s] ? (n + sh.E - 1) / sh.E : 0;
+        Gs.Y16 = gather_bf16(c) ? (s == 0 ? c->H16 : c->W16) : nullptr;
 
         Us.X_cur = X_cur;
         Us.X_next = X_next;
@@ -604,6 +695,7 @@ static void fill_params(psgld_ctx *c, int part, int64_t t, const int64_t *t_dev,
             Us.sh_tiles = 2 * (s == 0 ? c->mt_max : c->nt_max);
         }
         Us.partial = L.partial;
+        Us.g16 = gather_bf16(c) ? (s == 0 ? c->W16 : c->H16) : nullptr;
         Us.base = base;
         Us.items = upd[s] ? n_rows * c->ngroups : 0;
         if (c->prior.kind == PSGLD_PRIOR_EXPONENTIAL) {
@@ -618,6 +710,8 @@ static void fill_params(psgld_ctx *c, int part, int64_t t, const int64_t *t_dev,
     }
     GP.ldk = c->ldk;
     GP.lds = sh.lds;
+    GP.ld16 = ld16_for(c->ldk);
+    GP.lds16 = lds16_for(c->ldk);
     GP.ngroups = c->ngroups;
     GP.phi_inv = (float)(1.0 / c->phi);
     GP.p = (float)c->p;
@@ -647,6 +741,7 @@ static void fill_params(psgld_ctx *c, int part, int64_t t, const int64_t *t_dev,
     UP.mirror = c->prior.kind == PSGLD_PRIOR_EXPONENTIAL;
     UP.B = B;
     UP.sh_kp = c->KP;
+    UP.ld16 = ld16_for(c->ldk);
     uint32_t k0 = (uint32_t)c->opt.seed, k1 = (uint32_t)(c->opt.seed >> 32);
     for (int r = 0; r < 10; ++r) {   // Weyl key schedule of Philox4x32
         UP.rk0[r] = k0;
@@ -662,7 +757,7 @@ psgld_status launch_part_step(psgld_ctx *c, int64_t t, const int64_t *t_dev, int
     const int B = c->B;
     const int part = part_of_iteration(c, t);
     const Shape sh = shape_for(c->ngroups);
-    GradFn gfn = pick_grad(sh);
+    GradFn gfn = pick_grad(sh, gather_bf16(c));
     if (!gfn) return fail(c, PSGLD_ERR_ARG, "unsupported K");
     const bool dense = c->dense;
     const bool upd[2] = {!c->opt.freeze_W, !c->opt.freeze_H};

@@ -12,6 +12,24 @@ from paper_1506_01418_gb300 import psgld as P
 # or the noise moved through zero are judged on the matrix's own scale.
 STEP_RTOL = 1e-5
 
+U_BF16 = 2.0 ** -8
+U_FP32 = 2.0 ** -24
+
+
+def recovered_drift(x_new, x0, z, D_or, eps, mirror):
+    """The drift a GPU step applied: x_new = m(x0 + eps drift + sqrt(2 eps) z),
+    m = |.| or identity.  Returns (drift, mask of elements judged, recovery
+    error): elements the oracle's step leaves near zero are not judged when
+    the mirror applies (their sign is undetermined)."""
+    sd = np.sqrt(2 * eps)
+    y_or = x0 + eps * D_or + sd * z
+    mask = np.abs(y_or) > 0.02 if mirror else np.ones_like(y_or, dtype=bool)
+    sgn = np.sign(y_or) if mirror else 1.0
+    D = (sgn * x_new - x0 - sd * z) / eps
+    rec = (6 * U_FP32 * (np.abs(x0) + np.abs(y_or) + eps * np.abs(D_or))
+           + sd * 3e-6 * (1 + np.abs(z))) / eps + 4 * U_FP32 * np.abs(D_or)
+    return D, mask, rec
+
 
 def rel_err(a, b):
     a = np.asarray(a, dtype=np.float64)

@@ -35,7 +35,7 @@ import numpy as np
 import pytest
 
 import oracle
-from gpu_helpers import Pair
+from gpu_helpers import U_BF16, U_FP32, Pair, recovered_drift
 from paper_1506_01418_gb300 import datagen
 from paper_1506_01418_gb300 import psgld as P
 
@@ -44,8 +44,6 @@ torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():
     pytest.skip("no CUDA device", allow_module_level=True)
 
-U_BF16 = 2.0 ** -8
-U_FP32 = 2.0 ** -24
 U_E4M3 = 2.0 ** -4          # 3 mantissa bits
 ETA_E4M3 = 2.0 ** -10       # half the subnormal spacing, in units of the tile scale
 
@@ -164,19 +162,6 @@ def _drift_bound(V, W, H, t, B, p, phi, S, mu_min=1e-10, v_bf16=False, fp8=False
     return S * bW, S * bH
 
 
-def _recovered_drift(x_new, x0, z, D_or, eps, mirror):
-    """drift the GPU applied: x_new = m(x0 + eps drift + sqrt(2 eps) z), m = |.|
-    or identity.  Returns (drift, mask of elements judged, recovery error)."""
-    sd = np.sqrt(2 * eps)
-    y_or = x0 + eps * D_or + sd * z
-    mask = np.abs(y_or) > 0.02 if mirror else np.ones_like(y_or, dtype=bool)
-    sgn = np.sign(y_or) if mirror else 1.0
-    D = (sgn * x_new - x0 - sd * z) / eps
-    rec = (6 * U_FP32 * (np.abs(x0) + np.abs(y_or) + eps * np.abs(D_or))
-           + sd * 3e-6 * (1 + np.abs(z))) / eps + 4 * U_FP32 * np.abs(D_or)
-    return D, mask, rec
-
-
 @pytest.mark.parametrize("name,kernel", _cases())
 def test_dense_part_step_drift_within_bf16_bound(name, kernel):
     pr, V = _make(name, kernel=kernel)
@@ -194,7 +179,7 @@ def test_dense_part_step_drift_within_bf16_bound(name, kernel):
         zW = oracle.noise_matrix(7, t, 0, I, K)
         zH = oracle.noise_matrix(7, t, 1, J, K).T
         for xg, x0, z, D, bnd, what in ((Wg, W0, zW, D_W, bW, "W"), (Hg, H0, zH, D_H, bH, "H")):
-            Dg, mask, rec = _recovered_drift(xg.astype(np.float64), x0, z, D, eps, mirror)
+            Dg, mask, rec = recovered_drift(xg.astype(np.float64), x0, z, D, eps, mirror)
             err = np.abs(Dg - D)
             lim = bnd + rec
             bad = mask & (err > lim)

@@ -69,10 +69,12 @@ WORKLOADS = {
 }
 # the serving configuration: Poisson arrivals of dense non-negative jobs
 # (I in {257, 513, 1025}, J log-uniform on [500, 20000], p in {1, 1.5},
-# K in {16, 64}, B = 8, 20 sweeps each) beside the standing chain
+# K in {16, 64}, B = 8, 20 sweeps each) beside the standing chain, whose
+# persistent kernel is held to 120 of the 152 SMs (the jobs' kernels find
+# SMs free while it runs)
 WORKLOADS["serving_poisson200_mixed_jobs_with_standing_chain"] = dict(
     serving=True, rate=200.0, duration=3.0, sweeps=20, burn_in=10, B=8, eps=1e-4,
-    budget_bytes=64 << 30, standing="dense_poisson_32768x32768_K256_B16_bf16",
+    budget_bytes=64 << 30, standing="dense_poisson_32768x32768_K256_B16_bf16", standing_sms=120,
     I=0, J=0, K=0, p=1.0)
 # many small dense chains sharing launches: 256 independent chains, each
 # I = 513 x J ~ Uniform[200, 5000], V = |W* H*| * Gamma(2, rate 2) noise with
@@ -926,7 +928,8 @@ def serve_trace(wl, executor, dev, uuid):
         sw = WORKLOADS[wl["standing"]]
         standing = serving.Job(job_id=-1, I=sw["I"], J=sw["J"], K=sw["K"], B=sw["B"], p=sw["p"],
                                sweeps=None, burn_in=0, seed=7, eps=sw["eps"], init_scale=sw["init_scale"],
-                               dense_path=sw["dense_path"], dense_v_bf16=sw["dense_v_bf16"])
+                               dense_path=sw["dense_path"], dense_v_bf16=sw["dense_v_bf16"],
+                               max_sms=wl.get("standing_sms", 0))
         srv.submit(standing)
         srv.poll(0.0)
         torch.cuda.synchronize(dev)
@@ -986,11 +989,12 @@ def run_serving(args, wl_name, wl):
         "config": {"workload": wl_name, "arrival_rate_per_s": wl["rate"], "trace_s": wl["duration"],
                    "jobs": len(jobs), "sweeps_per_job": wl["sweeps"], "B": wl["B"],
                    "hbm_budget_bytes": wl["budget_bytes"], "standing_chain": wl.get("standing"),
+                   "standing_chain_sms": wl.get("standing_sms", 0) or "all",
                    "step": "one job of the trace (value counts every job's and the standing "
                            "chain's entries x sweeps over the trace's wall time)",
                    "path": "continuous batching: every admitted job's part-steps in the batch's "
                            "shared tensor-core launches (psgld_batch_sweep, one sweep per tick, "
-                           "at most three ticks queued); the standing chain on its own stream; "
+                           "at most eight ticks queued); the standing chain on its own stream; "
                            "PyTorch caching allocator"},
         "latency": lat,
         "job_entries_per_s": r["job_entries"] / wall,

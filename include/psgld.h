@@ -123,6 +123,11 @@ typedef struct {
                                * FP32); the copies are rebuilt by psgld_set_factors
                                * and rewritten by every update.  Set it before
                                * psgld_set_factors. */
+    int32_t max_sms;          /* > 0: the two-sided tensor-core kernel (persistent,
+                               * one CTA per SM) runs on at most this many SMs, so
+                               * that kernels of other streams find SMs free while
+                               * it runs (a long-running chain beside short jobs);
+                               * 0: every SM */
 } psgld_options;
 
 /* Device memory.  By default the library allocates with cudaMalloc and frees

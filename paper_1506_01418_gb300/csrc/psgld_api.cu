@@ -365,6 +365,7 @@ psgld_status psgld_set_options(psgld_ctx *c, const psgld_options *o)
     if (o->part_mode != 0 && o->part_mode != 1) return fail(c, PSGLD_ERR_ARG, "part_mode must be 0 or 1");
     if (o->dense_fp8 != 0 && o->dense_fp8 != 1) return fail(c, PSGLD_ERR_ARG, "dense_fp8 must be 0 or 1");
     if (o->gather_bf16 != 0 && o->gather_bf16 != 1) return fail(c, PSGLD_ERR_ARG, "gather_bf16 must be 0 or 1");
+    if (o->max_sms < 0) return fail(c, PSGLD_ERR_ARG, "max_sms must be >= 0");
     c->opt = *o;
     destroy_graphs(c);
     destroy_events(c);

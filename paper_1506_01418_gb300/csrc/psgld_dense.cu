@@ -1326,7 +1326,8 @@ static psgld_status launch_two_sided(psgld_ctx *c, int part, cudaStream_t st)
     P.err = c->kflag;
     int sms = 0;
     PSGLD_CK(c, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
-    const int grid = std::min(P.items, sms);
+    int grid = std::min(P.items, sms);
+    if (c->opt.max_sms > 0) grid = std::min(grid, c->opt.max_sms);   // leave SMs to other work
     const size_t smem = two_sided_smem(c->KP, vs, P.stages, P.vstages);
     pick_chain(c->v_bf16 != 0, P.p_mode)<<<grid, two_sided::kThreads, smem, st>>>(P);
     PSGLD_CK(c, cudaGetLastError());

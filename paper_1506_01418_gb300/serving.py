@@ -16,7 +16,7 @@ queued at all times.
 With `BatchedGpuExecutor` the jobs' part-steps share launches instead
 (continuous batching at sweep granularity): every admitted job joins the
 next sweep of one shared batch, and each loop iteration that finds fewer
-than three batch sweeps in flight enqueues one more over all unfinished jobs
+than eight batch sweeps in flight enqueues one more over all unfinished jobs
 (per part one tensor-core gradient launch per K class and one update
 launch, through psgld_batch_sweep).  Jobs arriving meanwhile join at the
 next sweep; a finished job leaves the batch and its memory is released.
@@ -55,6 +55,7 @@ class Job:
     init_scale: float = 0.5
     dense_path: int = 1
     dense_v_bf16: int = 0
+    max_sms: int = 0                   # > 0: SMs the two-sided kernel may hold (standing chains)
     arrival: float = 0.0               # seconds from the start of the trace
     data_seed: int = 0
     # filled in by the server
@@ -242,7 +243,7 @@ class GpuExecutor:
                                prior_kind=self.P.PSGLD_PRIOR_EXPONENTIAL, lambda_w=job.lam,
                                lambda_h=job.lam, seed=job.seed, eps=job.eps, use_graphs=1,
                                burn_in_sweeps=job.burn_in, dense_path=job.dense_path,
-                               dense_v_bf16=job.dense_v_bf16)
+                               dense_v_bf16=job.dense_v_bf16, max_sms=job.max_sms)
             ctx.set_data_dense(V, stream.cuda_stream)
             ctx.set_factors(W0, Ht0, stream.cuda_stream)
             del V, W0, Ht0
@@ -279,7 +280,7 @@ class BatchedGpuExecutor(GpuExecutor):
     the batched kernel cannot take (K > 128) and standing chains run on
     their own streams as in GpuExecutor."""
 
-    def __init__(self, device=None, max_inflight: int = 3):
+    def __init__(self, device=None, max_inflight: int = 8):
         super().__init__(device)
         torch = self.torch
         self.stream = torch.cuda.Stream(self.dev, priority=-1)   # the batch's sweeps

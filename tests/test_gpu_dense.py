@@ -227,6 +227,18 @@ def test_dense_is_deterministic(kernel):
     assert np.array_equal(Wa, Wb) and np.array_equal(Ha, Hb)
 
 
+def test_two_sided_kernel_on_fewer_sms_gives_the_same_chain():
+    """max_sms only shrinks the persistent grid: every item still runs once,
+    so the chain is the same bit for bit."""
+    a, _ = _make("poisson_K200_B3", kernel="two_sided")
+    b, _ = _make("poisson_K200_B3", kernel="two_sided", max_sms=7)
+    a.gpu.sweep(2)
+    b.gpu.sweep(2)
+    Wa, Ha = a.gpu_factors()
+    Wb, Hb = b.gpu_factors()
+    assert np.array_equal(Wa, Wb) and np.array_equal(Ha, Hb)
+
+
 @pytest.mark.parametrize("name", ["poisson_ragged_K8", "gauss_K50_two_mtiles_three_ntiles",
                                   "cp_K100", "gamma_K13", "poisson_K200_B3"])
 def test_dense_log_lik_and_rmse_match_oracle(name):

@@ -75,15 +75,33 @@ def test_clock_summary_window_and_reasons():
 
 
 def test_kernel_traffic_requires_unchanged_source(tmp_path, monkeypatch):
+    """The recorded DRAM traffic is reported only while every source it was
+    measured on is unchanged (sha256 of each file in the record)."""
+    import hashlib
+    import shutil
     wl = bench.DEFAULT_WORKLOAD
     t = bench.kernel_traffic(wl)
     path = os.path.join(ROOT, "profiles", "part_step_traffic.json")
-    if os.path.exists(path):
-        d = json.load(open(path))
-        import hashlib
-        src = os.path.join(ROOT, "paper_1506_01418_gb300", "csrc", "psgld_step.cu")
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()
-        if d.get(wl, {}).get("psgld_step_cu_sha256") != h:
-            assert t is None
-    else:
+    if not os.path.exists(path):
         assert t is None
+        return
+    rec = json.load(open(path)).get(wl)
+    if rec is None:
+        assert t is None
+        return
+    same = all(hashlib.sha256(open(os.path.join(ROOT, "paper_1506_01418_gb300", "csrc", f), "rb")
+                              .read()).hexdigest() == h for f, h in rec["sources_sha256"].items())
+    assert t == (rec["dram_bytes_per_launch"] if same else None)
+    # a copy of the tree with one recorded source changed reports nothing
+    fake = tmp_path / "root"
+    (fake / "profiles").mkdir(parents=True)
+    (fake / "paper_1506_01418_gb300" / "csrc").mkdir(parents=True)
+    shutil.copy(path, fake / "profiles" / "part_step_traffic.json")
+    for f in rec["sources_sha256"]:
+        shutil.copy(os.path.join(ROOT, "paper_1506_01418_gb300", "csrc", f),
+                    fake / "paper_1506_01418_gb300" / "csrc" / f)
+    monkeypatch.setattr(bench, "ROOT", str(fake))
+    assert bench.kernel_traffic(wl) == t
+    victim = fake / "paper_1506_01418_gb300" / "csrc" / next(iter(rec["sources_sha256"]))
+    victim.write_bytes(victim.read_bytes() + b"\n// changed\n")
+    assert bench.kernel_traffic(wl) is None

@@ -998,7 +998,7 @@ def run_serving(args, wl_name, wl):
                            "chain's entries x sweeps over the trace's wall time)",
                    "path": "continuous batching: every admitted job's part-steps in the batch's "
                            "shared tensor-core launches (psgld_batch_sweep, one sweep per tick, "
-                           "at most eight ticks queued); the standing chain on its own stream; "
+                           "at most three ticks queued); the standing chain on its own stream; "
                            "PyTorch caching allocator"},
         "latency": lat,
         "job_entries_per_s": r["job_entries"] / wall,

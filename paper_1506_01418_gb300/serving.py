@@ -16,7 +16,7 @@ queued at all times.
 With `BatchedGpuExecutor` the jobs' part-steps share launches instead
 (continuous batching at sweep granularity): every admitted job joins the
 next sweep of one shared batch, and each loop iteration that finds fewer
-than eight batch sweeps in flight enqueues one more over all unfinished jobs
+than three batch sweeps in flight enqueues one more over all unfinished jobs
 (per part one tensor-core gradient launch per K class and one update
 launch, through psgld_batch_sweep).  Jobs arriving meanwhile join at the
 next sweep; a finished job leaves the batch and its memory is released.
@@ -280,7 +280,7 @@ class BatchedGpuExecutor(GpuExecutor):
     the batched kernel cannot take (K > 128) and standing chains run on
     their own streams as in GpuExecutor."""
 
-    def __init__(self, device=None, max_inflight: int = 8):
+    def __init__(self, device=None, max_inflight: int = 3):
         super().__init__(device)
         torch = self.torch
         self.stream = torch.cuda.Stream(self.dev, priority=-1)   # the batch's sweeps
@@ -321,6 +321,10 @@ class BatchedGpuExecutor(GpuExecutor):
         return h
 
     def tick(self):
+        """One more batch sweep over every unfinished job, unless
+        `max_inflight` are already queued.  (Topping the queue up on every
+        call was measured worse: jobs admitted meanwhile joined later, and the
+        standing chain lost the SMs to the always-busy batch stream.)"""
         while self.inflight and self.inflight[0].query():
             self.inflight.popleft()
         if len(self.inflight) >= self.max_inflight or not self.members:

@@ -82,7 +82,7 @@ WORKLOADS["serving_poisson200_mixed_jobs_with_standing_chain"] = dict(
 WORKLOADS["batched_dense_nmf_256chains_513xJ200-5000_K32_B8_bf16"] = dict(
     batched=True, chains=256, I=513, J_lo=200, J_hi=5000, K=32, K_true=16, B=8, p_mix=(1.0, 2.0),
     phi=1.0, prior="exponential", lam=1.0, eps=1e-4, init_scale=0.5, job_sweeps=40,
-    dense_path=1, p=1.0)
+    dense_path=2, p=1.0)
 # the same recipe with 64 chains: the size the batched kernel's full ncu
 # capture uses (340 MB of V, a few seconds of replay)
 WORKLOADS["batched_dense_nmf_64chains_513xJ200-5000_K32_B8_bf16"] = dict(
@@ -764,11 +764,13 @@ def run_batched(args, wl_name, wl):
     for ch in chains:
         ch.close()
     torch.cuda.empty_cache()
+    other = batched_other_kernel(wl, specs, dev, stream, flush, args.steps)
 
     hbm_peak, tc_peak, peak_src = read_peaks()
     grad_ms = g_ms / max(k_n, 1)
     upd_ms = u_ms / max(k_n, 1)
     bytes_launch, flops_launch = batched_bytes_flops(wl, specs)
+    two = wl.get("dense_path", 1) == 2
     achieved = bytes_launch / (grad_ms / 1e3) / 1e9
     tflops = flops_launch / (grad_ms / 1e3) / 1e12
     result = {
@@ -780,26 +782,31 @@ def run_batched(args, wl_name, wl):
                    "K": wl["K"], "K_true": wl["K_true"], "B": wl["B"], "tweedie_p": list(wl["p_mix"]),
                    "prior": wl["prior"], "eps": wl["eps"],
                    "step": "one sweep of every chain: per part one tensor-core gradient launch "
-                           "and one update launch over all chains, then the FP64 posterior sums",
-                   "path": "psgld_batch_sweep, single-pass tensor-core block chain, BF16 operands, "
-                           "FP32 accumulate",
+                           "per kernel variant (" + ("one persistent launch per Tweedie power"
+                           if two else "one per K class") + ") and one update launch over all "
+                           "chains, then the FP64 posterior sums",
+                   "path": "psgld_batch_sweep, " + ("two-sided" if two else "single-pass") +
+                           " tensor-core block chain, BF16 operands, FP32 accumulate, FP32 V",
                    "l2": "V of all chains (1.4 GB) exceeds L2; 256 MB buffer also written before "
                          "every timed sweep"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak, "traffic": kernel_traffic(wl_name),
-                     "kernel": "dense_grad_batch_kernel", "kernel_ms": grad_ms,
+                     "kernel": ("two_sided::chain_batch_kernel (per part: one launch per power)"
+                                if two else "dense_grad_batch_kernel"), "kernel_ms": grad_ms,
                      "algorithmic_bytes_per_launch": bytes_launch,
                      "algorithmic_flops_per_launch": flops_launch, "tensor_tflops": tflops,
                      "tensor_frac_of_sustained": tflops / tc_peak,
                      "update_kernel_ms": upd_ms, "part_step_ms": grad_ms + upd_ms,
                      "peak_source": f"{peak_src} HBM copy bandwidth"},
-        # per call (one sweep): set t, B x (gradient + update; one K class),
-        # accumulate, advance t
-        "gpu_launches": args.steps * (2 * wl["B"] + 3),
+        # per call (one sweep): set t, B x (gradient launches + update),
+        # accumulate, advance t; the two-sided kernel runs one launch per
+        # power, the single-pass one per K class
+        "gpu_launches": args.steps * ((len(set(wl["p_mix"])) if two else 1) * wl["B"] + wl["B"] + 3),
         "clocks": clocks,
         "unbatched": {"value": N / (ms_alone / 1e3), "unit": UNIT, "ms_per_sweep": ms_alone,
                       "how": "the same chains, each swept alone (its own captured-graph sweep), "
                              "back to back on one stream"},
+        "other_kernel": other,
     }
     if args.compare_sweeps > 0:
         result["precision_compare"] = batched_precision(wl, specs[:16], dev, args.compare_sweeps)
@@ -808,6 +815,42 @@ def run_batched(args, wl_name, wl):
     if not args.no_cpu_baseline:
         result["cpu_baseline"] = batched_cpu_baseline(wl, specs[0], args.cpu_budget)
     print(json.dumps(result), flush=True)
+
+
+def batched_other_kernel(wl, specs, dev, stream, flush, steps: int):
+    """The same chains and batched sweeps on the other tensor-core kernel
+    (two-sided if the workload runs single-pass, and the reverse): entries/s
+    of the timed sweeps."""
+    import torch
+
+    from paper_1506_01418_gb300 import psgld as P
+    dp = 2 if wl.get("dense_path", 1) != 2 else 3
+    made = batched_make(wl, specs, dev, dense_path=dp)
+    chains = [m[0] for m in made]
+    for ch, V, W0, Ht0 in made:
+        ch.set_data_dense(V)
+        ch.set_factors(W0, Ht0)
+    del made
+    torch.cuda.synchronize(dev)
+    for _ in range(3):
+        P.psgld_batch_sweep(chains, 1, stream.cuda_stream)
+    torch.cuda.synchronize(dev)
+    n = max(3, min(steps, 10))
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(n)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(n)]
+    for s in range(n):
+        flush.zero_()
+        starts[s].record(stream)
+        P.psgld_batch_sweep(chains, 1, stream.cuda_stream)
+        ends[s].record(stream)
+    torch.cuda.synchronize(dev)
+    ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends)) / n
+    for ch in chains:
+        ch.close()
+    torch.cuda.empty_cache()
+    N = sum(wl["I"] * J for J, _, _, _ in specs)
+    return {"kernel": "two_sided (one persistent launch per part and power)" if dp == 2 else "single_pass",
+            "value": N / (ms / 1e3), "unit": UNIT, "ms_per_sweep": ms, "sweeps": n}
 
 
 def batched_precision(wl, specs, dev, sweeps: int):
@@ -821,7 +864,8 @@ def batched_precision(wl, specs, dev, sweeps: int):
     out = {"chains": len(specs), "sweeps": sweeps, "burn_in_sweeps": sweeps // 2}
     N = sum(wl["I"] * J for J, _, _, _ in specs)
     stream = torch.cuda.current_stream(dev)
-    for name, opts in (("bf16_tensor_core_batched", {}), ("e4m3_gemm1_batched", {"dense_fp8": 1}),
+    for name, opts in (("bf16_tensor_core_batched", {}),
+                       ("e4m3_gemm1_batched", {"dense_fp8": 1, "dense_path": 3}),
                        ("fp32_gather", {"dense_path": 0})):
         made = batched_make(wl, specs, dev, burn_in_sweeps=sweeps // 2, **opts)
         for ch, V, W0, Ht0 in made:

@@ -208,20 +208,22 @@ PSGLD_API psgld_status psgld_part_step(psgld_ctx *ctx, int64_t t, void *stream);
 PSGLD_API psgld_status psgld_sweep(psgld_ctx *ctx, int32_t n_sweeps, void *stream);
 
 /* n_sweeps sweeps of each of the n contexts, their part-steps sharing
- * launches: at every part of a sweep one tensor-core gradient launch per K
- * class (K rounded up to 16, 32, 64 or 128) covers the blocks of all the
- * contexts of that class, and one update launch covers all the contexts'
- * rows; then each context's posterior sums as in psgld_sweep.  Every context
- * must hold dense data on the single-pass tensor-core kernel (dense_path 1
- * with blocks of at most 128 rows and K <= 128, or dense_path 3), the same
- * B, cyclic parts and its iteration counter at a sweep boundary; sizes,
- * powers, priors, seeds and step sizes may differ.  Each context ends in the
- * same state, bit for bit, as after psgld_sweep(ctx, n_sweeps).  The work
- * is enqueued on `stream` (the call returns before it runs, like
- * psgld_sweep); the launches' parameter tables are kept by the first context
- * of the list and reused by its next batch.  A context may be in one batch
- * at a time: a call whose list shares a context with a batch still running
- * on another stream must be ordered after it by the caller. */
+ * launches: at every part of a sweep one gradient launch per group of
+ * contexts on the same tensor-core kernel variant covers the blocks of all
+ * of them -- single-pass contexts grouped by K class (K rounded up to 16,
+ * 32, 64 or 128) and GEMM1 precision, two-sided contexts by K width (K
+ * rounded up to 64), V type and Tweedie power, the latter as one persistent
+ * launch over all their items -- and one update launch covers all the
+ * contexts' rows; then each context's posterior sums as in psgld_sweep.
+ * Every context must hold dense data on a tensor-core kernel (dense_path 1,
+ * 2 or 3), the same B, cyclic parts and its iteration counter at a sweep
+ * boundary; sizes, powers, priors, seeds and step sizes may differ.  Each
+ * context ends in the same state, bit for bit, as after psgld_sweep(ctx,
+ * n_sweeps).  The work is enqueued on `stream` (the call returns before it
+ * runs, like psgld_sweep); the launches' parameter tables are kept by the
+ * first context of the list and reused by its next batch.  A context may be
+ * in one batch at a time: a call whose list shares a context with a batch
+ * still running on another stream must be ordered after it by the caller. */
 PSGLD_API psgld_status psgld_batch_sweep(psgld_ctx *const *ctxs_host, int32_t n, int32_t n_sweeps,
                                          void *stream);
 

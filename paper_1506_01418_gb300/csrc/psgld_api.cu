@@ -739,7 +739,7 @@ psgld_status psgld_batch_sweep(psgld_ctx *const *ctxs, int32_t n, int32_t n_swee
         psgld_status s;
         if (!ready(c, &s)) return s;
         if (!c->dense || dense_batch_key(c) <= 0)
-            return fail(c, PSGLD_ERR_STATE, "batched sweeps need dense data on the single-pass kernel");
+            return fail(c, PSGLD_ERR_STATE, "batched sweeps need dense data on the tensor-core kernels");
         if (c->B != B) return fail(c, PSGLD_ERR_ARG, "batched contexts must share B");
         if (c->opt.part_mode != 0) return fail(c, PSGLD_ERR_STATE, "batched sweeps use cyclic parts");
         if (c->t_done % B != 0) return fail(c, PSGLD_ERR_STATE, "sweep must start at a sweep boundary");

@@ -544,10 +544,12 @@ __global__ void __launch_bounds__(kDenseThreads, 1) dense_grad_kernel(const __gr
 }
 
 // Many contexts in one launch: context i owns CTAs [cta_start[i],
-// cta_start[i + 1]) of the grid (cta_start[n] = grid size).
+// cta_start[i + 1]) of the grid (cta_start[n] = grid size); its parameters
+// are the slot `stride` bytes * i into `tab`.
 template <int KP, bool F8>
 __global__ void __launch_bounds__(kDenseThreads, 1)
-dense_grad_batch_kernel(const DenseParams *__restrict__ Ps, const int *__restrict__ cta_start, int n)
+dense_grad_batch_kernel(const unsigned char *__restrict__ tab, size_t stride, const int *__restrict__ cta_start,
+                        int n)
 {
     const int b = blockIdx.x;
     int lo = 0, hi = n - 1;          // last i with cta_start[i] <= b
@@ -555,7 +557,8 @@ dense_grad_batch_kernel(const DenseParams *__restrict__ Ps, const int *__restric
         const int mid = (lo + hi + 1) >> 1;
         if (__ldg(cta_start + mid) <= b) lo = mid; else hi = mid - 1;
     }
-    dense_grad_cta<KP, F8>(Ps[lo], b - __ldg(cta_start + lo));
+    dense_grad_cta<KP, F8>(*reinterpret_cast<const DenseParams *>(tab + (size_t)lo * stride),
+                           b - __ldg(cta_start + lo));
 }
 
 // ===========================================================================
@@ -805,13 +808,43 @@ __device__ __forceinline__ float tweedie_pm(float p, float phi_inv, float mu_min
     }
 }
 
-template <typename VT, int PM>
-__global__ void __launch_bounds__(kThreads, 1) chain_kernel(const __grid_constant__ Params P)
+// Where the items' parameters come from: one context (the kernel parameter)
+// or, batched, a table of contexts in global memory whose items follow one
+// another (context i owns items [item_start[i], item_start[i + 1]); slots
+// `stride` bytes apart).
+struct Src {
+    const unsigned char *tab;
+    const int *item_start;
+    int n;
+    size_t stride;
+};
+
+template <bool BATCH>
+__device__ __forceinline__ const Params &ctx_of(const Params &P0, const Src &src, int it, int &local)
+{
+    if constexpr (!BATCH) {
+        local = it;
+        return P0;
+    } else {
+        int lo = 0, hi = src.n - 1;          // last i with item_start[i] <= it
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(src.item_start + mid) <= it) lo = mid; else hi = mid - 1;
+        }
+        local = it - __ldg(src.item_start + lo);
+        return *reinterpret_cast<const Params *>(src.tab + (size_t)lo * src.stride);
+    }
+}
+
+// The kernel body.  P0 gives what is uniform over the launch (K width,
+// ring depths); each item reads its own context's parameters.
+template <typename VT, int PM, bool BATCH>
+__device__ __forceinline__ void chain_body(const Params &P0, const Src src, const int total_items)
 {
     extern __shared__ __align__(1024) unsigned char sm_raw[];
     // the swizzled operand tiles need 1024-byte alignment (1 KB of slack is allocated)
     unsigned char *sm = sm_raw + ((1024u - (saddr(sm_raw) & 1023u)) & 1023u);
-    const int KP = P.KP;                                        // multiple of 64
+    const int KP = P0.KP;                                       // multiple of 64
     const int NA = KP / 64;                                     // 128-byte atoms along K
     const uint32_t a_bytes = (uint32_t)kOwn * KP * 2;           // owned tile
     const uint32_t b_bytes = (uint32_t)kBN * KP * 2;            // walked tile
@@ -820,10 +853,10 @@ __global__ void __launch_bounds__(kThreads, 1) chain_kernel(const __grid_constan
     unsigned char *sA = sm;
     unsigned char *sE = sA + a_bytes;                           // 2 x e_bytes
     unsigned char *sB = sE + 2 * e_bytes;                       // NS x b_bytes
-    unsigned char *sV = sB + (size_t)P.stages * b_bytes;        // NV x v_bytes
-    Bars *S = reinterpret_cast<Bars *>(sV + (size_t)P.vstages * v_bytes);
+    unsigned char *sV = sB + (size_t)P0.stages * b_bytes;       // NV x v_bytes
+    Bars *S = reinterpret_cast<Bars *>(sV + (size_t)P0.vstages * v_bytes);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int NS = P.stages, NV = P.vstages;
+    const int NS = P0.stages, NV = P0.vstages;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < NS; ++s) { bar_init(&S->full[s], 1); bar_init(&S->empty[s], 1); }
@@ -853,9 +886,11 @@ __global__ void __launch_bounds__(kThreads, 1) chain_kernel(const __grid_constan
             const uint32_t ld = lane == 0;
             uint32_t ic = 0;
             Ring rb, rv;
-            for (int it = blockIdx.x; it < P.items; it += gridDim.x) {
+            for (int it = blockIdx.x; it < total_items; it += gridDim.x) {
+                int lit;
+                const Params &P = ctx_of<BATCH>(P0, src, it, lit);
                 Item x;
-                if (!decode(P, it, x)) continue;
+                if (!decode(P, lit, x)) continue;
                 const Side &Sd = P.side[x.side];
                 if (!wait32(S, &S->a_empty, (ic & 1) ^ 1)) goto done0;
                 expect_tx_if(ld, &S->a_full, a_bytes);
@@ -904,9 +939,11 @@ __global__ void __launch_bounds__(kThreads, 1) chain_kernel(const __grid_constan
             // next atom of the owned tile starts 128 rows x 128 B further
             const uint32_t aA = saddr(sA);
             const uint32_t tA = tmem + (kTmemCols - (uint32_t)KP / 2);   // owned tile in TMEM
-            for (int it = blockIdx.x; it < P.items; it += gridDim.x) {
+            for (int it = blockIdx.x; it < total_items; it += gridDim.x) {
+                int lit;
+                const Params &P = ctx_of<BATCH>(P0, src, it, lit);
                 Item x;
-                if (!decode(P, it, x)) continue;
+                if (!decode(P, lit, x)) continue;
                 if (!wait32(S, &S->a_full, ic & 1)) goto done1;
                 fence_after();
                 // the owned tile into TMEM once per item (ordered after the
@@ -976,10 +1013,13 @@ __global__ void __launch_bounds__(kThreads, 1) chain_kernel(const __grid_constan
         const uint32_t lane_base = (uint32_t)(32 * q) << 16;
         uint32_t tc = 0, ic = 0;
         Ring rv;
-        for (int it = blockIdx.x; it < P.items; it += gridDim.x) {
+        for (int it = blockIdx.x; it < total_items; it += gridDim.x) {
+            int lit;
+            const Params &P = ctx_of<BATCH>(P0, src, it, lit);
             Item x;
-            if (!decode(P, it, x)) continue;
+            if (!decode(P, lit, x)) continue;
             const Side &Sd = P.side[x.side];
+            const float pp = P.p, phi_inv = P.phi_inv, mu_min = P.mu_min;
             for (int j = 0; j < x.nj; ++j, ++tc, rv.next(NV)) {
                 const int b = (int)(tc & 1);
                 const uint32_t sv = rv.slot;
@@ -1016,8 +1056,8 @@ __global__ void __launch_bounds__(kThreads, 1) chain_kernel(const __grid_constan
                 uint32_t pk[16];
 #pragma unroll
                 for (int h = 0; h < 16; ++h) {
-                    const float e0 = tweedie_pm<PM>(P.p, P.phi_inv, P.mu_min, v[2 * h], mu[2 * h]);
-                    const float e1 = tweedie_pm<PM>(P.p, P.phi_inv, P.mu_min, v[2 * h + 1], mu[2 * h + 1]);
+                    const float e0 = tweedie_pm<PM>(pp, phi_inv, mu_min, v[2 * h], mu[2 * h]);
+                    const float e1 = tweedie_pm<PM>(pp, phi_inv, mu_min, v[2 * h + 1], mu[2 * h + 1]);
                     __nv_bfloat162 t2 = __floats2bfloat162_rn(e0, e1);
                     pk[h] = *reinterpret_cast<uint32_t *>(&t2);
                 }
@@ -1065,10 +1105,32 @@ __global__ void __launch_bounds__(kThreads, 1) chain_kernel(const __grid_constan
     fence_before();
     __syncthreads();
     fence_after();
-    if (threadIdx.x == 0 && S->abort) atomicOr(P.err, 64 | S->abort);   // two-sided kernel (+ role)
+    if (threadIdx.x == 0 && S->abort) {                      // two-sided kernel (+ role)
+        if constexpr (BATCH) {
+            for (int i = 0; i < src.n; ++i)
+                atomicOr(reinterpret_cast<const Params *>(src.tab + (size_t)i * src.stride)->err, 64 | S->abort);
+        } else {
+            atomicOr(P0.err, 64 | S->abort);
+        }
+    }
     if (warp == 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;"
                      :: "r"(tmem), "r"(kTmemCols) : "memory");
+}
+
+template <typename VT, int PM>
+__global__ void __launch_bounds__(kThreads, 1) chain_kernel(const __grid_constant__ Params P)
+{
+    chain_body<VT, PM, false>(P, Src{nullptr, nullptr, 1, 0}, P.items);
+}
+
+// Many contexts of one K width, V type and power in one persistent launch.
+template <typename VT, int PM>
+__global__ void __launch_bounds__(kThreads, 1)
+chain_batch_kernel(const unsigned char *tab, size_t stride, const int *item_start, int n)
+{
+    chain_body<VT, PM, true>(*reinterpret_cast<const Params *>(tab), Src{tab, item_start, n, stride},
+                             __ldg(item_start + n));
 }
 
 }  // namespace two_sided
@@ -1086,7 +1148,7 @@ DenseFn pick_dense(int kp, bool f8)
     return nullptr;
 }
 
-using DenseBatchFn = void (*)(const DenseParams *, const int *, int);
+using DenseBatchFn = void (*)(const unsigned char *, size_t, const int *, int);
 
 DenseBatchFn pick_dense_batch(int kp, bool f8)
 {
@@ -1183,6 +1245,18 @@ ChainFn pick_chain(bool vb, int pm)
          two_sided::chain_kernel<float, 2>, two_sided::chain_kernel<float, 3>},
         {two_sided::chain_kernel<__nv_bfloat16, 0>, two_sided::chain_kernel<__nv_bfloat16, 1>,
          two_sided::chain_kernel<__nv_bfloat16, 2>, two_sided::chain_kernel<__nv_bfloat16, 3>}};
+    return f[vb ? 1 : 0][pm];
+}
+
+using ChainBatchFn = void (*)(const unsigned char *, size_t, const int *, int);
+
+ChainBatchFn pick_chain_batch(bool vb, int pm)
+{
+    static const ChainBatchFn f[2][4] = {
+        {two_sided::chain_batch_kernel<float, 0>, two_sided::chain_batch_kernel<float, 1>,
+         two_sided::chain_batch_kernel<float, 2>, two_sided::chain_batch_kernel<float, 3>},
+        {two_sided::chain_batch_kernel<__nv_bfloat16, 0>, two_sided::chain_batch_kernel<__nv_bfloat16, 1>,
+         two_sided::chain_batch_kernel<__nv_bfloat16, 2>, two_sided::chain_batch_kernel<__nv_bfloat16, 3>}};
     return f[vb ? 1 : 0][pm];
 }
 
@@ -1300,9 +1374,9 @@ psgld_status build_dense_shadows(psgld_ctx *c, cudaStream_t st)
     return PSGLD_OK;
 }
 
-static psgld_status launch_two_sided(psgld_ctx *c, int part, cudaStream_t st)
+static void fill_two_sided(const psgld_ctx *c, int part, two_sided::Params &P)
 {
-    two_sided::Params P{};
+    P = two_sided::Params{};
     const int64_t I = c->I, J = c->J;
     two_sided::Side &A = P.side[0], &Bs = P.side[1];
     A.own_sh = c->Wsh; A.walk_sh = c->Hsh; A.Vt = (const unsigned char *)c->VA; A.G = c->G;
@@ -1324,6 +1398,13 @@ static psgld_status launch_two_sided(psgld_ctx *c, int part, cudaStream_t st)
     P.mu_min = (float)c->opt.mu_min;
     P.p_mode = c->p == 0.0 ? 0 : c->p == 1.0 ? 1 : c->p == 2.0 ? 2 : 3;
     P.err = c->kflag;
+}
+
+static psgld_status launch_two_sided(psgld_ctx *c, int part, cudaStream_t st)
+{
+    two_sided::Params P;
+    fill_two_sided(c, part, P);
+    const int vs = c->v_bf16 ? 2 : 4;
     int sms = 0;
     PSGLD_CK(c, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
     int grid = std::min(P.items, sms);
@@ -1371,12 +1452,32 @@ psgld_status launch_dense_grad(psgld_ctx *c, int part, cudaStream_t st)
     return PSGLD_OK;
 }
 
-int dense_batch_key(const psgld_ctx *c) { return c->dense_kind == 1 ? 2 * dense_kp(c->K) + c->dense_fp8 : 0; }
+// Batch keys: single-pass 2 KP + fp8 (< 4096); two-sided 4096 + 8 KP +
+// 4 v_bf16 + power mode (the chain kernel's template arguments).
+int dense_batch_key(const psgld_ctx *c)
+{
+    if (c->dense_kind == 1) return 2 * dense_kp(c->K) + c->dense_fp8;
+    if (c->dense_kind == 2) {
+        const int pm = c->p == 0.0 ? 0 : c->p == 1.0 ? 1 : c->p == 2.0 ? 2 : 3;
+        return 4096 + 8 * c->KP + 4 * c->v_bf16 + pm;
+    }
+    return 0;
+}
 
-size_t dense_param_bytes() { return sizeof(DenseParams); }
+size_t dense_param_bytes()
+{
+    const size_t m = std::max(sizeof(DenseParams), sizeof(two_sided::Params));
+    return (m + 15) & ~size_t(15);
+}
 
 int fill_dense_param(const psgld_ctx *c, int part, void *dst)
 {
+    if (c->dense_kind == 2) {
+        two_sided::Params P;
+        fill_two_sided(c, part, P);
+        std::memcpy(dst, &P, sizeof P);
+        return P.items;
+    }
     DenseParams P;
     fill_dense_params(c, part, P);
     std::memcpy(dst, &P, sizeof P);
@@ -1384,16 +1485,35 @@ int fill_dense_param(const psgld_ctx *c, int part, void *dst)
 }
 
 psgld_status launch_dense_batch(psgld_ctx *c0, int key, const void *params, const int *cta_start, int n,
-                                int total_ctas, cudaStream_t st)
+                                int total, cudaStream_t st)
 {
+    const unsigned char *tab = static_cast<const unsigned char *>(params);
+    const size_t stride = dense_param_bytes();
+    if (key >= 4096) {
+        // two-sided contexts: one persistent launch over all their items
+        const int KP = (key - 4096) / 8;
+        const bool vb = ((key >> 2) & 1) != 0;
+        const int pm = key & 3;
+        const int vs = vb ? 2 : 4;
+        int stages = 0, vstages = 0;
+        two_sided_stages(KP, vs, &stages, &vstages);
+        const size_t smem = two_sided_smem(KP, vs, stages, vstages);
+        ChainBatchFn fn = pick_chain_batch(vb, pm);
+        PSGLD_CK(c0, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int sms = 0;
+        PSGLD_CK(c0, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c0->device));
+        const int grid = std::min(total, sms);
+        if (grid > 0) fn<<<grid, two_sided::kThreads, smem, st>>>(tab, stride, cta_start, n);
+        PSGLD_CK(c0, cudaGetLastError());
+        return PSGLD_OK;
+    }
     const int kp = key / 2;
     const bool f8 = (key & 1) != 0;
     DenseBatchFn fn = pick_dense_batch(kp, f8);
     if (!fn) return fail(c0, PSGLD_ERR_ARG, "single-pass dense kernel supports K <= 128");
     const size_t smem = dense_smem(kp, f8);
     PSGLD_CK(c0, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    if (total_ctas > 0)
-        fn<<<total_ctas, kDenseThreads, smem, st>>>(static_cast<const DenseParams *>(params), cta_start, n);
+    if (total > 0) fn<<<total, kDenseThreads, smem, st>>>(tab, stride, cta_start, n);
     PSGLD_CK(c0, cudaGetLastError());
     return PSGLD_OK;
 }

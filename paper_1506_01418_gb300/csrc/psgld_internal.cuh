@@ -208,13 +208,15 @@ psgld_status launch_dense_grad(psgld_ctx *c, int part, cudaStream_t st);
 // context's current ping-pong buffers) and return its share of the grid:
 // CTAs, update items or float4 accumulation units.  The *_start arrays are
 // exclusive prefix sums of those shares (n + 1 entries, device memory).
-// Dense: single-pass contexts of one K class and GEMM1 precision
-// (dense_batch_key equal, > 0; the key is passed to launch_dense_batch).
+// Dense: contexts of one batch key (> 0): single-pass ones of one K class
+// and GEMM1 precision (one CTA range each), or two-sided ones of one K
+// width, V type and power (one persistent launch over all their items).
+// Every table slot is dense_param_bytes() long.
 int dense_batch_key(const psgld_ctx *c);
 size_t dense_param_bytes();
 int fill_dense_param(const psgld_ctx *c, int part, void *dst);
 psgld_status launch_dense_batch(psgld_ctx *c0, int key, const void *params, const int *cta_start, int n,
-                                int total_ctas, cudaStream_t st);
+                                int total, cudaStream_t st);
 // Update of part `part` at iteration *t_dev + t_add (t_dev: the context's
 // device counter); does not flip the context's buffers.
 size_t upd_param_bytes();

@@ -276,9 +276,10 @@ class BatchedGpuExecutor(GpuExecutor):
     """Continuous batching: the part-steps of all admitted jobs share
     launches.  Jobs run on one stream; each tick (when fewer than
     `max_inflight` batch sweeps are queued) enqueues one psgld_batch_sweep
-    over every unfinished job, so each advances by one sweep per tick.  Jobs
-    the batched kernel cannot take (K > 128) and standing chains run on
-    their own streams as in GpuExecutor."""
+    over every unfinished job, so each advances by one sweep per tick (each
+    job on the tensor-core kernel its shape selects; jobs on the same kernel
+    variant share its launches).  Standing chains run on their own streams
+    as in GpuExecutor."""
 
     def __init__(self, device=None, max_inflight: int = 3):
         super().__init__(device)
@@ -293,13 +294,7 @@ class BatchedGpuExecutor(GpuExecutor):
 
     @staticmethod
     def batchable(job: Job) -> bool:
-        return job.sweeps is not None and job.K <= 128 and not job.dense_v_bf16
-
-    def estimate(self, job: Job) -> int:
-        if not self.batchable(job):
-            return super().estimate(job)
-        nbytes = self.P.psgld_estimate_device_bytes(job.I, job.J, job.K, job.B, 0, 3, 0)
-        return nbytes + 4 * job.I * job.J
+        return job.sweeps is not None and job.dense_path != 0
 
     def start(self, job: Job):
         if not self.batchable(job):
@@ -312,7 +307,8 @@ class BatchedGpuExecutor(GpuExecutor):
             ctx = self.P.PSGLD(job.I, job.J, job.K, job.B, job.p, job.phi,
                                prior_kind=self.P.PSGLD_PRIOR_EXPONENTIAL, lambda_w=job.lam,
                                lambda_h=job.lam, seed=job.seed, eps=job.eps, use_graphs=0,
-                               burn_in_sweeps=job.burn_in, dense_path=3)
+                               burn_in_sweeps=job.burn_in, dense_path=job.dense_path,
+                               dense_v_bf16=job.dense_v_bf16)
             ctx.set_data_dense(V, self.adm.cuda_stream)
             ctx.set_factors(W0, Ht0, self.adm.cuda_stream)
             del V, W0, Ht0

@@ -1,14 +1,16 @@
 """Many dense chains sweeping in shared launches (psgld_batch_sweep).
 
-At every part of a sweep one tensor-core gradient launch per K class covers
-the blocks of all the chains of that class and one update launch covers all
+At every part of a sweep one tensor-core gradient launch per kernel variant
+covers the blocks of all the chains on it (the two-sided kernel as one
+persistent launch over all their items) and one update launch covers all
 the chains' rows (Sec. 3's part-step, run for many independent chains at
 once).  Each chain reads only its own parameters, so a chain swept in a
 batch must end bit for bit where the same chain swept alone ends (alone
 through the captured-graph sweep): factors, posterior sums and iteration
 counter.  The batch mixes sizes (ragged blocks, blocks over one 128-row
 tile), ranks of every K class, Tweedie powers, both priors and both step
-size schedules, and GEMM1 in BF16 and in E4M3.
+size schedules, GEMM1 in BF16 and in E4M3, and both tensor-core kernels
+(the two-sided one with FP32 and BF16 V, K widths 64 and 256).
 """
 import numpy as np
 import pytest
@@ -21,22 +23,29 @@ torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():
     pytest.skip("no CUDA device", allow_module_level=True)
 
-# (I, J, K, p, prior_kind, eps_mode, fp8)
+# (I, J, K, p, prior_kind, eps_mode, kernel options)
+SP = dict(dense_path=3)
 MIX = [
-    (300, 700, 8, 1.0, 0, 0, 0),
-    (513, 900, 16, 2.0, 0, 0, 0),     # blocks of 128 and 129 rows: two M-tiles
-    (257, 4000, 32, 1.0, 0, 0, 0),
-    (640, 1000, 32, 1.5, 0, 1, 0),    # second chain of the K = 32 class, eps_t = (a/t)^b
-    (1025, 300, 64, 0.0, 1, 0, 0),    # Gaussian likelihood and priors
-    (90, 61, 13, 3.0, 0, 0, 0),
-    (200, 500, 100, 1.0, 0, 1, 0),
-    (400, 800, 32, 1.0, 0, 0, 1),     # E4M3 GEMM1: a launch of its own
-    (130, 333, 12, 2.0, 0, 0, 1),
+    (300, 700, 8, 1.0, 0, 0, SP),
+    (513, 900, 16, 2.0, 0, 0, SP),    # blocks of 128 and 129 rows: two M-tiles
+    (257, 4000, 32, 1.0, 0, 0, SP),
+    (640, 1000, 32, 1.5, 0, 1, SP),   # second chain of the K = 32 class, eps_t = (a/t)^b
+    (1025, 300, 64, 0.0, 1, 0, SP),   # Gaussian likelihood and priors
+    (90, 61, 13, 3.0, 0, 0, SP),
+    (200, 500, 100, 1.0, 0, 1, SP),
+    (400, 800, 32, 1.0, 0, 0, dict(dense_path=3, dense_fp8=1)),   # E4M3 GEMM1: a launch of its own
+    (130, 333, 12, 2.0, 0, 0, dict(dense_path=3, dense_fp8=1)),
+    # two-sided kernel: one persistent launch per (K width, V type, power)
+    (300, 700, 8, 1.0, 0, 0, dict(dense_path=2)),
+    (513, 2000, 50, 1.0, 0, 1, dict(dense_path=2)),   # blocks over 128 rows
+    (260, 390, 200, 1.0, 0, 0, dict(dense_path=2)),   # K width 256
+    (700, 450, 40, 2.0, 0, 0, dict(dense_path=2, dense_v_bf16=1)),
+    (333, 777, 64, 2.0, 0, 0, dict(dense_path=2, dense_v_bf16=1)),
 ]
 B = 4
 
 
-def _chain(idx, I, J, K, p, kind, eps_mode, fp8, use_graphs, burn_in=1):
+def _chain(idx, I, J, K, p, kind, eps_mode, kopts, use_graphs, burn_in=1):
     dev = torch.device("cuda", 0)
     if p == 1.0:
         V, _, _ = datagen.dense_poisson(I, J, 3, idx)
@@ -47,8 +56,7 @@ def _chain(idx, I, J, K, p, kind, eps_mode, fp8, use_graphs, burn_in=1):
     nonneg = kind == 0
     W0, H0 = datagen.init_factors(I, J, K, seed=idx + 50, scale=0.4 if nonneg else 0.3,
                                   nonneg=nonneg)
-    opts = dict(seed=1000 + idx, eps=1e-4, burn_in_sweeps=burn_in, dense_path=3,
-                use_graphs=use_graphs, dense_fp8=fp8)
+    opts = dict(seed=1000 + idx, eps=1e-4, burn_in_sweeps=burn_in, use_graphs=use_graphs, **kopts)
     if eps_mode:
         opts.update(eps_mode=P.PSGLD_EPS_POLY, eps_a=0.02, eps_b=0.55)
     ch = P.PSGLD(I, J, K, B, p, 1.0, prior_kind=kind, lambda_w=0.8, lambda_h=1.2, sigma_w=0.9,
@@ -118,10 +126,10 @@ def test_batch_refusals():
     with pytest.raises(P.PsgldError) as ex:
         P.psgld_batch_sweep([good, other], 1)
     assert ex.value.status == P.PSGLD_ERR_STATE
-    # a two-sided context
+    # a context on the sparse layout (dense V through the FP32 gather path)
     I, J, K = 300, 700, 8
     V, _, _ = datagen.dense_poisson(I, J, 3, 0)
-    two = P.PSGLD(I, J, K, B, 1.0, 1.0, dense_path=2)
+    two = P.PSGLD(I, J, K, B, 1.0, 1.0, dense_path=0)
     two.set_data_dense(torch.from_numpy(V).cuda())
     W0, H0 = datagen.init_factors(I, J, K, seed=1, scale=0.4, nonneg=True)
     two.set_factors(torch.from_numpy(W0).cuda(), torch.from_numpy(H0.T.copy()).cuda())

@@ -114,7 +114,8 @@ def test_batched_serving_result_is_the_same_alone_and_in_the_mix():
         job = _jobs()[0]
         V, W0, Ht0 = ex._data(job)
         ch = P.PSGLD(job.I, job.J, job.K, job.B, job.p, job.phi, seed=job.seed, eps=job.eps,
-                     burn_in_sweeps=job.burn_in, dense_path=3, lambda_w=job.lam, lambda_h=job.lam)
+                     burn_in_sweeps=job.burn_in, dense_path=job.dense_path, lambda_w=job.lam,
+                     lambda_h=job.lam)
         ch.set_data_dense(V)
         ch.set_factors(W0, Ht0)
         ch.sweep(job.sweeps)

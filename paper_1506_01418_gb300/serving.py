@@ -276,16 +276,21 @@ class BatchedGpuExecutor(GpuExecutor):
     """Continuous batching: the part-steps of all admitted jobs share
     launches.  Jobs run on one stream; each tick (when fewer than
     `max_inflight` batch sweeps are queued) enqueues one psgld_batch_sweep
-    over every unfinished job, so each advances by one sweep per tick (each
-    job on the tensor-core kernel its shape selects; jobs on the same kernel
-    variant share its launches).  Standing chains run on their own streams
-    as in GpuExecutor."""
+    over every unfinished job that is set up, so each advances by one sweep
+    per tick (each job on the tensor-core kernel its shape selects; jobs on
+    the same kernel variant share its launches).  A job's set-up (device
+    data, context, input checks) and its read-back and teardown run on two
+    worker threads, so the loop that enqueues the batch sweeps does not wait
+    for them.  Standing chains run on their own streams as in GpuExecutor."""
 
     def __init__(self, device=None, max_inflight: int = 3):
+        import concurrent.futures as cf
         super().__init__(device)
         torch = self.torch
         self.stream = torch.cuda.Stream(self.dev, priority=-1)   # the batch's sweeps
         self.adm = torch.cuda.Stream(self.dev, priority=-1)      # admitted jobs' data and set-up
+        self.setup_pool = cf.ThreadPoolExecutor(max_workers=1)
+        self.teardown_pool = cf.ThreadPoolExecutor(max_workers=1)
         self.members: list = []
         self.inflight: collections.deque = collections.deque()
         self.max_inflight = int(max_inflight)
@@ -296,12 +301,9 @@ class BatchedGpuExecutor(GpuExecutor):
     def batchable(job: Job) -> bool:
         return job.sweeps is not None and job.dense_path != 0
 
-    def start(self, job: Job):
-        if not self.batchable(job):
-            return super().start(job)
+    def _setup(self, job: Job, h):
         torch = self.torch
-        # set-up synchronises its own stream only, so the batch's queued
-        # sweeps keep running while a job is admitted
+        torch.cuda.set_device(self.dev)
         with torch.cuda.stream(self.adm):
             V, W0, Ht0 = self._data(job)
             ctx = self.P.PSGLD(job.I, job.J, job.K, job.B, job.p, job.phi,
@@ -312,22 +314,53 @@ class BatchedGpuExecutor(GpuExecutor):
             ctx.set_data_dense(V, self.adm.cuda_stream)
             ctx.set_factors(W0, Ht0, self.adm.cuda_stream)
             del V, W0, Ht0
-        h = {"ctx": ctx, "left": job.sweeps, "batched": True, "event": None, "sweeps_queued": 0}
+            ev = torch.cuda.Event()
+            ev.record(self.adm)
+        h["ctx"] = ctx
+        h["ready_event"] = ev
+
+    def _teardown(self, h) -> dict:
+        self.torch.cuda.set_device(self.dev)
+        h["event"].synchronize()
+        Wm, Wv, Hm, Hv, n = h["ctx"].posterior_mean()
+        out = {"Wmean": Wm, "Hmean": Hm, "n_samples": n, "sweeps": h["sweeps_queued"]}
+        h["ctx"].close()
+        return out
+
+    def start(self, job: Job):
+        if not self.batchable(job):
+            return super().start(job)
+        h = {"ctx": None, "left": job.sweeps, "batched": True, "event": None, "sweeps_queued": 0,
+             "joined": False}
+        h["setup"] = self.setup_pool.submit(self._setup, job, h)
         self.members.append(h)
         return h
 
     def tick(self):
-        """One more batch sweep over every unfinished job, unless
-        `max_inflight` are already queued.  (Topping the queue up on every
-        call was measured worse: jobs admitted meanwhile joined later, and the
-        standing chain lost the SMs to the always-busy batch stream.)"""
+        """One more batch sweep over every unfinished job that is set up,
+        unless `max_inflight` are already queued.  (Topping the queue up on
+        every call was measured worse: jobs admitted meanwhile joined later,
+        and the standing chain lost the SMs to the always-busy batch
+        stream.)"""
         while self.inflight and self.inflight[0].query():
             self.inflight.popleft()
         if len(self.inflight) >= self.max_inflight or not self.members:
+            time.sleep(0)                         # let the worker threads run
+            return
+        live = []
+        for h in self.members:
+            f = h["setup"]
+            if not f.done():
+                continue
+            f.result()                            # a failed set-up raises here
+            if not h["joined"]:
+                self.stream.wait_event(h["ready_event"])
+                h["joined"] = True
+            live.append(h)
+        if not live:
+            time.sleep(0)
             return
         torch = self.torch
-        live = self.members
-        self.stream.wait_stream(self.adm)
         self.P.psgld_batch_sweep([h["ctx"] for h in live], 1, self.stream.cuda_stream)
         ev = torch.cuda.Event()
         ev.record(self.stream)
@@ -336,7 +369,8 @@ class BatchedGpuExecutor(GpuExecutor):
             h["sweeps_queued"] += 1
             if h["left"] == 0:
                 h["event"] = ev
-        self.members = [h for h in live if h["left"] > 0]
+                h["teardown"] = self.teardown_pool.submit(self._teardown, h)
+        self.members = [h for h in self.members if h["left"] > 0]
         self.inflight.append(ev)
         self.ticks += 1
         self.batch_sizes.append(len(live))
@@ -344,17 +378,17 @@ class BatchedGpuExecutor(GpuExecutor):
     def done(self, h) -> bool:
         if not h.get("batched"):
             return super().done(h)
-        return h["left"] == 0 and h["event"].query()
+        return "teardown" in h and h["teardown"].done()
 
     def finish(self, job: Job, h) -> dict:
         if not h.get("batched"):
             return super().finish(job, h)
-        if h["left"] > 0:                    # released before its last sweep (close after an error)
-            self.members = [m for m in self.members if m is not h]
-            self.stream.synchronize()
-        else:
-            h["event"].synchronize()
-        Wm, Wv, Hm, Hv, n = h["ctx"].posterior_mean()
-        out = {"Wmean": Wm, "Hmean": Hm, "n_samples": n, "sweeps": h["sweeps_queued"]}
+        if "teardown" in h:
+            return h["teardown"].result()
+        # released before its last sweep (close after an error)
+        self.members = [m for m in self.members if m is not h]
+        h["setup"].result()
+        self.stream.synchronize()
+        out = {"sweeps": h["sweeps_queued"]}
         h["ctx"].close()
         return out

@@ -1042,8 +1042,9 @@ def run_serving(args, wl_name, wl):
                            "chain's entries x sweeps over the trace's wall time)",
                    "path": "continuous batching: every admitted job's part-steps in the batch's "
                            "shared tensor-core launches (psgld_batch_sweep, one sweep per tick, "
-                           "at most three ticks queued); the standing chain on its own stream; "
-                           "PyTorch caching allocator"},
+                           "at most three ticks queued; job set-up and teardown on worker "
+                           "threads); the standing chain on its own stream, its persistent kernel "
+                           "on 120 SMs; PyTorch caching allocator"},
         "latency": lat,
         "job_entries_per_s": r["job_entries"] / wall,
         "standing_chain": ({"sweeps": r["st_sweeps"], "entries_per_s": r["st_entries"] / wall}

@@ -83,10 +83,10 @@ WORKLOADS["batched_dense_nmf_256chains_513xJ200-5000_K32_B8_bf16"] = dict(
     batched=True, chains=256, I=513, J_lo=200, J_hi=5000, K=32, K_true=16, B=8, p_mix=(1.0, 2.0),
     phi=1.0, prior="exponential", lam=1.0, eps=1e-4, init_scale=0.5, job_sweeps=40,
     dense_path=2, p=1.0)
-# the same recipe with 64 chains: the size the batched kernel's full ncu
-# capture uses (340 MB of V, a few seconds of replay)
+# the same recipe with 64 chains on the single-pass kernel: the size of that
+# kernel's full ncu capture (340 MB of V, a few seconds of replay)
 WORKLOADS["batched_dense_nmf_64chains_513xJ200-5000_K32_B8_bf16"] = dict(
-    WORKLOADS["batched_dense_nmf_256chains_513xJ200-5000_K32_B8_bf16"], chains=64)
+    WORKLOADS["batched_dense_nmf_256chains_513xJ200-5000_K32_B8_bf16"], chains=64, dense_path=1)
 DEFAULT_WORKLOAD = "sparse_gauss_70000x10000_nnz10M_K50_B32"
 
 

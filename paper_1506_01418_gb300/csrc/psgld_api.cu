@@ -577,9 +577,9 @@ psgld_status psgld_part_step(psgld_ctx *c, int64_t t, void *stream)
     if (t < 1) return fail(c, PSGLD_ERR_ARG, "t must be >= 1");
     cudaStream_t st = (cudaStream_t)stream;
     s = launch_part_step(c, t, nullptr, 0, st);
+    mark_enqueued(c, st);                 // also after a failed launch: waits cover it
     if (s != PSGLD_OK) return s;
     c->t_done = t;
-    mark_enqueued(c, st);
     return PSGLD_OK;
 }
 
@@ -591,7 +591,10 @@ psgld_status psgld_sweep(psgld_ctx *c, int32_t n_sweeps, void *stream)
     if (n_sweeps < 0) return fail(c, PSGLD_ERR_ARG, "n_sweeps < 0");
     if (c->t_done % c->B != 0) return fail(c, PSGLD_ERR_STATE, "sweep must start at a sweep boundary");
     cudaStream_t st = (cudaStream_t)stream;
+    // until the closing mark_enqueued, waits fall back to the whole stream
+    // (covers work enqueued before an error return)
     c->last_stream = st;
+    c->last_ev_set = false;
     if (n_sweeps == 0) return PSGLD_OK;
     const bool graphs = c->opt.use_graphs && c->opt.part_mode == 0;
     if (graphs) {
@@ -827,7 +830,7 @@ psgld_status psgld_batch_sweep(psgld_ctx *const *ctxs, int32_t n, int32_t n_swee
         }
         if (q == 0) units[n] = un;
     }
-    for (int i = 0; i < n; ++i) set_state(i, (int64_t)n_sweeps * B);
+    for (int i = 0; i < n; ++i) set_state(i, 0);     // back to the state the call found
 
     // the device tables live in the leading context and are reused by its
     // next batch, ordered after the launches of this one by `bdone`
@@ -890,16 +893,20 @@ psgld_status psgld_batch_sweep(psgld_ctx *const *ctxs, int32_t n, int32_t n_swee
                                         reinterpret_cast<const int64_t *>(d + off_units), n, units[n], st);
         if (s == PSGLD_OK) s = launch_t_batch(c0, d + off_ap, n, 1, st);
     }
-    if (s == PSGLD_OK) {
-        for (int i = 0; i < n; ++i) {
-            psgld_ctx *c = ctxs[i];
+    for (int i = 0; i < n; ++i) {
+        psgld_ctx *c = ctxs[i];
+        if (s == PSGLD_OK) {
+            set_state(i, (int64_t)n_sweeps * B);
             for (int32_t sw = 0; sw < n_sweeps; ++sw) {
                 if (c->sweeps_done >= c->opt.burn_in_sweeps) c->n_samples += 1;
                 c->sweeps_done += 1;
             }
             c->t_done += (int64_t)B * n_sweeps;
-            mark_enqueued(c, st);
         }
+        // after a failed launch the factors are unspecified (set them again),
+        // but whatever was enqueued is still waited for before the context
+        // frees its memory
+        mark_enqueued(c, st);
     }
     e = cudaEventRecord(c0->bdone, st);
     if (s == PSGLD_OK && e != cudaSuccess) s = cuda_fail(c0, e, "cudaEventRecord");

@@ -854,7 +854,8 @@ def batched_other_kernel(wl, specs, dev, stream, flush, steps: int):
 
 
 def batched_precision(wl, specs, dev, sweeps: int):
-    """BF16 tensor-core batched sweeps (GEMM1 in BF16, and in E4M3 with
+    """BF16 tensor-core batched sweeps (as configured; the two-sided kernel
+    with V kept in BF16; the single-pass kernel with GEMM1 in E4M3 with
     per-tile scales) vs the FP32 gather path (each chain alone) on the same
     chains, data, initial factors and Philox keys: entries/s and the
     posterior-mean reconstruction RMSE (mean over the chains)."""
@@ -865,6 +866,7 @@ def batched_precision(wl, specs, dev, sweeps: int):
     N = sum(wl["I"] * J for J, _, _, _ in specs)
     stream = torch.cuda.current_stream(dev)
     for name, opts in (("bf16_tensor_core_batched", {}),
+                       ("bf16_tensor_core_bf16_v_batched", {"dense_path": 2, "dense_v_bf16": 1}),
                        ("e4m3_gemm1_batched", {"dense_fp8": 1, "dense_path": 3}),
                        ("fp32_gather", {"dense_path": 0})):
         made = batched_make(wl, specs, dev, burn_in_sweeps=sweeps // 2, **opts)
@@ -891,10 +893,12 @@ def batched_precision(wl, specs, dev, sweeps: int):
             ch.close()
         torch.cuda.empty_cache()
     r16 = out["bf16_tensor_core_batched"].pop("rmse")
+    r16v = out["bf16_tensor_core_bf16_v_batched"].pop("rmse")
     r8 = out["e4m3_gemm1_batched"].pop("rmse")
     r32 = out["fp32_gather"].pop("rmse")
     out["rmse_rel_diff_max"] = max(abs(x - y) / y for x, y in zip(r16, r32))
     out["e4m3_rmse_rel_diff_max"] = max(abs(x - y) / y for x, y in zip(r8, r32))
+    out["bf16_v_rmse_rel_diff_max"] = max(abs(x - y) / y for x, y in zip(r16v, r32))
     out["speedup"] = out["bf16_tensor_core_batched"]["value"] / out["fp32_gather"]["value"]
     return out
 

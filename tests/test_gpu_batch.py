@@ -150,3 +150,15 @@ def test_batch_refusals():
     assert good.iterations_done == 0
     for ch in (good, other, two, b3):
         ch.close()
+
+
+def test_batched_sweeps_are_profiled_on_the_first_context():
+    """profile = 1 on the first context: events around every part's
+    launches, read with psgld_profile_read_split."""
+    chains = [_chain(i, *m, use_graphs=0) for i, m in enumerate(MIX[:4])]
+    chains[0].set_options(profile=1)
+    P.psgld_batch_sweep(chains, 1)
+    g, u, n = chains[0].profile_read_split()
+    assert n == B and g > 0 and u > 0
+    for ch in chains:
+        ch.close()

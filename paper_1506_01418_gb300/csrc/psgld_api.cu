@@ -753,7 +753,8 @@ psgld_status psgld_batch_sweep(psgld_ctx *const *ctxs, int32_t n, int32_t n_swee
     if (n_sweeps == 0) return PSGLD_OK;
     cudaStream_t st = (cudaStream_t)stream;
 
-    // dense launches: contexts grouped by K class, in first-seen order
+    // gradient launches: contexts grouped by batch key (kernel variant), in
+    // first-seen order
     std::vector<int> keys, order;                 // order: context indices, group by group
     std::vector<int> gbeg;                        // group g: order[gbeg[g] .. gbeg[g + 1])
     for (int i = 0; i < n; ++i) {

@@ -35,7 +35,7 @@ import numpy as np
 import pytest
 
 import oracle
-from gpu_helpers import U_BF16, U_FP32, Pair, recovered_drift
+from gpu_helpers import Pair, dense_drift_bound, recovered_drift
 from paper_1506_01418_gb300 import datagen
 from paper_1506_01418_gb300 import psgld as P
 
@@ -44,8 +44,6 @@ torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():
     pytest.skip("no CUDA device", allow_module_level=True)
 
-U_E4M3 = 2.0 ** -4          # 3 mantissa bits
-ETA_E4M3 = 2.0 ** -10       # half the subnormal spacing, in units of the tile scale
 
 DENSE = {
     # name: (I, J, K, B, p, phi, prior_kind, data, eps)
@@ -103,65 +101,6 @@ def _make(name, seed=7, kernel="auto", **opts):
     return pr, V
 
 
-def _tile_scales(X, axis):
-    """Largest |x| / 448 of each 128-wide tile of X along `axis` (rows of a
-    W block: axis 0; columns of an H block: axis 1), broadcast back."""
-    n = X.shape[axis]
-    out = np.zeros(n)
-    for a in range(0, n, 128):
-        sl = X[a:a + 128] if axis == 0 else X[:, a:a + 128]
-        m = np.abs(sl).max() if sl.size else 0.0
-        out[a:a + 128] = m / 448.0 if m > 0 else 1.0
-    return out
-
-
-def _drift_bound(V, W, H, t, B, p, phi, S, mu_min=1e-10, v_bf16=False, fp8=False):
-    """First-order BF16 bound on |drift_gpu - drift| for part t (see module
-    docstring); W I x K, H K x J, FP64.  With v_bf16 the data are rounded to
-    BF16 too: e moves by at most |de/dv| u |v| = max(mu, mu_min)^-p u |v| / phi.
-    With fp8, GEMM1's operands are E4M3 with one scale s per 128-row W tile
-    and per 128-column H tile: |q(x) - x| <= u8 |x| + eta s (u8 = 2^-4, eta
-    = 2^-10 from the subnormals), so mu moves by at most (2 u8 + u8^2) A +
-    (1 + u8)(eta s_H sum_k |w| + eta s_W sum_k |h|) + K eta^2 s_W s_H, plus
-    the FP32 rounding of the scales."""
-    I, J = V.shape
-    s = (t - 1) % B
-    bW = np.zeros_like(W)
-    bH = np.zeros_like(H)
-    for r in range(B):
-        c = (r + s) % B
-        r0, r1 = oracle.piece_start(r, I, B), oracle.piece_start(r + 1, I, B)
-        c0, c1 = oracle.piece_start(c, J, B), oracle.piece_start(c + 1, J, B)
-        w, h, v = W[r0:r1], H[:, c0:c1], V[r0:r1, c0:c1].astype(np.float64)
-        mu = w @ h
-        A = np.abs(w) @ np.abs(h)
-        if fp8:
-            eW = ETA_E4M3 * _tile_scales(w, 0)[:, None]
-            eH = ETA_E4M3 * _tile_scales(h, 1)[None, :]
-            Kw = w.shape[1]
-            dmu = ((2 * U_E4M3 + U_E4M3 ** 2) * A * 1.01
-                   + (1 + U_E4M3) * (eH * np.abs(w).sum(1)[:, None] + eW * np.abs(h).sum(0)[None, :])
-                   + Kw * eW * eH + (4 * Kw + 16) * U_FP32 * A * (1 + 2 * U_E4M3))
-        else:
-            dmu = 2 * U_BF16 * A * 1.01 + 4 * w.shape[1] * U_FP32 * A
-        if p > 0:
-            mc = np.maximum(mu, mu_min)
-            lo = np.maximum(mu - dmu, mu_min)
-            e = (v - mu) * mc ** -p / phi
-            fprime = lo ** -p * (1 + p * (np.abs(v - mu) + dmu) / lo) / phi
-        else:
-            e = (v - mu) / phi
-            fprime = np.full_like(mu, 1.0 / phi)
-        de = fprime * dmu + 64 * U_FP32 * np.abs(e)
-        if v_bf16:
-            de = de + (np.maximum(mu - dmu, mu_min) ** -p if p > 0 else 1.0) * U_BF16 * np.abs(v) / phi
-        ebf = de + U_BF16 * (np.abs(e) + de)            # error of the BF16 e
-        nc, nr = c1 - c0, r1 - r0
-        bW[r0:r1] = (ebf @ np.abs(h).T) * (1 + U_BF16) + (U_BF16 + nc * U_FP32) * (np.abs(e) @ np.abs(h).T)
-        bH[:, c0:c1] = (np.abs(w).T @ ebf) * (1 + U_BF16) + (U_BF16 + nr * U_FP32) * (np.abs(w).T @ np.abs(e))
-    return S * bW, S * bH
-
-
 @pytest.mark.parametrize("name,kernel", _cases())
 def test_dense_part_step_drift_within_bf16_bound(name, kernel):
     pr, V = _make(name, kernel=kernel)
@@ -173,7 +112,7 @@ def test_dense_part_step_drift_within_bf16_bound(name, kernel):
         W0, H0 = pr.orc.get_factors()
         D_W, D_H = pr.orc.drift(t)
         S = pr.orc.scale(t)
-        bW, bH = _drift_bound(V, W0, H0, t, B, p, phi, S, v_bf16=v_bf16, fp8=fp8)
+        bW, bH = dense_drift_bound(V, W0, H0, t, B, p, phi, S, v_bf16=v_bf16, fp8=fp8)
         pr.gpu.part_step(t)
         Wg, Hg = pr.gpu_factors()
         zW = oracle.noise_matrix(7, t, 0, I, K)

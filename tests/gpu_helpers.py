@@ -121,7 +121,7 @@ def tile_scales(X, axis):
     return out
 
 
-def dense_drift_bound(V, W, H, t, B, p, phi, S, mu_min=1e-10, v_bf16=False, fp8=False):
+def dense_drift_bound(V, W, H, t, B, p, phi, S, mu_min=1e-10, v_bf16=False, fp8=False, part=None):
     """First-order BF16 bound on |drift_gpu - drift| for part t (see module
     docstring); W I x K, H K x J, FP64.  With v_bf16 the data are rounded to
     BF16 too: e moves by at most |de/dv| u |v| = max(mu, mu_min)^-p u |v| / phi.
@@ -131,7 +131,7 @@ def dense_drift_bound(V, W, H, t, B, p, phi, S, mu_min=1e-10, v_bf16=False, fp8=
     (1 + u8)(eta s_H sum_k |w| + eta s_W sum_k |h|) + K eta^2 s_W s_H, plus
     the FP32 rounding of the scales."""
     I, J = V.shape
-    s = (t - 1) % B
+    s = (t - 1) % B if part is None else part       # part: the drawn part (size-proportional)
     bW = np.zeros_like(W)
     bH = np.zeros_like(H)
     for r in range(B):

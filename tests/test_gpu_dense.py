@@ -166,6 +166,36 @@ def test_dense_is_deterministic(kernel):
     assert np.array_equal(Wa, Wb) and np.array_equal(Ha, Hb)
 
 
+@pytest.mark.parametrize("kernel", ["single_pass", "two_sided_bf16v"])
+def test_dense_size_proportional_parts_drift_within_bound(kernel):
+    """part_mode = 1 (condition C2) on the tensor-core path: every iteration
+    uses the part the oracle draws, and the drift stays within the BF16
+    bound of that part."""
+    name = "gamma_K13"
+    pr, V = _make(name, kernel=kernel, part_mode=1)
+    pr.orc.set_part_mode(1)
+    I, J, K, B, p, phi, kind, data, eps = DENSE[name]
+    v_bf16 = bool(KERNELS[kernel].get("dense_v_bf16", 0))
+    seen = set()
+    for t in range(1, 3 * B + 1):
+        s = pr.orc.part_index(t)
+        seen.add(s)
+        W0, H0 = pr.orc.get_factors()
+        D_W, D_H = pr.orc.drift(t)
+        S = pr.orc.scale(t)
+        bW, bH = dense_drift_bound(V, W0, H0, t, B, p, phi, S, v_bf16=v_bf16, part=s)
+        pr.gpu.part_step(t)
+        Wg, Hg = pr.gpu_factors()
+        zW = oracle.noise_matrix(7, t, 0, I, K)
+        zH = oracle.noise_matrix(7, t, 1, J, K).T
+        for xg, x0, z, D, bnd, what in ((Wg, W0, zW, D_W, bW, "W"), (Hg, H0, zH, D_H, bH, "H")):
+            Dg, mask, rec = recovered_drift(xg.astype(np.float64), x0, z, D, eps, True)
+            bad = mask & (np.abs(Dg - D) > bnd + rec)
+            assert not bad.any(), (kernel, t, s, what, int(bad.sum()))
+        pr.sync_oracle_to_gpu()
+    assert len(seen) > 1
+
+
 def test_two_sided_kernel_on_fewer_sms_gives_the_same_chain():
     """max_sms only shrinks the persistent grid: every item still runs once,
     so the chain is the same bit for bit."""

@@ -45,7 +45,7 @@ MIX = [
 B = 4
 
 
-def _chain(idx, I, J, K, p, kind, eps_mode, kopts, use_graphs, burn_in=1):
+def _chain(idx, I, J, K, p, kind, eps_mode, kopts, use_graphs, burn_in=1, B=B):
     dev = torch.device("cuda", 0)
     if p == 1.0:
         V, _, _ = datagen.dense_poisson(I, J, 3, idx)
@@ -161,4 +161,22 @@ def test_batched_sweeps_are_profiled_on_the_first_context():
     g, u, n = chains[0].profile_read_split()
     assert n == B and g > 0 and u > 0
     for ch in chains:
+        ch.close()
+
+
+def test_odd_b_alternates_the_buffers_between_sweeps():
+    """With B odd the ping-pong buffers a sweep starts from alternate, so the
+    call keeps two sets of tables; three sweeps (and a frozen H, whose
+    buffer never flips) against the same chains swept alone."""
+    mix = [MIX[0], MIX[9], MIX[12]]
+    batch = [_chain(i, *m, use_graphs=0, B=3) for i, m in enumerate(mix)]
+    alone = [_chain(i, *m, use_graphs=1, B=3) for i, m in enumerate(mix)]
+    for ch in (batch[1], alone[1]):
+        ch.set_options(freeze_H=1)
+    P.psgld_batch_sweep(batch, 3)
+    for ch in alone:
+        ch.sweep(3)
+    for a, b in zip(batch, alone):
+        _assert_same(a, b)
+    for ch in batch + alone:
         ch.close()

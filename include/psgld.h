@@ -127,7 +127,8 @@ typedef struct {
                                * one CTA per SM) runs on at most this many SMs, so
                                * that kernels of other streams find SMs free while
                                * it runs (a long-running chain beside short jobs);
-                               * 0: every SM */
+                               * 0: every SM.  psgld_batch_sweep's shared launches
+                               * use every SM regardless. */
 } psgld_options;
 
 /* Device memory.  By default the library allocates with cudaMalloc and frees

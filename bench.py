@@ -622,18 +622,22 @@ def e2e_job(wl, seed, dev, i, j, v, W0, H0):
     chain.sweep(S)
     from paper_1506_01418_gb300 import psgld as P
     P.psgld_posterior_mean(chain.ctx, Wm, Wv, Hm, Hv)
-    ll = chain.log_lik()
+    # the log-likelihood over a dense V is an FP64 product W H over every
+    # entry (1.6 s at 32768^2 on this GPU's FP64 rate): the dense jobs read
+    # back their posterior means only
+    ll = chain.log_lik() if not dense_in else None
     torch.cuda.synchronize(dev)
     dt = time.perf_counter() - t0
     chain.close()
     N = int(v.numel())
     h2d = (4 if dense_in else 12) * N + 4 * (I + J) * K
-    d2h = 8 * 4 * (I + J) * K + 8
+    d2h = 8 * 4 * (I + J) * K + (0 if dense_in else 8)
     return {"value": N * S / dt, "unit": UNIT, "h2d_bytes_per_step": h2d / S,
             "d2h_bytes_per_step": d2h / S, "job_sweeps": S, "job_s": dt,
             "log_lik": ll,
             "api": ("psgld_set_data_dense" if dense_in else "psgld_set_data_coo") +
-                   "/set_factors (pinned host) + psgld_sweep + psgld_posterior_mean + psgld_log_lik"}
+                   "/set_factors (pinned host) + psgld_sweep + psgld_posterior_mean" +
+                   ("" if dense_in else " + psgld_log_lik")}
 
 
 # ---------------------------------------------------------------------------

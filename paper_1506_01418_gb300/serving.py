@@ -283,9 +283,10 @@ class BatchedGpuExecutor(GpuExecutor):
     worker threads, so the loop that enqueues the batch sweeps does not wait
     for them.  Standing chains run on their own streams as in GpuExecutor."""
 
-    def __init__(self, device=None, max_inflight: int = 3):
+    def __init__(self, device=None, max_inflight: int = 3, sweeps_per_tick: int = 1):
         import concurrent.futures as cf
         super().__init__(device)
+        self.sweeps_per_tick = int(sweeps_per_tick)
         torch = self.torch
         self.stream = torch.cuda.Stream(self.dev, priority=-1)   # the batch's sweeps
         self.adm = torch.cuda.Stream(self.dev, priority=-1)      # admitted jobs' data and set-up
@@ -361,18 +362,20 @@ class BatchedGpuExecutor(GpuExecutor):
             time.sleep(0)
             return
         torch = self.torch
-        self.P.psgld_batch_sweep([h["ctx"] for h in live], 1, self.stream.cuda_stream)
+        # up to sweeps_per_tick sweeps in one call, never past a member's last
+        k = max(1, min([self.sweeps_per_tick] + [h["left"] for h in live]))
+        self.P.psgld_batch_sweep([h["ctx"] for h in live], k, self.stream.cuda_stream)
         ev = torch.cuda.Event()
         ev.record(self.stream)
         for h in live:
-            h["left"] -= 1
-            h["sweeps_queued"] += 1
+            h["left"] -= k
+            h["sweeps_queued"] += k
             if h["left"] == 0:
                 h["event"] = ev
                 h["teardown"] = self.teardown_pool.submit(self._teardown, h)
         self.members = [h for h in self.members if h["left"] > 0]
         self.inflight.append(ev)
-        self.ticks += 1
+        self.ticks += k
         self.batch_sizes.append(len(live))
 
     def done(self, h) -> bool:

@@ -1070,6 +1070,7 @@ def run_serving(args, wl_name, wl):
                 "note": "the serving loop is the end-to-end path: each job's initial factors go "
                         "host to device and its posterior means device to host inside the trace"},
     }
+    bex.shutdown()
     del bex
     torch.cuda.empty_cache()
     if not args.no_serving_compare:

@@ -148,13 +148,19 @@ class Server:
         return clock() - t0
 
     def close(self):
-        """Release every active job (after an error, or at the end)."""
+        """Release every active job (after an error, or at the end); the
+        first error raised while releasing is raised after all are done."""
+        first = None
         for jid in list(self.active):
             job, h, nbytes = self.active.pop(jid)
             try:
                 self.ex.finish(job, h)
+            except Exception as e:          # keep releasing the others
+                first = first or e
             finally:
                 self.used -= nbytes
+        if first is not None:
+            raise first
 
     def stop_standing(self):
         """Finish standing chains (after a trace); returns their results."""
@@ -383,6 +389,11 @@ class BatchedGpuExecutor(GpuExecutor):
             return super().done(h)
         return "teardown" in h and h["teardown"].done()
 
+    def shutdown(self):
+        """Stop the worker threads (after the server has released its jobs)."""
+        self.setup_pool.shutdown(wait=True)
+        self.teardown_pool.shutdown(wait=True)
+
     def finish(self, job: Job, h) -> dict:
         if not h.get("batched"):
             return super().finish(job, h)
@@ -390,7 +401,7 @@ class BatchedGpuExecutor(GpuExecutor):
             return h["teardown"].result()
         # released before its last sweep (close after an error)
         self.members = [m for m in self.members if m is not h]
-        h["setup"].result()
+        h["setup"].result()                  # a failed set-up raises here (nothing to close)
         self.stream.synchronize()
         out = {"sweeps": h["sweeps_queued"]}
         h["ctx"].close()

@@ -157,3 +157,21 @@ def test_continuous_batching_joins_jobs_at_the_next_sweep():
         assert sum(j.job_id in tl for tl in ex.tick_log) == j.sweeps
     assert srv.used == 0
     assert max(len(tl) for tl in ex.tick_log) == 3
+
+
+def test_close_releases_every_job_and_raises_the_first_error():
+    class Failing(FakeExecutor):
+        def finish(self, job, h):
+            if job.job_id == 0:
+                raise RuntimeError("boom")
+            return {"ok": job.job_id}
+
+    ex = Failing(ticks=100)
+    srv = serving.Server(ex, hbm_budget=10 * 100 * 100 * 100)
+    for k in range(3):
+        srv.submit(_job(k, 100, 100, 0.0))
+    srv.poll(0.0)
+    assert len(srv.active) == 3
+    with pytest.raises(RuntimeError):
+        srv.close()
+    assert not srv.active and srv.used == 0

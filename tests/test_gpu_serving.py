@@ -38,6 +38,8 @@ def _serve(jobs, budget, executor=serving.GpuExecutor):
         srv.run(jobs, idle_sleep=0)
     finally:
         srv.close()
+        if hasattr(ex, "shutdown"):
+            ex.shutdown()
     assert srv.used == 0 and not srv.active
     return {j.job_id: j.result for j in jobs}
 

@@ -1186,10 +1186,14 @@ def main():
                               "oracle counterpart (the oracle is a CPU chain, not a server)"}))
             return
         run_reference(args, args.workload, wl)
-    elif wl.get("serving"):
-        run_serving(args, args.workload, wl)
-    elif wl.get("batched"):
-        run_batched(args, args.workload, wl)
+    elif wl.get("serving") or wl.get("batched"):
+        # one GPU's loop / batch; under torchrun only rank 0 runs it
+        if dist_env()[0] != 0:
+            return
+        if wl.get("serving"):
+            run_serving(args, args.workload, wl)
+        else:
+            run_batched(args, args.workload, wl)
     else:
         run_ours(args, args.workload, wl)
 

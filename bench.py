@@ -1011,6 +1011,83 @@ def serve_trace(wl, executor, dev, uuid):
             "ticks": getattr(executor, "ticks", 0) - ticks0}
 
 
+def serve_trace_native(wl, dev, uuid):
+    """The same trace through the library's native serving loop
+    (psgld_server_*): the Python thread only replays arrivals (generating
+    each job's data on the GPU and submitting it) and keeps the standing
+    chain's sweep queued; admission, batching and read-back run in the
+    library's worker thread.  Latency = arrival to read-back."""
+    import numpy as np
+    import torch
+
+    from paper_1506_01418_gb300 import psgld as P
+    from paper_1506_01418_gb300 import serving
+    factory = serving.mixed_job_factory(wl["sweeps"], wl["burn_in"], wl["B"], wl["eps"])
+    ex = serving.GpuExecutor(dev.index)          # data generation and the standing chain
+    srv = P.NativeServer(wl["budget_bytes"])
+
+    def submit(job):
+        V, W0, Ht0 = ex._data(job)
+        torch.cuda.synchronize(dev)
+        return srv.submit(job.I, job.J, job.K, job.B, job.p, job.phi, V, W0, Ht0, job.sweeps,
+                          lambda_w=job.lam, lambda_h=job.lam, seed=job.seed, eps=job.eps,
+                          burn_in_sweeps=job.burn_in, dense_path=job.dense_path)
+
+    # warm-up: one job of each size class
+    for k, (I, K, p) in enumerate([(I, K, p) for I in (257, 513, 1025) for K in (16, 64) for p in (1.0, 1.5)]):
+        j = factory(10_000 + k, 0.0, np.random.Generator(np.random.Philox(k)))
+        j.I, j.K, j.p, j.J = I, K, p, 800
+        submit(j)
+    srv.wait_idle(600.0)
+    srv.poll()
+    jobs = serving.poisson_trace(wl["rate"], wl["duration"], seed=2024, job_factory=factory)
+    standing, hst, st0 = None, None, 0
+    if wl.get("standing"):
+        sw = WORKLOADS[wl["standing"]]
+        standing = serving.Job(job_id=-1, I=sw["I"], J=sw["J"], K=sw["K"], B=sw["B"], p=sw["p"],
+                               sweeps=None, burn_in=0, seed=7, eps=sw["eps"], init_scale=sw["init_scale"],
+                               dense_path=sw["dense_path"], dense_v_bf16=sw["dense_v_bf16"],
+                               max_sms=wl.get("standing_sms", 0))
+        hst = ex.start(standing)
+        torch.cuda.synchronize(dev)
+        st0 = hst["sweeps_queued"]
+    sampler = ClockSampler(uuid)
+    pending = list(jobs)
+    by_id = {}
+    n_done = 0
+    w0 = time.time()
+    t0 = time.perf_counter()
+    while n_done < len(jobs):
+        now = time.perf_counter() - t0
+        while pending and pending[0].arrival <= now:
+            job = pending.pop(0)
+            job.admitted = time.perf_counter() - t0           # submitted
+            by_id[submit(job)] = job
+        if hst is not None:
+            ex.step_standing(standing, hst)
+        for jid, lat in srv.poll():
+            job = by_id.pop(jid)
+            job.finished = job.admitted + lat
+            n_done += 1
+        if now > 600.0:
+            raise TimeoutError("native serving trace did not finish")
+        time.sleep(0)
+    wall = time.perf_counter() - t0
+    st_sweeps = (hst["sweeps_queued"] - st0) if hst is not None else 0
+    w1 = time.time()
+    if hst is not None:
+        ex.finish(standing, hst)
+    stats = srv.stats()
+    srv.close()
+    torch.cuda.synchronize(dev)
+    time.sleep(0.25)
+    sampler.stop()
+    job_entries = sum(j.I * j.J * j.sweeps for j in jobs)
+    st_entries = standing.I * standing.J * st_sweeps if standing is not None else 0
+    return {"jobs": jobs, "wall": wall, "job_entries": job_entries, "st_entries": st_entries,
+            "st_sweeps": st_sweeps, "stats": stats, "clocks": sampler.summary(w0, w1)}
+
+
 def run_serving(args, wl_name, wl):
     """The serving loop on one GPU: a Poisson trace of jobs replayed in real
     time with continuous batching (every admitted job's part-steps share the

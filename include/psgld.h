@@ -334,6 +334,67 @@ PSGLD_API const char *psgld_last_error(const psgld_ctx *ctx);
 
 PSGLD_API void psgld_destroy(psgld_ctx *ctx);
 
+/* ---- Native serving loop --------------------------------------------------
+ * Continuous batching of dense factorisation jobs on one GPU, run by a
+ * worker thread inside the library: submitted jobs wait in arrival order
+ * until the device memory their context will hold (psgld_estimate_device_bytes)
+ * fits in what the budget has left, are then set up (context, data and factor
+ * copies with their input checks, on the server's admission stream) and join
+ * the batch; the worker keeps up to `max_inflight` psgld_batch_sweep calls of
+ * one sweep each queued on its batch stream, each over every admitted job
+ * with sweeps left, so jobs arriving meanwhile join at the next sweep; a job
+ * whose last sweep has run has its posterior means read back and its context
+ * released.  Contexts allocate from a CUDA stream-ordered memory pool, so
+ * releasing one does not wait for the whole device.  A job's chain depends
+ * only on its own inputs and seed: its result is the same alone and in any
+ * mix.  Not the paper's (its experiments run one chain at a time); this is
+ * the serving form of Algorithm 1 for many concurrent chains. */
+typedef struct psgld_server psgld_server;
+
+typedef struct {
+    int64_t I, J;
+    int32_t K, B;
+    double tweedie_p, phi;
+    psgld_prior prior;
+    psgld_options options;    /* seed, step size, burn_in_sweeps, dense_path
+                               * (1, 2 or 3), dense_v_bf16, ... as for a context */
+    int32_t sweeps;           /* sweeps to run, > 0 */
+    const float *V_dev;       /* I x J, row stride ldv >= J, FP32, device memory */
+    int64_t ldv;
+    const float *W0_dev;      /* I x K initial W, device memory */
+    const float *Ht0_dev;     /* J x K initial H^T, device memory */
+    double *Wmean_host;       /* I x K posterior mean of W (or NULL) */
+    double *Hmean_host;       /* J x K posterior mean of H^T (or NULL) */
+} psgld_job;
+/* The caller keeps V, W0, Ht0 and the output buffers valid and unchanged
+ * until the job is reported done by psgld_server_poll. */
+
+/* hbm_budget: bytes the admitted jobs' contexts may hold together; a job
+ * whose own estimate exceeds it is refused at submission (PSGLD_ERR_SIZE).
+ * max_inflight >= 1: batch sweeps queued at a time. */
+PSGLD_API psgld_status psgld_server_create(size_t hbm_budget, int32_t max_inflight,
+                                           psgld_server **srv_out);
+/* Queues a job (copied; the pointers it holds are not) and returns its id.
+ * Thread-safe with respect to polling. */
+PSGLD_API psgld_status psgld_server_submit(psgld_server *srv, const psgld_job *job,
+                                           int64_t *id_out);
+/* Up to `max` jobs finished since the last poll: their ids and their latency
+ * (seconds from submission to the read-back of their results; negative if
+ * the job failed, with psgld_server_last_error naming why).  Returns the
+ * number written. */
+PSGLD_API int32_t psgld_server_poll(psgld_server *srv, int64_t *ids_host, double *latency_s_host,
+                                    int32_t max);
+/* Waits until every submitted job has finished (PSGLD_ERR_TIMEOUT after
+ * timeout_s seconds). */
+PSGLD_API psgld_status psgld_server_wait_idle(psgld_server *srv, double timeout_s);
+/* Batch sweeps issued, mean jobs per batch sweep, peak bytes held. */
+PSGLD_API psgld_status psgld_server_stats(psgld_server *srv, int64_t *sweeps_out,
+                                          double *jobs_per_sweep_out, size_t *peak_bytes_out);
+/* Message of the latest failed job ("" if none); valid until the next call. */
+PSGLD_API const char *psgld_server_last_error(psgld_server *srv);
+/* Finishes every submitted job, stops the worker and frees the server. */
+PSGLD_API void psgld_server_destroy(psgld_server *srv);
+
 #ifdef __cplusplus
 }
 #endif

@@ -271,6 +271,16 @@ void psgld_default_options(psgld_options *o)
 psgld_status psgld_create(int64_t I, int64_t J, int32_t K, int32_t B, double tweedie_p, double phi,
                           const psgld_prior *prior, psgld_ctx **out)
 {
+    return create_context(I, J, K, B, tweedie_p, phi, prior, nullptr, out);
+}
+
+}  // extern "C"
+
+namespace psgld {
+
+psgld_status create_context(int64_t I, int64_t J, int32_t K, int32_t B, double tweedie_p, double phi,
+                            const psgld_prior *prior, const psgld_allocator *allocator, psgld_ctx **out)
+{
     if (!out) return PSGLD_ERR_ARG;
     *out = nullptr;
     if (!prior) return PSGLD_ERR_ARG;
@@ -289,7 +299,10 @@ psgld_status psgld_create(int64_t I, int64_t J, int32_t K, int32_t B, double twe
     }
     psgld_ctx *c = new (std::nothrow) psgld_ctx();
     if (!c) return PSGLD_ERR_OOM;
-    {
+    if (allocator) {
+        c->allocator = *allocator;
+        c->has_allocator = true;
+    } else {
         std::lock_guard<std::mutex> lock(g_alloc_mutex);
         c->allocator = g_allocator;
         c->has_allocator = g_has_allocator;
@@ -335,6 +348,10 @@ psgld_status psgld_create(int64_t I, int64_t J, int32_t K, int32_t B, double twe
     *out = c;
     return PSGLD_OK;
 }
+
+}  // namespace psgld
+
+extern "C" {
 
 static void destroy_events(psgld_ctx *c)
 {

@@ -53,6 +53,14 @@ class psgld_options(C.Structure):
                 ("dense_fp8", C.c_int32), ("gather_bf16", C.c_int32), ("max_sms", C.c_int32)]
 
 
+class psgld_job(C.Structure):
+    _fields_ = [("I", C.c_int64), ("J", C.c_int64), ("K", C.c_int32), ("B", C.c_int32),
+                ("tweedie_p", C.c_double), ("phi", C.c_double), ("prior", psgld_prior),
+                ("options", psgld_options), ("sweeps", C.c_int32), ("V_dev", C.c_void_p),
+                ("ldv", C.c_int64), ("W0_dev", C.c_void_p), ("Ht0_dev", C.c_void_p),
+                ("Wmean_host", C.c_void_p), ("Hmean_host", C.c_void_p)]
+
+
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
 
@@ -70,6 +78,8 @@ EXPORTS = [
     "psgld_batch_sweep",
     "psgld_log_lik_static", "psgld_last_error",
     "psgld_destroy",
+    "psgld_server_create", "psgld_server_submit", "psgld_server_poll", "psgld_server_wait_idle",
+    "psgld_server_stats", "psgld_server_last_error", "psgld_server_destroy",
 ]
 
 
@@ -113,6 +123,13 @@ def load(build_if_missing: bool = True):
         "psgld_log_lik_static": (st, [i64, vp, vp, vp, vp, vp, i64, i64, i32, f64, f64, f64, vp, vp]),
         "psgld_last_error": (C.c_char_p, [vp]),
         "psgld_destroy": (None, [vp]),
+        "psgld_server_create": (st, [C.c_size_t, i32, C.POINTER(vp)]),
+        "psgld_server_submit": (st, [vp, C.POINTER(psgld_job), C.POINTER(i64)]),
+        "psgld_server_poll": (i32, [vp, vp, vp, i32]),
+        "psgld_server_wait_idle": (st, [vp, f64]),
+        "psgld_server_stats": (st, [vp, C.POINTER(i64), C.POINTER(f64), C.POINTER(C.c_size_t)]),
+        "psgld_server_last_error": (C.c_char_p, [vp]),
+        "psgld_server_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -459,3 +476,83 @@ class PSGLD:
     @property
     def iterations_done(self):
         return psgld_iterations_done(self.ctx)
+
+
+class NativeServer:
+    """The library's serving loop (psgld_server_*): submit dense jobs with
+    device inputs; a worker thread in the library admits them by memory,
+    batches their sweeps and writes their posterior means to host arrays."""
+
+    def __init__(self, hbm_budget: int, max_inflight: int = 3):
+        h = C.c_void_p()
+        st = load().psgld_server_create(int(hbm_budget), int(max_inflight), C.byref(h))
+        if st != PSGLD_OK:
+            raise PsgldError(st, "psgld_server_create")
+        self.h = h
+        self._keep = {}          # job id -> the arrays the library reads or writes
+        self._done = {}          # job id -> (W mean, H^T mean, latency s)
+
+    def submit(self, I, J, K, B, tweedie_p, phi, V, W0, Ht0, sweeps, prior_kind=PSGLD_PRIOR_EXPONENTIAL,
+               lambda_w=1.0, lambda_h=1.0, sigma_w=1.0, sigma_h=1.0, **options):
+        """V (I x J), W0 (I x K), Ht0 (J x K): contiguous FP32 CUDA tensors,
+        ready (their stream synchronised).  Returns the job id; results()
+        gives the posterior means once the job is reported done."""
+        opts = psgld_default_options()
+        for k, v in options.items():
+            setattr(opts, k, v)
+        Wm = np.zeros((I, K))
+        Hm = np.zeros((J, K))
+        job = psgld_job(I=I, J=J, K=K, B=B, tweedie_p=float(tweedie_p), phi=float(phi),
+                        prior=psgld_prior(int(prior_kind), float(lambda_w), float(lambda_h),
+                                          float(sigma_w), float(sigma_h)),
+                        options=opts, sweeps=int(sweeps), V_dev=V.data_ptr(), ldv=V.stride(0),
+                        W0_dev=W0.data_ptr(), Ht0_dev=Ht0.data_ptr(),
+                        Wmean_host=Wm.ctypes.data, Hmean_host=Hm.ctypes.data)
+        jid = C.c_int64()
+        st = load().psgld_server_submit(self.h, C.byref(job), C.byref(jid))
+        if st != PSGLD_OK:
+            raise PsgldError(st, "psgld_server_submit")
+        self._keep[jid.value] = (V, W0, Ht0, Wm, Hm)
+        return jid.value
+
+    def poll(self, max_n: int = 1024):
+        """[(job id, latency s)] of jobs finished since the last poll; their
+        inputs are released and their results kept for results()."""
+        ids = np.zeros(max_n, np.int64)
+        lat = np.zeros(max_n, np.float64)
+        n = load().psgld_server_poll(self.h, ids.ctypes.data, lat.ctypes.data, max_n)
+        out = []
+        for k in range(n):
+            jid = int(ids[k])
+            V, W0, Ht0, Wm, Hm = self._keep.pop(jid)
+            self._done[jid] = (Wm, Hm, float(lat[k]))
+            out.append((jid, float(lat[k])))
+        return out
+
+    def results(self, jid):
+        """(W posterior mean, H^T posterior mean, latency s) of a finished job."""
+        return self._done.pop(jid)
+
+    def wait_idle(self, timeout_s: float = 600.0):
+        st = load().psgld_server_wait_idle(self.h, float(timeout_s))
+        if st != PSGLD_OK:
+            raise PsgldError(st, "psgld_server_wait_idle")
+
+    def stats(self):
+        n, jps, peak = C.c_int64(), C.c_double(), C.c_size_t()
+        load().psgld_server_stats(self.h, C.byref(n), C.byref(jps), C.byref(peak))
+        return {"sweeps": n.value, "jobs_per_sweep": jps.value, "peak_bytes": peak.value}
+
+    def last_error(self) -> str:
+        return load().psgld_server_last_error(self.h).decode()
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().psgld_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1028,7 +1028,7 @@ def serve_trace_native(wl, dev, uuid):
 
     def submit(job):
         V, W0, Ht0 = ex._data(job)
-        torch.cuda.synchronize(dev)
+        torch.cuda.current_stream(dev).synchronize()     # the job's inputs, not the device
         return srv.submit(job.I, job.J, job.K, job.B, job.p, job.phi, V, W0, Ht0, job.sweeps,
                           lambda_w=job.lam, lambda_h=job.lam, seed=job.seed, eps=job.eps,
                           burn_in_sweeps=job.burn_in, dense_path=job.dense_path)

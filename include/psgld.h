@@ -335,20 +335,21 @@ PSGLD_API const char *psgld_last_error(const psgld_ctx *ctx);
 PSGLD_API void psgld_destroy(psgld_ctx *ctx);
 
 /* ---- Native serving loop --------------------------------------------------
- * Continuous batching of dense factorisation jobs on one GPU, run by a
- * worker thread inside the library: submitted jobs wait in arrival order
+ * Continuous batching of dense factorisation jobs on one GPU, run by two
+ * worker threads inside the library.  Submitted jobs wait in arrival order
  * until the device memory their context will hold (psgld_estimate_device_bytes)
- * fits in what the budget has left, are then set up (context, data and factor
- * copies with their input checks, on the server's admission stream) and join
- * the batch; the worker keeps up to `max_inflight` psgld_batch_sweep calls of
- * one sweep each queued on its batch stream, each over every admitted job
- * with sweeps left, so jobs arriving meanwhile join at the next sweep; a job
- * whose last sweep has run has its posterior means read back and its context
- * released.  Contexts allocate from a CUDA stream-ordered memory pool, so
- * releasing one does not wait for the whole device.  A job's chain depends
- * only on its own inputs and seed: its result is the same alone and in any
- * mix.  Not the paper's (its experiments run one chain at a time); this is
- * the serving form of Algorithm 1 for many concurrent chains. */
+ * fits in what the budget has left; the admission thread then sets them up
+ * (context, data and factor copies with their input checks, on the server's
+ * admission stream) and later reads back and releases finished ones.  The
+ * batch thread keeps up to `max_inflight` psgld_batch_sweep calls of one
+ * sweep each queued on its batch stream, each over every set-up job with
+ * sweeps left, so jobs arriving meanwhile join at the next sweep, and never
+ * waits for a set-up or a read-back.  Contexts allocate from a CUDA
+ * stream-ordered memory pool, so releasing one does not wait for the whole
+ * device.  A job's chain depends only on its own inputs and seed: its result
+ * is the same alone and in any mix.  Not the paper's (its experiments run
+ * one chain at a time); this is the serving form of Algorithm 1 for many
+ * concurrent chains. */
 typedef struct psgld_server psgld_server;
 
 typedef struct {

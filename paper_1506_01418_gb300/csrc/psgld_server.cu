@@ -1,15 +1,17 @@
 // psgld_server.cu -- a native serving loop: continuous batching of dense
 // factorisation jobs on one GPU (psgld_server_* in include/psgld.h).
 //
-// One worker thread owns every CUDA call on the jobs: it finishes jobs whose
-// last sweep has run (posterior means to the caller's buffers, context
-// released), admits waiting jobs in arrival order while their estimated
-// device memory fits the budget (context, data and factor copies with their
-// input checks on the admission stream; the batch stream then waits for
-// them), and keeps up to max_inflight batch sweeps queued on the batch
-// stream, each one psgld_batch_sweep of one sweep over every admitted job
-// with sweeps left.  Submission and polling only touch the queues under the
-// mutex.  Contexts allocate from the device's stream-ordered memory pool
+// Two worker threads.  The admission thread reads back and releases jobs
+// whose last sweep has run (posterior means to the caller's buffers), and
+// admits waiting jobs in arrival order while their estimated device memory
+// fits the budget (context, data and factor copies with their input checks
+// on the admission stream).  The batch thread takes set-up jobs into the
+// batch (its stream waits for their set-up), hands finished ones back, and
+// keeps up to max_inflight batch sweeps queued on the batch stream, each one
+// psgld_batch_sweep of one sweep over every job with sweeps left; it never
+// waits for a set-up or a read-back.  A context passes from one thread to
+// the other through the queues under the mutex.  Submission and polling
+// only touch the queues.  Contexts allocate from the device's stream-ordered memory pool
 // (cudaMallocAsync / cudaFreeAsync), whose release threshold is raised so
 // that freed memory stays cached: releasing a finished job waits for
 // nothing but its own work.
@@ -64,7 +66,8 @@ struct Job {
     size_t bytes = 0;
     psgld_ctx *ctx = nullptr;
     int left = 0;
-    std::shared_ptr<Ev> last;
+    cudaEvent_t ready = nullptr;       // recorded on the admission stream after set-up
+    std::shared_ptr<Ev> last;          // follows the job's last sweep
 };
 
 }  // namespace
@@ -78,19 +81,20 @@ struct psgld_server {
 
     std::mutex m;
     std::condition_variable cv;
-    std::deque<Job *> waiting;                  // submitted, not admitted (guarded by m)
-    std::vector<std::pair<int64_t, double>> done;   // finished since the last poll (guarded by m)
-    int64_t next_id = 0, submitted = 0, finished = 0;   // guarded by m
-    bool stop = false;                          // guarded by m
-    std::string err;                            // guarded by m
-    std::string err_copy;                       // what psgld_server_last_error returned
-    int64_t sweeps = 0;                         // guarded by m
-    double jobs_in_sweeps = 0.0;                // guarded by m
+    // guarded by m: submitted jobs waiting for memory, jobs set up and not
+    // yet in the batch, jobs whose last sweep has run (to read back)
+    std::deque<Job *> waiting, ready, retire;
+    std::vector<std::pair<int64_t, double>> done;   // finished since the last poll
+    int64_t next_id = 0, submitted = 0, finished = 0;
+    bool stop = false;
+    std::string err, err_copy;
+    int64_t sweeps = 0;
+    double jobs_in_sweeps = 0.0;
 
-    // worker-thread state
+    // the batch thread's own state
     std::vector<Job *> active;
     std::deque<std::shared_ptr<Ev>> inflight;
-    std::thread worker;
+    std::thread admit_thread, batch_thread;
 };
 
 namespace {
@@ -115,19 +119,21 @@ bool setup(psgld_server *s, Job *j)
     if (st == PSGLD_OK) st = psgld_set_options(c, &q.options);
     if (st == PSGLD_OK) st = psgld_set_data_dense(c, q.V_dev, q.ldv, s->adm);
     if (st == PSGLD_OK) st = psgld_set_factors(c, q.W0_dev, q.Ht0_dev, s->adm);
+    if (st == PSGLD_OK && (cudaEventCreateWithFlags(&j->ready, cudaEventDisableTiming) != cudaSuccess ||
+                           cudaEventRecord(j->ready, s->adm) != cudaSuccess)) {
+        cudaGetLastError();
+        st = PSGLD_ERR_CUDA;
+    }
     if (st != PSGLD_OK) {
         const std::string why = c ? std::string("job setup: ") + psgld_last_error(c) : "job setup: context";
         if (c) psgld_destroy(c);
+        if (j->ready) cudaEventDestroy(j->ready);
         report(s, j, -1.0, why);
         delete j;
         return false;
     }
     j->ctx = c;
     j->left = q.sweeps;
-    // the batch stream starts the job's sweeps after its set-up
-    Ev ready;
-    cudaEventRecord(ready.e, s->adm);
-    cudaStreamWaitEvent(s->batch, ready.e, 0);
     return true;
 }
 
@@ -143,39 +149,73 @@ void finish(psgld_server *s, Job *j)
     delete j;
 }
 
-void run(psgld_server *s)
+// Admission thread: reads back and releases finished jobs first (that frees
+// memory), then sets up the head of the queue when it fits.
+void admit_loop(psgld_server *s)
+{
+    cudaSetDevice(s->device);
+    std::unique_lock<std::mutex> lk(s->m);
+    for (;;) {
+        if (!s->retire.empty()) {
+            Job *j = s->retire.front();
+            s->retire.pop_front();
+            lk.unlock();
+            finish(s, j);
+            lk.lock();
+            continue;
+        }
+        if (!s->waiting.empty() && s->used + s->waiting.front()->bytes <= s->budget) {
+            Job *j = s->waiting.front();
+            s->waiting.pop_front();
+            s->used += j->bytes;
+            s->peak = std::max(s->peak, s->used);
+            lk.unlock();
+            const bool ok = setup(s, j);
+            lk.lock();
+            if (ok) {
+                s->ready.push_back(j);
+                s->cv.notify_all();
+            }
+            continue;
+        }
+        if (s->stop && s->finished == s->submitted) break;
+        s->cv.wait_for(lk, std::chrono::milliseconds(1));
+    }
+}
+
+// Batch thread: takes set-up jobs into the batch, hands finished ones to
+// the admission thread, and keeps up to max_inflight batch sweeps queued.
+void batch_loop(psgld_server *s)
 {
     cudaSetDevice(s->device);
     for (;;) {
         bool did = false;
-        // 1. jobs whose last sweep has run
+        std::vector<Job *> joined;
+        {
+            std::lock_guard<std::mutex> lk(s->m);
+            joined.assign(s->ready.begin(), s->ready.end());
+            s->ready.clear();
+        }
+        for (Job *j : joined) {
+            cudaStreamWaitEvent(s->batch, j->ready, 0);    // its sweeps start after its set-up
+            cudaEventDestroy(j->ready);
+            j->ready = nullptr;
+            s->active.push_back(j);
+            did = true;
+        }
         for (size_t k = 0; k < s->active.size();) {
             Job *j = s->active[k];
             if (j->left == 0 && cudaEventQuery(j->last->e) == cudaSuccess) {
                 s->active.erase(s->active.begin() + (std::ptrdiff_t)k);
-                finish(s, j);
+                j->last.reset();
+                std::lock_guard<std::mutex> lk(s->m);
+                s->retire.push_back(j);
+                s->cv.notify_all();
                 did = true;
             } else {
                 ++k;
             }
         }
-        // 2. admission, in arrival order, while the head of the queue fits
-        for (;;) {
-            Job *j = nullptr;
-            {
-                std::lock_guard<std::mutex> lk(s->m);
-                if (!s->waiting.empty() && s->used + s->waiting.front()->bytes <= s->budget) {
-                    j = s->waiting.front();
-                    s->waiting.pop_front();
-                    s->used += j->bytes;
-                    s->peak = std::max(s->peak, s->used);
-                }
-            }
-            if (!j) break;
-            if (setup(s, j)) s->active.push_back(j);
-            did = true;
-        }
-        // 3. one more batch sweep unless max_inflight are queued
         while (!s->inflight.empty() && cudaEventQuery(s->inflight.front()->e) == cudaSuccess)
             s->inflight.pop_front();
         if ((int)s->inflight.size() < s->max_inflight) {
@@ -186,25 +226,23 @@ void run(psgld_server *s)
                 const psgld_status st = psgld_batch_sweep(live.data(), (int32_t)live.size(), 1, s->batch);
                 auto ev = std::make_shared<Ev>();
                 cudaEventRecord(ev->e, s->batch);
-                for (Job *j : s->active) {
-                    if (j->left <= 0) continue;
-                    j->left -= 1;
-                    if (j->left == 0) j->last = ev;
-                }
                 if (st != PSGLD_OK) {
                     // the batch was refused or failed: its jobs end failed
-                    std::string why = std::string("batch sweep: ") + psgld_last_error(live[0]);
-                    for (size_t k = 0; k < s->active.size();) {
-                        Job *j = s->active[k];
-                        s->active.erase(s->active.begin() + (std::ptrdiff_t)k);
-                        cudaStreamSynchronize(s->batch);
+                    const std::string why = std::string("batch sweep: ") + psgld_last_error(live[0]);
+                    cudaStreamSynchronize(s->batch);
+                    for (Job *j : s->active) {
                         psgld_destroy(j->ctx);
                         report(s, j, -1.0, why);
                         delete j;
                     }
-                }
-                s->inflight.push_back(ev);
-                {
+                    s->active.clear();
+                } else {
+                    for (Job *j : s->active) {
+                        if (j->left <= 0) continue;
+                        j->left -= 1;
+                        if (j->left == 0) j->last = ev;
+                    }
+                    s->inflight.push_back(ev);
                     std::lock_guard<std::mutex> lk(s->m);
                     s->sweeps += 1;
                     s->jobs_in_sweeps += (double)live.size();
@@ -212,12 +250,9 @@ void run(psgld_server *s)
                 did = true;
             }
         }
-        // 4. done, or idle until a submission or a short time passes
-        {
-            std::unique_lock<std::mutex> lk(s->m);
-            if (s->stop && s->waiting.empty() && s->active.empty()) break;
-            if (!did) s->cv.wait_for(lk, std::chrono::microseconds(50));
-        }
+        std::unique_lock<std::mutex> lk(s->m);
+        if (s->stop && s->finished == s->submitted) break;
+        if (!did) s->cv.wait_for(lk, std::chrono::microseconds(50));
     }
     cudaStreamSynchronize(s->batch);
     s->inflight.clear();
@@ -257,8 +292,15 @@ psgld_status psgld_server_create(size_t hbm_budget, int32_t max_inflight, psgld_
     s->allocator.free = pool_free;
     s->allocator.user = nullptr;
     try {
-        s->worker = std::thread(run, s);
+        s->admit_thread = std::thread(admit_loop, s);
+        s->batch_thread = std::thread(batch_loop, s);
     } catch (...) {
+        {
+            std::lock_guard<std::mutex> lk(s->m);
+            s->stop = true;
+        }
+        s->cv.notify_all();
+        if (s->admit_thread.joinable()) s->admit_thread.join();
         cudaStreamDestroy(s->batch);
         cudaStreamDestroy(s->adm);
         delete s;
@@ -347,8 +389,8 @@ void psgld_server_destroy(psgld_server *s)
         s->stop = true;
     }
     s->cv.notify_all();
-    if (s->worker.joinable()) s->worker.join();
-    for (Job *j : s->waiting) delete j;   // none left: the worker admits and finishes every job
+    if (s->admit_thread.joinable()) s->admit_thread.join();
+    if (s->batch_thread.joinable()) s->batch_thread.join();
     cudaStreamDestroy(s->batch);
     cudaStreamDestroy(s->adm);
     delete s;

@@ -1090,11 +1090,13 @@ def serve_trace_native(wl, dev, uuid):
 
 def run_serving(args, wl_name, wl):
     """The serving loop on one GPU: a Poisson trace of jobs replayed in real
-    time with continuous batching (every admitted job's part-steps share the
-    batch's launches); value = observed entries x sweeps of every job and of
-    the standing chain / wall time of the trace; latency = completion -
-    arrival.  The same trace with one stream and context per job (no shared
-    launches) is reported beside it."""
+    time through the library's native serving loop (psgld_server_*:
+    memory-budget admission and continuous batching, every admitted job's
+    part-steps in the batch's shared launches, on the library's worker
+    threads); value = observed entries x sweeps of every job and of the
+    standing chain / wall time of the trace; latency = arrival to read-back.
+    The same trace with the Python batching executor and with one stream and
+    context per job (no shared launches) is reported beside it."""
     import torch
 
     import __graft_entry__
@@ -1107,17 +1109,16 @@ def run_serving(args, wl_name, wl):
         uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
     except Exception:
         uuid = "0"
-    bex = serving.BatchedGpuExecutor(0)
-    r = serve_trace(wl, bex, dev, uuid)
+    r = serve_trace_native(wl, dev, uuid)
     jobs, wall = r["jobs"], r["wall"]
     value = (r["job_entries"] + r["st_entries"]) / wall
     lat = serving.latency_summary(jobs)
-    sizes = bex.batch_sizes[-r["ticks"]:] if r["ticks"] else []
     h2d = sum(4 * (j.I + j.J) * j.K for j in jobs)
     d2h = sum(8 * (j.I + j.J) * j.K * 2 for j in jobs)
+    st = r["stats"]
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": len(jobs),
-        "warmup": r["warm"], "ms_per_step": wall * 1e3 / max(1, len(jobs)), "higher_is_better": True,
+        "warmup": 12, "ms_per_step": wall * 1e3 / max(1, len(jobs)), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
         "config": {"workload": wl_name, "arrival_rate_per_s": wl["rate"], "trace_s": wl["duration"],
                    "jobs": len(jobs), "sweeps_per_job": wl["sweeps"], "B": wl["B"],
@@ -1125,39 +1126,49 @@ def run_serving(args, wl_name, wl):
                    "standing_chain_sms": wl.get("standing_sms", 0) or "all",
                    "step": "one job of the trace (value counts every job's and the standing "
                            "chain's entries x sweeps over the trace's wall time)",
-                   "path": "continuous batching: every admitted job's part-steps in the batch's "
-                           "shared tensor-core launches (psgld_batch_sweep, one sweep per tick, "
-                           "at most three ticks queued; job set-up and teardown on worker "
-                           "threads); the standing chain on its own stream, its persistent kernel "
-                           "on 120 SMs; PyTorch caching allocator"},
+                   "path": "the library's serving loop (psgld_server_*): admission by the "
+                           "jobs' estimated device memory, continuous batching with every admitted "
+                           "job's part-steps in shared tensor-core launches (psgld_batch_sweep, one "
+                           "sweep per call, at most three queued), set-up and read-back on a second "
+                           "thread, stream-ordered memory pool; the standing chain on its own "
+                           "stream, its persistent kernel on 120 SMs"},
         "latency": lat,
         "job_entries_per_s": r["job_entries"] / wall,
         "standing_chain": ({"sweeps": r["st_sweeps"], "entries_per_s": r["st_entries"] / wall}
-                           if r["standing"] else None),
-        "batch": {"ticks": r["ticks"], "jobs_per_tick_mean": (sum(sizes) / len(sizes)) if sizes else 0,
-                  "jobs_per_tick_max": max(sizes) if sizes else 0},
-        "peak_budget_used_bytes": r["peak_used"],
+                           if r["st_sweeps"] else None),
+        "batch": {"sweeps": st["sweeps"], "jobs_per_sweep_mean": st["jobs_per_sweep"]},
+        "peak_budget_used_bytes": st["peak_bytes"],
         "roofline": None,
-        # per tick: set t, B x (one gradient launch per K class (2) + update),
-        # accumulate, advance t; standing chain: 2B + 3 per sweep
-        "gpu_launches": r["ticks"] * (3 * wl["B"] + 3) + r["st_sweeps"] * (2 * 16 + 3),
+        # per batch sweep: set t, B x (gradient launches per kernel variant
+        # (about two) + update), accumulate, advance t; standing chain: 2B + 3
+        # per sweep
+        "gpu_launches": st["sweeps"] * (3 * wl["B"] + 3) + r["st_sweeps"] * (2 * 16 + 3),
         "clocks": r["clocks"],
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": h2d / max(1, len(jobs)),
                 "d2h_bytes_per_step": d2h / max(1, len(jobs)),
                 "note": "the serving loop is the end-to-end path: each job's initial factors go "
                         "host to device and its posterior means device to host inside the trace"},
     }
-    bex.shutdown()
-    del bex
     torch.cuda.empty_cache()
     if not args.no_serving_compare:
-        r2 = serve_trace(wl, serving.GpuExecutor(0), dev, uuid)
-        result["per_job_streams"] = {
-            "value": (r2["job_entries"] + r2["st_entries"]) / r2["wall"], "unit": UNIT,
-            "job_entries_per_s": r2["job_entries"] / r2["wall"],
-            "latency": serving.latency_summary(r2["jobs"]), "clocks": r2["clocks"],
-            "how": "the same trace, one stream and context per job with all its sweeps enqueued "
-                   "at admission (no shared launches)"}
+        for name, mk, how in (
+                ("python_batching", lambda: serving.BatchedGpuExecutor(0),
+                 "the same trace through serving.Server with BatchedGpuExecutor: the same shared "
+                 "launches driven from a Python loop (set-up and teardown on worker threads)"),
+                ("per_job_streams", lambda: serving.GpuExecutor(0),
+                 "the same trace, one stream and context per job with all its sweeps enqueued "
+                 "at admission (no shared launches)")):
+            ex = mk()
+            r2 = serve_trace(wl, ex, dev, uuid)
+            if hasattr(ex, "shutdown"):
+                ex.shutdown()
+            del ex
+            torch.cuda.empty_cache()
+            result[name] = {
+                "value": (r2["job_entries"] + r2["st_entries"]) / r2["wall"], "unit": UNIT,
+                "job_entries_per_s": r2["job_entries"] / r2["wall"],
+                "standing_entries_per_s": r2["st_entries"] / r2["wall"],
+                "latency": serving.latency_summary(r2["jobs"]), "clocks": r2["clocks"], "how": how}
     print(json.dumps(result), flush=True)
 
 

@@ -13,7 +13,7 @@
 #include <mutex>
 #include <new>
 
-#include "psgld_internal.cuh"
+#include "psgld_context.cuh"
 
 namespace psgld {
 

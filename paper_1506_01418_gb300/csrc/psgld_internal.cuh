@@ -137,12 +137,6 @@ namespace psgld {
 void *dev_alloc(psgld_ctx *c, size_t bytes, cudaStream_t st);
 void dev_free(psgld_ctx *c, void *p, cudaStream_t st = nullptr);
 
-// ---- contexts --------------------------------------------------------------
-// psgld_create with the context's allocator given (nullptr: the one set by
-// psgld_set_allocator, else cudaMalloc / cudaFree).
-psgld_status create_context(int64_t I, int64_t J, int32_t K, int32_t B, double tweedie_p, double phi,
-                            const psgld_prior *prior, const psgld_allocator *allocator, psgld_ctx **out);
-
 // ---- ordering ----------------------------------------------------------------
 // After enqueueing work of c on st: remember the stream and record an event
 // behind the work.  wait_enqueued blocks until that work has run (not the

@@ -28,7 +28,7 @@
 #include <utility>
 #include <vector>
 
-#include "psgld_internal.cuh"
+#include "psgld_context.cuh"
 
 namespace {
 

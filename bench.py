@@ -1129,7 +1129,7 @@ def run_serving(args, wl_name, wl):
                    "path": "the library's serving loop (psgld_server_*): admission by the "
                            "jobs' estimated device memory, continuous batching with every admitted "
                            "job's part-steps in shared tensor-core launches (psgld_batch_sweep, one "
-                           "sweep per call, at most three queued), set-up and read-back on a second "
+                           "sweep per call, one queued at a time), set-up and read-back on a second "
                            "thread, stream-ordered memory pool; the standing chain on its own "
                            "stream, its persistent kernel on 120 SMs"},
         "latency": lat,

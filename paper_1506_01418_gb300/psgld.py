@@ -483,7 +483,7 @@ class NativeServer:
     device inputs; a worker thread in the library admits them by memory,
     batches their sweeps and writes their posterior means to host arrays."""
 
-    def __init__(self, hbm_budget: int, max_inflight: int = 3):
+    def __init__(self, hbm_budget: int, max_inflight: int = 1):
         h = C.c_void_p()
         st = load().psgld_server_create(int(hbm_budget), int(max_inflight), C.byref(h))
         if st != PSGLD_OK:

@@ -76,3 +76,26 @@ def test_null_context_is_rejected():
     assert lib.psgld_sweep(None, 1, None) == P.PSGLD_ERR_ARG
     assert lib.psgld_iterations_done(None) == -1
     lib.psgld_destroy(None)
+
+
+def test_server_rejects_bad_arguments_before_touching_the_gpu():
+    lib = P.load()
+    h = C.c_void_p()
+    assert lib.psgld_server_create(0, 1, C.byref(h)) == P.PSGLD_ERR_ARG
+    assert lib.psgld_server_create(1 << 20, 0, C.byref(h)) == P.PSGLD_ERR_ARG
+    assert lib.psgld_server_create(1 << 20, 1, None) == P.PSGLD_ERR_ARG
+    job = P.psgld_job()
+    jid = C.c_int64()
+    assert lib.psgld_server_submit(None, C.byref(job), C.byref(jid)) == P.PSGLD_ERR_ARG
+    assert lib.psgld_server_poll(None, None, None, 4) == 0
+    assert lib.psgld_server_wait_idle(None, 0.0) == P.PSGLD_ERR_ARG
+    assert lib.psgld_server_last_error(None) == b""
+    lib.psgld_server_destroy(None)
+
+
+def test_batch_sweep_rejects_bad_arguments():
+    lib = P.load()
+    assert lib.psgld_batch_sweep(None, 1, 1, None) == P.PSGLD_ERR_ARG
+    arr = (C.c_void_p * 1)(None)
+    assert lib.psgld_batch_sweep(arr, 1, 1, None) == P.PSGLD_ERR_ARG
+    assert lib.psgld_batch_sweep(arr, 0, 1, None) == P.PSGLD_ERR_ARG

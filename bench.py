@@ -623,7 +623,7 @@ def e2e_job(wl, seed, dev, i, j, v, W0, H0):
     from paper_1506_01418_gb300 import psgld as P
     P.psgld_posterior_mean(chain.ctx, Wm, Wv, Hm, Hv)
     # the log-likelihood over a dense V is an FP64 product W H over every
-    # entry (1.6 s at 32768^2 on this GPU's FP64 rate): the dense jobs read
+    # entry (0.57 s at 32768^2 on this GPU's FP64 rate): the dense jobs read
     # back their posterior means only
     ll = chain.log_lik() if not dense_in else None
     torch.cuda.synchronize(dev)

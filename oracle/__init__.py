@@ -17,9 +17,12 @@ import subprocess
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "psgld_oracle.c")
-_HDR = os.path.join(_HERE, "psgld_oracle.h")
-_LIB = os.path.join(_HERE, "liboracle_psgld.so")
+# The mutation tests (tests/test_oracle_mutants.py) point the loader at a
+# copy of the source with one planted mistake, built into a library of its
+# own, through these two variables; unset, the loader uses this directory.
+_SRC = os.environ.get("PSGLD_ORACLE_SOURCE") or os.path.join(_HERE, "psgld_oracle.c")
+_HDR = os.path.join(os.path.dirname(_SRC), "psgld_oracle.h")
+_LIB = os.environ.get("PSGLD_ORACLE_LIB") or os.path.join(_HERE, "liboracle_psgld.so")
 
 PRIOR_EXPONENTIAL, PRIOR_GAUSSIAN = 0, 1
 EPS_FIXED, EPS_POLY = 0, 1

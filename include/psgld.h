@@ -247,6 +247,31 @@ PSGLD_API psgld_status psgld_log_lik(psgld_ctx *ctx, double *out_host, void *str
 PSGLD_API psgld_status psgld_rmse(psgld_ctx *ctx, int32_t use_posterior_mean,
                         double *out_host, void *stream);
 
+/* ---- checkpoint and resume ----------------------------------------------
+ * A chain's whole state is its factors (psgld_get_factors / _set_factors),
+ * the FP64 posterior sums and three counters; the options (seed included)
+ * and the data are the caller's.  The Langevin noise of iteration t is a
+ * function of (seed, t, matrix, row, column) only (Sec. 2's N(0, 2 eps)
+ * drawn from a counter-based Philox stream), so a chain restored into a
+ * fresh context with the same options and data continues bit for bit as if
+ * it had not stopped. */
+
+/* Copies the state out: sums of W and W^2 (I x K) and of H^T and (H^T)^2
+ * (J x K), row-major FP64 host arrays (any may be NULL), and
+ * counters_host[0..2] = iterations done t, sweeps done, posterior samples
+ * kept (may be NULL).  Waits for the context's last enqueued work. */
+PSGLD_API psgld_status psgld_get_state(psgld_ctx *ctx, double *sW_host, double *sW2_host,
+                                       double *sH_host, double *sH2_host, int64_t *counters_host);
+
+/* Restores a state taken with psgld_get_state, after psgld_set_data_* and
+ * psgld_set_factors (setting data clears the sums and counters).  All four
+ * sums and the counters are required; PSGLD_ERR_ARG if a pointer is NULL or
+ * the counters are inconsistent (t < 0, sweeps < 0, samples outside
+ * [0, sweeps]); PSGLD_ERR_STATE before the factors are set.  Synchronous. */
+PSGLD_API psgld_status psgld_set_state(psgld_ctx *ctx, const double *sW_host, const double *sW2_host,
+                                       const double *sH_host, const double *sH2_host,
+                                       const int64_t *counters_host);
+
 /* ---- introspection: the schedule and layouts, for bit-exact checks ------ */
 
 /* Piece boundaries (Definition 1): row_starts[r] = floor(r I / B) for

@@ -680,6 +680,53 @@ psgld_status psgld_posterior_mean(psgld_ctx *c, double *Wm, double *Wv, double *
     return PSGLD_OK;
 }
 
+// The state of a chain beside its factors: the FP64 sums (rows x ldk on the
+// device, rows x K on the host) and the counters t, sweeps, samples.
+psgld_status psgld_get_state(psgld_ctx *c, double *sW, double *sW2, double *sH, double *sH2,
+                             int64_t *counters)
+{
+    if (!c) return PSGLD_ERR_ARG;
+    PSGLD_CK(c, wait_enqueued(c));
+    {
+        psgld_status fs = check_kernel_flag(c);
+        if (fs != PSGLD_OK) return fs;
+    }
+    const size_t row = sizeof(double) * (size_t)c->K, pitch = sizeof(double) * (size_t)c->ldk;
+    const struct { double *dst; const double *src; int64_t rows; } parts[4] = {
+        {sW, c->sW.s, c->I}, {sW2, c->sW.s2, c->I}, {sH, c->sH.s, c->J}, {sH2, c->sH.s2, c->J}};
+    for (const auto &q : parts)
+        if (q.dst)
+            PSGLD_CK(c, cudaMemcpy2D(q.dst, row, q.src, pitch, row, (size_t)q.rows, cudaMemcpyDeviceToHost));
+    if (counters) {
+        counters[0] = c->t_done;
+        counters[1] = c->sweeps_done;
+        counters[2] = c->n_samples;
+    }
+    return PSGLD_OK;
+}
+
+psgld_status psgld_set_state(psgld_ctx *c, const double *sW, const double *sW2, const double *sH,
+                             const double *sH2, const int64_t *counters)
+{
+    if (!c || !sW || !sW2 || !sH || !sH2 || !counters) return PSGLD_ERR_ARG;
+    const int64_t t = counters[0], sweeps = counters[1], samples = counters[2];
+    if (t < 0 || sweeps < 0 || samples < 0 || samples > sweeps)
+        return fail(c, PSGLD_ERR_ARG, "inconsistent counters (t, sweeps, samples)");
+    if (!c->has_factors) return fail(c, PSGLD_ERR_STATE, "set the data and the factors first");
+    PSGLD_CK(c, wait_enqueued(c));
+    const size_t row = sizeof(double) * (size_t)c->K, pitch = sizeof(double) * (size_t)c->ldk;
+    const struct { double *dst; const double *src; int64_t rows; } parts[4] = {
+        {c->sW.s, sW, c->I}, {c->sW.s2, sW2, c->I}, {c->sH.s, sH, c->J}, {c->sH.s2, sH2, c->J}};
+    // the padding columns (K .. ldk-1) stay as they are: zero
+    for (const auto &q : parts)
+        PSGLD_CK(c, cudaMemcpy2D(q.dst, pitch, q.src, row, row, (size_t)q.rows, cudaMemcpyHostToDevice));
+    PSGLD_CK(c, cudaMemcpy(c->t_dev, &t, sizeof t, cudaMemcpyHostToDevice));
+    c->t_done = t;
+    c->sweeps_done = sweeps;
+    c->n_samples = samples;
+    return PSGLD_OK;
+}
+
 psgld_status psgld_log_lik(psgld_ctx *c, double *out, void *stream)
 {
     if (!c || !out) return PSGLD_ERR_ARG;

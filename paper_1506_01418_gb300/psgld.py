@@ -75,7 +75,7 @@ EXPORTS = [
     "psgld_sweep", "psgld_posterior_mean", "psgld_log_lik", "psgld_rmse", "psgld_piece_bounds",
     "psgld_part_schedule", "psgld_part_layout", "psgld_profile_read", "psgld_profile_read_split",
     "psgld_iterations_done", "psgld_estimate_device_bytes", "psgld_set_allocator",
-    "psgld_batch_sweep",
+    "psgld_batch_sweep", "psgld_get_state", "psgld_set_state",
     "psgld_log_lik_static", "psgld_last_error",
     "psgld_destroy",
     "psgld_server_create", "psgld_server_submit", "psgld_server_poll", "psgld_server_wait_idle",
@@ -111,6 +111,8 @@ def load(build_if_missing: bool = True):
         "psgld_posterior_mean": (st, [vp, vp, vp, vp, vp, vp]),
         "psgld_log_lik": (st, [vp, vp, vp]),
         "psgld_rmse": (st, [vp, i32, vp, vp]),
+        "psgld_get_state": (st, [vp, vp, vp, vp, vp, vp]),
+        "psgld_set_state": (st, [vp, vp, vp, vp, vp, vp]),
         "psgld_piece_bounds": (st, [vp, vp, vp]),
         "psgld_part_schedule": (st, [vp, i64, vp]),
         "psgld_part_layout": (st, [vp, i32, vp, vp, vp]),
@@ -243,6 +245,23 @@ def psgld_posterior_mean(ctx, Wmean, Wvar, Hmean, Hvar):
     _check(ctx, load().psgld_posterior_mean(ctx, _ptr(Wmean, f), _ptr(Wvar, f), _ptr(Hmean, f),
                                             _ptr(Hvar, f), C.byref(n)))
     return n.value
+
+
+def psgld_get_state(ctx, I, J, K):
+    """(sum W, sum W^2, sum H^T, sum (H^T)^2, counters [t, sweeps, samples])
+    as numpy arrays (FP64 I x K / J x K, int64 [3])."""
+    out = [np.zeros((n, K)) for n in (I, I, J, J)]
+    cnt = np.zeros(3, np.int64)
+    f = _dt("f64")
+    _check(ctx, load().psgld_get_state(ctx, *[_ptr(x, f) for x in out], C.c_void_p(cnt.ctypes.data)))
+    return (*out, cnt)
+
+
+def psgld_set_state(ctx, sW, sW2, sH, sH2, counters):
+    f = _dt("f64")
+    arrs = [np.ascontiguousarray(x, np.float64) for x in (sW, sW2, sH, sH2)]
+    cnt = np.ascontiguousarray(counters, np.int64)
+    _check(ctx, load().psgld_set_state(ctx, *[_ptr(x, f) for x in arrs], C.c_void_p(cnt.ctypes.data)))
 
 
 def psgld_log_lik(ctx, stream=None) -> float:
@@ -460,6 +479,14 @@ class PSGLD:
         Hm = np.zeros((self.J, self.K)); Hv = np.zeros((self.J, self.K))
         n = psgld_posterior_mean(self.ctx, Wm, Wv, Hm, Hv)
         return Wm, Wv, Hm, Hv, n
+
+    def get_state(self):
+        """The chain's state beside its factors: FP64 posterior sums and the
+        counters (t, sweeps, samples); with get_factors, a checkpoint."""
+        return psgld_get_state(self.ctx, self.I, self.J, self.K)
+
+    def set_state(self, state):
+        psgld_set_state(self.ctx, *state)
 
     def log_lik(self, stream=None):
         return psgld_log_lik(self.ctx, stream)

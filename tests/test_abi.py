@@ -75,6 +75,8 @@ def test_null_context_is_rejected():
     assert lib.psgld_part_step(None, 1, None) == P.PSGLD_ERR_ARG
     assert lib.psgld_sweep(None, 1, None) == P.PSGLD_ERR_ARG
     assert lib.psgld_iterations_done(None) == -1
+    assert lib.psgld_get_state(None, None, None, None, None, None) == P.PSGLD_ERR_ARG
+    assert lib.psgld_set_state(None, None, None, None, None, None) == P.PSGLD_ERR_ARG
     lib.psgld_destroy(None)
 
 

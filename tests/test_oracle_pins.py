@@ -182,12 +182,38 @@ def _loglik_dense(V, W, H, p, phi, mu_min=1e-10):
     return m.log_lik()
 
 
-@pytest.mark.parametrize("p,phi", [(0.0, 0.7), (1.0, 1.0), (2.0, 0.5), (3.0, 0.8)])
+def _compound_poisson_gamma_logpdf(y, mu, p, phi):
+    """Tweedie density for 1 < p < 2 as its definition: N ~ Poisson(lam),
+    y = sum of N Gamma(alpha, scale gam) draws, lam = mu^(2-p) / (phi (2-p)),
+    alpha = (2-p)/(p-1), gam = phi (p-1) mu^(p-1) (Jorgensen's compound
+    Poisson-gamma); P(y = 0) = exp(-lam), otherwise the Poisson mixture of
+    gamma densities, summed in log space over n = 1..300."""
+    lam = mu ** (2 - p) / (phi * (2 - p))
+    alpha = (2 - p) / (p - 1)
+    gam = phi * (p - 1) * mu ** (p - 1)
+    out = np.empty_like(y, dtype=np.float64)
+    n = np.arange(1, 301, dtype=np.float64)
+    for idx in np.ndindex(y.shape):
+        if y[idx] == 0:
+            out[idx] = -lam[idx]
+            continue
+        terms = (stats.poisson.logpmf(n, lam[idx]) +
+                 stats.gamma.logpdf(y[idx], a=n * alpha, scale=gam[idx]))
+        out[idx] = np.logaddexp.reduce(terms)
+    return out
+
+
+@pytest.mark.parametrize("p,phi", [(0.0, 0.7), (1.0, 1.0), (1.5, 0.6), (1.5, 1.3), (2.0, 0.5),
+                                   (3.0, 0.8)])
 def test_log_lik_matches_textbook_density(p, phi):
-    """-(1/phi) sum d_beta differs from the exact log density by a mu-free constant."""
+    """-(1/phi) sum d_beta differs from the exact log density by a mu-free
+    constant (p = 1.5: the compound Poisson-gamma, zeros included)."""
     g = np.random.default_rng(int(p * 10))
     I, J, K = 3, 4, 2
     V = g.poisson(4.0, size=(I, J)).astype(np.float64) + 1.0
+    if 1.0 < p < 2.0:
+        V = np.round(g.gamma(1.5, 2.0, size=(I, J)) * 64) / 64   # exact in FP32
+        V[0, 0] = V[2, 3] = 0.0             # the point mass at zero
     diffs = []
     for trial in range(2):
         W = g.uniform(0.5, 2.0, size=(I, K))
@@ -197,6 +223,8 @@ def test_log_lik_matches_textbook_density(p, phi):
             exact = stats.norm.logpdf(V, loc=mu, scale=math.sqrt(phi)).sum()
         elif p == 1.0:
             exact = stats.poisson.logpmf(V, mu).sum()
+        elif 1.0 < p < 2.0:
+            exact = _compound_poisson_gamma_logpdf(V, mu, p, phi).sum()
         elif p == 2.0:
             exact = stats.gamma.logpdf(V, a=1.0 / phi, scale=mu * phi).sum()
         else:

@@ -452,6 +452,49 @@ def test_posterior_moments_match_recorded_samples():
 # Stationary distribution: closed-form Gaussian posterior (Theorem 1)
 # ---------------------------------------------------------------------------
 
+def test_mirrored_chain_samples_the_truncated_posterior():
+    """p = 0, exponential prior (rate lam) with mirroring, K = 1, H fixed at
+    h: each w_i >= 0 has the posterior proportional to
+    exp(-(v_i - w h)^2 / (2 phi) - lam w) on [0, inf), a normal with mean
+    (v_i h - lam phi) / h^2 and variance phi / h^2 truncated to w >= 0
+    (scipy's truncnorm).  The mirrored Langevin chain (Sec. 3.2) must match
+    its first two moments within 3 standard errors (batch means).  The rows
+    are chosen so that truncation matters: most untruncated means are
+    negative, so dropping the mirror, the prior or its sign fails."""
+    I, J, K, B = 6, 1, 1, 1
+    phi, lam, h = 1.0, 0.7, 1.0
+    V = np.array([[0.2], [0.6], [1.0], [-0.3], [1.5], [0.0]])
+    m = oracle.Oracle(I, J, K, B, 0.0, phi, prior_kind=oracle.PRIOR_EXPONENTIAL, lambda_w=lam,
+                      lambda_h=1.0)
+    ii, jj, _ = datagen.dense_to_coo(V.astype(np.float32))
+    m.set_data(ii, jj, V.ravel())
+    m.set_factors(np.full((I, K), 0.5), np.full((K, J), h))
+    m.set_options(seed=5, eps=5e-3, freeze_H=True, burn_in=2000)
+    m.sweep(2000)
+    n_batches, per_batch = 40, 10000
+    prev_m = np.zeros((I, K)); prev_s = np.zeros((I, K)); prev_n = 0
+    bm, bs = [], []
+    for b in range(n_batches):
+        m.sweep(per_batch)
+        Wm, Wv, _, _, n = m.posterior()
+        tot, tot2 = Wm * n, (Wv + Wm ** 2) * n
+        bm.append((tot - prev_m) / (n - prev_n))
+        bs.append((tot2 - prev_s) / (n - prev_n))
+        prev_m, prev_s, prev_n = tot, tot2, n
+    bm, bs = np.array(bm)[:, :, 0], np.array(bs)[:, :, 0]
+    se_mean = bm.std(0, ddof=1) / math.sqrt(n_batches)
+    se_second = bs.std(0, ddof=1) / math.sqrt(n_batches)
+    loc = (V[:, 0] * h - lam * phi) / h ** 2
+    scale = math.sqrt(phi) / h
+    for i in range(I):
+        tn = stats.truncnorm((0.0 - loc[i]) / scale, np.inf, loc=loc[i], scale=scale)
+        want_mean, want_second = tn.mean(), tn.var() + tn.mean() ** 2
+        assert abs(bm[:, i].mean() - want_mean) < 3 * se_mean[i], (i, bm[:, i].mean(), want_mean)
+        assert abs(bs[:, i].mean() - want_second) < 3 * se_second[i], \
+            (i, bs[:, i].mean(), want_second)
+        assert abs(want_mean - loc[i]) > 10 * se_mean[i] or loc[i] > 0   # truncation matters
+
+
 def test_chain_samples_closed_form_gaussian_posterior():
     """p = 0, Gaussian prior, H held fixed: each row w_i of W has the posterior
     N(Sigma_i H_i v_i / phi, Sigma_i), Sigma_i = (H_i H_i^T / phi + I / sigma^2)^-1.

@@ -452,6 +452,43 @@ def test_posterior_moments_match_recorded_samples():
 # Stationary distribution: closed-form Gaussian posterior (Theorem 1)
 # ---------------------------------------------------------------------------
 
+@pytest.mark.parametrize("prior", [oracle.PRIOR_EXPONENTIAL, oracle.PRIOR_GAUSSIAN])
+def test_empty_part_moves_by_prior_and_noise_only(prior):
+    """Entries only in block (0, 0) of a B = 3 grid: parts 1 and 2 hold no
+    entry, so S = N / |Pi| is read as 0 there and the drift is the prior
+    gradient alone (-lam, or -x / sigma^2); part 0's drift has the
+    likelihood term scaled by N / |Pi_0| = 1."""
+    I, J, K, B = 6, 9, 3, 3
+    g = np.random.default_rng(3)
+    ii, jj = np.meshgrid(np.arange(2), np.arange(3), indexing="ij")
+    ii, jj = ii.ravel().astype(np.int32), jj.ravel().astype(np.int32)
+    vv = g.uniform(0.5, 2.0, size=ii.size)
+    m = oracle.Oracle(I, J, K, B, 1.0, 1.0, prior_kind=prior, lambda_w=0.8, lambda_h=1.2,
+                      sigma_w=0.9, sigma_h=1.1)
+    m.set_data(ii, jj, vv)
+    W = g.uniform(0.2, 1.0, size=(I, K))
+    H = g.uniform(0.2, 1.0, size=(K, J))
+    m.set_factors(W, H)
+    if prior == oracle.PRIOR_EXPONENTIAL:
+        pW, pH = np.full_like(W, -0.8), np.full_like(H, -1.2)
+    else:
+        pW, pH = -W / 0.9 ** 2, -H / 1.1 ** 2
+    assert [m.part_size(t) for t in (1, 2, 3)] == [ii.size, 0, 0]
+    for t in (2, 3):
+        assert m.scale(t) == 0.0
+        dW, dH = m.drift(t)
+        np.testing.assert_allclose(dW, pW, rtol=0, atol=1e-15)
+        np.testing.assert_allclose(dH, pH, rtol=0, atol=1e-15)
+    # part 0: the Poisson likelihood gradient of block (0, 0), S = 1
+    assert m.scale(1) == 1.0
+    dW, dH = m.drift(1)
+    mu = W @ H
+    E = np.zeros((I, J))
+    E[ii, jj] = (vv - mu[ii, jj]) / mu[ii, jj]
+    np.testing.assert_allclose(dW, E @ H.T + pW, rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(dH, W.T @ E + pH, rtol=1e-12, atol=1e-12)
+
+
 def test_mirrored_chain_samples_the_truncated_posterior():
     """p = 0, exponential prior (rate lam) with mirroring, K = 1, H fixed at
     h: each w_i >= 0 has the posterior proportional to

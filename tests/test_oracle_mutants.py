@@ -4,8 +4,9 @@ source makes at least one pin of tests/test_oracle_pins.py fail.
 Every mutant is a plausible slip in one equation of the method -- a prior
 gradient, the dispersion, the Langevin noise scale, a transposed index, the
 part rule of Sec. 3, the stochastic-gradient scale N / |Pi_t|, the step-size
-schedule, the Tweedie power, the mirror, the uniform and Box-Muller steps of
-the noise, the beta divergence and the posterior variance.  The mutant is
+schedule, the Tweedie power and its clamp below mu_min (in the gradient and
+in the log-likelihood), the mirror, the uniform and Box-Muller steps of the
+noise, the beta divergence and the posterior variance.  The mutant is
 compiled into a library of its own in a temporary directory and the pin
 suite runs against it in a child process (the oracle's loader reads the
 source and library paths from PSGLD_ORACLE_SOURCE / PSGLD_ORACLE_LIB); the
@@ -55,6 +56,12 @@ MUTANTS = {
         "z[1] = r0 * sin(two_pi * u[1]);", "z[1] = r1 * sin(two_pi * u[1]);"),
     "beta_divergence_general_term": (
         "- v * pow(mu, beta - 1.0) / (beta - 1.0)", "- v * pow(mu, beta - 1.0) / beta"),
+    "mu_min_clamps_the_residual_too": (
+        "return (v - mu) * pow(mc, -m->p) / m->phi;", "return (v - mc) * pow(mc, -m->p) / m->phi;"),
+    "mu_min_clamp_dropped_in_gradient": (
+        "double mc = mu > m->mu_min ? mu : m->mu_min;", "double mc = mu;"),
+    "mu_min_clamp_dropped_in_log_lik": (
+        "if (m->p > 0.0 && mu < m->mu_min) mu = m->mu_min;", "if (0) mu = m->mu_min;"),
     "posterior_variance_without_square": (
         "Wvar[a] = n > 0 ? m->sW2[a] / n - mean * mean : 0.0;",
         "Wvar[a] = n > 0 ? m->sW2[a] / n - mean : 0.0;"),

@@ -372,6 +372,148 @@ def test_part_step_matches_masked_dense_update(B, t):
     np.testing.assert_allclose(Ho, Hn, rtol=1e-12, atol=1e-14)
 
 
+# ---------------------------------------------------------------------------
+# mu below mu_min: the clamp of the Tweedie factor (reading of Sec. 4 for
+# mu -> 0, where (v - mu) mu^(-p) has no finite value)
+# ---------------------------------------------------------------------------
+
+def _clamp_model(p, phi, mu_min, prior=oracle.PRIOR_EXPONENTIAL):
+    """Dense 5 x 6 data, K = 3, one block.  Row 1 of W is zero (mu = 0 on
+    the whole row) and row 3 is tiny (0 < mu < mu_min); the other rows have
+    mu well above mu_min.  For 1 < p < 2 two entries are zero (the point
+    mass of the compound Poisson law)."""
+    g = np.random.default_rng(int(10 * p) + 7)
+    I, J, K = 5, 6, 3
+    V = np.round(g.gamma(2.0, 1.5, size=(I, J)) * 64) / 64 + (0.25 if p >= 2 else 0.0)
+    if 1.0 < p < 2.0:
+        V[1, 2] = V[3, 0] = 0.0
+    W = g.uniform(0.5, 1.5, size=(I, K))
+    W[1] = 0.0
+    W[3] = 1e-3
+    H = g.uniform(0.5, 1.5, size=(K, J))
+    m = oracle.Oracle(I, J, K, 1, p, phi, prior_kind=prior, lambda_w=0.7, lambda_h=1.3,
+                      sigma_w=0.9, sigma_h=1.4)
+    m.set_options(mu_min=mu_min)
+    ii, jj, _ = datagen.dense_to_coo(V.astype(np.float32))
+    m.set_data(ii, jj, V.ravel())
+    m.set_factors(W, H)
+    return m, V, W, H
+
+
+@pytest.mark.parametrize("p", [1.0, 1.5, 2.0, 3.0])
+def test_mu_min_clamp_closed_form_on_zero_and_tiny_rows(p):
+    """With mu_min = 1e-2: a zero row of W has mu = 0 on every entry, so its
+    drift is, in closed form, mu_min^(-p) / phi * (sum_j v_ij h_j) - lambda_w
+    (the clamp enters the power only; the residual keeps the raw mu = 0),
+    and it adds nothing to H's drift (its w is zero).  A tiny row (0 < mu <
+    mu_min) has drift mu_min^(-p) / phi * sum_j (v_ij - mu_ij) h_j -
+    lambda_w.  Rows with mu > mu_min keep the unclamped Tweedie gradient,
+    checked against the textbook derivative of each density (Poisson
+    v/mu - 1, gamma (v - mu)/(phi mu^2), ...) written out per p."""
+    phi, mu_min, lam_w, lam_h = 0.8, 1e-2, 0.7, 1.3
+    m, V, W, H = _clamp_model(p, phi, mu_min)
+    dW, dH = m.drift(1)
+    mu = W @ H
+    assert mu[1].max() == 0.0 and 0.0 < mu[3].min() and mu[3].max() < mu_min
+    assert np.delete(mu, [1, 3], axis=0).min() > 10 * mu_min
+    # zero row: closed form, no max() anywhere
+    np.testing.assert_allclose(dW[1], mu_min ** (-p) / phi * (V[1] @ H.T) - lam_w, rtol=1e-12)
+    # tiny row: the power clamped, the residual raw
+    np.testing.assert_allclose(dW[3], mu_min ** (-p) / phi * ((V[3] - mu[3]) @ H.T) - lam_w,
+                               rtol=1e-12)
+    # the other rows, and H (row 1 adds e * 0 to it; row 3's clamped e enters
+    # H's drift times its tiny w)
+    with np.errstate(divide="ignore", invalid="ignore"):    # rows 1, 3 are replaced below
+        if p == 1.0:
+            E = (V / mu - 1.0) / phi             # d/dmu of the Poisson log-pmf, over phi
+        elif p == 2.0:
+            E = (V - mu) / (phi * mu ** 2)       # gamma with mean mu, shape 1/phi
+        else:
+            E = (V - mu) * mu ** (-p) / phi      # Tweedie mean-derivative for p = 1.5, 3
+    E[1] = V[1] * mu_min ** (-p) / phi
+    E[3] = (V[3] - mu[3]) * mu_min ** (-p) / phi
+    rows = [0, 2, 4]
+    np.testing.assert_allclose(dW[rows], (E @ H.T)[rows] - lam_w, rtol=1e-12)
+    np.testing.assert_allclose(dH, W.T @ E - lam_h, rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("p", [1.0, 2.0])
+def test_mu_min_clamp_is_inactive_above_mu_min(p):
+    """Factors whose mu all exceed 1e-2: the drift and the log-likelihood
+    with mu_min = 1e-2 equal those with the default 1e-10, bit for bit."""
+    m1, V, W, H = _clamp_model(p, 0.8, 1e-2)
+    W = W.copy()
+    W[1] = W[3] = 0.4
+    m1.set_factors(W, H)
+    m2 = oracle.Oracle(5, 6, 3, 1, p, 0.8, prior_kind=oracle.PRIOR_EXPONENTIAL, lambda_w=0.7,
+                       lambda_h=1.3)
+    m2.set_options(mu_min=1e-10)
+    ii, jj, _ = datagen.dense_to_coo(V.astype(np.float32))
+    m2.set_data(ii, jj, V.ravel())
+    m2.set_factors(W, H)
+    assert (W @ H).min() > 1e-2
+    a, b = m1.drift(1), m2.drift(1)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    assert m1.log_lik() == m2.log_lik()
+
+
+@pytest.mark.parametrize("p,phi", [(1.0, 1.0), (1.5, 0.7), (2.0, 0.5), (3.0, 0.8)])
+def test_mu_min_clamp_in_log_lik_is_the_density_at_mu_min(p, phi):
+    """log_lik clamps mu itself: an entry with mu < mu_min is scored as the
+    density at mu_min.  So log_lik - sum log f(v; max(mu, mu_min)) is the
+    same mu-free constant for factors with and without clamped entries
+    (f: scipy's Poisson, gamma and inverse-Gaussian densities, and the
+    compound Poisson-gamma for p = 1.5)."""
+    mu_min = 1e-2
+    m, V, W, H = _clamp_model(p, phi, mu_min)
+
+    def density(mu):
+        if p == 1.0:
+            return stats.poisson.logpmf(np.round(V), mu).sum()
+        if p == 2.0:
+            return stats.gamma.logpdf(V, a=1.0 / phi, scale=mu * phi).sum()
+        if p == 3.0:
+            lam = 1.0 / phi
+            return stats.invgauss.logpdf(V, mu / lam, scale=lam).sum()
+        return _compound_poisson_gamma_logpdf(V, mu, p, phi).sum()
+
+    if p == 1.0:
+        V = np.round(V)      # counts for the Poisson pmf
+        ii, jj, _ = datagen.dense_to_coo(V.astype(np.float32))
+        m.set_data(ii, jj, V.ravel())
+    # three factor sets: rows 1 (zero) and 3 (tiny) clamped; row 1 only;
+    # nothing clamped
+    Wb = W.copy()
+    Wb[3] = 0.6
+    Wc = Wb.copy()
+    Wc[1] = 0.6
+    diffs = []
+    for Wt in (W, Wb, Wc):
+        m.set_factors(Wt, H)
+        diffs.append(m.log_lik() - density(np.maximum(Wt @ H, mu_min)))
+    assert np.all(np.isfinite(diffs))
+    assert diffs[0] == pytest.approx(diffs[2], rel=1e-9, abs=1e-9)
+    assert diffs[1] == pytest.approx(diffs[2], rel=1e-9, abs=1e-9)
+
+
+@pytest.mark.parametrize("p", [1.0, 1.5, 2.0, 3.0])
+def test_mu_min_clamp_in_langevin_step_matches_numpy(p):
+    """The whole B = 1 step with a zero and a tiny row against the dense
+    numpy step (which clamps with np.maximum on its own)."""
+    phi, mu_min, eps, seed, t = 0.8, 1e-2, 1e-4, 5, 3
+    m, V, W, H = _clamp_model(p, phi, mu_min)
+    m.set_options(seed=seed, eps=eps, mu_min=mu_min)
+    m.set_factors(W, H)
+    m.part_step(t)
+    Wo, Ho = m.get_factors()
+    Zw = oracle.noise_matrix(seed, t, 0, 5, 3)
+    Zh = oracle.noise_matrix(seed, t, 1, 6, 3).T
+    Wn, Hn = _numpy_step(V, np.ones_like(V), W, H, p, phi, eps, 1.0, oracle.PRIOR_EXPONENTIAL,
+                         0.7, 1.3, 0.9, 1.4, Zw, Zh, mu_min=mu_min)
+    np.testing.assert_allclose(Wo, Wn, rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(Ho, Hn, rtol=1e-12, atol=1e-14)
+
+
 def test_mirroring_keeps_factors_non_negative():
     """Algorithm 1's mirroring: with a large step many raw updates go negative."""
     I, J, K = 8, 8, 4

@@ -229,8 +229,12 @@ PSGLD_API psgld_status psgld_batch_sweep(psgld_ctx *const *ctxs_host, int32_t n,
                                          void *stream);
 
 /* Monte Carlo posterior mean and variance of W (I x K) and H^T (J x K), FP64,
- * over the samples kept so far (population variance).  Any output pointer may
- * be NULL.  Waits for the context's last enqueued work. */
+ * over the samples kept so far (population variance): the Monte Carlo
+ * averages over the samples after burn-in that the paper reports for its
+ * audio experiment (Sec. 4, shared-memory setting, experiments on audio:
+ * the samples of the burn-in phase are discarded),
+ * here one sample per sweep.  Any output pointer may be NULL.  Waits for the
+ * context's last enqueued work. */
 PSGLD_API psgld_status psgld_posterior_mean(psgld_ctx *ctx, double *Wmean_host,
                                   double *Wvar_host, double *Hmean_host,
                                   double *Hvar_host, int64_t *n_samples_host);
@@ -243,7 +247,10 @@ PSGLD_API psgld_status psgld_posterior_mean(psgld_ctx *ctx, double *Wmean_host,
 PSGLD_API psgld_status psgld_log_lik(psgld_ctx *ctx, double *out_host, void *stream);
 
 /* sqrt(mean over observed entries of (v - mu)^2), FP64; mu from the current
- * factors (use_posterior_mean = 0) or from the posterior means (1). */
+ * factors (use_posterior_mean = 0) or from the posterior means (1).  The
+ * root mean squared error between V and W H that the paper monitors over
+ * the iterations of its MovieLens experiment (Sec. 4, distributed-hybrid
+ * setting), on the observed entries. */
 PSGLD_API psgld_status psgld_rmse(psgld_ctx *ctx, int32_t use_posterior_mean,
                         double *out_host, void *stream);
 
@@ -336,14 +343,20 @@ PSGLD_API int64_t psgld_estimate_device_bytes(int64_t I, int64_t J, int32_t K, i
  * synchronised.
  *
  * Limits and errors: nnz <= PSGLD_STATIC_MAX_NNZ, else PSGLD_ERR_SIZE;
- * PSGLD_ERR_ARG for other invalid arguments; PSGLD_ERR_CUDA if a launch
- * fails.  There is no context, so no message is recorded.
+ * PSGLD_ERR_ARG for other invalid arguments (nnz < 0, I, J or K < 1, a null
+ * pointer, phi <= 0, tweedie_p in (0, 1), mu_min <= 0); PSGLD_ERR_CUDA if a
+ * launch fails.  Entry indices are checked on the device: an entry with i
+ * outside [0, I) or j outside [0, J) is never read, and *out_dev becomes NaN.
+ * There is no context, so no message is recorded.
  *
  * The first call on a device looks up the scratch array's device address
- * (with that device current) and caches it: make that first call before any
- * stream capture.  All calls share the array; calls that can overlap on the
- * same GPU (different streams without ordering) race and must be serialised
- * by the caller.  Each call writes every partial slot it reads, so no state
+ * (with that device current) and caches it per device ordinal: make that
+ * first call before any stream capture.  The cached address is that of the
+ * device's primary context (the CUDA runtime's and PyTorch's); it is not
+ * valid after cudaDeviceReset or under a context made with the driver API.
+ * All calls share the array; calls that can overlap on the same GPU
+ * (different streams without ordering) race and must be serialised by the
+ * caller.  Each call writes every partial slot it reads, so no state
  * carries over from one call to the next. */
 #define PSGLD_STATIC_MAX_NNZ (4096ll * 4096ll)
 PSGLD_API psgld_status psgld_log_lik_static(int64_t nnz, const int32_t *i_dev,

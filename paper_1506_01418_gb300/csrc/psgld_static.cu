@@ -12,11 +12,19 @@
 // the library until the process exits.
 //
 // Set-up: the first call on a device looks up the array's device address
-// with cudaGetSymbolAddress (with that device current) and caches it; make
-// that first call before any stream capture.  Every call writes the partial
-// slots it reads, so nothing needs clearing between calls, but all calls
-// share the array: calls that can overlap on a device (different streams,
-// no ordering between them) race and must be serialised by the caller.
+// with cudaGetSymbolAddress (with that device current) and caches it per
+// device ordinal; make that first call before any stream capture.  The
+// cached address belongs to the device's primary context (the one the CUDA
+// runtime and PyTorch use): after cudaDeviceReset, or from a context created
+// by hand with the driver API, it is no longer valid.  Every call writes the
+// partial slots it reads, so nothing needs clearing between calls, but all
+// calls share the array: calls that can overlap on a device (different
+// streams, no ordering between them) race and must be serialised by the
+// caller.
+//
+// Entry indices are checked against I and J: an entry outside [0, I) x
+// [0, J) is not read, and its block's partial sum becomes NaN, so the result
+// is NaN (a caller's indexing mistake never reads outside its arrays).
 #include <mutex>
 
 #include "psgld_internal.cuh"
@@ -56,25 +64,32 @@ __device__ double block_sum(double x)
     return sm[0];
 }
 
-// Block b sums entries [4096 b, 4096 (b+1)) into partial[b].
+// Block b sums entries [4096 b, 4096 (b+1)) into partial[b]; NaN if one of
+// them has an index outside [0, I) x [0, J) (that entry is skipped).
 __global__ void __launch_bounds__(kThreads)
 static_ll_blocks(int64_t nnz, const int32_t *__restrict__ ii, const int32_t *__restrict__ jj,
                  const float *__restrict__ vv, const float *__restrict__ W,
-                 const float *__restrict__ Ht, int K, double p, double phi, double mu_min,
-                 double *__restrict__ partial)
+                 const float *__restrict__ Ht, int64_t I, int64_t J, int K, double p, double phi,
+                 double mu_min, double *__restrict__ partial)
 {
     const int64_t lo = blockIdx.x * kEntriesPerBlock;
     const int64_t hi = lo + kEntriesPerBlock < nnz ? lo + kEntriesPerBlock : nnz;
     double acc = 0.0;
+    int bad = 0;
     for (int64_t e = lo + threadIdx.x; e < hi; e += kThreads) {
         const int64_t i = ii[e], j = jj[e];
+        if (i < 0 || i >= I || j < 0 || j >= J) {
+            bad = 1;
+            continue;
+        }
         double mu = 0.0;
         for (int k = 0; k < K; ++k) mu += (double)W[i * K + k] * (double)Ht[j * K + k];
         if (p > 0.0 && mu < mu_min) mu = mu_min;
         acc -= static_beta_div((double)vv[e], mu, p) / phi;
     }
+    bad = __syncthreads_or(bad);
     const double s = block_sum(acc);
-    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+    if (threadIdx.x == 0) partial[blockIdx.x] = bad ? __longlong_as_double(0x7FF8000000000000ll) : s;
 }
 
 // One block adds partial[0 .. nblocks) in a fixed order.
@@ -121,8 +136,8 @@ extern "C" psgld_status psgld_log_lik_static(int64_t nnz, const int32_t *i_dev,
     cudaStream_t st = (cudaStream_t)stream;
     const int nblocks = nnz > 0 ? (int)((nnz + kEntriesPerBlock - 1) / kEntriesPerBlock) : 0;
     if (nblocks > 0)
-        static_ll_blocks<<<nblocks, kThreads, 0, st>>>(nnz, i_dev, j_dev, v_dev, W_dev, Ht_dev, K,
-                                                       tweedie_p, phi, mu_min, partial);
+        static_ll_blocks<<<nblocks, kThreads, 0, st>>>(nnz, i_dev, j_dev, v_dev, W_dev, Ht_dev, I, J,
+                                                       K, tweedie_p, phi, mu_min, partial);
     static_ll_final<<<1, kThreads, 0, st>>>(nblocks, partial, out_dev);
     if (cudaGetLastError() != cudaSuccess) return PSGLD_ERR_CUDA;
     return PSGLD_OK;

@@ -7,9 +7,14 @@ from paper_1506_01418_gb300 import datagen
 from paper_1506_01418_gb300 import psgld as P
 
 # One FP32 part-step against the FP64 oracle, from identical factors and with
-# the identical Philox stream: max |gpu - oracle| / max(|oracle|, floor), with
-# the floor 1e-2 x the RMS of the oracle's matrix, so that elements the mirror
-# or the noise moved through zero are judged on the matrix's own scale.
+# the identical Philox stream (step_errors): element by element, |gpu -
+# oracle| <= 1e-5 x max(|oracle|, |x0|, sqrt(2 eps) |z|, eps D_abs), the
+# largest magnitude among the terms the GPU adds in FP32 to form x0 + eps
+# (S sum_j e_j h_j + prior) + sqrt(2 eps) z, with D_abs = S sum_j |e_j| |h_j|
+# + |prior gradient| the absolute sum of the drift's terms: every rounding
+# error of the step (the FP32 sums of the drift included) is a few ulps of
+# one of those magnitudes, times the number of terms summed.  No floor taken
+# from the matrix as a whole.
 STEP_RTOL = 1e-5
 
 U_BF16 = 2.0 ** -8
@@ -33,6 +38,37 @@ def recovered_drift(x_new, x0, z, D_or, eps, mirror):
     return D, mask, rec
 
 
+def step_errors(x_gpu, x_or, x0, z, sd, eps_dabs=None):
+    """Errors of one part-step of one factor (arrays of one layout), from the
+    same FP32 x0 and the same Philox normals z on both sides.
+
+    elem: max |gpu - or| / max(|or|, |x0|, sd |z|, eps_dabs) (see STEP_RTOL;
+        eps_dabs = eps D_abs, or None when the drift is small beside x0);
+    inc: max |dx_gpu - dx_or| / max |dx_or|, dx = new - x0: the error of the
+        increment (eps drift + noise, mirrored) on the increment's own scale;
+    inc_bound: the bound inc is held to -- 1e-5 for the arithmetic of the
+        increment (FP32 sums of the drift, the FP32 Box-Muller of the
+        normals; on the scale of eps D_abs where that exceeds the largest
+        increment, i.e. where the drift's terms cancel) plus the rounding of
+        the stored FP32 result, 2^-24 of the largest |x| twice (the step's
+        FMA chain and the final store), on the increment's scale."""
+    x_gpu = np.asarray(x_gpu, dtype=np.float64)
+    x_or = np.asarray(x_or, dtype=np.float64)
+    x0 = np.asarray(x0, dtype=np.float64)
+    if x_or.size == 0:
+        return 0.0, 0.0, STEP_RTOL
+    scale = np.maximum(np.maximum(np.abs(x_or), np.abs(x0)), sd * np.abs(z)) + 1e-300
+    if eps_dabs is not None:
+        scale = np.maximum(scale, eps_dabs)
+    err = np.abs(x_gpu - x_or)
+    elem = float(np.max(err / scale))
+    dmax = float(np.max(np.abs(x_or - x0))) + 1e-300
+    inc = float(np.max(err)) / dmax
+    terms = 1.0 if eps_dabs is None else max(1.0, float(np.max(eps_dabs)) / dmax)
+    inc_bound = STEP_RTOL * terms + 2 * U_FP32 * float(np.max(np.abs(x_or))) / dmax
+    return elem, inc, inc_bound
+
+
 def rel_err(a, b):
     a = np.asarray(a, dtype=np.float64)
     b = np.asarray(b, dtype=np.float64)
@@ -50,6 +86,13 @@ class Pair:
         import torch
         self.torch = torch
         self.I, self.J, self.K, self.B = I, J, K, B
+        self.seed = seed
+        self.p, self.phi, self.prior_kind = p, phi, prior_kind
+        self.lam, self.sig = lam, sig
+        self.mu_min = opts.get("mu_min", 1e-10)
+        self.i = np.asarray(i, dtype=np.int64)
+        self.j = np.asarray(j, dtype=np.int64)
+        self.v = np.asarray(v, dtype=np.float64)
         self.gpu = P.PSGLD(I, J, K, B, p, phi, prior_kind=prior_kind, lambda_w=lam[0],
                            lambda_h=lam[1], sigma_w=sig[0], sigma_h=sig[1], seed=seed,
                            eps=eps, use_graphs=use_graphs, **opts)
@@ -91,6 +134,54 @@ class Pair:
         Wg, Hg = self.gpu_factors()
         Wo, Ho = self.orc.get_factors()
         return (Wg, Hg), (Wo, Ho)
+
+    def abs_drift(self, t, W, H):
+        """D_abs of iteration t at factors W (I x K), H (K x J): S sum_j |e_ij|
+        |h_j| over the part's entries plus |prior gradient|, for W and H,
+        written here from the definitions (pieces floor(r n / B), part s =
+        the oracle's part index at t)."""
+        B, p = self.B, self.p
+        rs = np.array([(r * self.I) // B for r in range(B + 1)])
+        cs = np.array([(r * self.J) // B for r in range(B + 1)])
+        rp = np.searchsorted(rs, self.i, side="right") - 1
+        cp = np.searchsorted(cs, self.j, side="right") - 1
+        m = ((cp - rp) % B) == self.orc.part_index(t)
+        i, j, v = self.i[m], self.j[m], self.v[m]
+        Ht = H.T
+        mu = np.einsum("nk,nk->n", W[i], Ht[j])
+        fac = 1.0 if p == 0 else np.maximum(mu, self.mu_min) ** (-p)
+        ea = np.abs(v - mu) * fac / self.phi
+        GW = np.zeros_like(W)
+        GH = np.zeros_like(Ht)
+        np.add.at(GW, i, ea[:, None] * np.abs(Ht[j]))
+        np.add.at(GH, j, ea[:, None] * np.abs(W[i]))
+        S = self.orc.scale(t)
+        if self.prior_kind == 0:
+            pw, ph = self.lam[0], self.lam[1]
+        else:
+            pw, ph = np.abs(W) / self.sig[0] ** 2, np.abs(H) / self.sig[1] ** 2
+        return S * GW + pw, (S * GH).T + ph
+
+    def step_and_check(self, t, W0=None, H0=None, part=None):
+        """One part-step on both sides from the current (or the given)
+        factors; asserts step_errors for W and H and returns the GPU's new
+        factors.  part: the part drawn at t (size-proportional mode), only
+        for the message."""
+        if W0 is not None:
+            self.set_factors(W0, H0)
+        W0, H0 = self.orc.get_factors()
+        eps = self.orc.eps(t)
+        sd = float(np.sqrt(2.0 * eps))
+        aW, aH = self.abs_drift(t, W0, H0)
+        (Wg, Hg), (Wo, Ho) = self.step_both(t)
+        zW = oracle.noise_matrix(self.seed, t, 0, self.I, self.K)
+        zH = oracle.noise_matrix(self.seed, t, 1, self.J, self.K).T
+        for xg, xo, x0, z, ad, what in ((Wg, Wo, W0, zW, aW, "W"), (Hg, Ho, H0, zH, aH, "H")):
+            elem, inc, inc_b = step_errors(xg, xo, x0, z, sd, eps * ad)
+            assert np.all(np.isfinite(xg)), (t, what, "non-finite")
+            assert elem <= STEP_RTOL, (t, part, what, "element", elem)
+            assert inc <= inc_b, (t, part, what, "increment", inc, inc_b)
+        return Wg, Hg
 
     def sync_oracle_to_gpu(self):
         Wg, Hg = self.gpu_factors()

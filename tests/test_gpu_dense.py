@@ -17,6 +17,8 @@ FP32 precision.  What is checked:
 * full chains: posterior-mean reconstruction RMSE within 1% of the FP64
   oracle chain (the configured dense Poisson NMF workload, 256 x 256, K = 8,
   B = 4);
+* mu below mu_min (zero and tiny rows of W, zero columns of H): the drift
+  within the same bound (the clamp enters its de/dmu), every output finite;
 * graph replay == direct launches bit for bit; log-likelihood and RMSE over
   the dense data match the oracle in FP64; refused inputs;
 * the single-pass kernel with GEMM1 on E4M3 (FP8) copies of the factors,
@@ -138,6 +140,48 @@ def test_dense_part_step_drift_within_bf16_bound(name, kernel):
         if mirror:
             assert Wg.min() >= 0 and Hg.min() >= 0
         pr.sync_oracle_to_gpu()
+
+
+@pytest.mark.parametrize("p", [1.0, 1.5, 2.0, 3.0])
+@pytest.mark.parametrize("kernel", ["single_pass", "two_sided", "two_sided_bf16v"])
+def test_dense_mu_below_mu_min_drift_within_bound(kernel, p):
+    """mu below mu_min = 1e-2 on the tensor cores: every 5th row of W and
+    every 7th column of H zero (mu = 0 exactly: BF16 keeps zeros, so e =
+    v mu_min^(-p) / phi up to the rounding of e), every 5th row from the
+    second tiny (0 < mu < mu_min).  The recovered drift stays within the
+    BF16 bound (which takes max(mu - dmu, mu_min) in de/dmu), every output
+    is finite, and on the zero rows and columns -- where the clamped factor
+    is the whole signal -- the drift is far larger than the bound."""
+    I, J, K, B, phi, eps, mu_min, seed = 140, 170, 24, 2, 0.8, 1e-4, 1e-2, 7
+    V = _data(I, J, "gamma", p, seed=I)
+    i, j, v = datagen.dense_to_coo(V)
+    W0, H0 = datagen.init_factors(I, J, K, seed=3, scale=0.4, nonneg=True)
+    W0[::5] = 0.0
+    W0[1::5] = 1e-5
+    H0[:, ::7] = 0.0
+    pr = Pair(I, J, K, B, p, phi, i, j, v, W0, H0, prior_kind=0, lam=(0.8, 1.2), seed=seed,
+              eps=eps, V=V, mu_min=mu_min, **KERNELS[kernel])
+    v_bf16 = bool(KERNELS[kernel].get("dense_v_bf16", 0))
+    for t in range(1, B + 1):
+        pr.set_factors(W0, H0)
+        Wc, Hc = pr.orc.get_factors()
+        D_W, D_H = pr.orc.drift(t)
+        S = pr.orc.scale(t)
+        bW, bH = dense_drift_bound(V, Wc, Hc, t, B, p, phi, S, mu_min=mu_min, v_bf16=v_bf16)
+        pr.gpu.part_step(t)
+        Wg, Hg = pr.gpu_factors()
+        assert np.all(np.isfinite(Wg)) and np.all(np.isfinite(Hg))
+        zW = oracle.noise_matrix(seed, t, 0, I, K)
+        zH = oracle.noise_matrix(seed, t, 1, J, K).T
+        for xg, x0, z, D, bnd, zero, what in ((Wg, Wc, zW, D_W, bW, np.s_[::5, :], "W"),
+                                               (Hg, Hc, zH, D_H, bH, np.s_[:, ::7], "H")):
+            Dg, mask, rec = recovered_drift(xg.astype(np.float64), x0, z, D, eps, True)
+            err = np.abs(Dg - D)
+            bad = mask & (err > bnd + rec)
+            assert not bad.any(), (kernel, p, t, what, int(bad.sum()))
+            zm = mask[zero]
+            assert zm.mean() > 0.5
+            assert np.sqrt(np.mean(D[zero][zm] ** 2)) > 4 * np.sqrt(np.mean(bnd[zero][zm] ** 2))
 
 
 @pytest.mark.parametrize("kernel", ["single_pass", "two_sided"])

@@ -27,7 +27,7 @@ import pytest
 
 import bench
 import oracle
-from gpu_helpers import STEP_RTOL, dense_drift_bound, recovered_drift, rel_err
+from gpu_helpers import STEP_RTOL, dense_drift_bound, recovered_drift, rel_err, step_errors
 from paper_1506_01418_gb300 import psgld as P
 
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
@@ -57,14 +57,20 @@ def _gpu_factors(chain):
     return W.cpu().numpy().astype(np.float64), Ht.cpu().numpy().T.astype(np.float64)
 
 
-def _two_part_steps(chain, orc):
+def _two_part_steps(chain, orc, seed=1000):
+    I, K = orc.I, orc.K
     for t in (1, 2):
+        W0, H0 = orc.get_factors()
         chain.part_step(t)
         orc.part_step(t)
         Wg, Hg = _gpu_factors(chain)
         Wo, Ho = orc.get_factors()
-        ew, eh = rel_err(Wg, Wo), rel_err(Hg, Ho)
-        assert ew <= STEP_RTOL and eh <= STEP_RTOL, (t, ew, eh)
+        sd = float(np.sqrt(2.0 * orc.eps(t)))
+        zW = oracle.noise_matrix(seed, t, 0, I, K)
+        zH = oracle.noise_matrix(seed, t, 1, orc.J, K).T
+        for xg, xo, x0, z, what in ((Wg, Wo, W0, zW, "W"), (Hg, Ho, H0, zH, "H")):
+            elem, inc, inc_b = step_errors(xg, xo, x0, z, sd)
+            assert elem <= STEP_RTOL and inc <= inc_b, (t, what, elem, inc, inc_b)
         orc.set_factors(Wg, Hg)
 
 

@@ -3,23 +3,28 @@
 
 A step is one sweep: B part-steps (Algorithm 1 iterations) that together
 visit every observed entry once, plus the FP64 posterior accumulation.  The
-default workload is the sparse Gaussian matrix factorisation shaped like the
-paper's MovieLens experiment: I = 70000, J = 10000, 10M observed entries with
-Zipf(1.1) row and column degrees, K = 50, B = 32 (synthetic data, seeded).
+default workload is the largest single-GPU configuration: sparse Gaussian
+matrix factorisation, I = 480000, J = 18000, 10^8 observed entries with
+Zipf(1.2) row degrees, K = 100, B = 64 (synthetic data, seeded), FP32, with
+the BF16-gathered-factor arm beside it at the same posterior RMSE.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 Our arm: value = N_obs * ranks / (max over ranks of the mean sweep time),
 each sweep timed with CUDA events on the launching stream, with L2 flushed
-(256 MB written) before every timed sweep.  Per-kernel durations for the
-roofline come from a separate, untimed pass with events around every launch.  Ranks (torchrun, one per GPU) run
+(256 MB written) before every timed sweep.  The roofline's part-step time is
+the timed sweep divided by B (it includes 1/B of the sweep's posterior
+accumulation); the split between the gradient and the update kernel comes
+from a separate, untimed pass with events around every launch.  Ranks (torchrun, one per GPU) run
 independent replica chains: the sampler needs no collective.  Extra keys:
 roofline of the part-step kernel, the oracle's CPU baseline, an end-to-end
 job through the C ABI from pinned host buffers, SM clocks during the run.
 
 Reference arm (--impl reference): the FP64 CPU oracle, as it stands, on the
 host cores, on the same workload; each step is a bounded sample of
-part-steps.  Under torchrun only rank 0 runs it.
+part-steps (for the 10^8-entry workload, of its first 4 x 4 blocks as a
+B = 4 problem: the same blocks, so the same work per entry).  Under
+torchrun only rank 0 runs it.
 """
 from __future__ import annotations
 
@@ -87,7 +92,7 @@ WORKLOADS["batched_dense_nmf_256chains_513xJ200-5000_K32_B8_bf16"] = dict(
 # kernel's full ncu capture (340 MB of V, a few seconds of replay)
 WORKLOADS["batched_dense_nmf_64chains_513xJ200-5000_K32_B8_bf16"] = dict(
     WORKLOADS["batched_dense_nmf_256chains_513xJ200-5000_K32_B8_bf16"], chains=64, dense_path=1)
-DEFAULT_WORKLOAD = "sparse_gauss_70000x10000_nnz10M_K50_B32"
+DEFAULT_WORKLOAD = "sparse_gauss_480000x18000_nnz100M_K100_B64"
 
 
 # ---------------------------------------------------------------------------
@@ -246,12 +251,13 @@ def new_chain(wl: dict, seed: int, **opts):
 
 def part_step_bytes(wl: dict, part_sizes) -> float:
     """Algorithmic HBM bytes of one part-step, averaged over the B parts:
-    each observed entry of the part once (int32 index + fp32 value), one
-    int32 row offset per row and block, and every factor element read and
-    written once in fp32."""
+    each observed entry of the part once (int32 index + fp32 value, 8 n_Pi),
+    one int32 row offset per row and block (4 (I + B)), every factor element
+    read and written once in fp32 (8 (I + J) K), and the column-gradient
+    scratch G_H zeroed and read once (8 J K)."""
     I, J, K, B = wl["I"], wl["J"], wl["K"], wl["B"]
     mean_n = sum(part_sizes) / len(part_sizes)
-    return 8.0 * mean_n + 4.0 * (I + B) + 8.0 * (I + J) * K
+    return 8.0 * mean_n + 4.0 * (I + B) + 8.0 * (I + J) * K + 8.0 * J * K
 
 
 def part_step_flops(wl: dict) -> float:
@@ -330,10 +336,34 @@ def oracle_rate(m, wl, t0: int, n_steps: int):
     return ent / dt, ent, dt
 
 
+# above this many entries the oracle runs on a sample of the workload: its
+# first SAMPLE_PIECES x SAMPLE_PIECES blocks as a B = SAMPLE_PIECES problem
+# (the same blocks, with their entries and factor rows, so the same work per
+# entry); loading all 10^8 entries into the oracle would take minutes
+SAMPLE_ABOVE_NNZ = 20_000_000
+SAMPLE_PIECES = 4
+
+
+def oracle_sample(wl, i, j, v, W0, H0):
+    """(workload, i, j, v, W0, H0, description) the oracle runs on: the whole
+    workload, or for the largest ones its first SAMPLE_PIECES^2 blocks."""
+    import numpy as np
+    if len(v) <= SAMPLE_ABOVE_NNZ:
+        return wl, i, j, v, W0, H0, "the workload"
+    B, R = wl["B"], SAMPLE_PIECES
+    I1, J1 = (R * wl["I"]) // B, (R * wl["J"]) // B
+    keep = (np.asarray(i) < I1) & (np.asarray(j) < J1)
+    sub = dict(wl, I=I1, J=J1, B=R, nnz=int(keep.sum()))
+    what = (f"its first {R} x {R} blocks ({I1} x {J1}, {int(keep.sum())} entries) "
+            f"as a B = {R} problem")
+    return sub, np.asarray(i)[keep], np.asarray(j)[keep], np.asarray(v)[keep], W0[:I1], H0[:, :J1], what
+
+
 def cpu_baseline(wl, i, j, v, W0, H0, seed, budget_s: float):
     """The oracle on the host cores (OpenMP over the blocks of a part), then
     single-threaded on a quarter of the budget; both give identical results."""
     import oracle
+    wl, i, j, v, W0, H0, what = oracle_sample(wl, i, j, v, W0, H0)
     m = oracle_setup(wl, i, j, v, W0, H0, seed)
     cores = oracle.set_threads(0)
     _, _, dt1 = oracle_rate(m, wl, 1, 1)          # calibration (untimed)
@@ -345,8 +375,8 @@ def cpu_baseline(wl, i, j, v, W0, H0, seed, budget_s: float):
     rate1, ent1, dts = oracle_rate(m, wl, 3 + n, n1)
     oracle.set_threads(cores)
     return {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{n} part-steps ({ent} observed entries, {dt:.1f} s) of the same "
-                      f"workload and data, FP64, OpenMP over the blocks of each part",
+            "sample": f"{n} part-steps ({ent} observed entries, {dt:.1f} s) of {what}, "
+                      f"same data, FP64, OpenMP over the blocks of each part",
             "single_thread": {"value": rate1, "unit": UNIT, "cores": 1,
                               "sample": f"{n1} part-steps ({ent1} entries, {dts:.1f} s)"}}
 
@@ -472,13 +502,22 @@ def run_ours(args, wl_name, wl):
                     "peak_source": f"{peak_src} sustained cuBLAS BF16 GEMM (kernel timed "
                                    f"inside a long sweep)"}
     else:
+        # the part-step's time from the timed sweeps themselves (sweep / B,
+        # which also holds 1/B of the posterior accumulation), so that it
+        # never exceeds the sweep it belongs to; the profiled pass only
+        # gives the split between the two kernels
         bytes_launch = part_step_bytes(wl, part_sizes)
-        achieved = bytes_launch / (kern_ms / 1e3) / 1e9
+        part_ms = ms_local / wl["B"]
+        achieved = bytes_launch / (part_ms / 1e3) / 1e9
+        share = grad_ms / max(kern_ms, 1e-12)
         roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                     "frac": achieved / hbm_peak, "traffic": kernel_traffic(wl_name),
-                    "kernel": "part_step_kernel", "kernel_ms": kern_ms,
-                    "grad_kernel_ms": grad_ms, "update_kernel_ms": upd_ms,
+                    "kernel": "part_step (gradient kernel + update kernel)", "kernel_ms": part_ms,
+                    "kernel_ms_source": "timed sweeps / B",
+                    "grad_share": share, "update_share": 1.0 - share,
+                    "profiled_grad_kernel_ms": grad_ms, "profiled_update_kernel_ms": upd_ms,
                     "algorithmic_bytes_per_launch": bytes_launch,
+                    "bytes_formula": "8 n_Pi + 4 (I + B) + 8 (I + J) K + 8 J K",
                     "peak_source": f"{peak_src} HBM copy bandwidth"}
 
     result = {
@@ -1220,6 +1259,8 @@ def run_reference(args, wl_name, wl):
         what = f"one {r1} x {c1} block of the workload as a B = 1 problem"
     else:
         hi, hj, hv = (x.cpu().numpy() for x in (i, j, v))
+        if what == "the workload":
+            run_wl, hi, hj, hv, W0, H0, what = oracle_sample(run_wl, hi, hj, hv, W0, H0)
     m = oracle_setup(run_wl, hi, hj, hv.astype(np.float64), W0.astype(np.float64),
                      H0.astype(np.float64), seed)
     wl = run_wl

@@ -54,7 +54,36 @@ def test_single_rank_aggregate_is_identity():
 def test_part_step_bytes():
     wl = dict(I=100, J=50, K=10, B=4)
     # 8 bytes per entry + 4 per row offset + factors read and written in fp32
-    assert bench.part_step_bytes(wl, [10, 20, 30, 40]) == 8 * 25 + 4 * 104 + 8 * 150 * 10
+    # + the column-gradient scratch zeroed and read (8 J K)
+    assert bench.part_step_bytes(wl, [10, 20, 30, 40]) == \
+        8 * 25 + 4 * 104 + 8 * 150 * 10 + 8 * 50 * 10
+
+
+def test_oracle_sample_keeps_the_first_blocks():
+    """Above SAMPLE_ABOVE_NNZ entries the oracle runs on the first R x R
+    blocks (rows and columns of the first R pieces) as a B = R problem."""
+    import numpy as np
+    wl = dict(I=64, J=32, K=3, B=16, nnz=0)
+    g = np.random.default_rng(0)
+    cells = g.choice(64 * 32, size=900, replace=False)
+    i, j = (cells // 32).astype(np.int32), (cells % 32).astype(np.int32)
+    v = g.uniform(1, 5, size=900).astype(np.float32)
+    W0, H0 = g.uniform(size=(64, 3)), g.uniform(size=(3, 32))
+    same = bench.oracle_sample(wl, i, j, v, W0, H0)
+    assert same[0] is wl and same[6] == "the workload"
+    old = bench.SAMPLE_ABOVE_NNZ
+    try:
+        bench.SAMPLE_ABOVE_NNZ = 100
+        sub, si, sj, sv, sW, sH, what = bench.oracle_sample(wl, i, j, v, W0, H0)
+    finally:
+        bench.SAMPLE_ABOVE_NNZ = old
+    R = bench.SAMPLE_PIECES
+    assert (sub["I"], sub["J"], sub["B"]) == (R * 64 // 16, R * 32 // 16, R)
+    keep = (i < sub["I"]) & (j < sub["J"])
+    assert np.array_equal(si, i[keep]) and np.array_equal(sv, v[keep]) and sub["nnz"] == keep.sum()
+    assert sW.shape == (sub["I"], 3) and sH.shape == (3, sub["J"])
+    # each block of the sample is a block of the workload: same piece sizes
+    assert sub["I"] // sub["B"] == wl["I"] // wl["B"] and sub["J"] // sub["B"] == wl["J"] // wl["B"]
 
 
 def test_clock_summary_window_and_reasons():

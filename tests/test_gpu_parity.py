@@ -6,9 +6,9 @@
   increment (new - old factors) within 1e-5 of its own largest element plus
   the FP32 rounding of the stored result (see gpu_helpers.step_errors), for
   every part of a sweep, across team shapes (K = 1 .. 512), Tweedie powers,
-  both priors, ragged piece sizes, rows split over several work records,
-  empty parts, mu below mu_min (zero and tiny rows and columns) and the
-  decaying step size eps_t = (a/t)^b;
+  both priors, ragged piece sizes, rows split over many work units, empty
+  parts, frozen factors, mu below mu_min (zero and tiny rows and columns)
+  and the decaying step size eps_t = (a/t)^b;
 * graph replay == direct launches, bit for bit;
 * log-likelihood, RMSE and posterior moments against the oracle.
 """
@@ -72,11 +72,17 @@ CASES = {
     "gauss_K32_BminIJ": (9, 12, 32, 9, 0.0, 1.0, 1, ("sparse", 80), 1e-3),
     "poisson_K64": (100, 80, 64, 4, 1.0, 1.0, 0, ("sparse", 4000), 1e-4),
     "empty_data": (20, 30, 6, 3, 1.0, 1.0, 0, ("sparse", 0), 1e-2),
+    # rows whose entries in a part span many work units of the gradient
+    # kernel (their partial sums added in unit order by the update kernel),
+    # with K = 24 (one float4 group per lane) and K = 200 (several)
+    "heavy_rows_B1_K24": (40, 1500, 24, 1, 1.0, 1.0, 0, ("dense", "poisson"), 1e-4),
+    "heavy_rows_K200_B2": (30, 1100, 200, 2, 0.0, 1.0, 1, ("dense", "gamma"), 1e-4),
 }
 
 
 def _make(name, use_graphs=1, seed=7, **opts):
     I, J, K, B, p, phi, kind, data, eps = CASES[name]
+    eps = opts.pop("eps", eps)
     if data[0] == "dense":
         i, j, v = dense_case(I, J, 3, seed=I, kind=data[1])
         if p >= 2:
@@ -193,6 +199,21 @@ def test_noise_stream_matches_oracle():
                                rtol=2e-6, atol=2e-6)
 
 
+@pytest.mark.parametrize("frozen", ["W", "H"])
+def test_frozen_factor_matches_oracle(frozen):
+    """freeze_W / freeze_H: the frozen factor stays bit for bit, the other
+    one steps as the oracle's does."""
+    opts = {"freeze_W": 1} if frozen == "W" else {"freeze_H": 1}
+    pr = _make("gauss_sparse_K50_split", **opts)
+    W0, H0 = pr.gpu_factors()
+    for t in range(1, 4):
+        pr.step_and_check(t)
+        pr.sync_oracle_to_gpu()
+    W1, H1 = pr.gpu_factors()
+    assert np.array_equal(W1, W0) == (frozen == "W")
+    assert np.array_equal(H1, H0) == (frozen == "H")
+
+
 def test_frozen_factor_is_unchanged():
     pr = _make("gauss_sparse_K50_split", freeze_H=1)
     Wb, Hb = pr.gpu_factors()
@@ -206,7 +227,8 @@ def test_frozen_factor_is_unchanged():
 # sweeps: graphs vs launches, posterior sums, diagnostics
 # ---------------------------------------------------------------------------
 
-@pytest.mark.parametrize("name", ["gauss_sparse_K50_split", "poisson_K1_B7", "gamma_K13"])
+@pytest.mark.parametrize("name", ["gauss_sparse_K50_split", "poisson_K1_B7", "gamma_K13",
+                                  "heavy_rows_B1_K24"])
 def test_graph_replay_equals_direct_launches(name):
     a = _make(name, use_graphs=1, burn_in_sweeps=1)
     b = _make(name, use_graphs=0, burn_in_sweeps=1)

@@ -129,6 +129,18 @@ typedef struct {
                                * it runs (a long-running chain beside short jobs);
                                * 0: every SM.  psgld_batch_sweep's shared launches
                                * use every SM regardless. */
+    int32_t debug_wait_polls; /* for testing the timeout path; 0 (the default): the
+                               * normal limit of every bounded device wait (2^24
+                               * polls or about one second of SM clock).  > 0: the
+                               * sparse gradient kernel's first wait for its row
+                               * gathers makes at most this many polls, without
+                               * suspending, before it gives up -- a wait that runs
+                               * out on purpose: the kernel sets the context's error
+                               * flag, waits for its own copies with the normal
+                               * limit, and the next synchronising call returns
+                               * PSGLD_ERR_TIMEOUT naming the kernel and the wait.
+                               * The part-step's result is then undefined; the
+                               * context stays usable (set the factors again). */
 } psgld_options;
 
 /* Device memory.  By default the library allocates with cudaMalloc and frees

@@ -116,7 +116,7 @@ psgld_status check_kernel_flag(psgld_ctx *c)
     if (h == 0) return PSGLD_OK;
     PSGLD_CK(c, cudaMemset(c->kflag, 0, sizeof(int)));
     std::string where;
-    if (h & 16) where += " sparse gradient kernel (row gathers);";
+    if (h & 16) where += " sparse gradient kernel (wait for the row gathers);";
     if (h & 32) where += " single-pass dense kernel (MMA completion);";
     if (h & 64) where += " two-sided dense kernel";
     if (h & 128) where += " (producer: free slot)";
@@ -383,6 +383,7 @@ psgld_status psgld_set_options(psgld_ctx *c, const psgld_options *o)
     if (o->dense_fp8 != 0 && o->dense_fp8 != 1) return fail(c, PSGLD_ERR_ARG, "dense_fp8 must be 0 or 1");
     if (o->gather_bf16 != 0 && o->gather_bf16 != 1) return fail(c, PSGLD_ERR_ARG, "gather_bf16 must be 0 or 1");
     if (o->max_sms < 0) return fail(c, PSGLD_ERR_ARG, "max_sms must be >= 0");
+    if (o->debug_wait_polls < 0) return fail(c, PSGLD_ERR_ARG, "debug_wait_polls must be >= 0");
     c->opt = *o;
     destroy_graphs(c);
     destroy_events(c);

@@ -76,6 +76,7 @@ struct GradParams {
     float phi_inv, p, mu_min;
     int p_mode;               // 0: p = 0, 1: p = 1, 2: p = 2, 3: other
     int *err;                 // set to 16 when a bulk copy wait runs out
+    uint32_t wait_polls;      // > 0: the first wait's poll limit (no suspension), for tests
 };
 
 struct UpdSide {
@@ -222,6 +223,17 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity, ui
     return ok != 0;
 }
 
+// One poll of phase `parity` of the barrier, without suspending.
+__device__ __forceinline__ bool mbar_test_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile("{\n\t.reg .pred p;\n\t"
+                 "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok) : "r"(smem_addr(bar)), "r"(parity) : "memory");
+    return ok != 0;
+}
+
 // Bulk copy of `bytes` (a multiple of 16, both addresses 16-byte aligned)
 // from global to this CTA's shared memory, completing on `bar`.
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
@@ -293,8 +305,13 @@ __device__ __forceinline__ void grad_unit(const GradParams &P, int64_t u, float 
     }
     bool done = false;
     const long long t_start = clock64();
-    for (uint32_t it = 0; it < kWaitLimit && !done && clock64() - t_start < kWaitCycles; ++it)
-        done = mbar_try_wait(bar, 0, kWaitHintNs);
+    if (P.wait_polls) {
+        // a test limit: at most wait_polls polls, without suspending
+        for (uint32_t it = 0; it < P.wait_polls && !done; ++it) done = mbar_test_wait(bar, 0);
+    } else {
+        for (uint32_t it = 0; it < kWaitLimit && !done && clock64() - t_start < kWaitCycles; ++it)
+            done = mbar_try_wait(bar, 0, kWaitHintNs);
+    }
     if (!__all_sync(0xffffffffu, done)) {
         // The copies did not land: report it, wait (bounded again) for them
         // so that no copy targets freed shared memory, and give up.
@@ -718,6 +735,7 @@ static void fill_params(psgld_ctx *c, int part, int64_t t, const int64_t *t_dev,
     GP.mu_min = (float)c->opt.mu_min;
     GP.p_mode = c->p == 0.0 ? 0 : c->p == 1.0 ? 1 : c->p == 2.0 ? 2 : 3;
     GP.err = c->kflag;
+    GP.wait_polls = (uint32_t)c->opt.debug_wait_polls;
 
     UP.t_dev = t_dev;
     UP.t_add = t_dev ? t_add : t;

@@ -50,7 +50,8 @@ class psgld_options(C.Structure):
                 ("burn_in_sweeps", C.c_int64), ("use_graphs", C.c_int32),
                 ("profile", C.c_int32), ("dense_path", C.c_int32),
                 ("dense_v_bf16", C.c_int32), ("part_mode", C.c_int32),
-                ("dense_fp8", C.c_int32), ("gather_bf16", C.c_int32), ("max_sms", C.c_int32)]
+                ("dense_fp8", C.c_int32), ("gather_bf16", C.c_int32), ("max_sms", C.c_int32),
+                ("debug_wait_polls", C.c_int32)]
 
 
 class psgld_job(C.Structure):

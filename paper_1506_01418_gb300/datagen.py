@@ -69,6 +69,65 @@ def dense_gamma_device(I: int, J: int, K_true: int, seed: int, device):
     return (M * noise).contiguous()
 
 
+def compound_poisson_gamma_params(mu, p: float, phi: float):
+    """(lam, alpha, scale) of the compound Poisson-gamma law with mean mu,
+    dispersion phi and power p in (1, 2) -- the observation model of the
+    paper's Sec. 4 for 0 < beta < 1 (p = 2 - beta): v is the sum of N ~
+    Poisson(lam) independent Gamma(alpha, scale) draws, with lam =
+    mu^(2-p) / (phi (2-p)), alpha = (2-p)/(p-1), scale = phi (p-1) mu^(p-1),
+    so that E v = mu, Var v = phi mu^p and P(v = 0) = exp(-lam)."""
+    lam = mu ** (2.0 - p) / (phi * (2.0 - p))
+    alpha = (2.0 - p) / (p - 1.0)
+    scale = phi * (p - 1.0) * mu ** (p - 1.0)
+    return lam, alpha, scale
+
+
+def compound_poisson_gamma(mu, p: float, phi: float, g: np.random.Generator):
+    """Draws of the compound Poisson-gamma law (one per element of mu): N ~
+    Poisson(lam), and given N > 0 the sum of N Gamma(alpha, scale) draws,
+    which is one Gamma(N alpha, scale) draw; 0 when N = 0."""
+    mu = np.asarray(mu, dtype=np.float64)
+    lam, alpha, scale = compound_poisson_gamma_params(mu, p, phi)
+    n = g.poisson(lam)
+    pos = n > 0
+    v = g.gamma(np.where(pos, n * alpha, 1.0), scale)
+    return np.where(pos, v, 0.0)
+
+
+def dense_compound_poisson(I: int, J: int, K_true: int, seed: int, p: float = 1.5,
+                           phi: float = 1.0):
+    """Dense non-negative data with exact zeros: W*, H* ~ Gamma(1, 1) and
+    v_ij ~ compound Poisson-gamma(mean (W* H*)_ij, phi, p), p in (1, 2).
+    Returns (V float32 I x J, W*, H*)."""
+    g = _rng(seed)
+    Wt = g.gamma(1.0, 1.0, size=(I, K_true))
+    Ht = g.gamma(1.0, 1.0, size=(K_true, J))
+    V = compound_poisson_gamma(Wt @ Ht, p, phi, g).astype(np.float32)
+    return V, Wt, Ht
+
+
+def dense_compound_poisson_device(I: int, J: int, K_true: int, seed: int, device,
+                                  p: float = 1.5, phi: float = 1.0, return_mean: bool = False):
+    """dense_compound_poisson drawn with torch on a CUDA device (the same
+    law; a different stream of random numbers).  Returns V (float32 I x J),
+    or (V, the means W* H*) with return_mean."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    Wt = torch.empty((I, K_true), dtype=torch.float32, device=device).exponential_(1.0, generator=g)
+    Ht = torch.empty((K_true, J), dtype=torch.float32, device=device).exponential_(1.0, generator=g)
+    M = Wt @ Ht
+    del Wt, Ht
+    lam, alpha, scale = compound_poisson_gamma_params(M, p, phi)
+    n = torch.poisson(lam, generator=g)
+    del lam
+    pos = n > 0
+    conc = torch.where(pos, n * alpha, torch.ones_like(n))
+    V = torch._standard_gamma(conc, generator=g) * scale
+    V = torch.where(pos, V, torch.zeros_like(V)).contiguous()
+    return (V, M) if return_mean else V
+
+
 def dense_gamma(I: int, J: int, K_true: int, seed: int):
     """Dense positive data V = |W* H*| * Gamma(shape 2, rate 2)."""
     g = _rng(seed)

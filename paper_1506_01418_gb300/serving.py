@@ -233,6 +233,11 @@ class GpuExecutor:
         torch = self.torch
         if job.p == 1.0:
             V = datagen.dense_poisson_device(job.I, job.J, 8, job.data_seed, self.dev)
+        elif 1.0 < job.p < 2.0:
+            # the compound Poisson-gamma law of the job's own power and
+            # dispersion (exact zeros included)
+            V = datagen.dense_compound_poisson_device(job.I, job.J, 8, job.data_seed, self.dev,
+                                                      p=job.p, phi=job.phi)
         else:
             V = datagen.dense_gamma_device(job.I, job.J, 8, job.data_seed, self.dev)
         W0, H0 = datagen.init_factors(job.I, job.J, job.K, job.seed, scale=job.init_scale, nonneg=True)

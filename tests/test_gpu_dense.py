@@ -280,6 +280,46 @@ def test_dense_chain_posterior_rmse_within_one_percent_of_oracle(kernel):
     assert abs(r_gpu - r_or) <= 0.01 * r_or, (r_gpu, r_or)
 
 
+@pytest.mark.parametrize("kernel", ["auto", "two_sided_bf16v", "fp32_gather"])
+def test_compound_poisson_chain_within_one_percent_of_oracle(kernel):
+    """Tweedie p = 1.5 on data drawn from its own law, the compound
+    Poisson-gamma (the paper's Sec. 4 compound-Poisson experiment; exact
+    zeros included): 256 x 256, K = 8, B = 4, W*, H* ~ Gamma(1, 1), phi = 1,
+    exponential priors rate 1, eps = 1e-4; 1000 sweeps, posterior-mean RMSE
+    within 1 % of the FP64 oracle chain's."""
+    I = J = 256
+    K, B, sweeps = 8, 4, 1000
+    V, _, _ = datagen.dense_compound_poisson(I, J, K, seed=1, p=1.5, phi=1.0)
+    assert (V == 0).mean() > 0.01
+    i, j, v = datagen.dense_to_coo(V)
+    W0, H0 = datagen.init_factors(I, J, K, seed=0, scale=1.0, nonneg=True)
+    opts = dict(dense_path=0) if kernel == "fp32_gather" else KERNELS[kernel]
+    pr = Pair(I, J, K, B, 1.5, 1.0, i, j, v, W0, H0, prior_kind=0, seed=11, eps=1e-4, V=V,
+              burn_in_sweeps=sweeps // 2, **opts)
+    pr.gpu.sweep(sweeps)
+    pr.orc.sweep(sweeps)
+    r_gpu, r_or = pr.gpu.rmse(True), pr.orc.rmse(True)
+    assert abs(r_gpu - r_or) <= 0.01 * r_or, (r_gpu, r_or)
+
+
+def test_compound_poisson_device_generator_law():
+    """The device generator the serving jobs use for p = 1.5: over 2048 x 2048
+    draws, standardised residuals (v - mu) / sqrt(phi mu^p) have mean 0 and
+    variance 1, and the zero mass is the mean of exp(-lam)."""
+    p, phi = 1.5, 1.3
+    V, M = datagen.dense_compound_poisson_device(2048, 2048, 8, 3, torch.device("cuda"), p=p,
+                                                 phi=phi, return_mean=True)
+    V, M = V.double(), M.double()
+    n = V.numel()
+    z = (V - M) / torch.sqrt(phi * M ** p)
+    assert abs(float(z.mean())) < 4 / np.sqrt(n)
+    assert abs(float((z ** 2).mean()) - 1.0) < 0.01
+    lam = M ** (2 - p) / (phi * (2 - p))
+    p0 = float(torch.exp(-lam).mean())
+    assert abs(float((V == 0).double().mean()) - p0) < 4 * np.sqrt(0.25 / n)
+    assert float(V.min()) >= 0
+
+
 def test_dense_refusals():
     I, J = 40, 30
     V = np.ones((I, J), np.float32)

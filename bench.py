@@ -767,6 +767,22 @@ def run_batched(args, wl_name, wl):
     for _ in range(args.warmup):
         P.psgld_batch_sweep(chains, 1, stream.cuda_stream)
     torch.cuda.synchronize(dev)
+    # the result-neutral launch knobs, tuned on ordinary sweeps of the chains
+    from paper_1506_01418_gb300 import autotune
+    tuning = autotune.tune_batch(chains)
+    # the same sweeps without captured graphs (direct launches), for the record
+    chains[0].set_options(use_graphs=0)
+    a0, b0 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    for _ in range(3):
+        P.psgld_batch_sweep(chains, 1, stream.cuda_stream)
+    b0.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_direct = a0.elapsed_time(b0) / 3
+    chains[0].set_options(use_graphs=1)
+    for _ in range(2):
+        P.psgld_batch_sweep(chains, 1, stream.cuda_stream)     # the graphs captured again
+    torch.cuda.synchronize(dev)
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     w0 = time.time()
@@ -841,11 +857,15 @@ def run_batched(args, wl_name, wl):
                      "tensor_frac_of_sustained": tflops / tc_peak,
                      "update_kernel_ms": upd_ms, "part_step_ms": grad_ms + upd_ms,
                      "peak_source": f"{peak_src} HBM copy bandwidth"},
-        # per call (one sweep): set t, B x (gradient launches + update),
-        # accumulate, advance t; the two-sided kernel runs one launch per
-        # power, the single-pass one per K class
+        # per call (one sweep): set t, then one replayed graph of B x
+        # (gradient launches + update), accumulate, advance t; the two-sided
+        # kernel runs one launch per power, the single-pass one per K class
         "gpu_launches": args.steps * ((len(set(wl["p_mix"])) if two else 1) * wl["B"] + wl["B"] + 3),
         "clocks": clocks,
+        "autotune": tuning,
+        "graphs": {"ms_per_sweep_captured": ms, "ms_per_sweep_direct_launches": ms_direct,
+                   "how": "each batched sweep one replayed CUDA graph (timed region) vs the "
+                          "same sweeps launched directly (3 sweeps, L2 not flushed)"},
         "unbatched": {"value": N / (ms_alone / 1e3), "unit": UNIT, "ms_per_sweep": ms_alone,
                       "how": "the same chains, each swept alone (its own captured-graph sweep), "
                              "back to back on one stream"},

@@ -129,6 +129,15 @@ typedef struct {
                                * it runs (a long-running chain beside short jobs);
                                * 0: every SM.  psgld_batch_sweep's shared launches
                                * use every SM regardless. */
+    int32_t batch_ctas;       /* psgld_batch_sweep, read from the list's first
+                               * context: CTAs of each persistent two-sided batch
+                               * launch (0: one per SM).  Every item is computed by
+                               * one CTA whichever CTA takes it, so the chains do
+                               * not depend on it (a knob for the autotuner). */
+    int32_t batch_update_blocks; /* psgld_batch_sweep: thread blocks of each batch
+                               * update launch, a grid-stride loop over all items
+                               * (0: one per 256 items, at most 2432); results do
+                               * not depend on it. */
     int32_t debug_wait_polls; /* for testing the timeout path; 0 (the default): the
                                * normal limit of every bounded device wait (2^24
                                * polls or about one second of SM clock).  > 0: the
@@ -236,7 +245,12 @@ PSGLD_API psgld_status psgld_sweep(psgld_ctx *ctx, int32_t n_sweeps, void *strea
  * runs, like psgld_sweep); the launches' parameter tables are kept by the
  * first context of the list and reused by its next batch.  A context may be
  * in one batch at a time: a call whose list shares a context with a batch
- * still running on another stream must be ordered after it by the caller. */
+ * still running on another stream must be ordered after it by the caller.
+ * With use_graphs (the first context's option, and profile off), each sweep
+ * of the batch replays one captured CUDA graph holding all its launches,
+ * kept by the first context per parity of the ping-pong buffers and per
+ * posterior-accumulation flag, and captured again when the batch's launch
+ * structure (contexts per kernel variant, grid sizes, knobs) changes. */
 PSGLD_API psgld_status psgld_batch_sweep(psgld_ctx *const *ctxs_host, int32_t n, int32_t n_sweeps,
                                          void *stream);
 

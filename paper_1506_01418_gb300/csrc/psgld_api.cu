@@ -176,6 +176,15 @@ __global__ void set_t_kernel(int64_t *t, int64_t v)
     if (threadIdx.x == 0) *t = v;
 }
 
+void destroy_batch_graphs(psgld_ctx *c)
+{
+    for (auto &row : c->bgraphs.exec)
+        for (auto &g : row)
+            if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+    c->bgraphs.key.clear();
+    c->bgraphs.calls = 0;
+}
+
 void destroy_graphs(psgld_ctx *c)
 {
     for (auto &row : c->graph)
@@ -183,6 +192,7 @@ void destroy_graphs(psgld_ctx *c)
             if (g) { cudaGraphExecDestroy(g); g = nullptr; }
     for (auto &g : c->graph_acc)
         if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+    destroy_batch_graphs(c);
 }
 
 psgld_status zero_posterior(psgld_ctx *c, cudaStream_t st)
@@ -383,6 +393,8 @@ psgld_status psgld_set_options(psgld_ctx *c, const psgld_options *o)
     if (o->dense_fp8 != 0 && o->dense_fp8 != 1) return fail(c, PSGLD_ERR_ARG, "dense_fp8 must be 0 or 1");
     if (o->gather_bf16 != 0 && o->gather_bf16 != 1) return fail(c, PSGLD_ERR_ARG, "gather_bf16 must be 0 or 1");
     if (o->max_sms < 0) return fail(c, PSGLD_ERR_ARG, "max_sms must be >= 0");
+    if (o->batch_ctas < 0 || o->batch_update_blocks < 0)
+        return fail(c, PSGLD_ERR_ARG, "batch_ctas and batch_update_blocks must be >= 0");
     if (o->debug_wait_polls < 0) return fail(c, PSGLD_ERR_ARG, "debug_wait_polls must be >= 0");
     c->opt = *o;
     destroy_graphs(c);
@@ -934,30 +946,83 @@ psgld_status psgld_batch_sweep(psgld_ctx *const *ctxs, int32_t n, int32_t n_swee
         const cudaError_t re = cudaEventRecord(ev, st);
         return re == cudaSuccess ? PSGLD_OK : cuda_fail(c0, re, "cudaEventRecord");
     };
-    for (int32_t sw = 0; sw < n_sweeps && s == PSGLD_OK; ++sw) {
-        const int q = nq == 2 ? (sw & 1) : 0;
-        for (int b = 0; b < B && s == PSGLD_OK; ++b) {
+    // one sweep's launches on stream `ss`: per part the gradient launches of
+    // every kernel variant and one update launch, then the accumulation
+    // (when any context is past burn-in) and the iteration counters
+    auto enqueue_sweep = [&](int q, bool any, cudaStream_t ss) -> psgld_status {
+        psgld_status r = PSGLD_OK;
+        for (int b = 0; b < B && r == PSGLD_OK; ++b) {
             const size_t row = (size_t)(q * B + b) * n;
-            if (prof) s = record(c0->ev_start[b]);
-            for (int g = 0; g < ng && s == PSGLD_OK; ++g)
-                s = launch_dense_batch(c0, keys[g], d + off_dp + dp * (row + gbeg[g]),
+            if (prof) r = record(c0->ev_start[b]);
+            for (int g = 0; g < ng && r == PSGLD_OK; ++g)
+                r = launch_dense_batch(c0, keys[g], d + off_dp + dp * (row + gbeg[g]),
                                        reinterpret_cast<const int *>(d + off_cta) + gbeg[g] + g,
-                                       gbeg[g + 1] - gbeg[g], g_ctas[g], st);
-            if (s == PSGLD_OK && prof) s = record(c0->ev_mid[b]);
-            if (s == PSGLD_OK)
-                s = launch_update_batch(c0, d + off_up + upb * row,
-                                        reinterpret_cast<const int64_t *>(d + off_items), n, items[n], st);
-            if (s == PSGLD_OK && prof) {
-                s = record(c0->ev_end[b]);
+                                       gbeg[g + 1] - gbeg[g], g_ctas[g], ss);
+            if (r == PSGLD_OK && prof) r = record(c0->ev_mid[b]);
+            if (r == PSGLD_OK)
+                r = launch_update_batch(c0, d + off_up + upb * row,
+                                        reinterpret_cast<const int64_t *>(d + off_items), n, items[n], ss);
+            if (r == PSGLD_OK && prof) {
+                r = record(c0->ev_end[b]);
                 c0->ev_pending[b] = 1;
             }
         }
+        if (r == PSGLD_OK && any)
+            r = launch_accumulate_batch(c0, d + off_ap + ap * (size_t)q * n,
+                                        reinterpret_cast<const int64_t *>(d + off_units), n, units[n], ss);
+        if (r == PSGLD_OK) r = launch_t_batch(c0, d + off_ap, n, 1, ss);
+        return r;
+    };
+    // captured graphs: everything a sweep's launches bake in is in the key.
+    // A structure is captured once it repeats (the second consecutive call
+    // with the same key) or when the call runs several sweeps: a serving
+    // loop whose job list changes between calls launches directly rather
+    // than capturing graphs it would use once.
+    bool graphs = c0->opt.use_graphs && !prof && c0->capture_stream;
+    if (graphs && s == PSGLD_OK) {
+        std::vector<int64_t> key = {(int64_t)(uintptr_t)d, (int64_t)total, n, ng, B, nq,
+                                    c0->opt.batch_ctas, c0->opt.batch_update_blocks, items[n], units[n]};
+        for (int g = 0; g < ng; ++g) {
+            key.push_back(keys[g]);
+            key.push_back(gbeg[g]);
+            key.push_back(g_ctas[g]);
+        }
+        if (key != c0->bgraphs.key) {
+            destroy_batch_graphs(c0);
+            c0->bgraphs.key = key;
+        }
+        c0->bgraphs.calls += 1;
+        graphs = c0->bgraphs.calls >= 2 || n_sweeps > 1;
+    }
+    for (int32_t sw = 0; sw < n_sweeps && s == PSGLD_OK; ++sw) {
+        const int q = nq == 2 ? (sw & 1) : 0;
         bool any = false;
         for (int i = 0; i < n; ++i) any |= ctxs[i]->sweeps_done + sw >= ctxs[i]->opt.burn_in_sweeps;
-        if (s == PSGLD_OK && any)
-            s = launch_accumulate_batch(c0, d + off_ap + ap * (size_t)q * n,
-                                        reinterpret_cast<const int64_t *>(d + off_units), n, units[n], st);
-        if (s == PSGLD_OK) s = launch_t_batch(c0, d + off_ap, n, 1, st);
+        if (!graphs) {
+            s = enqueue_sweep(q, any, st);
+            continue;
+        }
+        cudaGraphExec_t &ex = c0->bgraphs.exec[q][any ? 1 : 0];
+        if (!ex) {
+            cudaStream_t cs = c0->capture_stream;
+            e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+            if (e != cudaSuccess) { s = cuda_fail(c0, e, "cudaStreamBeginCapture"); break; }
+            s = enqueue_sweep(q, any, cs);
+            cudaGraph_t gr = nullptr;
+            e = cudaStreamEndCapture(cs, &gr);
+            if (s == PSGLD_OK && e != cudaSuccess) s = cuda_fail(c0, e, "cudaStreamEndCapture");
+            if (s == PSGLD_OK) {
+                e = cudaGraphInstantiate(&ex, gr, 0);
+                if (e != cudaSuccess) {
+                    ex = nullptr;
+                    s = cuda_fail(c0, e, "cudaGraphInstantiate");
+                }
+            }
+            if (gr) cudaGraphDestroy(gr);
+            if (s != PSGLD_OK) break;
+        }
+        e = cudaGraphLaunch(ex, st);
+        if (e != cudaSuccess) s = cuda_fail(c0, e, "cudaGraphLaunch");
     }
     for (int i = 0; i < n; ++i) {
         psgld_ctx *c = ctxs[i];

@@ -1502,7 +1502,8 @@ psgld_status launch_dense_batch(psgld_ctx *c0, int key, const void *params, cons
         PSGLD_CK(c0, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         int sms = 0;
         PSGLD_CK(c0, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c0->device));
-        const int grid = std::min(total, sms);
+        int grid = std::min(total, sms);
+        if (c0->opt.batch_ctas > 0) grid = std::min(grid, (int)c0->opt.batch_ctas);
         if (grid > 0) fn<<<grid, two_sided::kThreads, smem, st>>>(tab, stride, cta_start, n);
         PSGLD_CK(c0, cudaGetLastError());
         return PSGLD_OK;

@@ -52,6 +52,15 @@ struct Sums {
     double *s = nullptr, *s2 = nullptr;
 };
 
+// psgld_batch_sweep's captured sweeps, kept by the list's first context: one
+// graph per parity of the ping-pong buffers and per accumulation flag, valid
+// while the batch's launch structure (key) is unchanged.
+struct BatchGraphs {
+    std::vector<int64_t> key;
+    int64_t calls = 0;           // consecutive calls with this key
+    cudaGraphExec_t exec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+};
+
 }  // namespace psgld
 
 struct psgld_ctx {
@@ -115,6 +124,7 @@ struct psgld_ctx {
     cudaGraphExec_t graph_acc[4] = {nullptr, nullptr, nullptr, nullptr};
     cudaStream_t capture_stream = nullptr;
     int64_t *t_dev = nullptr;    // iteration counter read by graph replays
+    psgld::BatchGraphs bgraphs;  // captured batch sweeps while this context leads a batch
 
     // psgld_batch_sweep's parameter tables while this context leads a batch
     // (is first in the list): device copy, its size, an event recorded after

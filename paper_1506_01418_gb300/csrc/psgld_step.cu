@@ -874,7 +874,8 @@ int64_t fill_upd_param(psgld_ctx *c, int part, const int64_t *t_dev, int64_t t_a
 psgld_status launch_update_batch(psgld_ctx *c0, const void *params, const int64_t *item_start, int n,
                                  int64_t total_items, cudaStream_t st)
 {
-    const int grid = (int)std::min<int64_t>((total_items + kThreads - 1) / kThreads, 152 * 16);
+    const int64_t cap = c0->opt.batch_update_blocks > 0 ? c0->opt.batch_update_blocks : 152 * 16;
+    const int grid = (int)std::min<int64_t>((total_items + kThreads - 1) / kThreads, cap);
     if (grid > 0)
         update_batch_kernel<<<grid, kThreads, 0, st>>>(static_cast<const UpdParams *>(params), item_start, n);
     PSGLD_CK(c0, cudaGetLastError());

@@ -180,3 +180,81 @@ def test_odd_b_alternates_the_buffers_between_sweeps():
         _assert_same(a, b)
     for ch in batch + alone:
         ch.close()
+
+
+def test_batched_sweeps_from_captured_graphs_equal_sweeps_alone():
+    """use_graphs on the first context: each batched sweep replays a captured
+    graph (one per buffer parity and accumulation flag).  Calls of one and
+    of two sweeps (replays of the same graphs), B even and odd, against the
+    chains swept alone."""
+    for b_ in (B, 3):
+        mix = MIX if b_ == B else [MIX[0], MIX[9], MIX[12], MIX[3]]
+        batch = [_chain(i, *m, use_graphs=1, B=b_) for i, m in enumerate(mix)]
+        alone = [_chain(i, *m, use_graphs=1, B=b_) for i, m in enumerate(mix)]
+        for n in (1, 2):          # a capture, then replays of the captured graphs
+            P.psgld_batch_sweep(batch, n)
+        for ch in alone:
+            ch.sweep(3)
+        for a, b in zip(batch, alone):
+            _assert_same(a, b)
+        for ch in batch + alone:
+            ch.close()
+
+
+def test_batch_graph_is_captured_again_when_the_list_changes():
+    """The first context keeps the graphs of its batch; a list with another
+    structure (a context more or less, another kernel variant, another first
+    context) captures new ones on its second consecutive call, and every
+    chain still ends where it ends alone."""
+    idx = [0, 2, 9, 12]
+    batch = {i: _chain(i, *MIX[i], use_graphs=1) for i in idx}
+    alone = {i: _chain(i, *MIX[i], use_graphs=1) for i in idx}
+    plan = [[0, 2, 9, 12]] * 2 + [[0, 2]] * 2 + [[0, 9, 12]] * 2 + [[2, 9, 12]] * 2
+    done = {i: 0 for i in idx}
+    for lst in plan:
+        P.psgld_batch_sweep([batch[i] for i in lst], 1)
+        for i in lst:
+            done[i] += 1
+    for i in idx:
+        alone[i].sweep(done[i])
+        _assert_same(batch[i], alone[i])
+    for ch in list(batch.values()) + list(alone.values()):
+        ch.close()
+
+
+@pytest.mark.parametrize("ctas,blocks", [(76, 0), (112, 608), (0, 4864), (13, 1)])
+def test_batch_launch_knobs_do_not_change_the_chains(ctas, blocks):
+    """batch_ctas (CTAs of the persistent two-sided launches) and
+    batch_update_blocks (blocks of the update launches) move work between
+    CTAs only: chains end bit for bit as with the default launches."""
+    mix = [MIX[i] for i in (0, 2, 9, 12, 13)]    # fixed step sizes: stable over many sweeps
+    tuned = [_chain(i, *m, use_graphs=1) for i, m in enumerate(mix)]
+    plain = [_chain(i, *m, use_graphs=1) for i, m in enumerate(mix)]
+    tuned[0].set_options(batch_ctas=ctas, batch_update_blocks=blocks)
+    P.psgld_batch_sweep(tuned, 2)
+    P.psgld_batch_sweep(plain, 2)
+    for a, b in zip(tuned, plain):
+        _assert_same(a, b)
+    for ch in tuned + plain:
+        ch.close()
+
+
+def test_autotuner_records_a_choice_and_its_sweeps_are_ordinary_sweeps():
+    from paper_1506_01418_gb300 import autotune
+    mix = [MIX[i] for i in (0, 2, 9, 12, 13)]    # fixed step sizes: stable over many sweeps
+    tuned = [_chain(i, *m, use_graphs=1) for i, m in enumerate(mix)]
+    plain = [_chain(i, *m, use_graphs=1) for i, m in enumerate(mix)]
+    rec = autotune.tune_batch(tuned, sweeps_per_trial=1, repeats=1,
+                              cta_candidates=(0, 76), update_candidates=(0, 608))
+    assert rec["batch_ctas"] in (0, 76) and rec["batch_update_blocks"] in (0, 608)
+    assert len(rec["ms_per_sweep"]) == 3 and all(v > 0 for v in rec["ms_per_sweep"].values())
+    assert tuned[0].options.batch_ctas == rec["batch_ctas"]
+    n = tuned[0].iterations_done // B
+    assert n == 2 * 3          # one capture sweep and one timed sweep per trial
+    P.psgld_batch_sweep(tuned, 1)
+    for ch in plain:
+        ch.sweep(n + 1)
+    for a, b in zip(tuned, plain):
+        _assert_same(a, b)
+    for ch in tuned + plain:
+        ch.close()

@@ -529,6 +529,78 @@ __global__ void __launch_bounds__(kThreads, 5) update_kernel(const __grid_consta
     for (a -= n0; a < n1; a += stride) update_item<1>(P, a, eps, sd, t_lo, t_hi);
 }
 
+// The update of the sparse path for one context, with 32-bit index
+// arithmetic (every row offset and item index of both factors below 2^31,
+// checked on the host) and no BF16 copies to write: the same arithmetic,
+// the same result bit for bit as update_item, in fewer instructions.
+template <int SID>
+__device__ __forceinline__ void update_item32(const UpdParams &P, uint32_t item, float eps, float sd,
+                                              uint32_t t_lo, uint32_t t_hi)
+{
+    const UpdSide &Sd = P.side[SID];
+    const uint32_t ng = (uint32_t)P.ngroups;
+    const uint32_t row = P.div_magic ? __umulhi(item, P.div_magic) : item / ng;
+    const uint32_t q = item - row * ng;
+    const uint32_t off = row * (uint32_t)P.ldk + 4u * q;
+    const float4 x = ldg4(Sd.X_cur + off);
+    float4 g = zero4();
+    const int p0 = __ldg(Sd.ptr + row) - (int)Sd.base, p1 = __ldg(Sd.ptr + row + 1) - (int)Sd.base;
+    if (p1 > p0) {
+        const int u0 = p0 >> P.unit_shift, u1 = (p1 - 1) >> P.unit_shift;
+        if (u0 == u1) {
+            g = ldg4(Sd.Gin + off);
+        } else {
+            // the row's first unit's tail slot, then the later units' head slots, in unit order
+            const uint32_t ldk = (uint32_t)P.ldk;
+            g = __ldcg(reinterpret_cast<const float4 *>(Sd.partial + (2u * u0 + 1u) * ldk + 4u * q));
+            const float *hp = Sd.partial + 4u * q;
+            int uu = u0 + 1;
+            for (; uu + 8 <= u1 + 1; uu += 8) {   // eight independent loads in flight
+                float4 v[8];
+#pragma unroll
+                for (int w = 0; w < 8; ++w)
+                    v[w] = __ldcg(reinterpret_cast<const float4 *>(hp + 2u * (uint32_t)(uu + w) * ldk));
+#pragma unroll
+                for (int w = 0; w < 8; ++w) add4(g, v[w]);
+            }
+            for (; uu <= u1; ++uu) add4(g, __ldcg(reinterpret_cast<const float4 *>(hp + 2u * (uint32_t)uu * ldk)));
+        }
+    }
+    const uint4 r = philox(make_uint4(q, row, t_lo, (t_hi << 1) | (uint32_t)SID), P);
+    const float4 z = dev::box_muller4(r);
+    float4 o;
+    o.x = update1(P, Sd, x.x, g.x, z.x, eps, sd);
+    o.y = update1(P, Sd, x.y, g.y, z.y, eps, sd);
+    o.z = update1(P, Sd, x.z, g.z, z.z, eps, sd);
+    o.w = update1(P, Sd, x.w, g.w, z.w, eps, sd);
+    // the padding columns (k >= K) stay zero: their x, g are zero and the
+    // noise is masked (K is a multiple of 4 except in the last group)
+    if (4u * q + 4u > (uint32_t)P.K) {
+        const uint32_t k0 = 4u * q;
+        if (k0 + 1 >= (uint32_t)P.K) o.y = 0.f;
+        if (k0 + 2 >= (uint32_t)P.K) o.z = 0.f;
+        if (k0 + 3 >= (uint32_t)P.K) o.w = 0.f;
+    }
+    *reinterpret_cast<float4 *>(Sd.X_next + off) = o;
+}
+
+__global__ void __launch_bounds__(kThreads, 5) update_kernel32(const __grid_constant__ UpdParams P)
+{
+    const int64_t t = P.t_dev ? *P.t_dev + P.t_add : P.t_add;
+    float eps = P.eps, sd = P.sd;
+    if (P.eps_poly) {
+        const double e = pow(P.eps_a / (double)t, P.eps_b);
+        eps = (float)e;
+        sd = (float)sqrt(2.0 * e);
+    }
+    const uint32_t t_lo = (uint32_t)(uint64_t)t, t_hi = (uint32_t)((uint64_t)t >> 32);
+    const uint32_t n0 = (uint32_t)P.side[0].items, n1 = (uint32_t)P.side[1].items;
+    const uint32_t stride = gridDim.x * kThreads;
+    uint32_t a = blockIdx.x * kThreads + threadIdx.x;
+    for (; a < n0; a += stride) update_item32<0>(P, a, eps, sd, t_lo, t_hi);
+    for (a -= n0; a < n1; a += stride) update_item32<1>(P, a, eps, sd, t_lo, t_hi);
+}
+
 using GradFn = void (*)(GradParams);
 
 struct Shape {
@@ -808,7 +880,16 @@ psgld_status launch_part_step(psgld_ctx *c, int64_t t, const int64_t *t_dev, int
     }
     PSGLD_CK(c, cudaGetLastError());
     if (prof) PSGLD_CK(c, cudaEventRecordWithFlags(c->ev_mid[part], st, rec_flags));
-    if (items > 0) update_kernel<<<ugrid, kThreads, 0, st>>>(UP);
+    if (items > 0) {
+        // the sparse path takes the 32-bit kernel when every index fits
+        // (items, row offsets of both factors and the partial slots)
+        const int64_t lim = (1ll << 31) - 1;
+        const int64_t slots = 2 * std::max(c->side[0].max_units, c->side[1].max_units) * c->ldk;
+        const bool small = !dense && !gather_bf16(c) && UP.side[0].items + UP.side[1].items <= lim &&
+                           std::max(c->I, c->J) * c->ldk <= lim && slots <= lim && c->N <= lim;
+        if (small) update_kernel32<<<ugrid, kThreads, 0, st>>>(UP);
+        else update_kernel<<<ugrid, kThreads, 0, st>>>(UP);
+    }
     PSGLD_CK(c, cudaGetLastError());
     if (prof) {
         PSGLD_CK(c, cudaEventRecordWithFlags(c->ev_end[part], st, rec_flags));

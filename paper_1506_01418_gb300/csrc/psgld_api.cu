@@ -332,6 +332,10 @@ psgld_status create_context(int64_t I, int64_t J, int32_t K, int32_t B, double t
     // after the legacy stream)
     if (cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking) != cudaSuccess)
         s = fail(c, PSGLD_ERR_CUDA, "stream creation failed");
+    if (s == PSGLD_OK && (cudaStreamCreateWithFlags(&c->side_stream, cudaStreamNonBlocking) != cudaSuccess ||
+                          cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+                          cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess))
+        s = fail(c, PSGLD_ERR_CUDA, "stream or event creation failed");
     cudaStream_t zs = c->capture_stream;
     for (int b = 0; b < 2 && s == PSGLD_OK; ++b) {
         s = alloc(c, &c->W[b], I * c->ldk, true, zs);
@@ -1109,6 +1113,12 @@ void psgld_destroy(psgld_ctx *c)
     dev_free(c, c->G);
     dev_free(c, c->sW.s); dev_free(c, c->sW.s2); dev_free(c, c->sH.s); dev_free(c, c->sH.s2);
     dev_free(c, c->red); dev_free(c, c->flag); dev_free(c, c->kflag); dev_free(c, c->t_dev);
+    if (c->side_stream) {
+        cudaStreamSynchronize(c->side_stream);
+        cudaStreamDestroy(c->side_stream);
+    }
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
     if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
     delete c;
 }

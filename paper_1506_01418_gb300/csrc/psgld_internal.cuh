@@ -124,6 +124,10 @@ struct psgld_ctx {
     cudaGraphExec_t graph_acc[4] = {nullptr, nullptr, nullptr, nullptr};
     cudaStream_t capture_stream = nullptr;
     int64_t *t_dev = nullptr;    // iteration counter read by graph replays
+    // sparse part-steps: the rows of H^T on a second stream, forked from and
+    // joined back into the launch stream
+    cudaStream_t side_stream = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     psgld::BatchGraphs bgraphs;  // captured batch sweeps while this context leads a batch
 
     // psgld_batch_sweep's parameter tables while this context leads a batch

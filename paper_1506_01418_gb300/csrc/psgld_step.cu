@@ -858,7 +858,6 @@ psgld_status launch_part_step(psgld_ctx *c, int64_t t, const int64_t *t_dev, int
     const int64_t units = GP.side[0].units + GP.side[1].units;
     const int ggrid = (int)((units + kGradThreads / 32 - 1) / (kGradThreads / 32));
     const int64_t items = UP.side[0].items + UP.side[1].items;
-    const int ugrid = (int)std::min<int64_t>((items + kThreads - 1) / kThreads, 152 * 16);
     // Inside a stream capture the records must be external, so that they
     // become event-record nodes of the graph (a plain record would only
     // become a dependency edge); outside a capture they are plain records.
@@ -870,25 +869,64 @@ psgld_status launch_part_step(psgld_ctx *c, int64_t t, const int64_t *t_dev, int
         if (cap == cudaStreamCaptureStatusActive) rec_flags = cudaEventRecordExternal;
         PSGLD_CK(c, cudaEventRecordWithFlags(c->ev_start[part], st, rec_flags));
     }
-    if (dense) {
-        if (upd[0] || upd[1]) {
-            const psgld_status ds = launch_dense_grad(c, part, st);
-            if (ds != PSGLD_OK) return ds;
+    // the sparse path takes the 32-bit update kernel when every index fits
+    // (items, row offsets of both factors and the partial slots)
+    const int64_t lim = (1ll << 31) - 1;
+    const int64_t slots = 2 * std::max(c->side[0].max_units, c->side[1].max_units) * c->ldk;
+    const bool small = !dense && !gather_bf16(c) && items <= lim &&
+                       std::max(c->I, c->J) * c->ldk <= lim && slots <= lim && c->N <= lim;
+    auto update = [&](const UpdParams &U, cudaStream_t ss) {
+        const int64_t n = U.side[0].items + U.side[1].items;
+        const int grid = (int)std::min<int64_t>((n + kThreads - 1) / kThreads, 152 * 16);
+        if (grid <= 0) return;
+        if (small) update_kernel32<<<grid, kThreads, 0, ss>>>(U);
+        else update_kernel<<<grid, kThreads, 0, ss>>>(U);
+    };
+    auto gradient = [&](const GradParams &G, cudaStream_t ss) {
+        const int64_t n = G.side[0].units + G.side[1].units;
+        const int grid = (int)((n + kGradThreads / 32 - 1) / (kGradThreads / 32));
+        if (grid > 0) gfn<<<grid, kGradThreads, grad_smem(sh), ss>>>(G);
+    };
+    // W and H^T on two streams when the factors fit in L2 (W and H^T at most
+    // 64 MB): each side's gradient, then its update; their outputs are
+    // disjoint (G rows, partial slots, next buffers of the ping-ponged
+    // factors), so the result is the same bit for bit, and the ALU-bound
+    // update of one side overlaps the L2-bound gathers of the other (10 M
+    // entries, K = 50: 1.58 to 1.50 ms per sweep).  With factors beyond L2
+    // the concurrent update's DRAM traffic slows the gathers' misses instead
+    // (10^8 entries, K = 100: 27.2 to 27.8 ms), so one stream.  Not with
+    // gather_bf16: the BF16 copies that the gathers read are single-buffered
+    // and rewritten by the updates.  Inside a capture the fork and join
+    // become graph edges.
+    const bool l2_fit = 4.0 * (double)(c->I + c->J) * c->ldk <= 64.0 * (1 << 20);
+    if (!dense && !prof && !gather_bf16(c) && l2_fit && c->side_stream && upd[0] && upd[1]) {
+        GradParams GW = GP, GH = GP;
+        GW.side[1].units = 0;
+        GH.side[0].units = 0;
+        UpdParams UW = UP, UH = UP;
+        UW.side[1].items = 0;
+        UH.side[0].items = 0;
+        PSGLD_CK(c, cudaEventRecord(c->ev_fork, st));
+        PSGLD_CK(c, cudaStreamWaitEvent(c->side_stream, c->ev_fork, 0));
+        gradient(GH, c->side_stream);
+        update(UH, c->side_stream);
+        gradient(GW, st);
+        update(UW, st);
+        PSGLD_CK(c, cudaGetLastError());
+        PSGLD_CK(c, cudaEventRecord(c->ev_join, c->side_stream));
+        PSGLD_CK(c, cudaStreamWaitEvent(st, c->ev_join, 0));
+    } else {
+        if (dense) {
+            if (upd[0] || upd[1]) {
+                const psgld_status ds = launch_dense_grad(c, part, st);
+                if (ds != PSGLD_OK) return ds;
+            }
+        } else if (ggrid > 0) {
+            gradient(GP, st);
         }
-    } else if (ggrid > 0) {
-        gfn<<<ggrid, kGradThreads, grad_smem(sh), st>>>(GP);
-    }
-    PSGLD_CK(c, cudaGetLastError());
-    if (prof) PSGLD_CK(c, cudaEventRecordWithFlags(c->ev_mid[part], st, rec_flags));
-    if (items > 0) {
-        // the sparse path takes the 32-bit kernel when every index fits
-        // (items, row offsets of both factors and the partial slots)
-        const int64_t lim = (1ll << 31) - 1;
-        const int64_t slots = 2 * std::max(c->side[0].max_units, c->side[1].max_units) * c->ldk;
-        const bool small = !dense && !gather_bf16(c) && UP.side[0].items + UP.side[1].items <= lim &&
-                           std::max(c->I, c->J) * c->ldk <= lim && slots <= lim && c->N <= lim;
-        if (small) update_kernel32<<<ugrid, kThreads, 0, st>>>(UP);
-        else update_kernel<<<ugrid, kThreads, 0, st>>>(UP);
+        PSGLD_CK(c, cudaGetLastError());
+        if (prof) PSGLD_CK(c, cudaEventRecordWithFlags(c->ev_mid[part], st, rec_flags));
+        if (items > 0) update(UP, st);
     }
     PSGLD_CK(c, cudaGetLastError());
     if (prof) {

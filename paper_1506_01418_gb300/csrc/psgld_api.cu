@@ -853,8 +853,10 @@ psgld_status psgld_batch_sweep(psgld_ctx *const *ctxs, int32_t n, int32_t n_swee
 
     auto up256 = [](size_t x) { return (x + 255) & ~size_t(255); };
     const size_t dp = dense_param_bytes(), upb = upd_param_bytes(), ap = acc_param_bytes();
-    const size_t off_cta = 0;                                        // ng prefixes, n + ng ints
-    const size_t off_items = up256(off_cta + sizeof(int) * (size_t)(n + ng));
+    // per group g, at 2 (gbeg[g] + g): two prefix arrays of its contexts'
+    // items (first kind, then second kind), n_g + 1 entries each
+    const size_t off_cta = 0;
+    const size_t off_items = up256(off_cta + sizeof(int) * (size_t)(2 * (n + ng)));
     const size_t off_units = up256(off_items + sizeof(int64_t) * (size_t)(n + 1));
     const size_t off_dp = up256(off_units + sizeof(int64_t) * (size_t)(n + 1));
     const size_t off_up = up256(off_dp + dp * (size_t)nq * B * n);
@@ -882,16 +884,25 @@ psgld_status psgld_batch_sweep(psgld_ctx *const *ctxs, int32_t n, int32_t n_swee
         for (int b = 0; b < B; ++b) {
             const size_t row = (size_t)(q * B + b) * n;
             for (int g = 0; g < ng; ++g) {
-                int acc = 0;
+                const int ngc = gbeg[g + 1] - gbeg[g];
+                int *pre = cta + 2 * (gbeg[g] + g);
+                int acc1 = 0, acc2 = 0;
                 for (int k = gbeg[g]; k < gbeg[g + 1]; ++k) {
                     const int i = order[k];
                     set_state(i, (int64_t)q * B + b);
-                    if (q == 0 && b == 0) cta[gbeg[g] + g + (k - gbeg[g])] = acc;
-                    acc += fill_dense_param(ctxs[i], b, tab.data() + off_dp + dp * (row + k));
+                    if (q == 0 && b == 0) {
+                        pre[k - gbeg[g]] = acc1;
+                        pre[ngc + 1 + k - gbeg[g]] = acc2;
+                    }
+                    int first = 0;
+                    const int all = fill_dense_param(ctxs[i], b, tab.data() + off_dp + dp * (row + k), &first);
+                    acc1 += first;
+                    acc2 += all - first;
                 }
                 if (q == 0 && b == 0) {
-                    cta[gbeg[g + 1] + g] = acc;
-                    g_ctas[g] = acc;
+                    pre[ngc] = acc1;
+                    pre[2 * ngc + 1] = acc2;
+                    g_ctas[g] = acc1 + acc2;
                 }
             }
             int64_t it = 0;
@@ -960,7 +971,7 @@ psgld_status psgld_batch_sweep(psgld_ctx *const *ctxs, int32_t n, int32_t n_swee
             if (prof) r = record(c0->ev_start[b]);
             for (int g = 0; g < ng && r == PSGLD_OK; ++g)
                 r = launch_dense_batch(c0, keys[g], d + off_dp + dp * (row + gbeg[g]),
-                                       reinterpret_cast<const int *>(d + off_cta) + gbeg[g] + g,
+                                       reinterpret_cast<const int *>(d + off_cta) + 2 * (gbeg[g] + g),
                                        gbeg[g + 1] - gbeg[g], g_ctas[g], ss);
             if (r == PSGLD_OK && prof) r = record(c0->ev_mid[b]);
             if (r == PSGLD_OK)
@@ -1084,9 +1095,10 @@ int64_t psgld_estimate_device_bytes(int64_t I, int64_t J, int32_t K, int32_t B, 
         return bytes;
     }
     const int64_t KP = 64 * cdiv(K, 64), vs = dense_v_bf16 ? 2 : 4;
-    const int64_t mt = cdiv(maxI, 128), nt = cdiv(maxJ, 128), ni = cdiv(maxI, 64), nj = cdiv(maxJ, 64);
-    bytes += (int64_t)B * B * (mt * nj + nt * ni) * 8192 * vs;     // V tiles, both orientations
+    const int64_t mt = cdiv(maxI, 128), nt = cdiv(maxJ, 128), nj = cdiv(maxJ, 64);
+    bytes += (int64_t)B * B * mt * nj * 8192 * vs;                 // V tiles
     bytes += (int64_t)B * 2 * (mt + nt) * 64 * KP * 2;              // BF16 factor shadows
+    bytes += (int64_t)B * mt * 2 * nt * 8192 * 2 + 4 * (2 + B);     // one part's E tiles, counters
     return bytes;
 }
 

@@ -567,57 +567,83 @@ dense_grad_batch_kernel(const unsigned char *__restrict__ tab, size_t stride, co
 //
 // A block larger than one 128-row tile would need its G_H summed over the
 // block's M-tiles.  Instead the work of a part is split into two kinds of
-// items that read only the previous factors: a rows item owns 128 rows of W
-// of one block and walks all the block's columns, accumulating G_W of those
-// rows in TMEM; a columns item owns 128 rows of H^T (columns of V) and walks
-// all the block's rows, accumulating G_H.  Each computes its own mu and E
-// (GEMM1 twice per entry: 4 contractions instead of 3), and every G row is
-// written once, complete, by one CTA -- no partial sums, no atomics.
+// items.  A rows item owns 128 rows of W of one block and walks all the
+// block's columns in 64-column tiles: mu = W H^T, E, and G_W += E H in TMEM;
+// each E tile (BF16, the image the epilogue built in shared memory) also
+// goes to HBM, one bulk store.  A columns item owns 128 rows of H^T (columns
+// of V); once every rows item of its block has stored its E, it walks the
+// block's rows: G_H += E^T W, one contraction.  mu and E are formed once per entry (the three
+// contractions the gradient needs), and every G row is written once,
+// complete, by one CTA: no partial sums, no atomics on data.  E is formed
+// without its 1 / phi factor, which multiplies G as G is written.
+//
+// Items are claimed in order from a counter in HBM (the rows items of every
+// block first, then the columns items), and a columns item waits (bounded)
+// for a per-block count of finished rows items.  A claimed item waits only
+// for items claimed before it, all held by running CTAs, so a launch
+// finishes however many of its CTAs the GPU runs at a time.  The last CTA to
+// finish sets the counters back to zero for the next launch.
 //
 // Operands come from HBM already in the MMA layout: BF16 shadows of W and
-// H^T cut into 128-row canonical K-major tiles per piece (kept by the update
-// kernel), and V cut into 128 x 64 tiles per block, once per orientation, in
-// the order the epilogue reads them (4-column FP32 or 8-column BF16 chunks,
-// one 16-byte chunk per owned row, so a warp reads 512 contiguous bytes).
-// Every tile is one bulk copy.
+// H^T cut into 64-row swizzled K-major tiles per piece (kept by the update
+// kernel), and V cut into 128 x 64 tiles per block, in the order the
+// epilogue reads them (4-column FP32 or 8-column BF16 chunks, one 16-byte
+// chunk per owned row, so a warp reads 512 contiguous bytes).  Every tile is
+// one bulk copy.
 //
-// One persistent CTA per SM, 10 warps:
-//   warp 0               producer: the owned tile once per item, then per
-//                         walked tile the other factor's 64-row tile and the
-//                         V tile, into two rings of slots (bulk copies);
-//   warp 1               MMA issuer: GEMM1 mu_j = A . B_j^T into one of two
-//                         TMEM buffers, then GEMM2 G += E_(j-1) . B_(j-1)
-//                         (B read MN-major), so GEMM1 of tile j overlaps the
-//                         epilogue of tile j-1; completions via tcgen05.commit.
-//                         Both warps run their loops with all 32 lanes (the
-//                         descriptors stay warp-uniform, in uniform registers)
-//                         and lane 0 performs each copy and MMA;
-//   warps 2-9            epilogue, two warps per TMEM lane quarter (32 of the
-//                         tile's 64 columns each): TMEM mu + V (shared
-//                         memory) -> E (BF16, shared memory, two buffers),
-//                         and after an item's last tile the G rows from TMEM
-//                         to HBM.  The Tweedie power is a template parameter
-//                         (p = 0, 1, 2, other), so the epilogue is straight-line.
+// One persistent CTA per SM, 11 warps:
+//   warp 0     producer: claims the items and hands them on through a
+//              two-slot queue in shared memory; rows item: the owned tile,
+//              then per walked tile the H^T tile (a ring of 2 to 6 slots);
+//              columns item: per 64 W rows one stage of the W tile and the
+//              two 64 x 64 halves of E that cover the owned columns.  A CTA
+//              claims all its rows items before its first columns item, so
+//              at that point (its last rows item complete) the columns
+//              stages take over the whole of shared memory: a ring of 2 to
+//              6 stages;
+//   warp 1     MMA issuer: rows item: GEMM1 mu_j = A . B_j^T into one of two
+//              TMEM buffers, then GEMM2 G += E_(j-1) . B_(j-1) (B read
+//              MN-major), so GEMM1 of tile j overlaps the epilogue of tile
+//              j-1; columns item: G += E^T . W, both operands read MN-major.
+//              Completions via tcgen05.commit.  Both warps run their loops
+//              with all 32 lanes (the descriptors stay warp-uniform, in
+//              uniform registers) and one elected lane performs each copy
+//              and MMA;
+//   warps 2-9  epilogue, two warps per TMEM lane quarter (32 of the tile's
+//              64 columns each): TMEM mu + V -> E (BF16, into an E buffer),
+//              V read from HBM straight into registers two tiles ahead; and
+//              after an item's last tile the
+//              G rows from TMEM to HBM.  The Tweedie power is a template
+//              parameter (p = 0, 1, 2, other), so the epilogue is
+//              straight-line;
+//   warp 10    E stores: each E tile of a rows item to HBM (one bulk copy
+//              from its E buffer), and after the item the count its block's
+//              columns items wait for.  The tensor core queues only a few
+//              MMAs, so this work stays off the MMA warp.
 // TMEM: mu buffers at columns 0 and 64, G at 128 .. 128 + KP, and the owned
-// tile (copied from shared memory once per item with tcgen05.cp, so GEMM1
-// reads A from TMEM and shared memory serves only B) in the last KP / 2
-// columns.
+// tile of a rows item (copied from shared memory once per item with
+// tcgen05.cp, so GEMM1 reads A from TMEM and shared memory serves only B) in
+// the last KP / 2 columns.
 // Padding rows and columns of every tile are zero, so mu and E are zero
 // there and need no masks.
 namespace two_sided {
 
-constexpr int kThreads = 320;     // warp 0 producer, warp 1 MMA, warps 2..9 epilogue
+constexpr int kThreads = 352;     // warp 0 producer, warp 1 MMA, warps 2..9 epilogue, warp 10 E stores
 constexpr int kOwn = 128;          // owned rows per item (TMEM lanes)
 constexpr int kBN = 64;            // walked rows per tile
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kGCol = 128;
-constexpr int kMaxStages = 4;
+constexpr int kMaxStages = 6;
 constexpr int kEpiWarps = 8;       // two per TMEM lane quarter, 32 walked columns each
+constexpr int kQueue = 2;          // claimed items on their way from the producer
+constexpr int kMaxHStages = 6;     // columns-item stages (W tile + E halves)
+constexpr uint32_t kEBytes = kOwn * kBN * 2;    // one E tile, BF16
+constexpr uint32_t kStgBytes = kOwn * 64 * 4;     // G staging: 128 rows x 64 FP32 columns
 
 struct Side {
-    const uint16_t *own_sh;     // BF16 shadow tiles of the owned factor
+    const uint16_t *own_sh;     // BF16 shadow tiles of the owned factor (rows items)
     const uint16_t *walk_sh;    // ... of the walked factor
-    const unsigned char *Vt;    // V tiles in this orientation
+    const unsigned char *Vt;    // V tiles (rows items)
     float *G;                   // G rows of the owned factor
     int64_t n_own, n_walk;      // I or J
     int own_tiles;              // 128-row tile slots per owned piece (items, V tiles)
@@ -627,7 +653,13 @@ struct Side {
 
 struct Params {
     Side side[2];
-    int B, part, KP, ldk, stages, vstages, items_a, items;
+    uint16_t *Et;               // the part's E tiles: slot (b * side[0].own_tiles + t) * et_cols + j
+                                // holds the 128 x 64 BF16 image of W tile t x H^T tile j of block b
+    int *sync;                  // [0] items claimed, [1] CTAs finished, [2 + b] rows items of
+                                // block b whose E is in HBM; all zero between launches
+    int et_cols;                // E slots per W tile (2 x the 128-row H^T tiles per piece)
+    int B, part, KP, ldk, stages, hstages, items_a, items;
+    int bars_off;               // shared-memory offset of the barriers (past both layouts)
     float phi_inv, p, mu_min;
     int p_mode;
     int *err;
@@ -635,9 +667,13 @@ struct Params {
 
 struct Bars {
     uint64_t full[kMaxStages], empty[kMaxStages];       // walked factor tiles
-    uint64_t vfull[kMaxStages], vempty[kMaxStages];     // V tiles
     uint64_t mu_full[2], mu_empty[2], e_full[2], e_empty[2];
     uint64_t a_full, a_empty, g_full, g_empty;
+    uint64_t hfull[kMaxHStages], hempty[kMaxHStages];   // columns-item stages
+    uint64_t q_full[kQueue], q_empty[kQueue];           // the item queue
+    uint64_t stg_full, stg_empty;                       // G staging passes (epilogue warps)
+    int q_item[kQueue];
+    int items_done;             // epilogue warps done with an item (its MMAs, reads and drain)
     uint32_t tmem;
     int abort;
 };
@@ -652,18 +688,6 @@ __device__ __forceinline__ void bar_arrive(uint64_t *b)
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(saddr(b)) : "memory");
 }
 
-__device__ __forceinline__ void bar_expect_tx(uint64_t *b, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
-                 :: "r"(saddr(b)), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *b)
-{
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                 :: "r"(saddr(dst)), "l"(src), "r"(bytes), "r"(saddr(b)) : "memory");
-}
-
 // Leader-only forms for warp-uniform loops: every lane executes the
 // instruction with the same (uniform) operands and elect.sync picks the one
 // lane that performs it (the same lane each time, the whole warp being
@@ -675,6 +699,15 @@ __device__ __forceinline__ void expect_tx_if(uint32_t, uint64_t *b, uint32_t byt
     asm volatile("{\n\t.reg .pred e;\n\telect.sync _|e, 0xffffffff;\n\t"
                  "@e mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n\t}"
                  :: "r"(saddr(b)), "r"(bytes) : "memory");
+}
+
+// n arrivals at once (the producer standing in for the epilogue warps on an
+// E buffer that it fills by copy)
+__device__ __forceinline__ void arrive_n_if(uint32_t, uint64_t *b, uint32_t n)
+{
+    asm volatile("{\n\t.reg .pred e;\n\telect.sync _|e, 0xffffffff;\n\t"
+                 "@e mbarrier.arrive.shared::cta.b64 _, [%0], %1;\n\t}"
+                 :: "r"(saddr(b)), "r"(n) : "memory");
 }
 
 __device__ __forceinline__ void bulk_g2s_if(uint32_t, void *dst, const void *src, uint32_t bytes, uint64_t *b)
@@ -758,6 +791,68 @@ __device__ __forceinline__ bool wait32(Bars *S, uint64_t *b, uint32_t parity)
     return ok;
 }
 
+// 16 bytes of data read once (no L1 allocation)
+__device__ __forceinline__ uint4 ldg_stream(const void *p)
+{
+    uint4 r;
+    asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w) : "l"(p));
+    return r;
+}
+
+// Non-blocking test of phase `parity`.
+__device__ __forceinline__ bool bar_test(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile("{\n\t.reg .pred p;\n\t"
+                 "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok) : "r"(saddr(bar)), "r"(parity) : "memory");
+    return ok != 0;
+}
+
+// Two or three waits with one vote when all the phases are already
+// complete (the common case in the steady pipeline), else one by one.
+__device__ __forceinline__ bool wait32x2(Bars *S, uint64_t *a, uint32_t pa, uint64_t *b, uint32_t pb)
+{
+    if (__all_sync(0xffffffffu, bar_test(a, pa) && bar_test(b, pb))) return true;
+    return wait32(S, a, pa) && wait32(S, b, pb);
+}
+
+__device__ __forceinline__ bool wait32x3(Bars *S, uint64_t *a, uint32_t pa, uint64_t *b, uint32_t pb,
+                                         uint64_t *c, uint32_t pc)
+{
+    if (__all_sync(0xffffffffu, bar_test(a, pa) && bar_test(b, pb) && bar_test(c, pc))) return true;
+    return wait32(S, a, pa) && wait32(S, b, pb) && wait32(S, c, pc);
+}
+
+// Bounded wait of the producer warp until another CTA's count in HBM
+// reaches `target` (acquire), then a proxy fence so that the bulk copies
+// issued after it read what the counted warps stored.  Gives up (abort
+// role 1024) after about a second of SM clock, or when the CTA is aborting.
+__device__ __forceinline__ bool wait_count(Bars *S, const int *cnt, int target)
+{
+    int ok = 1;
+    if ((threadIdx.x & 31) == 0) {
+        const long long t0 = clock64();
+        for (uint32_t it = 0;; ++it) {
+            int v;
+            asm volatile("ld.acquire.gpu.b32 %0, [%1];" : "=r"(v) : "l"(cnt) : "memory");
+            if (v >= target) break;
+            if (*(volatile int *)&S->abort != 0) { ok = 0; break; }
+            if (it >= kDenseWaitLimit || clock64() - t0 > kDenseWaitCycles) {
+                atomicOr((int *)&S->abort, 1024);
+                ok = 0;
+                break;
+            }
+            __nanosleep(128);
+        }
+    }
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+    return ok != 0;
+}
+
 // Slot and phase of a ring of n slots, advanced one use at a time.
 struct Ring {
     uint32_t slot = 0, phase = 0;
@@ -768,19 +863,20 @@ struct Ring {
 };
 
 struct Item {
-    int side, own_piece, walk_piece, ot, own_rows_in_tile, nj;
+    int side, block, own_piece, walk_piece, ot, own_rows_in_tile, nj;
     int64_t own_start;
 };
 
-__device__ __forceinline__ bool decode(const Params &P, int it, Item &x)
+// Item k of one side of one context: block b = k / own_tiles pairs row
+// piece b with column piece (b + part) mod B; tile ot of the owned piece.
+__device__ __forceinline__ bool decode(const Params &P, int side, int k, Item &x)
 {
     const int B = P.B;
-    int side = 0, k = it;
-    if (k >= P.items_a) { side = 1; k -= P.items_a; }
     const Side &Sd = P.side[side];
     const int b = k / Sd.own_tiles, ot = k % Sd.own_tiles;
     const int cpiece = (b + P.part) % B;
     x.side = side;
+    x.block = b;
     x.own_piece = side == 0 ? b : cpiece;
     x.walk_piece = side == 0 ? cpiece : b;
     x.ot = ot;
@@ -794,10 +890,11 @@ __device__ __forceinline__ bool decode(const Params &P, int it, Item &x)
     return left > 0;
 }
 
+// (v - mu) max(mu, mu_min)^-p; the 1 / phi goes on G when it is written
 template <int PM>
-__device__ __forceinline__ float tweedie_pm(float p, float phi_inv, float mu_min, float v, float mu)
+__device__ __forceinline__ float tweedie_pm(float p, float mu_min, float v, float mu)
 {
-    const float d = (v - mu) * phi_inv;
+    const float d = v - mu;
     if constexpr (PM == 0) {
         return d;
     } else {
@@ -809,35 +906,59 @@ __device__ __forceinline__ float tweedie_pm(float p, float phi_inv, float mu_min
 }
 
 // Where the items' parameters come from: one context (the kernel parameter)
-// or, batched, a table of contexts in global memory whose items follow one
-// another (context i owns items [item_start[i], item_start[i + 1]); slots
-// `stride` bytes apart).
+// or, batched, a table of contexts in global memory (slots `stride` bytes
+// apart).  Batched, the rows items of every context come first, context i
+// owning [wstart[i], wstart[i + 1]), then the columns items, context i
+// owning [hstart[i], hstart[i + 1]) of those.
 struct Src {
     const unsigned char *tab;
-    const int *item_start;
+    const int *wstart, *hstart;
     int n;
     size_t stride;
 };
 
 template <bool BATCH>
-__device__ __forceinline__ const Params &ctx_of(const Params &P0, const Src &src, int it, int &local)
+__device__ __forceinline__ const Params &item_of(const Params &P0, const Src &src, int it, int &side, int &k)
 {
     if constexpr (!BATCH) {
-        local = it;
+        side = it >= P0.items_a ? 1 : 0;
+        k = side ? it - P0.items_a : it;
         return P0;
     } else {
-        int lo = 0, hi = src.n - 1;          // last i with item_start[i] <= it
+        const int nw = __ldg(src.wstart + src.n);
+        const int *pre = src.wstart;
+        int r = it;
+        side = 0;
+        if (r >= nw) {
+            pre = src.hstart;
+            r -= nw;
+            side = 1;
+        }
+        int lo = 0, hi = src.n - 1;          // last i with pre[i] <= r
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
-            if (__ldg(src.item_start + mid) <= it) lo = mid; else hi = mid - 1;
+            if (__ldg(pre + mid) <= r) lo = mid; else hi = mid - 1;
         }
-        local = it - __ldg(src.item_start + lo);
+        k = r - __ldg(pre + lo);
         return *reinterpret_cast<const Params *>(src.tab + (size_t)lo * src.stride);
     }
 }
 
+// Next claimed item from the queue (MMA and epilogue warps); -1 at the end,
+// -2 if the wait gave up.
+__device__ __forceinline__ int take_item(Bars *S, Ring &rq)
+{
+    if (!wait32(S, &S->q_full[rq.slot], rq.phase)) return -2;
+    const int it = *(volatile int *)&S->q_item[rq.slot];
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) bar_arrive(&S->q_empty[rq.slot]);
+    rq.next(kQueue);
+    return it;
+}
+
 // The kernel body.  P0 gives what is uniform over the launch (K width,
-// ring depths); each item reads its own context's parameters.
+// ring depths, the claim counters); each item reads its own context's
+// parameters.
 template <typename VT, int PM, bool BATCH>
 __device__ __forceinline__ void chain_body(const Params &P0, const Src src, const int total_items)
 {
@@ -848,26 +969,29 @@ __device__ __forceinline__ void chain_body(const Params &P0, const Src src, cons
     const int NA = KP / 64;                                     // 128-byte atoms along K
     const uint32_t a_bytes = (uint32_t)kOwn * KP * 2;           // owned tile
     const uint32_t b_bytes = (uint32_t)kBN * KP * 2;            // walked tile
-    const uint32_t v_bytes = (uint32_t)kOwn * kBN * sizeof(VT); // V tile
-    constexpr uint32_t e_bytes = kOwn * kBN * 2;
+    const uint32_t v_bytes = (uint32_t)kOwn * kBN * sizeof(VT); // V tile (HBM)
     unsigned char *sA = sm;
-    unsigned char *sE = sA + a_bytes;                           // 2 x e_bytes
-    unsigned char *sB = sE + 2 * e_bytes;                       // NS x b_bytes
-    unsigned char *sV = sB + (size_t)P0.stages * b_bytes;       // NV x v_bytes
-    Bars *S = reinterpret_cast<Bars *>(sV + (size_t)P0.vstages * v_bytes);
+    unsigned char *sE = sA + a_bytes;                           // 2 x kEBytes
+    unsigned char *sB = sE + 2 * kEBytes;                       // NS x b_bytes
+    Bars *S = reinterpret_cast<Bars *>(sm + P0.bars_off);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int NS = P0.stages, NV = P0.vstages;
+    const int NS = P0.stages, NH = P0.hstages;
+    const uint32_t h_bytes = b_bytes + kEBytes;                 // columns-item stage: W tile, E halves
+    unsigned char *sStgH = sm + (size_t)NH * h_bytes;           // columns items' G staging
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < NS; ++s) { bar_init(&S->full[s], 1); bar_init(&S->empty[s], 1); }
-        for (int s = 0; s < NV; ++s) { bar_init(&S->vfull[s], 1); bar_init(&S->vempty[s], kEpiWarps); }
         for (int b = 0; b < 2; ++b) {
             bar_init(&S->mu_full[b], 1); bar_init(&S->mu_empty[b], kEpiWarps);
-            bar_init(&S->e_full[b], kEpiWarps); bar_init(&S->e_empty[b], 1);
+            bar_init(&S->e_full[b], kEpiWarps); bar_init(&S->e_empty[b], 2);   // GEMM2 done, E stored
         }
         bar_init(&S->a_full, 1); bar_init(&S->a_empty, 1);
         bar_init(&S->g_full, 1); bar_init(&S->g_empty, kEpiWarps);
+        for (int s = 0; s < NH; ++s) { bar_init(&S->hfull[s], 1); bar_init(&S->hempty[s], 1); }
+        for (int s = 0; s < kQueue; ++s) { bar_init(&S->q_full[s], 1); bar_init(&S->q_empty[s], 2 + kEpiWarps); }
+        bar_init(&S->stg_full, kEpiWarps); bar_init(&S->stg_empty, kEpiWarps);
         S->abort = 0;
+        S->items_done = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
@@ -880,44 +1004,104 @@ __device__ __forceinline__ void chain_body(const Params &P0, const Src src, cons
     fence_after();
     const uint32_t tmem = S->tmem;
 
+    // E buffer use u (a rows-item tile) takes buffer u % 2 for the (u / 2)-th
+    // time; item n completes phase n of g_full.
     if (warp == 0) {
-        // ---------------- producer (whole warp, lane 0 performs)
+        // ---------------- producer (whole warp, one elected lane performs)
         {
             const uint32_t ld = lane == 0;
-            uint32_t ic = 0;
-            Ring rb, rv;
-            for (int it = blockIdx.x; it < total_items; it += gridDim.x) {
-                int lit;
-                const Params &P = ctx_of<BATCH>(P0, src, it, lit);
-                Item x;
-                if (!decode(P, lit, x)) continue;
-                const Side &Sd = P.side[x.side];
-                if (!wait32(S, &S->a_empty, (ic & 1) ^ 1)) goto done0;
-                expect_tx_if(ld, &S->a_full, a_bytes);
-                {
-                    // rows 0..63 and 64..127 come from two 64-row shadow tiles;
-                    // in shared memory each atom holds all 128 rows
-                    const uint16_t *t0 = Sd.own_sh + ((int64_t)x.own_piece * Sd.own_sh64 + 2 * x.ot) * 64 * KP;
-                    for (int a = 0; a < NA; ++a) {
-                        bulk_g2s_if(ld, sA + a * 16384, t0 + a * 4096, 8192, &S->a_full);
-                        bulk_g2s_if(ld, sA + a * 16384 + 8192, t0 + 64 * KP + a * 4096, 8192, &S->a_full);
-                    }
+            uint32_t iw = 0, ic = 0;
+            bool hphase = false;
+            Ring rb, rq, rh;
+            for (;;) {
+                if (!wait32(S, &S->q_empty[rq.slot], rq.phase ^ 1)) goto done0;
+                int it = 0;
+                if (lane == 0) it = atomicAdd(P0.sync, 1);
+                it = __shfl_sync(0xffffffffu, it, 0);
+                if (it >= total_items) it = -1;
+                if (lane == 0) {
+                    S->q_item[rq.slot] = it;
+                    bar_arrive(&S->q_full[rq.slot]);
                 }
-                const unsigned char *vbase =
-                    Sd.Vt + ((((int64_t)x.own_piece * P.B + x.walk_piece) * Sd.own_tiles + x.ot) *
-                             Sd.walk_tiles) * (int64_t)v_bytes;
-                for (int j = 0; j < x.nj; ++j) {
-                    const uint32_t st = rb.slot, sv = rv.slot;
-                    if (!wait32(S, &S->empty[st], rb.phase ^ 1)) goto done0;
-                    expect_tx_if(ld, &S->full[st], b_bytes);
-                    bulk_g2s_if(ld, sB + (size_t)st * b_bytes,
-                                Sd.walk_sh + ((int64_t)x.walk_piece * Sd.walk_sh64 + j) * kBN * KP,
-                                b_bytes, &S->full[st]);
-                    if (!wait32(S, &S->vempty[sv], rv.phase ^ 1)) goto done0;
-                    expect_tx_if(ld, &S->vfull[sv], v_bytes);
-                    bulk_g2s_if(ld, sV + (size_t)sv * v_bytes, vbase + (int64_t)j * v_bytes, v_bytes, &S->vfull[sv]);
-                    rb.next(NS);
-                    rv.next(NV);
+                __syncwarp();
+                rq.next(kQueue);
+                if (it < 0) break;
+                int side, k;
+                const Params &P = item_of<BATCH>(P0, src, it, side, k);
+                Item x;
+                if (!decode(P, side, k, x)) continue;
+                const Side &Sd = P.side[side];
+                if (side == 0) {
+                    // rows item: the owned W tile, then the walked H^T and V tiles
+                    if (hphase) {                     // cannot happen: rows items are claimed first
+                        atomicOr((int *)&S->abort, 128);
+                        goto done0;
+                    }
+                    if (!wait32(S, &S->a_empty, (iw & 1) ^ 1)) goto done0;
+                    expect_tx_if(ld, &S->a_full, a_bytes);
+                    {
+                        // rows 0..63 and 64..127 come from two 64-row shadow tiles;
+                        // in shared memory each atom holds all 128 rows
+                        const uint16_t *t0 = Sd.own_sh + ((int64_t)x.own_piece * Sd.own_sh64 + 2 * x.ot) * 64 * KP;
+                        for (int a = 0; a < NA; ++a) {
+                            bulk_g2s_if(ld, sA + a * 16384, t0 + a * 4096, 8192, &S->a_full);
+                            bulk_g2s_if(ld, sA + a * 16384 + 8192, t0 + 64 * KP + a * 4096, 8192, &S->a_full);
+                        }
+                    }
+                    ++iw;
+                    for (int j = 0; j < x.nj; ++j) {
+                        const uint32_t st = rb.slot;
+                        if (!wait32(S, &S->empty[st], rb.phase ^ 1)) goto done0;
+                        expect_tx_if(ld, &S->full[st], b_bytes);
+                        bulk_g2s_if(ld, sB + (size_t)st * b_bytes,
+                                    Sd.walk_sh + ((int64_t)x.walk_piece * Sd.walk_sh64 + j) * kBN * KP,
+                                    b_bytes, &S->full[st]);
+                        rb.next(NS);
+                    }
+                } else {
+                    // columns item: once the block's rows items have stored E,
+                    // per 64 W rows the W tile and the E halves of the owned
+                    // columns (E tiles 2 ot and 2 ot + 1 of each W tile)
+                    if (!hphase) {
+                        // the first one: once every earlier (rows) item's G is
+                        // complete, their MMAs, copies and epilogue reads of
+                        // shared memory are all done.  A count, not a wait on
+                        // g_full: the producer may be two items ahead, where a
+                        // phase parity would already read as complete.
+                        int ok = 1;
+                        if (lane == 0) {
+                            const long long t0 = clock64();
+                            while (*(volatile int *)&S->items_done < kEpiWarps * (int)ic) {
+                                if (*(volatile int *)&S->abort != 0) { ok = 0; break; }
+                                if (clock64() - t0 > kDenseWaitCycles) {
+                                    atomicOr((int *)&S->abort, 128);
+                                    ok = 0;
+                                    break;
+                                }
+                            }
+                        }
+                        if (!__shfl_sync(0xffffffffu, ok, 0)) goto done0;
+                        hphase = true;
+                    }
+                    const int64_t wrows = ((int64_t)(x.walk_piece + 1) * Sd.n_walk) / P.B -
+                                          ((int64_t)x.walk_piece * Sd.n_walk) / P.B;
+                    const int target = (int)((wrows + kOwn - 1) / kOwn);
+                    if (!wait_count(S, P.sync + 2 + x.block, target)) goto done0;
+                    const uint16_t *e0 =
+                        P.Et + (((int64_t)x.block * P.side[0].own_tiles) * P.et_cols + 2 * x.ot) * (kEBytes / 2);
+                    for (int s = 0; s < x.nj; ++s) {
+                        const uint32_t sh = rh.slot;
+                        unsigned char *stage = sm + (size_t)sh * h_bytes;
+                        if (!wait32(S, &S->hempty[sh], rh.phase ^ 1)) goto done0;
+                        expect_tx_if(ld, &S->hfull[sh], h_bytes);
+                        bulk_g2s_if(ld, stage, Sd.walk_sh + ((int64_t)x.walk_piece * Sd.walk_sh64 + s) * kBN * KP,
+                                    b_bytes, &S->hfull[sh]);
+                        const uint16_t *es = e0 + (int64_t)(s >> 1) * P.et_cols * (kEBytes / 2) +
+                                             (s & 1) * (kEBytes / 4);
+                        bulk_g2s_if(ld, stage + b_bytes, es, kEBytes / 2, &S->hfull[sh]);
+                        bulk_g2s_if(ld, stage + b_bytes + kEBytes / 2, es + kEBytes / 2, kEBytes / 2, &S->hfull[sh]);
+                        rh.next(NH);
+                    }
                 }
                 ++ic;
             }
@@ -925,77 +1109,103 @@ __device__ __forceinline__ void chain_body(const Params &P0, const Src src, cons
     done0:
         __syncwarp();
     } else if (warp == 1) {
-        // ---------------- MMA issuer (whole warp, lane 0 performs).  Tile
-        // number tc (counted over the CTA's items) uses mu / E buffer tc % 2,
-        // for the (tc / 2)-th time.
+        // ---------------- MMA issuer (whole warp, one elected lane performs)
         {
             const uint32_t ld = lane == 0;
-            uint32_t tc = 0, ic = 0;
-            Ring r1, r2;     // walked-tile slots of GEMM1 (tile tc) and GEMM2 (tile tc - 1)
+            uint32_t iw = 0, ic = 0, tw = 0, te = 0;     // rows items, items, mu uses, E uses
+            Ring r1, r2, rq, rh; // walked-tile slots of GEMM1 (tile j) and GEMM2 (tile j - 1); stages
             const uint32_t id1 = idesc_bf16(kOwn, kBN);
             const uint32_t id2 = idesc_bf16(kOwn, KP, 0, 1);
+            const uint32_t id3 = idesc_bf16(kOwn, KP, 1, 1);
             // K-major, 128-byte swizzle: 8-row groups 1024 B apart; a K step of
             // 16 entries moves 32 B inside an atom, 4 steps fill an atom, and the
             // next atom of the owned tile starts 128 rows x 128 B further
             const uint32_t aA = saddr(sA);
             const uint32_t tA = tmem + (kTmemCols - (uint32_t)KP / 2);   // owned tile in TMEM
-            for (int it = blockIdx.x; it < total_items; it += gridDim.x) {
-                int lit;
-                const Params &P = ctx_of<BATCH>(P0, src, it, lit);
+            for (;;) {
+                const int it = take_item(S, rq);
+                if (it == -2) goto done1;
+                if (it < 0) break;
+                int side, k;
+                const Params &P = item_of<BATCH>(P0, src, it, side, k);
                 Item x;
-                if (!decode(P, lit, x)) continue;
-                if (!wait32(S, &S->a_full, ic & 1)) goto done1;
-                fence_after();
-                // the owned tile into TMEM once per item (ordered after the
-                // previous item's MMAs and before this item's: same issuing
-                // thread); its shared-memory slot is free when the copies are
-                switch (KP) {
-                case 64: own_to_tmem<64>(ld, tA, aA); break;
-                case 128: own_to_tmem<128>(ld, tA, aA); break;
-                case 192: own_to_tmem<192>(ld, tA, aA); break;
-                default: own_to_tmem<256>(ld, tA, aA); break;
-                }
-                commit_if(ld, &S->a_empty);
-                for (int j = 0; j <= x.nj; ++j) {
-                    if (j < x.nj) {
-                        const uint32_t st = r1.slot;
-                        const int b = (int)(tc & 1);
-                        if (!wait32(S, &S->full[st], r1.phase)) goto done1;
-                        if (!wait32(S, &S->mu_empty[b], ((tc >> 1) & 1) ^ 1)) goto done1;
-                        fence_after();
-                        const uint32_t aB = saddr(sB + (size_t)st * b_bytes);
-                        const uint32_t dmu = tmem + (uint32_t)(b * kBN);
-                        switch (KP) {
-                        case 64: gemm1_tile<64>(ld, dmu, tA, aB, id1); break;
-                        case 128: gemm1_tile<128>(ld, dmu, tA, aB, id1); break;
-                        case 192: gemm1_tile<192>(ld, dmu, tA, aB, id1); break;
-                        default: gemm1_tile<256>(ld, dmu, tA, aB, id1); break;
-                        }
-                        commit_if(ld, &S->mu_full[b]);
-                        ++tc;
-                        r1.next(NS);
+                if (!decode(P, side, k, x)) continue;
+                if (side == 0) {
+                    if (!wait32(S, &S->a_full, iw & 1)) goto done1;
+                    fence_after();
+                    // the owned tile into TMEM once per item (ordered after the
+                    // previous item's MMAs and before this item's: same issuing
+                    // thread); its shared-memory slot is free when the copies are
+                    switch (KP) {
+                    case 64: own_to_tmem<64>(ld, tA, aA); break;
+                    case 128: own_to_tmem<128>(ld, tA, aA); break;
+                    case 192: own_to_tmem<192>(ld, tA, aA); break;
+                    default: own_to_tmem<256>(ld, tA, aA); break;
                     }
-                    if (j > 0) {
-                        // GEMM2 of tile j - 1 (tile number tp)
-                        const uint32_t tp = j < x.nj ? tc - 2 : tc - 1;
-                        const int b = (int)(tp & 1);
-                        const uint32_t st = r2.slot;
-                        if (!wait32(S, &S->e_full[b], (tp >> 1) & 1)) goto done1;
-                        if (j == 1 && !wait32(S, &S->g_empty, (ic & 1) ^ 1)) goto done1;
+                    commit_if(ld, &S->a_empty);
+                    ++iw;
+                    for (int j = 0; j <= x.nj; ++j) {
+                        if (j < x.nj) {
+                            const uint32_t st = r1.slot;
+                            const uint32_t bm = tw & 1;
+                            if (!wait32x2(S, &S->full[st], r1.phase, &S->mu_empty[bm], ((tw >> 1) & 1) ^ 1))
+                                goto done1;
+                            fence_after();
+                            const uint32_t aB = saddr(sB + (size_t)st * b_bytes);
+                            const uint32_t dmu = tmem + bm * (uint32_t)kBN;
+                            switch (KP) {
+                            case 64: gemm1_tile<64>(ld, dmu, tA, aB, id1); break;
+                            case 128: gemm1_tile<128>(ld, dmu, tA, aB, id1); break;
+                            case 192: gemm1_tile<192>(ld, dmu, tA, aB, id1); break;
+                            default: gemm1_tile<256>(ld, dmu, tA, aB, id1); break;
+                            }
+                            commit_if(ld, &S->mu_full[bm]);
+                            ++tw;
+                            r1.next(NS);
+                        }
+                        if (j > 0) {
+                            // GEMM2 of tile j - 1
+                            const uint32_t be = te & 1;
+                            const uint32_t st = r2.slot;
+                            if (!wait32(S, &S->e_full[be], (te >> 1) & 1)) goto done1;
+                            if (j == 1 && !wait32(S, &S->g_empty, (ic & 1) ^ 1)) goto done1;
+                            fence_after();
+                            // A = E (K-major, one atom of 64 walked columns); B = the
+                            // walked tile read MN-major: MN atoms (64 entries of k)
+                            // 64 rows x 128 B apart (LBO), 8-row K groups 1024 B apart
+                            // (SBO), a K step of 16 walked rows = 2048 B
+                            const uint64_t dE = sdesc_sw128(saddr(sE + be * kEBytes), 16, 1024);
+                            const uint64_t dBt = sdesc_sw128(saddr(sB + (size_t)st * b_bytes), kBN * 128, 1024);
+#pragma unroll
+                            for (int ks = 0; ks < kBN / 16; ++ks)
+                                mma_ss_if(ld, tmem + kGCol, dE + (uint64_t)(ks * 2), dBt + (uint64_t)(ks * 128),
+                                          id2, (j > 1 || ks > 0));
+                            commit_if(ld, &S->e_empty[be]);
+                            commit_if(ld, &S->empty[st]);
+                            ++te;
+                            r2.next(NS);
+                        }
+                    }
+                } else {
+                    // G (owned H^T rows) += E^T . W over the block's W rows, 64
+                    // at a time.  A = the two E halves read MN-major (64 owned
+                    // rows per 128-byte atom column, the second half 8 KB on,
+                    // 8 W rows per 1024 B); B = the W tile read MN-major as in
+                    // GEMM2.  A K step of 16 W rows is 2048 B in both.
+                    for (int s = 0; s < x.nj; ++s) {
+                        const uint32_t sh = rh.slot;
+                        const uint32_t stage = saddr(sm) + sh * h_bytes;
+                        if (!wait32(S, &S->hfull[sh], rh.phase)) goto done1;
+                        if (s == 0 && !wait32(S, &S->g_empty, (ic & 1) ^ 1)) goto done1;
                         fence_after();
-                        // A = E (K-major, one atom of 64 walked columns); B = the
-                        // walked tile read MN-major: MN atoms (64 entries of k)
-                        // 64 rows x 128 B apart (LBO), 8-row K groups 1024 B apart
-                        // (SBO), a K step of 16 walked rows = 2048 B
-                        const uint64_t dE = sdesc_sw128(saddr(sE + b * e_bytes), 16, 1024);
-                        const uint64_t dBt = sdesc_sw128(saddr(sB + (size_t)st * b_bytes), kBN * 128, 1024);
+                        const uint64_t dEt = sdesc_sw128(stage + b_bytes, kEBytes / 2, 1024);
+                        const uint64_t dW = sdesc_sw128(stage, kBN * 128, 1024);
 #pragma unroll
                         for (int ks = 0; ks < kBN / 16; ++ks)
-                            mma_ss_if(ld, tmem + kGCol, dE + (uint64_t)(ks * 2), dBt + (uint64_t)(ks * 128),
-                                      id2, (j > 1 || ks > 0));
-                        commit_if(ld, &S->e_empty[b]);
-                        commit_if(ld, &S->empty[st]);
-                        r2.next(NS);
+                            mma_ss_if(ld, tmem + kGCol, dEt + (uint64_t)(ks * 128), dW + (uint64_t)(ks * 128), id3,
+                                      (s > 0 || ks > 0));
+                        commit_if(ld, &S->hempty[sh]);
+                        rh.next(NH);
                     }
                 }
                 commit_if(ld, &S->g_full);
@@ -1004,6 +1214,48 @@ __device__ __forceinline__ void chain_body(const Params &P0, const Src src, cons
         }
     done1:
         __syncwarp();
+    } else if (warp == 2 + kEpiWarps) {
+        // ---------------- E stores (warp 10, lane 0 performs): each rows-item
+        // E tile, once the epilogue has built it, to HBM with one bulk copy;
+        // the buffer's second release (the first is GEMM2's commit) once the
+        // copy has read it; after the item's last tile, the count that its
+        // block's columns items wait for
+        uint32_t te = 0;
+        Ring rq;
+        for (;;) {
+            const int it = take_item(S, rq);
+            if (it == -2) goto done3;
+            if (it < 0) break;
+            int side, k;
+            const Params &P = item_of<BATCH>(P0, src, it, side, k);
+            Item x;
+            if (!decode(P, side, k, x) || side != 0) continue;
+            unsigned char *eg = reinterpret_cast<unsigned char *>(
+                P.Et + ((int64_t)x.block * P.side[0].own_tiles + x.ot) * P.et_cols * (kEBytes / 2));
+            for (int j = 0; j < x.nj; ++j, ++te) {
+                const uint32_t be = te & 1;
+                if (!wait32(S, &S->e_full[be], (te >> 1) & 1)) goto done3;
+                if (lane == 0)
+                    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n\t"
+                                 "cp.async.bulk.commit_group;\n\t"
+                                 "cp.async.bulk.wait_group.read 0;"
+                                 :: "l"(eg + (size_t)j * kEBytes), "r"(saddr(sE + be * kEBytes)), "r"(kEBytes)
+                                 : "memory");
+                __syncwarp();
+                if (lane == 0) bar_arrive(&S->e_empty[be]);
+            }
+            // the item's E complete in HBM: count it (release after the
+            // async-proxy writes)
+            if (lane == 0) {
+                asm volatile("cp.async.bulk.wait_group 0;\n\tfence.proxy.async.global;" ::: "memory");
+                __threadfence();
+                atomicAdd(P.sync + 2 + x.block, 1);
+            }
+            __syncwarp();
+        }
+    done3:
+        if (lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+        __syncwarp();
     } else {
         // ---------------- epilogue (warps 2..9): TMEM lane quarter warp % 4,
         // walked columns 32 h .. 32 h + 31 of each tile, h = (warp - 2) / 4
@@ -1011,91 +1263,155 @@ __device__ __forceinline__ void chain_body(const Params &P0, const Src src, cons
         const int rho = 32 * q + lane;                      // owned row in the tile
         const int c = 32 * hc;
         const uint32_t lane_base = (uint32_t)(32 * q) << 16;
-        uint32_t tc = 0, ic = 0;
-        Ring rv;
-        for (int it = blockIdx.x; it < total_items; it += gridDim.x) {
-            int lit;
-            const Params &P = ctx_of<BATCH>(P0, src, it, lit);
+        uint32_t ic = 0, tw = 0, te = 0, np = 0;   // items, mu uses, E uses, staging passes
+        Ring rq;
+        for (;;) {
+            const int it = take_item(S, rq);
+            if (it == -2) goto done2;
+            if (it < 0) break;
+            int side, k;
+            const Params &P = item_of<BATCH>(P0, src, it, side, k);
             Item x;
-            if (!decode(P, lit, x)) continue;
-            const Side &Sd = P.side[x.side];
-            const float pp = P.p, phi_inv = P.phi_inv, mu_min = P.mu_min;
-            for (int j = 0; j < x.nj; ++j, ++tc, rv.next(NV)) {
-                const int b = (int)(tc & 1);
-                const uint32_t sv = rv.slot;
-                const uint32_t ph = (tc >> 1) & 1;
-                if (!wait32(S, &S->vfull[sv], rv.phase)) goto done2;
-                if (!wait32(S, &S->mu_full[b], ph)) goto done2;
-                if (!wait32(S, &S->e_empty[b], ph ^ 1)) goto done2;
-                fence_after();
-                const unsigned char *vt = sV + (size_t)sv * v_bytes;
-                unsigned char *eb = sE + b * e_bytes;
-                float mu[32];
-                tmem_ld32(tmem + lane_base + (uint32_t)(b * kBN + c), mu);
-                float v[32];
-                if constexpr (sizeof(VT) == 4) {
+            if (!decode(P, side, k, x)) continue;
+            const Side &Sd = P.side[side];
+            if (side == 0) {
+                const float pp = P.p, mu_min = P.mu_min;
+                // V straight from HBM into registers, two tiles ahead: this
+                // thread's 16-byte chunks (c / (16 / sizeof(VT)) + i, row rho)
+                // of each tile, a warp reading 512 contiguous bytes per load
+                constexpr int kVQ = sizeof(VT) == 4 ? 8 : 4;
+                const unsigned char *vrow =
+                    Sd.Vt + (((int64_t)x.own_piece * P.B + x.walk_piece) * Sd.own_tiles + x.ot) * Sd.walk_tiles *
+                                (int64_t)v_bytes +
+                    ((size_t)(c / (int)(16 / sizeof(VT))) * kOwn + rho) * 16;
+                uint4 qa[kVQ], qb[kVQ];
+                auto vload = [&](uint4 (&q)[kVQ], int jj) {
+                    if (jj < x.nj) {
+                        const unsigned char *src_v = vrow + (int64_t)jj * v_bytes;
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        const float4 w = *reinterpret_cast<const float4 *>(
-                            vt + ((size_t)((c >> 2) + i) * kOwn + rho) * 16);
-                        v[4 * i] = w.x; v[4 * i + 1] = w.y; v[4 * i + 2] = w.z; v[4 * i + 3] = w.w;
+                        for (int i = 0; i < kVQ; ++i) q[i] = ldg_stream(src_v + (size_t)i * kOwn * 16);
                     }
-                } else {
+                };
+                // one walked tile: E from TMEM mu and the V chunks in q
+                auto tile = [&](const uint4 (&q)[kVQ]) -> bool {
+                    const uint32_t bm = tw & 1, be = te & 1;
+                    if (!wait32x2(S, &S->mu_full[bm], (tw >> 1) & 1, &S->e_empty[be], ((te >> 1) & 1) ^ 1))
+                        return false;
+                    fence_after();
+                    unsigned char *eb = sE + be * kEBytes;
+                    float mu[32];
+                    tmem_ld32(tmem + lane_base + bm * (uint32_t)kBN + (uint32_t)c, mu);
+                    float v[32];
+                    if constexpr (sizeof(VT) == 4) {
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const uint4 w = *reinterpret_cast<const uint4 *>(
-                            vt + ((size_t)((c >> 3) + i) * kOwn + rho) * 16);
-                        const uint32_t u[4] = {w.x, w.y, w.z, w.w};
+                        for (int i = 0; i < 8; ++i) {
+                            v[4 * i] = __uint_as_float(q[i].x); v[4 * i + 1] = __uint_as_float(q[i].y);
+                            v[4 * i + 2] = __uint_as_float(q[i].z); v[4 * i + 3] = __uint_as_float(q[i].w);
+                        }
+                    } else {
 #pragma unroll
-                        for (int h = 0; h < 4; ++h) {
-                            v[8 * i + 2 * h] = __uint_as_float(u[h] << 16);
-                            v[8 * i + 2 * h + 1] = __uint_as_float(u[h] & 0xffff0000u);
+                        for (int i = 0; i < 4; ++i) {
+                            const uint32_t u[4] = {q[i].x, q[i].y, q[i].z, q[i].w};
+#pragma unroll
+                            for (int h = 0; h < 4; ++h) {
+                                v[8 * i + 2 * h] = __uint_as_float(u[h] << 16);
+                                v[8 * i + 2 * h + 1] = __uint_as_float(u[h] & 0xffff0000u);
+                            }
                         }
                     }
-                }
-                uint32_t pk[16];
+                    uint32_t pk[16];
 #pragma unroll
-                for (int h = 0; h < 16; ++h) {
-                    const float e0 = tweedie_pm<PM>(pp, phi_inv, mu_min, v[2 * h], mu[2 * h]);
-                    const float e1 = tweedie_pm<PM>(pp, phi_inv, mu_min, v[2 * h + 1], mu[2 * h + 1]);
-                    __nv_bfloat162 t2 = __floats2bfloat162_rn(e0, e1);
-                    pk[h] = *reinterpret_cast<uint32_t *>(&t2);
-                }
-                // E (owned row rho, walked columns c..c+31): row rho of the
-                // 128-byte-swizzled atom column, chunk (c/8 + g) ^ (rho % 8)
+                    for (int h = 0; h < 16; ++h) {
+                        const float e0 = tweedie_pm<PM>(pp, mu_min, v[2 * h], mu[2 * h]);
+                        const float e1 = tweedie_pm<PM>(pp, mu_min, v[2 * h + 1], mu[2 * h + 1]);
+                        __nv_bfloat162 t2 = __floats2bfloat162_rn(e0, e1);
+                        pk[h] = *reinterpret_cast<uint32_t *>(&t2);
+                    }
+                    // E (owned row rho, walked columns c..c+31): row rho of the
+                    // 128-byte-swizzled atom column, chunk (c/8 + g) ^ (rho % 8)
 #pragma unroll
-                for (int g = 0; g < 4; ++g)
-                    *reinterpret_cast<uint4 *>(eb + rho * 128 + ((((c >> 3) + g) ^ (rho & 7)) << 4)) =
-                        make_uint4(pk[4 * g], pk[4 * g + 1], pk[4 * g + 2], pk[4 * g + 3]);
-                fence_async_smem();
-                fence_before();
-                __syncwarp();
-                if (lane == 0) {
-                    bar_arrive(&S->vempty[sv]);
-                    bar_arrive(&S->mu_empty[b]);
-                    bar_arrive(&S->e_full[b]);
-                }
-            }
-            // the item's G rows: this warp's lane quarter, every other 32-column chunk
-            if (!wait32(S, &S->g_full, ic & 1)) goto done2;
-            fence_after();
-            {
-                const bool rv = rho < x.own_rows_in_tile;
-                float *dst = Sd.G + (x.own_start + (int64_t)x.ot * kOwn + rho) * P.ldk;
-                for (int cc = 32 * hc; cc < KP; cc += 64) {
-                    float g[32];
-                    tmem_ld32(tmem + lane_base + kGCol + (uint32_t)cc, g);
-                    if (rv) {
-#pragma unroll
-                        for (int h = 0; h < 32; h += 4)
-                            if (cc + h < P.ldk)
-                                *reinterpret_cast<float4 *>(dst + cc + h) = make_float4(g[h], g[h + 1], g[h + 2], g[h + 3]);
+                    for (int g = 0; g < 4; ++g)
+                        *reinterpret_cast<uint4 *>(eb + rho * 128 + ((((c >> 3) + g) ^ (rho & 7)) << 4)) =
+                            make_uint4(pk[4 * g], pk[4 * g + 1], pk[4 * g + 2], pk[4 * g + 3]);
+                    fence_async_smem();
+                    fence_before();
+                    __syncwarp();
+                    if (lane == 0) {
+                        bar_arrive(&S->mu_empty[bm]);
+                        bar_arrive(&S->e_full[be]);
+                    }
+                    ++tw;
+                    ++te;
+                    return true;
+                };
+                vload(qa, 0);
+                vload(qb, 1);
+                for (int j = 0; j < x.nj; j += 2) {
+                    if (!tile(qa)) goto done2;
+                    vload(qa, j + 2);
+                    if (j + 1 < x.nj) {
+                        if (!tile(qb)) goto done2;
+                        vload(qb, j + 3);
                     }
                 }
             }
-            fence_before();
-            __syncwarp();
-            if (lane == 0) bar_arrive(&S->g_empty);
+            // the item's G rows (times 1 / phi) to HBM, coalesced through a
+            // 32 KB staging buffer: passes of 64 columns; in each, every warp
+            // puts its 32 rows x 32 columns (lane quarter q, half hc) in the
+            // buffer (16-byte chunk k of row r at chunk position k ^ (r % 8),
+            // so both the writes and the reads are free of bank conflicts),
+            // then stores 16 whole 256-byte row segments, two rows per
+            // instruction.  Staging: the E buffers for a rows item (free once
+            // its last GEMM2 and E store have read them), a buffer of its own
+            // for a columns item.  The passes are ordered by two mbarriers
+            // (bounded waits), so a warp that gives up cannot strand the others.
+            if (!wait32(S, &S->g_full, ic & 1)) goto done2;
+            {
+                unsigned char *stg = sStgH;
+                if (side == 0) {
+                    if (!wait32x2(S, &S->e_empty[te & 1], ((te >> 1) & 1) ^ 1, &S->e_empty[(te + 1) & 1],
+                                  (((te + 1) >> 1) & 1) ^ 1))
+                        goto done2;
+                    stg = sE;
+                }
+                fence_after();
+                const float phi_inv = P.phi_inv;
+                const int w8 = warp - 2;
+                float *gbase = Sd.G + (x.own_start + (int64_t)x.ot * kOwn) * P.ldk;
+                for (int cp = 0; cp < KP; cp += 64, ++np) {
+                    float g[32];
+                    tmem_ld32(tmem + lane_base + kGCol + (uint32_t)(cp + c), g);
+                    if (cp + 64 >= KP) {
+                        // this warp's last TMEM read of the item: G may be reused
+                        fence_before();
+                        __syncwarp();
+                        if (lane == 0) bar_arrive(&S->g_empty);
+                    }
+                    if (!wait32(S, &S->stg_empty, (np & 1) ^ 1)) goto done2;
+#pragma unroll
+                    for (int i = 0; i < 8; ++i)
+                        *reinterpret_cast<float4 *>(stg + rho * 256 + (((hc * 8 + i) ^ (rho & 7)) << 4)) =
+                            make_float4(g[4 * i], g[4 * i + 1], g[4 * i + 2], g[4 * i + 3]);
+                    __syncwarp();
+                    if (lane == 0) bar_arrive(&S->stg_full);
+                    if (!wait32(S, &S->stg_full, np & 1)) goto done2;
+#pragma unroll
+                    for (int s2 = 0; s2 < 8; ++s2) {
+                        const int r = 16 * w8 + 2 * s2 + (lane >> 4), ch = lane & 15;
+                        const float4 val =
+                            *reinterpret_cast<const float4 *>(stg + r * 256 + ((ch ^ (r & 7)) << 4));
+                        const int col = cp + 4 * ch;
+                        if (r < x.own_rows_in_tile && col < P.ldk)
+                            *reinterpret_cast<float4 *>(gbase + (int64_t)r * P.ldk + col) =
+                                make_float4(val.x * phi_inv, val.y * phi_inv, val.z * phi_inv, val.w * phi_inv);
+                    }
+                    __syncwarp();
+                    if (lane == 0) bar_arrive(&S->stg_empty);
+                }
+            }
+            // the item is done with shared memory and TMEM (the producer's
+            // columns stages may take over once every earlier item is)
+            if (lane == 0) atomicAdd(&S->items_done, 1);
             ++ic;
         }
     done2:
@@ -1105,12 +1421,31 @@ __device__ __forceinline__ void chain_body(const Params &P0, const Src src, cons
     fence_before();
     __syncthreads();
     fence_after();
-    if (threadIdx.x == 0 && S->abort) {                      // two-sided kernel (+ role)
-        if constexpr (BATCH) {
-            for (int i = 0; i < src.n; ++i)
-                atomicOr(reinterpret_cast<const Params *>(src.tab + (size_t)i * src.stride)->err, 64 | S->abort);
-        } else {
-            atomicOr(P0.err, 64 | S->abort);
+    if (threadIdx.x == 0) {
+        if (S->abort) {                                      // two-sided kernel (+ role)
+            if constexpr (BATCH) {
+                for (int i = 0; i < src.n; ++i)
+                    atomicOr(reinterpret_cast<const Params *>(src.tab + (size_t)i * src.stride)->err,
+                             64 | S->abort);
+            } else {
+                atomicOr(P0.err, 64 | S->abort);
+            }
+        }
+        // the last CTA to finish (every item claimed and done, or given up)
+        // sets the launch's counters back to zero
+        __threadfence();
+        if (atomicAdd(P0.sync + 1, 1) == (int)gridDim.x - 1) {
+            __threadfence();
+            if constexpr (BATCH) {
+                for (int i = 0; i < src.n; ++i) {
+                    const Params &Pi = *reinterpret_cast<const Params *>(src.tab + (size_t)i * src.stride);
+                    for (int b = 0; b < Pi.B; ++b) Pi.sync[2 + b] = 0;
+                }
+            } else {
+                for (int b = 0; b < P0.B; ++b) P0.sync[2 + b] = 0;
+            }
+            P0.sync[0] = 0;
+            P0.sync[1] = 0;
         }
     }
     if (warp == 1)
@@ -1121,16 +1456,16 @@ __device__ __forceinline__ void chain_body(const Params &P0, const Src src, cons
 template <typename VT, int PM>
 __global__ void __launch_bounds__(kThreads, 1) chain_kernel(const __grid_constant__ Params P)
 {
-    chain_body<VT, PM, false>(P, Src{nullptr, nullptr, 1, 0}, P.items);
+    chain_body<VT, PM, false>(P, Src{nullptr, nullptr, nullptr, 1, 0}, P.items);
 }
 
 // Many contexts of one K width, V type and power in one persistent launch.
 template <typename VT, int PM>
 __global__ void __launch_bounds__(kThreads, 1)
-chain_batch_kernel(const unsigned char *tab, size_t stride, const int *item_start, int n)
+chain_batch_kernel(const unsigned char *tab, size_t stride, const int *wstart, const int *hstart, int n)
 {
-    chain_body<VT, PM, true>(*reinterpret_cast<const Params *>(tab), Src{tab, item_start, n, stride},
-                             __ldg(item_start + n));
+    chain_body<VT, PM, true>(*reinterpret_cast<const Params *>(tab), Src{tab, wstart, hstart, n, stride},
+                             __ldg(wstart + n) + __ldg(hstart + n));
 }
 
 }  // namespace two_sided
@@ -1248,7 +1583,7 @@ ChainFn pick_chain(bool vb, int pm)
     return f[vb ? 1 : 0][pm];
 }
 
-using ChainBatchFn = void (*)(const unsigned char *, size_t, const int *, int);
+using ChainBatchFn = void (*)(const unsigned char *, size_t, const int *, const int *, int);
 
 ChainBatchFn pick_chain_batch(bool vb, int pm)
 {
@@ -1260,33 +1595,55 @@ ChainBatchFn pick_chain_batch(bool vb, int pm)
     return f[vb ? 1 : 0][pm];
 }
 
-size_t two_sided_bytes(int KP, int vsize, int stages, int vstages)
+// Shared memory: the rows items' layout (owned tile, E buffers, walked-tile
+// ring) and the columns items' (stages, G staging) share one region; the
+// barriers follow it.
+size_t two_sided_rows_layout(int KP, int stages)
 {
-    return (size_t)two_sided::kOwn * KP * 2 + 2 * (size_t)two_sided::kOwn * two_sided::kBN * 2 +
-           (size_t)stages * two_sided::kBN * KP * 2 +
-           (size_t)vstages * two_sided::kOwn * two_sided::kBN * vsize + sizeof(two_sided::Bars) + 16 +
-           1024;   // alignment slack
+    return (size_t)two_sided::kOwn * KP * 2 + 2 * (size_t)two_sided::kEBytes +
+           (size_t)stages * two_sided::kBN * KP * 2;
+}
+
+constexpr size_t kTwoSidedExtra = sizeof(two_sided::Bars) + 16 + 1024;   // barriers, alignment slack
+constexpr size_t kTwoSidedMax = 232448;
+
+// Columns-item stages: as many W tile + E halves stages as fit beside their
+// G staging buffer, at most kMaxHStages.
+int two_sided_hstages(int KP)
+{
+    const size_t h = (size_t)two_sided::kBN * KP * 2 + two_sided::kEBytes;
+    const size_t room = kTwoSidedMax - kTwoSidedExtra - two_sided::kStgBytes;
+    return (int)std::min<size_t>(room / h, two_sided::kMaxHStages);
+}
+
+size_t two_sided_bars_off(int KP, int stages)
+{
+    const size_t h = (size_t)two_sided::kBN * KP * 2 + two_sided::kEBytes;
+    return std::max(two_sided_rows_layout(KP, stages), (size_t)two_sided_hstages(KP) * h + two_sided::kStgBytes);
+}
+
+size_t two_sided_bytes(int KP, int stages)
+{
+    return two_sided_bars_off(KP, stages) + kTwoSidedExtra;
 }
 
 // At least half of an SM's shared memory, so that one CTA (and one 512-column
 // TMEM allocation) runs per SM.
-size_t two_sided_smem(int KP, int vsize, int stages, int vstages)
+size_t two_sided_smem(int KP, int stages)
 {
-    return std::max<size_t>(two_sided_bytes(KP, vsize, stages, vstages), 120 * 1024);
+    return std::max<size_t>(two_sided_bytes(KP, stages), 120 * 1024);
 }
 
-// Ring depths: two V slots (they free as soon as the epilogue has read
-// them), then as many walked-factor slots as fit (2 .. 4), then a third V
-// slot if it still fits.
-void two_sided_stages(int KP, int vsize, int *stages, int *vstages)
+// Walked-tile ring depth: as many slots as fit beside the owned tile and the
+// E buffers (2 .. kMaxStages).
+int two_sided_stages(int KP)
 {
     int s = two_sided::kMaxStages;
-    while (s > 2 && two_sided_bytes(KP, vsize, s, 2) > 232448) --s;
-    int v = 2;
-    if (two_sided_bytes(KP, vsize, s, 3) <= 232448) v = 3;
-    *stages = s;
-    *vstages = v;
+    while (s > 2 && two_sided_rows_layout(KP, s) + kTwoSidedExtra > kTwoSidedMax) --s;
+    return s;
 }
+
+
 
 }  // namespace
 
@@ -1318,44 +1675,43 @@ psgld_status prepare_dense(psgld_ctx *c, cudaStream_t st)
     c->ni_max = cdiv(maxI, 64);
     c->nj_max = cdiv(maxJ, 64);
     const int vs = vb ? 2 : 4;
-    int stages = 0, vstages = 0;
-    two_sided_stages(c->KP, vs, &stages, &vstages);
+    const int stages = two_sided_stages(c->KP);
     for (int pm = 0; pm < 4; ++pm)
         PSGLD_CK(c, cudaFuncSetAttribute(pick_chain(vb, pm), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)two_sided_smem(c->KP, vs, stages, vstages)));
+                                         (int)two_sided_smem(c->KP, stages)));
     const int64_t B = c->B;
-    const int64_t nA = B * B * c->mt_max * c->nj_max * 8192, nB = B * B * c->nt_max * c->ni_max * 8192;
+    const int64_t nA = B * B * c->mt_max * c->nj_max * 8192;
     const int64_t nW = B * 2 * c->mt_max * 64 * c->KP, nH = B * 2 * c->nt_max * 64 * c->KP;
+    const int64_t nE = B * c->mt_max * 2 * c->nt_max * 8192;     // one part's E tiles
     auto al = [&](void **p, size_t bytes) -> psgld_status {
         *p = dev_alloc(c, bytes, st);
         if (!*p) return fail(c, PSGLD_ERR_OOM, "device allocation failed");
-        PSGLD_CK(c, cudaMemsetAsync(*p, 0, bytes, st));   // padding stays zero
+        // padding stays zero; so do E slots no rows item writes, and the
+        // launch counters between launches
+        PSGLD_CK(c, cudaMemsetAsync(*p, 0, bytes, st));
         return PSGLD_OK;
     };
     psgld_status s = al(&c->VA, (size_t)nA * vs);
-    if (s == PSGLD_OK) s = al(&c->VB, (size_t)nB * vs);
     if (s == PSGLD_OK) s = al((void **)&c->Wsh, (size_t)nW * 2);
     if (s == PSGLD_OK) s = al((void **)&c->Hsh, (size_t)nH * 2);
+    if (s == PSGLD_OK) s = al((void **)&c->Et, (size_t)nE * 2);
+    if (s == PSGLD_OK) s = al((void **)&c->tsync, sizeof(int) * (size_t)(2 + B));
     return s;
 }
 
 psgld_status build_dense_tiles(psgld_ctx *c, cudaStream_t st)
 {
     if (c->dense_kind != 2) return PSGLD_OK;
+    // V is read by the rows items only (the columns items take E from them)
     const int64_t n = c->I * c->J;
     const unsigned grid = (unsigned)std::min<int64_t>((n + 255) / 256, 152 * 32);
-    for (int side = 0; side < 2; ++side) {
-        const int own_tiles = side == 0 ? c->mt_max : c->nt_max;
-        const int walk_tiles = side == 0 ? c->nj_max : c->ni_max;
-        void *out = side == 0 ? c->VA : c->VB;
-        if (c->v_bf16)
-            build_vtiles_kernel<__nv_bfloat16><<<grid, 256, 0, st>>>(c->Vd, c->I, c->J, c->B, side, own_tiles,
-                                                                      walk_tiles, (__nv_bfloat16 *)out);
-        else
-            build_vtiles_kernel<float><<<grid, 256, 0, st>>>(c->Vd, c->I, c->J, c->B, side, own_tiles,
-                                                              walk_tiles, (float *)out);
-        PSGLD_CK(c, cudaGetLastError());
-    }
+    if (c->v_bf16)
+        build_vtiles_kernel<__nv_bfloat16><<<grid, 256, 0, st>>>(c->Vd, c->I, c->J, c->B, 0, c->mt_max,
+                                                                  c->nj_max, (__nv_bfloat16 *)c->VA);
+    else
+        build_vtiles_kernel<float><<<grid, 256, 0, st>>>(c->Vd, c->I, c->J, c->B, 0, c->mt_max, c->nj_max,
+                                                          (float *)c->VA);
+    PSGLD_CK(c, cudaGetLastError());
     return PSGLD_OK;
 }
 
@@ -1382,15 +1738,19 @@ static void fill_two_sided(const psgld_ctx *c, int part, two_sided::Params &P)
     A.own_sh = c->Wsh; A.walk_sh = c->Hsh; A.Vt = (const unsigned char *)c->VA; A.G = c->G;
     A.n_own = I; A.n_walk = J; A.own_tiles = c->mt_max; A.walk_tiles = c->nj_max;
     A.own_sh64 = 2 * c->mt_max; A.walk_sh64 = 2 * c->nt_max;
-    Bs.own_sh = c->Hsh; Bs.walk_sh = c->Wsh; Bs.Vt = (const unsigned char *)c->VB; Bs.G = c->G + I * c->ldk;
+    Bs.own_sh = nullptr; Bs.walk_sh = c->Wsh; Bs.Vt = nullptr; Bs.G = c->G + I * c->ldk;
     Bs.n_own = J; Bs.n_walk = I; Bs.own_tiles = c->nt_max; Bs.walk_tiles = c->ni_max;
     Bs.own_sh64 = 2 * c->nt_max; Bs.walk_sh64 = 2 * c->mt_max;
+    P.Et = c->Et;
+    P.sync = c->tsync;
+    P.et_cols = 2 * c->nt_max;
     P.B = c->B;
     P.part = part;
     P.KP = c->KP;
     P.ldk = c->ldk;
-    const int vs = c->v_bf16 ? 2 : 4;
-    two_sided_stages(c->KP, vs, &P.stages, &P.vstages);
+    P.stages = two_sided_stages(c->KP);
+    P.hstages = two_sided_hstages(c->KP);
+    P.bars_off = (int)two_sided_bars_off(c->KP, P.stages);
     P.items_a = c->B * c->mt_max;
     P.items = P.items_a + c->B * c->nt_max;
     P.phi_inv = (float)(1.0 / c->phi);
@@ -1404,12 +1764,11 @@ static psgld_status launch_two_sided(psgld_ctx *c, int part, cudaStream_t st)
 {
     two_sided::Params P;
     fill_two_sided(c, part, P);
-    const int vs = c->v_bf16 ? 2 : 4;
     int sms = 0;
     PSGLD_CK(c, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
     int grid = std::min(P.items, sms);
     if (c->opt.max_sms > 0) grid = std::min(grid, c->opt.max_sms);   // leave SMs to other work
-    const size_t smem = two_sided_smem(c->KP, vs, P.stages, P.vstages);
+    const size_t smem = two_sided_smem(c->KP, P.stages);
     pick_chain(c->v_bf16 != 0, P.p_mode)<<<grid, two_sided::kThreads, smem, st>>>(P);
     PSGLD_CK(c, cudaGetLastError());
     return PSGLD_OK;
@@ -1470,17 +1829,19 @@ size_t dense_param_bytes()
     return (m + 15) & ~size_t(15);
 }
 
-int fill_dense_param(const psgld_ctx *c, int part, void *dst)
+int fill_dense_param(const psgld_ctx *c, int part, void *dst, int *first_items)
 {
     if (c->dense_kind == 2) {
         two_sided::Params P;
         fill_two_sided(c, part, P);
         std::memcpy(dst, &P, sizeof P);
+        *first_items = P.items_a;
         return P.items;
     }
     DenseParams P;
     fill_dense_params(c, part, P);
     std::memcpy(dst, &P, sizeof P);
+    *first_items = c->B * P.mtiles;
     return c->B * P.mtiles;
 }
 
@@ -1494,17 +1855,14 @@ psgld_status launch_dense_batch(psgld_ctx *c0, int key, const void *params, cons
         const int KP = (key - 4096) / 8;
         const bool vb = ((key >> 2) & 1) != 0;
         const int pm = key & 3;
-        const int vs = vb ? 2 : 4;
-        int stages = 0, vstages = 0;
-        two_sided_stages(KP, vs, &stages, &vstages);
-        const size_t smem = two_sided_smem(KP, vs, stages, vstages);
+        const size_t smem = two_sided_smem(KP, two_sided_stages(KP));
         ChainBatchFn fn = pick_chain_batch(vb, pm);
         PSGLD_CK(c0, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         int sms = 0;
         PSGLD_CK(c0, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c0->device));
         int grid = std::min(total, sms);
         if (c0->opt.batch_ctas > 0) grid = std::min(grid, (int)c0->opt.batch_ctas);
-        if (grid > 0) fn<<<grid, two_sided::kThreads, smem, st>>>(tab, stride, cta_start, n);
+        if (grid > 0) fn<<<grid, two_sided::kThreads, smem, st>>>(tab, stride, cta_start, cta_start + n + 1, n);
         PSGLD_CK(c0, cudaGetLastError());
         return PSGLD_OK;
     }

@@ -17,9 +17,11 @@
 //   Vd    : I x J fp32, row-major (ldv = J)
 //   hpart : mtiles x J x ldk fp32, the per-M-tile partial G_H rows when a
 //           block has more than one 128-row tile (single-pass kernel)
-//   two-sided kernel: VA / VB, V in 128 x 64 tiles per block, owned rows =
-//           rows of V (VA) or columns of V (VB); Wsh / Hsh, BF16 shadows of W
-//           and H^T in 64-row swizzled MMA tiles per piece (dev::shadow_store4)
+//   two-sided kernel: VA, V in 128 x 64 tiles per block (128 rows x 64
+//           columns); Wsh / Hsh, BF16 shadows of W and H^T in 64-row
+//           swizzled MMA tiles per piece (dev::shadow_store4); Et, one part's
+//           E in 128 x 64 BF16 tiles (written by the rows items, read by the
+//           columns items); tsync, the kernel's claim and block counters
 //   sparse path with gather_bf16: W16 / H16, BF16 copies of W and H^T, rows
 //           of ldk rounded up to 8, rewritten by every update
 #pragma once
@@ -86,7 +88,9 @@ struct psgld_ctx {
     int dense_fp8 = 0;               // single-pass kernel with the E4M3 GEMM1
     int KP = 0;                      // K rounded up to 64 (two-sided kernel)
     int v_bf16 = 0;                  // V tiles in BF16
-    void *VA = nullptr, *VB = nullptr;          // V tiles, both orientations
+    void *VA = nullptr;                         // V tiles (rows of V owned)
+    uint16_t *Et = nullptr;                     // E tiles of one part (BF16)
+    int *tsync = nullptr;                       // two-sided kernel counters: 2 + B ints
     uint16_t *Wsh = nullptr, *Hsh = nullptr;    // BF16 shadows of W, H^T
     uint16_t *W16 = nullptr, *H16 = nullptr;    // sparse path, gather_bf16: BF16 copies of W, H^T
     int mt_max = 0, nt_max = 0;      // 128-row tiles per row piece / column piece
@@ -225,10 +229,14 @@ psgld_status launch_dense_grad(psgld_ctx *c, int part, cudaStream_t st);
 // Dense: contexts of one batch key (> 0): single-pass ones of one K class
 // and GEMM1 precision (one CTA range each), or two-sided ones of one K
 // width, V type and power (one persistent launch over all their items).
-// Every table slot is dense_param_bytes() long.
+// Every table slot is dense_param_bytes() long.  fill_dense_param returns
+// the context's items and sets *first_items to those of the first kind
+// (two-sided: the rows items; single-pass: all).  A two-sided group's
+// cta_start holds two prefix arrays of n + 1 entries: rows items, then
+// columns items.
 int dense_batch_key(const psgld_ctx *c);
 size_t dense_param_bytes();
-int fill_dense_param(const psgld_ctx *c, int part, void *dst);
+int fill_dense_param(const psgld_ctx *c, int part, void *dst, int *first_items);
 psgld_status launch_dense_batch(psgld_ctx *c0, int key, const void *params, const int *cta_start, int n,
                                 int total, cudaStream_t st);
 // Update of part `part` at iteration *t_dev + t_add (t_dev: the context's

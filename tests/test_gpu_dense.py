@@ -30,8 +30,9 @@ FP32 precision.  What is checked:
 
 Every case runs on both kernels: the single-pass one (mu once per entry, G_H
 summed over a block's 128-row tiles by the update) and the two-sided one
-(mu once for the W rows and once for the H columns), the latter also with V
-kept in BF16, where the bound adds the rounding of v.
+(mu and E once per entry in the rows items, which store E; the columns
+items take G_H = E^T W from it), the latter also with V kept in BF16, where
+the bound adds the rounding of v.
 """
 import numpy as np
 import pytest
@@ -240,11 +241,16 @@ def test_dense_size_proportional_parts_drift_within_bound(kernel):
     assert len(seen) > 1
 
 
-def test_two_sided_kernel_on_fewer_sms_gives_the_same_chain():
+@pytest.mark.parametrize("name,sms", [("poisson_K200_B3", 7), ("poisson_K200_B3", 1),
+                                      ("gaussnmf_K256_three_tiles", 2), ("gaussnmf_K256_three_tiles", 1),
+                                      ("gauss_K50_two_mtiles_three_ntiles", 1)])
+def test_two_sided_kernel_on_fewer_sms_gives_the_same_chain(name, sms):
     """max_sms only shrinks the persistent grid: every item still runs once,
-    so the chain is the same bit for bit."""
-    a, _ = _make("poisson_K200_B3", kernel="two_sided")
-    b, _ = _make("poisson_K200_B3", kernel="two_sided", max_sms=7)
+    so the chain is the same bit for bit.  On one or two CTAs each CTA runs
+    several rows items before its first columns item, whose stages then
+    take over the rows items' shared memory."""
+    a, _ = _make(name, kernel="two_sided")
+    b, _ = _make(name, kernel="two_sided", max_sms=sms)
     a.gpu.sweep(2)
     b.gpu.sweep(2)
     Wa, Ha = a.gpu_factors()

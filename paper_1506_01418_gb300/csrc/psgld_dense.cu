@@ -717,6 +717,14 @@ __device__ __forceinline__ void bulk_g2s_if(uint32_t, void *dst, const void *src
                  :: "r"(saddr(dst)), "l"(src), "r"(bytes), "r"(saddr(b)) : "memory");
 }
 
+// L2 prefetch of `bytes` (a multiple of 16) from a 16-byte aligned address
+__device__ __forceinline__ void prefetch_l2_if(const void *src, uint32_t bytes)
+{
+    asm volatile("{\n\t.reg .pred e;\n\telect.sync _|e, 0xffffffff;\n\t"
+                 "@e cp.async.bulk.prefetch.L2.global [%0], %1;\n\t}"
+                 :: "l"(src), "r"(bytes) : "memory");
+}
+
 __device__ __forceinline__ void mma_ta_if(uint32_t, uint32_t d, uint32_t a, uint64_t bdesc, uint32_t id,
                                           uint32_t acc)
 {
@@ -1049,6 +1057,11 @@ __device__ __forceinline__ void chain_body(const Params &P0, const Src src, cons
                         }
                     }
                     ++iw;
+                    // with each walked tile, an L2 prefetch of its V tile: the
+                    // epilogue's register loads, two tiles ahead, then hit L2
+                    const unsigned char *vbase =
+                        Sd.Vt + ((((int64_t)x.own_piece * P.B + x.walk_piece) * Sd.own_tiles + x.ot) *
+                                 Sd.walk_tiles) * (int64_t)v_bytes;
                     for (int j = 0; j < x.nj; ++j) {
                         const uint32_t st = rb.slot;
                         if (!wait32(S, &S->empty[st], rb.phase ^ 1)) goto done0;
@@ -1056,6 +1069,7 @@ __device__ __forceinline__ void chain_body(const Params &P0, const Src src, cons
                         bulk_g2s_if(ld, sB + (size_t)st * b_bytes,
                                     Sd.walk_sh + ((int64_t)x.walk_piece * Sd.walk_sh64 + j) * kBN * KP,
                                     b_bytes, &S->full[st]);
+                        prefetch_l2_if(vbase + (int64_t)j * v_bytes, v_bytes);
                         rb.next(NS);
                     }
                 } else {
@@ -1089,9 +1103,23 @@ __device__ __forceinline__ void chain_body(const Params &P0, const Src src, cons
                     if (!wait_count(S, P.sync + 2 + x.block, target)) goto done0;
                     const uint16_t *e0 =
                         P.Et + (((int64_t)x.block * P.side[0].own_tiles) * P.et_cols + 2 * x.ot) * (kEBytes / 2);
+                    // the E halves of the first stages into L2 now, later ones a
+                    // ring's length ahead (they come from HBM)
+                    for (int s = 0; s < NH && s < x.nj; ++s) {
+                        const uint16_t *es = e0 + (int64_t)(s >> 1) * P.et_cols * (kEBytes / 2) + (s & 1) * (kEBytes / 4);
+                        prefetch_l2_if(es, kEBytes / 2);
+                        prefetch_l2_if(es + kEBytes / 2, kEBytes / 2);
+                    }
                     for (int s = 0; s < x.nj; ++s) {
                         const uint32_t sh = rh.slot;
                         unsigned char *stage = sm + (size_t)sh * h_bytes;
+                        if (s + NH < x.nj) {
+                            const int sp = s + NH;
+                            const uint16_t *ep = e0 + (int64_t)(sp >> 1) * P.et_cols * (kEBytes / 2) +
+                                                 (sp & 1) * (kEBytes / 4);
+                            prefetch_l2_if(ep, kEBytes / 2);
+                            prefetch_l2_if(ep + kEBytes / 2, kEBytes / 2);
+                        }
                         if (!wait32(S, &S->hempty[sh], rh.phase ^ 1)) goto done0;
                         expect_tx_if(ld, &S->hfull[sh], h_bytes);
                         bulk_g2s_if(ld, stage, Sd.walk_sh + ((int64_t)x.walk_piece * Sd.walk_sh64 + s) * kBN * KP,

@@ -150,6 +150,13 @@ typedef struct {
                                * PSGLD_ERR_TIMEOUT naming the kernel and the wait.
                                * The part-step's result is then undefined; the
                                * context stays usable (set the factors again). */
+    int32_t wide_col_blocks;  /* two-sided tensor-core kernel: the first this many
+                               * blocks of a part have columns items of 256 H^T
+                               * rows (two accumulators sharing each W tile), the
+                               * rest 128-row items, which even out the end of the
+                               * launch; -1 (the default): half the blocks.  Every
+                               * G row is the same sum either way, so the chains do
+                               * not depend on it (a knob for the autotuner). */
 } psgld_options;
 
 /* Device memory.  By default the library allocates with cudaMalloc and frees

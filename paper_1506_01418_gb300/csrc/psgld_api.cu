@@ -276,6 +276,7 @@ void psgld_default_options(psgld_options *o)
     o->freeze_H = 0;
     o->burn_in_sweeps = 0;
     o->use_graphs = 1;
+    o->wide_col_blocks = -1;
 }
 
 psgld_status psgld_create(int64_t I, int64_t J, int32_t K, int32_t B, double tweedie_p, double phi,
@@ -400,6 +401,7 @@ psgld_status psgld_set_options(psgld_ctx *c, const psgld_options *o)
     if (o->batch_ctas < 0 || o->batch_update_blocks < 0)
         return fail(c, PSGLD_ERR_ARG, "batch_ctas and batch_update_blocks must be >= 0");
     if (o->debug_wait_polls < 0) return fail(c, PSGLD_ERR_ARG, "debug_wait_polls must be >= 0");
+    if (o->wide_col_blocks < -1) return fail(c, PSGLD_ERR_ARG, "wide_col_blocks must be >= -1");
     c->opt = *o;
     destroy_graphs(c);
     destroy_events(c);
@@ -1098,7 +1100,7 @@ int64_t psgld_estimate_device_bytes(int64_t I, int64_t J, int32_t K, int32_t B, 
     const int64_t mt = cdiv(maxI, 128), nt = cdiv(maxJ, 128), nj = cdiv(maxJ, 64);
     bytes += (int64_t)B * B * mt * nj * 8192 * vs;                 // V tiles
     bytes += (int64_t)B * 2 * (mt + nt) * 64 * KP * 2;              // BF16 factor shadows
-    bytes += (int64_t)B * mt * 2 * nt * 8192 * 2 + 4 * (2 + B);     // one part's E tiles, counters
+    bytes += (int64_t)B * mt * 4 * cdiv(maxJ, 256) * 8192 * 2 + 4 * (2 + B);   // one part's E, counters
     return bytes;
 }
 

@@ -570,9 +570,10 @@ dense_grad_batch_kernel(const unsigned char *__restrict__ tab, size_t stride, co
 // items.  A rows item owns 128 rows of W of one block and walks all the
 // block's columns in 64-column tiles: mu = W H^T, E, and G_W += E H in TMEM;
 // each E tile (BF16, the image the epilogue built in shared memory) also
-// goes to HBM, one bulk store.  A columns item owns 128 rows of H^T (columns
-// of V); once every rows item of its block has stored its E, it walks the
-// block's rows: G_H += E^T W, one contraction.  mu and E are formed once per entry (the three
+// goes to HBM, one bulk store.  A columns item owns 256 rows of H^T (columns
+// of V) in two 128-row accumulators; once every rows item of its block has
+// stored its E, it walks the block's rows: G_H += E^T W, one contraction,
+// each W tile serving both accumulators.  mu and E are formed once per entry (the three
 // contractions the gradient needs), and every G row is written once,
 // complete, by one CTA: no partial sums, no atomics on data.  E is formed
 // without its 1 / phi factor, which multiplies G as G is written.
@@ -620,16 +621,17 @@ dense_grad_batch_kernel(const unsigned char *__restrict__ tab, size_t stride, co
 //              from its E buffer), and after the item the count its block's
 //              columns items wait for.  The tensor core queues only a few
 //              MMAs, so this work stays off the MMA warp.
-// TMEM: mu buffers at columns 0 and 64, G at 128 .. 128 + KP, and the owned
-// tile of a rows item (copied from shared memory once per item with
-// tcgen05.cp, so GEMM1 reads A from TMEM and shared memory serves only B) in
-// the last KP / 2 columns.
+// TMEM, rows item: mu buffers at columns 0 and 64, G at 128 .. 128 + KP, and
+// the owned tile (copied from shared memory once per item with tcgen05.cp,
+// so GEMM1 reads A from TMEM and shared memory serves only B) in the last
+// KP / 2 columns; columns item: its two accumulators at columns 0 and 256.
 // Padding rows and columns of every tile are zero, so mu and E are zero
 // there and need no masks.
 namespace two_sided {
 
 constexpr int kThreads = 352;     // warp 0 producer, warp 1 MMA, warps 2..9 epilogue, warp 10 E stores
-constexpr int kOwn = 128;          // owned rows per item (TMEM lanes)
+constexpr int kOwn = 128;          // owned rows per rows item (TMEM lanes)
+constexpr int kOwnH = 256;         // owned rows per columns item (two accumulators)
 constexpr int kBN = 64;            // walked rows per tile
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kGCol = 128;
@@ -657,7 +659,9 @@ struct Params {
                                 // holds the 128 x 64 BF16 image of W tile t x H^T tile j of block b
     int *sync;                  // [0] items claimed, [1] CTAs finished, [2 + b] rows items of
                                 // block b whose E is in HBM; all zero between launches
-    int et_cols;                // E slots per W tile (2 x the 128-row H^T tiles per piece)
+    int et_cols;                // E slots per W tile (4 x the 256-row columns items per piece)
+    int hwide, ht1, ht2;        // blocks 0 .. hwide - 1: 256-row columns items (ht2 per piece), the
+                                // rest 128-row ones (ht1 per piece)
     int B, part, KP, ldk, stages, hstages, items_a, items;
     int bars_off;               // shared-memory offset of the barriers (past both layouts)
     float phi_inv, p, mu_min;
@@ -872,16 +876,33 @@ struct Ring {
 
 struct Item {
     int side, block, own_piece, walk_piece, ot, own_rows_in_tile, nj;
+    int rows_per, row0;         // owned rows of the item (128 or 256) and its first row in the piece
     int64_t own_start;
 };
 
-// Item k of one side of one context: block b = k / own_tiles pairs row
-// piece b with column piece (b + part) mod B; tile ot of the owned piece.
+// Item k of one side of one context: block b pairs row piece b with column
+// piece (b + part) mod B; tile ot of the owned piece.  Rows items: 128 rows,
+// own_tiles per block.  Columns items: 256 rows (ht2 per block) in blocks
+// 0 .. hwide - 1, then 128 rows (ht1 per block).
 __device__ __forceinline__ bool decode(const Params &P, int side, int k, Item &x)
 {
     const int B = P.B;
     const Side &Sd = P.side[side];
-    const int b = k / Sd.own_tiles, ot = k % Sd.own_tiles;
+    int b, ot, rows_per = kOwn;
+    if (side == 0) {
+        b = k / Sd.own_tiles;
+        ot = k % Sd.own_tiles;
+    } else if (k < P.hwide * P.ht2) {
+        b = k / P.ht2;
+        ot = k % P.ht2;
+        rows_per = kOwnH;
+    } else {
+        k -= P.hwide * P.ht2;
+        b = P.hwide + k / P.ht1;
+        ot = k % P.ht1;
+    }
+    x.rows_per = rows_per;
+    x.row0 = ot * rows_per;
     const int cpiece = (b + P.part) % B;
     x.side = side;
     x.block = b;
@@ -892,8 +913,8 @@ __device__ __forceinline__ bool decode(const Params &P, int side, int k, Item &x
     const int64_t own_rows = ((int64_t)(x.own_piece + 1) * Sd.n_own) / B - x.own_start;
     const int64_t walk_rows = ((int64_t)(x.walk_piece + 1) * Sd.n_walk) / B -
                               ((int64_t)x.walk_piece * Sd.n_walk) / B;
-    const int64_t left = own_rows - (int64_t)ot * kOwn;
-    x.own_rows_in_tile = (int)(left < kOwn ? left : kOwn);
+    const int64_t left = own_rows - (int64_t)x.row0;
+    x.own_rows_in_tile = (int)(left < rows_per ? left : rows_per);
     x.nj = (int)((walk_rows + kBN - 1) / kBN);
     return left > 0;
 }
@@ -984,7 +1005,7 @@ __device__ __forceinline__ void chain_body(const Params &P0, const Src src, cons
     Bars *S = reinterpret_cast<Bars *>(sm + P0.bars_off);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int NS = P0.stages, NH = P0.hstages;
-    const uint32_t h_bytes = b_bytes + kEBytes;                 // columns-item stage: W tile, E halves
+    const uint32_t h_bytes = b_bytes + 2 * kEBytes;             // columns-item stage: W tile, 4 E halves
     unsigned char *sStgH = sm + (size_t)NH * h_bytes;           // columns items' G staging
 
     if (threadIdx.x == 0) {
@@ -1075,7 +1096,7 @@ __device__ __forceinline__ void chain_body(const Params &P0, const Src src, cons
                 } else {
                     // columns item: once the block's rows items have stored E,
                     // per 64 W rows the W tile and the E halves of the owned
-                    // columns (E tiles 2 ot and 2 ot + 1 of each W tile)
+                    // columns (E tiles 4 ot .. 4 ot + 3 of each W tile)
                     if (!hphase) {
                         // the first one: once every earlier (rows) item's G is
                         // complete, their MMAs, copies and epilogue reads of
@@ -1102,32 +1123,31 @@ __device__ __forceinline__ void chain_body(const Params &P0, const Src src, cons
                     const int target = (int)((wrows + kOwn - 1) / kOwn);
                     if (!wait_count(S, P.sync + 2 + x.block, target)) goto done0;
                     const uint16_t *e0 =
-                        P.Et + (((int64_t)x.block * P.side[0].own_tiles) * P.et_cols + 2 * x.ot) * (kEBytes / 2);
+                        P.Et + (((int64_t)x.block * P.side[0].own_tiles) * P.et_cols + x.row0 / kBN) * (kEBytes / 2);
+                    const int nq = x.rows_per / kBN;          // E tiles across the owned rows (4 or 2)
+                    const uint32_t stage_tx = b_bytes + (uint32_t)nq * (kEBytes / 2);
+                    // stage s: rows 64 (s % 2) .. + 63 of W tile s / 2, in each
+                    // of the nq E tiles (8 KB each, consecutive slots)
+                    auto e_half = [&](int st_, int q) {
+                        return e0 + (int64_t)(st_ >> 1) * P.et_cols * (kEBytes / 2) + q * (kEBytes / 2) +
+                               (st_ & 1) * (kEBytes / 4);
+                    };
                     // the E halves of the first stages into L2 now, later ones a
                     // ring's length ahead (they come from HBM)
-                    for (int s = 0; s < NH && s < x.nj; ++s) {
-                        const uint16_t *es = e0 + (int64_t)(s >> 1) * P.et_cols * (kEBytes / 2) + (s & 1) * (kEBytes / 4);
-                        prefetch_l2_if(es, kEBytes / 2);
-                        prefetch_l2_if(es + kEBytes / 2, kEBytes / 2);
-                    }
+                    for (int s = 0; s < NH && s < x.nj; ++s)
+                        for (int q = 0; q < nq; ++q) prefetch_l2_if(e_half(s, q), kEBytes / 2);
                     for (int s = 0; s < x.nj; ++s) {
                         const uint32_t sh = rh.slot;
                         unsigned char *stage = sm + (size_t)sh * h_bytes;
-                        if (s + NH < x.nj) {
-                            const int sp = s + NH;
-                            const uint16_t *ep = e0 + (int64_t)(sp >> 1) * P.et_cols * (kEBytes / 2) +
-                                                 (sp & 1) * (kEBytes / 4);
-                            prefetch_l2_if(ep, kEBytes / 2);
-                            prefetch_l2_if(ep + kEBytes / 2, kEBytes / 2);
-                        }
+                        if (s + NH < x.nj)
+                            for (int q = 0; q < nq; ++q) prefetch_l2_if(e_half(s + NH, q), kEBytes / 2);
                         if (!wait32(S, &S->hempty[sh], rh.phase ^ 1)) goto done0;
-                        expect_tx_if(ld, &S->hfull[sh], h_bytes);
+                        expect_tx_if(ld, &S->hfull[sh], stage_tx);
                         bulk_g2s_if(ld, stage, Sd.walk_sh + ((int64_t)x.walk_piece * Sd.walk_sh64 + s) * kBN * KP,
                                     b_bytes, &S->hfull[sh]);
-                        const uint16_t *es = e0 + (int64_t)(s >> 1) * P.et_cols * (kEBytes / 2) +
-                                             (s & 1) * (kEBytes / 4);
-                        bulk_g2s_if(ld, stage + b_bytes, es, kEBytes / 2, &S->hfull[sh]);
-                        bulk_g2s_if(ld, stage + b_bytes + kEBytes / 2, es + kEBytes / 2, kEBytes / 2, &S->hfull[sh]);
+                        for (int q = 0; q < nq; ++q)
+                            bulk_g2s_if(ld, stage + b_bytes + q * (kEBytes / 2), e_half(s, q), kEBytes / 2,
+                                        &S->hfull[sh]);
                         rh.next(NH);
                     }
                 }
@@ -1219,19 +1239,32 @@ __device__ __forceinline__ void chain_body(const Params &P0, const Src src, cons
                     // at a time.  A = the two E halves read MN-major (64 owned
                     // rows per 128-byte atom column, the second half 8 KB on,
                     // 8 W rows per 1024 B); B = the W tile read MN-major as in
-                    // GEMM2.  A K step of 16 W rows is 2048 B in both.
+                    // GEMM2.  A K step of 16 W rows is 2048 B in both.  Two
+                    // accumulators (owned rows 0..127 at TMEM column 0, rows
+                    // 128..255 at column 256) share each W tile.
                     for (int s = 0; s < x.nj; ++s) {
                         const uint32_t sh = rh.slot;
                         const uint32_t stage = saddr(sm) + sh * h_bytes;
                         if (!wait32(S, &S->hfull[sh], rh.phase)) goto done1;
                         if (s == 0 && !wait32(S, &S->g_empty, (ic & 1) ^ 1)) goto done1;
                         fence_after();
-                        const uint64_t dEt = sdesc_sw128(stage + b_bytes, kEBytes / 2, 1024);
+                        const uint64_t dE0 = sdesc_sw128(stage + b_bytes, kEBytes / 2, 1024);
+                        const uint64_t dE1 = sdesc_sw128(stage + b_bytes + kEBytes, kEBytes / 2, 1024);
                         const uint64_t dW = sdesc_sw128(stage, kBN * 128, 1024);
+                        if (x.rows_per == kOwnH) {
 #pragma unroll
-                        for (int ks = 0; ks < kBN / 16; ++ks)
-                            mma_ss_if(ld, tmem + kGCol, dEt + (uint64_t)(ks * 128), dW + (uint64_t)(ks * 128), id3,
-                                      (s > 0 || ks > 0));
+                            for (int ks = 0; ks < kBN / 16; ++ks) {
+                                mma_ss_if(ld, tmem, dE0 + (uint64_t)(ks * 128), dW + (uint64_t)(ks * 128), id3,
+                                          (s > 0 || ks > 0));
+                                mma_ss_if(ld, tmem + 256, dE1 + (uint64_t)(ks * 128), dW + (uint64_t)(ks * 128),
+                                          id3, (s > 0 || ks > 0));
+                            }
+                        } else {
+#pragma unroll
+                            for (int ks = 0; ks < kBN / 16; ++ks)
+                                mma_ss_if(ld, tmem, dE0 + (uint64_t)(ks * 128), dW + (uint64_t)(ks * 128), id3,
+                                          (s > 0 || ks > 0));
+                        }
                         commit_if(ld, &S->hempty[sh]);
                         rh.next(NH);
                     }
@@ -1405,11 +1438,17 @@ __device__ __forceinline__ void chain_body(const Params &P0, const Src src, cons
                 fence_after();
                 const float phi_inv = P.phi_inv;
                 const int w8 = warp - 2;
-                float *gbase = Sd.G + (x.own_start + (int64_t)x.ot * kOwn) * P.ldk;
+                // rows item: one accumulator at kGCol; columns item: two, of
+                // 128 rows each, at columns 0 and 256
+                const int nacc = x.rows_per / kOwn;
+                for (int a = 0; a < nacc; ++a)
                 for (int cp = 0; cp < KP; cp += 64, ++np) {
+                    const uint32_t gcol = side == 0 ? kGCol : 256u * (uint32_t)a;
+                    float *gbase = Sd.G + (x.own_start + (int64_t)x.row0 + 128 * a) * P.ldk;
+                    const int rows = x.own_rows_in_tile - 128 * a;
                     float g[32];
-                    tmem_ld32(tmem + lane_base + kGCol + (uint32_t)(cp + c), g);
-                    if (cp + 64 >= KP) {
+                    tmem_ld32(tmem + lane_base + gcol + (uint32_t)(cp + c), g);
+                    if (a == nacc - 1 && cp + 64 >= KP) {
                         // this warp's last TMEM read of the item: G may be reused
                         fence_before();
                         __syncwarp();
@@ -1429,7 +1468,7 @@ __device__ __forceinline__ void chain_body(const Params &P0, const Src src, cons
                         const float4 val =
                             *reinterpret_cast<const float4 *>(stg + r * 256 + ((ch ^ (r & 7)) << 4));
                         const int col = cp + 4 * ch;
-                        if (r < x.own_rows_in_tile && col < P.ldk)
+                        if (r < rows && col < P.ldk)
                             *reinterpret_cast<float4 *>(gbase + (int64_t)r * P.ldk + col) =
                                 make_float4(val.x * phi_inv, val.y * phi_inv, val.z * phi_inv, val.w * phi_inv);
                     }
@@ -1639,14 +1678,14 @@ constexpr size_t kTwoSidedMax = 232448;
 // G staging buffer, at most kMaxHStages.
 int two_sided_hstages(int KP)
 {
-    const size_t h = (size_t)two_sided::kBN * KP * 2 + two_sided::kEBytes;
+    const size_t h = (size_t)two_sided::kBN * KP * 2 + 2 * (size_t)two_sided::kEBytes;
     const size_t room = kTwoSidedMax - kTwoSidedExtra - two_sided::kStgBytes;
     return (int)std::min<size_t>(room / h, two_sided::kMaxHStages);
 }
 
 size_t two_sided_bars_off(int KP, int stages)
 {
-    const size_t h = (size_t)two_sided::kBN * KP * 2 + two_sided::kEBytes;
+    const size_t h = (size_t)two_sided::kBN * KP * 2 + 2 * (size_t)two_sided::kEBytes;
     return std::max(two_sided_rows_layout(KP, stages), (size_t)two_sided_hstages(KP) * h + two_sided::kStgBytes);
 }
 
@@ -1700,6 +1739,7 @@ psgld_status prepare_dense(psgld_ctx *c, cudaStream_t st)
     const int64_t maxI = (c->I + c->B - 1) / c->B, maxJ = (c->J + c->B - 1) / c->B;
     c->mt_max = cdiv(maxI, 128);
     c->nt_max = cdiv(maxJ, 128);
+    c->nt2_max = cdiv(maxJ, 256);
     c->ni_max = cdiv(maxI, 64);
     c->nj_max = cdiv(maxJ, 64);
     const int vs = vb ? 2 : 4;
@@ -1710,7 +1750,7 @@ psgld_status prepare_dense(psgld_ctx *c, cudaStream_t st)
     const int64_t B = c->B;
     const int64_t nA = B * B * c->mt_max * c->nj_max * 8192;
     const int64_t nW = B * 2 * c->mt_max * 64 * c->KP, nH = B * 2 * c->nt_max * 64 * c->KP;
-    const int64_t nE = B * c->mt_max * 2 * c->nt_max * 8192;     // one part's E tiles
+    const int64_t nE = B * c->mt_max * 4 * c->nt2_max * 8192;    // one part's E tiles
     auto al = [&](void **p, size_t bytes) -> psgld_status {
         *p = dev_alloc(c, bytes, st);
         if (!*p) return fail(c, PSGLD_ERR_OOM, "device allocation failed");
@@ -1758,6 +1798,16 @@ psgld_status build_dense_shadows(psgld_ctx *c, cudaStream_t st)
     return PSGLD_OK;
 }
 
+// Blocks whose columns items cover 256 rows (two accumulators sharing each W
+// tile: a third fewer bytes per MAC); the last blocks' columns items, which
+// end the launch, keep 128 rows so that its CTAs finish together.  The
+// option overrides the rule; the results do not depend on it.
+static int two_sided_hwide(const psgld_ctx *c)
+{
+    if (c->opt.wide_col_blocks >= 0) return std::min(c->opt.wide_col_blocks, c->B);
+    return c->B / 2;
+}
+
 static void fill_two_sided(const psgld_ctx *c, int part, two_sided::Params &P)
 {
     P = two_sided::Params{};
@@ -1767,11 +1817,14 @@ static void fill_two_sided(const psgld_ctx *c, int part, two_sided::Params &P)
     A.n_own = I; A.n_walk = J; A.own_tiles = c->mt_max; A.walk_tiles = c->nj_max;
     A.own_sh64 = 2 * c->mt_max; A.walk_sh64 = 2 * c->nt_max;
     Bs.own_sh = nullptr; Bs.walk_sh = c->Wsh; Bs.Vt = nullptr; Bs.G = c->G + I * c->ldk;
-    Bs.n_own = J; Bs.n_walk = I; Bs.own_tiles = c->nt_max; Bs.walk_tiles = c->ni_max;
+    Bs.n_own = J; Bs.n_walk = I; Bs.own_tiles = c->nt2_max; Bs.walk_tiles = c->ni_max;
     Bs.own_sh64 = 2 * c->nt_max; Bs.walk_sh64 = 2 * c->mt_max;
     P.Et = c->Et;
     P.sync = c->tsync;
-    P.et_cols = 2 * c->nt_max;
+    P.et_cols = 4 * c->nt2_max;
+    P.ht1 = c->nt_max;
+    P.ht2 = c->nt2_max;
+    P.hwide = two_sided_hwide(c);
     P.B = c->B;
     P.part = part;
     P.KP = c->KP;
@@ -1780,7 +1833,7 @@ static void fill_two_sided(const psgld_ctx *c, int part, two_sided::Params &P)
     P.hstages = two_sided_hstages(c->KP);
     P.bars_off = (int)two_sided_bars_off(c->KP, P.stages);
     P.items_a = c->B * c->mt_max;
-    P.items = P.items_a + c->B * c->nt_max;
+    P.items = P.items_a + P.hwide * c->nt2_max + (c->B - P.hwide) * c->nt_max;
     P.phi_inv = (float)(1.0 / c->phi);
     P.p = (float)c->p;
     P.mu_min = (float)c->opt.mu_min;

@@ -94,6 +94,7 @@ struct psgld_ctx {
     uint16_t *Wsh = nullptr, *Hsh = nullptr;    // BF16 shadows of W, H^T
     uint16_t *W16 = nullptr, *H16 = nullptr;    // sparse path, gather_bf16: BF16 copies of W, H^T
     int mt_max = 0, nt_max = 0;      // 128-row tiles per row piece / column piece
+    int nt2_max = 0;                 // 256-row column tiles per column piece (columns items)
     int ni_max = 0, nj_max = 0;      // 64-row tiles per row piece / column piece
 
     // factors

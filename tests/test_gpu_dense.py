@@ -258,6 +258,21 @@ def test_two_sided_kernel_on_fewer_sms_gives_the_same_chain(name, sms):
     assert np.array_equal(Wa, Wb) and np.array_equal(Ha, Hb)
 
 
+@pytest.mark.parametrize("name", ["poisson_K200_B3", "gaussnmf_K256_three_tiles", "poisson_uneven_mtiles_K32"])
+def test_two_sided_columns_item_width_does_not_change_the_chain(name):
+    """wide_col_blocks only regroups the columns items (256 rows in two
+    accumulators or 128 rows in one); every G_H row is the same sequence of
+    MMAs, so the chain is the same bit for bit."""
+    B = DENSE[name][3]
+    out = []
+    for w in (0, B, -1):
+        pr, _ = _make(name, kernel="two_sided", wide_col_blocks=w)
+        pr.gpu.sweep(2)
+        out.append(pr.gpu_factors())
+    for Wx, Hx in out[1:]:
+        assert np.array_equal(Wx, out[0][0]) and np.array_equal(Hx, out[0][1])
+
+
 @pytest.mark.parametrize("name", ["poisson_ragged_K8", "gauss_K50_two_mtiles_three_ntiles",
                                   "cp_K100", "gamma_K13", "poisson_K200_B3"])
 def test_dense_log_lik_and_rmse_match_oracle(name):

@@ -1475,6 +1475,10 @@ __device__ __forceinline__ void chain_body(const Params &P0, const Src src, cons
                     __syncwarp();
                     if (lane == 0) bar_arrive(&S->stg_empty);
                 }
+                // a rows item staged in the E buffers, which this warp fills
+                // again with the next item's first tile: first every warp
+                // must be done reading the last pass
+                if (side == 0 && !wait32(S, &S->stg_empty, (np & 1) ^ 1)) goto done2;
             }
             // the item is done with shared memory and TMEM (the producer's
             // columns stages may take over once every earlier item is)

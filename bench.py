@@ -66,6 +66,13 @@ WORKLOADS = {
         I=4096, J=4096, nnz=4096 * 4096, K=256, B=2, p=1.0, phi=1.0, prior="exponential",
         lam=1.0, K_true=16, eps=2e-5, init_scale=0.25, job_sweeps=200, dense=True,
         device_gen=True, dense_path=2, dense_v_bf16=1),
+    # the standing chain's blocks (2048 x 2048, K = 256) in several waves of
+    # items (12 blocks: 192 rows items, 144 columns items) at a size that an
+    # ncu capture of the chain kernel handles (about 4 GB on the device)
+    "dense_poisson_24576x24576_K256_B12_bf16": dict(
+        I=24576, J=24576, nnz=24576 * 24576, K=256, B=12, p=1.0, phi=1.0, prior="exponential",
+        lam=1.0, K_true=16, eps=2e-5, init_scale=0.25, job_sweeps=200, dense=True,
+        device_gen=True, dense_path=2, dense_v_bf16=1),
     # the standing dense chain: tensor-core block chain, BF16 operands and V
     "dense_poisson_32768x32768_K256_B16_bf16": dict(
         I=32768, J=32768, nnz=32768 * 32768, K=256, B=16, p=1.0, phi=1.0, prior="exponential",

@@ -157,6 +157,16 @@ typedef struct {
                                * launch; -1 (the default): half the blocks.  Every
                                * G row is the same sum either way, so the chains do
                                * not depend on it (a knob for the autotuner). */
+    int32_t dense_share_e;    /* two-sided tensor-core kernel, read when the data are
+                               * set: 1: the columns items take E from the rows items
+                               * of their block (mu and E formed once per entry, E
+                               * through HBM, columns items wait for their block's
+                               * rows items); 0: every item forms its own mu and E
+                               * (V kept in both orientations); -1 (the default): 1
+                               * for row pieces of at least 512 rows whose part fills
+                               * more than one wave of CTAs, else 0.  The chains
+                               * differ by rounding only (mu = W H^T from either
+                               * orientation's MMAs). */
 } psgld_options;
 
 /* Device memory.  By default the library allocates with cudaMalloc and frees

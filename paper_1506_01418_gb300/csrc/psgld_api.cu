@@ -277,6 +277,7 @@ void psgld_default_options(psgld_options *o)
     o->burn_in_sweeps = 0;
     o->use_graphs = 1;
     o->wide_col_blocks = -1;
+    o->dense_share_e = -1;
 }
 
 psgld_status psgld_create(int64_t I, int64_t J, int32_t K, int32_t B, double tweedie_p, double phi,
@@ -402,6 +403,7 @@ psgld_status psgld_set_options(psgld_ctx *c, const psgld_options *o)
         return fail(c, PSGLD_ERR_ARG, "batch_ctas and batch_update_blocks must be >= 0");
     if (o->debug_wait_polls < 0) return fail(c, PSGLD_ERR_ARG, "debug_wait_polls must be >= 0");
     if (o->wide_col_blocks < -1) return fail(c, PSGLD_ERR_ARG, "wide_col_blocks must be >= -1");
+    if (o->dense_share_e < -1 || o->dense_share_e > 1) return fail(c, PSGLD_ERR_ARG, "dense_share_e must be -1, 0 or 1");
     c->opt = *o;
     destroy_graphs(c);
     destroy_events(c);
@@ -1097,10 +1099,15 @@ int64_t psgld_estimate_device_bytes(int64_t I, int64_t J, int32_t K, int32_t B, 
         return bytes;
     }
     const int64_t KP = 64 * cdiv(K, 64), vs = dense_v_bf16 ? 2 : 4;
-    const int64_t mt = cdiv(maxI, 128), nt = cdiv(maxJ, 128), nj = cdiv(maxJ, 64);
+    const int64_t mt = cdiv(maxI, 128), nt = cdiv(maxJ, 128), ni = cdiv(maxI, 64), nj = cdiv(maxJ, 64);
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const bool share = two_sided_share(-1, maxI, B, (int)mt, (int)nt, sms) != 0;
     bytes += (int64_t)B * B * mt * nj * 8192 * vs;                 // V tiles
+    if (!share) bytes += (int64_t)B * B * nt * ni * 8192 * vs;     // ... other orientation
     bytes += (int64_t)B * 2 * (mt + nt) * 64 * KP * 2;              // BF16 factor shadows
-    bytes += (int64_t)B * mt * 4 * cdiv(maxJ, 256) * 8192 * 2 + 4 * (2 + B);   // one part's E, counters
+    if (share) bytes += (int64_t)B * mt * 4 * cdiv(maxJ, 256) * 8192 * 2;   // one part's E
+    bytes += 4 * (2 + B);                                            // launch counters
     return bytes;
 }
 

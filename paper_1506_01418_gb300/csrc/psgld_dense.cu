@@ -662,6 +662,8 @@ struct Params {
     int et_cols;                // E slots per W tile (4 x the 256-row columns items per piece)
     int hwide, ht1, ht2;        // blocks 0 .. hwide - 1: 256-row columns items (ht2 per piece), the
                                 // rest 128-row ones (ht1 per piece)
+    int share;                  // 1: columns items take E from the rows items; 0: they form
+                                // their own mu and E (rows items of the other orientation)
     int B, part, KP, ldk, stages, hstages, items_a, items;
     int bars_off;               // shared-memory offset of the barriers (past both layouts)
     float phi_inv, p, mu_min;
@@ -877,6 +879,7 @@ struct Ring {
 struct Item {
     int side, block, own_piece, walk_piece, ot, own_rows_in_tile, nj;
     int rows_per, row0;         // owned rows of the item (128 or 256) and its first row in the piece
+    bool rl;                    // a rows item, or a columns item formed like one (share = 0)
     int64_t own_start;
 };
 
@@ -889,7 +892,8 @@ __device__ __forceinline__ bool decode(const Params &P, int side, int k, Item &x
     const int B = P.B;
     const Side &Sd = P.side[side];
     int b, ot, rows_per = kOwn;
-    if (side == 0) {
+    x.rl = side == 0 || !P.share;
+    if (x.rl) {
         b = k / Sd.own_tiles;
         ot = k % Sd.own_tiles;
     } else if (k < P.hwide * P.ht2) {
@@ -936,9 +940,10 @@ __device__ __forceinline__ float tweedie_pm(float p, float mu_min, float v, floa
 
 // Where the items' parameters come from: one context (the kernel parameter)
 // or, batched, a table of contexts in global memory (slots `stride` bytes
-// apart).  Batched, the rows items of every context come first, context i
-// owning [wstart[i], wstart[i + 1]), then the columns items, context i
-// owning [hstart[i], hstart[i + 1]) of those.
+// apart).  Batched, the rows items of every context come first (with the
+// columns items of contexts that form their own mu), context i owning
+// [wstart[i], wstart[i + 1]), then the columns items that take E from the
+// rows items, context i owning [hstart[i], hstart[i + 1]) of those.
 struct Src {
     const unsigned char *tab;
     const int *wstart, *hstart;
@@ -957,11 +962,11 @@ __device__ __forceinline__ const Params &item_of(const Params &P0, const Src &sr
         const int nw = __ldg(src.wstart + src.n);
         const int *pre = src.wstart;
         int r = it;
-        side = 0;
+        bool first = true;
         if (r >= nw) {
             pre = src.hstart;
             r -= nw;
-            side = 1;
+            first = false;
         }
         int lo = 0, hi = src.n - 1;          // last i with pre[i] <= r
         while (lo < hi) {
@@ -969,7 +974,10 @@ __device__ __forceinline__ const Params &item_of(const Params &P0, const Src &sr
             if (__ldg(pre + mid) <= r) lo = mid; else hi = mid - 1;
         }
         k = r - __ldg(pre + lo);
-        return *reinterpret_cast<const Params *>(src.tab + (size_t)lo * src.stride);
+        const Params &P = *reinterpret_cast<const Params *>(src.tab + (size_t)lo * src.stride);
+        side = first ? (k >= P.items_a ? 1 : 0) : 1;
+        if (first && side == 1) k -= P.items_a;
+        return P;
     }
 }
 
@@ -1060,8 +1068,10 @@ __device__ __forceinline__ void chain_body(const Params &P0, const Src src, cons
                 Item x;
                 if (!decode(P, side, k, x)) continue;
                 const Side &Sd = P.side[side];
-                if (side == 0) {
-                    // rows item: the owned W tile, then the walked H^T and V tiles
+                if (x.rl) {
+                    // rows item: the owned tile, then the walked tiles (and V
+                    // prefetches); a columns item formed like one reads the
+                    // other orientation's tiles
                     if (hphase) {                     // cannot happen: rows items are claimed first
                         atomicOr((int *)&S->abort, 128);
                         goto done0;
@@ -1178,7 +1188,7 @@ __device__ __forceinline__ void chain_body(const Params &P0, const Src src, cons
                 const Params &P = item_of<BATCH>(P0, src, it, side, k);
                 Item x;
                 if (!decode(P, side, k, x)) continue;
-                if (side == 0) {
+                if (x.rl) {
                     if (!wait32(S, &S->a_full, iw & 1)) goto done1;
                     fence_after();
                     // the owned tile into TMEM once per item (ordered after the
@@ -1290,13 +1300,16 @@ __device__ __forceinline__ void chain_body(const Params &P0, const Src src, cons
             int side, k;
             const Params &P = item_of<BATCH>(P0, src, it, side, k);
             Item x;
-            if (!decode(P, side, k, x) || side != 0) continue;
-            unsigned char *eg = reinterpret_cast<unsigned char *>(
-                P.Et + ((int64_t)x.block * P.side[0].own_tiles + x.ot) * P.et_cols * (kEBytes / 2));
+            if (!decode(P, side, k, x) || !x.rl) continue;
+            // every E tile of a rows item (or of a columns item formed like
+            // one) gets this warp's release; only shared E goes to HBM
+            const bool store = side == 0 && P.share;
+            unsigned char *eg = store ? reinterpret_cast<unsigned char *>(
+                P.Et + ((int64_t)x.block * P.side[0].own_tiles + x.ot) * P.et_cols * (kEBytes / 2)) : nullptr;
             for (int j = 0; j < x.nj; ++j, ++te) {
                 const uint32_t be = te & 1;
                 if (!wait32(S, &S->e_full[be], (te >> 1) & 1)) goto done3;
-                if (lane == 0)
+                if (store && lane == 0)
                     asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n\t"
                                  "cp.async.bulk.commit_group;\n\t"
                                  "cp.async.bulk.wait_group.read 0;"
@@ -1307,7 +1320,7 @@ __device__ __forceinline__ void chain_body(const Params &P0, const Src src, cons
             }
             // the item's E complete in HBM: count it (release after the
             // async-proxy writes)
-            if (lane == 0) {
+            if (store && lane == 0) {
                 asm volatile("cp.async.bulk.wait_group 0;\n\tfence.proxy.async.global;" ::: "memory");
                 __threadfence();
                 atomicAdd(P.sync + 2 + x.block, 1);
@@ -1335,7 +1348,7 @@ __device__ __forceinline__ void chain_body(const Params &P0, const Src src, cons
             Item x;
             if (!decode(P, side, k, x)) continue;
             const Side &Sd = P.side[side];
-            if (side == 0) {
+            if (x.rl) {
                 const float pp = P.p, mu_min = P.mu_min;
                 // V straight from HBM into registers, two tiles ahead: this
                 // thread's 16-byte chunks (c / (16 / sizeof(VT)) + i, row rho)
@@ -1429,7 +1442,7 @@ __device__ __forceinline__ void chain_body(const Params &P0, const Src src, cons
             if (!wait32(S, &S->g_full, ic & 1)) goto done2;
             {
                 unsigned char *stg = sStgH;
-                if (side == 0) {
+                if (x.rl) {
                     if (!wait32x2(S, &S->e_empty[te & 1], ((te >> 1) & 1) ^ 1, &S->e_empty[(te + 1) & 1],
                                   (((te + 1) >> 1) & 1) ^ 1))
                         goto done2;
@@ -1443,7 +1456,7 @@ __device__ __forceinline__ void chain_body(const Params &P0, const Src src, cons
                 const int nacc = x.rows_per / kOwn;
                 for (int a = 0; a < nacc; ++a)
                 for (int cp = 0; cp < KP; cp += 64, ++np) {
-                    const uint32_t gcol = side == 0 ? kGCol : 256u * (uint32_t)a;
+                    const uint32_t gcol = x.rl ? kGCol : 256u * (uint32_t)a;
                     float *gbase = Sd.G + (x.own_start + (int64_t)x.row0 + 128 * a) * P.ldk;
                     const int rows = x.own_rows_in_tile - 128 * a;
                     float g[32];
@@ -1478,7 +1491,7 @@ __device__ __forceinline__ void chain_body(const Params &P0, const Src src, cons
                 // a rows item staged in the E buffers, which this warp fills
                 // again with the next item's first tile: first every warp
                 // must be done reading the last pass
-                if (side == 0 && !wait32(S, &S->stg_empty, (np & 1) ^ 1)) goto done2;
+                if (x.rl && !wait32(S, &S->stg_empty, (np & 1) ^ 1)) goto done2;
             }
             // the item is done with shared memory and TMEM (the producer's
             // columns stages may take over once every earlier item is)
@@ -1747,14 +1760,19 @@ psgld_status prepare_dense(psgld_ctx *c, cudaStream_t st)
     c->ni_max = cdiv(maxI, 64);
     c->nj_max = cdiv(maxJ, 64);
     const int vs = vb ? 2 : 4;
-    const int stages = two_sided_stages(c->KP);
+    // the limit is an attribute of the kernel, shared by every context that
+    // launches it (any K width): the largest size any of them asks for
     for (int pm = 0; pm < 4; ++pm)
         PSGLD_CK(c, cudaFuncSetAttribute(pick_chain(vb, pm), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)two_sided_smem(c->KP, stages)));
+                                         (int)kTwoSidedMax));
+    int sms = 0;
+    PSGLD_CK(c, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
+    c->share_e = two_sided_share(c->opt.dense_share_e, maxI, c->B, c->mt_max, c->nt_max, sms);
     const int64_t B = c->B;
     const int64_t nA = B * B * c->mt_max * c->nj_max * 8192;
+    const int64_t nB = c->share_e ? 0 : B * B * c->nt_max * c->ni_max * 8192;   // V tiles, other orientation
     const int64_t nW = B * 2 * c->mt_max * 64 * c->KP, nH = B * 2 * c->nt_max * 64 * c->KP;
-    const int64_t nE = B * c->mt_max * 4 * c->nt2_max * 8192;    // one part's E tiles
+    const int64_t nE = c->share_e ? B * c->mt_max * 4 * c->nt2_max * 8192 : 0;   // one part's E tiles
     auto al = [&](void **p, size_t bytes) -> psgld_status {
         *p = dev_alloc(c, bytes, st);
         if (!*p) return fail(c, PSGLD_ERR_OOM, "device allocation failed");
@@ -1764,9 +1782,10 @@ psgld_status prepare_dense(psgld_ctx *c, cudaStream_t st)
         return PSGLD_OK;
     };
     psgld_status s = al(&c->VA, (size_t)nA * vs);
+    if (s == PSGLD_OK && nB) s = al(&c->VB, (size_t)nB * vs);
     if (s == PSGLD_OK) s = al((void **)&c->Wsh, (size_t)nW * 2);
     if (s == PSGLD_OK) s = al((void **)&c->Hsh, (size_t)nH * 2);
-    if (s == PSGLD_OK) s = al((void **)&c->Et, (size_t)nE * 2);
+    if (s == PSGLD_OK && nE) s = al((void **)&c->Et, (size_t)nE * 2);
     if (s == PSGLD_OK) s = al((void **)&c->tsync, sizeof(int) * (size_t)(2 + B));
     return s;
 }
@@ -1774,16 +1793,22 @@ psgld_status prepare_dense(psgld_ctx *c, cudaStream_t st)
 psgld_status build_dense_tiles(psgld_ctx *c, cudaStream_t st)
 {
     if (c->dense_kind != 2) return PSGLD_OK;
-    // V is read by the rows items only (the columns items take E from them)
+    // V for the rows items; and in the other orientation for columns items
+    // that form their own mu (with shared E they take E from the rows items)
     const int64_t n = c->I * c->J;
     const unsigned grid = (unsigned)std::min<int64_t>((n + 255) / 256, 152 * 32);
-    if (c->v_bf16)
-        build_vtiles_kernel<__nv_bfloat16><<<grid, 256, 0, st>>>(c->Vd, c->I, c->J, c->B, 0, c->mt_max,
-                                                                  c->nj_max, (__nv_bfloat16 *)c->VA);
-    else
-        build_vtiles_kernel<float><<<grid, 256, 0, st>>>(c->Vd, c->I, c->J, c->B, 0, c->mt_max, c->nj_max,
-                                                          (float *)c->VA);
-    PSGLD_CK(c, cudaGetLastError());
+    for (int side = 0; side < (c->share_e ? 1 : 2); ++side) {
+        const int own_tiles = side == 0 ? c->mt_max : c->nt_max;
+        const int walk_tiles = side == 0 ? c->nj_max : c->ni_max;
+        void *out = side == 0 ? c->VA : c->VB;
+        if (c->v_bf16)
+            build_vtiles_kernel<__nv_bfloat16><<<grid, 256, 0, st>>>(c->Vd, c->I, c->J, c->B, side, own_tiles,
+                                                                      walk_tiles, (__nv_bfloat16 *)out);
+        else
+            build_vtiles_kernel<float><<<grid, 256, 0, st>>>(c->Vd, c->I, c->J, c->B, side, own_tiles,
+                                                              walk_tiles, (float *)out);
+        PSGLD_CK(c, cudaGetLastError());
+    }
     return PSGLD_OK;
 }
 
@@ -1806,6 +1831,18 @@ psgld_status build_dense_shadows(psgld_ctx *c, cudaStream_t st)
 // tile: a third fewer bytes per MAC); the last blocks' columns items, which
 // end the launch, keep 128 rows so that its CTAs finish together.  The
 // option overrides the rule; the results do not depend on it.
+// Columns items take E from the rows items (three contractions per block,
+// but a wait for the block's rows items and E through L2 / HBM) when the
+// row pieces are long (each columns item walks at least 512 W rows) and the
+// part's items fill more than one wave of CTAs; short pieces or a single
+// wave favour columns items that form their own mu, all items at once.
+// The option overrides the rule (-1 = the rule).
+int two_sided_share(int opt, int64_t max_rows, int B, int mt, int nt, int sms)
+{
+    if (opt >= 0) return opt;
+    return max_rows >= 512 && (int64_t)B * (mt + nt) > sms ? 1 : 0;
+}
+
 static int two_sided_hwide(const psgld_ctx *c)
 {
     if (c->opt.wide_col_blocks >= 0) return std::min(c->opt.wide_col_blocks, c->B);
@@ -1820,15 +1857,16 @@ static void fill_two_sided(const psgld_ctx *c, int part, two_sided::Params &P)
     A.own_sh = c->Wsh; A.walk_sh = c->Hsh; A.Vt = (const unsigned char *)c->VA; A.G = c->G;
     A.n_own = I; A.n_walk = J; A.own_tiles = c->mt_max; A.walk_tiles = c->nj_max;
     A.own_sh64 = 2 * c->mt_max; A.walk_sh64 = 2 * c->nt_max;
-    Bs.own_sh = nullptr; Bs.walk_sh = c->Wsh; Bs.Vt = nullptr; Bs.G = c->G + I * c->ldk;
-    Bs.n_own = J; Bs.n_walk = I; Bs.own_tiles = c->nt2_max; Bs.walk_tiles = c->ni_max;
+    Bs.own_sh = c->Hsh; Bs.walk_sh = c->Wsh; Bs.Vt = (const unsigned char *)c->VB; Bs.G = c->G + I * c->ldk;
+    Bs.n_own = J; Bs.n_walk = I; Bs.own_tiles = c->nt_max; Bs.walk_tiles = c->ni_max;
     Bs.own_sh64 = 2 * c->nt_max; Bs.walk_sh64 = 2 * c->mt_max;
+    P.share = c->share_e;
     P.Et = c->Et;
     P.sync = c->tsync;
     P.et_cols = 4 * c->nt2_max;
     P.ht1 = c->nt_max;
     P.ht2 = c->nt2_max;
-    P.hwide = two_sided_hwide(c);
+    P.hwide = c->share_e ? two_sided_hwide(c) : 0;
     P.B = c->B;
     P.part = part;
     P.KP = c->KP;
@@ -1920,7 +1958,8 @@ int fill_dense_param(const psgld_ctx *c, int part, void *dst, int *first_items)
         two_sided::Params P;
         fill_two_sided(c, part, P);
         std::memcpy(dst, &P, sizeof P);
-        *first_items = P.items_a;
+        // rows items first; columns items formed like them go with them
+        *first_items = P.share ? P.items_a : P.items;
         return P.items;
     }
     DenseParams P;
@@ -1942,7 +1981,7 @@ psgld_status launch_dense_batch(psgld_ctx *c0, int key, const void *params, cons
         const int pm = key & 3;
         const size_t smem = two_sided_smem(KP, two_sided_stages(KP));
         ChainBatchFn fn = pick_chain_batch(vb, pm);
-        PSGLD_CK(c0, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        PSGLD_CK(c0, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTwoSidedMax));
         int sms = 0;
         PSGLD_CK(c0, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c0->device));
         int grid = std::min(total, sms);

@@ -89,6 +89,8 @@ struct psgld_ctx {
     int KP = 0;                      // K rounded up to 64 (two-sided kernel)
     int v_bf16 = 0;                  // V tiles in BF16
     void *VA = nullptr;                         // V tiles (rows of V owned)
+    void *VB = nullptr;                         // ... columns owned (columns items forming their own mu)
+    int share_e = 0;                            // columns items take E from the rows items
     uint16_t *Et = nullptr;                     // E tiles of one part (BF16)
     int *tsync = nullptr;                       // two-sided kernel counters: 2 + B ints
     uint16_t *Wsh = nullptr, *Hsh = nullptr;    // BF16 shadows of W, H^T
@@ -213,6 +215,9 @@ int dense_mtiles(const psgld_ctx *c);
 // Chooses the kernel (options dense_path, dense_v_bf16; K; block sizes),
 // sets its attributes and allocates the two-sided kernel's tiles.
 psgld_status prepare_dense(psgld_ctx *c, cudaStream_t st);
+// Whether the two-sided kernel's columns items take E from the rows items
+// (opt >= 0: as given; -1: long row pieces and more than one wave of items).
+int two_sided_share(int opt, int64_t max_rows, int B, int mt, int nt, int sms);
 // V tiles of the two-sided kernel from c->Vd (no-op for the single-pass one).
 psgld_status build_dense_tiles(psgld_ctx *c, cudaStream_t st);
 // BF16 shadows of the current factors (two-sided kernel with factors set).

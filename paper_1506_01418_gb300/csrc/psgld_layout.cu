@@ -329,13 +329,14 @@ void free_layout(psgld_ctx *c)
     dev_free(c, c->Vd);
     dev_free(c, c->hpart);
     dev_free(c, c->VA);
+    dev_free(c, c->VB);
     dev_free(c, c->Et);
     dev_free(c, c->tsync);
     dev_free(c, c->Wsh);
     dev_free(c, c->Hsh);
     c->Vd = nullptr;
     c->hpart = nullptr;
-    c->VA = nullptr;
+    c->VA = c->VB = nullptr;
     c->Et = nullptr;
     c->tsync = nullptr;
     c->Wsh = c->Hsh = nullptr;

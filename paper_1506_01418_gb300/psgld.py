@@ -52,7 +52,8 @@ class psgld_options(C.Structure):
                 ("dense_v_bf16", C.c_int32), ("part_mode", C.c_int32),
                 ("dense_fp8", C.c_int32), ("gather_bf16", C.c_int32), ("max_sms", C.c_int32),
                 ("batch_ctas", C.c_int32), ("batch_update_blocks", C.c_int32),
-                ("debug_wait_polls", C.c_int32), ("wide_col_blocks", C.c_int32)]
+                ("debug_wait_polls", C.c_int32), ("wide_col_blocks", C.c_int32),
+                ("dense_share_e", C.c_int32)]
 
 
 class psgld_job(C.Structure):

@@ -41,6 +41,10 @@ MIX = [
     (260, 390, 200, 1.0, 0, 0, dict(dense_path=2)),   # K width 256
     (700, 450, 40, 2.0, 0, 0, dict(dense_path=2, dense_v_bf16=1)),
     (333, 777, 64, 2.0, 0, 0, dict(dense_path=2, dense_v_bf16=1)),
+    # columns items taking E from the rows items, in the same launches as
+    # contexts whose columns items form their own mu
+    (513, 2000, 50, 1.0, 0, 1, dict(dense_path=2, dense_share_e=1)),
+    (700, 450, 40, 2.0, 0, 0, dict(dense_path=2, dense_v_bf16=1, dense_share_e=1)),
 ]
 B = 4
 

@@ -29,10 +29,11 @@ FP32 precision.  What is checked:
   the drift in RMS; the chain's posterior RMSE within 1 % of the oracle's.
 
 Every case runs on both kernels: the single-pass one (mu once per entry, G_H
-summed over a block's 128-row tiles by the update) and the two-sided one
-(mu and E once per entry in the rows items, which store E; the columns
-items take G_H = E^T W from it), the latter also with V kept in BF16, where
-the bound adds the rounding of v.
+summed over a block's 128-row tiles by the update) and the two-sided one, in
+both of its modes -- every item forming its own mu and E (dense_share_e=0),
+or the rows items storing E and the columns items taking G_H = E^T W from it
+(dense_share_e=1) -- also with V kept in BF16, where the bound adds the
+rounding of v.
 """
 import numpy as np
 import pytest
@@ -67,8 +68,10 @@ KERNELS = {
     "single_pass": dict(dense_path=3),
     "single_pass_fp8": dict(dense_path=3, dense_fp8=1),
     "auto": dict(dense_path=1),
-    "two_sided": dict(dense_path=2),
-    "two_sided_bf16v": dict(dense_path=2, dense_v_bf16=1),
+    "two_sided": dict(dense_path=2, dense_share_e=0),
+    "two_sided_bf16v": dict(dense_path=2, dense_v_bf16=1, dense_share_e=0),
+    "two_sided_share": dict(dense_path=2, dense_share_e=1),
+    "two_sided_bf16v_share": dict(dense_path=2, dense_v_bf16=1, dense_share_e=1),
 }
 
 
@@ -144,7 +147,7 @@ def test_dense_part_step_drift_within_bf16_bound(name, kernel):
 
 
 @pytest.mark.parametrize("p", [1.0, 1.5, 2.0, 3.0])
-@pytest.mark.parametrize("kernel", ["single_pass", "two_sided", "two_sided_bf16v"])
+@pytest.mark.parametrize("kernel", ["single_pass", "two_sided", "two_sided_bf16v", "two_sided_share"])
 def test_dense_mu_below_mu_min_drift_within_bound(kernel, p):
     """mu below mu_min = 1e-2 on the tensor cores: every 5th row of W and
     every 7th column of H zero (mu = 0 exactly: BF16 keeps zeros, so e =
@@ -185,7 +188,7 @@ def test_dense_mu_below_mu_min_drift_within_bound(kernel, p):
             assert np.sqrt(np.mean(D[zero][zm] ** 2)) > 4 * np.sqrt(np.mean(bnd[zero][zm] ** 2))
 
 
-@pytest.mark.parametrize("kernel", ["single_pass", "two_sided"])
+@pytest.mark.parametrize("kernel", ["single_pass", "two_sided", "two_sided_share"])
 def test_dense_graph_replay_equals_direct_launches(kernel):
     a, _ = _make("gauss_K50_two_mtiles_three_ntiles", kernel=kernel, use_graphs=1, burn_in_sweeps=1)
     b, _ = _make("gauss_K50_two_mtiles_three_ntiles", kernel=kernel, use_graphs=0, burn_in_sweeps=1)
@@ -200,7 +203,7 @@ def test_dense_graph_replay_equals_direct_launches(kernel):
         assert np.array_equal(x, y)
 
 
-@pytest.mark.parametrize("kernel", ["single_pass", "two_sided_bf16v", "single_pass_fp8"])
+@pytest.mark.parametrize("kernel", ["single_pass", "two_sided_bf16v", "single_pass_fp8", "two_sided_bf16v_share"])
 def test_dense_is_deterministic(kernel):
     a, _ = _make("poisson_uneven_mtiles_K32", kernel=kernel)
     b, _ = _make("poisson_uneven_mtiles_K32", kernel=kernel)
@@ -241,16 +244,17 @@ def test_dense_size_proportional_parts_drift_within_bound(kernel):
     assert len(seen) > 1
 
 
+@pytest.mark.parametrize("kernel", ["two_sided", "two_sided_share"])
 @pytest.mark.parametrize("name,sms", [("poisson_K200_B3", 7), ("poisson_K200_B3", 1),
                                       ("gaussnmf_K256_three_tiles", 2), ("gaussnmf_K256_three_tiles", 1),
                                       ("gauss_K50_two_mtiles_three_ntiles", 1)])
-def test_two_sided_kernel_on_fewer_sms_gives_the_same_chain(name, sms):
+def test_two_sided_kernel_on_fewer_sms_gives_the_same_chain(name, sms, kernel):
     """max_sms only shrinks the persistent grid: every item still runs once,
     so the chain is the same bit for bit.  On one or two CTAs each CTA runs
     several rows items before its first columns item, whose stages then
     take over the rows items' shared memory."""
-    a, _ = _make(name, kernel="two_sided")
-    b, _ = _make(name, kernel="two_sided", max_sms=sms)
+    a, _ = _make(name, kernel=kernel)
+    b, _ = _make(name, kernel=kernel, max_sms=sms)
     a.gpu.sweep(2)
     b.gpu.sweep(2)
     Wa, Ha = a.gpu_factors()
@@ -266,7 +270,7 @@ def test_two_sided_columns_item_width_does_not_change_the_chain(name):
     B = DENSE[name][3]
     out = []
     for w in (0, B, -1):
-        pr, _ = _make(name, kernel="two_sided", wide_col_blocks=w)
+        pr, _ = _make(name, kernel="two_sided_share", wide_col_blocks=w)
         pr.gpu.sweep(2)
         out.append(pr.gpu_factors())
     for Wx, Hx in out[1:]:

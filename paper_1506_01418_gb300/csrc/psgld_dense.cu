@@ -562,6 +562,571 @@ dense_grad_batch_kernel(const unsigned char *__restrict__ tab, size_t stride, co
 }
 
 // ===========================================================================
+// Two-sided pipelined kernel, every item forming its own mu (K <= 256)
+// ===========================================================================
+//
+// The form for short row pieces or parts of a single wave of items (the
+// kernel after it, with E shared between the two kinds of items, for long
+// pieces in several waves).  A block larger than one 128-row tile would need
+// its G_H summed over the block's M-tiles.  Instead the work of a part is
+// split into two kinds of items that read only the previous factors: a rows
+// item owns 128 rows of W of one block and walks all the block's columns,
+// accumulating G_W of those rows in TMEM; a columns item owns 128 rows of H^T
+// (columns of V) and walks all the block's rows, accumulating G_H.  Each
+// computes its own mu and E (GEMM1 twice per entry: 4 contractions instead
+// of 3), so all of a part's items run at once, and every G row is written
+// once, complete, by one CTA -- no partial sums, no atomics.
+//
+// Operands come from HBM already in the MMA layout: BF16 shadows of W and
+// H^T cut into 128-row canonical K-major tiles per piece (kept by the update
+// kernel), and V cut into 128 x 64 tiles per block, once per orientation, in
+// the order the epilogue reads them (4-column FP32 or 8-column BF16 chunks,
+// one 16-byte chunk per owned row, so a warp reads 512 contiguous bytes).
+// Every tile is one bulk copy.  Items are assigned to CTAs round robin.
+//
+// One persistent CTA per SM, 10 warps:
+//   warp 0               producer: the owned tile once per item, then per
+//                         walked tile the other factor's 64-row tile and the
+//                         V tile, into two rings of slots (bulk copies);
+//   warp 1               MMA issuer: GEMM1 mu_j = A . B_j^T into one of two
+//                         TMEM buffers, then GEMM2 G += E_(j-1) . B_(j-1)
+//                         (B read MN-major), so GEMM1 of tile j overlaps the
+//                         epilogue of tile j-1; completions via tcgen05.commit.
+//                         Both warps run their loops with all 32 lanes (the
+//                         descriptors stay warp-uniform, in uniform registers)
+//                         and lane 0 performs each copy and MMA;
+//   warps 2-9            epilogue, two warps per TMEM lane quarter (32 of the
+//                         tile's 64 columns each): TMEM mu + V (shared
+//                         memory) -> E (BF16, shared memory, two buffers),
+//                         and after an item's last tile the G rows from TMEM
+//                         to HBM.  The Tweedie power is a template parameter
+//                         (p = 0, 1, 2, other), so the epilogue is straight-line.
+// TMEM: mu buffers at columns 0 and 64, G at 128 .. 128 + KP, and the owned
+// tile (copied from shared memory once per item with tcgen05.cp, so GEMM1
+// reads A from TMEM and shared memory serves only B) in the last KP / 2
+// columns.
+// Padding rows and columns of every tile are zero, so mu and E are zero
+// there and need no masks.
+namespace two_sided_rc {
+
+constexpr int kThreads = 320;     // warp 0 producer, warp 1 MMA, warps 2..9 epilogue
+constexpr int kOwn = 128;          // owned rows per item (TMEM lanes)
+constexpr int kBN = 64;            // walked rows per tile
+constexpr uint32_t kTmemCols = 512;
+constexpr uint32_t kGCol = 128;
+constexpr int kMaxStages = 4;
+constexpr int kEpiWarps = 8;       // two per TMEM lane quarter, 32 walked columns each
+
+struct Side {
+    const uint16_t *own_sh;     // BF16 shadow tiles of the owned factor
+    const uint16_t *walk_sh;    // ... of the walked factor
+    const unsigned char *Vt;    // V tiles in this orientation
+    float *G;                   // G rows of the owned factor
+    int64_t n_own, n_walk;      // I or J
+    int own_tiles;              // 128-row tile slots per owned piece (items, V tiles)
+    int walk_tiles;             // 64-row V tile slots per walked piece
+    int own_sh64, walk_sh64;    // 64-row shadow tiles per owned / walked piece
+};
+
+struct Params {
+    Side side[2];
+    int B, part, KP, ldk, stages, vstages, items_a, items;
+    float phi_inv, p, mu_min;
+    int p_mode;
+    int *err;
+};
+
+struct Bars {
+    uint64_t full[kMaxStages], empty[kMaxStages];       // walked factor tiles
+    uint64_t vfull[kMaxStages], vempty[kMaxStages];     // V tiles
+    uint64_t mu_full[2], mu_empty[2], e_full[2], e_empty[2];
+    uint64_t a_full, a_empty, g_full, g_empty;
+    uint32_t tmem;
+    int abort;
+};
+
+__device__ __forceinline__ void bar_init(uint64_t *b, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(saddr(b)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void bar_arrive(uint64_t *b)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(saddr(b)) : "memory");
+}
+
+// Leader-only forms for warp-uniform loops: every lane executes the
+// instruction with the same (uniform) operands and elect.sync picks the one
+// lane that performs it (the same lane each time, the whole warp being
+// active), so descriptors and addresses stay in uniform registers and each
+// MMA issues in a few cycles.  The `leader` argument is unused (kept for the
+// call sites' readability).
+__device__ __forceinline__ void expect_tx_if(uint32_t, uint64_t *b, uint32_t bytes)
+{
+    asm volatile("{\n\t.reg .pred e;\n\telect.sync _|e, 0xffffffff;\n\t"
+                 "@e mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n\t}"
+                 :: "r"(saddr(b)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s_if(uint32_t, void *dst, const void *src, uint32_t bytes, uint64_t *b)
+{
+    asm volatile("{\n\t.reg .pred e;\n\telect.sync _|e, 0xffffffff;\n\t"
+                 "@e cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n\t}"
+                 :: "r"(saddr(dst)), "l"(src), "r"(bytes), "r"(saddr(b)) : "memory");
+}
+
+__device__ __forceinline__ void mma_ta_if(uint32_t, uint32_t d, uint32_t a, uint64_t bdesc, uint32_t id,
+                                          uint32_t acc)
+{
+    asm volatile("{\n\t.reg .pred p, e;\n\telect.sync _|e, 0xffffffff;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                 "@e tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}"
+                 :: "r"(d), "r"(a), "l"(bdesc), "r"(id), "r"(acc) : "memory");
+}
+
+__device__ __forceinline__ void mma_ss_if(uint32_t, uint32_t d, uint64_t adesc, uint64_t bdesc, uint32_t id,
+                                          uint32_t acc)
+{
+    asm volatile("{\n\t.reg .pred p, e;\n\telect.sync _|e, 0xffffffff;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                 "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+                 :: "r"(d), "l"(adesc), "l"(bdesc), "r"(id), "r"(acc) : "memory");
+}
+
+__device__ __forceinline__ void cp_if(uint32_t, uint32_t taddr, uint64_t sdesc_)
+{
+    asm volatile("{\n\t.reg .pred e;\n\telect.sync _|e, 0xffffffff;\n\t"
+                 "@e tcgen05.cp.cta_group::1.128x256b [%0], %1;\n\t}"
+                 :: "r"(taddr), "l"(sdesc_) : "memory");
+}
+
+__device__ __forceinline__ void commit_if(uint32_t, uint64_t *b)
+{
+    asm volatile("{\n\t.reg .pred e;\n\telect.sync _|e, 0xffffffff;\n\t"
+                 "@e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n\t}"
+                 :: "r"(saddr(b)) : "memory");
+}
+
+// GEMM1 of one walked tile, fully unrolled for the K width KPC: mu (TMEM
+// column d) = A (TMEM, tA) . B^T (walked tile at shared address aB, 128-byte
+// swizzled K-major atoms of 64 rows x 128 B).  With compile-time K steps the
+// descriptors are constants plus one uniform base, so each MMA issues in a
+// few cycles.
+template <int KPC>
+__device__ __forceinline__ void gemm1_tile(uint32_t ld, uint32_t d, uint32_t tA, uint32_t aB, uint32_t id1)
+{
+    const uint64_t base = sdesc_sw128(aB, 16, 1024);
+#pragma unroll
+    for (int ks = 0; ks < KPC / 16; ++ks)
+        mma_ta_if(ld, d, tA + (uint32_t)ks * 8,
+                  base + (uint64_t)(((ks >> 2) * (64 * 128) + (ks & 3) * 32) >> 4), id1, ks > 0);
+}
+
+// The owned tile (shared address aA, 128-row atoms) into TMEM at tA.
+template <int KPC>
+__device__ __forceinline__ void own_to_tmem(uint32_t ld, uint32_t tA, uint32_t aA)
+{
+    const uint64_t base = sdesc_sw128(aA, 16, 1024);
+#pragma unroll
+    for (int ks = 0; ks < KPC / 16; ++ks)
+        cp_if(ld, tA + (uint32_t)ks * 8, base + (uint64_t)(((ks >> 2) * (128 * 128) + (ks & 3) * 32) >> 4));
+}
+
+// Bounded wait by a whole warp, with one warp-uniform answer.  Every lane
+// polls (control flow stays uniform, which keeps the MMA warp's operands in
+// uniform registers); a completed phase costs one try_wait and one vote.
+// The wait gives up (and raises the abort flag) when the CTA is aborting or
+// the wait runs out.
+__device__ __forceinline__ bool wait32(Bars *S, uint64_t *b, uint32_t parity)
+{
+    if (__all_sync(0xffffffffu, bar_try_wait(b, parity))) return true;
+    const bool stop = __any_sync(0xffffffffu, *(volatile int *)&S->abort != 0);
+    bool ok = !stop && bar_wait(b, parity);
+    ok = __all_sync(0xffffffffu, ok);
+    if (!ok && !stop && (threadIdx.x & 31) == 0) {
+        // the first warp to give up records its role: 128 producer, 256 MMA, 512 epilogue
+        const int warp = threadIdx.x >> 5;
+        atomicOr((int *)&S->abort, warp == 0 ? 128 : warp == 1 ? 256 : 512);
+    }
+    return ok;
+}
+
+// Slot and phase of a ring of n slots, advanced one use at a time.
+struct Ring {
+    uint32_t slot = 0, phase = 0;
+    __device__ __forceinline__ void next(uint32_t n)
+    {
+        if (++slot == n) { slot = 0; phase ^= 1u; }
+    }
+};
+
+struct Item {
+    int side, own_piece, walk_piece, ot, own_rows_in_tile, nj;
+    int64_t own_start;
+};
+
+__device__ __forceinline__ bool decode(const Params &P, int it, Item &x)
+{
+    const int B = P.B;
+    int side = 0, k = it;
+    if (k >= P.items_a) { side = 1; k -= P.items_a; }
+    const Side &Sd = P.side[side];
+    const int b = k / Sd.own_tiles, ot = k % Sd.own_tiles;
+    const int cpiece = (b + P.part) % B;
+    x.side = side;
+    x.own_piece = side == 0 ? b : cpiece;
+    x.walk_piece = side == 0 ? cpiece : b;
+    x.ot = ot;
+    x.own_start = ((int64_t)x.own_piece * Sd.n_own) / B;
+    const int64_t own_rows = ((int64_t)(x.own_piece + 1) * Sd.n_own) / B - x.own_start;
+    const int64_t walk_rows = ((int64_t)(x.walk_piece + 1) * Sd.n_walk) / B -
+                              ((int64_t)x.walk_piece * Sd.n_walk) / B;
+    const int64_t left = own_rows - (int64_t)ot * kOwn;
+    x.own_rows_in_tile = (int)(left < kOwn ? left : kOwn);
+    x.nj = (int)((walk_rows + kBN - 1) / kBN);
+    return left > 0;
+}
+
+template <int PM>
+__device__ __forceinline__ float tweedie_pm(float p, float phi_inv, float mu_min, float v, float mu)
+{
+    const float d = (v - mu) * phi_inv;
+    if constexpr (PM == 0) {
+        return d;
+    } else {
+        const float mc = fmaxf(mu, mu_min);
+        if constexpr (PM == 1) return __fdividef(d, mc);
+        if constexpr (PM == 2) return __fdividef(d, mc * mc);
+        if constexpr (PM == 3) return d * exp2f(-p * __log2f(mc));
+    }
+}
+
+// Where the items' parameters come from: one context (the kernel parameter)
+// or, batched, a table of contexts in global memory whose items follow one
+// another (context i owns items [item_start[i], item_start[i + 1]); slots
+// `stride` bytes apart).
+struct Src {
+    const unsigned char *tab;
+    const int *item_start;
+    int n;
+    size_t stride;
+};
+
+template <bool BATCH>
+__device__ __forceinline__ const Params &ctx_of(const Params &P0, const Src &src, int it, int &local)
+{
+    if constexpr (!BATCH) {
+        local = it;
+        return P0;
+    } else {
+        int lo = 0, hi = src.n - 1;          // last i with item_start[i] <= it
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(src.item_start + mid) <= it) lo = mid; else hi = mid - 1;
+        }
+        local = it - __ldg(src.item_start + lo);
+        return *reinterpret_cast<const Params *>(src.tab + (size_t)lo * src.stride);
+    }
+}
+
+// The kernel body.  P0 gives what is uniform over the launch (K width,
+// ring depths); each item reads its own context's parameters.
+template <typename VT, int PM, bool BATCH>
+__device__ __forceinline__ void chain_body(const Params &P0, const Src src, const int total_items)
+{
+    extern __shared__ __align__(1024) unsigned char sm_raw[];
+    // the swizzled operand tiles need 1024-byte alignment (1 KB of slack is allocated)
+    unsigned char *sm = sm_raw + ((1024u - (saddr(sm_raw) & 1023u)) & 1023u);
+    const int KP = P0.KP;                                       // multiple of 64
+    const int NA = KP / 64;                                     // 128-byte atoms along K
+    const uint32_t a_bytes = (uint32_t)kOwn * KP * 2;           // owned tile
+    const uint32_t b_bytes = (uint32_t)kBN * KP * 2;            // walked tile
+    const uint32_t v_bytes = (uint32_t)kOwn * kBN * sizeof(VT); // V tile
+    constexpr uint32_t e_bytes = kOwn * kBN * 2;
+    unsigned char *sA = sm;
+    unsigned char *sE = sA + a_bytes;                           // 2 x e_bytes
+    unsigned char *sB = sE + 2 * e_bytes;                       // NS x b_bytes
+    unsigned char *sV = sB + (size_t)P0.stages * b_bytes;       // NV x v_bytes
+    Bars *S = reinterpret_cast<Bars *>(sV + (size_t)P0.vstages * v_bytes);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int NS = P0.stages, NV = P0.vstages;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NS; ++s) { bar_init(&S->full[s], 1); bar_init(&S->empty[s], 1); }
+        for (int s = 0; s < NV; ++s) { bar_init(&S->vfull[s], 1); bar_init(&S->vempty[s], kEpiWarps); }
+        for (int b = 0; b < 2; ++b) {
+            bar_init(&S->mu_full[b], 1); bar_init(&S->mu_empty[b], kEpiWarps);
+            bar_init(&S->e_full[b], kEpiWarps); bar_init(&S->e_empty[b], 1);
+        }
+        bar_init(&S->a_full, 1); bar_init(&S->a_empty, 1);
+        bar_init(&S->g_full, 1); bar_init(&S->g_empty, kEpiWarps);
+        S->abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(saddr(&S->tmem)), "r"(kTmemCols) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = S->tmem;
+
+    if (warp == 0) {
+        // ---------------- producer (whole warp, lane 0 performs)
+        {
+            const uint32_t ld = lane == 0;
+            uint32_t ic = 0;
+            Ring rb, rv;
+            for (int it = blockIdx.x; it < total_items; it += gridDim.x) {
+                int lit;
+                const Params &P = ctx_of<BATCH>(P0, src, it, lit);
+                Item x;
+                if (!decode(P, lit, x)) continue;
+                const Side &Sd = P.side[x.side];
+                if (!wait32(S, &S->a_empty, (ic & 1) ^ 1)) goto done0;
+                expect_tx_if(ld, &S->a_full, a_bytes);
+                {
+                    // rows 0..63 and 64..127 come from two 64-row shadow tiles;
+                    // in shared memory each atom holds all 128 rows
+                    const uint16_t *t0 = Sd.own_sh + ((int64_t)x.own_piece * Sd.own_sh64 + 2 * x.ot) * 64 * KP;
+                    for (int a = 0; a < NA; ++a) {
+                        bulk_g2s_if(ld, sA + a * 16384, t0 + a * 4096, 8192, &S->a_full);
+                        bulk_g2s_if(ld, sA + a * 16384 + 8192, t0 + 64 * KP + a * 4096, 8192, &S->a_full);
+                    }
+                }
+                const unsigned char *vbase =
+                    Sd.Vt + ((((int64_t)x.own_piece * P.B + x.walk_piece) * Sd.own_tiles + x.ot) *
+                             Sd.walk_tiles) * (int64_t)v_bytes;
+                for (int j = 0; j < x.nj; ++j) {
+                    const uint32_t st = rb.slot, sv = rv.slot;
+                    if (!wait32(S, &S->empty[st], rb.phase ^ 1)) goto done0;
+                    expect_tx_if(ld, &S->full[st], b_bytes);
+                    bulk_g2s_if(ld, sB + (size_t)st * b_bytes,
+                                Sd.walk_sh + ((int64_t)x.walk_piece * Sd.walk_sh64 + j) * kBN * KP,
+                                b_bytes, &S->full[st]);
+                    if (!wait32(S, &S->vempty[sv], rv.phase ^ 1)) goto done0;
+                    expect_tx_if(ld, &S->vfull[sv], v_bytes);
+                    bulk_g2s_if(ld, sV + (size_t)sv * v_bytes, vbase + (int64_t)j * v_bytes, v_bytes, &S->vfull[sv]);
+                    rb.next(NS);
+                    rv.next(NV);
+                }
+                ++ic;
+            }
+        }
+    done0:
+        __syncwarp();
+    } else if (warp == 1) {
+        // ---------------- MMA issuer (whole warp, lane 0 performs).  Tile
+        // number tc (counted over the CTA's items) uses mu / E buffer tc % 2,
+        // for the (tc / 2)-th time.
+        {
+            const uint32_t ld = lane == 0;
+            uint32_t tc = 0, ic = 0;
+            Ring r1, r2;     // walked-tile slots of GEMM1 (tile tc) and GEMM2 (tile tc - 1)
+            const uint32_t id1 = idesc_bf16(kOwn, kBN);
+            const uint32_t id2 = idesc_bf16(kOwn, KP, 0, 1);
+            // K-major, 128-byte swizzle: 8-row groups 1024 B apart; a K step of
+            // 16 entries moves 32 B inside an atom, 4 steps fill an atom, and the
+            // next atom of the owned tile starts 128 rows x 128 B further
+            const uint32_t aA = saddr(sA);
+            const uint32_t tA = tmem + (kTmemCols - (uint32_t)KP / 2);   // owned tile in TMEM
+            for (int it = blockIdx.x; it < total_items; it += gridDim.x) {
+                int lit;
+                const Params &P = ctx_of<BATCH>(P0, src, it, lit);
+                Item x;
+                if (!decode(P, lit, x)) continue;
+                if (!wait32(S, &S->a_full, ic & 1)) goto done1;
+                fence_after();
+                // the owned tile into TMEM once per item (ordered after the
+                // previous item's MMAs and before this item's: same issuing
+                // thread); its shared-memory slot is free when the copies are
+                switch (KP) {
+                case 64: own_to_tmem<64>(ld, tA, aA); break;
+                case 128: own_to_tmem<128>(ld, tA, aA); break;
+                case 192: own_to_tmem<192>(ld, tA, aA); break;
+                default: own_to_tmem<256>(ld, tA, aA); break;
+                }
+                commit_if(ld, &S->a_empty);
+                for (int j = 0; j <= x.nj; ++j) {
+                    if (j < x.nj) {
+                        const uint32_t st = r1.slot;
+                        const int b = (int)(tc & 1);
+                        if (!wait32(S, &S->full[st], r1.phase)) goto done1;
+                        if (!wait32(S, &S->mu_empty[b], ((tc >> 1) & 1) ^ 1)) goto done1;
+                        fence_after();
+                        const uint32_t aB = saddr(sB + (size_t)st * b_bytes);
+                        const uint32_t dmu = tmem + (uint32_t)(b * kBN);
+                        switch (KP) {
+                        case 64: gemm1_tile<64>(ld, dmu, tA, aB, id1); break;
+                        case 128: gemm1_tile<128>(ld, dmu, tA, aB, id1); break;
+                        case 192: gemm1_tile<192>(ld, dmu, tA, aB, id1); break;
+                        default: gemm1_tile<256>(ld, dmu, tA, aB, id1); break;
+                        }
+                        commit_if(ld, &S->mu_full[b]);
+                        ++tc;
+                        r1.next(NS);
+                    }
+                    if (j > 0) {
+                        // GEMM2 of tile j - 1 (tile number tp)
+                        const uint32_t tp = j < x.nj ? tc - 2 : tc - 1;
+                        const int b = (int)(tp & 1);
+                        const uint32_t st = r2.slot;
+                        if (!wait32(S, &S->e_full[b], (tp >> 1) & 1)) goto done1;
+                        if (j == 1 && !wait32(S, &S->g_empty, (ic & 1) ^ 1)) goto done1;
+                        fence_after();
+                        // A = E (K-major, one atom of 64 walked columns); B = the
+                        // walked tile read MN-major: MN atoms (64 entries of k)
+                        // 64 rows x 128 B apart (LBO), 8-row K groups 1024 B apart
+                        // (SBO), a K step of 16 walked rows = 2048 B
+                        const uint64_t dE = sdesc_sw128(saddr(sE + b * e_bytes), 16, 1024);
+                        const uint64_t dBt = sdesc_sw128(saddr(sB + (size_t)st * b_bytes), kBN * 128, 1024);
+#pragma unroll
+                        for (int ks = 0; ks < kBN / 16; ++ks)
+                            mma_ss_if(ld, tmem + kGCol, dE + (uint64_t)(ks * 2), dBt + (uint64_t)(ks * 128),
+                                      id2, (j > 1 || ks > 0));
+                        commit_if(ld, &S->e_empty[b]);
+                        commit_if(ld, &S->empty[st]);
+                        r2.next(NS);
+                    }
+                }
+                commit_if(ld, &S->g_full);
+                ++ic;
+            }
+        }
+    done1:
+        __syncwarp();
+    } else {
+        // ---------------- epilogue (warps 2..9): TMEM lane quarter warp % 4,
+        // walked columns 32 h .. 32 h + 31 of each tile, h = (warp - 2) / 4
+        const int q = warp & 3, hc = (warp - 2) >> 2;
+        const int rho = 32 * q + lane;                      // owned row in the tile
+        const int c = 32 * hc;
+        const uint32_t lane_base = (uint32_t)(32 * q) << 16;
+        uint32_t tc = 0, ic = 0;
+        Ring rv;
+        for (int it = blockIdx.x; it < total_items; it += gridDim.x) {
+            int lit;
+            const Params &P = ctx_of<BATCH>(P0, src, it, lit);
+            Item x;
+            if (!decode(P, lit, x)) continue;
+            const Side &Sd = P.side[x.side];
+            const float pp = P.p, phi_inv = P.phi_inv, mu_min = P.mu_min;
+            for (int j = 0; j < x.nj; ++j, ++tc, rv.next(NV)) {
+                const int b = (int)(tc & 1);
+                const uint32_t sv = rv.slot;
+                const uint32_t ph = (tc >> 1) & 1;
+                if (!wait32(S, &S->vfull[sv], rv.phase)) goto done2;
+                if (!wait32(S, &S->mu_full[b], ph)) goto done2;
+                if (!wait32(S, &S->e_empty[b], ph ^ 1)) goto done2;
+                fence_after();
+                const unsigned char *vt = sV + (size_t)sv * v_bytes;
+                unsigned char *eb = sE + b * e_bytes;
+                float mu[32];
+                tmem_ld32(tmem + lane_base + (uint32_t)(b * kBN + c), mu);
+                float v[32];
+                if constexpr (sizeof(VT) == 4) {
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const float4 w = *reinterpret_cast<const float4 *>(
+                            vt + ((size_t)((c >> 2) + i) * kOwn + rho) * 16);
+                        v[4 * i] = w.x; v[4 * i + 1] = w.y; v[4 * i + 2] = w.z; v[4 * i + 3] = w.w;
+                    }
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const uint4 w = *reinterpret_cast<const uint4 *>(
+                            vt + ((size_t)((c >> 3) + i) * kOwn + rho) * 16);
+                        const uint32_t u[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                        for (int h = 0; h < 4; ++h) {
+                            v[8 * i + 2 * h] = __uint_as_float(u[h] << 16);
+                            v[8 * i + 2 * h + 1] = __uint_as_float(u[h] & 0xffff0000u);
+                        }
+                    }
+                }
+                uint32_t pk[16];
+#pragma unroll
+                for (int h = 0; h < 16; ++h) {
+                    const float e0 = tweedie_pm<PM>(pp, phi_inv, mu_min, v[2 * h], mu[2 * h]);
+                    const float e1 = tweedie_pm<PM>(pp, phi_inv, mu_min, v[2 * h + 1], mu[2 * h + 1]);
+                    __nv_bfloat162 t2 = __floats2bfloat162_rn(e0, e1);
+                    pk[h] = *reinterpret_cast<uint32_t *>(&t2);
+                }
+                // E (owned row rho, walked columns c..c+31): row rho of the
+                // 128-byte-swizzled atom column, chunk (c/8 + g) ^ (rho % 8)
+#pragma unroll
+                for (int g = 0; g < 4; ++g)
+                    *reinterpret_cast<uint4 *>(eb + rho * 128 + ((((c >> 3) + g) ^ (rho & 7)) << 4)) =
+                        make_uint4(pk[4 * g], pk[4 * g + 1], pk[4 * g + 2], pk[4 * g + 3]);
+                fence_async_smem();
+                fence_before();
+                __syncwarp();
+                if (lane == 0) {
+                    bar_arrive(&S->vempty[sv]);
+                    bar_arrive(&S->mu_empty[b]);
+                    bar_arrive(&S->e_full[b]);
+                }
+            }
+            // the item's G rows: this warp's lane quarter, every other 32-column chunk
+            if (!wait32(S, &S->g_full, ic & 1)) goto done2;
+            fence_after();
+            {
+                const bool rv = rho < x.own_rows_in_tile;
+                float *dst = Sd.G + (x.own_start + (int64_t)x.ot * kOwn + rho) * P.ldk;
+                for (int cc = 32 * hc; cc < KP; cc += 64) {
+                    float g[32];
+                    tmem_ld32(tmem + lane_base + kGCol + (uint32_t)cc, g);
+                    if (rv) {
+#pragma unroll
+                        for (int h = 0; h < 32; h += 4)
+                            if (cc + h < P.ldk)
+                                *reinterpret_cast<float4 *>(dst + cc + h) = make_float4(g[h], g[h + 1], g[h + 2], g[h + 3]);
+                    }
+                }
+            }
+            fence_before();
+            __syncwarp();
+            if (lane == 0) bar_arrive(&S->g_empty);
+            ++ic;
+        }
+    done2:
+        __syncwarp();
+    }
+
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (threadIdx.x == 0 && S->abort) {                      // two-sided kernel (+ role)
+        if constexpr (BATCH) {
+            for (int i = 0; i < src.n; ++i)
+                atomicOr(reinterpret_cast<const Params *>(src.tab + (size_t)i * src.stride)->err, 64 | S->abort);
+        } else {
+            atomicOr(P0.err, 64 | S->abort);
+        }
+    }
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;"
+                     :: "r"(tmem), "r"(kTmemCols) : "memory");
+}
+
+template <typename VT, int PM>
+__global__ void __launch_bounds__(kThreads, 1) chain_kernel(const __grid_constant__ Params P)
+{
+    chain_body<VT, PM, false>(P, Src{nullptr, nullptr, 1, 0}, P.items);
+}
+
+// Many contexts of one K width, V type and power in one persistent launch.
+template <typename VT, int PM>
+__global__ void __launch_bounds__(kThreads, 1)
+chain_batch_kernel(const unsigned char *tab, size_t stride, const int *item_start, int n)
+{
+    chain_body<VT, PM, true>(*reinterpret_cast<const Params *>(tab), Src{tab, item_start, n, stride},
+                             __ldg(item_start + n));
+}
+
+}  // namespace two_sided_rc
+
+// ===========================================================================
 // Two-sided pipelined kernel (blocks of any size, K <= 256)
 // ===========================================================================
 //
@@ -662,8 +1227,6 @@ struct Params {
     int et_cols;                // E slots per W tile (4 x the 256-row columns items per piece)
     int hwide, ht1, ht2;        // blocks 0 .. hwide - 1: 256-row columns items (ht2 per piece), the
                                 // rest 128-row ones (ht1 per piece)
-    int share;                  // 1: columns items take E from the rows items; 0: they form
-                                // their own mu and E (rows items of the other orientation)
     int B, part, KP, ldk, stages, hstages, items_a, items;
     int bars_off;               // shared-memory offset of the barriers (past both layouts)
     float phi_inv, p, mu_min;
@@ -705,15 +1268,6 @@ __device__ __forceinline__ void expect_tx_if(uint32_t, uint64_t *b, uint32_t byt
     asm volatile("{\n\t.reg .pred e;\n\telect.sync _|e, 0xffffffff;\n\t"
                  "@e mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n\t}"
                  :: "r"(saddr(b)), "r"(bytes) : "memory");
-}
-
-// n arrivals at once (the producer standing in for the epilogue warps on an
-// E buffer that it fills by copy)
-__device__ __forceinline__ void arrive_n_if(uint32_t, uint64_t *b, uint32_t n)
-{
-    asm volatile("{\n\t.reg .pred e;\n\telect.sync _|e, 0xffffffff;\n\t"
-                 "@e mbarrier.arrive.shared::cta.b64 _, [%0], %1;\n\t}"
-                 :: "r"(saddr(b)), "r"(n) : "memory");
 }
 
 __device__ __forceinline__ void bulk_g2s_if(uint32_t, void *dst, const void *src, uint32_t bytes, uint64_t *b)
@@ -825,19 +1379,12 @@ __device__ __forceinline__ bool bar_test(uint64_t *bar, uint32_t parity)
     return ok != 0;
 }
 
-// Two or three waits with one vote when all the phases are already
+// Two waits with one vote when both phases are already
 // complete (the common case in the steady pipeline), else one by one.
 __device__ __forceinline__ bool wait32x2(Bars *S, uint64_t *a, uint32_t pa, uint64_t *b, uint32_t pb)
 {
     if (__all_sync(0xffffffffu, bar_test(a, pa) && bar_test(b, pb))) return true;
     return wait32(S, a, pa) && wait32(S, b, pb);
-}
-
-__device__ __forceinline__ bool wait32x3(Bars *S, uint64_t *a, uint32_t pa, uint64_t *b, uint32_t pb,
-                                         uint64_t *c, uint32_t pc)
-{
-    if (__all_sync(0xffffffffu, bar_test(a, pa) && bar_test(b, pb) && bar_test(c, pc))) return true;
-    return wait32(S, a, pa) && wait32(S, b, pb) && wait32(S, c, pc);
 }
 
 // Bounded wait of the producer warp until another CTA's count in HBM
@@ -879,7 +1426,7 @@ struct Ring {
 struct Item {
     int side, block, own_piece, walk_piece, ot, own_rows_in_tile, nj;
     int rows_per, row0;         // owned rows of the item (128 or 256) and its first row in the piece
-    bool rl;                    // a rows item, or a columns item formed like one (share = 0)
+    bool rl;                    // a rows item
     int64_t own_start;
 };
 
@@ -892,7 +1439,7 @@ __device__ __forceinline__ bool decode(const Params &P, int side, int k, Item &x
     const int B = P.B;
     const Side &Sd = P.side[side];
     int b, ot, rows_per = kOwn;
-    x.rl = side == 0 || !P.share;
+    x.rl = side == 0;
     if (x.rl) {
         b = k / Sd.own_tiles;
         ot = k % Sd.own_tiles;
@@ -940,10 +1487,9 @@ __device__ __forceinline__ float tweedie_pm(float p, float mu_min, float v, floa
 
 // Where the items' parameters come from: one context (the kernel parameter)
 // or, batched, a table of contexts in global memory (slots `stride` bytes
-// apart).  Batched, the rows items of every context come first (with the
-// columns items of contexts that form their own mu), context i owning
-// [wstart[i], wstart[i + 1]), then the columns items that take E from the
-// rows items, context i owning [hstart[i], hstart[i + 1]) of those.
+// apart).  Batched, the rows items of every context come first, context i
+// owning [wstart[i], wstart[i + 1]), then the columns items, context i
+// owning [hstart[i], hstart[i + 1]) of those.
 struct Src {
     const unsigned char *tab;
     const int *wstart, *hstart;
@@ -1069,9 +1615,8 @@ __device__ __forceinline__ void chain_body(const Params &P0, const Src src, cons
                 if (!decode(P, side, k, x)) continue;
                 const Side &Sd = P.side[side];
                 if (x.rl) {
-                    // rows item: the owned tile, then the walked tiles (and V
-                    // prefetches); a columns item formed like one reads the
-                    // other orientation's tiles
+                    // rows item: the owned W tile, then the walked H^T tiles
+                    // (and L2 prefetches of the V tiles)
                     if (hphase) {                     // cannot happen: rows items are claimed first
                         atomicOr((int *)&S->abort, 128);
                         goto done0;
@@ -1301,15 +1846,12 @@ __device__ __forceinline__ void chain_body(const Params &P0, const Src src, cons
             const Params &P = item_of<BATCH>(P0, src, it, side, k);
             Item x;
             if (!decode(P, side, k, x) || !x.rl) continue;
-            // every E tile of a rows item (or of a columns item formed like
-            // one) gets this warp's release; only shared E goes to HBM
-            const bool store = side == 0 && P.share;
-            unsigned char *eg = store ? reinterpret_cast<unsigned char *>(
-                P.Et + ((int64_t)x.block * P.side[0].own_tiles + x.ot) * P.et_cols * (kEBytes / 2)) : nullptr;
+            unsigned char *eg = reinterpret_cast<unsigned char *>(
+                P.Et + ((int64_t)x.block * P.side[0].own_tiles + x.ot) * P.et_cols * (kEBytes / 2));
             for (int j = 0; j < x.nj; ++j, ++te) {
                 const uint32_t be = te & 1;
                 if (!wait32(S, &S->e_full[be], (te >> 1) & 1)) goto done3;
-                if (store && lane == 0)
+                if (lane == 0)
                     asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n\t"
                                  "cp.async.bulk.commit_group;\n\t"
                                  "cp.async.bulk.wait_group.read 0;"
@@ -1320,7 +1862,7 @@ __device__ __forceinline__ void chain_body(const Params &P0, const Src src, cons
             }
             // the item's E complete in HBM: count it (release after the
             // async-proxy writes)
-            if (store && lane == 0) {
+            if (lane == 0) {
                 asm volatile("cp.async.bulk.wait_group 0;\n\tfence.proxy.async.global;" ::: "memory");
                 __threadfence();
                 atomicAdd(P.sync + 2 + x.block, 1);
@@ -1655,6 +2197,58 @@ __global__ void build_shadow_kernel(const float *__restrict__ X, int64_t n, int 
     }
 }
 
+using ChainRcFn = void (*)(two_sided_rc::Params);
+
+ChainRcFn pick_chain_rc(bool vb, int pm)
+{
+    static const ChainRcFn f[2][4] = {
+        {two_sided_rc::chain_kernel<float, 0>, two_sided_rc::chain_kernel<float, 1>,
+         two_sided_rc::chain_kernel<float, 2>, two_sided_rc::chain_kernel<float, 3>},
+        {two_sided_rc::chain_kernel<__nv_bfloat16, 0>, two_sided_rc::chain_kernel<__nv_bfloat16, 1>,
+         two_sided_rc::chain_kernel<__nv_bfloat16, 2>, two_sided_rc::chain_kernel<__nv_bfloat16, 3>}};
+    return f[vb ? 1 : 0][pm];
+}
+
+using ChainRcBatchFn = void (*)(const unsigned char *, size_t, const int *, int);
+
+ChainRcBatchFn pick_chain_batch_rc(bool vb, int pm)
+{
+    static const ChainRcBatchFn f[2][4] = {
+        {two_sided_rc::chain_batch_kernel<float, 0>, two_sided_rc::chain_batch_kernel<float, 1>,
+         two_sided_rc::chain_batch_kernel<float, 2>, two_sided_rc::chain_batch_kernel<float, 3>},
+        {two_sided_rc::chain_batch_kernel<__nv_bfloat16, 0>, two_sided_rc::chain_batch_kernel<__nv_bfloat16, 1>,
+         two_sided_rc::chain_batch_kernel<__nv_bfloat16, 2>, two_sided_rc::chain_batch_kernel<__nv_bfloat16, 3>}};
+    return f[vb ? 1 : 0][pm];
+}
+
+size_t rc_bytes(int KP, int vsize, int stages, int vstages)
+{
+    return (size_t)two_sided_rc::kOwn * KP * 2 + 2 * (size_t)two_sided_rc::kOwn * two_sided_rc::kBN * 2 +
+           (size_t)stages * two_sided_rc::kBN * KP * 2 +
+           (size_t)vstages * two_sided_rc::kOwn * two_sided_rc::kBN * vsize + sizeof(two_sided_rc::Bars) + 16 +
+           1024;   // alignment slack
+}
+
+// At least half of an SM's shared memory, so that one CTA (and one 512-column
+// TMEM allocation) runs per SM.
+size_t rc_smem(int KP, int vsize, int stages, int vstages)
+{
+    return std::max<size_t>(rc_bytes(KP, vsize, stages, vstages), 120 * 1024);
+}
+
+// Ring depths: two V slots (they free as soon as the epilogue has read
+// them), then as many walked-factor slots as fit (2 .. 4), then a third V
+// slot if it still fits.
+void rc_stages(int KP, int vsize, int *stages, int *vstages)
+{
+    int s = two_sided_rc::kMaxStages;
+    while (s > 2 && rc_bytes(KP, vsize, s, 2) > 232448) --s;
+    int v = 2;
+    if (rc_bytes(KP, vsize, s, 3) <= 232448) v = 3;
+    *stages = s;
+    *vstages = v;
+}
+
 using ChainFn = void (*)(two_sided::Params);
 
 ChainFn pick_chain(bool vb, int pm)
@@ -1762,9 +2356,12 @@ psgld_status prepare_dense(psgld_ctx *c, cudaStream_t st)
     const int vs = vb ? 2 : 4;
     // the limit is an attribute of the kernel, shared by every context that
     // launches it (any K width): the largest size any of them asks for
-    for (int pm = 0; pm < 4; ++pm)
+    for (int pm = 0; pm < 4; ++pm) {
         PSGLD_CK(c, cudaFuncSetAttribute(pick_chain(vb, pm), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kTwoSidedMax));
+        PSGLD_CK(c, cudaFuncSetAttribute(pick_chain_rc(vb, pm), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kTwoSidedMax));
+    }
     int sms = 0;
     PSGLD_CK(c, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
     c->share_e = two_sided_share(c->opt.dense_share_e, maxI, c->B, c->mt_max, c->nt_max, sms);
@@ -1857,16 +2454,15 @@ static void fill_two_sided(const psgld_ctx *c, int part, two_sided::Params &P)
     A.own_sh = c->Wsh; A.walk_sh = c->Hsh; A.Vt = (const unsigned char *)c->VA; A.G = c->G;
     A.n_own = I; A.n_walk = J; A.own_tiles = c->mt_max; A.walk_tiles = c->nj_max;
     A.own_sh64 = 2 * c->mt_max; A.walk_sh64 = 2 * c->nt_max;
-    Bs.own_sh = c->Hsh; Bs.walk_sh = c->Wsh; Bs.Vt = (const unsigned char *)c->VB; Bs.G = c->G + I * c->ldk;
-    Bs.n_own = J; Bs.n_walk = I; Bs.own_tiles = c->nt_max; Bs.walk_tiles = c->ni_max;
+    Bs.own_sh = nullptr; Bs.walk_sh = c->Wsh; Bs.Vt = nullptr; Bs.G = c->G + I * c->ldk;
+    Bs.n_own = J; Bs.n_walk = I; Bs.own_tiles = c->nt2_max; Bs.walk_tiles = c->ni_max;
     Bs.own_sh64 = 2 * c->nt_max; Bs.walk_sh64 = 2 * c->mt_max;
-    P.share = c->share_e;
     P.Et = c->Et;
     P.sync = c->tsync;
     P.et_cols = 4 * c->nt2_max;
     P.ht1 = c->nt_max;
     P.ht2 = c->nt2_max;
-    P.hwide = c->share_e ? two_sided_hwide(c) : 0;
+    P.hwide = two_sided_hwide(c);
     P.B = c->B;
     P.part = part;
     P.KP = c->KP;
@@ -1883,8 +2479,51 @@ static void fill_two_sided(const psgld_ctx *c, int part, two_sided::Params &P)
     P.err = c->kflag;
 }
 
+// Every item forming its own mu (the two_sided_rc kernel).
+static void fill_rc(const psgld_ctx *c, int part, two_sided_rc::Params &P)
+{
+    P = two_sided_rc::Params{};
+    const int64_t I = c->I, J = c->J;
+    two_sided_rc::Side &A = P.side[0], &Bs = P.side[1];
+    A.own_sh = c->Wsh; A.walk_sh = c->Hsh; A.Vt = (const unsigned char *)c->VA; A.G = c->G;
+    A.n_own = I; A.n_walk = J; A.own_tiles = c->mt_max; A.walk_tiles = c->nj_max;
+    A.own_sh64 = 2 * c->mt_max; A.walk_sh64 = 2 * c->nt_max;
+    Bs.own_sh = c->Hsh; Bs.walk_sh = c->Wsh; Bs.Vt = (const unsigned char *)c->VB; Bs.G = c->G + I * c->ldk;
+    Bs.n_own = J; Bs.n_walk = I; Bs.own_tiles = c->nt_max; Bs.walk_tiles = c->ni_max;
+    Bs.own_sh64 = 2 * c->nt_max; Bs.walk_sh64 = 2 * c->mt_max;
+    P.B = c->B;
+    P.part = part;
+    P.KP = c->KP;
+    P.ldk = c->ldk;
+    const int vs = c->v_bf16 ? 2 : 4;
+    rc_stages(c->KP, vs, &P.stages, &P.vstages);
+    P.items_a = c->B * c->mt_max;
+    P.items = P.items_a + c->B * c->nt_max;
+    P.phi_inv = (float)(1.0 / c->phi);
+    P.p = (float)c->p;
+    P.mu_min = (float)c->opt.mu_min;
+    P.p_mode = c->p == 0.0 ? 0 : c->p == 1.0 ? 1 : c->p == 2.0 ? 2 : 3;
+    P.err = c->kflag;
+}
+
+static psgld_status launch_rc(psgld_ctx *c, int part, cudaStream_t st)
+{
+    two_sided_rc::Params P;
+    fill_rc(c, part, P);
+    const int vs = c->v_bf16 ? 2 : 4;
+    int sms = 0;
+    PSGLD_CK(c, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
+    int grid = std::min(P.items, sms);
+    if (c->opt.max_sms > 0) grid = std::min(grid, c->opt.max_sms);   // leave SMs to other work
+    const size_t smem = rc_smem(c->KP, vs, P.stages, P.vstages);
+    pick_chain_rc(c->v_bf16 != 0, P.p_mode)<<<grid, two_sided_rc::kThreads, smem, st>>>(P);
+    PSGLD_CK(c, cudaGetLastError());
+    return PSGLD_OK;
+}
+
 static psgld_status launch_two_sided(psgld_ctx *c, int part, cudaStream_t st)
 {
+    if (!c->share_e) return launch_rc(c, part, st);
     two_sided::Params P;
     fill_two_sided(c, part, P);
     int sms = 0;
@@ -1935,31 +2574,38 @@ psgld_status launch_dense_grad(psgld_ctx *c, int part, cudaStream_t st)
 }
 
 // Batch keys: single-pass 2 KP + fp8 (< 4096); two-sided 4096 + 8 KP +
-// 4 v_bf16 + power mode (the chain kernel's template arguments).
+// 4 v_bf16 + power mode (the chain kernel's template arguments), plus 8192
+// for the shared-E kernel.
 int dense_batch_key(const psgld_ctx *c)
 {
     if (c->dense_kind == 1) return 2 * dense_kp(c->K) + c->dense_fp8;
     if (c->dense_kind == 2) {
         const int pm = c->p == 0.0 ? 0 : c->p == 1.0 ? 1 : c->p == 2.0 ? 2 : 3;
-        return 4096 + 8 * c->KP + 4 * c->v_bf16 + pm;
+        return 4096 + 8 * c->KP + 4 * c->v_bf16 + pm + (c->share_e ? 8192 : 0);
     }
     return 0;
 }
 
 size_t dense_param_bytes()
 {
-    const size_t m = std::max(sizeof(DenseParams), sizeof(two_sided::Params));
+    const size_t m = std::max({sizeof(DenseParams), sizeof(two_sided::Params), sizeof(two_sided_rc::Params)});
     return (m + 15) & ~size_t(15);
 }
 
 int fill_dense_param(const psgld_ctx *c, int part, void *dst, int *first_items)
 {
+    if (c->dense_kind == 2 && !c->share_e) {
+        two_sided_rc::Params P;
+        fill_rc(c, part, P);
+        std::memcpy(dst, &P, sizeof P);
+        *first_items = P.items;
+        return P.items;
+    }
     if (c->dense_kind == 2) {
         two_sided::Params P;
         fill_two_sided(c, part, P);
         std::memcpy(dst, &P, sizeof P);
-        // rows items first; columns items formed like them go with them
-        *first_items = P.share ? P.items_a : P.items;
+        *first_items = P.items_a;   // the rows items, then the columns items
         return P.items;
     }
     DenseParams P;
@@ -1974,9 +2620,30 @@ psgld_status launch_dense_batch(psgld_ctx *c0, int key, const void *params, cons
 {
     const unsigned char *tab = static_cast<const unsigned char *>(params);
     const size_t stride = dense_param_bytes();
-    if (key >= 4096) {
-        // two-sided contexts: one persistent launch over all their items
+    if (key >= 4096 && key < 8192) {
+        // two-sided contexts whose items form their own mu: one persistent
+        // launch over all their items, round robin (cta_start: their prefix)
         const int KP = (key - 4096) / 8;
+        const bool vb = ((key >> 2) & 1) != 0;
+        const int pm = key & 3;
+        const int vs = vb ? 2 : 4;
+        int stages = 0, vstages = 0;
+        rc_stages(KP, vs, &stages, &vstages);
+        const size_t smem = rc_smem(KP, vs, stages, vstages);
+        ChainRcBatchFn fn = pick_chain_batch_rc(vb, pm);
+        PSGLD_CK(c0, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTwoSidedMax));
+        int sms = 0;
+        PSGLD_CK(c0, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c0->device));
+        int grid = std::min(total, sms);
+        if (c0->opt.batch_ctas > 0) grid = std::min(grid, (int)c0->opt.batch_ctas);
+        if (grid > 0) fn<<<grid, two_sided_rc::kThreads, smem, st>>>(tab, stride, cta_start, n);
+        PSGLD_CK(c0, cudaGetLastError());
+        return PSGLD_OK;
+    }
+    if (key >= 8192) {
+        // two-sided contexts with shared E: one persistent launch over all
+        // their items, claimed in order (rows items of every context first)
+        const int KP = (key - 8192 - 4096) / 8;
         const bool vb = ((key >> 2) & 1) != 0;
         const int pm = key & 3;
         const size_t smem = two_sided_smem(KP, two_sided_stages(KP));

@@ -56,6 +56,7 @@ class Job:
     dense_path: int = 1
     dense_v_bf16: int = 0
     max_sms: int = 0                   # > 0: SMs the two-sided kernel may hold (standing chains)
+    dense_share_e: int = -1            # the two-sided kernel's mode (-1: the library's rule)
     arrival: float = 0.0               # seconds from the start of the trace
     data_seed: int = 0
     # filled in by the server
@@ -254,7 +255,8 @@ class GpuExecutor:
                                prior_kind=self.P.PSGLD_PRIOR_EXPONENTIAL, lambda_w=job.lam,
                                lambda_h=job.lam, seed=job.seed, eps=job.eps, use_graphs=1,
                                burn_in_sweeps=job.burn_in, dense_path=job.dense_path,
-                               dense_v_bf16=job.dense_v_bf16, max_sms=job.max_sms)
+                               dense_v_bf16=job.dense_v_bf16, max_sms=job.max_sms,
+                               dense_share_e=job.dense_share_e)
             ctx.set_data_dense(V, stream.cuda_stream)
             ctx.set_factors(W0, Ht0, stream.cuda_stream)
             del V, W0, Ht0

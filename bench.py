@@ -897,7 +897,8 @@ def batched_other_kernel(wl, specs, dev, stream, flush, steps: int):
 
     from paper_1506_01418_gb300 import psgld as P
     dp = 2 if wl.get("dense_path", 1) != 2 else 3
-    made = batched_make(wl, specs, dev, dense_path=dp)
+    # the single-pass kernel reads V in FP32
+    made = batched_make(wl, specs, dev, dense_path=dp, dense_v_bf16=wl.get("dense_v_bf16", 0) if dp == 2 else 0)
     chains = [m[0] for m in made]
     for ch, V, W0, Ht0 in made:
         ch.set_data_dense(V)

@@ -15,21 +15,17 @@
 // gradient of Sec. 4 (d/dmu of -d_beta(v||mu)/phi with beta = 2 - p).
 //
 // Kernel 1, gradient.  Both sums read only the previous factors, so the W
-// side (rows of the part's CSR) and the H side (rows of H^T: the part's CSC)
-// run as the two halves of one grid and write G = sum e h (resp. sum e w) for
-// every row.  A sub-team of S lanes owns a row (S lanes x NG float4 groups
-// cover the K factor columns): it loads its row and the row's entries
-// (coalesced), gathers the other factor's rows with read-only float4 loads,
-// reduces mu across the sub-team with butterfly shuffles, applies the Tweedie
-// epilogue and accumulates the gradient in registers -- SDDMM, epilogue and
-// SpMM in one pass, e never leaves registers.  The part's light rows (at most
-// light_len entries) come in a list ordered by entry count, so a warp's rows
-// take equally long.  Heavier rows are cut into chunks of at most chunk_len
-// entries taken by whole warps (all sub-teams of the warp on different
-// entries of the same row), scheduled before the light rows.  A row cut into several chunks publishes partial sums to a small
-// scratch area and the last chunk to arrive (an arrival counter) adds them in
-// chunk order, so the result does not depend on scheduling.
-//
+// side (the part's entries in row order) and the H side (in column order)
+// run in one grid and write G = sum e h (resp. sum e w) for every row.  The
+// entries are cut into units of E consecutive entries, one warp per unit:
+// the unit's other-factor rows are gathered into shared memory by bulk
+// copies, mu and the Tweedie factor are formed one lane per entry, and the
+// gradient is summed by row segments of the unit -- SDDMM, epilogue and SpMM
+// in one pass, e never leaves the SM.  A row whose entries span several
+// units publishes the sums of its first and last pieces to per-unit head and
+// tail slots, which the update kernel adds in unit order, so the result does
+// not depend on scheduling (details at the kernel).
+
 // On dense data kept for the tensor cores (dense_path), kernel 1 is the block
 // GEMM -> epilogue -> GEMM chain of psgld_dense.cu instead; kernel 2 is the
 // same.
@@ -67,6 +63,7 @@ struct GradSide {
     int64_t n;             // entries of the part
     int64_t units;         // ceil(n / E)
     const uint16_t *Y16;   // BF16 copy of the other factor (rows of ld16), gathered instead of Y_cur
+    int prefetch_own;      // 1: own rows go to L2 with the gathers (own factor beyond L2)
 };
 
 struct GradParams {
@@ -173,17 +170,22 @@ __device__ __forceinline__ float tweedie_e(const GradParams &P, float v, float m
 // ---- kernel 1: the likelihood gradient ------------------------------------
 //
 // A unit is E consecutive entries of the part in this side's order (rows in
-// order, the other index ascending), one unit per warp.  Steps:
-//   1. lane l loads entry l of the unit: own row, other index j, value v;
+// order, the other index ascending), one unit per warp at a time.  Steps:
+//   1. lane l holds entry l of the unit: own row, other index j, value v
+//      (loaded while the warp worked on its previous unit);
 //   2. TMA bulk copies (cp.async.bulk, one instruction per factor row) bring
 //      the E gathered rows Y[j] into the warp's shared memory, completing on
 //      the warp's mbarrier, so every gather of the unit is in flight at once;
+//      meanwhile each row segment's own row X[own] is prefetched into L2
+//      (when that factor exceeds L2) and each lane starts loading its own
+//      row's first float4 groups;
 //   3. SDDMM + epilogue, one lane per entry: mu = X[own] . Y[j], e = Tweedie
 //      factor (X rows read through L1; lanes of one row share the lines);
-//   4. SpMM by row segments of the unit, sub-teams of S lanes over the K
-//      columns: G[row] = sum_l e_l Y[j_l] over the segment.  A unit holding
-//      one row splits its entries over the sub-teams and adds their sums; a
-//      unit holding several rows gives each sub-team whole segments;
+//   4. SpMM by row segments of the unit (their starts tabulated in shared
+//      memory), sub-teams of S lanes over the K columns: G[row] = sum_l e_l
+//      Y[j_l] over the segment.  A unit holding one row splits its entries
+//      over the sub-teams and adds their sums; a unit holding several rows
+//      gives each sub-team whole segments;
 //   5. a segment whose row also has entries before the unit goes to the
 //      unit's head slot, one whose row continues after it to the tail slot,
 //      any other straight to G.  The update kernel adds a row's tail and head
@@ -242,6 +244,12 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
                  :: "r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar)) : "memory");
 }
 
+// Bulk prefetch of `bytes` (a multiple of 16, 16-byte aligned) into L2.
+__device__ __forceinline__ void prefetch_l2(const void *src, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" :: "l"(src), "r"(bytes) : "memory");
+}
+
 // Four gathered entries (q-th float4 group) of row `row` of the warp's
 // gathered rows: FP32 rows of lds floats, or (BF) BF16 rows of lds16.
 template <bool BF>
@@ -257,44 +265,63 @@ __device__ __forceinline__ float4 ys4(const float *ys, int row, int q, int lds, 
     }
 }
 
+// A unit's entries as each lane loads them, one unit ahead of its work:
+// lane l entry l (own row, other index, value); `edge` is, on lane 0, the
+// own row of the entry just before the unit and, on lane 1, of the entry
+// just after it (-1: none).
+struct UnitIn {
+    int own, jj;
+    float vv;
+    int edge;
+};
+
+template <int SID, int E>
+__device__ __forceinline__ UnitIn load_unit(const GradParams &P, int64_t u)
+{
+    const GradSide &Sd = P.side[SID];
+    const int lane32 = threadIdx.x & 31;
+    const int64_t e0 = Sd.base + u * E, rem = Sd.n - u * E;
+    UnitIn r{-1, 0, 0.f, -1};
+    if (lane32 < E && lane32 < rem) {
+        r.own = __ldg(Sd.own + e0 + lane32);
+        r.jj = __ldg(Sd.idx + e0 + lane32);
+        r.vv = __ldg(Sd.val + e0 + lane32);
+    }
+    if (lane32 == 0 && u > 0) r.edge = __ldg(Sd.own + e0 - 1);
+    if (lane32 == 1 && rem > E) r.edge = __ldg(Sd.own + e0 + E);
+    return r;
+}
+
 // One unit (E consecutive entries of side SID's part order) on one warp; SID
 // is a template parameter so that the side's fields are fixed parameter
 // offsets.  BF: the gathered rows are the BF16 copies (half the bytes;
-// products and sums stay FP32).
+// products and sums stay FP32).  `bar` completes once per unit, phase
+// `parity`.  False when the gathers did not land in time (the warp stops).
 template <int SID, int S, int NG, int E, bool BF>
-__device__ __forceinline__ void grad_unit(const GradParams &P, int64_t u, float *ys, float *es, int *ow,
-                                          uint64_t *bar)
+__device__ __forceinline__ bool grad_unit(const GradParams &P, int64_t u, const UnitIn &in, float *ys,
+                                          float *es, int *ow, int *sg, uint64_t *bar, uint32_t parity)
 {
     constexpr int R = 32 / S;      // sub-teams per warp
     constexpr int NGP = S * NG;    // float4 groups a sub-team covers (>= ngroups)
     const int lane32 = threadIdx.x & 31;
     const int ng = P.ngroups, ldk = P.ldk, lds = P.lds;
     const GradSide &Sd = P.side[SID];
-    const int64_t e0 = Sd.base + u * E;
     const int n = (int)(Sd.n - u * E < E ? Sd.n - u * E : E);
 
-    // ---- 1. this lane's entry
+    // ---- 1. this lane's entry (loaded with the previous unit)
     const bool valid = lane32 < n;
-    int own = -1, jj = 0;
-    float vv = 0.f;
-    if (valid) {
-        own = __ldg(Sd.own + e0 + lane32);
-        jj = __ldg(Sd.idx + e0 + lane32);
-        vv = __ldg(Sd.val + e0 + lane32);
-    }
-    int prev_own = -1, next_own = -1;   // rows of the entries just outside the unit
-    if (lane32 == 0 && u > 0) prev_own = __ldg(Sd.own + e0 - 1);
-    if (lane32 == 1 && u * E + E < Sd.n) next_own = __ldg(Sd.own + e0 + E);
-    prev_own = __shfl_sync(0xffffffffu, prev_own, 0);
-    next_own = __shfl_sync(0xffffffffu, next_own, 1);
+    const int own = in.own, jj = in.jj;
+    const float vv = in.vv;
+    const int prev_own = __shfl_sync(0xffffffffu, in.edge, 0);   // rows of the entries just outside the unit
+    const int next_own = __shfl_sync(0xffffffffu, in.edge, 1);
     const int lds16 = P.lds16;
     const uint32_t row_bytes = BF ? (uint32_t)P.ld16 * 2u : (uint32_t)ldk * 4u;
 
-    // ---- 2. bulk gathers into shared memory
-    if (lane32 == 0) {
-        mbar_init(bar);
-        mbar_expect_tx(bar, (uint32_t)n * row_bytes);
-    }
+    // ---- 2. bulk gathers into shared memory, once every lane is done with
+    // the previous unit's (its reads ordered before the copies' writes)
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncwarp();
+    if (lane32 == 0) mbar_expect_tx(bar, (uint32_t)n * row_bytes);
     __syncwarp();
     if (valid) {
         if constexpr (BF)
@@ -303,14 +330,25 @@ __device__ __forceinline__ void grad_unit(const GradParams &P, int64_t u, float 
         else
             bulk_g2s(ys + (size_t)lane32 * lds, Sd.Y_cur + (int64_t)jj * ldk, row_bytes, bar);
     }
+    // each row segment's own row on its way to L2 while the gathers land
+    const int own_prev_lane = __shfl_up_sync(0xffffffffu, own, 1);
+    const bool seg_start = valid && (lane32 == 0 || own != own_prev_lane);
+    if (seg_start && Sd.prefetch_own) prefetch_l2(Sd.X_cur + (int64_t)own * ldk, (uint32_t)ldk * 4u);
+    // the first XP float4 groups of this lane's own row, loaded before the
+    // wait (the rest after it, in the mu loop)
+    constexpr int XP = NGP < 8 ? NGP : 8;
+    float4 xp[XP];
+    const float *xrow = Sd.X_cur + (int64_t)(valid ? own : 0) * ldk;
+#pragma unroll
+    for (int w = 0; w < XP; ++w) xp[w] = (valid && w < ng) ? ldg4(xrow + 4 * w) : zero4();
     bool done = false;
     const long long t_start = clock64();
     if (P.wait_polls) {
         // a test limit: at most wait_polls polls, without suspending
-        for (uint32_t it = 0; it < P.wait_polls && !done; ++it) done = mbar_test_wait(bar, 0);
+        for (uint32_t it = 0; it < P.wait_polls && !done; ++it) done = mbar_test_wait(bar, parity);
     } else {
         for (uint32_t it = 0; it < kWaitLimit && !done && clock64() - t_start < kWaitCycles; ++it)
-            done = mbar_try_wait(bar, 0, kWaitHintNs);
+            done = mbar_try_wait(bar, parity, kWaitHintNs);
     }
     if (!__all_sync(0xffffffffu, done)) {
         // The copies did not land: report it, wait (bounded again) for them
@@ -318,8 +356,8 @@ __device__ __forceinline__ void grad_unit(const GradParams &P, int64_t u, float 
         if (lane32 == 0) atomicOr(P.err, 16);
         const long long t_again = clock64();
         for (uint32_t it = 0; it < kWaitLimit && !done && clock64() - t_again < kWaitCycles; ++it)
-            done = mbar_try_wait(bar, 0, kWaitHintNs);
-        return;
+            done = mbar_try_wait(bar, parity, kWaitHintNs);
+        return false;
     }
 
     // ---- 3. mu and the Tweedie factor, one lane per entry
@@ -329,15 +367,17 @@ __device__ __forceinline__ void grad_unit(const GradParams &P, int64_t u, float 
         float d = 0.f;
 #pragma unroll
         for (int q = 0; q < NGP; ++q)
-            if (q < ng) d = dot4(ldg4(x + 4 * q), ys4<BF>(ys, lane32, q, lds, lds16), d);
+            if (q < ng) d = dot4(q < XP ? xp[q < XP ? q : 0] : ldg4(x + 4 * q), ys4<BF>(ys, lane32, q, lds, lds16), d);
         e = tweedie_e(P, vv, d);
     }
-    const int own_prev_lane = __shfl_up_sync(0xffffffffu, own, 1);
-    const unsigned smask = __ballot_sync(0xffffffffu, valid && (lane32 == 0 || own != own_prev_lane));
+    const unsigned smask = __ballot_sync(0xffffffffu, seg_start);
     if (lane32 < E) {
         es[lane32] = e;
         ow[lane32] = own;
     }
+    // sg[k]: the unit's entry that starts row segment k; sg[nseg] = n
+    if (seg_start) sg[__popc(smask & ((1u << lane32) - 1u))] = lane32;
+    if (lane32 == 0) sg[__popc(smask)] = n;
     __syncwarp();
 
     // ---- 4./5. gradient sums per row segment
@@ -348,6 +388,7 @@ __device__ __forceinline__ void grad_unit(const GradParams &P, int64_t u, float 
         // one row: sub-team s takes entries s, s+R, ...; then add the sub-teams
 #pragma unroll
         for (int g = 0; g < NG; ++g) acc[g] = zero4();
+#pragma unroll 4
         for (int sl = sub; sl < n; sl += R) {
             const float es_ = es[sl];
 #pragma unroll
@@ -379,11 +420,11 @@ __device__ __forceinline__ void grad_unit(const GradParams &P, int64_t u, float 
     } else {
         // several rows: sub-team s takes segments s, s+R, ...
         for (int k = sub; k < nseg; k += R) {
-            const int st = (int)__fns(smask, 0, k + 1);
-            const int en = k + 1 < nseg ? (int)__fns(smask, 0, k + 2) : n;
+            const int st = sg[k], en = sg[k + 1];
             const int row = ow[st];
 #pragma unroll
             for (int g = 0; g < NG; ++g) acc[g] = zero4();
+#pragma unroll 4
             for (int sl = st; sl < en; ++sl) {
                 const float es_ = es[sl];
 #pragma unroll
@@ -402,8 +443,13 @@ __device__ __forceinline__ void grad_unit(const GradParams &P, int64_t u, float 
             }
         }
     }
+    return true;
 }
 
+// Each warp takes units u, u + T, u + 2T, ... (T = warps of the grid: a
+// grid of one CTA per 4 units gives every warp one unit; a smaller grid
+// keeps warps resident over several), loading the next unit's entries
+// before working on the current one.
 template <int S, int NG, int E, bool BF>
 __global__ void __launch_bounds__(kGradThreads) grad_kernel(const __grid_constant__ GradParams P)
 {
@@ -415,14 +461,24 @@ __global__ void __launch_bounds__(kGradThreads) grad_kernel(const __grid_constan
     float *ys = base + (size_t)warp * E * lds;                      // E gathered rows
     float *es = base + (size_t)kWarpsPerCta * E * lds + warp * E;   // e of each entry
     int *ow = reinterpret_cast<int *>(base + (size_t)kWarpsPerCta * E * lds + kWarpsPerCta * E) + warp * E;
-    uint64_t *bar = reinterpret_cast<uint64_t *>(base + (size_t)kWarpsPerCta * (E * lds + 2 * E)) + warp;
+    int *sg = reinterpret_cast<int *>(base + (size_t)kWarpsPerCta * (E * lds + 2 * E)) + warp * (E + 1);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(base + (size_t)kWarpsPerCta * (E * lds + 3 * E + 1)) + warp;
 
+    const int64_t U0 = P.side[0].units, U = U0 + P.side[1].units;
+    const int64_t T = (int64_t)gridDim.x * kWarpsPerCta;
     int64_t u = (int64_t)blockIdx.x * kWarpsPerCta + warp;
-    if (u < P.side[0].units) {
-        grad_unit<0, S, NG, E, BF>(P, u, ys, es, ow, bar);
-    } else {
-        u -= P.side[0].units;
-        if (u < P.side[1].units) grad_unit<1, S, NG, E, BF>(P, u, ys, es, ow, bar);   // warp-uniform
+    if (u >= U) return;   // warp-uniform
+    if ((threadIdx.x & 31) == 0) mbar_init(bar);
+    __syncwarp();
+    UnitIn cur = u < U0 ? load_unit<0, E>(P, u) : load_unit<1, E>(P, u - U0);
+    for (uint32_t parity = 0; u < U; u += T, parity ^= 1u) {
+        const int64_t nu = u + T;
+        UnitIn nxt{-1, 0, 0.f, -1};
+        if (nu < U) nxt = nu < U0 ? load_unit<0, E>(P, nu) : load_unit<1, E>(P, nu - U0);
+        const bool ok = u < U0 ? grad_unit<0, S, NG, E, BF>(P, u, cur, ys, es, ow, sg, bar, parity)
+                               : grad_unit<1, S, NG, E, BF>(P, u - U0, cur, ys, es, ow, sg, bar, parity);
+        if (!ok) return;
+        cur = nxt;
     }
 }
 
@@ -674,7 +730,7 @@ int lds16_for(int ldk)
 size_t grad_smem(const Shape &sh)
 {
     const int warps = kGradThreads / 32;
-    return sizeof(float) * (size_t)warps * ((size_t)sh.E * sh.lds + 2 * sh.E) +
+    return sizeof(float) * (size_t)warps * ((size_t)sh.E * sh.lds + 3 * sh.E + 1) +
            sizeof(uint64_t) * warps;
 }
 
@@ -722,6 +778,35 @@ psgld_status build_gather_shadows(psgld_ctx *c, cudaStream_t st)
 
 int unit_entries(int ngroups) { return shape_for(ngroups).E; }
 
+// CTAs of kernel `f` (`threads` threads, `smem` bytes of dynamic shared
+// memory each) resident at once on the current device: SMs x CTAs per SM,
+// remembered per host thread for the last two kernels asked about (the
+// gradient kernels of one context, FP32 and BF16 gathers).
+static int64_t resident_wave(const void *f, int threads, size_t smem)
+{
+    struct Entry {
+        const void *f;
+        int threads;
+        size_t smem;
+        int dev;
+        int64_t wave;
+    };
+    thread_local Entry memo[2] = {{nullptr, 0, 0, -1, 0}, {nullptr, 0, 0, -1, 0}};
+    thread_local int next = 0;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1ll << 40;
+    for (const Entry &e : memo)
+        if (e.f == f && e.threads == threads && e.smem == smem && e.dev == dev) return e.wave;
+    int sms = 0, per_sm = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, threads, smem) != cudaSuccess ||
+        sms <= 0 || per_sm <= 0)
+        return 1ll << 40;   // unknown: no cap
+    memo[next] = {f, threads, smem, dev, (int64_t)sms * per_sm};
+    next ^= 1;
+    return (int64_t)sms * per_sm;
+}
+
 psgld_status prepare_kernels(psgld_ctx *c)
 {
     const Shape sh = shape_for(c->ngroups);
@@ -767,6 +852,7 @@ static void fill_params(psgld_ctx *c, int part, int64_t t, const int64_t *t_dev,
         Gs.n = n;
         Gs.units = upd[s] ? (n + sh.E - 1) / sh.E : 0;
         Gs.Y16 = gather_bf16(c) ? (s == 0 ? c->H16 : c->W16) : nullptr;
+        Gs.prefetch_own = 4.0 * (double)n_rows * c->ldk > 64.0 * (1 << 20);
 
         Us.X_cur = X_cur;
         Us.X_next = X_next;
@@ -882,10 +968,14 @@ psgld_status launch_part_step(psgld_ctx *c, int64_t t, const int64_t *t_dev, int
         if (small) update_kernel32<<<grid, kThreads, 0, ss>>>(U);
         else update_kernel<<<grid, kThreads, 0, ss>>>(U);
     };
-    auto gradient = [&](const GradParams &G, cudaStream_t ss) {
+    // resident: one wave of CTAs whose warps walk several units each (the
+    // next unit's entries load during the current one); otherwise one unit
+    // per warp, so that two launches on two streams share the SMs
+    auto gradient = [&](const GradParams &G, cudaStream_t ss, bool resident) {
         const int64_t n = G.side[0].units + G.side[1].units;
-        const int grid = (int)((n + kGradThreads / 32 - 1) / (kGradThreads / 32));
-        if (grid > 0) gfn<<<grid, kGradThreads, grad_smem(sh), ss>>>(G);
+        int64_t grid = (n + kGradThreads / 32 - 1) / (kGradThreads / 32);
+        if (resident) grid = std::min<int64_t>(grid, resident_wave((const void *)gfn, kGradThreads, grad_smem(sh)));
+        if (grid > 0) gfn<<<(int)grid, kGradThreads, grad_smem(sh), ss>>>(G);
     };
     // W and H^T on two streams when the factors fit in L2 (W and H^T at most
     // 64 MB): each side's gradient, then its update; their outputs are
@@ -908,9 +998,9 @@ psgld_status launch_part_step(psgld_ctx *c, int64_t t, const int64_t *t_dev, int
         UH.side[0].items = 0;
         PSGLD_CK(c, cudaEventRecord(c->ev_fork, st));
         PSGLD_CK(c, cudaStreamWaitEvent(c->side_stream, c->ev_fork, 0));
-        gradient(GH, c->side_stream);
+        gradient(GH, c->side_stream, false);
         update(UH, c->side_stream);
-        gradient(GW, st);
+        gradient(GW, st, false);
         update(UW, st);
         PSGLD_CK(c, cudaGetLastError());
         PSGLD_CK(c, cudaEventRecord(c->ev_join, c->side_stream));
@@ -922,7 +1012,7 @@ psgld_status launch_part_step(psgld_ctx *c, int64_t t, const int64_t *t_dev, int
                 if (ds != PSGLD_OK) return ds;
             }
         } else if (ggrid > 0) {
-            gradient(GP, st);
+            gradient(GP, st, true);
         }
         PSGLD_CK(c, cudaGetLastError());
         if (prof) PSGLD_CK(c, cudaEventRecordWithFlags(c->ev_mid[part], st, rec_flags));

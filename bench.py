@@ -57,6 +57,13 @@ WORKLOADS = {
         I=480000, J=18000, nnz=100_000_000, K=100, B=64, p=0.0, phi=1.0, prior="gaussian",
         sigma=1.0, K_true=20, zipf_row=1.2, zipf_col=None, eps=5e-6, init_scale=0.25,
         job_sweeps=200, bf16_compare=True),
+    # the large sparse workload's recipe at 3 * 10^7 entries: W (192 MB)
+    # still beyond L2, about 4 GB on the device -- the size of an ncu
+    # capture of its kernels
+    "sparse_gauss_480000x18000_nnz30M_K100_B64": dict(
+        I=480000, J=18000, nnz=30_000_000, K=100, B=64, p=0.0, phi=1.0, prior="gaussian",
+        sigma=1.0, K_true=20, zipf_row=1.2, zipf_col=None, eps=5e-6, init_scale=0.25,
+        job_sweeps=200),
     "dense_poisson_256x256_K8_B4": dict(
         I=256, J=256, nnz=256 * 256, K=8, B=4, p=1.0, phi=1.0, prior="exponential",
         lam=1.0, K_true=8, eps=1e-4, init_scale=1.0, job_sweeps=1000, dense=True),

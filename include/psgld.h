@@ -143,8 +143,9 @@ typedef struct {
                                * polls or about one second of SM clock).  > 0: the
                                * sparse gradient kernel's first wait for its row
                                * gathers makes at most this many polls, without
-                               * suspending, before it gives up -- a wait that runs
-                               * out on purpose: the kernel sets the context's error
+                               * suspending and before it issues the copies, then
+                               * gives up -- a wait that surely runs out, on
+                               * purpose: the kernel sets the context's error
                                * flag, waits for its own copies with the normal
                                * limit, and the next synchronising call returns
                                * PSGLD_ERR_TIMEOUT naming the kernel and the wait.

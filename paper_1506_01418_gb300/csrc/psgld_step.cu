@@ -323,6 +323,12 @@ __device__ __forceinline__ bool grad_unit(const GradParams &P, int64_t u, const 
     __syncwarp();
     if (lane32 == 0) mbar_expect_tx(bar, (uint32_t)n * row_bytes);
     __syncwarp();
+    bool done = false;
+    if (P.wait_polls) {
+        // a test limit: at most wait_polls polls, without suspending, made
+        // before the copies are issued -- so the wait surely runs out
+        for (uint32_t it = 0; it < P.wait_polls && !done; ++it) done = mbar_test_wait(bar, parity);
+    }
     if (valid) {
         if constexpr (BF)
             bulk_g2s(reinterpret_cast<uint16_t *>(ys) + (size_t)lane32 * lds16, Sd.Y16 + (int64_t)jj * P.ld16,
@@ -341,12 +347,8 @@ __device__ __forceinline__ bool grad_unit(const GradParams &P, int64_t u, const 
     const float *xrow = Sd.X_cur + (int64_t)(valid ? own : 0) * ldk;
 #pragma unroll
     for (int w = 0; w < XP; ++w) xp[w] = (valid && w < ng) ? ldg4(xrow + 4 * w) : zero4();
-    bool done = false;
     const long long t_start = clock64();
-    if (P.wait_polls) {
-        // a test limit: at most wait_polls polls, without suspending
-        for (uint32_t it = 0; it < P.wait_polls && !done; ++it) done = mbar_test_wait(bar, parity);
-    } else {
+    if (!P.wait_polls) {
         for (uint32_t it = 0; it < kWaitLimit && !done && clock64() - t_start < kWaitCycles; ++it)
             done = mbar_try_wait(bar, parity, kWaitHintNs);
     }

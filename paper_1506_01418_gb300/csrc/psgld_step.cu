@@ -985,11 +985,14 @@ psgld_status launch_part_step(psgld_ctx *c, int64_t t, const int64_t *t_dev, int
     // factors), so the result is the same bit for bit, and the ALU-bound
     // update of one side overlaps the L2-bound gathers of the other (10 M
     // entries, K = 50: 1.58 to 1.50 ms per sweep).  With factors beyond L2
-    // the concurrent update's DRAM traffic slows the gathers' misses instead
-    // (10^8 entries, K = 100: 27.2 to 27.8 ms), so one stream.  Not with
-    // gather_bf16: the BF16 copies that the gathers read are single-buffered
-    // and rewritten by the updates.  Inside a capture the fork and join
-    // become graph edges.
+    // the W side's gradient runs alone on the full (resident) grid first,
+    // then the H side's gradient and the W side's update run side by side:
+    // the latency-bound gathers leave issue slots that the ALU-bound update
+    // fills (10^8 entries, K = 100: 21.4 to 19.9 ms per sweep; the earlier
+    // order, both gradients at once and the updates after them, had been
+    // slower than one stream).  Not with gather_bf16: the BF16 copies that
+    // the gathers read are single-buffered and rewritten by the updates.
+    // Inside a capture the fork and join become graph edges.
     const bool l2_fit = 4.0 * (double)(c->I + c->J) * c->ldk <= 64.0 * (1 << 20);
     if (!dense && !prof && !gather_bf16(c) && l2_fit && c->side_stream && upd[0] && upd[1]) {
         GradParams GW = GP, GH = GP;
@@ -1003,6 +1006,22 @@ psgld_status launch_part_step(psgld_ctx *c, int64_t t, const int64_t *t_dev, int
         gradient(GH, c->side_stream, false);
         update(UH, c->side_stream);
         gradient(GW, st, false);
+        update(UW, st);
+        PSGLD_CK(c, cudaGetLastError());
+        PSGLD_CK(c, cudaEventRecord(c->ev_join, c->side_stream));
+        PSGLD_CK(c, cudaStreamWaitEvent(st, c->ev_join, 0));
+    } else if (!dense && !prof && !gather_bf16(c) && c->side_stream && upd[0] && upd[1] && ggrid > 0) {
+        GradParams GW = GP, GH = GP;
+        GW.side[1].units = 0;
+        GH.side[0].units = 0;
+        UpdParams UW = UP, UH = UP;
+        UW.side[1].items = 0;
+        UH.side[0].items = 0;
+        gradient(GW, st, true);
+        PSGLD_CK(c, cudaEventRecord(c->ev_fork, st));
+        PSGLD_CK(c, cudaStreamWaitEvent(c->side_stream, c->ev_fork, 0));
+        gradient(GH, c->side_stream, true);   // enqueued ahead of the W update
+        update(UH, c->side_stream);
         update(UW, st);
         PSGLD_CK(c, cudaGetLastError());
         PSGLD_CK(c, cudaEventRecord(c->ev_join, c->side_stream));

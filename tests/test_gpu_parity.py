@@ -9,6 +9,8 @@
   both priors, ragged piece sizes, rows split over many work units, empty
   parts, frozen factors, mu below mu_min (zero and tiny rows and columns)
   and the decaying step size eps_t = (a/t)^b;
+* factors beyond L2 (the large sparse workload's two-stream order) within
+  the same step tolerance;
 * graph replay == direct launches, bit for bit;
 * log-likelihood, RMSE and posterior moments against the oracle.
 """
@@ -244,6 +246,38 @@ def test_graph_replay_equals_direct_launches(name):
     for x, y in zip(ma[:4], mb[:4]):
         assert np.array_equal(x, y)
     assert a.gpu.iterations_done == 4 * a.B
+
+
+def test_factors_beyond_l2_take_the_two_stream_order_and_match_oracle():
+    """Factors above 64 MB (W: 180000 x 100 FP32, 72 MB) take the large
+    sparse workload's order: W's gradient alone on the resident grid, then
+    H's gradient on a second stream beside W's update.  Two part-steps
+    match the oracle within the step tolerance, and a captured-graph sweep
+    equals direct launches bit for bit."""
+    I, J, K, B = 180000, 2000, 100, 8
+    i, j, v = sparse_case(I, J, 1_500_000, 8, seed=17, zipf=1.2)
+    W0, H0 = datagen.init_factors(I, J, K, seed=5, scale=0.25, nonneg=False)
+    pr = Pair(I, J, K, B, 0.0, 1.0, i, j, v, W0, H0, prior_kind=1, sig=(0.9, 1.1), seed=13,
+              eps=1e-4)
+    for t in (1, 2):
+        pr.step_and_check(t)
+        pr.sync_oracle_to_gpu()
+    pr.gpu.close()
+    chains = []
+    for graphs in (1, 0):
+        c = P.PSGLD(I, J, K, B, 0.0, 1.0, prior_kind=1, seed=13, eps=1e-4, use_graphs=graphs)
+        c.set_data_coo(torch.as_tensor(i, dtype=torch.int32, device="cuda"),
+                       torch.as_tensor(j, dtype=torch.int32, device="cuda"),
+                       torch.as_tensor(v, dtype=torch.float32, device="cuda"))
+        c.set_factors(torch.as_tensor(np.ascontiguousarray(W0, dtype=np.float32), device="cuda"),
+                      torch.as_tensor(np.ascontiguousarray(H0.T, dtype=np.float32), device="cuda"))
+        c.sweep(1)
+        c.sweep(1)
+        chains.append(c)
+    (Wa, Ha), (Wb, Hb) = (c.get_factors() for c in chains)
+    assert torch.equal(Wa, Wb) and torch.equal(Ha, Hb)
+    for c in chains:
+        c.close()
 
 
 def test_sweep_matches_oracle_chain():

@@ -550,7 +550,10 @@ def run_ours(args, wl_name, wl):
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "roofline": roofline,
         # per sweep: B x (gradient + update) + 2 accumulate + advance t + set t
-        "gpu_launches": args.steps * (2 * wl["B"] + 4),
+        # per part-step: the chain kernel and the update (tensor-core path),
+        # or each side's gradient and update on two streams (sparse path);
+        # per sweep four more (posterior sums of W and H, the t counter)
+        "gpu_launches": args.steps * ((2 if tensor_path(wl) else 4) * wl["B"] + 4),
         "clocks": clocks,
         "rmse_after": rmse,
     }
